@@ -1,0 +1,554 @@
+/*
+ * Plain CPU FP64 oracle for the kinetic-fluid parareal method of Laidin & Rey
+ * (arXiv 2502.02704).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * CPU-baseline / reference leg may load this.  The CUDA library never links or
+ * calls it and the two share no code.
+ *
+ * What is followed, function by function:
+ *   velocity grid           Sec. 3 (finite-volume cells K_ij, uniform cubes on [-L,L]^3),
+ *                           nodes at the cube centres
+ *   or_lift                 Def. 2 and the discrete lifting, Eq. (17)
+ *   or_project              Def. 1 and the discrete projection, Eq. (18)
+ *   or_fine_step            the IMEX scheme, Eqs. (11)-(13): explicit x-transport with
+ *                           the upwind flux (flux limiter of Sec. 3.1 as MUSCL-minmod),
+ *                           moments of the transported f (explicit by conservation),
+ *                           implicit BGK relaxation of Eq. (7)
+ *   or_coarse_run           Euler system Eq. (14), explicit update Eq. (15) with the
+ *                           Rusanov flux Eq. (16), CFL-limited local steps (Sec. 2.2)
+ *   or_parareal             Algorithm 1 (alg=1) and Algorithm 2 (alg=2), stopping
+ *                           error of Eq. (10)
+ *
+ * Readings of garbled or silent passages (each also noted where it is used):
+ *   R1  upwind flux sign: F_{i+1/2} = v^+ f_i - v^- f_{i+1} with v^- = -min(v,0) >= 0
+ *       (Eq. 13 prints a plus sign, which would not be upwind).
+ *   R2  the missing 1/dx in Eq. (12) and dt/dx in Eq. (15) are inserted.
+ *   R3  tau = 1: the relaxation rate is 1/eps (Eq. 7 leaves tau unspecified).
+ *   R4  Rusanov flux: (h(V_i)+h(V_{i+1}))/2 - S (V_{i+1}-V_i)/2 on conserved V
+ *       (Eq. 16 prints a difference of h and U in place of V).
+ *   R5  sound speed: sqrt(5 theta/3) (gamma = 5/3 of the monoatomic Euler system,
+ *       Eq. 5) by default; the printed sqrt(theta) is selectable.
+ *   R6  parareal state corrected and stored in conserved variables.
+ *   R7  error = max over slices, cells and the 5 conserved components of |dV|.
+ *   R8  parareal correction in the standard form of the ODE statement in Sec. 1:
+ *       U^{n,k} = G(U^{n-1,k}) + PFL(U^{n-1,k-1}) - G(U^{n-1,k-1}); at iteration k
+ *       Algorithm 2 recomputes only the slices n >= k.
+ *   R9  fine steps per slice: n_f = ceil(dT_g / dt_stab), dt_stab = cfl dx / max|v_x|,
+ *       uniform dt = dT_g / n_f inside the slice.
+ *   R10 MUSCL: minmod slopes, forward Euler in time.
+ *   R11 boundary ghosts: periodic wrap; outflow (the paper's "absorbing") copies the
+ *       boundary cell; reflecting mirrors the cell and reverses v_x.
+ *   R12 a non-positive density or temperature is an error (no clamping).
+ */
+#include "pr_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;
+
+void or_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int or_get_threads(void) { return g_threads; }
+
+/* Velocity cell centres on [-L, L] with nv uniform cells (Sec. 3, cubes V_j). */
+void or_velocity_nodes(int nv, double L, double* v)
+{
+    double dv = 2.0 * L / nv;
+    for (int j = 0; j < nv; ++j) v[j] = -L + (j + 0.5) * dv;
+}
+
+/* Conserved variables of the Euler system, Eq. (14): V = (rho, rho u, E),
+ * E = rho |u|^2 / 2 + 3 rho theta / 2 (Eq. 5 with d_v = 3). */
+void or_prim_to_cons(int nx, const double* U, double* V)
+{
+    for (int i = 0; i < nx; ++i) {
+        double rho = U[0 * nx + i], ux = U[1 * nx + i], uy = U[2 * nx + i];
+        double uz = U[3 * nx + i], th = U[4 * nx + i];
+        V[0 * nx + i] = rho;
+        V[1 * nx + i] = rho * ux;
+        V[2 * nx + i] = rho * uy;
+        V[3 * nx + i] = rho * uz;
+        V[4 * nx + i] = 0.5 * rho * (ux * ux + uy * uy + uz * uz) + 1.5 * rho * th;
+    }
+}
+
+int or_cons_to_prim(int nx, const double* V, double* U)
+{
+    int bad = 0;
+    for (int i = 0; i < nx; ++i) {
+        double rho = V[0 * nx + i];
+        double ux = V[1 * nx + i] / rho, uy = V[2 * nx + i] / rho, uz = V[3 * nx + i] / rho;
+        double th = (2.0 * V[4 * nx + i] / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+        if (!(rho > 0.0) || !(th > 0.0)) bad = 1;
+        U[0 * nx + i] = rho;
+        U[1 * nx + i] = ux;
+        U[2 * nx + i] = uy;
+        U[3 * nx + i] = uz;
+        U[4 * nx + i] = th;
+    }
+    return bad ? OR_ENONPHYS : OR_OK;
+}
+
+static int check_kin(const or_kin* k)
+{
+    if (!k || k->nx < 1 || k->nv < 1 || !(k->L > 0.0) || !(k->x1 > k->x0)) return OR_EINVAL;
+    if (k->bc < 0 || k->bc > 2 || k->scheme < 0 || k->scheme > 1) return OR_EINVAL;
+    if (!(k->eps > 0.0)) return OR_EINVAL;
+    /* MUSCL needs two ghost cells; a reflecting wall can only mirror them
+     * from two interior cells. */
+    if (k->scheme == OR_MUSCL && k->bc == OR_BC_REFLECT && k->nx < 2) return OR_EINVAL;
+    return OR_OK;
+}
+
+/* Discrete lifting, Eq. (17): pointwise Maxwellian of Eq. (4) at the velocity
+ * nodes, evaluated directly with exp (no factorisation). */
+int or_lift(const or_kin* k, const double* U, double* f)
+{
+    int rc = check_kin(k);
+    if (rc) return rc;
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv;
+    double* v = malloc(sizeof(double) * nv);
+    if (!v) return OR_ENOMEM;
+    or_velocity_nodes(nv, k->L, v);
+    const double pi = 3.14159265358979323846;
+    int bad = 0;
+    for (int i = 0; i < nx; ++i) {
+        double rho = U[0 * nx + i], ux = U[1 * nx + i], uy = U[2 * nx + i];
+        double uz = U[3 * nx + i], th = U[4 * nx + i];
+        if (!(rho > 0.0) || !(th > 0.0)) bad = 1;
+        double pref = rho / pow(2.0 * pi * th, 1.5);
+        for (int jx = 0; jx < nv; ++jx)
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    double cx = v[jx] - ux, cy = v[jy] - uy, cz = v[jz] - uz;
+                    double c2 = cx * cx + cy * cy + cz * cz;
+                    f[(long)i * nv3 + ((long)jx * nv + jy) * nv + jz] = pref * exp(-c2 / (2.0 * th));
+                }
+    }
+    free(v);
+    return bad ? OR_ENONPHYS : OR_OK;
+}
+
+/* Moments of one x column by the first-order quadrature of Eq. (18), summed in
+ * lexicographic (jx, jy, jz) order: rho = sum f dv^3, rho u = sum v f dv^3,
+ * 3 rho theta = sum |v - u|^2 f dv^3 (two passes: u first, then theta). */
+static void column_moments(int nv, const double* v, double dv3, const double* fc,
+                           double* rho, double* u, double* th)
+{
+    double s0 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int jx = 0; jx < nv; ++jx)
+        for (int jy = 0; jy < nv; ++jy)
+            for (int jz = 0; jz < nv; ++jz) {
+                double fv = fc[((long)jx * nv + jy) * nv + jz];
+                s0 += fv * dv3;
+                sx += v[jx] * fv * dv3;
+                sy += v[jy] * fv * dv3;
+                sz += v[jz] * fv * dv3;
+            }
+    double r = s0;
+    double ux = sx / r, uy = sy / r, uz = sz / r;
+    double s2 = 0.0;
+    for (int jx = 0; jx < nv; ++jx)
+        for (int jy = 0; jy < nv; ++jy)
+            for (int jz = 0; jz < nv; ++jz) {
+                double fv = fc[((long)jx * nv + jy) * nv + jz];
+                double cx = v[jx] - ux, cy = v[jy] - uy, cz = v[jz] - uz;
+                s2 += (cx * cx + cy * cy + cz * cz) * fv * dv3;
+            }
+    *rho = r;
+    u[0] = ux;
+    u[1] = uy;
+    u[2] = uz;
+    *th = s2 / (3.0 * r);
+}
+
+/* Discrete projection P, Def. 1 / Eq. (18), primitive output [5][nx]. */
+int or_project(const or_kin* k, const double* f, double* U)
+{
+    int rc = check_kin(k);
+    if (rc) return rc;
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv;
+    double* v = malloc(sizeof(double) * nv);
+    if (!v) return OR_ENOMEM;
+    or_velocity_nodes(nv, k->L, v);
+    double dv = 2.0 * k->L / nv, dv3 = dv * dv * dv;
+    int bad = 0;
+    for (int i = 0; i < nx; ++i) {
+        double rho, u[3], th;
+        column_moments(nv, v, dv3, f + (long)i * nv3, &rho, u, &th);
+        if (!(rho > 0.0) || !(th > 0.0)) bad = 1;
+        U[0 * nx + i] = rho;
+        U[1 * nx + i] = u[0];
+        U[2 * nx + i] = u[1];
+        U[3 * nx + i] = u[2];
+        U[4 * nx + i] = th;
+    }
+    free(v);
+    return bad ? OR_ENONPHYS : OR_OK;
+}
+
+int or_project_cons(const or_kin* k, const double* f, double* V)
+{
+    double* U = malloc(sizeof(double) * 5 * k->nx);
+    if (!U) return OR_ENOMEM;
+    int rc = or_project(k, f, U);
+    or_prim_to_cons(k->nx, U, V);
+    free(U);
+    return rc;
+}
+
+/* Value of f at x cell c (possibly a ghost, -2 <= c <= nx+1) and velocity
+ * (jx, jy, jz), through the boundary condition (reading R11). */
+static double ext_value(const or_kin* k, const double* f, long nv3, int c, int jx, int jy, int jz)
+{
+    int nx = k->nx, nv = k->nv;
+    int cc = c, jxx = jx;
+    if (c < 0 || c >= nx) {
+        if (k->bc == OR_BC_PERIODIC) {
+            cc = ((c % nx) + nx) % nx;
+        } else if (k->bc == OR_BC_OUTFLOW) {
+            cc = c < 0 ? 0 : nx - 1;
+        } else { /* reflecting: mirror cell, reversed v_x */
+            cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
+            jxx = nv - 1 - jx;
+        }
+    }
+    return f[(long)cc * nv3 + ((long)jxx * nv + jy) * nv + jz];
+}
+
+static double minmod(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+/* Numerical flux F_{c+1/2} at velocity (jx, jy, jz), Eq. (13) with reading R1;
+ * for MUSCL the interface values are the minmod-limited reconstructions
+ * f_c + sigma_c / 2 (from the left) and f_{c+1} - sigma_{c+1} / 2 (from the right). */
+static double xflux(const or_kin* k, const double* f, long nv3, double vx, int c, int jx, int jy, int jz)
+{
+    double fl, fr;
+    if (k->scheme == OR_UPWIND) {
+        fl = ext_value(k, f, nv3, c, jx, jy, jz);
+        fr = ext_value(k, f, nv3, c + 1, jx, jy, jz);
+    } else {
+        double fm = ext_value(k, f, nv3, c - 1, jx, jy, jz);
+        double f0 = ext_value(k, f, nv3, c, jx, jy, jz);
+        double f1 = ext_value(k, f, nv3, c + 1, jx, jy, jz);
+        double f2 = ext_value(k, f, nv3, c + 2, jx, jy, jz);
+        fl = f0 + 0.5 * minmod(f0 - fm, f1 - f0);
+        fr = f1 - 0.5 * minmod(f1 - f0, f2 - f1);
+    }
+    double vplus = vx > 0.0 ? vx : 0.0;
+    double vminus = vx < 0.0 ? -vx : 0.0;
+    return vplus * fl - vminus * fr;
+}
+
+/* One fine step of the IMEX scheme, Eqs. (11)-(13):
+ *   f*_ij   = f_ij - dt/dx (F_{i+1/2,j} - F_{i-1/2,j})         (explicit transport)
+ *   (rho,u,theta)_i = P(f*_i)                                 (explicit by conservation)
+ *   f^{n+1}_ij = (eps f*_ij + dt M_ij) / (eps + dt)            (implicit BGK, R3)
+ * With E = 0 the velocity flux G of Eq. (13) vanishes.  eps = +inf drops BGK. */
+int or_fine_step(const or_kin* k, double dt, const double* f, double* fout)
+{
+    int rc = check_kin(k);
+    if (rc) return rc;
+    if (!(dt > 0.0)) return OR_EINVAL;
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv;
+    double dx = (k->x1 - k->x0) / nx;
+    double dv = 2.0 * k->L / nv, dv3 = dv * dv * dv;
+    double* v = malloc(sizeof(double) * nv);
+    if (!v) return OR_ENOMEM;
+    or_velocity_nodes(nv, k->L, v);
+    const double pi = 3.14159265358979323846;
+    int collide = isfinite(k->eps);
+    int bad = 0;
+
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads) reduction(| : bad)
+#endif
+    for (int i = 0; i < nx; ++i) {
+        double* out = fout + (long)i * nv3;
+        /* transport */
+        for (int jx = 0; jx < nv; ++jx)
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    double fr = xflux(k, f, nv3, v[jx], i, jx, jy, jz);
+                    double fl = xflux(k, f, nv3, v[jx], i - 1, jx, jy, jz);
+                    long j = ((long)jx * nv + jy) * nv + jz;
+                    out[j] = f[(long)i * nv3 + j] - dt / dx * (fr - fl);
+                }
+        if (!collide) continue;
+        /* moments of f*, then the Maxwellian and the implicit relaxation */
+        double rho, u[3], th;
+        column_moments(nv, v, dv3, out, &rho, u, &th);
+        if (!(rho > 0.0) || !(th > 0.0)) bad = 1;
+        double pref = rho / pow(2.0 * pi * th, 1.5);
+        for (int jx = 0; jx < nv; ++jx)
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    long j = ((long)jx * nv + jy) * nv + jz;
+                    double cx = v[jx] - u[0], cy = v[jy] - u[1], cz = v[jz] - u[2];
+                    double M = pref * exp(-(cx * cx + cy * cy + cz * cz) / (2.0 * th));
+                    out[j] = (k->eps * out[j] + dt * M) / (k->eps + dt);
+                }
+    }
+    free(v);
+    return bad ? OR_ENONPHYS : OR_OK;
+}
+
+int or_fine_run(const or_kin* k, double dt, int nsteps, double* f)
+{
+    int rc = check_kin(k);
+    if (rc) return rc;
+    if (nsteps < 0) return OR_EINVAL;
+    long n = (long)k->nx * k->nv * k->nv * k->nv;
+    double* tmp = malloc(sizeof(double) * n);
+    if (!tmp) return OR_ENOMEM;
+    for (int s = 0; s < nsteps; ++s) {
+        rc = or_fine_step(k, dt, f, tmp);
+        memcpy(f, tmp, sizeof(double) * n);
+        if (rc) break;
+    }
+    free(tmp);
+    return rc;
+}
+
+/* Stable fine step for the x transport: dt_stab = cfl dx / max|v_x|, max|v_x|
+ * being the outermost velocity node (Sec. 2.2, local steps). */
+double or_fine_dt_stab(const or_kin* k, double cfl)
+{
+    double dx = (k->x1 - k->x0) / k->nx;
+    double dv = 2.0 * k->L / k->nv;
+    double vmax = k->L - 0.5 * dv;
+    return cfl * dx / vmax;
+}
+
+/* Reading R9: n_f = ceil(dT_g / dt_stab); a relative slack of 1e-9 keeps an
+ * exact ratio (e.g. 12.000000000000002) from adding a step. */
+int or_fine_nsteps(const or_pr* p, double* dt_out)
+{
+    double dTg = p->T / p->N;
+    int nf = p->nf;
+    if (nf <= 0) {
+        double r = dTg / or_fine_dt_stab(&p->kin, p->cfl_f);
+        nf = (int)ceil(r * (1.0 - 1e-9));
+        if (nf < 1) nf = 1;
+    }
+    if (dt_out) *dt_out = dTg / nf;
+    return nf;
+}
+
+/* ---------------- coarse propagator: Euler, Rusanov (Eqs. 14-16) ---------------- */
+
+static void euler_prim(const double* Vc, double* ux, double* uy, double* uz, double* p, double* th)
+{
+    double rho = Vc[0];
+    *ux = Vc[1] / rho;
+    *uy = Vc[2] / rho;
+    *uz = Vc[3] / rho;
+    *th = (2.0 * Vc[4] / rho - (*ux * *ux + *uy * *uy + *uz * *uz)) / 3.0;
+    *p = rho * *th;
+}
+
+/* Physical flux h(V) of Eq. (14). */
+static void euler_flux(const double* Vc, double* h)
+{
+    double ux, uy, uz, p, th;
+    euler_prim(Vc, &ux, &uy, &uz, &p, &th);
+    h[0] = Vc[1];
+    h[1] = Vc[1] * ux + p;
+    h[2] = Vc[1] * uy;
+    h[3] = Vc[1] * uz;
+    h[4] = ux * (Vc[4] + p);
+}
+
+static double wave_speed(const double* Vc, int sound)
+{
+    double ux, uy, uz, p, th;
+    euler_prim(Vc, &ux, &uy, &uz, &p, &th);
+    double c = sound == OR_SOUND_SQRT_THETA ? sqrt(th) : sqrt(5.0 * th / 3.0);
+    return fabs(ux) + c;
+}
+
+/* Ghost cell value for the fluid state (reading R11; reflecting negates rho u_x). */
+static void ext_state(int nx, int bc, const double* V, int c, double* out)
+{
+    int cc = c, flip = 0;
+    if (c < 0 || c >= nx) {
+        if (bc == OR_BC_PERIODIC) cc = ((c % nx) + nx) % nx;
+        else if (bc == OR_BC_OUTFLOW) cc = c < 0 ? 0 : nx - 1;
+        else {
+            cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
+            flip = 1;
+        }
+    }
+    for (int q = 0; q < 5; ++q) out[q] = V[q * nx + cc];
+    if (flip) out[1] = -out[1];
+}
+
+/* Rusanov flux H_{c+1/2} (reading R4). */
+static void rusanov(int nx, int bc, int sound, const double* V, int c, double* H)
+{
+    double a[5], b[5], ha[5], hb[5];
+    ext_state(nx, bc, V, c, a);
+    ext_state(nx, bc, V, c + 1, b);
+    euler_flux(a, ha);
+    euler_flux(b, hb);
+    double sa = wave_speed(a, sound), sb = wave_speed(b, sound);
+    double S = sa > sb ? sa : sb;
+    for (int q = 0; q < 5; ++q) H[q] = 0.5 * (ha[q] + hb[q]) - 0.5 * S * (b[q] - a[q]);
+}
+
+/* G over dT: explicit Rusanov updates, Eq. (15) with reading R2, local steps
+ * dt = min(cfl dx / max S, remaining) until dT is reached (Sec. 2.2). */
+int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
+                  double dT, const double* Vin, double* Vout, int* nsub)
+{
+    if (nx < 1 || !(x1 > x0) || !(cfl > 0.0) || dT < 0.0) return OR_EINVAL;
+    double dx = (x1 - x0) / nx;
+    double* V = malloc(sizeof(double) * 5 * nx);
+    double* W = malloc(sizeof(double) * 5 * nx);
+    if (!V || !W) {
+        free(V);
+        free(W);
+        return OR_ENOMEM;
+    }
+    memcpy(V, Vin, sizeof(double) * 5 * nx);
+    double t = 0.0;
+    int steps = 0, rc = OR_OK;
+    while (t < dT) {
+        double smax = 0.0;
+        for (int i = 0; i < nx; ++i) {
+            double Vc[5];
+            for (int q = 0; q < 5; ++q) Vc[q] = V[q * nx + i];
+            double ux, uy, uz, p, th;
+            euler_prim(Vc, &ux, &uy, &uz, &p, &th);
+            if (!(Vc[0] > 0.0) || !(th > 0.0)) rc = OR_ENONPHYS;
+            double s = wave_speed(Vc, sound);
+            if (s > smax) smax = s;
+        }
+        if (rc) break;
+        double rem = dT - t;
+        double dt = cfl * dx / smax;
+        int last = 0;
+        if (dt >= rem) {
+            dt = rem;
+            last = 1;
+        }
+        for (int i = 0; i < nx; ++i) {
+            double Hr[5], Hl[5];
+            rusanov(nx, bc, sound, V, i, Hr);
+            rusanov(nx, bc, sound, V, i - 1, Hl);
+            for (int q = 0; q < 5; ++q) W[q * nx + i] = V[q * nx + i] - dt / dx * (Hr[q] - Hl[q]);
+        }
+        memcpy(V, W, sizeof(double) * 5 * nx);
+        ++steps;
+        if (last) break;
+        t += dt;
+    }
+    memcpy(Vout, V, sizeof(double) * 5 * nx);
+    if (nsub) *nsub = steps;
+    free(V);
+    free(W);
+    return rc;
+}
+
+/* ---------------- propagators and the parareal algorithms ---------------- */
+
+/* P F L: lift the conserved state (Eq. 17), n_f fine steps, project (Eq. 18). */
+int or_fine_propagate(const or_pr* p, const double* Vin, double* Vout)
+{
+    const or_kin* k = &p->kin;
+    int nx = k->nx;
+    long n = (long)nx * k->nv * k->nv * k->nv;
+    double dt;
+    int nf = or_fine_nsteps(p, &dt);
+    double* U = malloc(sizeof(double) * 5 * nx);
+    double* f = malloc(sizeof(double) * n);
+    if (!U || !f) {
+        free(U);
+        free(f);
+        return OR_ENOMEM;
+    }
+    int rc = or_cons_to_prim(nx, Vin, U);
+    if (!rc) rc = or_lift(k, U, f);
+    if (!rc) rc = or_fine_run(k, dt, nf, f);
+    if (!rc) rc = or_project_cons(k, f, Vout);
+    free(U);
+    free(f);
+    return rc;
+}
+
+int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout)
+{
+    const or_kin* k = &p->kin;
+    return or_coarse_run(k->nx, k->x0, k->x1, k->bc, p->cfl_g, p->sound, p->T / p->N, Vin, Vout, 0);
+}
+
+/* Algorithms 1 and 2 (reading R8).  U0 is primitive [5][nx].  Uall receives
+ * every level: Uall[(k*(N+1) + n)*5*nx + q*nx + i], conserved, k = 0..K.
+ * errs[k-1] is the Eq. (10) error of iteration k (reading R7).  With tol > 0
+ * the loop stops after the first iteration whose error is below tol; levels
+ * after *k_done are left as copies of level *k_done. */
+int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
+                double* Uall, double* errs, int* k_done)
+{
+    const or_kin* k0 = &p->kin;
+    int rc = check_kin(k0);
+    if (rc) return rc;
+    if (p->N < 1 || K < 0 || (alg != 1 && alg != 2)) return OR_EINVAL;
+    int nx = k0->nx, N = p->N;
+    long lvl = (long)(N + 1) * 5 * nx;
+    double* D = malloc(sizeof(double) * lvl);  /* jumps Delta^n */
+    double* a = malloc(sizeof(double) * 5 * nx);
+    double* b = malloc(sizeof(double) * 5 * nx);
+    if (!D || !a || !b) {
+        free(D);
+        free(a);
+        free(b);
+        return OR_ENOMEM;
+    }
+#define UL(kk, n) (Uall + (long)(kk) * lvl + (long)(n) * 5 * nx)
+    or_prim_to_cons(nx, U0, UL(0, 0));
+    for (int n = 1; n <= N && !rc; ++n) rc = or_coarse_propagate(p, UL(0, n - 1), UL(0, n));
+    int done = 0;
+    for (int k = 1; k <= K && !rc; ++k) {
+        int start = alg == 2 ? k : 1;
+        if (start > N + 1) start = N + 1;
+        for (int n = 0; n < start && n <= N; ++n) memcpy(UL(k, n), UL(k - 1, n), sizeof(double) * 5 * nx);
+        for (int n = start; n <= N && !rc; ++n) {
+            rc = or_fine_propagate(p, UL(k - 1, n - 1), a);
+            if (!rc) rc = or_coarse_propagate(p, UL(k - 1, n - 1), b);
+            for (int q = 0; q < 5 * nx; ++q) D[(long)n * 5 * nx + q] = a[q] - b[q];
+        }
+        for (int n = start; n <= N && !rc; ++n) {
+            rc = or_coarse_propagate(p, UL(k, n - 1), b);
+            for (int q = 0; q < 5 * nx; ++q) UL(k, n)[q] = b[q] + D[(long)n * 5 * nx + q];
+        }
+        double err = 0.0;
+        for (int n = 0; n <= N; ++n)
+            for (int q = 0; q < 5 * nx; ++q) {
+                double d = fabs(UL(k, n)[q] - UL(k - 1, n)[q]);
+                if (d > err) err = d;
+            }
+        if (errs) errs[k - 1] = err;
+        done = k;
+        if (tol > 0.0 && err < tol) break;
+    }
+    for (int k = done + 1; k <= K; ++k) memcpy(UL(k, 0), UL(done, 0), sizeof(double) * lvl);
+#undef UL
+    if (k_done) *k_done = done;
+    free(D);
+    free(a);
+    free(b);
+    return rc;
+}

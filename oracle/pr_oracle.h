@@ -1,0 +1,84 @@
+/*
+ * Plain CPU FP64 oracle for the kinetic-fluid parareal method of Laidin & Rey
+ * (arXiv 2502.02704).  TEST INFRASTRUCTURE ONLY: it is used by tests/, by
+ * __graft_entry__.smoke() and by bench.py's cpu_baseline / reference leg.  The
+ * product path (the CUDA library) never links, loads or calls it, and it shares
+ * no code, header or constant with that path.
+ *
+ * Everything is double precision, naive loops, in the order the paper states
+ * the scheme.  Readings of garbled or silent passages are listed with each
+ * function.  Conventions:
+ *   primitive  U = (rho, u_x, u_y, u_z, theta)   stored [5][nx]
+ *   conserved  V = (rho, rho u_x, rho u_y, rho u_z, E), E = rho|u|^2/2 + 3 rho theta/2
+ *   f[i][j], i = 0..nx-1 (x cell), j = (jx*nv + jy)*nv + jz (velocity cell)
+ */
+#ifndef PR_ORACLE_H
+#define PR_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_OK 0
+#define OR_EINVAL -1
+#define OR_ENOMEM -2
+#define OR_ENONPHYS -5
+
+#define OR_BC_PERIODIC 0
+#define OR_BC_OUTFLOW 1
+#define OR_BC_REFLECT 2
+
+#define OR_UPWIND 0
+#define OR_MUSCL 1
+
+#define OR_SOUND_GAMMA53 0
+#define OR_SOUND_SQRT_THETA 1
+
+typedef struct {
+    int nx;        /* x cells on [x0, x1]                                  */
+    double x0, x1;
+    int bc;        /* OR_BC_*                                              */
+    int nv;        /* velocity cells per direction on [-L, L]^3            */
+    double L;
+    double eps;    /* Knudsen number; +inf means collisionless (no BGK)    */
+    int scheme;    /* OR_UPWIND or OR_MUSCL                                */
+} or_kin;
+
+typedef struct {
+    or_kin kin;
+    double T;      /* final time                                           */
+    int N;         /* number of coarse slices N_g                          */
+    double cfl_f;  /* fine CFL (x transport)                               */
+    double cfl_g;  /* coarse CFL (Rusanov)                                 */
+    int sound;     /* OR_SOUND_*                                           */
+    int nf;        /* fine steps per slice; <= 0: derived from cfl_f       */
+} or_pr;
+
+void or_set_threads(int n);
+int or_get_threads(void);
+
+void or_velocity_nodes(int nv, double L, double* v);
+void or_prim_to_cons(int nx, const double* U, double* V);
+int or_cons_to_prim(int nx, const double* V, double* U);
+
+int or_lift(const or_kin* k, const double* U, double* f);
+int or_project(const or_kin* k, const double* f, double* U);
+int or_project_cons(const or_kin* k, const double* f, double* V);
+
+double or_fine_dt_stab(const or_kin* k, double cfl);
+int or_fine_nsteps(const or_pr* p, double* dt_out);
+int or_fine_step(const or_kin* k, double dt, const double* f, double* fout);
+int or_fine_run(const or_kin* k, double dt, int nsteps, double* f);
+
+int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
+                  double dT, const double* Vin, double* Vout, int* nsub);
+
+int or_fine_propagate(const or_pr* p, const double* Vin, double* Vout);
+int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout);
+
+int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
+                double* Uall, double* errs, int* k_done);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
