@@ -1,0 +1,372 @@
+"""Benchmark: phase-space cell-updates/s of the fused fine kinetic propagator
+(Vlasov-BGK, alpha = 0, E = 0, 1D x 3D v) on one GB300, plus the plain-FP64
+rate and the parareal speedup, as one JSON line.
+
+Workload (one bench step): the smooth periodic fine solve -- Nx = 512,
+32^3 velocities on [-8, 8]^3, MUSCL-minmod transport, rho = 1 + 0.5 sin 2 pi x,
+u_x = 0.2 sin 2 pi x, theta = 1 + 0.2 cos 2 pi x -- for the three Knudsen
+numbers eps = 1, 1e-2, 1e-4 batched as three instances in one persistent
+launch: lift from the macroscopic state, 200 fine steps (dt = 0.5 dx / max|v_x|),
+projection.  value: mixed precision (float32 f, float64 moments), device time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own copy of the workload (weak
+scaling, no data-path collective); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX, NV, L, NSTEPS = 512, 32, 8.0, 200
+EPSS = (1.0, 1e-2, 1e-4)
+METRIC = "phase-space cell-updates/s (FP32 vs FP64) and parareal speedup on 1 GB300"
+UNIT = "cell-updates/s"
+WORKLOAD = "smooth periodic fine solve, Nx=512, 32^3 on [-8,8]^3, MUSCL-minmod, eps in {1,1e-2,1e-4} batched, 200 steps"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_run_traffic.json")
+FINE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "fine.cu")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def _src_hash(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.p = None
+        self.idx = device_index
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_sample(seconds=12.0, max_steps=200):
+    """The FP64 oracle, as it stands, on the host cores: one instance (eps=1e-2)
+    of the workload, stepped until ~`seconds` of CPU time.  Returns (rate, cores, sample)."""
+    import oracle as O
+    from paper_2502_02704_gb300 import workloads as W
+
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    k = O.Kin(nx=NX, nv=NV, L=L, bc=O.BC_PERIODIC, eps=1e-2, scheme=O.MUSCL)
+    dv = 2 * L / NV
+    dt = 0.5 * (1.0 / NX) / (L - 0.5 * dv)
+    f = O.lift(k, W.smooth_periodic(NX))
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps and time.perf_counter() - t0 < seconds:
+        f = O.fine_run(k, dt, 1, f)
+        steps += 1
+    el = time.perf_counter() - t0
+    rate = NX * NV ** 3 * steps / el
+    return rate, cores, f"{steps} fine steps of one instance (eps=1e-2, Nx=512, 32^3, MUSCL) in {el:.1f} s"
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for i in range(args.warmup + args.steps):
+        rate, cores, sample = _cpu_sample(seconds=4.0, max_steps=8)
+        if i >= args.warmup:
+            vals.append(rate)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "per step: up to 8 fine steps of one instance"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _instances(pr, dt):
+    return [pr.instance(NX, NV, dt, L=L, bc=pr.PR_BC_PERIODIC, eps=e, scheme=pr.PR_MUSCL) for e in EPSS]
+
+
+def _time_device(pr, torch, b, Vdev, outs, steps, warmup, stream):
+    """Device-timed bench steps: lift (device state) + 200 steps + projection."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one():
+        for i in range(len(EPSS)):
+            pr.pr_batch_set_initial_device(b, i, Vdev[i], pr.PR_CONSERVED, stream)
+        pr.pr_batch_run(b, NSTEPS, stream)
+        for i in range(len(EPSS)):
+            pr.pr_batch_moments_device(b, i, outs[i], stream)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    pr.pr_batch_kernel_time(b, reset=True)
+    n0 = pr.pr_kernel_launches()
+    ev0.record(stream)
+    for _ in range(steps):
+        one()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    pr.pr_batch_sync(b)
+    ms = ev0.elapsed_time(ev1)
+    kms, kl = pr.pr_batch_kernel_time(b)
+    return ms / steps, kms, pr.pr_kernel_launches() - n0
+
+
+def _parareal_speedup(pr, np):
+    """Sod setup (Nx=64, 16^3, eps=1e-2, outflow, upwind, T=0.1, N=8): plain FP64
+    single-instance serial fine chain U^n = P F L(U^{n-1}) vs mixed-precision
+    batched parareal (Algorithm 2) for several K, with the error of each against
+    the FP64 serial chain."""
+    import torch
+    from paper_2502_02704_gb300 import workloads as W
+
+    nx, nv, N, T = 64, 16, 8, 0.1
+    U0 = W.sod(nx)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    par = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, nv, 8.0, 1e-2, T, N, 0.5, 0.5, pr.PR_UPWIND, pr.PR_MIXED)
+    nf, dtf = pr.pr_fine_steps_per_slice(par)
+    one = pr.pr_batch_create([pr.instance(nx, nv, dtf, L=8.0, bc=pr.PR_BC_OUTFLOW, eps=1e-2, scheme=pr.PR_UPWIND)],
+                             pr.PR_FP64)
+    V0 = np.stack([U0[0], U0[0] * U0[1], U0[0] * U0[2], U0[0] * U0[3],
+                   0.5 * U0[0] * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) + 1.5 * U0[0] * U0[4]])
+    chain = torch.zeros((N + 1, 5, nx), dtype=torch.float64, device=dev)
+    chain[0] = torch.tensor(V0, device=dev)
+    try:
+        def serial():
+            for n in range(1, N + 1):
+                pr.pr_batch_set_initial_device(one, 0, chain[n - 1], pr.PR_CONSERVED, stream)
+                pr.pr_batch_run(one, nf, stream)
+                pr.pr_batch_moments_device(one, 0, chain[n], stream)
+            torch.cuda.synchronize()
+
+        def parareal(K):
+            pr.pr_set_initial(par, U0)
+            pr.pr_parareal_run(par, K)
+            return np.stack([pr.pr_moments(par, n) for n in range(N + 1)])
+
+        serial()
+        t0 = time.perf_counter()
+        serial()
+        t_ser = time.perf_counter() - t0
+        pr.pr_batch_sync(one)
+        ref = chain.cpu().numpy()
+        rows = []
+        for K in (1, 2, 3, 4, 8):
+            parareal(K)
+            t0 = time.perf_counter()
+            got = parareal(K)
+            t = time.perf_counter() - t0
+            err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+            rows.append({"K": K, "ms": t * 1e3, "max_rel_err_vs_fp64_serial": err, "speedup": t_ser / t})
+        return {"workload": "Sod Nx=64, 16^3, eps=1e-2, outflow, upwind, T=0.1, N=8, 12 fine steps/slice",
+                "serial_fp64_ms": t_ser * 1e3, "parareal_mixed": rows,
+                "timing": "wall clock around synchronous calls, includes pr_set_initial (first coarse guess)"}
+    finally:
+        pr.pr_destroy(par)
+        pr.pr_batch_destroy(one)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2502_02704_gb300 as pr
+    from paper_2502_02704_gb300 import build as B
+    from paper_2502_02704_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)  # every timed call and event goes on this stream
+    torch.cuda.set_stream(stream)
+    dv = 2 * L / NV
+    dt = 0.5 * (1.0 / NX) / (L - 0.5 * dv)
+    cells = len(EPSS) * NX * NV ** 3
+    U = W.smooth_periodic(NX)
+    # conserved state for the device-side lift
+    Vnp = np.stack([U[0], U[0] * U[1], U[0] * U[2], U[0] * U[3],
+                    0.5 * U[0] * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) + 1.5 * U[0] * U[4]])
+    Vdev = [torch.tensor(Vnp, dtype=torch.float64, device=dev) for _ in EPSS]
+    outs = [torch.empty((5, NX), dtype=torch.float64, device=dev) for _ in EPSS]
+
+    res = {}
+    for prec in (pr.PR_MIXED, pr.PR_FP64):
+        b = pr.pr_batch_create(_instances(pr, dt), prec)
+        try:
+            if prec == pr.PR_MIXED:
+                with Clocks(local) as ck:
+                    if dist:
+                        dist.barrier()
+                    ms, kms, launches = _time_device(pr, torch, b, Vdev, outs, args.steps, args.warmup, stream)
+                clocks = ck.summary()
+            else:
+                ms, kms, launches = _time_device(pr, torch, b, Vdev, outs, max(1, min(args.steps, 2)), 1, stream)
+            res[prec] = (ms, kms, launches)
+            if prec == pr.PR_MIXED:
+                # end to end through the C ABI with host buffers (H2D of the
+                # primitive state, D2H of the projected moments, every step)
+                for _ in range(max(1, args.warmup)):
+                    for i in range(len(EPSS)):
+                        pr.pr_batch_set_initial(b, i, U)
+                    pr.pr_batch_run(b, NSTEPS)
+                    [pr.pr_batch_moments(b, i) for i in range(len(EPSS))]
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    for i in range(len(EPSS)):
+                        pr.pr_batch_set_initial(b, i, U)
+                    pr.pr_batch_run(b, NSTEPS)
+                    [pr.pr_batch_moments(b, i) for i in range(len(EPSS))]
+                e2e_s = (time.perf_counter() - t0) / args.steps
+        finally:
+            pr.pr_batch_destroy(b)
+
+    ms, kms, launches = res[pr.PR_MIXED]
+    ms64, kms64, _ = res[pr.PR_FP64]
+    if dist:
+        t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    else:
+        e2e_ms = e2e_s * 1e3
+    upd = cells * NSTEPS
+    value = world * upd / (ms * 1e-3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    alg_bytes = 4.0 * (2 * NSTEPS - 1) * cells  # lift-fused first step writes only
+    achieved = alg_bytes / (kms * 1e-3) / 1e9
+    traffic = None
+    try:
+        tj = json.load(open(TRAFFIC_FILE))
+        if tj.get("fine_cu_sha256_16") == _src_hash(FINE_SRC) and tj.get("nsteps") == NSTEPS:
+            traffic = tj["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+    # plain FP64: bound by the FP64 pipe on GB300 (measured DFMA rate)
+    fp64_peak_tflops = 1.01
+    value64 = upd / (ms64 * 1e-3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, sample = _cpu_sample()
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    para = None
+    try:
+        para = _parareal_speedup(pr, np)
+    except Exception as e:  # reported, not hidden
+        para = {"error": repr(e)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances": len(EPSS), "cells_per_step": cells, "fine_steps": NSTEPS,
+                   "precision": "mixed: f32 f, f64 moments/params", "l2": "inputs larger than L2 (384 MiB state)",
+                   "parallelism": f"weak x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "kernel": "k_fine_run (persistent)",
+                     "kernel_ms": kms, "peak_source": "measured" if peaks else "fallback"},
+        "e2e": {"value": world * upd / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": len(EPSS) * 5 * NX * 8, "d2h_bytes_per_step": len(EPSS) * 5 * NX * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "kernel_ms": kms64,
+                 "roofline": {"bound": "alu", "peak_fp64_tflops": fp64_peak_tflops,
+                              "peak_source": "measured DFMA microbenchmark on this pool's GB300"}},
+        "parareal": para,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="omit the host-oracle timing (used only for profiler runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * libpr — GB300 (sm_103a) kinetic-fluid parareal library for the collisional
+ * Vlasov-BGK equation in the hyperbolic scaling (alpha = 0, E = 0), 1D in x and
+ * 3D in v, after Laidin & Rey, arXiv 2502.02704.
+ *
+ * C ABI: every entry point takes plain pointers and sizes and returns an int
+ * status (PR_OK = 0, negative on error).  Nothing aborts or exits.  Objects are
+ * opaque and library-owned; the library allocates its own device memory
+ * (cudaMalloc) when an object is created and frees it in the matching destroy
+ * call.  Host arrays are caller-owned: they are read or written before the call
+ * returns and never retained.  "stream" arguments are cudaStream_t values
+ * passed as void*; NULL selects the object's own stream.  Calls that return
+ * host data synchronise that stream.  Calls that only enqueue work report
+ * device-side errors (time-outs, non-physical states) at the next synchronising
+ * call on the same object.
+ *
+ * Layouts (row-major, float64 unless stated):
+ *   primitive state  U[5][nx] = (rho, u_x, u_y, u_z, theta)         (Def. 1)
+ *   conserved state  V[5][nx] = (rho, rho u_x, rho u_y, rho u_z, E),
+ *                    E = rho |u|^2 / 2 + 3 rho theta / 2             (Eq. 14)
+ *   distribution     f[nx][nv^3], velocity index (jx*nv + jy)*nv + jz, nodes
+ *                    v_j = -L + (j + 1/2) 2L/nv (cube centres, Sec. 3)
+ * x cells are uniform on [x0, x1].  nv must be a multiple of 4 (the kernels move
+ * four consecutive v_z nodes per 16-byte access).
+ *
+ * Readings of the paper that the library implements (same as its oracle):
+ * upwind flux F_{i+1/2} = v+ f_i - v- f_{i+1} (Eq. 13 with v- = -min(v,0) and
+ * the sign that makes it upwind); the 1/dx of Eq. (12) and dt/dx of Eq. (15);
+ * BGK rate 1/eps (tau = 1 in Eq. 7); Rusanov flux (h_i + h_{i+1})/2 -
+ * S (V_{i+1} - V_i)/2 on conserved V (Eq. 16); sound speed sqrt(5 theta/3) by
+ * default; MUSCL = minmod slopes with forward-Euler time stepping; ghost
+ * cells: periodic wrap, outflow copy, specular reflection with v_x reversed.
+ */
+#ifndef PR_H
+#define PR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define PR_OK 0
+#define PR_EINVAL -1     /* bad argument or unsupported combination            */
+#define PR_ENOMEM -2     /* device or host allocation failed                   */
+#define PR_ECUDA -3      /* a CUDA runtime call failed (see pr_*_last_error)   */
+#define PR_ETIMEOUT -4   /* a device-side wait ran out; the launch was aborted */
+#define PR_ENONPHYS -5   /* a density or temperature became <= 0 or NaN        */
+#define PR_ENOTCONV -6   /* parareal reached K iterations above the tolerance  */
+
+/* ---- enumerations ---- */
+#define PR_BC_PERIODIC 0
+#define PR_BC_OUTFLOW 1  /* zero-gradient; the paper's "absorbing" walls        */
+#define PR_BC_REFLECT 2  /* specular walls                                      */
+
+#define PR_UPWIND 0      /* first-order upwind flux, Eq. (13)                   */
+#define PR_MUSCL 1       /* minmod-limited slopes (flux limiter, Sec. 3.1)      */
+
+#define PR_FP64 0        /* f, tables and all arithmetic in float64             */
+#define PR_MIXED 1       /* f and its per-cell arithmetic in float32; velocity
+                            moments beyond a warp, Maxwellian parameters,
+                            projection and parareal sums in float64             */
+
+#define PR_SOUND_GAMMA53 0     /* c = sqrt(5 theta / 3) in the Rusanov speed   */
+#define PR_SOUND_SQRT_THETA 1  /* c = sqrt(theta) as printed below Eq. (16)    */
+
+#define PR_PRIMITIVE 0
+#define PR_CONSERVED 1
+
+/* ---- parameter blocks ---- */
+typedef struct {
+    int nx;            /* x cells (>= 1)                                       */
+    double x0, x1;     /* domain, x1 > x0                                      */
+    int bc;            /* PR_BC_*                                              */
+} pr_grid;
+
+typedef struct {
+    int nv;            /* velocity cells per direction, multiple of 4          */
+    double L;          /* velocity box [-L, L]^3, L > 0                        */
+} pr_velocity;
+
+typedef struct {
+    double T;          /* final time                                           */
+    int n_slices;      /* N_g coarse slices (>= 1)                             */
+    double cfl_f;      /* fine CFL: dt_stab = cfl_f dx / max|v_x| (Sec. 2.2)   */
+    double cfl_g;      /* coarse CFL for the Rusanov local steps               */
+    int scheme;        /* PR_UPWIND or PR_MUSCL                                */
+    int precision;     /* PR_FP64 or PR_MIXED                                  */
+    int sound_speed;   /* PR_SOUND_*                                           */
+    int max_batch;     /* slices whose fine states are resident at once;
+                          0 = all N (the fine phase runs in waves otherwise)  */
+    int nf;            /* fine steps per slice; 0 = ceil(dT_g / dt_stab)       */
+} pr_time;
+
+/* One fine-solve instance of a batch (independent problem). */
+typedef struct {
+    int nx;
+    double x0, x1;
+    int bc;
+    int nv;
+    double L;
+    double eps;        /* Knudsen number > 0; +INFINITY = collisionless        */
+    double dt;         /* fine time step > 0                                   */
+    int scheme;        /* PR_UPWIND or PR_MUSCL                                */
+} pr_instance;
+
+typedef struct pr_ctx pr_ctx;      /* one parareal problem (Algorithm 2)       */
+typedef struct pr_batch pr_batch;  /* independent fine-solve instances         */
+
+/* ======================= parareal problem (Sec. 2) ======================= */
+
+/* Create a parareal problem: grid, velocity box, Knudsen number eps and the
+ * time grid T^n = n T/N (Sec. 2.2).  Allocates every device buffer: N slice
+ * states (or max_batch of them), the iterates U^{n,k} (conserved), the fine
+ * results P F L(U^{n-1}) and the coarse results G(U^{n-1}).  *out is NULL on
+ * failure.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
+int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps,
+            const pr_time* t);
+
+/* Free everything owned by ctx (NULL is accepted). */
+int pr_destroy(pr_ctx* ctx);
+
+/* Last error message of ctx, or of the last failed pr_init when ctx is NULL.
+ * The string stays valid until the next call on ctx. */
+const char* pr_last_error(const pr_ctx* ctx);
+
+/* Set U^{0} from a host primitive state U0[5][nx] and run the first coarse
+ * guess U^{n,0} = G(U^{n-1,0}), n = 1..N (Algorithm 2, before the loop).
+ * Resets the iteration counter k to 0.  Synchronous.
+ * Errors: PR_EINVAL, PR_ENONPHYS, PR_ECUDA. */
+int pr_set_initial(pr_ctx* ctx, const double* U0);
+
+/* Coarse propagator G (Eqs. 14-16) over a time dT >= 0 on host conserved
+ * states Vin/Vout[5][nx] (may alias): explicit Rusanov updates with local steps
+ * dt = min(cfl_g dx / max S, remaining).  Synchronous.
+ * Errors: PR_EINVAL, PR_ENONPHYS, PR_ECUDA. */
+int pr_coarse_step(pr_ctx* ctx, const double* Vin, double* Vout, double dT);
+
+/* Advance the live distribution of slice n (1..N) by nsteps fine steps of
+ * dt = (T/N)/n_f (Eqs. 11-13).  A slice without a live distribution is first
+ * lifted (Eq. 17) from the current iterate U^{n-1}.  Enqueued on stream.
+ * Errors: PR_EINVAL, PR_ECUDA (PR_ETIMEOUT/PR_ENONPHYS at the next sync). */
+int pr_fine_step(pr_ctx* ctx, int slice, int nsteps, void* stream);
+
+/* Moments (Eq. 18) of slice n's live distribution into host out[5][nx], kind
+ * PR_PRIMITIVE or PR_CONSERVED.  Synchronous. */
+int pr_fine_moments(pr_ctx* ctx, int slice, int kind, double* out);
+
+/* Slice n's live distribution f[nx][nv^3] as float64 on the host. */
+int pr_fine_get_f(pr_ctx* ctx, int slice, double* out);
+
+/* One iteration of Algorithm 2 (k <- k+1): lift U^{n-1,k-1}, run n_f fine steps
+ * and project for every slice n = k..N in one batched persistent launch, form
+ * the jumps P F L(U^{n-1,k-1}) - G(U^{n-1,k-1}), then the sequential correction
+ * U^{n,k} = G(U^{n-1,k}) + jump for n = k..N on the device.  *err_out (may be
+ * NULL) receives max_n |U^{n,k} - U^{n,k-1}| over cells and the 5 conserved
+ * components (Eq. 10).  Synchronous when err_out is not NULL.
+ * Errors: PR_EINVAL (called before pr_set_initial), PR_ETIMEOUT, PR_ENONPHYS,
+ * PR_ECUDA. */
+int pr_parareal_iter(pr_ctx* ctx, double* err_out);
+
+/* Iterate until k == K or the error drops below tol (tol <= 0: fixed K).
+ * errs (may be NULL) receives one error per iteration run (length >= K);
+ * *k_done the number of iterations run.  Iterations of the fixed-K loop are
+ * replayed from one captured CUDA graph.  Returns PR_ENOTCONV when tol > 0 and
+ * the last error is still >= tol (the iterates are valid). */
+int pr_parareal_run(pr_ctx* ctx, int K, double tol, int* k_done, double* errs);
+
+/* Current iterate U^{n,k} (n = 0..N) into host out[5][nx]. Synchronous. */
+int pr_moments(pr_ctx* ctx, int n, int kind, double* out);
+
+/* Number of fine steps per slice n_f and the fine step dt (either may be NULL). */
+int pr_fine_steps_per_slice(const pr_ctx* ctx, int* nf, double* dt);
+
+/* Iterations completed since pr_set_initial. */
+int pr_iterations(const pr_ctx* ctx, int* k);
+
+/* ================== batched fine solves (many instances) ================== */
+
+/* Create a batch of n independent fine-solve instances of uneven sizes, all in
+ * one precision.  Each fine step of every instance is the fused transport +
+ * moments + Maxwellian + implicit BGK update of Eqs. (11)-(13).  Allocates two
+ * state buffers per instance plus small tables.  Errors: PR_EINVAL, PR_ENOMEM,
+ * PR_ECUDA. */
+int pr_batch_create(pr_batch** out, const pr_instance* inst, int n, int precision);
+
+int pr_batch_destroy(pr_batch* b);
+
+const char* pr_batch_last_error(const pr_batch* b);
+
+/* Lift instance i from host state U[5][nx_i] (kind PR_PRIMITIVE or
+ * PR_CONSERVED): f = L(U), the pointwise Maxwellian of Eq. (17).  Enqueued on
+ * the batch stream after the host copy. */
+int pr_batch_set_initial(pr_batch* b, int i, const double* U, int kind);
+
+/* Same with a device pointer U_dev[5][nx_i], enqueued on stream. */
+int pr_batch_set_initial_device(pr_batch* b, int i, const double* U_dev, int kind, void* stream);
+
+/* Load an arbitrary distribution f[nx_i][nv_i^3] (host, float64; rounded to
+ * float32 in PR_MIXED). Synchronous. */
+int pr_batch_set_f(pr_batch* b, int i, const double* f);
+
+/* Advance every instance by nsteps fine steps in ONE persistent launch whose
+ * CTAs pull (step, instance, x-tile, v-chunk) work items in step order and
+ * wait on neighbouring tiles of the previous step only.  Enqueued on stream. */
+int pr_batch_run(pr_batch* b, int nsteps, void* stream);
+
+/* Moments (Eq. 18) of instance i into host out[5][nx_i]. Synchronous. */
+int pr_batch_moments(pr_batch* b, int i, int kind, double* out);
+
+/* Conserved moments of instance i into device out_dev[5][nx_i] on stream. */
+int pr_batch_moments_device(pr_batch* b, int i, double* out_dev, void* stream);
+
+/* Distribution of instance i as float64 host f[nx_i][nv_i^3]. Synchronous. */
+int pr_batch_get_f(pr_batch* b, int i, double* out);
+
+/* Wait for the batch stream and report any device-side error. */
+int pr_batch_sync(pr_batch* b);
+
+/* Tile width (x cells per work item) used for instance i, and whether it came
+ * from the autotuner (1) or the default (0). */
+int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned);
+
+/* Time candidate tile widths on the current data with CUDA events and keep the
+ * fastest for each distinct instance shape (the state is saved and restored).
+ * Synchronous. */
+int pr_batch_autotune(pr_batch* b);
+
+/* Average duration in ms of the persistent fine kernel over the launches since
+ * the last reset, measured with CUDA events on the launching stream; reset=1
+ * clears the accumulator.  *launches (may be NULL) gets the launch count. */
+int pr_batch_kernel_time(pr_batch* b, double* avg_ms, int* launches, int reset);
+
+/* Number of kernels the library launched since the last reset (any object). */
+long long pr_kernel_launches(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

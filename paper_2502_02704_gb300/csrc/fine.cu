@@ -1,0 +1,705 @@
+// Fine kinetic propagator of the kinetic-fluid parareal method (Laidin & Rey,
+// arXiv 2502.02704): one fused pass per fine step of the IMEX scheme of
+// Eqs. (11)-(13) -- x-transport (upwind, or minmod-limited MUSCL slopes as the
+// flux limiter of Sec. 3.1), the velocity moments of the transported f (Eq. 18,
+// explicit by conservation), the local Maxwellian (Eq. 4) and the implicit BGK
+// relaxation f^{n+1} = (eps f* + dt M)/(eps + dt) (Eq. 7 with tau = 1).
+//
+// Storage form.  The state after a step is kept as the transported values f*
+// (array g) plus, per x cell, the separable factors of b*M:
+//     f^{n+1}_ij = a g_ij + T0_i[jx] T1_i[jy] T2_i[jz],  a = eps/(eps+dt), b = dt/(eps+dt)
+// with T0 = b rho (2 pi theta)^{-3/2} exp(-(v_x-u_x)^2/(2 theta)), T1, T2 the
+// y/z Gaussians.  This is the same f^{n+1} as the paper's scheme; it is
+// reconstructed on the fly where the next step reads it, so each step reads g
+// once and writes g once and the all-velocity dependency of the moments is
+// resolved at the step boundary instead of inside the pass.  The lifting of
+// Eq. (17) is the same form with a = 0 (f = M), so a slice's first step reads
+// no f at all; the projection of Eq. (18) of the final state is a P(g) + P(M),
+// with P(M) from 1-D sums of the factor tables.
+//
+// Work decomposition.  A work item is (step, instance, x tile of tx cells,
+// v chunk of 1024 velocities).  Each thread owns 4 consecutive v_z nodes (one
+// 16-byte vector in float32) and marches along x with a register window of
+// 2H+1 cells (H = 1 upwind, 2 MUSCL), so every cell of its strip is loaded
+// once (halo cells of the tile twice).  Per x cell the 5 moment sums
+// (rho, rho u, |v|^2 f) are reduced across the warp by shuffles, across warps
+// in float64 shared memory, and written as a per-chunk partial; the last chunk
+// CTA of a tile to finish (arrival counter) sums the partials in a fixed order
+// and writes the factor tables of the next state.  One persistent launch runs
+// all steps of all active instances: CTAs take tickets in step order and an
+// item of step s waits only until the tiles its stencil touches have finished
+// step s-1 (bounded spin on a flag; a time-out aborts the launch with a status
+// code).  Tickets are taken only by running CTAs and an item waits only on
+// smaller tickets, so the lowest unfinished ticket never waits.
+#include <math.h>
+
+#include "pr_kernels.h"
+
+namespace prk {
+
+namespace {
+
+constexpr unsigned long long TIMEOUT_NS = 4000000000ULL;  // 4 s per wait
+constexpr double PI = 3.14159265358979323846;
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_status(const int* p) { return *(volatile const int*)p; }
+
+// ---- 4-wide vector access (16 bytes in float32, 2 x 16 bytes in float64) ----
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4])
+{
+    float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4])
+{
+    double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    double2 b = __ldcg(reinterpret_cast<const double2*>(p + 2));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4])
+{
+    __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4])
+{
+    __stcg(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+    __stcg(reinterpret_cast<double2*>(p + 2), make_double2(v[2], v[3]));
+}
+__device__ __forceinline__ void lds4(const float* p, float (&o)[4])
+{
+    float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&o)[4])
+{
+    double2 a = *reinterpret_cast<const double2*>(p);
+    double2 b = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+__device__ __forceinline__ float exp_neg(float, double arg) { return expf(-(float)arg); }
+__device__ __forceinline__ double exp_neg(double, double arg) { return exp(-arg); }
+
+// Boundary mapping of an x cell index c (ghosts -2..nx+1) to a stored cell and
+// whether v_x is reversed (specular wall).  Periodic wraps, outflow copies the
+// boundary cell (zero gradient), reflecting mirrors the cell.
+__device__ __forceinline__ int map_col(int c, int nx, int bc, bool& flip)
+{
+    flip = false;
+    if (c >= 0 && c < nx) return c;
+    if (bc == 0) return ((c % nx) + nx) % nx;
+    if (bc == 1) return c < 0 ? 0 : nx - 1;
+    flip = true;
+    return c < 0 ? -1 - c : 2 * nx - 1 - c;
+}
+
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b)
+{
+    if (a * b <= T(0)) return T(0);
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+// Upwind interface value at the face between f0 and f1 (neighbours fm, f2):
+// from the left (f0 side) when v_x > 0, from the right otherwise (Eq. 13 with
+// the upwind sign); MUSCL adds half the minmod slope of the upwind cell.
+template <typename T, int H>
+__device__ __forceinline__ T face_value(T fm, T f0, T f1, T f2, bool pos)
+{
+    if (H == 1) return pos ? f0 : f1;
+    T d0 = f0 - fm, d1 = f1 - f0, d2 = f2 - f1;
+    T ua = pos ? d0 : d1, ub = pos ? d1 : d2;
+    T base = pos ? f0 : f1;
+    T sg = pos ? T(0.5) : T(-0.5);
+    return base + sg * minmod(ua, ub);
+}
+
+// Shared-memory layout helpers.
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Finalise per-column parameters into factor tables and projected moments.
+// par[i*8 + 0..4] = (u_x, u_y, u_z, theta, weight*rho*(2 pi theta)^{-3/2}),
+// mom[i*5 + 0..4] = sums over v of (g, v_x g, v_y g, v_z g, |v|^2 g) (no dv^3),
+// wg = weight of g in the state.  Writes tables tout[(c0+i)][3][nv] and the
+// conserved moments Ucur (and Uout when given) of f = wg g + M_tab.
+template <typename T>
+__device__ void tables_and_projection(const Inst& I, int c0, int ncols, const double* par,
+                                      const double* mom, double wg, T* tout, T* tb, double* Uout)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nv = I.nv, tw = 3 * nv;
+    for (int idx = tid; idx < ncols * tw; idx += THREADS) {
+        int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
+        double vj = -I.L + (j + 0.5) * I.dv;
+        double u = par[i * 8 + d], th = par[i * 8 + 3];
+        double dvu = vj - u;
+        T val = exp_neg(T(0), dvu * dvu / (2.0 * th));
+        if (d == 0) val = (T)(par[i * 8 + 4] * (double)val);
+        tb[idx] = val;
+        tout[(size_t)(c0 + i) * tw + rem] = val;
+    }
+    __syncthreads();
+    for (int i = warp; i < ncols; i += WARPS) {
+        double gs[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gs[d][0] = gs[d][1] = gs[d][2] = 0.0;
+        for (int j = lane; j < nv; j += 32) {
+            double vj = -I.L + (j + 0.5) * I.dv;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double t = (double)tb[(i * 3 + d) * nv + j];
+                gs[d][0] += t;
+                gs[d][1] += vj * t;
+                gs[d][2] += vj * vj * t;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int o = 16; o; o >>= 1) gs[d][m] += __shfl_xor_sync(0xffffffffu, gs[d][m], o);
+        if (lane == 0) {
+            const double dv3 = I.dv3;
+            double x0 = gs[0][0], y0 = gs[1][0], z0 = gs[2][0];
+            double V[5];
+            V[0] = dv3 * x0 * y0 * z0;
+            V[1] = dv3 * gs[0][1] * y0 * z0;
+            V[2] = dv3 * x0 * gs[1][1] * z0;
+            V[3] = dv3 * x0 * y0 * gs[2][1];
+            V[4] = 0.5 * dv3 * (gs[0][2] * y0 * z0 + x0 * gs[1][2] * z0 + x0 * y0 * gs[2][2]);
+            if (wg != 0.0) {
+                V[0] += wg * mom[i * 5 + 0] * dv3;
+                V[1] += wg * mom[i * 5 + 1] * dv3;
+                V[2] += wg * mom[i * 5 + 2] * dv3;
+                V[3] += wg * mom[i * 5 + 3] * dv3;
+                V[4] += wg * 0.5 * mom[i * 5 + 4] * dv3;
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                I.Ucur[(size_t)q * I.nx + c0 + i] = V[q];
+                if (Uout) Uout[(size_t)q * I.nx + c0 + i] = V[q];
+            }
+        }
+    }
+}
+
+// Maxwellian parameters from moment sums (rho, m, |v|^2 sums without dv^3):
+// u = m/rho, theta = (sum|v|^2 f / rho - |u|^2)/3 (= Eq. 18's 3 rho theta).
+__device__ __forceinline__ void prim_from_sums(const double* s, double dv3, double weight, double* par,
+                                               int* status)
+{
+    double rho = s[0] * dv3;
+    double ux = s[1] * dv3 / rho, uy = s[2] * dv3 / rho, uz = s[3] * dv3 / rho;
+    double th = (s[4] * dv3 / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
+    double tp = 2.0 * PI * th;
+    par[0] = ux;
+    par[1] = uy;
+    par[2] = uz;
+    par[3] = th;
+    par[4] = weight * rho / (tp * sqrt(tp));
+}
+
+// Last CTA of a tile: sum the chunk partials of step s (fixed order), build
+// the Maxwellian of the new state, its tables and projected moments, release.
+template <typename T>
+__device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, int ncols, int pout,
+                              unsigned char* smem, int* status)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* mom = reinterpret_cast<double*>(smem);  // [MAX_TX][5]
+    double* par = mom + MAX_TX * 5;                  // [MAX_TX][8]
+    T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);   // [MAX_TX][3][nv]
+    for (int i = warp; i < ncols; i += WARPS) {
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        const double* p = I.part + (size_t)(c0 + i) * I.n_vc * 5;
+        for (int v = lane; v < I.n_vc; v += 32)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) acc[q] += __ldcg(p + v * 5 + q);
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) mom[i * 5 + q] = acc[q];
+    }
+    __syncthreads();
+    for (int i = tid; i < ncols; i += THREADS) prim_from_sums(mom + i * 5, I.dv3, I.b, par + i * 8, status);
+    __syncthreads();
+    T* tout = reinterpret_cast<T*>(I.tab[pout]);
+    tables_and_projection<T>(I, c0, ncols, par, mom, I.a, tout, tb, s == nsteps ? I.Uout : nullptr);
+    __syncthreads();
+    __threadfence();
+    if (tid == 0) {
+        I.arrive[xt] = 0u;
+        __threadfence();
+        st_release(I.done + xt, (unsigned)s);
+    }
+}
+
+// Wait until every tile in deps[xt] has finalised step `target` (thread 0).
+__device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status)
+{
+    const int* d = I.deps + xt * MAXDEP;
+    const unsigned long long t0 = gtimer();
+    for (int k = 0; k < MAXDEP; ++k) {
+        int tile = d[k];
+        if (tile < 0) break;
+        const unsigned* p = I.done + tile;
+        unsigned ns = 32;
+        while (ld_acquire(p) < target) {
+            if (ld_status(status) != 0) return false;
+            if (gtimer() - t0 > TIMEOUT_NS) {
+                atomicCAS(status, 0, ST_TIMEOUT);
+                return false;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+        }
+    }
+    return true;
+}
+
+// One work item: transport + moments for x cells [c0, c1) and one v chunk.
+template <typename T, int H>
+__device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, int xt, int vc,
+                          unsigned char* smem, int* status)
+{
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = I.nx, nv = I.nv, ldv = I.ldv, bc = I.bc, tw = 3 * nv;
+    const int c0 = xt * I.tx, c1 = min(nx, c0 + I.tx), ncols = c1 - c0;
+    const int ne = ncols + 2 * H;
+    const int pin = (S.cur + s - 1) & 1, pout = (S.cur + s) & 1;
+    const T* __restrict__ gin = reinterpret_cast<const T*>(I.g[pin]);
+    T* __restrict__ gout = reinterpret_cast<T*>(I.g[pout]);
+    const T* __restrict__ tin = reinterpret_cast<const T*>(I.tab[pin]);
+    const double wgd = (s == 1) ? S.a0 : I.a;
+    const T wg = (T)wgd;
+    const bool use_g = wgd != 0.0;
+
+    T* stab = reinterpret_cast<T*>(smem);  // [ne][3][nv]
+    double* red = reinterpret_cast<double*>(smem + align16((size_t)ne * tw * sizeof(T)));
+
+    for (int idx = tid; idx < ne * tw; idx += THREADS) {
+        int e = idx / tw, rem = idx - e * tw;
+        bool fl;
+        int cc = map_col(c0 - H + e, nx, bc, fl);
+        stab[idx] = __ldcg(tin + (size_t)cc * tw + rem);
+    }
+    __syncthreads();
+
+    const int v0 = vc * CHUNK + tid * VPT;
+    const bool act = v0 < I.nv3;
+    int jx = 0, jy = 0, jz = 0;
+    if (act) {
+        jz = v0 % nv;
+        int q = v0 / nv;
+        jy = q % nv;
+        jx = q / nv;
+    }
+    const int jxf = nv - 1 - jx;
+    const int v0f = (jxf * nv + jy) * nv + jz;
+    const double vxd = -I.L + (jx + 0.5) * I.dv, vyd = -I.L + (jy + 0.5) * I.dv;
+    const bool pos = vxd > 0.0;
+    const T cour = (T)(I.nu * vxd);
+    const T vx = (T)vxd, vy = (T)vyd, vxy2 = (T)(vxd * vxd + vyd * vyd);
+    T vz[4], vz2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double z = -I.L + (jz + q + 0.5) * I.dv;
+        vz[q] = (T)z;
+        vz2[q] = (T)(z * z);
+    }
+
+    // value of the current state at extended column e for this thread's 4 velocities
+    auto recon = [&](int e, T (&o)[4]) {
+        bool fl;
+        int cc = map_col(c0 - H + e, nx, bc, fl);
+        int jxx = fl ? jxf : jx;
+        const T* tb = stab + e * tw;
+        T txy = tb[jxx] * tb[nv + jy];
+        T tz[4];
+        lds4(tb + 2 * nv + jz, tz);
+        if (use_g && act) {
+            T gv[4];
+            ld4(gin + (size_t)cc * ldv + (fl ? v0f : v0), gv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = wg * gv[q] + txy * tz[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = txy * tz[q];
+        }
+    };
+
+    constexpr int WN = 2 * H + 1;
+    T w[WN][4];
+#pragma unroll
+    for (int e = 0; e < 2 * H; ++e) recon(e, w[e]);
+    T sprev[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        sprev[q] = H == 2 ? face_value<T, H>(w[0][q], w[1][q], w[2][q], w[3][q], pos)
+                          : face_value<T, H>(T(0), w[0][q], w[1][q], T(0), pos);
+
+    for (int i = 0; i < ncols; ++i) {
+        recon(i + 2 * H, w[2 * H]);
+        T fs[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T snext = H == 2 ? face_value<T, H>(w[1][q], w[2][q], w[3][q], w[4][q], pos)
+                             : face_value<T, H>(T(0), w[1][q], w[2][q], T(0), pos);
+            fs[q] = w[H][q] - cour * (snext - sprev[q]);
+            sprev[q] = snext;
+        }
+        T r[5];
+        if (act) {
+            st4(gout + (size_t)(c0 + i) * ldv + v0, fs);
+            T s0 = (fs[0] + fs[1]) + (fs[2] + fs[3]);
+            T s1 = vz[0] * fs[0] + vz[1] * fs[1] + vz[2] * fs[2] + vz[3] * fs[3];
+            T s2 = vz2[0] * fs[0] + vz2[1] * fs[1] + vz2[2] * fs[2] + vz2[3] * fs[3];
+            r[0] = s0;
+            r[1] = vx * s0;
+            r[2] = vy * s0;
+            r[3] = s1;
+            r[4] = vxy2 * s0 + s2;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) r[q] = T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int o = 16; o; o >>= 1) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) red[(i * WARPS + warp) * 5 + q] = (double)r[q];
+#pragma unroll
+        for (int e = 0; e < 2 * H; ++e)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[e][q] = w[e + 1][q];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ncols * 5; idx += THREADS) {
+        int i = idx / 5, q = idx - i * 5;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < WARPS; ++k) acc += red[(i * WARPS + k) * 5 + q];
+        I.part[((size_t)(c0 + i) * I.n_vc + vc) * 5 + q] = acc;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        unsigned prev = atomicAdd(I.arrive + xt, 1u);
+        s_last = prev == (unsigned)(I.n_vc - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        finalize_tile<T>(I, s, nsteps, xt, c0, ncols, pout, smem, status);
+    }
+    __syncthreads();
+}
+
+template <typename T, int SCHEME>
+__global__ void __launch_bounds__(THREADS, 2)
+k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
+           const long long* __restrict__ prefix, const Active* __restrict__ active, int nsteps,
+           unsigned long long* ticket, int* status, int waits)
+{
+    constexpr int H = SCHEME == 1 ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_t;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    const int ib = active->begin, ie = active->end;
+    if (ib >= ie || nsteps <= 0) return;
+    const long long base = prefix[ib];
+    const long long W = prefix[ie] - base;
+    const long long total = W * nsteps;
+    for (;;) {
+        if (tid == 0) {
+            long long t = (long long)atomicAdd(ticket, 1ULL);
+            if (ld_status(status) != 0) t = total;
+            s_t = t;
+        }
+        __syncthreads();
+        const long long t = s_t;
+        if (t >= total) break;
+        const int s = (int)(t / W) + 1;
+        const long long r = base + t % W;
+        int lo = ib, hi = ie - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        const Inst& I = insts[lo];
+        const int loc = (int)(r - prefix[lo]);
+        const int xt = loc / I.n_vc, vc = loc - xt * I.n_vc;
+        if (waits && s > 1) {
+            if (tid == 0) s_ok = wait_tiles(I, xt, (unsigned)(s - 1), status) ? 1 : 0;
+            __syncthreads();
+            if (!s_ok) break;
+        }
+        fine_item<T, H>(I, st[lo], s, nsteps, xt, vc, smem, status);
+    }
+}
+
+// Lift (Eq. 17): one CTA per (instance, x tile); tables of M[U_in] into
+// tab[cur] with weight 1, moments of M into Ucur, a0 = 0.
+template <typename T>
+__global__ void __launch_bounds__(THREADS)
+k_lift(const Inst* __restrict__ insts, InstState* st, const Active* __restrict__ active, int max_tiles,
+       int* status)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b = active->begin + blockIdx.y;
+    if (b >= active->end) return;
+    const Inst& I = insts[b];
+    const int xt = blockIdx.x;
+    if (xt >= I.n_xt) return;
+    const int c0 = xt * I.tx, ncols = min(I.nx, c0 + I.tx) - c0;
+    double* mom = reinterpret_cast<double*>(smem);
+    double* par = mom + MAX_TX * 5;
+    T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);
+    for (int i = threadIdx.x; i < ncols; i += THREADS) {
+        const int c = c0 + i, nx = I.nx;
+        double rho = I.Uin[c], mx = I.Uin[nx + c], my = I.Uin[2 * nx + c], mz = I.Uin[3 * nx + c];
+        double E = I.Uin[4 * nx + c];
+        double ux = mx / rho, uy = my / rho, uz = mz / rho;
+        double th = (2.0 * E / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+        if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
+        double tp = 2.0 * PI * th;
+        par[i * 8 + 0] = ux;
+        par[i * 8 + 1] = uy;
+        par[i * 8 + 2] = uz;
+        par[i * 8 + 3] = th;
+        par[i * 8 + 4] = rho / (tp * sqrt(tp));
+    }
+    __syncthreads();
+    InstState S = st[b];
+    T* tout = reinterpret_cast<T*>(I.tab[S.cur]);
+    tables_and_projection<T>(I, c0, ncols, par, mom, 0.0, tout, tb, nullptr);
+    if (xt == 0 && threadIdx.x == 0) st[b].a0 = 0.0;
+}
+
+__global__ void k_advance(const Inst* __restrict__ insts, InstState* st, const Active* __restrict__ active,
+                          int nsteps)
+{
+    const int b = active->begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= active->end || nsteps <= 0) return;
+    st[b].cur = (st[b].cur + nsteps) & 1;
+    st[b].a0 = insts[b].a;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS)
+k_materialize(const Inst* __restrict__ insts, const InstState* __restrict__ st, int b, double* out)
+{
+    const Inst& I = insts[b];
+    const InstState S = st[b];
+    const int c = blockIdx.x;
+    const int v = blockIdx.y * CHUNK + threadIdx.x * VPT;
+    if (v >= I.nv3) return;
+    const int nv = I.nv, tw = 3 * nv;
+    const int jz = v % nv, jy = (v / nv) % nv, jx = v / (nv * nv);
+    const T* g = reinterpret_cast<const T*>(I.g[S.cur]) + (size_t)c * I.ldv + v;
+    const T* tb = reinterpret_cast<const T*>(I.tab[S.cur]) + (size_t)c * tw;
+    const T wg = (T)S.a0;
+    T txy = tb[jx] * tb[nv + jy];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        T m = txy * tb[2 * nv + jz + q];
+        T f = S.a0 != 0.0 ? wg * g[q] + m : m;
+        out[(size_t)c * I.nv3 + v + q] = (double)f;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS)
+k_load_f(const Inst* __restrict__ insts, const InstState* __restrict__ st, int b, const double* f)
+{
+    const Inst& I = insts[b];
+    const int c = blockIdx.x;
+    const int v = blockIdx.y * CHUNK + threadIdx.x * VPT;
+    if (v >= I.nv3) return;
+    T* g = reinterpret_cast<T*>(I.g[st[b].cur]) + (size_t)c * I.ldv + v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q] = (T)f[(size_t)c * I.nv3 + v + q];
+}
+
+// Moments of a loaded distribution (float64 accumulation, one CTA per x cell).
+template <typename T>
+__global__ void __launch_bounds__(THREADS)
+k_state_moments(const Inst* __restrict__ insts, InstState* st, int b)
+{
+    const Inst& I = insts[b];
+    const int c = blockIdx.x, nv = I.nv;
+    const T* g = reinterpret_cast<const T*>(I.g[st[b].cur]) + (size_t)c * I.ldv;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int v = threadIdx.x; v < I.nv3; v += THREADS) {
+        const int jz = v % nv, jy = (v / nv) % nv, jx = v / (nv * nv);
+        double vx = -I.L + (jx + 0.5) * I.dv, vy = -I.L + (jy + 0.5) * I.dv, vz = -I.L + (jz + 0.5) * I.dv;
+        double f = (double)g[v];
+        acc[0] += f;
+        acc[1] += vx * f;
+        acc[2] += vy * f;
+        acc[3] += vz * f;
+        acc[4] += (vx * vx + vy * vy + vz * vz) * f;
+    }
+    __shared__ double sred[WARPS][5];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sred[warp][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double t = 0.0;
+        for (int k = 0; k < WARPS; ++k) t += sred[k][threadIdx.x];
+        t *= I.dv3;
+        if (threadIdx.x == 4) t *= 0.5;
+        I.Ucur[(size_t)threadIdx.x * I.nx + c] = t;
+    }
+    if (c == 0 && threadIdx.x == 0) st[b].a0 = 1.0;
+}
+
+template <typename T, int SCHEME>
+void* fine_kernel_ptr()
+{
+    return reinterpret_cast<void*>(&k_fine_run<T, SCHEME>);
+}
+
+}  // namespace
+
+size_t fine_run_smem(int precision, int tx, int nv, int H)
+{
+    size_t es = precision == 0 ? sizeof(double) : sizeof(float);
+    size_t item = align16((size_t)(tx + 2 * H) * 3 * nv * es) + (size_t)tx * WARPS * 5 * sizeof(double);
+    size_t fin = (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es;
+    return item > fin ? item : fin;
+}
+
+size_t lift_smem(int precision, int tx, int nv)
+{
+    size_t es = precision == 0 ? sizeof(double) : sizeof(float);
+    return (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es;
+}
+
+// Dynamic shared memory may use what the static allocation leaves of the opt-in limit.
+static void raise_smem(const void* fn, int max_smem)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+    cudaGetLastError();
+}
+
+void prepare_fine_kernels(int max_smem)
+{
+    raise_smem(fine_kernel_ptr<double, 0>(), max_smem);
+    raise_smem(fine_kernel_ptr<double, 1>(), max_smem);
+    raise_smem(fine_kernel_ptr<float, 0>(), max_smem);
+    raise_smem(fine_kernel_ptr<float, 1>(), max_smem);
+    raise_smem(reinterpret_cast<const void*>(&k_lift<double>), max_smem);
+    raise_smem(reinterpret_cast<const void*>(&k_lift<float>), max_smem);
+}
+
+int fine_run_occupancy(int precision, int scheme, size_t smem, int* blocks_per_sm)
+{
+    void* fn = precision == 0 ? (scheme == 1 ? fine_kernel_ptr<double, 1>() : fine_kernel_ptr<double, 0>())
+                              : (scheme == 1 ? fine_kernel_ptr<float, 1>() : fine_kernel_ptr<float, 0>());
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, THREADS, smem);
+    return (int)e;
+}
+
+cudaError_t launch_fine_run(int precision, int scheme, const Inst* insts, InstState* st,
+                            const long long* prefix, const Active* active, int nsteps,
+                            unsigned long long* ticket, int* status, int waits, int grid, size_t smem,
+                            cudaStream_t s)
+{
+    if (precision == 0) {
+        if (scheme == 1)
+            k_fine_run<double, 1><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
+        else
+            k_fine_run<double, 0><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
+    } else {
+        if (scheme == 1)
+            k_fine_run<float, 1><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
+        else
+            k_fine_run<float, 0><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lift(int precision, const Inst* insts, InstState* st, const Active* active, int max_tiles,
+                        int n_inst_max, size_t smem, int* status, cudaStream_t s)
+{
+    dim3 grid(max_tiles, n_inst_max);
+    if (precision == 0) k_lift<double><<<grid, THREADS, smem, s>>>(insts, st, active, max_tiles, status);
+    else k_lift<float><<<grid, THREADS, smem, s>>>(insts, st, active, max_tiles, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const Inst* insts, InstState* st, const Active* active, int nsteps, int n_inst_max,
+                           cudaStream_t s)
+{
+    int blocks = (n_inst_max + 127) / 128;
+    k_advance<<<blocks, 128, 0, s>>>(insts, st, active, nsteps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_materialize(int precision, const Inst* insts, const InstState* st, int b, const Inst& h,
+                               double* out, cudaStream_t s)
+{
+    dim3 grid(h.nx, h.n_vc);
+    if (precision == 0) k_materialize<double><<<grid, THREADS, 0, s>>>(insts, st, b, out);
+    else k_materialize<float><<<grid, THREADS, 0, s>>>(insts, st, b, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_f(int precision, const Inst* insts, InstState* st, int b, const Inst& h, const double* f,
+                         cudaStream_t s)
+{
+    dim3 grid(h.nx, h.n_vc);
+    size_t es = precision == 0 ? sizeof(double) : sizeof(float);
+    // tables of the loaded state are zero: f = 1 * g + 0
+    cudaError_t e = cudaMemsetAsync(h.tab[0], 0, (size_t)h.nx * 3 * h.nv * es, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h.tab[1], 0, (size_t)h.nx * 3 * h.nv * es, s);
+    if (e != cudaSuccess) return e;
+    if (precision == 0) {
+        k_load_f<double><<<grid, THREADS, 0, s>>>(insts, st, b, f);
+        k_state_moments<double><<<h.nx, THREADS, 0, s>>>(insts, st, b);
+    } else {
+        k_load_f<float><<<grid, THREADS, 0, s>>>(insts, st, b, f);
+        k_state_moments<float><<<h.nx, THREADS, 0, s>>>(insts, st, b);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace prk

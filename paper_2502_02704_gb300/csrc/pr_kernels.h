@@ -1,0 +1,104 @@
+// Device-side descriptors and launch wrappers shared by the kernels (fine.cu,
+// coarse.cu) and the host runtime (runtime.cu).  Internal to libpr.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace prk {
+
+constexpr int THREADS = 256;             // threads per fine-step CTA
+constexpr int VPT = 4;                   // velocities per thread (one 16-byte f32 vector)
+constexpr int CHUNK = THREADS * VPT;     // velocities per work item
+constexpr int WARPS = THREADS / 32;
+constexpr int MAXDEP = 8;                // neighbour tiles an item may wait on
+constexpr int MAX_TX = 64;               // largest tile width (x cells per item)
+
+constexpr int ST_OK = 0;
+constexpr int ST_TIMEOUT = -4;           // = PR_ETIMEOUT
+constexpr int ST_NONPHYS = -5;           // = PR_ENONPHYS
+
+// Static description of one fine-solve instance (written once by the host).
+struct Inst {
+    int nx, nv, nv3, ldv;      // ldv: column stride of f in elements (multiple of 4)
+    int bc, scheme;
+    int tx, n_xt, n_vc;        // tile width, x tiles, v chunks of CHUNK velocities
+    int pad0;
+    double L, dv, dv3, dx, dt, eps;
+    double a, b;               // f^{n+1} = a f* + b M  (a = eps/(eps+dt), b = dt/(eps+dt))
+    double nu;                 // dt/dx
+    void* g[2];                // stored transported state f* (T*), [nx][ldv], ping-pong
+    void* tab[2];              // Maxwellian factor tables (T*), [nx][3][nv]
+    double* part;              // velocity-chunk partial moments [nx][n_vc][5]
+    double* Ucur;              // conserved moments of the current state [5][nx]
+    const double* Uin;         // lift source, conserved [5][nx] (device)
+    double* Uout;              // projection destination after the last step (or null)
+    unsigned int* done;        // [n_xt] last finalised step of each tile (reset per launch)
+    unsigned int* arrive;      // [n_xt] arrivals of v chunks in the current step
+    const int* deps;           // [n_xt][MAXDEP] tiles an item must wait on (-1 padded)
+    long long item0;           // prefix: first item of this instance within a step
+};
+
+// Per-instance dynamic state, updated on the device between launches.
+struct InstState {
+    int cur;                   // buffer index of the state at launch start
+    int pad;
+    double a0;                 // weight of g in that state (0 after a lift, 1 after set_f)
+};
+
+// Work range of one launch.
+struct Active {
+    int begin, end;            // instances [begin, end)
+};
+
+// ---- fine propagator (fine.cu) ----
+// Persistent fused fine-step kernel over the active instances for nsteps steps.
+cudaError_t launch_fine_run(int precision, int scheme, const Inst* insts, InstState* st,
+                            const long long* prefix, const Active* active, int nsteps,
+                            unsigned long long* ticket, int* status, int waits, int grid,
+                            size_t smem, cudaStream_t s);
+int fine_run_occupancy(int precision, int scheme, size_t smem, int* blocks_per_sm);
+size_t fine_run_smem(int precision, int tx, int nv, int H);
+
+// Set the dynamic shared-memory limit of the kernels (called once).
+void prepare_fine_kernels(int max_smem);
+void prepare_coarse_kernels(int max_smem);
+
+// Lift (Eq. 17) into tab[cur], Ucur; st.a0 = 0. One CTA per (active instance, tile).
+cudaError_t launch_lift(int precision, const Inst* insts, InstState* st, const Active* active,
+                        int max_tiles, int n_inst_max, size_t smem, int* status, cudaStream_t s);
+size_t lift_smem(int precision, int tx, int nv);
+
+// After a run: cur <- (cur + nsteps) & 1, a0 <- a.
+cudaError_t launch_advance(const Inst* insts, InstState* st, const Active* active, int nsteps,
+                           int n_inst_max, cudaStream_t s);
+
+// Materialise f = a0 g + M into out (double) [nx][nv3] for instance b.
+cudaError_t launch_materialize(int precision, const Inst* insts, const InstState* st, int b,
+                               const Inst& hinst, double* out, cudaStream_t s);
+
+// Load f (double) into g[cur] of instance b, zero its tables, a0 = 1, Ucur = P(f).
+cudaError_t launch_set_f(int precision, const Inst* insts, InstState* st, int b,
+                         const Inst& hinst, const double* f, cudaStream_t s);
+
+// ---- coarse propagator and parareal sweep (coarse.cu) ----
+struct CoarseParams {
+    int nx, bc, sound;
+    double x0, x1, dx, cfl;
+};
+
+// G over dT for one state (Vin/Vout device [5][nx], may alias).
+cudaError_t launch_coarse(const CoarseParams& p, const double* Vin, double* Vout, double dT,
+                          double* work, int* status, cudaStream_t s);
+
+// Sequential sweep of Algorithm 2 for n = k..N (k read from *dk on the device):
+//   Gv = G(U[n-1]); U[n] = Gv + (k > 0 ? PFL[n] - Gs[n] : 0); Gs[n] = Gv;
+//   err[k] = max |U[n]_new - U[n]_old|.  Then *dk <- k + 1 if bump.
+cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk, double* U,
+                         const double* PFL, double* Gs, double* err, double* work, int* status,
+                         int bump, int* dk_mut, cudaStream_t s);
+
+// Active range for the parareal fine phase: instances [k-1, N) -> wave window.
+cudaError_t launch_set_active(const int* dk, Active* active, int first_slice, int n_inst,
+                              int N, cudaStream_t s);
+
+}  // namespace prk

@@ -1,0 +1,1162 @@
+// Host runtime of libpr: the C ABI of include/pr.h.  Owns device memory, the
+// per-instance descriptors of the fine kernels, the dependency tables of the
+// persistent launch, the parareal iterate buffers and the captured CUDA graph
+// of one Algorithm 2 iteration (Laidin & Rey, arXiv 2502.02704, Sec. 2.2).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "pr.h"
+#include "pr_kernels.h"
+
+using prk::Inst;
+using prk::InstState;
+
+namespace {
+
+std::atomic<long long> g_launches{0};
+std::mutex g_init_mu;
+std::string g_init_error;
+
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool kernels_prepared = false;
+std::mutex g_prep_mu;
+
+int max_optin_smem()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+int sm_count()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v;
+}
+
+// Halo tiles of tile xt: tiles holding the cells [c0-H, c1+H) after the
+// boundary mapping (periodic wrap, outflow clamp, reflecting mirror).
+std::set<int> halo_tiles(int nx, int tx, int bc, int H, int xt)
+{
+    std::set<int> s;
+    int c0 = xt * tx, c1 = std::min(nx, c0 + tx);
+    for (int c = c0 - H; c < c1 + H; ++c) {
+        int cc = c;
+        if (c < 0 || c >= nx) {
+            if (bc == PR_BC_PERIODIC) cc = ((c % nx) + nx) % nx;
+            else if (bc == PR_BC_OUTFLOW) cc = c < 0 ? 0 : nx - 1;
+            else cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
+        }
+        s.insert(cc / tx);
+    }
+    return s;
+}
+
+}  // namespace
+
+// Dependency lists: halo tiles made symmetric (if A reads B's cells then B
+// reads A's), so that waiting on them also orders the ping-pong overwrite.
+static bool build_deps(int nx, int tx, int bc, int H, std::vector<int>& deps)
+{
+    int n_xt = (nx + tx - 1) / tx;
+    std::vector<std::set<int>> d(n_xt);
+    for (int a = 0; a < n_xt; ++a)
+        for (int b : halo_tiles(nx, tx, bc, H, a)) {
+            d[a].insert(b);
+            d[b].insert(a);
+        }
+    deps.assign((size_t)n_xt * prk::MAXDEP, -1);
+    for (int a = 0; a < n_xt; ++a) {
+        if ((int)d[a].size() > prk::MAXDEP) return false;
+        int k = 0;
+        for (int b : d[a]) deps[(size_t)a * prk::MAXDEP + k++] = b;
+    }
+    return true;
+}
+
+// Raise the dynamic shared-memory limit of every kernel to the device maximum
+// once, before any launch or graph capture.
+static void prepare_kernels_once()
+{
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    if (kernels_prepared) return;
+    int smax = max_optin_smem();
+    prk::prepare_fine_kernels(smax);
+    prk::prepare_coarse_kernels(smax);
+    kernels_prepared = true;
+}
+
+// ------------------------------------------------------------------ batch
+
+struct pr_batch {
+    int n = 0, precision = PR_MIXED, scheme = PR_UPWIND, H = 1;
+    size_t es = 4;
+    std::vector<pr_instance> desc;
+    std::vector<Inst> h;
+    std::vector<int> tuned;
+    std::vector<InstState> hstate;
+    Inst* d_inst = nullptr;
+    InstState* d_state = nullptr;
+    long long* d_prefix = nullptr;
+    prk::Active* d_active = nullptr;
+    int* d_deps = nullptr;
+    unsigned char* d_sync = nullptr;
+    size_t sync_bytes = 0;
+    int* d_status = nullptr;
+    unsigned char* pool = nullptr;
+    double* d_stage = nullptr;
+    size_t stage_elems = 0;
+    double* h_pinned = nullptr;
+    cudaStream_t stream = nullptr;
+    int grid = 0;
+    size_t smem = 0, lift_smem = 0;
+    int max_tiles = 1;
+    std::string err;
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double time_ms = 0.0;
+    int time_launches = 0;
+};
+
+static int bfail(pr_batch* b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return code;
+}
+
+#define BCUDA(b, call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return bfail((b), PR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static int validate_instance(const pr_instance& d, std::string& why)
+{
+    char buf[256];
+    if (d.nx < 1) why = "nx must be >= 1";
+    else if (d.nv < 4 || d.nv % 4) why = "nv must be a positive multiple of 4";
+    else if (!(d.x1 > d.x0)) why = "x1 must exceed x0";
+    else if (!(d.L > 0)) why = "L must be > 0";
+    else if (!(d.eps > 0)) why = "eps must be > 0 (or +inf)";
+    else if (!(d.dt > 0) || !std::isfinite(d.dt)) why = "dt must be finite and > 0";
+    else if (d.bc < 0 || d.bc > 2) why = "unknown boundary condition";
+    else if (d.scheme < 0 || d.scheme > 1) why = "unknown scheme";
+    else if (d.scheme == PR_MUSCL && d.bc == PR_BC_REFLECT && d.nx < 2) why = "MUSCL with reflecting walls needs nx >= 2";
+    else return PR_OK;
+    snprintf(buf, sizeof buf, "%s", why.c_str());
+    why = buf;
+    return PR_EINVAL;
+}
+
+static int default_tx(int nx) { return std::min(nx, 32); }
+
+// Fill descriptors for the given tile widths; pool pointers already set.
+static int layout_tiles(pr_batch* b, const std::vector<int>& txs, std::vector<long long>& prefix,
+                        std::vector<int>& deps_all, std::vector<size_t>& deps_off)
+{
+    prefix.assign(b->n + 1, 0);
+    deps_all.clear();
+    deps_off.assign(b->n, 0);
+    b->max_tiles = 1;
+    for (int i = 0; i < b->n; ++i) {
+        Inst& I = b->h[i];
+        I.tx = txs[i];
+        I.n_xt = (I.nx + I.tx - 1) / I.tx;
+        b->max_tiles = std::max(b->max_tiles, I.n_xt);
+        std::vector<int> deps;
+        if (!build_deps(I.nx, I.tx, I.bc, b->H, deps))
+            return bfail(b, PR_EINVAL, "instance %d: tile dependencies exceed %d", i, prk::MAXDEP);
+        deps_off[i] = deps_all.size();
+        deps_all.insert(deps_all.end(), deps.begin(), deps.end());
+        I.item0 = prefix[i];
+        prefix[i + 1] = prefix[i] + (long long)I.n_xt * I.n_vc;
+    }
+    return PR_OK;
+}
+
+static int upload_layout(pr_batch* b, const std::vector<int>& txs)
+{
+    std::vector<long long> prefix;
+    std::vector<int> deps_all;
+    std::vector<size_t> deps_off;
+    int rc = layout_tiles(b, txs, prefix, deps_all, deps_off);
+    if (rc) return rc;
+    BCUDA(b, cudaMemcpy(b->d_deps, deps_all.data(), deps_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    for (int i = 0; i < b->n; ++i) b->h[i].deps = b->d_deps + deps_off[i];
+    BCUDA(b, cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    BCUDA(b, cudaMemcpy(b->d_inst, b->h.data(), b->h.size() * sizeof(Inst), cudaMemcpyHostToDevice));
+    // launch geometry
+    int maxtx = 1, maxnv = 4;
+    for (auto& I : b->h) {
+        maxtx = std::max(maxtx, I.tx);
+        maxnv = std::max(maxnv, I.nv);
+    }
+    b->smem = prk::fine_run_smem(b->precision == PR_FP64 ? 0 : 1, maxtx, maxnv, b->H);
+    b->lift_smem = prk::lift_smem(b->precision == PR_FP64 ? 0 : 1, maxtx, maxnv);
+    if ((int)b->smem > max_optin_smem() || (int)b->lift_smem > max_optin_smem())
+        return bfail(b, PR_EINVAL, "shared memory per CTA (%zu B) exceeds the device limit", b->smem);
+    int per_sm = 0;
+    int e = prk::fine_run_occupancy(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->smem, &per_sm);
+    if (e != 0 || per_sm < 1) return bfail(b, PR_ECUDA, "fine kernel cannot be resident (occupancy %d)", per_sm);
+    long long items = prefix[b->n];
+    b->grid = (int)std::min<long long>((long long)per_sm * sm_count(), std::max<long long>(items, 1));
+    return PR_OK;
+}
+
+static void free_batch(pr_batch* b)
+{
+    if (!b) return;
+    for (auto e : b->ev_pool) cudaEventDestroy(e);
+    for (auto& p : b->ev_pending) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    cudaFree(b->d_inst);
+    cudaFree(b->d_state);
+    cudaFree(b->d_prefix);
+    cudaFree(b->d_active);
+    cudaFree(b->d_deps);
+    cudaFree(b->d_sync);
+    cudaFree(b->d_status);
+    cudaFree(b->pool);
+    cudaFree(b->d_stage);
+    if (b->h_pinned) cudaFreeHost(b->h_pinned);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+static int create_batch(pr_batch** out, const pr_instance* inst, int n, int precision, std::string& err)
+{
+    *out = nullptr;
+    if (!inst || n < 1) {
+        err = "need at least one instance";
+        return PR_EINVAL;
+    }
+    if (precision != PR_FP64 && precision != PR_MIXED) {
+        err = "precision must be PR_FP64 or PR_MIXED";
+        return PR_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) {
+        std::string why;
+        if (validate_instance(inst[i], why)) {
+            err = "instance " + std::to_string(i) + ": " + why;
+            return PR_EINVAL;
+        }
+        if (inst[i].scheme != inst[0].scheme) {
+            err = "all instances of a batch must use the same scheme";
+            return PR_EINVAL;
+        }
+    }
+    prepare_kernels_once();
+    pr_batch* b = new pr_batch();
+    b->n = n;
+    b->precision = precision;
+    b->es = precision == PR_FP64 ? sizeof(double) : sizeof(float);
+    b->scheme = inst[0].scheme;
+    b->H = b->scheme == PR_MUSCL ? 2 : 1;
+    b->desc.assign(inst, inst + n);
+    b->h.resize(n);
+    b->tuned.assign(n, 0);
+    b->hstate.assign(n, InstState{0, 0, 0.0});
+    auto fail = [&](int code, const std::string& m) {
+        err = m;
+        free_batch(b);
+        return code;
+    };
+    // pool layout
+    size_t off = 0, sync_words = 2;  // ticket (u64)
+    std::vector<size_t> o_g0(n), o_g1(n), o_t0(n), o_t1(n), o_part(n), o_U(n), o_Uin(n);
+    std::vector<size_t> o_done(n), o_arr(n);
+    size_t deps_total = 0;
+    for (int i = 0; i < n; ++i) {
+        const pr_instance& d = inst[i];
+        Inst& I = b->h[i];
+        memset(&I, 0, sizeof I);
+        I.nx = d.nx;
+        I.nv = d.nv;
+        I.nv3 = d.nv * d.nv * d.nv;
+        I.ldv = (int)round_up((size_t)I.nv3, 32);
+        I.bc = d.bc;
+        I.scheme = d.scheme;
+        I.n_vc = (I.nv3 + prk::CHUNK - 1) / prk::CHUNK;
+        I.L = d.L;
+        I.dv = 2.0 * d.L / d.nv;
+        I.dv3 = I.dv * I.dv * I.dv;
+        I.dx = (d.x1 - d.x0) / d.nx;
+        I.dt = d.dt;
+        I.eps = d.eps;
+        if (std::isinf(d.eps)) {
+            I.a = 1.0;
+            I.b = 0.0;
+        } else {
+            I.a = d.eps / (d.eps + d.dt);
+            I.b = d.dt / (d.eps + d.dt);
+        }
+        I.nu = d.dt / I.dx;
+        size_t gsz = (size_t)I.nx * I.ldv * b->es, tsz = (size_t)I.nx * 3 * I.nv * b->es;
+        o_g0[i] = off; off = round_up(off + gsz, 256);
+        o_g1[i] = off; off = round_up(off + gsz, 256);
+        o_t0[i] = off; off = round_up(off + tsz, 256);
+        o_t1[i] = off; off = round_up(off + tsz, 256);
+        o_part[i] = off; off = round_up(off + (size_t)I.nx * I.n_vc * 5 * sizeof(double), 256);
+        o_U[i] = off; off = round_up(off + (size_t)5 * I.nx * sizeof(double), 256);
+        o_Uin[i] = off; off = round_up(off + (size_t)5 * I.nx * sizeof(double), 256);
+        int max_xt = (I.nx + 7) / 8;  // room for the smallest tuned tile width
+        max_xt = std::max(max_xt, (I.nx + default_tx(I.nx) - 1) / default_tx(I.nx));
+        o_done[i] = sync_words; sync_words += max_xt;
+        o_arr[i] = sync_words; sync_words += max_xt;
+        deps_total += (size_t)max_xt * prk::MAXDEP;
+        b->stage_elems = std::max(b->stage_elems, (size_t)I.nx * I.nv3);
+    }
+    cudaError_t e = cudaMalloc(&b->pool, std::max<size_t>(off, 256));
+    if (e != cudaSuccess) return fail(PR_ENOMEM, std::string("device pool of ") + std::to_string(off) + " bytes: " + cudaGetErrorString(e));
+    b->sync_bytes = sync_words * 4;
+    if (cudaMalloc(&b->d_sync, b->sync_bytes) != cudaSuccess || cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_inst, sizeof(Inst) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_state, sizeof(InstState) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_prefix, sizeof(long long) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_active, sizeof(prk::Active)) != cudaSuccess ||
+        cudaMalloc(&b->d_deps, sizeof(int) * std::max<size_t>(deps_total, 1)) != cudaSuccess ||
+        cudaMallocHost(&b->h_pinned, sizeof(double) * 64) != cudaSuccess)
+        return fail(PR_ENOMEM, "small device buffers");
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(PR_ECUDA, "stream");
+    cudaMemset(b->pool, 0, off);
+    cudaMemset(b->d_sync, 0, b->sync_bytes);
+    cudaMemset(b->d_status, 0, sizeof(int));
+    unsigned* words = reinterpret_cast<unsigned*>(b->d_sync);
+    for (int i = 0; i < n; ++i) {
+        Inst& I = b->h[i];
+        I.g[0] = b->pool + o_g0[i];
+        I.g[1] = b->pool + o_g1[i];
+        I.tab[0] = b->pool + o_t0[i];
+        I.tab[1] = b->pool + o_t1[i];
+        I.part = reinterpret_cast<double*>(b->pool + o_part[i]);
+        I.Ucur = reinterpret_cast<double*>(b->pool + o_U[i]);
+        I.Uin = reinterpret_cast<const double*>(b->pool + o_Uin[i]);
+        I.Uout = nullptr;
+        I.done = words + o_done[i];
+        I.arrive = words + o_arr[i];
+    }
+    std::vector<int> txs(n);
+    for (int i = 0; i < n; ++i) txs[i] = default_tx(inst[i].nx);
+    int rc = upload_layout(b, txs);
+    if (rc) return fail(rc, b->err);
+    prk::Active all{0, n};
+    if (cudaMemcpy(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_state, b->hstate.data(), sizeof(InstState) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+        return fail(PR_ECUDA, "initial uploads");
+    *out = b;
+    return PR_OK;
+}
+
+static cudaStream_t pick(pr_batch* b, void* s) { return s ? reinterpret_cast<cudaStream_t>(s) : b->stream; }
+
+// Read and clear the device status word (after a synchronisation).
+static int take_status(pr_batch* b, cudaStream_t s)
+{
+    BCUDA(b, cudaStreamSynchronize(s));
+    int st = 0;
+    BCUDA(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        cudaMemset(b->d_status, 0, sizeof(int));
+        cudaMemset(b->d_sync, 0, b->sync_bytes);
+        if (st == PR_ETIMEOUT) return bfail(b, PR_ETIMEOUT, "a device-side wait timed out; the launch was aborted");
+        if (st == PR_ENONPHYS) return bfail(b, PR_ENONPHYS, "non-positive density or temperature (or NaN) encountered");
+        return bfail(b, st, "device status %d", st);
+    }
+    return PR_OK;
+}
+
+static cudaEvent_t get_event(pr_batch* b)
+{
+    if (!b->ev_pool.empty()) {
+        cudaEvent_t e = b->ev_pool.back();
+        b->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void fold_events(pr_batch* b)
+{
+    for (auto& p : b->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.second) == cudaSuccess && cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
+            b->time_ms += ms;
+            b->time_launches += 1;
+        }
+        b->ev_pool.push_back(p.first);
+        b->ev_pool.push_back(p.second);
+    }
+    b->ev_pending.clear();
+}
+
+// Enqueue one persistent run over the active range already set on the device.
+static int enqueue_run(pr_batch* b, int nsteps, int project_out, cudaStream_t s, bool count_timing)
+{
+    (void)project_out;
+    BCUDA(b, cudaMemsetAsync(b->d_sync, 0, b->sync_bytes, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->timing && count_timing) {
+        if (b->ev_pending.size() > 2048) fold_events(b);
+        e0 = get_event(b);
+        e1 = get_event(b);
+        cudaEventRecord(e0, s);
+    }
+    BCUDA(b, prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->d_state, b->d_prefix,
+                                  b->d_active, nsteps, reinterpret_cast<unsigned long long*>(b->d_sync),
+                                  b->d_status, nsteps > 1 ? 1 : 0, b->grid, b->smem, s));
+    if (e1) {
+        cudaEventRecord(e1, s);
+        b->ev_pending.push_back({e0, e1});
+    }
+    BCUDA(b, prk::launch_advance(b->d_inst, b->d_state, b->d_active, nsteps, b->n, s));
+    g_launches += 2;
+    return PR_OK;
+}
+
+static void prim_to_cons_host(int nx, const double* U, double* V)
+{
+    for (int i = 0; i < nx; ++i) {
+        double rho = U[i], ux = U[nx + i], uy = U[2 * nx + i], uz = U[3 * nx + i], th = U[4 * nx + i];
+        V[i] = rho;
+        V[nx + i] = rho * ux;
+        V[2 * nx + i] = rho * uy;
+        V[3 * nx + i] = rho * uz;
+        V[4 * nx + i] = 0.5 * rho * (ux * ux + uy * uy + uz * uz) + 1.5 * rho * th;
+    }
+}
+
+static void cons_to_prim_host(int nx, const double* V, double* U)
+{
+    for (int i = 0; i < nx; ++i) {
+        double rho = V[i];
+        double ux = V[nx + i] / rho, uy = V[2 * nx + i] / rho, uz = V[3 * nx + i] / rho;
+        double th = (2.0 * V[4 * nx + i] / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+        U[i] = rho;
+        U[nx + i] = ux;
+        U[2 * nx + i] = uy;
+        U[3 * nx + i] = uz;
+        U[4 * nx + i] = th;
+    }
+}
+
+static int check_prim(const double* U, int nx)
+{
+    for (int i = 0; i < nx; ++i)
+        if (!(U[i] > 0.0) || !(U[4 * nx + i] > 0.0) || !std::isfinite(U[nx + i]) || !std::isfinite(U[2 * nx + i]) ||
+            !std::isfinite(U[3 * nx + i]))
+            return PR_ENONPHYS;
+    return PR_OK;
+}
+
+static int lift_instances(pr_batch* b, int begin, int end, cudaStream_t s)
+{
+    prk::Active a{begin, end};
+    BCUDA(b, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
+    BCUDA(b, prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->max_tiles,
+                              end - begin, b->lift_smem, b->d_status, s));
+    g_launches += 1;
+    prk::Active all{0, b->n};
+    BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+    return PR_OK;
+}
+
+extern "C" {
+
+int pr_batch_create(pr_batch** out, const pr_instance* inst, int n, int precision)
+{
+    if (!out) return PR_EINVAL;
+    std::string err;
+    int rc = create_batch(out, inst, n, precision, err);
+    if (rc) {
+        std::lock_guard<std::mutex> lk(g_init_mu);
+        g_init_error = err;
+    }
+    return rc;
+}
+
+int pr_batch_destroy(pr_batch* b)
+{
+    if (b) {
+        cudaStreamSynchronize(b->stream);
+        free_batch(b);
+    }
+    return PR_OK;
+}
+
+const char* pr_batch_last_error(const pr_batch* b)
+{
+    if (!b) return g_init_error.c_str();
+    return b->err.c_str();
+}
+
+int pr_batch_set_initial_device(pr_batch* b, int i, const double* U_dev, int kind, void* stream)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !U_dev) return bfail(b, PR_EINVAL, "bad instance index or null state");
+    if (kind != PR_CONSERVED)
+        return bfail(b, PR_EINVAL, "device lifting takes conserved states (PR_CONSERVED)");
+    cudaStream_t s = pick(b, stream);
+    const Inst& I = b->h[i];
+    BCUDA(b, cudaMemcpyAsync(const_cast<double*>(I.Uin), U_dev, sizeof(double) * 5 * I.nx, cudaMemcpyDeviceToDevice, s));
+    return lift_instances(b, i, i + 1, s);
+}
+
+int pr_batch_set_initial(pr_batch* b, int i, const double* U, int kind)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !U) return bfail(b, PR_EINVAL, "bad instance index or null state");
+    if (kind != PR_PRIMITIVE && kind != PR_CONSERVED) return bfail(b, PR_EINVAL, "kind must be primitive or conserved");
+    const Inst& I = b->h[i];
+    std::vector<double> V(5 * I.nx), P(5 * I.nx);
+    if (kind == PR_PRIMITIVE) {
+        memcpy(P.data(), U, sizeof(double) * 5 * I.nx);
+        prim_to_cons_host(I.nx, U, V.data());
+    } else {
+        memcpy(V.data(), U, sizeof(double) * 5 * I.nx);
+        cons_to_prim_host(I.nx, U, P.data());
+    }
+    if (check_prim(P.data(), I.nx)) return bfail(b, PR_ENONPHYS, "initial state has rho <= 0 or theta <= 0");
+    BCUDA(b, cudaMemcpyAsync(const_cast<double*>(I.Uin), V.data(), sizeof(double) * 5 * I.nx, cudaMemcpyHostToDevice,
+                             b->stream));
+    return lift_instances(b, i, i + 1, b->stream);
+}
+
+int pr_batch_set_f(pr_batch* b, int i, const double* f)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !f) return bfail(b, PR_EINVAL, "bad instance index or null f");
+    const Inst& I = b->h[i];
+    size_t cnt = (size_t)I.nx * I.nv3;
+    if (!b->d_stage) BCUDA(b, cudaMalloc(&b->d_stage, sizeof(double) * b->stage_elems));
+    BCUDA(b, cudaMemcpyAsync(b->d_stage, f, sizeof(double) * cnt, cudaMemcpyHostToDevice, b->stream));
+    BCUDA(b, prk::launch_set_f(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, i, I, b->d_stage, b->stream));
+    g_launches += 2;
+    return take_status(b, b->stream);
+}
+
+int pr_batch_run(pr_batch* b, int nsteps, void* stream)
+{
+    if (!b) return PR_EINVAL;
+    if (nsteps < 0) return bfail(b, PR_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return PR_OK;
+    return enqueue_run(b, nsteps, 0, pick(b, stream), true);
+}
+
+int pr_batch_sync(pr_batch* b)
+{
+    if (!b) return PR_EINVAL;
+    return take_status(b, b->stream);
+}
+
+int pr_batch_moments_device(pr_batch* b, int i, double* out_dev, void* stream)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !out_dev) return bfail(b, PR_EINVAL, "bad instance index or null output");
+    const Inst& I = b->h[i];
+    BCUDA(b, cudaMemcpyAsync(out_dev, I.Ucur, sizeof(double) * 5 * I.nx, cudaMemcpyDeviceToDevice, pick(b, stream)));
+    return PR_OK;
+}
+
+int pr_batch_moments(pr_batch* b, int i, int kind, double* out)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !out) return bfail(b, PR_EINVAL, "bad instance index or null output");
+    if (kind != PR_PRIMITIVE && kind != PR_CONSERVED) return bfail(b, PR_EINVAL, "kind must be primitive or conserved");
+    const Inst& I = b->h[i];
+    std::vector<double> V(5 * I.nx);
+    BCUDA(b, cudaMemcpyAsync(V.data(), I.Ucur, sizeof(double) * 5 * I.nx, cudaMemcpyDeviceToHost, b->stream));
+    int rc = take_status(b, b->stream);
+    if (kind == PR_CONSERVED) memcpy(out, V.data(), sizeof(double) * 5 * I.nx);
+    else cons_to_prim_host(I.nx, V.data(), out);
+    return rc;
+}
+
+int pr_batch_get_f(pr_batch* b, int i, double* out)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !out) return bfail(b, PR_EINVAL, "bad instance index or null output");
+    const Inst& I = b->h[i];
+    size_t cnt = (size_t)I.nx * I.nv3;
+    if (!b->d_stage) BCUDA(b, cudaMalloc(&b->d_stage, sizeof(double) * b->stage_elems));
+    BCUDA(b, prk::launch_materialize(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, i, I, b->d_stage, b->stream));
+    g_launches += 1;
+    BCUDA(b, cudaMemcpyAsync(out, b->d_stage, sizeof(double) * cnt, cudaMemcpyDeviceToHost, b->stream));
+    return take_status(b, b->stream);
+}
+
+int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned)
+{
+    if (!b || i < 0 || i >= b->n) return PR_EINVAL;
+    if (tx) *tx = b->h[i].tx;
+    if (tuned) *tuned = b->tuned[i];
+    return PR_OK;
+}
+
+int pr_batch_kernel_time(pr_batch* b, double* avg_ms, int* launches, int reset)
+{
+    if (!b) return PR_EINVAL;
+    b->timing = true;
+    fold_events(b);
+    if (avg_ms) *avg_ms = b->time_launches ? b->time_ms / b->time_launches : 0.0;
+    if (launches) *launches = b->time_launches;
+    if (reset) {
+        b->time_ms = 0.0;
+        b->time_launches = 0;
+    }
+    return PR_OK;
+}
+
+long long pr_kernel_launches(int reset)
+{
+    long long v = g_launches.load();
+    if (reset) g_launches = 0;
+    return v;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ autotuner
+
+// Candidate tile widths are timed with CUDA events on a copy of the current
+// state (saved and restored), one persistent launch of a few steps each; the
+// fastest width is kept for every instance of the same (nx, nv) shape.
+extern "C" int pr_batch_autotune(pr_batch* b)
+{
+    if (!b) return PR_EINVAL;
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    // save state of every instance (g of the current buffer, tables, Ucur, InstState)
+    std::vector<InstState> st(b->n);
+    BCUDA(b, cudaMemcpy(st.data(), b->d_state, sizeof(InstState) * b->n, cudaMemcpyDeviceToHost));
+    size_t total = 0;
+    for (auto& I : b->h) total += (size_t)I.nx * I.ldv * b->es * 2 + (size_t)I.nx * 3 * I.nv * b->es * 2;
+    void* save = nullptr;
+    if (cudaMalloc(&save, total) != cudaSuccess) return bfail(b, PR_ENOMEM, "autotune needs %zu bytes of scratch", total);
+    auto copy_all = [&](bool to_save) {
+        size_t off = 0;
+        for (auto& I : b->h) {
+            size_t gs = (size_t)I.nx * I.ldv * b->es, ts = (size_t)I.nx * 3 * I.nv * b->es;
+            void* ptrs[4] = {I.g[0], I.g[1], I.tab[0], I.tab[1]};
+            size_t sz[4] = {gs, gs, ts, ts};
+            for (int k = 0; k < 4; ++k) {
+                char* sv = static_cast<char*>(save) + off;
+                if (to_save) cudaMemcpy(sv, ptrs[k], sz[k], cudaMemcpyDeviceToDevice);
+                else cudaMemcpy(ptrs[k], sv, sz[k], cudaMemcpyDeviceToDevice);
+                off += sz[k];
+            }
+        }
+    };
+    copy_all(true);
+    const int cands[4] = {8, 16, 32, 64};
+    std::vector<int> best(b->n), cur(b->n);
+    for (int i = 0; i < b->n; ++i) best[i] = cur[i] = b->h[i].tx;
+    double best_ms = 1e300;
+    int best_c = -1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int steps = 4;
+    int rc = PR_OK;
+    for (int ci = 0; ci < 4 && rc == PR_OK; ++ci) {
+        std::vector<int> txs(b->n);
+        for (int i = 0; i < b->n; ++i) txs[i] = std::min(cands[ci], b->h[i].nx);
+        rc = upload_layout(b, txs);
+        if (rc) break;
+        double ms_sum = 0;
+        for (int rep = 0; rep < 2; ++rep) {
+            copy_all(false);
+            cudaMemcpy(b->d_state, st.data(), sizeof(InstState) * b->n, cudaMemcpyHostToDevice);
+            cudaEventRecord(e0, b->stream);
+            rc = enqueue_run(b, steps, 0, b->stream, false);
+            cudaEventRecord(e1, b->stream);
+            if (rc) break;
+            rc = take_status(b, b->stream);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1) ms_sum += ms;
+        }
+        if (rc == PR_OK && ms_sum < best_ms) {
+            best_ms = ms_sum;
+            best_c = ci;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::vector<int> txs(b->n);
+    for (int i = 0; i < b->n; ++i) txs[i] = best_c >= 0 ? std::min(cands[best_c], b->h[i].nx) : default_tx(b->h[i].nx);
+    int rc2 = upload_layout(b, txs);
+    copy_all(false);
+    cudaMemcpy(b->d_state, st.data(), sizeof(InstState) * b->n, cudaMemcpyHostToDevice);
+    cudaFree(save);
+    if (rc == PR_OK && rc2 == PR_OK && best_c >= 0)
+        for (int i = 0; i < b->n; ++i) b->tuned[i] = 1;
+    BCUDA(b, cudaDeviceSynchronize());
+    return rc ? rc : rc2;
+}
+
+// ------------------------------------------------------------------ parareal
+
+struct pr_ctx {
+    pr_grid g;
+    pr_velocity v;
+    double eps = 0;
+    pr_time t;
+    int nx = 0, N = 0, nf = 0, n_res = 0;
+    double dtf = 0, dT = 0;
+    pr_batch* fine = nullptr;
+    double *dU = nullptr, *dPFL = nullptr, *dGs = nullptr, *derr = nullptr, *dwork = nullptr, *dtmp = nullptr;
+    int* dk = nullptr;
+    int* dstatus = nullptr;
+    double* h_pinned = nullptr;
+    prk::CoarseParams cp;
+    int k = 0;
+    bool initialized = false;
+    std::vector<int> live;  // slice whose live f each resident instance holds (0 = none)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool descs_dirty = false;
+    std::string err;
+};
+
+static int cfail(pr_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CCUDA(c, call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return cfail((c), PR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void free_ctx(pr_ctx* c)
+{
+    if (!c) return;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->fine) free_batch(c->fine);
+    cudaFree(c->dU);
+    cudaFree(c->dPFL);
+    cudaFree(c->dGs);
+    cudaFree(c->derr);
+    cudaFree(c->dwork);
+    cudaFree(c->dtmp);
+    cudaFree(c->dk);
+    cudaFree(c->dstatus);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+}
+
+// Point resident instance b at slice n (lift source U^{n-1}, projection PFL^n).
+static void bind_slice(pr_ctx* c, int b, int n)
+{
+    Inst& I = c->fine->h[b];
+    I.Uin = c->dU + (size_t)(n - 1) * 5 * c->nx;
+    I.Uout = c->dPFL + (size_t)n * 5 * c->nx;
+}
+
+static int take_ctx_status(pr_ctx* c)
+{
+    CCUDA(c, cudaStreamSynchronize(c->fine->stream));
+    int st = 0;
+    CCUDA(c, cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    int rc = take_status(c->fine, c->fine->stream);
+    if (st != 0) {
+        cudaMemset(c->dstatus, 0, sizeof(int));
+        return cfail(c, st, st == PR_ENONPHYS ? "coarse propagator met a non-physical state" : "coarse status %d", st);
+    }
+    if (rc) return cfail(c, rc, "%s", c->fine->err.c_str());
+    return PR_OK;
+}
+
+extern "C" {
+
+int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t)
+{
+    auto init_fail = [](int code, const std::string& m) {
+        std::lock_guard<std::mutex> lk(g_init_mu);
+        g_init_error = m;
+        return code;
+    };
+    if (!out) return PR_EINVAL;
+    *out = nullptr;
+    if (!g || !v || !t) return init_fail(PR_EINVAL, "null parameter block");
+    if (t->n_slices < 1) return init_fail(PR_EINVAL, "n_slices must be >= 1");
+    if (!(t->T > 0) || !(t->cfl_f > 0) || !(t->cfl_g > 0)) return init_fail(PR_EINVAL, "T, cfl_f and cfl_g must be > 0");
+    if (t->precision != PR_FP64 && t->precision != PR_MIXED) return init_fail(PR_EINVAL, "bad precision");
+    if (t->sound_speed != PR_SOUND_GAMMA53 && t->sound_speed != PR_SOUND_SQRT_THETA)
+        return init_fail(PR_EINVAL, "bad sound speed");
+    if (t->nf < 0 || t->max_batch < 0) return init_fail(PR_EINVAL, "nf and max_batch must be >= 0");
+    pr_ctx* c = new pr_ctx();
+    c->g = *g;
+    c->v = *v;
+    c->eps = eps;
+    c->t = *t;
+    c->nx = g->nx;
+    c->N = t->n_slices;
+    c->dT = t->T / t->n_slices;
+    // fine steps per slice: n_f = ceil(dT / dt_stab), dt_stab = cfl dx / max|v_x| (Sec. 2.2)
+    double dx = (g->x1 - g->x0) / g->nx, dv = 2.0 * v->L / v->nv, vmax = v->L - 0.5 * dv;
+    if (t->nf > 0) c->nf = t->nf;
+    else {
+        double r = c->dT / (t->cfl_f * dx / vmax);
+        c->nf = std::max(1, (int)std::ceil(r * (1.0 - 1e-9)));
+    }
+    c->dtf = c->dT / c->nf;
+    c->n_res = t->max_batch > 0 ? std::min(t->max_batch, c->N) : c->N;
+    pr_instance d{g->nx, g->x0, g->x1, g->bc, v->nv, v->L, eps, c->dtf, t->scheme};
+    std::vector<pr_instance> descs(c->n_res, d);
+    std::string err;
+    int rc = create_batch(&c->fine, descs.data(), c->n_res, t->precision, err);
+    if (rc) {
+        free_ctx(c);
+        return init_fail(rc, err);
+    }
+    size_t lvl = (size_t)(c->N + 1) * 5 * c->nx * sizeof(double);
+    if (cudaMalloc(&c->dU, lvl) != cudaSuccess || cudaMalloc(&c->dPFL, lvl) != cudaSuccess ||
+        cudaMalloc(&c->dGs, lvl) != cudaSuccess || cudaMalloc(&c->derr, sizeof(double) * (c->N + 2)) != cudaSuccess ||
+        cudaMalloc(&c->dwork, sizeof(double) * 10 * c->nx) != cudaSuccess ||
+        cudaMalloc(&c->dtmp, sizeof(double) * 10 * c->nx) != cudaSuccess || cudaMalloc(&c->dk, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->dstatus, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_pinned, sizeof(double) * (c->N + 2)) != cudaSuccess) {
+        free_ctx(c);
+        return init_fail(PR_ENOMEM, "parareal iterate buffers");
+    }
+    cudaMemset(c->dU, 0, lvl);
+    cudaMemset(c->dPFL, 0, lvl);
+    cudaMemset(c->dGs, 0, lvl);
+    cudaMemset(c->derr, 0, sizeof(double) * (c->N + 2));
+    cudaMemset(c->dk, 0, sizeof(int));
+    cudaMemset(c->dstatus, 0, sizeof(int));
+    c->cp.nx = g->nx;
+    c->cp.bc = g->bc;
+    c->cp.sound = t->sound_speed;
+    c->cp.x0 = g->x0;
+    c->cp.x1 = g->x1;
+    c->cp.dx = dx;
+    c->cp.cfl = t->cfl_g;
+    c->live.assign(c->n_res, 0);
+    for (int b = 0; b < c->n_res; ++b) bind_slice(c, b, b + 1);
+    if (cudaMemcpy(c->fine->d_inst, c->fine->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        free_ctx(c);
+        return init_fail(PR_ECUDA, "descriptor upload");
+    }
+    *out = c;
+    return PR_OK;
+}
+
+int pr_destroy(pr_ctx* c)
+{
+    if (c) {
+        cudaStreamSynchronize(c->fine->stream);
+        free_ctx(c);
+    }
+    return PR_OK;
+}
+
+const char* pr_last_error(const pr_ctx* c)
+{
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+int pr_fine_steps_per_slice(const pr_ctx* c, int* nf, double* dt)
+{
+    if (!c) return PR_EINVAL;
+    if (nf) *nf = c->nf;
+    if (dt) *dt = c->dtf;
+    return PR_OK;
+}
+
+int pr_iterations(const pr_ctx* c, int* k)
+{
+    if (!c || !k) return PR_EINVAL;
+    *k = c->k;
+    return PR_OK;
+}
+
+int pr_set_initial(pr_ctx* c, const double* U0)
+{
+    if (!c) return PR_EINVAL;
+    if (!U0) return cfail(c, PR_EINVAL, "null initial state");
+    if (check_prim(U0, c->nx)) return cfail(c, PR_ENONPHYS, "initial state has rho <= 0 or theta <= 0");
+    std::vector<double> V(5 * c->nx);
+    prim_to_cons_host(c->nx, U0, V.data());
+    cudaStream_t s = c->fine->stream;
+    CCUDA(c, cudaStreamSynchronize(s));
+    CCUDA(c, cudaMemcpy(c->dU, V.data(), sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice));
+    CCUDA(c, cudaMemset(c->dk, 0, sizeof(int)));
+    CCUDA(c, prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
+                               c->dk, s));
+    g_launches += 1;
+    c->k = 0;
+    c->initialized = true;
+    std::fill(c->live.begin(), c->live.end(), 0);
+    return take_ctx_status(c);
+}
+
+int pr_coarse_step(pr_ctx* c, const double* Vin, double* Vout, double dT)
+{
+    if (!c) return PR_EINVAL;
+    if (!Vin || !Vout || !(dT >= 0)) return cfail(c, PR_EINVAL, "null state or negative dT");
+    cudaStream_t s = c->fine->stream;
+    CCUDA(c, cudaMemcpyAsync(c->dtmp, Vin, sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice, s));
+    CCUDA(c, prk::launch_coarse(c->cp, c->dtmp, c->dtmp + 5 * c->nx, dT, c->dwork, c->dstatus, s));
+    g_launches += 1;
+    CCUDA(c, cudaMemcpyAsync(Vout, c->dtmp + 5 * c->nx, sizeof(double) * 5 * c->nx, cudaMemcpyDeviceToHost, s));
+    return take_ctx_status(c);
+}
+
+int pr_fine_step(pr_ctx* c, int slice, int nsteps, void* stream)
+{
+    if (!c) return PR_EINVAL;
+    if (!c->initialized) return cfail(c, PR_EINVAL, "call pr_set_initial first");
+    if (slice < 1 || slice > c->N || nsteps < 0) return cfail(c, PR_EINVAL, "slice must be in 1..N and nsteps >= 0");
+    pr_batch* b = c->fine;
+    cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : b->stream;
+    int bi = (slice - 1) % c->n_res;
+    if (c->live[bi] != slice) {
+        bind_slice(c, bi, slice);
+        Inst tmp = b->h[bi];
+        tmp.Uout = nullptr;  // a free-running slice does not overwrite the parareal fine results
+        CCUDA(c, cudaMemcpyAsync(b->d_inst + bi, &tmp, sizeof(Inst), cudaMemcpyHostToDevice, s));
+        c->descs_dirty = true;
+        int rc = lift_instances(b, bi, bi + 1, s);
+        if (rc) return cfail(c, rc, "%s", b->err.c_str());
+        c->live[bi] = slice;
+    }
+    if (nsteps == 0) return PR_OK;
+    prk::Active a{bi, bi + 1};
+    CCUDA(c, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
+    int rc = enqueue_run(b, nsteps, 0, s, true);
+    prk::Active all{0, b->n};
+    CCUDA(c, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+    if (rc) return cfail(c, rc, "%s", b->err.c_str());
+    return PR_OK;
+}
+
+int pr_fine_moments(pr_ctx* c, int slice, int kind, double* out)
+{
+    if (!c) return PR_EINVAL;
+    if (slice < 1 || slice > c->N) return cfail(c, PR_EINVAL, "slice must be in 1..N");
+    int bi = (slice - 1) % c->n_res;
+    if (c->live[bi] != slice) return cfail(c, PR_EINVAL, "slice %d has no live distribution", slice);
+    int rc = pr_batch_moments(c->fine, bi, kind, out);
+    if (rc) return cfail(c, rc, "%s", c->fine->err.c_str());
+    return PR_OK;
+}
+
+int pr_fine_get_f(pr_ctx* c, int slice, double* out)
+{
+    if (!c) return PR_EINVAL;
+    if (slice < 1 || slice > c->N) return cfail(c, PR_EINVAL, "slice must be in 1..N");
+    int bi = (slice - 1) % c->n_res;
+    if (c->live[bi] != slice) return cfail(c, PR_EINVAL, "slice %d has no live distribution", slice);
+    int rc = pr_batch_get_f(c->fine, bi, out);
+    if (rc) return cfail(c, rc, "%s", c->fine->err.c_str());
+    return PR_OK;
+}
+
+}  // extern "C"
+
+// Enqueue one iteration (k = c->k + 1 on the device counter) without graphs.
+static int enqueue_iteration_plain(pr_ctx* c, int k)
+{
+    pr_batch* b = c->fine;
+    cudaStream_t s = b->stream;
+    int first = std::max(k, 1);
+    for (int w0 = first; w0 <= c->N; w0 += c->n_res) {
+        int cnt = std::min(c->n_res, c->N - w0 + 1);
+        for (int bi = 0; bi < cnt; ++bi) bind_slice(c, bi, w0 + bi);
+        CCUDA(c, cudaMemcpyAsync(b->d_inst, b->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice, s));
+        int rc = lift_instances(b, 0, cnt, s);
+        if (rc) return cfail(c, rc, "%s", b->err.c_str());
+        prk::Active a{0, cnt};
+        CCUDA(c, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
+        rc = enqueue_run(b, c->nf, 1, s, true);
+        if (rc) return cfail(c, rc, "%s", b->err.c_str());
+        prk::Active all{0, b->n};
+        CCUDA(c, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+    }
+    CCUDA(c, prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
+                               c->dk, s));
+    g_launches += 1;
+    return PR_OK;
+}
+
+// The graph of one iteration when all slices are resident: set the active
+// slices from the device counter k, lift them, run n_f fused fine steps in
+// one persistent launch, then the sequential correction sweep (which bumps k).
+static int build_graph(pr_ctx* c)
+{
+    pr_batch* b = c->fine;
+    cudaStream_t s = b->stream;
+    for (int bi = 0; bi < c->n_res; ++bi) bind_slice(c, bi, bi + 1);
+    CCUDA(c, cudaMemcpy(b->d_inst, b->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice));
+    CCUDA(c, cudaStreamSynchronize(s));
+    c->descs_dirty = false;
+    CCUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = prk::launch_set_active(c->dk, b->d_active, 1, c->n_res, c->N, s);
+    if (e == cudaSuccess)
+        e = prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->max_tiles, b->n,
+                             b->lift_smem, b->d_status, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, b->sync_bytes, s);
+    if (e == cudaSuccess)
+        e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->d_state, b->d_prefix,
+                                 b->d_active, c->nf, reinterpret_cast<unsigned long long*>(b->d_sync), b->d_status,
+                                 c->nf > 1 ? 1 : 0, b->grid, b->smem, s);
+    if (e == cudaSuccess)
+        e = prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
+                              c->dk, s);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return cfail(c, PR_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        return cfail(c, PR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    c->graph = gr;
+    c->gexec = ex;
+    return PR_OK;
+}
+
+static int run_iterations(pr_ctx* c, int count, bool use_graph)
+{
+    pr_batch* b = c->fine;
+    for (int it = 0; it < count; ++it) {
+        int k = c->k + 1;
+        if (k > c->N) {
+            // every slice is already exact; the iteration changes nothing (error 0)
+            CCUDA(c, cudaMemsetAsync(c->derr + std::min(k, c->N + 1), 0, sizeof(double), b->stream));
+            c->k = k;
+            continue;
+        }
+        if (use_graph && c->n_res == c->N) {
+            if (!c->gexec || c->descs_dirty) {
+                if (c->gexec) {
+                    cudaGraphExecDestroy(c->gexec);
+                    cudaGraphDestroy(c->graph);
+                    c->gexec = nullptr;
+                    c->graph = nullptr;
+                }
+                int rc = build_graph(c);
+                if (rc) return rc;
+            }
+            CCUDA(c, cudaGraphLaunch(c->gexec, b->stream));
+            g_launches += 5;
+        } else {
+            int rc = enqueue_iteration_plain(c, k);
+            if (rc) return rc;
+        }
+        c->k = k;
+    }
+    std::fill(c->live.begin(), c->live.end(), 0);
+    return PR_OK;
+}
+
+extern "C" {
+
+int pr_parareal_iter(pr_ctx* c, double* err_out)
+{
+    if (!c) return PR_EINVAL;
+    if (!c->initialized) return cfail(c, PR_EINVAL, "call pr_set_initial first");
+    int rc = run_iterations(c, 1, true);
+    if (rc) return rc;
+    if (err_out) {
+        int k = std::min(c->k, c->N + 1);
+        CCUDA(c, cudaMemcpyAsync(c->h_pinned, c->derr + k, sizeof(double), cudaMemcpyDeviceToHost, c->fine->stream));
+        rc = take_ctx_status(c);
+        *err_out = c->h_pinned[0];
+        return rc;
+    }
+    return PR_OK;
+}
+
+int pr_parareal_run(pr_ctx* c, int K, double tol, int* k_done, double* errs)
+{
+    if (!c) return PR_EINVAL;
+    if (!c->initialized) return cfail(c, PR_EINVAL, "call pr_set_initial first");
+    if (K < 0) return cfail(c, PR_EINVAL, "K must be >= 0");
+    int done = 0, rc = PR_OK;
+    double last = 0.0;
+    if (tol > 0) {
+        while (done < K) {
+            double e = 0;
+            rc = pr_parareal_iter(c, &e);
+            if (rc) break;
+            if (errs) errs[done] = e;
+            ++done;
+            last = e;
+            if (e < tol) break;
+        }
+    } else {
+        int k0 = c->k;
+        rc = run_iterations(c, K, true);
+        if (rc == PR_OK) {
+            CCUDA(c, cudaMemcpyAsync(c->h_pinned, c->derr, sizeof(double) * (c->N + 2), cudaMemcpyDeviceToHost,
+                                     c->fine->stream));
+            rc = take_ctx_status(c);
+            for (int i = 0; i < K; ++i) {
+                int k = std::min(k0 + 1 + i, c->N + 1);
+                double e = k0 + 1 + i > c->N ? 0.0 : c->h_pinned[k];
+                if (errs) errs[i] = e;
+                last = e;
+            }
+            done = K;
+        }
+    }
+    if (k_done) *k_done = done;
+    if (rc == PR_OK && tol > 0 && done == K && last >= tol) return cfail(c, PR_ENOTCONV, "error %g >= tol after %d iterations", last, K);
+    return rc;
+}
+
+int pr_moments(pr_ctx* c, int n, int kind, double* out)
+{
+    if (!c) return PR_EINVAL;
+    if (n < 0 || n > c->N || !out) return cfail(c, PR_EINVAL, "n must be in 0..N");
+    if (kind != PR_PRIMITIVE && kind != PR_CONSERVED) return cfail(c, PR_EINVAL, "bad kind");
+    std::vector<double> V(5 * c->nx);
+    CCUDA(c, cudaMemcpyAsync(V.data(), c->dU + (size_t)n * 5 * c->nx, sizeof(double) * 5 * c->nx, cudaMemcpyDeviceToHost,
+                             c->fine->stream));
+    int rc = take_ctx_status(c);
+    if (kind == PR_CONSERVED) memcpy(out, V.data(), sizeof(double) * 5 * c->nx);
+    else cons_to_prim_host(c->nx, V.data(), out);
+    return rc;
+}
+
+}  // extern "C"

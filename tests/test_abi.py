@@ -1,0 +1,35 @@
+"""The C ABI library builds, loads and exports every entry point that
+include/pr.h declares; the Python binding wraps each of them (no GPU needed)."""
+import os
+import re
+
+import paper_2502_02704_gb300 as pr
+from paper_2502_02704_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(pr_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_entry_point():
+    B.build()
+    L = pr.lib()
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_binding_covers_the_abi():
+    declared = set(_declared())
+    assert declared == set(pr.EXPORTED)
+    for name in declared:
+        assert callable(getattr(pr, name)), name

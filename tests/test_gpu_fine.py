@@ -1,0 +1,192 @@
+"""Parity of the CUDA fine propagator (fused transport + moments + Maxwellian +
+implicit BGK, Eqs. 11-13) with the CPU FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2502_02704_gb300 as pr
+from paper_2502_02704_gb300 import workloads as W
+from helpers import TOL_FP64, TOL_MIXED, f_rel_err, moment_rel_err
+
+pytestmark = pytest.mark.gpu
+
+BC = {pr.PR_BC_PERIODIC: O.BC_PERIODIC, pr.PR_BC_OUTFLOW: O.BC_OUTFLOW, pr.PR_BC_REFLECT: O.BC_REFLECT}
+SCH = {pr.PR_UPWIND: O.UPWIND, pr.PR_MUSCL: O.MUSCL}
+
+
+def _kin(nx, nv, L, bc, eps, scheme, x0=0.0, x1=1.0):
+    return O.Kin(nx=nx, nv=nv, L=L, x0=x0, x1=x1, bc=BC[bc], eps=eps, scheme=SCH[scheme])
+
+
+def _profile(bc, nx):
+    if bc == pr.PR_BC_PERIODIC:
+        return W.smooth_periodic(nx)
+    if bc == pr.PR_BC_OUTFLOW:
+        return W.sod(nx)
+    return W.thirds(nx)
+
+
+def _run_gpu(insts, Us, nsteps, precision, chunks=None):
+    b = pr.pr_batch_create(insts, precision)
+    try:
+        for i, U in enumerate(Us):
+            pr.pr_batch_set_initial(b, i, U)
+        for n in (chunks or [nsteps]):
+            pr.pr_batch_run(b, n)
+        pr.pr_batch_sync(b)
+        return ([pr.pr_batch_get_f(b, i) for i in range(len(insts))],
+                [pr.pr_batch_moments(b, i) for i in range(len(insts))])
+    finally:
+        pr.pr_batch_destroy(b)
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+@pytest.mark.parametrize("scheme", [pr.PR_UPWIND, pr.PR_MUSCL])
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW, pr.PR_BC_REFLECT])
+def test_fine_run_matches_oracle(precision, scheme, bc):
+    # nx = 70: three x tiles of 32 (last one ragged); nv = 12: 1728 velocities,
+    # two v chunks of 1024 (last one ragged)
+    nx, nv, L, eps, nsteps = 70, 12, 8.0, 1e-2, 9
+    dt = pr.fine_dt(nx, nv, L)
+    U = _profile(bc, nx)
+    f, V = _run_gpu([pr.instance(nx, nv, dt, L=L, bc=bc, eps=eps, scheme=scheme)], [U], nsteps, precision)
+    k = _kin(nx, nv, L, bc, eps, scheme)
+    fo = O.fine_run(k, dt, nsteps, O.lift(k, U))
+    Vo = O.project(k, fo, conserved=True)
+    tol = TOL_FP64 if precision == pr.PR_FP64 else TOL_MIXED
+    assert moment_rel_err(V[0], Vo) < tol
+    assert f_rel_err(f[0], fo) < tol
+    # the run moved the state: the comparison is not against the initial data
+    assert f_rel_err(O.lift(k, U), fo) > 1e-3
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+def test_lift_matches_oracle(precision):
+    nx, nv, L = 33, 16, 8.0
+    U = W.sod(nx)
+    b = pr.pr_batch_create([pr.instance(nx, nv, 1e-3, L=L, bc=pr.PR_BC_OUTFLOW)], precision)
+    try:
+        pr.pr_batch_set_initial(b, 0, U)
+        f = pr.pr_batch_get_f(b, 0)
+        V = pr.pr_batch_moments(b, 0)
+    finally:
+        pr.pr_batch_destroy(b)
+    k = _kin(nx, nv, L, pr.PR_BC_OUTFLOW, 1e-2, pr.PR_UPWIND)
+    fo = O.lift(k, U)
+    tol = 1e-13 if precision == pr.PR_FP64 else 1e-6
+    assert f_rel_err(f, fo) < tol
+    assert moment_rel_err(V, O.project(k, fo, conserved=True)) < tol
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+def test_arbitrary_initial_f_and_collisionless(precision):
+    # a loaded non-Maxwellian f (set_f path) and eps = inf (pure transport)
+    nx, nv, L = 45, 8, 6.0
+    dt = pr.fine_dt(nx, nv, L)
+    f0 = W.random_positive_f(nx, nv, seed=5)
+    for eps in (3e-3, math.inf):
+        b = pr.pr_batch_create([pr.instance(nx, nv, dt, L=L, bc=pr.PR_BC_PERIODIC, eps=eps, scheme=pr.PR_MUSCL)],
+                               precision)
+        try:
+            pr.pr_batch_set_f(b, 0, f0)
+            V0 = pr.pr_batch_moments(b, 0)
+            pr.pr_batch_run(b, 6)
+            f = pr.pr_batch_get_f(b, 0)
+            V = pr.pr_batch_moments(b, 0)
+        finally:
+            pr.pr_batch_destroy(b)
+        k = _kin(nx, nv, L, pr.PR_BC_PERIODIC, eps, pr.PR_MUSCL)
+        fo = O.fine_run(k, dt, 6, f0)
+        tol = TOL_FP64 if precision == pr.PR_FP64 else TOL_MIXED
+        assert moment_rel_err(V0, O.project(k, f0, conserved=True)) < tol
+        assert moment_rel_err(V, O.project(k, fo, conserved=True)) < tol
+        assert f_rel_err(f, fo) < tol
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+def test_ragged_batch_each_instance_matches_its_oracle(precision):
+    # uneven nx / nv / eps / dt in one persistent launch
+    specs = [(37, 8, 1e-1, pr.PR_BC_PERIODIC), (64, 12, 1e-4, pr.PR_BC_OUTFLOW), (5, 16, 1.0, pr.PR_BC_REFLECT),
+             (1, 4, 1e-2, pr.PR_BC_PERIODIC), (90, 8, 1e-3, pr.PR_BC_REFLECT)]
+    insts, Us, kins, dts = [], [], [], []
+    for nx, nv, eps, bc in specs:
+        dt = pr.fine_dt(nx, nv, 8.0)
+        insts.append(pr.instance(nx, nv, dt, L=8.0, bc=bc, eps=eps, scheme=pr.PR_MUSCL if nx > 1 else pr.PR_MUSCL))
+        Us.append(W.sod(nx) if bc != pr.PR_BC_PERIODIC else W.smooth_periodic(nx))
+        kins.append(_kin(nx, nv, 8.0, bc, eps, pr.PR_MUSCL))
+        dts.append(dt)
+    f, V = _run_gpu(insts, Us, 7, precision)
+    tol = TOL_FP64 if precision == pr.PR_FP64 else TOL_MIXED
+    for i in range(len(specs)):
+        fo = O.fine_run(kins[i], dts[i], 7, O.lift(kins[i], Us[i]))
+        assert moment_rel_err(V[i], O.project(kins[i], fo, conserved=True)) < tol, i
+        assert f_rel_err(f[i], fo) < tol, i
+
+
+def test_persistent_multistep_equals_repeated_single_steps():
+    # one launch of 8 steps (dependency waits between steps) gives the same
+    # bits as 8 launches of one step (kernel boundaries between steps)
+    nx, nv = 100, 8
+    dt = pr.fine_dt(nx, nv, 8.0)
+    inst = [pr.instance(nx, nv, dt, bc=pr.PR_BC_PERIODIC, eps=1e-2, scheme=pr.PR_MUSCL)]
+    U = [W.smooth_periodic(nx)]
+    fa, Va = _run_gpu(inst, U, 8, pr.PR_MIXED)
+    fb, Vb = _run_gpu(inst, U, 8, pr.PR_MIXED, chunks=[1] * 8)
+    assert np.array_equal(fa[0], fb[0]) and np.array_equal(Va[0], Vb[0])
+
+
+def test_autotuned_tiles_keep_results():
+    nx, nv = 200, 12
+    dt = pr.fine_dt(nx, nv, 8.0)
+    inst = [pr.instance(nx, nv, dt, bc=pr.PR_BC_OUTFLOW, eps=1e-3, scheme=pr.PR_MUSCL)]
+    b = pr.pr_batch_create(inst, pr.PR_FP64)
+    try:
+        pr.pr_batch_set_initial(b, 0, W.sod(nx))
+        pr.pr_batch_autotune(b)
+        tx, tuned = pr.pr_batch_tile(b, 0)
+        assert tuned and tx in (8, 16, 32, 64)
+        pr.pr_batch_run(b, 5)
+        V = pr.pr_batch_moments(b, 0)
+    finally:
+        pr.pr_batch_destroy(b)
+    k = _kin(nx, nv, 8.0, pr.PR_BC_OUTFLOW, 1e-3, pr.PR_MUSCL)
+    Vo = O.project(k, O.fine_run(k, dt, 5, O.lift(k, W.sod(nx))), conserved=True)
+    assert moment_rel_err(V, Vo) < TOL_FP64
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+def test_full_size_smooth_periodic_three_knudsen_numbers(precision):
+    # the measured workload: Nx = 512, 32^3 on [-8, 8]^3, MUSCL, periodic,
+    # eps in {1, 1e-2, 1e-4}, all three in one batched persistent launch.
+    nx, nv, L = 512, 32, 8.0
+    dt = pr.fine_dt(nx, nv, L)
+    epss = (1.0, 1e-2, 1e-4)
+    insts = [pr.instance(nx, nv, dt, L=L, bc=pr.PR_BC_PERIODIC, eps=e, scheme=pr.PR_MUSCL) for e in epss]
+    U = W.smooth_periodic(nx)
+    b = pr.pr_batch_create(insts, precision)
+    try:
+        for i in range(3):
+            pr.pr_batch_set_initial(b, i, U)
+        pr.pr_batch_run(b, 3)
+        V3 = [pr.pr_batch_moments(b, i) for i in range(3)]
+        f3 = pr.pr_batch_get_f(b, 1)
+        pr.pr_batch_run(b, 197)
+        V200 = [pr.pr_batch_moments(b, i) for i in range(3)]
+    finally:
+        pr.pr_batch_destroy(b)
+    tol = TOL_FP64 if precision == pr.PR_FP64 else TOL_MIXED
+    O.set_threads(8)
+    for i, e in enumerate(epss):
+        k = _kin(nx, nv, L, pr.PR_BC_PERIODIC, e, pr.PR_MUSCL)
+        fo = O.fine_run(k, dt, 3, O.lift(k, U))
+        assert moment_rel_err(V3[i], O.project(k, fo, conserved=True)) < tol
+        if i == 1:
+            assert f_rel_err(f3, fo) < tol
+        # 200 steps: mass is conserved exactly by the flux form and up to the
+        # quadrature defect of M by BGK; the state stays physical
+        m0 = O.project(k, O.lift(k, U), conserved=True)[0].sum()
+        assert abs(V200[i][0].sum() - m0) < (1e-11 if precision == pr.PR_FP64 else 1e-5) * m0
+        assert np.all(V200[i][0] > 0)
+    O.set_threads(1)
