@@ -233,6 +233,31 @@ int pr_batch_kernel_time(pr_batch* b, double* avg_ms, int* launches, int reset);
 /* Number of kernels the library launched since the last reset (any object). */
 long long pr_kernel_launches(int reset);
 
+/* ============== one fine step without any memory allocation ============== */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory themselves or let a library do it --
+ * for example an application whose GPU memory is entirely owned by another
+ * allocator or pool, or code that must not allocate once it is set up.
+ *
+ * Computes one fused float64 fine step of the instance *inst (transport,
+ * moments, Maxwellian and implicit BGK, the same arithmetic as pr_batch_run):
+ * f_out = F(f_in), both caller-owned device arrays [nx][nv^3] of float64,
+ * 16-byte aligned, distinct (no in-place update).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  All scratch (descriptor, factor
+ * tables, moment partials, counters, status) lives in one static device array
+ * of 4 MiB that every GPU which loads libpr holds until the process exits;
+ * instances needing more (about nx * (6 nv + 5 ceil(nv^3/1024)) * 8 bytes plus
+ * a few KiB) are rejected with PR_EINVAL.  The first call on a device looks up
+ * that array's device address (with the device current), so make the first
+ * call before any stream capture.  Each call clears what must start at zero;
+ * calls share the array, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  Enqueued on
+ * stream (NULL: the legacy default stream), then synchronises it and returns
+ * the device status (PR_ENONPHYS for a non-physical state, PR_ECUDA on a
+ * runtime error). */
+int pr_fine_step_noalloc(const pr_instance* inst, const double* f_in, double* f_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

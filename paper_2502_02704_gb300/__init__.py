@@ -94,6 +94,7 @@ _SIGS = {
     "pr_batch_autotune": (C.c_int, [_VP]),
     "pr_batch_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_kernel_launches": (C.c_longlong, [C.c_int]),
+    "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -344,6 +345,14 @@ def pr_batch_kernel_time(b, reset=False):
 
 def pr_kernel_launches(reset=False) -> int:
     return int(lib().pr_kernel_launches(int(bool(reset))))
+
+
+def pr_fine_step_noalloc(inst, f_in_dev, f_out_dev, stream=None):
+    """One float64 fine step f_out = F(f_in) on caller-owned device arrays,
+    with all scratch in the library's static device array (no allocation)."""
+    rc = lib().pr_fine_step_noalloc(C.byref(inst), _dptr(f_in_dev), _dptr(f_out_dev), _stream(stream))
+    if rc != PR_OK:
+        raise PrError(rc, (lib().pr_batch_last_error(None) or b"").decode() or "pr_fine_step_noalloc failed")
 
 
 def fine_dt(nx, nv, L, cfl=0.5, x0=0.0, x1=1.0) -> float:

@@ -22,6 +22,7 @@ UNITS = {
     "fine.cu": [],
     "coarse.cu": ["-fmad=false"],
     "runtime.cu": [],
+    "noalloc.cu": [],
 }
 
 

@@ -485,6 +485,13 @@ static int lift_instances(pr_batch* b, int begin, int end, cudaStream_t s)
     return PR_OK;
 }
 
+// Message for pr_batch_last_error(NULL) from entry points that own no object.
+void pr_internal_set_global_error(const char* msg)
+{
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    g_init_error = msg ? msg : "";
+}
+
 extern "C" {
 
 int pr_batch_create(pr_batch** out, const pr_instance* inst, int n, int precision)
