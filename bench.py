@@ -260,9 +260,15 @@ def run_ours(args):
     outs = [torch.empty((5, NX), dtype=torch.float64, device=dev) for _ in EPSS]
 
     res = {}
+    tiles = {}
     for prec in (pr.PR_MIXED, pr.PR_FP64):
         b = pr.pr_batch_create(_instances(pr, dt), prec)
         try:
+            # the library's autotuner picks the tile width on the live state
+            for i in range(len(EPSS)):
+                pr.pr_batch_set_initial(b, i, U)
+            pr.pr_batch_autotune(b)
+            tiles[prec] = pr.pr_batch_tile(b, 0)[0]
             if prec == pr.PR_MIXED:
                 with Clocks(local) as ck:
                     if dist:
@@ -334,7 +340,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances": len(EPSS), "cells_per_step": cells, "fine_steps": NSTEPS,
                    "precision": "mixed: f32 f, f64 moments/params", "l2": "inputs larger than L2 (384 MiB state)",
-                   "parallelism": f"weak x{world}"},
+                   "parallelism": f"weak x{world}",
+                   "tile_x": tiles.get(pr.PR_MIXED), "tile_x_fp64": tiles.get(pr.PR_FP64)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "kernel": "k_fine_run (persistent)",
                      "kernel_ms": kms, "peak_source": "measured" if peaks else "fallback"},

@@ -64,17 +64,6 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v)
 __device__ __forceinline__ int ld_status(const int* p) { return *(volatile const int*)p; }
 
 // ---- 4-wide vector access (16 bytes in float32, 2 x 16 bytes in float64) ----
-__device__ __forceinline__ void ld4(const float* p, float (&o)[4])
-{
-    float4 v = __ldcg(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double (&o)[4])
-{
-    double2 a = __ldcg(reinterpret_cast<const double2*>(p));
-    double2 b = __ldcg(reinterpret_cast<const double2*>(p + 2));
-    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
 __device__ __forceinline__ void st4(float* p, const float (&v)[4])
 {
     __stcg(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
@@ -119,6 +108,17 @@ __device__ __forceinline__ T minmod(T a, T b)
     return fabs(a) < fabs(b) ? a : b;
 }
 
+// minmod without branches: the argument of smaller magnitude when both have
+// the same sign, else 0 (max(0, min(a,b)) + min(0, max(a,b))).
+__device__ __forceinline__ float minmod2(float a, float b)
+{
+    return fmaxf(0.f, fminf(a, b)) + fminf(0.f, fmaxf(a, b));
+}
+__device__ __forceinline__ double minmod2(double a, double b)
+{
+    return fmax(0.0, fmin(a, b)) + fmin(0.0, fmax(a, b));
+}
+
 // Upwind interface value at the face between f0 and f1 (neighbours fm, f2):
 // from the left (f0 side) when v_x > 0, from the right otherwise (Eq. 13 with
 // the upwind sign); MUSCL adds half the minmod slope of the upwind cell.
@@ -136,28 +136,58 @@ __device__ __forceinline__ T face_value(T fm, T f0, T f1, T f2, bool pos)
 // Shared-memory layout helpers.
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Finalise per-column parameters into factor tables and projected moments.
-// par[i*8 + 0..4] = (u_x, u_y, u_z, theta, weight*rho*(2 pi theta)^{-3/2}),
-// mom[i*5 + 0..4] = sums over v of (g, v_x g, v_y g, v_z g, |v|^2 g) (no dv^3),
-// wg = weight of g in the state.  Writes tables tout[(c0+i)][3][nv] and the
-// conserved moments Ucur (and Uout when given) of f = wg g + M_tab.
+// Factor tables of the Maxwellians of ncols x cells.  par[i*8 + 0..4] =
+// (u_x, u_y, u_z, theta, weight*rho*(2 pi theta)^{-3/2}) in float64.  The
+// float32 tables are evaluated in float32 from the float64 parameters (the
+// FP64 pipe of this GPU is ~1/64 rate); the float64 tables in float64.
 template <typename T>
-__device__ void tables_and_projection(const Inst& I, int c0, int ncols, const double* par,
-                                      const double* mom, double wg, T* tout, T* tb, double* Uout)
+__device__ void write_tables(const Inst& I, int c0, int ncols, const double* par, T* tout, T* tb)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int nv = I.nv, tw = 3 * nv;
-    for (int idx = tid; idx < ncols * tw; idx += THREADS) {
-        int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
-        double vj = -I.L + (j + 0.5) * I.dv;
-        double u = par[i * 8 + d], th = par[i * 8 + 3];
-        double dvu = vj - u;
-        T val = exp_neg(T(0), dvu * dvu / (2.0 * th));
-        if (d == 0) val = (T)(par[i * 8 + 4] * (double)val);
-        tb[idx] = val;
-        tout[(size_t)(c0 + i) * tw + rem] = val;
+    if (sizeof(T) == 4) {
+        float* pf = reinterpret_cast<float*>(tb + ncols * tw);  // [ncols][5]: u_x, u_y, u_z, 1/(2 theta), weight*C
+        for (int i = tid; i < ncols; i += THREADS) {
+            pf[i * 5 + 0] = (float)par[i * 8 + 0];
+            pf[i * 5 + 1] = (float)par[i * 8 + 1];
+            pf[i * 5 + 2] = (float)par[i * 8 + 2];
+            pf[i * 5 + 3] = (float)(0.5 / par[i * 8 + 3]);
+            pf[i * 5 + 4] = (float)par[i * 8 + 4];
+        }
+        __syncthreads();
+        const float Lf = (float)I.L, dvf = (float)I.dv;
+        for (int idx = tid; idx < ncols * tw; idx += THREADS) {
+            int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
+            float vj = -Lf + ((float)j + 0.5f) * dvf;
+            float dvu = vj - pf[i * 5 + d];
+            float val = expf(-(dvu * dvu) * pf[i * 5 + 3]);
+            if (d == 0) val *= pf[i * 5 + 4];
+            tb[idx] = (T)val;
+            tout[(size_t)(c0 + i) * tw + rem] = (T)val;
+        }
+    } else {
+        for (int idx = tid; idx < ncols * tw; idx += THREADS) {
+            int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
+            double vj = -I.L + (j + 0.5) * I.dv;
+            double u = par[i * 8 + d], th = par[i * 8 + 3];
+            double dvu = vj - u;
+            T val = exp_neg(T(0), dvu * dvu / (2.0 * th));
+            if (d == 0) val = (T)(par[i * 8 + 4] * (double)val);
+            tb[idx] = val;
+            tout[(size_t)(c0 + i) * tw + rem] = val;
+        }
     }
-    __syncthreads();
+}
+
+// Conserved moments (Eq. 18) of f = wg g + M_tab for ncols x cells, from the
+// g sums mom[i*5 + 0..4] = (g, v_x g, v_y g, v_z g, |v|^2 g) (no dv^3) and the
+// 1-D sums of the tables tb (separable M): written to Ucur (and Uout).
+template <typename T>
+__device__ void project_columns(const Inst& I, int c0, int ncols, const double* mom, double wg, const T* tb,
+                                double* Uout)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nv = I.nv;
     for (int i = warp; i < ncols; i += WARPS) {
         double gs[3][3];
 #pragma unroll
@@ -209,8 +239,9 @@ __device__ __forceinline__ void prim_from_sums(const double* s, double dv3, doub
                                                int* status)
 {
     double rho = s[0] * dv3;
-    double ux = s[1] * dv3 / rho, uy = s[2] * dv3 / rho, uz = s[3] * dv3 / rho;
-    double th = (s[4] * dv3 / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    double ir = 1.0 / rho;
+    double ux = s[1] * dv3 * ir, uy = s[2] * dv3 * ir, uz = s[3] * dv3 * ir;
+    double th = (s[4] * dv3 * ir - (ux * ux + uy * uy + uz * uz)) / 3.0;
     if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
     double tp = 2.0 * PI * th;
     par[0] = ux;
@@ -220,35 +251,34 @@ __device__ __forceinline__ void prim_from_sums(const double* s, double dv3, doub
     par[4] = weight * rho / (tp * sqrt(tp));
 }
 
-// Last CTA of a tile: sum the chunk partials of step s (fixed order), build
-// the Maxwellian of the new state, its tables and projected moments, release.
+// Last CTA of a tile: sum the chunk partials of step s (fixed order, one
+// thread per (x cell, moment)), build the Maxwellian of the new state and its
+// tables; at the last step of the launch also the projected moments; release.
 template <typename T>
 __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, int ncols, int pout,
                               unsigned char* smem, int* status)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     double* mom = reinterpret_cast<double*>(smem);  // [MAX_TX][5]
     double* par = mom + MAX_TX * 5;                  // [MAX_TX][8]
-    T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);   // [MAX_TX][3][nv]
-    for (int i = warp; i < ncols; i += WARPS) {
-        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        const double* p = I.part + (size_t)(c0 + i) * I.n_vc * 5;
-        for (int v = lane; v < I.n_vc; v += 32)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) acc[q] += __ldcg(p + v * 5 + q);
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int o = 16; o; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) mom[i * 5 + q] = acc[q];
+    T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);   // [MAX_TX][3][nv] (+ float parameters)
+    const int n_vc = I.n_vc;
+    for (int idx = tid; idx < ncols * 5; idx += THREADS) {
+        const int i = idx / 5, q = idx - i * 5;
+        const double* p = I.part + (size_t)(c0 + i) * n_vc * 5 + q;
+        double acc = 0.0;
+        for (int v = 0; v < n_vc; ++v) acc += __ldcg(p + v * 5);
+        mom[idx] = acc;
     }
     __syncthreads();
     for (int i = tid; i < ncols; i += THREADS) prim_from_sums(mom + i * 5, I.dv3, I.b, par + i * 8, status);
     __syncthreads();
     T* tout = reinterpret_cast<T*>(I.tab[pout]);
-    tables_and_projection<T>(I, c0, ncols, par, mom, I.a, tout, tb, s == nsteps ? I.Uout : nullptr);
+    write_tables<T>(I, c0, ncols, par, tout, tb);
+    if (s == nsteps) {
+        __syncthreads();
+        project_columns<T>(I, c0, ncols, mom, I.a, tb, I.Uout);
+    }
     __syncthreads();
     __threadfence();
     if (tid == 0) {
@@ -258,27 +288,86 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
     }
 }
 
-// Wait until every tile in deps[xt] has finalised step `target` (thread 0).
-__device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status)
+// Wait until every tile in deps[xt] has finalised step `target`.  Called by
+// warp 0: lane k spins on dependency k, so the flags are polled in parallel.
+__device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status, int lane)
 {
-    const int* d = I.deps + xt * MAXDEP;
-    const unsigned long long t0 = gtimer();
-    for (int k = 0; k < MAXDEP; ++k) {
-        int tile = d[k];
-        if (tile < 0) break;
-        const unsigned* p = I.done + tile;
-        unsigned ns = 32;
-        while (ld_acquire(p) < target) {
-            if (ld_status(status) != 0) return false;
-            if (gtimer() - t0 > TIMEOUT_NS) {
-                atomicCAS(status, 0, ST_TIMEOUT);
-                return false;
+    bool ok = true;
+    if (lane < MAXDEP) {
+        const int tile = I.deps[xt * MAXDEP + lane];
+        if (tile >= 0) {
+            const unsigned* p = I.done + tile;
+            const unsigned long long t0 = gtimer();
+            unsigned ns = 32;
+            while (ld_acquire(p) < target) {
+                if (ld_status(status) != 0) {
+                    ok = false;
+                    break;
+                }
+                if (gtimer() - t0 > TIMEOUT_NS) {
+                    atomicCAS(status, 0, ST_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 1024) ns <<= 1;
             }
-            __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
         }
     }
-    return true;
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Per-thread asynchronous prefetch of its own 16-byte pieces of g into a ring of
+// RING column slots in shared memory (cp.async, L2 only).  Each thread reads back
+// only what it copied, so no barrier is needed; one commit group per column.
+template <typename T>
+struct Ring {
+    static constexpr int SLOTS = sizeof(T) == 4 ? 8 : 4;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Sum five per-lane values over the warp with 8 shuffles (transposed butterfly):
+// afterwards lanes 0-3 hold the total of r0, 4-7 of r1, 8-15 of r2, 16-23 of r3,
+// 24-31 of r4.  Fixed order, deterministic.
+template <typename T>
+__device__ __forceinline__ T warp_sum5(const T (&r)[5], int lane)
+{
+    const unsigned F = 0xffffffffu;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    // level 16: lanes 0-15 keep (r0, r1, r2), lanes 16-31 keep (r3, r4)
+    T y1 = __shfl_xor_sync(F, h16 ? r[0] : r[3], 16);
+    T y2 = __shfl_xor_sync(F, h16 ? r[1] : r[4], 16);
+    T y3 = __shfl_xor_sync(F, h16 ? r[2] : T(0), 16);
+    T a = (h16 ? r[3] : r[0]) + y1;
+    T b = (h16 ? r[4] : r[1]) + y2;
+    T c = h16 ? T(0) : r[2] + y3;
+    // level 8: 0-7 keep (a, b) = (r0, r1); 8-15 keep c = r2; 16-23 keep a = r3; 24-31 keep b = r4
+    T x4 = !h16 ? (h8 ? a : c) : (h8 ? a : b);
+    T y4 = __shfl_xor_sync(F, x4, 8);
+    T y5 = __shfl_xor_sync(F, b, 8);
+    T p, q = T(0);
+    if (!h16) {
+        if (!h8) { p = a + y4; q = b + y5; }
+        else p = c + y4;
+    } else {
+        p = (h8 ? b : a) + y4;
+    }
+    // level 4: lanes 0-3 keep p (r0), 4-7 keep q (r1); the others keep p
+    const bool grp01 = !h16 && !h8;
+    T x6 = grp01 ? (h4 ? p : q) : p;
+    T y6 = __shfl_xor_sync(F, x6, 4);
+    p = (grp01 && h4) ? q + y6 : p + y6;
+    p += __shfl_xor_sync(F, p, 2);
+    p += __shfl_xor_sync(F, p, 1);
+    return p;
 }
 
 // One work item: transport + moments for x cells [c0, c1) and one v chunk.
@@ -287,6 +376,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
                           unsigned char* smem, int* status)
 {
     __shared__ int s_last;
+    constexpr int RING = Ring<T>::SLOTS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = I.nx, nv = I.nv, ldv = I.ldv, bc = I.bc, tw = 3 * nv;
     const int c0 = xt * I.tx, c1 = min(nx, c0 + I.tx), ncols = c1 - c0;
@@ -299,16 +389,10 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     const T wg = (T)wgd;
     const bool use_g = wgd != 0.0;
 
-    T* stab = reinterpret_cast<T*>(smem);  // [ne][3][nv]
-    double* red = reinterpret_cast<double*>(smem + align16((size_t)ne * tw * sizeof(T)));
-
-    for (int idx = tid; idx < ne * tw; idx += THREADS) {
-        int e = idx / tw, rem = idx - e * tw;
-        bool fl;
-        int cc = map_col(c0 - H + e, nx, bc, fl);
-        stab[idx] = __ldcg(tin + (size_t)cc * tw + rem);
-    }
-    __syncthreads();
+    T* ring = reinterpret_cast<T*>(smem);  // [RING][THREADS][4]
+    T* stab = ring + RING * THREADS * 4;    // [ne][3][nv]
+    T* red = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(stab) +
+                                  align16((size_t)ne * tw * sizeof(T)));  // [tx][WARPS][5] warp totals
 
     const int v0 = vc * CHUNK + tid * VPT;
     const bool act = v0 < I.nv3;
@@ -321,64 +405,135 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     }
     const int jxf = nv - 1 - jx;
     const int v0f = (jxf * nv + jy) * nv + jz;
+    const bool load = use_g && act;
+
+    // prefetch the first RING extended columns of g (one commit group each)
+    auto issue = [&](int e) {
+        if (load && e < ne) {
+            bool fl;
+            int cc = map_col(c0 - H + e, nx, bc, fl);
+            const T* src = gin + (size_t)cc * ldv + (fl ? v0f : v0);
+            T* dst = ring + ((e % RING) * THREADS + tid) * 4;
+#pragma unroll
+            for (int k = 0; k < (int)(4 * sizeof(T)) / 16; ++k) cp_async16(dst + k * (16 / sizeof(T)), src + k * (16 / sizeof(T)));
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int e = 0; e < RING; ++e) issue(e);
+
+    for (int idx = tid; idx < ne * tw; idx += THREADS) {
+        int e = idx / tw, rem = idx - e * tw;
+        bool fl;
+        int cc = map_col(c0 - H + e, nx, bc, fl);
+        stab[idx] = __ldcg(tin + (size_t)cc * tw + rem);
+    }
+    __syncthreads();
+
     const double vxd = -I.L + (jx + 0.5) * I.dv, vyd = -I.L + (jy + 0.5) * I.dv;
     const bool pos = vxd > 0.0;
     const T cour = (T)(I.nu * vxd);
     const T vx = (T)vxd, vy = (T)vyd, vxy2 = (T)(vxd * vxd + vyd * vyd);
-    T vz[4], vz2[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        double z = -I.L + (jz + q + 0.5) * I.dv;
-        vz[q] = (T)z;
-        vz2[q] = (T)(z * z);
-    }
+    const T vz0 = (T)(-I.L + (jz + 0.5) * I.dv), dvz = (T)I.dv;
+    const T zz0 = vz0 * vz0, zz1 = (vz0 + dvz) * (vz0 + dvz), zz2 = (vz0 + T(2) * dvz) * (vz0 + T(2) * dvz),
+            zz3 = (vz0 + T(3) * dvz) * (vz0 + T(3) * dvz);
 
-    // value of the current state at extended column e for this thread's 4 velocities
+    // value of the current state at extended column e (its g is in ring slot e % RING)
     auto recon = [&](int e, T (&o)[4]) {
         bool fl;
-        int cc = map_col(c0 - H + e, nx, bc, fl);
+        map_col(c0 - H + e, nx, bc, fl);
         int jxx = fl ? jxf : jx;
         const T* tb = stab + e * tw;
         T txy = tb[jxx] * tb[nv + jy];
         T tz[4];
         lds4(tb + 2 * nv + jz, tz);
-        if (use_g && act) {
+        cp_async_wait<RING - 1>();
+        if (load) {
             T gv[4];
-            ld4(gin + (size_t)cc * ldv + (fl ? v0f : v0), gv);
+            lds4(ring + ((e % RING) * THREADS + tid) * 4, gv);
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] = wg * gv[q] + txy * tz[q];
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) o[q] = txy * tz[q];
         }
+        issue(e + RING);
     };
 
-    constexpr int WN = 2 * H + 1;
-    T w[WN][4];
-#pragma unroll
-    for (int e = 0; e < 2 * H; ++e) recon(e, w[e]);
-    T sprev[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        sprev[q] = H == 2 ? face_value<T, H>(w[0][q], w[1][q], w[2][q], w[3][q], pos)
-                          : face_value<T, H>(T(0), w[0][q], w[1][q], T(0), pos);
-
-    for (int i = 0; i < ncols; ++i) {
-        recon(i + 2 * H, w[2 * H]);
-        T fs[4];
+    // March along x.  State before output cell i: fc = f_i, fn = f_{i+1},
+    // dm = f_i - f_{i-1}, dp = f_{i+1} - f_i (MUSCL), sp = face value at i-1/2.
+    T fc[4], fn[4], dm[4], dp[4], sp[4];
+    if (H == 2) {
+        T f0[4], f1[4];
+        recon(0, f0);
+        recon(1, f1);
+        recon(2, fc);
+        recon(3, fn);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            T snext = H == 2 ? face_value<T, H>(w[1][q], w[2][q], w[3][q], w[4][q], pos)
-                             : face_value<T, H>(T(0), w[1][q], w[2][q], T(0), pos);
-            fs[q] = w[H][q] - cour * (snext - sprev[q]);
-            sprev[q] = snext;
+            T d0 = f1[q] - f0[q];
+            dm[q] = fc[q] - f1[q];
+            dp[q] = fn[q] - fc[q];
+            sp[q] = pos ? f1[q] + T(0.5) * minmod2(d0, dm[q]) : fc[q] - T(0.5) * minmod2(dm[q], dp[q]);
+        }
+    } else {
+        T f0[4];
+        recon(0, f0);
+        recon(1, fc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sp[q] = pos ? f0[q] : fc[q];
+    }
+
+    const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
+    const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
+#pragma unroll 1
+    for (int i = 0; i < ncols; ++i) {
+        T fs[4];
+        if (H == 2) {
+            T fnn[4];
+            recon(i + 4, fnn);
+            if (pos) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    T dpp = fnn[q] - fn[q];
+                    T face = fc[q] + T(0.5) * minmod2(dm[q], dp[q]);
+                    fs[q] = fc[q] - cour * (face - sp[q]);
+                    sp[q] = face;
+                    fc[q] = fn[q];
+                    fn[q] = fnn[q];
+                    dm[q] = dp[q];
+                    dp[q] = dpp;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    T dpp = fnn[q] - fn[q];
+                    T face = fn[q] - T(0.5) * minmod2(dp[q], dpp);
+                    fs[q] = fc[q] - cour * (face - sp[q]);
+                    sp[q] = face;
+                    fc[q] = fn[q];
+                    fn[q] = fnn[q];
+                    dm[q] = dp[q];
+                    dp[q] = dpp;
+                }
+            }
+        } else {
+            recon(i + 2, fn);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                T face = pos ? fc[q] : fn[q];
+                fs[q] = fc[q] - cour * (face - sp[q]);
+                sp[q] = face;
+                fc[q] = fn[q];
+            }
         }
         T r[5];
         if (act) {
             st4(gout + (size_t)(c0 + i) * ldv + v0, fs);
             T s0 = (fs[0] + fs[1]) + (fs[2] + fs[3]);
-            T s1 = vz[0] * fs[0] + vz[1] * fs[1] + vz[2] * fs[2] + vz[3] * fs[3];
-            T s2 = vz2[0] * fs[0] + vz2[1] * fs[1] + vz2[2] * fs[2] + vz2[3] * fs[3];
+            // v_z of the four nodes: vz0 + q dv
+            T s1 = vz0 * s0 + dvz * (fs[1] + T(2) * fs[2] + T(3) * fs[3]);
+            T s2 = zz0 * fs[0] + zz1 * fs[1] + zz2 * fs[2] + zz3 * fs[3];
             r[0] = s0;
             r[1] = vx * s0;
             r[2] = vy * s0;
@@ -388,24 +543,16 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
 #pragma unroll
             for (int q = 0; q < 5; ++q) r[q] = T(0);
         }
-#pragma unroll
-        for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int o = 16; o; o >>= 1) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) red[(i * WARPS + warp) * 5 + q] = (double)r[q];
-#pragma unroll
-        for (int e = 0; e < 2 * H; ++e)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) w[e][q] = w[e + 1][q];
+        T tot = warp_sum5(r, lane);
+        if (writer) red[(i * WARPS + warp) * 5 + qsel] = tot;
     }
+    cp_async_wait<0>();
     __syncthreads();
     for (int idx = tid; idx < ncols * 5; idx += THREADS) {
         int i = idx / 5, q = idx - i * 5;
         double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < WARPS; ++k) acc += red[(i * WARPS + k) * 5 + q];
+        for (int k = 0; k < WARPS; ++k) acc += (double)red[(i * WARPS + k) * 5 + q];
         I.part[((size_t)(c0 + i) * I.n_vc + vc) * 5 + q] = acc;
     }
     __threadfence();
@@ -422,8 +569,14 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     __syncthreads();
 }
 
+// float32: 3 CTAs per SM (80 registers), float64: 2 CTAs per SM (128 registers)
+template <typename T>
+struct MinBlocks {
+    static constexpr int value = sizeof(T) == 4 ? 3 : 2;
+};
+
 template <typename T, int SCHEME>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, MinBlocks<T>::value)
 k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
            const long long* __restrict__ prefix, const Active* __restrict__ active, int nsteps,
            unsigned long long* ticket, int* status, int waits)
@@ -438,15 +591,13 @@ k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
     const long long base = prefix[ib];
     const long long W = prefix[ie] - base;
     const long long total = W * nsteps;
+    // Each CTA claims its next ticket while it works on the current one, so
+    // the atomic's latency is hidden; tickets stay increasing per CTA.
+    if (tid == 0) s_t = (long long)atomicAdd(ticket, 1ULL);
+    __syncthreads();
     for (;;) {
-        if (tid == 0) {
-            long long t = (long long)atomicAdd(ticket, 1ULL);
-            if (ld_status(status) != 0) t = total;
-            s_t = t;
-        }
-        __syncthreads();
         const long long t = s_t;
-        if (t >= total) break;
+        if (t >= total || ld_status(status) != 0) break;
         const int s = (int)(t / W) + 1;
         const long long r = base + t % W;
         int lo = ib, hi = ie - 1;
@@ -459,11 +610,18 @@ k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
         const int loc = (int)(r - prefix[lo]);
         const int xt = loc / I.n_vc, vc = loc - xt * I.n_vc;
         if (waits && s > 1) {
-            if (tid == 0) s_ok = wait_tiles(I, xt, (unsigned)(s - 1), status) ? 1 : 0;
+            if (tid < 32) {
+                bool ok = wait_tiles(I, xt, (unsigned)(s - 1), status, tid);
+                if (tid == 0) s_ok = ok ? 1 : 0;
+            }
             __syncthreads();
             if (!s_ok) break;
         }
+        long long next = 0;
+        if (tid == 0) next = (long long)atomicAdd(ticket, 1ULL);
         fine_item<T, H>(I, st[lo], s, nsteps, xt, vc, smem, status);
+        if (tid == 0) s_t = next;
+        __syncthreads();
     }
 }
 
@@ -501,7 +659,9 @@ k_lift(const Inst* __restrict__ insts, InstState* st, const Active* __restrict__
     __syncthreads();
     InstState S = st[b];
     T* tout = reinterpret_cast<T*>(I.tab[S.cur]);
-    tables_and_projection<T>(I, c0, ncols, par, mom, 0.0, tout, tb, nullptr);
+    write_tables<T>(I, c0, ncols, par, tout, tb);
+    __syncthreads();
+    project_columns<T>(I, c0, ncols, mom, 0.0, tb, nullptr);
     if (xt == 0 && threadIdx.x == 0) st[b].a0 = 0.0;
 }
 
@@ -600,15 +760,16 @@ void* fine_kernel_ptr()
 size_t fine_run_smem(int precision, int tx, int nv, int H)
 {
     size_t es = precision == 0 ? sizeof(double) : sizeof(float);
-    size_t item = align16((size_t)(tx + 2 * H) * 3 * nv * es) + (size_t)tx * WARPS * 5 * sizeof(double);
-    size_t fin = (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es;
+    size_t ring = (size_t)(precision == 0 ? Ring<double>::SLOTS : Ring<float>::SLOTS) * THREADS * 4 * es;
+    size_t item = ring + align16((size_t)(tx + 2 * H) * 3 * nv * es) + (size_t)tx * WARPS * 5 * es;
+    size_t fin = (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es + (size_t)tx * 5 * sizeof(float);
     return item > fin ? item : fin;
 }
 
 size_t lift_smem(int precision, int tx, int nv)
 {
     size_t es = precision == 0 ? sizeof(double) : sizeof(float);
-    return (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es;
+    return (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es + (size_t)tx * 5 * sizeof(float);
 }
 
 // Dynamic shared memory may use what the static allocation leaves of the opt-in limit.
