@@ -140,14 +140,14 @@ __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) &
 // (u_x, u_y, u_z, theta, weight*rho*(2 pi theta)^{-3/2}) in float64.  The
 // float32 tables are evaluated in float32 from the float64 parameters (the
 // FP64 pipe of this GPU is ~1/64 rate); the float64 tables in float64.
-template <typename T>
+template <typename T, int NT>
 __device__ void write_tables(const Inst& I, int c0, int ncols, const double* par, T* tout, T* tb)
 {
     const int tid = threadIdx.x;
     const int nv = I.nv, tw = 3 * nv;
     if (sizeof(T) == 4) {
         float* pf = reinterpret_cast<float*>(tb + ncols * tw);  // [ncols][5]: u_x, u_y, u_z, 1/(2 theta), weight*C
-        for (int i = tid; i < ncols; i += THREADS) {
+        for (int i = tid; i < ncols; i += NT) {
             pf[i * 5 + 0] = (float)par[i * 8 + 0];
             pf[i * 5 + 1] = (float)par[i * 8 + 1];
             pf[i * 5 + 2] = (float)par[i * 8 + 2];
@@ -156,7 +156,7 @@ __device__ void write_tables(const Inst& I, int c0, int ncols, const double* par
         }
         __syncthreads();
         const float Lf = (float)I.L, dvf = (float)I.dv;
-        for (int idx = tid; idx < ncols * tw; idx += THREADS) {
+        for (int idx = tid; idx < ncols * tw; idx += NT) {
             int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
             float vj = -Lf + ((float)j + 0.5f) * dvf;
             float dvu = vj - pf[i * 5 + d];
@@ -166,7 +166,7 @@ __device__ void write_tables(const Inst& I, int c0, int ncols, const double* par
             tout[(size_t)(c0 + i) * tw + rem] = (T)val;
         }
     } else {
-        for (int idx = tid; idx < ncols * tw; idx += THREADS) {
+        for (int idx = tid; idx < ncols * tw; idx += NT) {
             int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
             double vj = -I.L + (j + 0.5) * I.dv;
             double u = par[i * 8 + d], th = par[i * 8 + 3];
@@ -182,13 +182,13 @@ __device__ void write_tables(const Inst& I, int c0, int ncols, const double* par
 // Conserved moments (Eq. 18) of f = wg g + M_tab for ncols x cells, from the
 // g sums mom[i*5 + 0..4] = (g, v_x g, v_y g, v_z g, |v|^2 g) (no dv^3) and the
 // 1-D sums of the tables tb (separable M): written to Ucur (and Uout).
-template <typename T>
+template <typename T, int NT>
 __device__ void project_columns(const Inst& I, int c0, int ncols, const double* mom, double wg, const T* tb,
                                 double* Uout)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nv = I.nv;
-    for (int i = warp; i < ncols; i += WARPS) {
+    for (int i = warp; i < ncols; i += NT / 32) {
         double gs[3][3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) gs[d][0] = gs[d][1] = gs[d][2] = 0.0;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void prim_from_sums(const double* s, double dv3, doub
 // Last CTA of a tile: sum the chunk partials of step s (fixed order, one
 // thread per (x cell, moment)), build the Maxwellian of the new state and its
 // tables; at the last step of the launch also the projected moments; release.
-template <typename T>
+template <typename T, int NT>
 __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, int ncols, int pout,
                               unsigned char* smem, int* status)
 {
@@ -263,7 +263,7 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
     double* par = mom + MAX_TX * 5;                  // [MAX_TX][8]
     T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);   // [MAX_TX][3][nv] (+ float parameters)
     const int n_vc = I.n_vc;
-    for (int idx = tid; idx < ncols * 5; idx += THREADS) {
+    for (int idx = tid; idx < ncols * 5; idx += NT) {
         const int i = idx / 5, q = idx - i * 5;
         const double* p = I.part + (size_t)(c0 + i) * n_vc * 5 + q;
         double acc = 0.0;
@@ -271,19 +271,19 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
         mom[idx] = acc;
     }
     __syncthreads();
-    for (int i = tid; i < ncols; i += THREADS) prim_from_sums(mom + i * 5, I.dv3, I.b, par + i * 8, status);
+    for (int i = tid; i < ncols; i += NT) prim_from_sums(mom + i * 5, I.dv3, I.b, par + i * 8, status);
     __syncthreads();
     T* tout = reinterpret_cast<T*>(I.tab[pout]);
-    write_tables<T>(I, c0, ncols, par, tout, tb);
+    write_tables<T, NT>(I, c0, ncols, par, tout, tb);
     if (s == nsteps) {
         __syncthreads();
-        project_columns<T>(I, c0, ncols, mom, I.a, tb, I.Uout);
+        project_columns<T, NT>(I, c0, ncols, mom, I.a, tb, I.Uout);
     }
+    // release the tile: the barrier orders the CTA's table writes before
+    // thread 0's release store of the completion flag
     __syncthreads();
-    __threadfence();
     if (tid == 0) {
         I.arrive[xt] = 0u;
-        __threadfence();
         st_release(I.done + xt, (unsigned)s);
     }
 }
@@ -370,13 +370,16 @@ __device__ __forceinline__ T warp_sum5(const T (&r)[5], int lane)
     return p;
 }
 
-// One work item: transport + moments for x cells [c0, c1) and one v chunk.
-template <typename T, int H>
+// One work item: transport + moments for x cells [c0, c1) and one v chunk of
+// CHUNK velocities, V consecutive v_z nodes per thread (V = 4 or 8, same row).
+template <typename T, int H, int V>
 __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, int xt, int vc,
                           unsigned char* smem, int* status)
 {
-    __shared__ int s_last;
+    constexpr int NT = CHUNK / V, NW = NT / 32, NV4 = V / 4;
     constexpr int RING = Ring<T>::SLOTS;
+    constexpr int CPY = V * (int)sizeof(T) / 16;  // 16-byte copies per thread and column
+    __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = I.nx, nv = I.nv, ldv = I.ldv, bc = I.bc, tw = 3 * nv;
     const int c0 = xt * I.tx, c1 = min(nx, c0 + I.tx), ncols = c1 - c0;
@@ -389,12 +392,12 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     const T wg = (T)wgd;
     const bool use_g = wgd != 0.0;
 
-    T* ring = reinterpret_cast<T*>(smem);  // [RING][THREADS][4]
-    T* stab = ring + RING * THREADS * 4;    // [ne][3][nv]
+    T* ring = reinterpret_cast<T*>(smem);  // [RING][NT][V]
+    T* stab = ring + RING * NT * V;         // [ne][3][nv]
     T* red = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(stab) +
-                                  align16((size_t)ne * tw * sizeof(T)));  // [tx][WARPS][5] warp totals
+                                  align16((size_t)ne * tw * sizeof(T)));  // [tx][NW][5] warp totals
 
-    const int v0 = vc * CHUNK + tid * VPT;
+    const int v0 = vc * CHUNK + tid * V;
     const bool act = v0 < I.nv3;
     int jx = 0, jy = 0, jz = 0;
     if (act) {
@@ -406,95 +409,108 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     const int jxf = nv - 1 - jx;
     const int v0f = (jxf * nv + jy) * nv + jz;
     const bool load = use_g && act;
+    T* const myslot = ring + tid * V;
 
-    // prefetch the first RING extended columns of g (one commit group each)
+    // prefetch of extended column e of g into ring slot e % RING (one commit group each)
     auto issue = [&](int e) {
         if (load && e < ne) {
             bool fl;
             int cc = map_col(c0 - H + e, nx, bc, fl);
             const T* src = gin + (size_t)cc * ldv + (fl ? v0f : v0);
-            T* dst = ring + ((e % RING) * THREADS + tid) * 4;
+            T* dst = myslot + (e % RING) * (NT * V);
 #pragma unroll
-            for (int k = 0; k < (int)(4 * sizeof(T)) / 16; ++k) cp_async16(dst + k * (16 / sizeof(T)), src + k * (16 / sizeof(T)));
+            for (int k = 0; k < CPY; ++k) cp_async16(dst + k * (16 / sizeof(T)), src + k * (16 / sizeof(T)));
         }
         cp_async_commit();
     };
+    // factor tables of the ne extended columns: 16-byte asynchronous copies
+    // (first commit group), overlapped with the prefetch of g below
+    {
+        constexpr int PER = 16 / (int)sizeof(T);
+        const int rowv = tw / PER;
+        for (int idx = tid; idx < ne * rowv; idx += NT) {
+            int e = idx / rowv, k = idx - e * rowv;
+            bool fl;
+            int cc = map_col(c0 - H + e, nx, bc, fl);
+            cp_async16(stab + e * tw + k * PER, tin + (size_t)cc * tw + k * PER);
+        }
+        cp_async_commit();
+    }
 #pragma unroll
     for (int e = 0; e < RING; ++e) issue(e);
-
-    for (int idx = tid; idx < ne * tw; idx += THREADS) {
-        int e = idx / tw, rem = idx - e * tw;
-        bool fl;
-        int cc = map_col(c0 - H + e, nx, bc, fl);
-        stab[idx] = __ldcg(tin + (size_t)cc * tw + rem);
-    }
+    cp_async_wait<RING>();
     __syncthreads();
 
     const double vxd = -I.L + (jx + 0.5) * I.dv, vyd = -I.L + (jy + 0.5) * I.dv;
+    const double vzd = -I.L + (jz + 0.5) * I.dv;
     const bool pos = vxd > 0.0;
     const T cour = (T)(I.nu * vxd);
     const T vx = (T)vxd, vy = (T)vyd, vxy2 = (T)(vxd * vxd + vyd * vyd);
-    const T vz0 = (T)(-I.L + (jz + 0.5) * I.dv), dvz = (T)I.dv;
-    const T zz0 = vz0 * vz0, zz1 = (vz0 + dvz) * (vz0 + dvz), zz2 = (vz0 + T(2) * dvz) * (vz0 + T(2) * dvz),
-            zz3 = (vz0 + T(3) * dvz) * (vz0 + T(3) * dvz);
+    // v_z of node q of this thread = vz0 + q dv:  sum vz f = vz0 s0 + dv t1,
+    // sum vz^2 f = vz0^2 s0 + 2 vz0 dv t1 + dv^2 t2, t1 = sum q f_q, t2 = sum q^2 f_q
+    const T vz0 = (T)vzd, dvz = (T)I.dv, zz0 = (T)(vzd * vzd), zz1 = (T)(2.0 * vzd * I.dv), zz2 = (T)(I.dv * I.dv);
 
-    // value of the current state at extended column e (its g is in ring slot e % RING)
-    auto recon = [&](int e, T (&o)[4]) {
+    // value of the current state at extended column e for this thread's V velocities
+    auto recon = [&](int e, T (&o)[V]) {
         bool fl;
         map_col(c0 - H + e, nx, bc, fl);
         int jxx = fl ? jxf : jx;
         const T* tb = stab + e * tw;
         T txy = tb[jxx] * tb[nv + jy];
-        T tz[4];
-        lds4(tb + 2 * nv + jz, tz);
+        T tz[V];
+#pragma unroll
+        for (int k = 0; k < NV4; ++k) lds4(tb + 2 * nv + jz + 4 * k, *reinterpret_cast<T(*)[4]>(tz + 4 * k));
         cp_async_wait<RING - 1>();
         if (load) {
-            T gv[4];
-            lds4(ring + ((e % RING) * THREADS + tid) * 4, gv);
+            T gv[V];
+            const T* sl = myslot + (e % RING) * (NT * V);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = wg * gv[q] + txy * tz[q];
+            for (int k = 0; k < NV4; ++k) lds4(sl + 4 * k, *reinterpret_cast<T(*)[4]>(gv + 4 * k));
+#pragma unroll
+            for (int q = 0; q < V; ++q) o[q] = wg * gv[q] + txy * tz[q];
         } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = txy * tz[q];
+            for (int q = 0; q < V; ++q) o[q] = txy * tz[q];
         }
         issue(e + RING);
     };
 
     // March along x.  State before output cell i: fc = f_i, fn = f_{i+1},
     // dm = f_i - f_{i-1}, dp = f_{i+1} - f_i (MUSCL), sp = face value at i-1/2.
-    T fc[4], fn[4], dm[4], dp[4], sp[4];
+    T fc[V], fn[V], dm[V], dp[V], sp[V];
     if (H == 2) {
-        T f0[4], f1[4];
+        T f0[V], f1[V];
         recon(0, f0);
         recon(1, f1);
         recon(2, fc);
         recon(3, fn);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < V; ++q) {
             T d0 = f1[q] - f0[q];
             dm[q] = fc[q] - f1[q];
             dp[q] = fn[q] - fc[q];
             sp[q] = pos ? f1[q] + T(0.5) * minmod2(d0, dm[q]) : fc[q] - T(0.5) * minmod2(dm[q], dp[q]);
         }
     } else {
-        T f0[4];
+        T f0[V];
         recon(0, f0);
         recon(1, fc);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sp[q] = pos ? f0[q] : fc[q];
+        for (int q = 0; q < V; ++q) sp[q] = pos ? f0[q] : fc[q];
     }
 
     const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
     const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
+    T* outp = gout + (size_t)c0 * ldv + v0;
 #pragma unroll 1
-    for (int i = 0; i < ncols; ++i) {
-        T fs[4];
+    for (int i = 0; i < ncols; ++i, outp += ldv) {
+        T fs[V];
         if (H == 2) {
-            T fnn[4];
+            T fnn[V];
             recon(i + 4, fnn);
             if (pos) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < V; ++q) {
                     T dpp = fnn[q] - fn[q];
                     T face = fc[q] + T(0.5) * minmod2(dm[q], dp[q]);
                     fs[q] = fc[q] - cour * (face - sp[q]);
@@ -506,7 +522,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
                 }
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < V; ++q) {
                     T dpp = fnn[q] - fn[q];
                     T face = fn[q] - T(0.5) * minmod2(dp[q], dpp);
                     fs[q] = fc[q] - cour * (face - sp[q]);
@@ -520,7 +536,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
         } else {
             recon(i + 2, fn);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < V; ++q) {
                 T face = pos ? fc[q] : fn[q];
                 fs[q] = fc[q] - cour * (face - sp[q]);
                 sp[q] = face;
@@ -529,54 +545,62 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
         }
         T r[5];
         if (act) {
-            st4(gout + (size_t)(c0 + i) * ldv + v0, fs);
-            T s0 = (fs[0] + fs[1]) + (fs[2] + fs[3]);
-            // v_z of the four nodes: vz0 + q dv
-            T s1 = vz0 * s0 + dvz * (fs[1] + T(2) * fs[2] + T(3) * fs[3]);
-            T s2 = zz0 * fs[0] + zz1 * fs[1] + zz2 * fs[2] + zz3 * fs[3];
+#pragma unroll
+            for (int k = 0; k < NV4; ++k) st4(outp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
+            T s0 = T(0), t1 = T(0), t2 = T(0);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                s0 += fs[q];
+                t1 += T(q) * fs[q];
+                t2 += T(q * q) * fs[q];
+            }
             r[0] = s0;
             r[1] = vx * s0;
             r[2] = vy * s0;
-            r[3] = s1;
-            r[4] = vxy2 * s0 + s2;
+            r[3] = vz0 * s0 + dvz * t1;
+            r[4] = (vxy2 + zz0) * s0 + zz1 * t1 + zz2 * t2;
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) r[q] = T(0);
         }
         T tot = warp_sum5(r, lane);
-        if (writer) red[(i * WARPS + warp) * 5 + qsel] = tot;
+        if (writer) red[(i * NW + warp) * 5 + qsel] = tot;
     }
     cp_async_wait<0>();
     __syncthreads();
-    for (int idx = tid; idx < ncols * 5; idx += THREADS) {
+    for (int idx = tid; idx < ncols * 5; idx += NT) {
         int i = idx / 5, q = idx - i * 5;
         double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < WARPS; ++k) acc += (double)red[(i * WARPS + k) * 5 + q];
+        for (int k = 0; k < NW; ++k) acc += (double)red[(i * NW + k) * 5 + q];
         I.part[((size_t)(c0 + i) * I.n_vc + vc) * 5 + q] = acc;
     }
-    __threadfence();
+    // Arrival: the barrier orders every thread's stores (f* and partials)
+    // before thread 0's gpu-scope fence and counter increment (cumulative
+    // release); the last arriver fences again before its CTA reads the
+    // other chunks' partials (acquire), then finalises the tile.
     __syncthreads();
     if (tid == 0) {
+        __threadfence();
         unsigned prev = atomicAdd(I.arrive + xt, 1u);
         s_last = prev == (unsigned)(I.n_vc - 1);
+        if (s_last) __threadfence();
     }
     __syncthreads();
-    if (s_last) {
-        __threadfence();
-        finalize_tile<T>(I, s, nsteps, xt, c0, ncols, pout, smem, status);
-    }
+    if (s_last) finalize_tile<T, NT>(I, s, nsteps, xt, c0, ncols, pout, smem, status);
     __syncthreads();
 }
 
-// float32: 3 CTAs per SM (80 registers), float64: 2 CTAs per SM (128 registers)
-template <typename T>
+// Resident CTAs per SM the register budget is sized for: float32 with 8
+// velocities per thread (128 threads): 4; float32 with 4 (256 threads): 3;
+// float64 (256 threads): 2.
+template <typename T, int V>
 struct MinBlocks {
-    static constexpr int value = sizeof(T) == 4 ? 3 : 2;
+    static constexpr int value = sizeof(T) == 4 ? (V == 8 ? 4 : 3) : 2;
 };
 
-template <typename T, int SCHEME>
-__global__ void __launch_bounds__(THREADS, MinBlocks<T>::value)
+template <typename T, int SCHEME, int V>
+__global__ void __launch_bounds__(CHUNK / V, MinBlocks<T, V>::value)
 k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
            const long long* __restrict__ prefix, const Active* __restrict__ active, int nsteps,
            unsigned long long* ticket, int* status, int waits)
@@ -619,7 +643,7 @@ k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
         }
         long long next = 0;
         if (tid == 0) next = (long long)atomicAdd(ticket, 1ULL);
-        fine_item<T, H>(I, st[lo], s, nsteps, xt, vc, smem, status);
+        fine_item<T, H, V>(I, st[lo], s, nsteps, xt, vc, smem, status);
         if (tid == 0) s_t = next;
         __syncthreads();
     }
@@ -659,9 +683,9 @@ k_lift(const Inst* __restrict__ insts, InstState* st, const Active* __restrict__
     __syncthreads();
     InstState S = st[b];
     T* tout = reinterpret_cast<T*>(I.tab[S.cur]);
-    write_tables<T>(I, c0, ncols, par, tout, tb);
+    write_tables<T, THREADS>(I, c0, ncols, par, tout, tb);
     __syncthreads();
-    project_columns<T>(I, c0, ncols, mom, 0.0, tb, nullptr);
+    project_columns<T, THREADS>(I, c0, ncols, mom, 0.0, tb, nullptr);
     if (xt == 0 && threadIdx.x == 0) st[b].a0 = 0.0;
 }
 
@@ -749,19 +773,27 @@ k_state_moments(const Inst* __restrict__ insts, InstState* st, int b)
     if (c == 0 && threadIdx.x == 0) st[b].a0 = 1.0;
 }
 
-template <typename T, int SCHEME>
+template <typename T, int SCHEME, int V>
 void* fine_kernel_ptr()
 {
-    return reinterpret_cast<void*>(&k_fine_run<T, SCHEME>);
+    return reinterpret_cast<void*>(&k_fine_run<T, SCHEME, V>);
+}
+
+void* fine_kernel(int precision, int scheme, int vpt)
+{
+    if (precision == 0) return scheme == 1 ? fine_kernel_ptr<double, 1, 4>() : fine_kernel_ptr<double, 0, 4>();
+    if (vpt == 8) return scheme == 1 ? fine_kernel_ptr<float, 1, 8>() : fine_kernel_ptr<float, 0, 8>();
+    return scheme == 1 ? fine_kernel_ptr<float, 1, 4>() : fine_kernel_ptr<float, 0, 4>();
 }
 
 }  // namespace
 
-size_t fine_run_smem(int precision, int tx, int nv, int H)
+size_t fine_run_smem(int precision, int vpt, int tx, int nv, int H)
 {
     size_t es = precision == 0 ? sizeof(double) : sizeof(float);
-    size_t ring = (size_t)(precision == 0 ? Ring<double>::SLOTS : Ring<float>::SLOTS) * THREADS * 4 * es;
-    size_t item = ring + align16((size_t)(tx + 2 * H) * 3 * nv * es) + (size_t)tx * WARPS * 5 * es;
+    int nw = CHUNK / vpt / 32;
+    size_t ring = (size_t)(precision == 0 ? Ring<double>::SLOTS : Ring<float>::SLOTS) * CHUNK * es;
+    size_t item = ring + align16((size_t)(tx + 2 * H) * 3 * nv * es) + (size_t)tx * nw * 5 * es;
     size_t fin = (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es + (size_t)tx * 5 * sizeof(float);
     return item > fin ? item : fin;
 }
@@ -783,39 +815,29 @@ static void raise_smem(const void* fn, int max_smem)
 
 void prepare_fine_kernels(int max_smem)
 {
-    raise_smem(fine_kernel_ptr<double, 0>(), max_smem);
-    raise_smem(fine_kernel_ptr<double, 1>(), max_smem);
-    raise_smem(fine_kernel_ptr<float, 0>(), max_smem);
-    raise_smem(fine_kernel_ptr<float, 1>(), max_smem);
+    const int vp[3][2] = {{0, 4}, {1, 4}, {1, 8}};
+    for (auto& c : vp)
+        for (int sch = 0; sch < 2; ++sch) raise_smem(fine_kernel(c[0], sch, c[1]), max_smem);
     raise_smem(reinterpret_cast<const void*>(&k_lift<double>), max_smem);
     raise_smem(reinterpret_cast<const void*>(&k_lift<float>), max_smem);
 }
 
-int fine_run_occupancy(int precision, int scheme, size_t smem, int* blocks_per_sm)
+int fine_run_occupancy(int precision, int scheme, int vpt, size_t smem, int* blocks_per_sm)
 {
-    void* fn = precision == 0 ? (scheme == 1 ? fine_kernel_ptr<double, 1>() : fine_kernel_ptr<double, 0>())
-                              : (scheme == 1 ? fine_kernel_ptr<float, 1>() : fine_kernel_ptr<float, 0>());
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, THREADS, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fine_kernel(precision, scheme, vpt),
+                                                                  CHUNK / vpt, smem);
     return (int)e;
 }
 
-cudaError_t launch_fine_run(int precision, int scheme, const Inst* insts, InstState* st,
+cudaError_t launch_fine_run(int precision, int scheme, int vpt, const Inst* insts, InstState* st,
                             const long long* prefix, const Active* active, int nsteps,
                             unsigned long long* ticket, int* status, int waits, int grid, size_t smem,
                             cudaStream_t s)
 {
-    if (precision == 0) {
-        if (scheme == 1)
-            k_fine_run<double, 1><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
-        else
-            k_fine_run<double, 0><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
-    } else {
-        if (scheme == 1)
-            k_fine_run<float, 1><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
-        else
-            k_fine_run<float, 0><<<grid, THREADS, smem, s>>>(insts, st, prefix, active, nsteps, ticket, status, waits);
-    }
-    return cudaGetLastError();
+    if (precision == 0) vpt = 4;
+    void* args[] = {(void*)&insts, (void*)&st, (void*)&prefix, (void*)&active, (void*)&nsteps,
+                    (void*)&ticket, (void*)&status, (void*)&waits};
+    return cudaLaunchKernel(fine_kernel(precision, scheme, vpt), dim3(grid), dim3(CHUNK / vpt), args, smem, s);
 }
 
 cudaError_t launch_lift(int precision, const Inst* insts, InstState* st, const Active* active, int max_tiles,

@@ -145,14 +145,14 @@ extern "C" int pr_fine_step_noalloc(const pr_instance* d, const double* f_in, do
     const prk::Active* dA = reinterpret_cast<const prk::Active*>(base + o_active);
     int* dstatus = reinterpret_cast<int*>(base + o_status);
     const int H = d->scheme == PR_MUSCL ? 2 : 1;
-    size_t smem = prk::fine_run_smem(0, I.tx, I.nv, H);
+    size_t smem = prk::fine_run_smem(0, 4, I.tx, I.nv, H);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (prk::fine_run_occupancy(0, d->scheme, smem, &per_sm) != 0 || per_sm < 1) return PR_EINVAL;
+    if (prk::fine_run_occupancy(0, d->scheme, 4, smem, &per_sm) != 0 || per_sm < 1) return PR_EINVAL;
     long long items = prefix[1];
     int grid = (int)(items < (long long)per_sm * sms ? items : (long long)per_sm * sms);
-    e = prk::launch_fine_run(0, d->scheme, dI, dS, reinterpret_cast<const long long*>(base + o_prefix), dA, 1,
+    e = prk::launch_fine_run(0, d->scheme, 4, dI, dS, reinterpret_cast<const long long*>(base + o_prefix), dA, 1,
                              reinterpret_cast<unsigned long long*>(base + o_sync), dstatus, 0, grid, smem, s);
     // f_out now holds f*; apply the implicit relaxation in place: f = a f* + b M
     if (e == cudaSuccess) e = prk::launch_advance(dI, dS, dA, 1, 1, s);

@@ -52,12 +52,14 @@ struct Active {
 
 // ---- fine propagator (fine.cu) ----
 // Persistent fused fine-step kernel over the active instances for nsteps steps.
-cudaError_t launch_fine_run(int precision, int scheme, const Inst* insts, InstState* st,
+// vpt: velocities per thread (4, or 8 in float32 when every nv is a multiple
+// of 8); the CTA has CHUNK / vpt threads.
+cudaError_t launch_fine_run(int precision, int scheme, int vpt, const Inst* insts, InstState* st,
                             const long long* prefix, const Active* active, int nsteps,
                             unsigned long long* ticket, int* status, int waits, int grid,
                             size_t smem, cudaStream_t s);
-int fine_run_occupancy(int precision, int scheme, size_t smem, int* blocks_per_sm);
-size_t fine_run_smem(int precision, int tx, int nv, int H);
+int fine_run_occupancy(int precision, int scheme, int vpt, size_t smem, int* blocks_per_sm);
+size_t fine_run_smem(int precision, int vpt, int tx, int nv, int H);
 
 // Set the dynamic shared-memory limit of the kernels (called once).
 void prepare_fine_kernels(int max_smem);

@@ -103,6 +103,7 @@ static void prepare_kernels_once()
 
 struct pr_batch {
     int n = 0, precision = PR_MIXED, scheme = PR_UPWIND, H = 1;
+    int vpt = 4;  // velocities per thread of the fine kernel
     size_t es = 4;
     std::vector<pr_instance> desc;
     std::vector<Inst> h;
@@ -211,12 +212,16 @@ static int upload_layout(pr_batch* b, const std::vector<int>& txs)
         maxtx = std::max(maxtx, I.tx);
         maxnv = std::max(maxnv, I.nv);
     }
-    b->smem = prk::fine_run_smem(b->precision == PR_FP64 ? 0 : 1, maxtx, maxnv, b->H);
+    // eight v_z nodes per thread in float32 when every row allows it
+    bool all8 = true;
+    for (auto& I : b->h) all8 = all8 && I.nv % 8 == 0;
+    b->vpt = (b->precision == PR_MIXED && all8) ? 8 : 4;
+    b->smem = prk::fine_run_smem(b->precision == PR_FP64 ? 0 : 1, b->vpt, maxtx, maxnv, b->H);
     b->lift_smem = prk::lift_smem(b->precision == PR_FP64 ? 0 : 1, maxtx, maxnv);
     if ((int)b->smem > max_optin_smem() || (int)b->lift_smem > max_optin_smem())
         return bfail(b, PR_EINVAL, "shared memory per CTA (%zu B) exceeds the device limit", b->smem);
     int per_sm = 0;
-    int e = prk::fine_run_occupancy(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->smem, &per_sm);
+    int e = prk::fine_run_occupancy(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->smem, &per_sm);
     if (e != 0 || per_sm < 1) return bfail(b, PR_ECUDA, "fine kernel cannot be resident (occupancy %d)", per_sm);
     long long items = prefix[b->n];
     b->grid = (int)std::min<long long>((long long)per_sm * sm_count(), std::max<long long>(items, 1));
@@ -426,7 +431,7 @@ static int enqueue_run(pr_batch* b, int nsteps, int project_out, cudaStream_t s,
         e1 = get_event(b);
         cudaEventRecord(e0, s);
     }
-    BCUDA(b, prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->d_state, b->d_prefix,
+    BCUDA(b, prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state, b->d_prefix,
                                   b->d_active, nsteps, reinterpret_cast<unsigned long long*>(b->d_sync),
                                   b->d_status, nsteps > 1 ? 1 : 0, b->grid, b->smem, s));
     if (e1) {
@@ -1039,7 +1044,7 @@ static int build_graph(pr_ctx* c)
                              b->lift_smem, b->d_status, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, b->sync_bytes, s);
     if (e == cudaSuccess)
-        e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->d_state, b->d_prefix,
+        e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state, b->d_prefix,
                                  b->d_active, c->nf, reinterpret_cast<unsigned long long*>(b->d_sync), b->d_status,
                                  c->nf > 1 ? 1 : 0, b->grid, b->smem, s);
     if (e == cudaSuccess)
