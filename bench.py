@@ -35,7 +35,7 @@ EPSS = (1.0, 1e-2, 1e-4)
 METRIC = "phase-space cell-updates/s (FP32 vs FP64) and parareal speedup on 1 GB300"
 UNIT = "cell-updates/s"
 WORKLOAD = "smooth periodic fine solve, Nx=512, 32^3 on [-8,8]^3, MUSCL-minmod, eps in {1,1e-2,1e-4} batched, 200 steps"
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_run_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_run_traffic.txt")
 FINE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "fine.cu")
 
 
