@@ -93,6 +93,7 @@ def lib():
                 "or_coarse_propagate": (C.c_int, [pp, _D, _D]),
                 "or_parareal": (C.c_int, [pp, _D, C.c_int, C.c_double, C.c_int, _D, _D,
                                           C.POINTER(C.c_int)]),
+                "or_adjoint": (C.c_int, [pk, C.c_double, C.c_int, _D, _D, _D, _D]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -256,6 +257,18 @@ def parareal(p: Parareal, U0: np.ndarray, K: int, tol: float = 0.0, alg: int = 2
     _check(lib().or_parareal(C.byref(pc), _ptr(U0), K, tol, alg, _ptr(Uall), _ptr(errs),
                              C.byref(kd)), "parareal")
     return Uall, errs[:K], kd.value
+
+
+def adjoint(k: Kin, dt: float, nsteps: int, U0: np.ndarray, lamV: np.ndarray):
+    """(dJ/dU0 [5, nx] primitive, dJ/dlog eps) for a scalar J of the final
+    conserved moments with dJ/dV(T) = lamV [5, nx] (upwind fine run)."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    lamV = np.ascontiguousarray(lamV, dtype=np.float64)
+    dU0 = np.empty_like(U0)
+    de = C.c_double()
+    kc = k.c()
+    _check(lib().or_adjoint(C.byref(kc), dt, nsteps, _ptr(U0), _ptr(lamV), _ptr(dU0), C.byref(de)), "adjoint")
+    return dU0, de.value
 
 
 INF = math.inf

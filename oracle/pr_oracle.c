@@ -552,3 +552,172 @@ int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
     free(b);
     return rc;
 }
+
+/* ---------------- reference gradient (adjoint of the fine run) ----------------
+ *
+ * Not in the paper: the gradient of a scalar J(V(T)) of the final conserved
+ * moments V(T) = P(f^N) with respect to the primitive initial state U0 of the
+ * lifted distribution f^0 = L(U0) and to log(eps), for the upwind scheme.
+ * Derived by hand from the forward steps above and written plainly: all
+ * states are stored, the transport transpose is formed by scattering every
+ * coefficient of the forward stencil (through the same ghost mapping), and
+ * the BGK step is differentiated through the Maxwellian parameters
+ * (rho, u, theta) of the transported column.
+ */
+
+/* g = T(f): the transport half of or_fine_step. */
+static void transport_only(const or_kin* k, double dt, const double* v, const double* f, double* g)
+{
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv;
+    double dx = (k->x1 - k->x0) / nx;
+    for (int i = 0; i < nx; ++i)
+        for (int jx = 0; jx < nv; ++jx)
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    long j = ((long)jx * nv + jy) * nv + jz;
+                    double fr = xflux(k, f, nv3, v[jx], i, jx, jy, jz);
+                    double fl = xflux(k, f, nv3, v[jx], i - 1, jx, jy, jz);
+                    g[(long)i * nv3 + j] = f[(long)i * nv3 + j] - dt / dx * (fr - fl);
+                }
+}
+
+/* Add w * lg to lf at the stored cell of (possibly ghost) x cell c. */
+static void scatter(const or_kin* k, double* lf, long nv3, int c, int jx, int jy, int jz, double w)
+{
+    int nx = k->nx, nv = k->nv;
+    int cc = c, jxx = jx;
+    if (c < 0 || c >= nx) {
+        if (k->bc == OR_BC_PERIODIC) cc = ((c % nx) + nx) % nx;
+        else if (k->bc == OR_BC_OUTFLOW) cc = c < 0 ? 0 : nx - 1;
+        else {
+            cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
+            jxx = nv - 1 - jx;
+        }
+    }
+    lf[(long)cc * nv3 + ((long)jxx * nv + jy) * nv + jz] += w;
+}
+
+/* lf = T^T lg for the upwind transport: g_i = f_i - dt/dx (F_{i+1/2} - F_{i-1/2}),
+ * F_{c+1/2} = v+ f_c - v- f_{c+1}; every coefficient is scattered back. */
+static void transport_transpose(const or_kin* k, double dt, const double* v, const double* lg, double* lf)
+{
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv;
+    double r = dt / ((k->x1 - k->x0) / nx);
+    memset(lf, 0, sizeof(double) * nx * nv3);
+    for (int i = 0; i < nx; ++i)
+        for (int jx = 0; jx < nv; ++jx) {
+            double vp = v[jx] > 0.0 ? v[jx] : 0.0, vm = v[jx] < 0.0 ? -v[jx] : 0.0;
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    double l = lg[(long)i * nv3 + ((long)jx * nv + jy) * nv + jz];
+                    scatter(k, lf, nv3, i, jx, jy, jz, l);              /* f_i        */
+                    scatter(k, lf, nv3, i, jx, jy, jz, -r * vp * l);    /* -r F_{i+1/2}: v+ f_i   */
+                    scatter(k, lf, nv3, i + 1, jx, jy, jz, r * vm * l); /*               -v- f_{i+1} */
+                    scatter(k, lf, nv3, i - 1, jx, jy, jz, r * vp * l); /* +r F_{i-1/2}: v+ f_{i-1} */
+                    scatter(k, lf, nv3, i, jx, jy, jz, -r * vm * l);    /*               -v- f_i  */
+                }
+        }
+}
+
+int or_adjoint(const or_kin* k, double dt, int nsteps, const double* U0, const double* lamV,
+               double* dU0, double* dlogeps)
+{
+    int rc = check_kin(k);
+    if (rc) return rc;
+    if (k->scheme != OR_UPWIND || nsteps < 0 || !(dt > 0.0)) return OR_EINVAL;
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv, n = (long)nx * nv3;
+    double dv = 2.0 * k->L / nv, dv3 = dv * dv * dv;
+    const double pi = 3.14159265358979323846;
+    int collide = isfinite(k->eps);
+    double a = collide ? k->eps / (k->eps + dt) : 1.0, b = collide ? dt / (k->eps + dt) : 0.0;
+    double* v = malloc(sizeof(double) * nv);
+    double* F = malloc(sizeof(double) * n * (nsteps + 1)); /* f^0 .. f^N */
+    double* g = malloc(sizeof(double) * n);
+    double* lam = malloc(sizeof(double) * n);
+    double* lg = malloc(sizeof(double) * n);
+    if (!v || !F || !g || !lam || !lg) {
+        free(v); free(F); free(g); free(lam); free(lg);
+        return OR_ENOMEM;
+    }
+    or_velocity_nodes(nv, k->L, v);
+    rc = or_lift(k, U0, F);
+    for (int s = 0; s < nsteps && !rc; ++s) rc = or_fine_step(k, dt, F + s * n, F + (s + 1) * n);
+    /* seed: dJ/df^N_ij = dv^3 sum_q lamV_q,i phi_q(v_j), phi = (1, v, |v|^2/2) */
+    for (int i = 0; i < nx; ++i)
+        for (int jx = 0; jx < nv; ++jx)
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    double e = 0.5 * (v[jx] * v[jx] + v[jy] * v[jy] + v[jz] * v[jz]);
+                    lam[(long)i * nv3 + ((long)jx * nv + jy) * nv + jz] =
+                        dv3 * (lamV[i] + lamV[nx + i] * v[jx] + lamV[2 * nx + i] * v[jy] + lamV[3 * nx + i] * v[jz] +
+                               lamV[4 * nx + i] * e);
+                }
+    double deps = 0.0;
+    for (int s = nsteps - 1; s >= 0 && !rc; --s) {
+        /* step s: f^{s+1} = a g + b M[rho,u,theta of g], g = T(f^s) */
+        transport_only(k, dt, v, F + s * n, g);
+        for (int i = 0; i < nx; ++i) {
+            const double* gc = g + (long)i * nv3;
+            const double* lc = lam + (long)i * nv3;
+            double* lgc = lg + (long)i * nv3;
+            if (!collide) {
+                memcpy(lgc, lc, sizeof(double) * nv3);
+                continue;
+            }
+            double rho, u[3], th;
+            column_moments(nv, v, dv3, gc, &rho, u, &th);
+            double pref = rho / pow(2.0 * pi * th, 1.5);
+            double Ar = 0.0, Au[3] = {0.0, 0.0, 0.0}, At = 0.0;
+            for (int jx = 0; jx < nv; ++jx)
+                for (int jy = 0; jy < nv; ++jy)
+                    for (int jz = 0; jz < nv; ++jz) {
+                        long j = ((long)jx * nv + jy) * nv + jz;
+                        double c[3] = {v[jx] - u[0], v[jy] - u[1], v[jz] - u[2]};
+                        double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+                        double M = pref * exp(-c2 / (2.0 * th));
+                        double l = lc[j];
+                        Ar += l * M / rho;
+                        for (int d = 0; d < 3; ++d) Au[d] += l * M * c[d] / th;
+                        At += l * M * (c2 / (2.0 * th * th) - 1.5 / th);
+                        deps += l * a * b * (gc[j] - M);
+                    }
+            /* d rho/dg_j = dv3, d u/dg_j = dv3 (v_j - u)/rho, d theta/dg_j = dv3 (|v_j-u|^2 - 3 theta)/(3 rho) */
+            for (int jx = 0; jx < nv; ++jx)
+                for (int jy = 0; jy < nv; ++jy)
+                    for (int jz = 0; jz < nv; ++jz) {
+                        long j = ((long)jx * nv + jy) * nv + jz;
+                        double c[3] = {v[jx] - u[0], v[jy] - u[1], v[jz] - u[2]};
+                        double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+                        double dM = Ar * dv3 + (Au[0] * c[0] + Au[1] * c[1] + Au[2] * c[2]) * dv3 / rho +
+                                    At * dv3 * (c2 - 3.0 * th) / (3.0 * rho);
+                        lgc[j] = a * lc[j] + b * dM;
+                    }
+        }
+        transport_transpose(k, dt, v, lg, lam);
+    }
+    /* lift: f^0_ij = M[rho_i, u_i, theta_i](v_j) */
+    for (int i = 0; i < nx && !rc; ++i) {
+        double rho = U0[i], u[3] = {U0[nx + i], U0[2 * nx + i], U0[3 * nx + i]}, th = U0[4 * nx + i];
+        double pref = rho / pow(2.0 * pi * th, 1.5);
+        double s[5] = {0, 0, 0, 0, 0};
+        for (int jx = 0; jx < nv; ++jx)
+            for (int jy = 0; jy < nv; ++jy)
+                for (int jz = 0; jz < nv; ++jz) {
+                    long j = ((long)jx * nv + jy) * nv + jz;
+                    double c[3] = {v[jx] - u[0], v[jy] - u[1], v[jz] - u[2]};
+                    double c2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+                    double M = pref * exp(-c2 / (2.0 * th));
+                    double l = lam[(long)i * nv3 + j];
+                    s[0] += l * M / rho;
+                    for (int d = 0; d < 3; ++d) s[1 + d] += l * M * c[d] / th;
+                    s[4] += l * M * (c2 / (2.0 * th * th) - 1.5 / th);
+                }
+        for (int q = 0; q < 5; ++q) dU0[q * nx + i] = s[q];
+    }
+    if (dlogeps) *dlogeps = deps;
+    free(v); free(F); free(g); free(lam); free(lg);
+    return rc;
+}

@@ -78,6 +78,11 @@ int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout);
 int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
                 double* Uall, double* errs, int* k_done);
 
+/* Gradient of J(V(T)) w.r.t. the primitive initial state U0 [5][nx] and log eps,
+ * given lamV = dJ/dV(T) [5][nx] (conserved final moments); upwind scheme. */
+int or_adjoint(const or_kin* k, double dt, int nsteps, const double* U0, const double* lamV,
+               double* dU0, double* dlogeps);
+
 #ifdef __cplusplus
 }
 #endif
