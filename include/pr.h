@@ -230,6 +230,21 @@ int pr_batch_autotune(pr_batch* b);
  * clears the accumulator.  *launches (may be NULL) gets the launch count. */
 int pr_batch_kernel_time(pr_batch* b, double* avg_ms, int* launches, int reset);
 
+/* Gradient of a scalar J(V(T)) of the final conserved moments V(T)[5][nx_i] of
+ * instance i after nsteps fine steps from its lifted initial state (the state
+ * set by the last pr_batch_set_initial), for the float64 upwind scheme with
+ * periodic or outflow boundaries (PR_EINVAL otherwise).  Input lamV = dJ/dV(T)
+ * (host [5][nx_i]).  Output dU0 = dJ/dU0 with respect to the primitive initial
+ * state U0 = (rho, u_x, u_y, u_z, theta) (host [5][nx_i]) and *dlogeps =
+ * dJ/d(log eps).  The hand-written adjoint of each fine step (transposed
+ * transport, BGK relaxation differentiated through rho, u, theta of the
+ * transported column, Eqs. 11-13, 17, 18) runs backwards from checkpoints of
+ * f stored every `checkpoint` steps; each segment is recomputed forward.  Not
+ * in the paper.  Allocates and frees its work buffers; synchronous.  The
+ * instance's state afterwards is unspecified (set it again before reuse). */
+int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int checkpoint, const double* lamV, double* dU0,
+                     double* dlogeps);
+
 /* Number of kernels the library launched since the last reset (any object). */
 long long pr_kernel_launches(int reset);
 

@@ -94,6 +94,7 @@ _SIGS = {
     "pr_batch_autotune": (C.c_int, [_VP]),
     "pr_batch_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_kernel_launches": (C.c_longlong, [C.c_int]),
+    "pr_batch_adjoint": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
     "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
 }
 
@@ -341,6 +342,18 @@ def pr_batch_kernel_time(b, reset=False):
     n = C.c_int()
     _batch_check(b, lib().pr_batch_kernel_time(b.ptr, C.byref(ms), C.byref(n), int(bool(reset))))
     return ms.value, n.value
+
+
+def pr_batch_adjoint(b, i, nsteps, lamV, checkpoint=16):
+    """(dJ/dU0 [5, nx] primitive, dJ/dlog eps) for dJ/dV(T) = lamV [5, nx]
+    (float64 upwind instance, lifted start)."""
+    nx = b.shapes[i][0]
+    lamV = _f64(lamV, (5, nx))
+    dU0 = np.empty((5, nx))
+    de = C.c_double()
+    _batch_check(b, lib().pr_batch_adjoint(b.ptr, int(i), int(nsteps), int(checkpoint), _p(lamV), _p(dU0),
+                                           C.byref(de)))
+    return dU0, de.value
 
 
 def pr_kernel_launches(reset=False) -> int:

@@ -23,6 +23,7 @@ UNITS = {
     "coarse.cu": ["-fmad=false"],
     "runtime.cu": [],
     "noalloc.cu": [],
+    "adjoint.cu": [],
 }
 
 

@@ -82,6 +82,14 @@ cudaError_t launch_materialize(int precision, const Inst* insts, const InstState
 cudaError_t launch_set_f(int precision, const Inst* insts, InstState* st, int b,
                          const Inst& hinst, const double* f, cudaStream_t s);
 
+// ---- adjoint of the float64 upwind fine run (adjoint.cu) ----
+cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_t s);
+cudaError_t adj_moments(const Inst& I, const double* g, double* m, cudaStream_t s);
+cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const double* m, double* coef,
+                     double* eps_acc, double* lam_out, cudaStream_t s);
+cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double* dU0, cudaStream_t s);
+cudaError_t adj_copy_state(const Inst* insts, const InstState* st, int b, double* dst, cudaStream_t s);
+
 // ---- coarse propagator and parareal sweep (coarse.cu) ----
 struct CoarseParams {
     int nx, bc, sound;

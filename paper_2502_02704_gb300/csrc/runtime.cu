@@ -652,6 +652,109 @@ long long pr_kernel_launches(int reset)
 
 }  // extern "C"
 
+// ------------------------------------------------------------------ adjoint
+
+// Checkpointed reverse sweep of the float64 upwind fine run (see adjoint.cu).
+extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const double* lamV, double* dU0,
+                                double* dlogeps)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !lamV || !dU0 || nsteps < 0 || ckpt < 1)
+        return bfail(b, PR_EINVAL, "bad instance, buffers, step count or checkpoint interval");
+    if (b->precision != PR_FP64 || b->scheme != PR_UPWIND)
+        return bfail(b, PR_EINVAL, "the adjoint covers the float64 upwind scheme");
+    const Inst I = b->h[i];
+    if (I.bc == PR_BC_REFLECT) return bfail(b, PR_EINVAL, "the adjoint covers periodic and outflow boundaries");
+    cudaStream_t s = b->stream;
+    const size_t st = (size_t)I.nx * I.ldv, sv = (size_t)I.nx * I.nv3, m5 = (size_t)5 * I.nx;
+    const int nck = nsteps > 0 ? (nsteps + ckpt - 1) / ckpt : 0;
+    const int seg = std::min(ckpt, std::max(nsteps, 1));
+    // work: checkpoints, segment states and moments, two adjoint buffers, small vectors
+    size_t need = ((size_t)nck * sv + (size_t)seg * st + (size_t)seg * m5 + 2 * sv + 5 * I.nx + I.nx + 2 * m5) * sizeof(double);
+    double* w = nullptr;
+    if (cudaMalloc(&w, need) != cudaSuccess) return bfail(b, PR_ENOMEM, "adjoint work buffers (%zu bytes)", need);
+    double* ck = w;
+    double* sg = ck + (size_t)nck * sv;
+    double* sm = sg + (size_t)seg * st;
+    double* la = sm + (size_t)seg * m5;
+    double* lb = la + sv;
+    double* coef = lb + sv;
+    double* eps = coef + 5 * I.nx;
+    double* dv = eps + I.nx;   // lamV on the device
+    double* du = dv + m5;      // dU0 on the device
+    int rc = PR_OK;
+    auto run1 = [&]() -> int {
+        prk::Active a{i, i + 1};
+        BCUDA(b, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
+        int r = enqueue_run(b, 1, 0, s, false);
+        prk::Active all{0, b->n};
+        BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+        return r;
+    };
+    do {
+        // forward from the lifted state, storing f every ckpt steps
+        if ((rc = lift_instances(b, i, i + 1, s))) break;
+        for (int t = 0; t < nsteps && !rc; ++t) {
+            if (t % ckpt == 0) {
+                if (prk::launch_materialize(0, b->d_inst, b->d_state, i, I, ck + (size_t)(t / ckpt) * sv, s) != cudaSuccess) {
+                    rc = bfail(b, PR_ECUDA, "checkpoint");
+                    break;
+                }
+                g_launches += 1;
+            }
+            rc = run1();
+        }
+        if (rc) break;
+        if (cudaMemcpyAsync(dv, lamV, sizeof(double) * m5, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(eps, 0, sizeof(double) * I.nx, s) != cudaSuccess ||
+            prk::adj_seed(I, dv, la, s) != cudaSuccess) {
+            rc = bfail(b, PR_ECUDA, "adjoint seed");
+            break;
+        }
+        g_launches += 1;
+        for (int k = nck - 1; k >= 0 && !rc; --k) {
+            const int s0 = k * ckpt, s1 = std::min(s0 + ckpt, nsteps);
+            if (k == 0) rc = lift_instances(b, i, i + 1, s);
+            else if (prk::launch_set_f(0, b->d_inst, b->d_state, i, I, ck + (size_t)k * sv, s) != cudaSuccess)
+                rc = bfail(b, PR_ECUDA, "reload checkpoint");
+            else g_launches += 2;
+            for (int t = s0; t < s1 && !rc; ++t) {
+                if ((rc = run1())) break;
+                if (prk::adj_copy_state(b->d_inst, b->d_state, i, sg + (size_t)(t - s0) * st, s) != cudaSuccess ||
+                    prk::adj_moments(I, sg + (size_t)(t - s0) * st, sm + (size_t)(t - s0) * m5, s) != cudaSuccess)
+                    rc = bfail(b, PR_ECUDA, "segment store");
+                g_launches += 2;
+            }
+            for (int t = s1 - 1; t >= s0 && !rc; --t) {
+                if (prk::adj_step(I, la, sg + (size_t)(t - s0) * st, sm + (size_t)(t - s0) * m5, coef, eps, lb, s) !=
+                    cudaSuccess)
+                    rc = bfail(b, PR_ECUDA, "adjoint step");
+                g_launches += 2;
+                std::swap(la, lb);
+            }
+        }
+        if (rc) break;
+        if (prk::adj_lift(I, la, I.Uin, du, s) != cudaSuccess) {
+            rc = bfail(b, PR_ECUDA, "lift adjoint");
+            break;
+        }
+        g_launches += 1;
+        std::vector<double> e(I.nx);
+        if (cudaMemcpyAsync(dU0, du, sizeof(double) * m5, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(e.data(), eps, sizeof(double) * I.nx, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            rc = bfail(b, PR_ECUDA, "adjoint readback");
+            break;
+        }
+        rc = take_status(b, s);
+        double tot = 0.0;
+        for (double x : e) tot += x;
+        if (dlogeps) *dlogeps = tot;
+    } while (false);
+    cudaStreamSynchronize(s);
+    cudaFree(w);
+    return rc;
+}
+
 // ------------------------------------------------------------------ autotuner
 
 // Candidate tile widths are timed with CUDA events on a copy of the current
