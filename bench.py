@@ -227,6 +227,94 @@ def _parareal_speedup(pr, np):
         pr.pr_batch_destroy(one)
 
 
+def _ragged_section(pr, torch):
+    """32 seeded ragged Sod-type instances (Nx in [128, 1024], 16^3/24^3/32^3,
+    log10 eps in [-5, 0], MUSCL, outflow), mixed precision, one persistent
+    launch of 200 steps; device time with CUDA events."""
+    from paper_2502_02704_gb300 import workloads as W
+
+    insts, Us = [], []
+    for r in W.ragged_instances(32):
+        dt = pr.fine_dt(r["nx"], r["nv"], r["L"])
+        insts.append(pr.instance(r["nx"], r["nv"], dt, L=r["L"], bc=pr.PR_BC_OUTFLOW, eps=r["eps"],
+                                 scheme=pr.PR_MUSCL))
+        Us.append(r["U"])
+    cells = sum(d.nx * d.nv ** 3 for d in insts)
+    b = pr.pr_batch_create(insts, pr.PR_MIXED)
+    stream = torch.cuda.current_stream()
+    try:
+        for i, U in enumerate(Us):
+            pr.pr_batch_set_initial(b, i, U)
+        pr.pr_batch_autotune(b)
+        res = []
+        for rep in range(3):
+            for i, U in enumerate(Us):
+                pr.pr_batch_set_initial(b, i, U)
+            pr.pr_batch_sync(b)
+            pr.pr_batch_kernel_time(b, reset=True)
+            pr.pr_batch_run(b, NSTEPS)
+            pr.pr_batch_sync(b)
+            res.append(pr.pr_batch_kernel_time(b)[0])
+        ms = min(res[1:])
+        alg = 4.0 * (2 * NSTEPS - 1) * cells
+        return {"workload": "32 seeded ragged Sod-type instances, Nx in [128,1024], 16^3/24^3/32^3, "
+                            "log10 eps in [-5,0], MUSCL, outflow, 200 steps, one persistent launch",
+                "cells": cells, "value": cells * NSTEPS / (ms * 1e-3), "unit": UNIT, "kernel_ms": ms,
+                "hbm_frac": alg / (ms * 1e-3) / 1e9 / (_peaks() or {"hbm_gbs": 6800.0})["hbm_gbs"]}
+    finally:
+        pr.pr_batch_destroy(b)
+
+
+def _large_section(pr, np, torch):
+    """Two interacting shocks: Nx = 2048, 48^3 on [-10, 10]^3, thirds profile,
+    reflecting walls, eps = 1e-4, MUSCL, T = 0.05, N = 128 slices (16 fine steps
+    each), K = 6: mixed-precision batched parareal vs the plain FP64
+    single-instance serial fine chain, wall clock, with the error of each
+    parareal iterate against the FP64 chain."""
+    from paper_2502_02704_gb300 import workloads as W
+
+    nx, nv, L, N, T, eps, K = 2048, 48, 10.0, 128, 0.05, 1e-4, 6
+    U0 = W.thirds(nx)
+    ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_REFLECT, nv, L, eps, T, N, 0.5, 0.5, pr.PR_MUSCL, pr.PR_MIXED)
+    try:
+        nf, dtf = pr.pr_fine_steps_per_slice(ctx)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr.pr_set_initial(ctx, U0)
+        kd, errs = pr.pr_parareal_run(ctx, K)
+        par = np.stack([pr.pr_moments(ctx, n) for n in range(N + 1)])
+        t_par = time.perf_counter() - t0
+    finally:
+        pr.pr_destroy(ctx)
+    one = pr.pr_batch_create([pr.instance(nx, nv, dtf, L=L, bc=pr.PR_BC_REFLECT, eps=eps, scheme=pr.PR_MUSCL)],
+                             pr.PR_FP64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    V0 = np.stack([U0[0], U0[0] * U0[1], U0[0] * U0[2], U0[0] * U0[3],
+                   0.5 * U0[0] * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) + 1.5 * U0[0] * U0[4]])
+    chain = torch.zeros((N + 1, 5, nx), dtype=torch.float64, device=dev)
+    chain[0] = torch.tensor(V0, device=dev)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for n in range(1, N + 1):
+            pr.pr_batch_set_initial_device(one, 0, chain[n - 1], pr.PR_CONSERVED, stream)
+            pr.pr_batch_run(one, nf, stream)
+            pr.pr_batch_moments_device(one, 0, chain[n], stream)
+        torch.cuda.synchronize()
+        pr.pr_batch_sync(one)
+        t_ser = time.perf_counter() - t0
+    finally:
+        pr.pr_batch_destroy(one)
+    ref = chain.cpu().numpy()
+    err = float(np.max(np.abs(par - ref)) / np.max(np.abs(ref)))
+    return {"workload": "two shocks, Nx=2048, 48^3 on [-10,10]^3, reflecting, eps=1e-4, MUSCL, T=0.05, "
+                        "N=128 (16 fine steps/slice), K=6",
+            "parareal_mixed_s": t_par, "serial_fp64_s": t_ser, "speedup": t_ser / t_par,
+            "successive_errors": [float(e) for e in errs], "max_rel_err_vs_fp64_serial": err,
+            "timing": "wall clock, parareal includes the first coarse guess and the moment readback"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -334,6 +422,16 @@ def run_ours(args):
         para = _parareal_speedup(pr, np)
     except Exception as e:  # reported, not hidden
         para = {"error": repr(e)}
+    ragged = large = None
+    try:
+        ragged = _ragged_section(pr, torch)
+    except Exception as e:
+        ragged = {"error": repr(e)}
+    if not args.no_large:
+        try:
+            large = _large_section(pr, np, torch)
+        except Exception as e:
+            large = {"error": repr(e)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -353,6 +451,8 @@ def run_ours(args):
                  "roofline": {"bound": "alu", "peak_fp64_tflops": fp64_peak_tflops,
                               "peak_source": "measured DFMA microbenchmark on this pool's GB300"}},
         "parareal": para,
+        "ragged_batch": ragged,
+        "parareal_large": large,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -368,6 +468,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="omit the host-oracle timing (used only for profiler runs)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="omit the 2048 x 48^3 parareal comparison (about 30 s, 120 GB)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -114,9 +114,15 @@ __device__ __forceinline__ float minmod2(float a, float b)
 {
     return fmaxf(0.f, fminf(a, b)) + fminf(0.f, fmaxf(a, b));
 }
+// float64: the same selection on the IEEE bit patterns with integer
+// operations only (sign bits equal -> the smaller magnitude, else 0), which
+// keeps the limiter off this GPU's reduced-rate FP64 pipe.
 __device__ __forceinline__ double minmod2(double a, double b)
 {
-    return fmax(0.0, fmin(a, b)) + fmin(0.0, fmax(a, b));
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    const long long r = ma < mb ? ia : ib;
+    return (ia ^ ib) >= 0 ? __longlong_as_double(r) : 0.0;
 }
 
 // Upwind interface value at the face between f0 and f1 (neighbours fm, f2):
@@ -158,7 +164,11 @@ __device__ void write_tables(const Inst& I, int c0, int ncols, const double* par
         const float Lf = (float)I.L, dvf = (float)I.dv;
         for (int idx = tid; idx < ncols * tw; idx += NT) {
             int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
-            float vj = -Lf + ((float)j + 0.5f) * dvf;
+            // nodes of the upper half are the exact negatives of the lower half,
+            // so the float32 tables keep the grid's mirror symmetry
+            const int jm = j < nv - 1 - j ? j : nv - 1 - j;
+            const float vlow = -Lf + ((float)jm + 0.5f) * dvf;
+            float vj = j == jm ? vlow : -vlow;
             float dvu = vj - pf[i * 5 + d];
             float val = expf(-(dvu * dvu) * pf[i * 5 + 3]);
             if (d == 0) val *= pf[i * 5 + 4];

@@ -1,0 +1,109 @@
+"""The measured workloads at their own sizes: 32 seeded ragged Sod-type
+instances in one persistent launch, and the two-shock reflecting-wall
+parareal (scaled for the oracle, and at full size against properties)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2502_02704_gb300 as pr
+from paper_2502_02704_gb300 import workloads as W
+from helpers import TOL_FP64, TOL_MIXED, moment_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged():
+    insts, Us = [], []
+    for r in W.ragged_instances(32):
+        dt = pr.fine_dt(r["nx"], r["nv"], r["L"])
+        insts.append(pr.instance(r["nx"], r["nv"], dt, L=r["L"], bc=pr.PR_BC_OUTFLOW, eps=r["eps"],
+                                 scheme=pr.PR_MUSCL))
+        Us.append(r["U"])
+    return insts, Us
+
+
+def test_ragged_batch_of_32_instances():
+    insts, Us = _ragged()
+    sizes = [d.nx * d.nv ** 3 for d in insts]
+    b = pr.pr_batch_create(insts, pr.PR_MIXED)
+    try:
+        for i, U in enumerate(Us):
+            pr.pr_batch_set_initial(b, i, U)
+        pr.pr_batch_run(b, 3)
+        V3 = [pr.pr_batch_moments(b, i) for i in range(32)]
+        pr.pr_batch_run(b, 197)
+        V200 = [pr.pr_batch_moments(b, i) for i in range(32)]
+    finally:
+        pr.pr_batch_destroy(b)
+    # sampled instances (the four smallest) against the oracle after 3 steps
+    O.set_threads(8)
+    for i in np.argsort(sizes)[:4]:
+        d = insts[i]
+        k = O.Kin(nx=d.nx, nv=d.nv, L=d.L, bc=O.BC_OUTFLOW, eps=d.eps, scheme=O.MUSCL)
+        Vo = O.project(k, O.fine_run(k, d.dt, 3, O.lift(k, Us[i])), conserved=True)
+        assert moment_rel_err(V3[i], Vo) < TOL_MIXED, i
+    O.set_threads(1)
+    for i in range(32):
+        U = V200[i]
+        rho = U[0]
+        th = (2 * U[4] / rho - (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / rho ** 2) / 3
+        assert np.all(np.isfinite(U)) and np.all(rho > 0) and np.all(th > 0), i
+    # an instance gives the same bits alone as inside the batch
+    j = int(np.argsort(sizes)[1])
+    b1 = pr.pr_batch_create([insts[j]], pr.PR_MIXED)
+    try:
+        pr.pr_batch_set_initial(b1, 0, Us[j])
+        pr.pr_batch_run(b1, 200)
+        assert np.array_equal(pr.pr_batch_moments(b1, 0), V200[j])
+    finally:
+        pr.pr_batch_destroy(b1)
+
+
+@pytest.mark.parametrize("precision,tol", [(pr.PR_FP64, TOL_FP64), (pr.PR_MIXED, TOL_MIXED)])
+def test_two_shock_reflecting_parareal_scaled(precision, tol):
+    # the two-shock workload at a size the oracle finishes quickly:
+    # Nx = 128, 16^3 on [-10, 10]^3, thirds profile, reflecting walls,
+    # eps = 1e-4, MUSCL, T = 0.05, N = 8, K = 3
+    nx, nv, L, N, K = 128, 16, 10.0, 8, 3
+    U0 = W.thirds(nx)
+    k = O.Kin(nx=nx, nv=nv, L=L, bc=O.BC_REFLECT, eps=1e-4, scheme=O.MUSCL)
+    O.set_threads(8)
+    Uo, errs_o, _ = O.parareal(O.Parareal(kin=k, T=0.05, N=N), U0, K=K)
+    O.set_threads(1)
+    ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_REFLECT, nv, L, 1e-4, 0.05, N, 0.5, 0.5, pr.PR_MUSCL, precision)
+    try:
+        pr.pr_set_initial(ctx, U0)
+        kd, errs = pr.pr_parareal_run(ctx, K)
+        for n in range(N + 1):
+            assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < tol, n
+    finally:
+        pr.pr_destroy(ctx)
+
+
+def test_two_shock_reflecting_parareal_full_size_properties():
+    # full size: Nx = 2048, 48^3 on [-10, 10]^3 (226.5 M cells per slice, FP32
+    # f), N = 128 slices resident in waves of 64 (116 GiB of f), one iteration.
+    # Walls are reflecting: the total mass of every slice equals the initial
+    # one up to the Maxwellian quadrature defect and float32 rounding, which
+    # the correction accumulates over slices (~5e-8 per fine step); the
+    # profile is mirror-symmetric about x = 1/2.
+    nx, nv, L, N = 2048, 48, 10.0, 128
+    U0 = W.thirds(nx)
+    ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_REFLECT, nv, L, 1e-4, 0.05, N, 0.5, 0.5, pr.PR_MUSCL, pr.PR_MIXED,
+                     pr.PR_SOUND_GAMMA53, 64, 0)
+    try:
+        assert pr.pr_fine_steps_per_slice(ctx)[0] == 16
+        pr.pr_set_initial(ctx, U0)
+        e1 = pr.pr_parareal_iter(ctx)
+        assert np.isfinite(e1) and e1 > 0
+        m0 = pr.pr_moments(ctx, 0)[0].sum()
+        for n in (1, 2, 64, 128):
+            V = pr.pr_moments(ctx, n)
+            assert abs(V[0].sum() - m0) < 2e-4 * m0, n
+            assert np.all(V[0] > 0)
+            assert np.max(np.abs(V[0] - V[0][::-1])) < 1e-4 * np.max(V[0])
+            assert np.max(np.abs(V[1] + V[1][::-1])) < 1e-4 * np.max(V[0])
+    finally:
+        pr.pr_destroy(ctx)
