@@ -220,6 +220,11 @@ int pr_batch_sync(pr_batch* b);
  * from the autotuner (1) or the default (0). */
 int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned);
 
+/* Set the tile width (x cells per work item, 1..64; capped at each instance's
+ * nx, and widths below 8 are raised to 8) of every instance, replacing the
+ * default or tuned width.  Synchronous. */
+int pr_batch_set_tile(pr_batch* b, int tx);
+
 /* Time candidate tile widths on the current data with CUDA events and keep the
  * fastest for each distinct instance shape (the state is saved and restored).
  * Synchronous. */

@@ -92,6 +92,7 @@ _SIGS = {
     "pr_batch_sync": (C.c_int, [_VP]),
     "pr_batch_tile": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pr_batch_autotune": (C.c_int, [_VP]),
+    "pr_batch_set_tile": (C.c_int, [_VP, C.c_int]),
     "pr_batch_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_kernel_launches": (C.c_longlong, [C.c_int]),
     "pr_batch_adjoint": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
@@ -331,6 +332,10 @@ def pr_batch_tile(b, i):
     tx, tuned = C.c_int(), C.c_int()
     _batch_check(b, lib().pr_batch_tile(b.ptr, int(i), C.byref(tx), C.byref(tuned)))
     return tx.value, bool(tuned.value)
+
+
+def pr_batch_set_tile(b, tx):
+    _batch_check(b, lib().pr_batch_set_tile(b.ptr, int(tx)))
 
 
 def pr_batch_autotune(b):

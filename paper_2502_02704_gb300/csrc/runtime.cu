@@ -629,6 +629,21 @@ int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned)
     return PR_OK;
 }
 
+int pr_batch_set_tile(pr_batch* b, int tx)
+{
+    if (!b) return PR_EINVAL;
+    if (tx < 1 || tx > prk::MAX_TX) return bfail(b, PR_EINVAL, "tile width must be in 1..%d", prk::MAX_TX);
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    std::vector<int> txs(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        // the dependency tables were sized for tiles of at least 8 cells (or the default width)
+        int t = std::min(tx, b->h[i].nx);
+        txs[i] = std::max(t, std::min(8, b->h[i].nx));
+        b->tuned[i] = 0;
+    }
+    return upload_layout(b, txs);
+}
+
 int pr_batch_kernel_time(pr_batch* b, double* avg_ms, int* launches, int reset)
 {
     if (!b) return PR_EINVAL;
@@ -758,8 +773,8 @@ extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const 
 // ------------------------------------------------------------------ autotuner
 
 // Candidate tile widths are timed with CUDA events on a copy of the current
-// state (saved and restored), one persistent launch of a few steps each; the
-// fastest width is kept for every instance of the same (nx, nv) shape.
+// state (saved and restored), one persistent launch of 16 steps each after one
+// untimed launch; the fastest width is kept for all instances.
 extern "C" int pr_batch_autotune(pr_batch* b)
 {
     if (!b) return PR_EINVAL;
@@ -794,7 +809,7 @@ extern "C" int pr_batch_autotune(pr_batch* b)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int steps = 4;
+    const int steps = 16;  // long enough for the steady state of the persistent launch
     int rc = PR_OK;
     for (int ci = 0; ci < 4 && rc == PR_OK; ++ci) {
         std::vector<int> txs(b->n);
