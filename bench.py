@@ -410,9 +410,20 @@ def run_ours(args):
             traffic = tj["dram_bytes_per_launch"]
     except Exception:
         traffic = None
-    # plain FP64: bound by the FP64 pipe on GB300 (measured DFMA rate)
+    # plain FP64: bound by the FP64 pipe on GB300 (measured DFMA rate); FP64
+    # flops per cell-update from the committed ncu counter summary
     fp64_peak_tflops = 1.01
     value64 = upd / (ms64 * 1e-3)
+    fp64_alu = None
+    try:
+        fj = json.load(open(os.path.join(ROOT, "profiles", "fine_run_fp64_flops.txt")))
+        if fj.get("fine_cu_sha256_16") == _src_hash(FINE_SRC):
+            ach = fj["fp64_flops_per_cell_update"] * upd / (kms64 * 1e-3) / 1e12
+            fp64_alu = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                        "frac": ach / fp64_peak_tflops, "flops_per_cell_update": fj["fp64_flops_per_cell_update"],
+                        "peak_source": "measured DFMA microbenchmark on this pool's GB300"}
+    except Exception:
+        fp64_alu = None
     cpu = None
     if not args.no_cpu_baseline:
         rate, cores, sample = _cpu_sample()
@@ -448,8 +459,9 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "kernel_ms": kms64,
-                 "roofline": {"bound": "alu", "peak_fp64_tflops": fp64_peak_tflops,
-                              "peak_source": "measured DFMA microbenchmark on this pool's GB300"}},
+                 "roofline": fp64_alu or {"bound": "alu", "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                                          "achieved": None, "frac": None,
+                                          "peak_source": "measured DFMA microbenchmark on this pool's GB300"}},
         "parareal": para,
         "ragged_batch": ragged,
         "parareal_large": large,

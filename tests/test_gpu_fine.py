@@ -190,3 +190,25 @@ def test_full_size_smooth_periodic_three_knudsen_numbers(precision):
         assert abs(V200[i][0].sum() - m0) < (1e-11 if precision == pr.PR_FP64 else 1e-5) * m0
         assert np.all(V200[i][0] > 0)
     O.set_threads(1)
+
+
+@pytest.mark.parametrize("tx", [8, 13, 64])
+def test_manual_tile_widths_keep_results(tx):
+    # tile width 13 leaves a ragged last tile; widths below 8 are raised to 8
+    nx, nv = 90, 8
+    dt = pr.fine_dt(nx, nv, 8.0)
+    inst = [pr.instance(nx, nv, dt, bc=pr.PR_BC_PERIODIC, eps=1e-2, scheme=pr.PR_MUSCL)]
+    b = pr.pr_batch_create(inst, pr.PR_FP64)
+    try:
+        pr.pr_batch_set_tile(b, tx)
+        assert pr.pr_batch_tile(b, 0) == (tx, False)
+        pr.pr_batch_set_initial(b, 0, W.smooth_periodic(nx))
+        pr.pr_batch_run(b, 6)
+        V = pr.pr_batch_moments(b, 0)
+        with pytest.raises(pr.PrError):
+            pr.pr_batch_set_tile(b, 65)
+    finally:
+        pr.pr_batch_destroy(b)
+    k = _kin(nx, nv, 8.0, pr.PR_BC_PERIODIC, 1e-2, pr.PR_MUSCL)
+    Vo = O.project(k, O.fine_run(k, dt, 6, O.lift(k, W.smooth_periodic(nx))), conserved=True)
+    assert moment_rel_err(V, Vo) < TOL_FP64
