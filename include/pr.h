@@ -213,6 +213,15 @@ int pr_batch_moments_device(pr_batch* b, int i, double* out_dev, void* stream);
 /* Distribution of instance i as float64 host f[nx_i][nv_i^3]. Synchronous. */
 int pr_batch_get_f(pr_batch* b, int i, double* out);
 
+/* Failure-detection check (not in the paper): one persistent launch of nsteps
+ * >= 2 steps in which the dependency waits of step 2 wait for a step that no
+ * item ever completes, with the wait limit shortened to wait_ms.  The waiting
+ * CTAs give up, record PR_ETIMEOUT and every CTA leaves the launch; the call
+ * returns that status after clearing it (PR_ETIMEOUT is the expected result).
+ * The batch stays usable; its instance states are unspecified until they are
+ * set again.  No GPU fault is involved.  Synchronous. */
+int pr_batch_inject_wait_timeout(pr_batch* b, int nsteps, int wait_ms);
+
 /* Wait for the batch stream and report any device-side error. */
 int pr_batch_sync(pr_batch* b);
 

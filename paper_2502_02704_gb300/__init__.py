@@ -90,6 +90,7 @@ _SIGS = {
     "pr_batch_moments_device": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "pr_batch_get_f": (C.c_int, [_VP, C.c_int, _D]),
     "pr_batch_sync": (C.c_int, [_VP]),
+    "pr_batch_inject_wait_timeout": (C.c_int, [_VP, C.c_int, C.c_int]),
     "pr_batch_tile": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pr_batch_autotune": (C.c_int, [_VP]),
     "pr_batch_set_tile": (C.c_int, [_VP, C.c_int]),
@@ -322,6 +323,12 @@ def pr_batch_get_f(b, i):
     out = np.empty((nx, nv ** 3))
     _batch_check(b, lib().pr_batch_get_f(b.ptr, int(i), _p(out)))
     return out
+
+
+def pr_batch_inject_wait_timeout(b, nsteps=3, wait_ms=50) -> int:
+    """Run the failure-detection launch; returns the status it reported
+    (PR_ETIMEOUT expected) without raising."""
+    return int(lib().pr_batch_inject_wait_timeout(b.ptr, int(nsteps), int(wait_ms)))
 
 
 def pr_batch_sync(b):

@@ -40,7 +40,6 @@ namespace prk {
 
 namespace {
 
-constexpr unsigned long long TIMEOUT_NS = 4000000000ULL;  // 4 s per wait
 constexpr double PI = 3.14159265358979323846;
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -301,7 +300,8 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
 
 // Wait until every tile in deps[xt] has finalised step `target`.  Called by
 // warp 0: lane k spins on dependency k, so the flags are polled in parallel.
-__device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status, int lane)
+__device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status, int lane,
+                           unsigned long long limit_ns)
 {
     bool ok = true;
     if (lane < MAXDEP) {
@@ -315,7 +315,7 @@ __device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status, 
                     ok = false;
                     break;
                 }
-                if (gtimer() - t0 > TIMEOUT_NS) {
+                if (gtimer() - t0 > limit_ns) {
                     atomicCAS(status, 0, ST_TIMEOUT);
                     ok = false;
                     break;
@@ -619,7 +619,7 @@ template <typename T, int SCHEME, int V>
 __global__ void __launch_bounds__(CHUNK / V, MinBlocks<T, V>::value)
 k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
            const long long* __restrict__ prefix, const Active* __restrict__ active, int nsteps,
-           unsigned long long* ticket, int* status, int waits)
+           unsigned long long* ticket, int* status, long long wait_ns, int poison)
 {
     constexpr int H = SCHEME == 1 ? 2 : 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -653,9 +653,12 @@ k_fine_run(const Inst* __restrict__ insts, const InstState* __restrict__ st,
         // items of the next step find their dependencies finished
         const int pidx = loc / I.n_vc, vc = loc - pidx * I.n_vc;
         const int xt = (pidx & 1) ? I.n_xt - 1 - (pidx >> 1) : (pidx >> 1);
-        if (waits && s > 1) {
+        if (wait_ns > 0 && s > 1) {
+            // poison (failure-detection check): the items of step 2 wait for a
+            // step that never completes, so the bounded wait runs out
+            const unsigned target = (poison && s == 2) ? 0xffffffffu : (unsigned)(s - 1);
             if (tid < 32) {
-                bool ok = wait_tiles(I, xt, (unsigned)(s - 1), status, tid);
+                bool ok = wait_tiles(I, xt, target, status, tid, (unsigned long long)wait_ns);
                 if (tid == 0) s_ok = ok ? 1 : 0;
             }
             __syncthreads();
@@ -847,12 +850,12 @@ int fine_run_occupancy(int precision, int scheme, int vpt, size_t smem, int* blo
 
 cudaError_t launch_fine_run(int precision, int scheme, int vpt, const Inst* insts, InstState* st,
                             const long long* prefix, const Active* active, int nsteps,
-                            unsigned long long* ticket, int* status, int waits, int grid, size_t smem,
-                            cudaStream_t s)
+                            unsigned long long* ticket, int* status, long long wait_ns, int grid, size_t smem,
+                            cudaStream_t s, int poison)
 {
     if (precision == 0) vpt = 4;
     void* args[] = {(void*)&insts, (void*)&st, (void*)&prefix, (void*)&active, (void*)&nsteps,
-                    (void*)&ticket, (void*)&status, (void*)&waits};
+                    (void*)&ticket, (void*)&status, (void*)&wait_ns, (void*)&poison};
     return cudaLaunchKernel(fine_kernel(precision, scheme, vpt), dim3(grid), dim3(CHUNK / vpt), args, smem, s);
 }
 

@@ -153,7 +153,7 @@ extern "C" int pr_fine_step_noalloc(const pr_instance* d, const double* f_in, do
     long long items = prefix[1];
     int grid = (int)(items < (long long)per_sm * sms ? items : (long long)per_sm * sms);
     e = prk::launch_fine_run(0, d->scheme, 4, dI, dS, reinterpret_cast<const long long*>(base + o_prefix), dA, 1,
-                             reinterpret_cast<unsigned long long*>(base + o_sync), dstatus, 0, grid, smem, s);
+                             reinterpret_cast<unsigned long long*>(base + o_sync), dstatus, 0LL, grid, smem, s);
     // f_out now holds f*; apply the implicit relaxation in place: f = a f* + b M
     if (e == cudaSuccess) e = prk::launch_advance(dI, dS, dA, 1, 1, s);
     if (e == cudaSuccess) e = prk::launch_materialize(0, dI, dS, 0, I, f_out, s);

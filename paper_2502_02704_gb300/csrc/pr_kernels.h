@@ -13,6 +13,7 @@ constexpr int WARPS = THREADS / 32;
 constexpr int MAXDEP = 8;                // neighbour tiles an item may wait on
 constexpr int MAX_TX = 64;               // largest tile width (x cells per item)
 
+constexpr long long WAIT_LIMIT_NS = 4000000000LL;  // a dependency wait gives up after 4 s
 constexpr int ST_OK = 0;
 constexpr int ST_TIMEOUT = -4;           // = PR_ETIMEOUT
 constexpr int ST_NONPHYS = -5;           // = PR_ENONPHYS
@@ -54,10 +55,13 @@ struct Active {
 // Persistent fused fine-step kernel over the active instances for nsteps steps.
 // vpt: velocities per thread (4, or 8 in float32 when every nv is a multiple
 // of 8); the CTA has CHUNK / vpt threads.
+// wait_ns: limit of each dependency wait (<= 0: no waits, for one-step launches);
+// poison = 1 makes the items of step 2 wait for a step that never completes
+// (failure-detection check: the wait runs out and the launch reports PR_ETIMEOUT).
 cudaError_t launch_fine_run(int precision, int scheme, int vpt, const Inst* insts, InstState* st,
                             const long long* prefix, const Active* active, int nsteps,
-                            unsigned long long* ticket, int* status, int waits, int grid,
-                            size_t smem, cudaStream_t s);
+                            unsigned long long* ticket, int* status, long long wait_ns, int grid,
+                            size_t smem, cudaStream_t s, int poison = 0);
 int fine_run_occupancy(int precision, int scheme, int vpt, size_t smem, int* blocks_per_sm);
 size_t fine_run_smem(int precision, int vpt, int tx, int nv, int H);
 

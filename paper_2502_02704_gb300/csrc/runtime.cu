@@ -420,7 +420,8 @@ static void fold_events(pr_batch* b)
 }
 
 // Enqueue one persistent run over the active range already set on the device.
-static int enqueue_run(pr_batch* b, int nsteps, int project_out, cudaStream_t s, bool count_timing)
+static int enqueue_run(pr_batch* b, int nsteps, int project_out, cudaStream_t s, bool count_timing,
+                       long long wait_ns = prk::WAIT_LIMIT_NS, int poison = 0)
 {
     (void)project_out;
     BCUDA(b, cudaMemsetAsync(b->d_sync, 0, b->sync_bytes, s));
@@ -433,7 +434,7 @@ static int enqueue_run(pr_batch* b, int nsteps, int project_out, cudaStream_t s,
     }
     BCUDA(b, prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state, b->d_prefix,
                                   b->d_active, nsteps, reinterpret_cast<unsigned long long*>(b->d_sync),
-                                  b->d_status, nsteps > 1 ? 1 : 0, b->grid, b->smem, s));
+                                  b->d_status, nsteps > 1 ? wait_ns : 0, b->grid, b->smem, s, poison));
     if (e1) {
         cudaEventRecord(e1, s);
         b->ev_pending.push_back({e0, e1});
@@ -577,6 +578,16 @@ int pr_batch_run(pr_batch* b, int nsteps, void* stream)
     if (nsteps < 0) return bfail(b, PR_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return PR_OK;
     return enqueue_run(b, nsteps, 0, pick(b, stream), true);
+}
+
+int pr_batch_inject_wait_timeout(pr_batch* b, int nsteps, int wait_ms)
+{
+    if (!b) return PR_EINVAL;
+    if (nsteps < 2 || wait_ms < 1) return bfail(b, PR_EINVAL, "needs nsteps >= 2 and wait_ms >= 1");
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    int rc = enqueue_run(b, nsteps, 0, b->stream, false, (long long)wait_ms * 1000000LL, 1);
+    if (rc) return rc;
+    return take_status(b, b->stream);
 }
 
 int pr_batch_sync(pr_batch* b)
@@ -1164,7 +1175,7 @@ static int build_graph(pr_ctx* c)
     if (e == cudaSuccess)
         e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state, b->d_prefix,
                                  b->d_active, c->nf, reinterpret_cast<unsigned long long*>(b->d_sync), b->d_status,
-                                 c->nf > 1 ? 1 : 0, b->grid, b->smem, s);
+                                 c->nf > 1 ? prk::WAIT_LIMIT_NS : 0, b->grid, b->smem, s);
     if (e == cudaSuccess)
         e = prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
                               c->dk, s);

@@ -1,0 +1,79 @@
+"""Failure detection on the device without a GPU fault: a dependency wait of
+the persistent launch that runs out (a flag nothing sets), non-physical
+states, and that each object stays usable afterwards."""
+import numpy as np
+import pytest
+
+import paper_2502_02704_gb300 as pr
+from paper_2502_02704_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(precision=pr.PR_MIXED):
+    nx, nv = 64, 8
+    dt = pr.fine_dt(nx, nv, 8.0)
+    return pr.pr_batch_create([pr.instance(nx, nv, dt, bc=pr.PR_BC_PERIODIC, eps=1e-2, scheme=pr.PR_MUSCL)],
+                              precision)
+
+
+def _reference_run(steps):
+    b = _batch()
+    try:
+        pr.pr_batch_set_initial(b, 0, W.smooth_periodic(64))
+        pr.pr_batch_run(b, steps)
+        return pr.pr_batch_moments(b, 0)
+    finally:
+        pr.pr_batch_destroy(b)
+
+
+def test_dependency_wait_runs_out_and_batch_stays_usable():
+    b = _batch()
+    try:
+        pr.pr_batch_set_initial(b, 0, W.smooth_periodic(64))
+        for wait_ms in (20, 50):
+            assert pr.pr_batch_inject_wait_timeout(b, 3, wait_ms) == pr.PR_ETIMEOUT
+            assert "timed out" in pr.pr_batch_last_error(b)
+        # the status was cleared: a normal run afterwards gives the normal bits
+        pr.pr_batch_set_initial(b, 0, W.smooth_periodic(64))
+        pr.pr_batch_run(b, 5)
+        V = pr.pr_batch_moments(b, 0)
+    finally:
+        pr.pr_batch_destroy(b)
+    assert np.array_equal(V, _reference_run(5))
+
+
+def test_nonphysical_state_is_reported_and_cleared():
+    b = _batch(pr.PR_FP64)
+    try:
+        f = W.random_positive_f(64, 8, seed=2)
+        f[10] *= -1.0  # negative density in x cell 10
+        pr.pr_batch_set_f(b, 0, f)
+        pr.pr_batch_run(b, 2)
+        with pytest.raises(pr.PrError) as ei:
+            pr.pr_batch_sync(b)
+        assert ei.value.code == pr.PR_ENONPHYS
+        pr.pr_batch_set_initial(b, 0, W.smooth_periodic(64))
+        pr.pr_batch_run(b, 2)
+        pr.pr_batch_sync(b)
+        assert np.all(pr.pr_batch_moments(b, 0, pr.PR_PRIMITIVE)[4] > 0)
+    finally:
+        pr.pr_batch_destroy(b)
+
+
+def test_coarse_solver_reports_negative_temperature():
+    nx = 32
+    ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, 4, 8.0, 1e-2, 0.1, 2)
+    try:
+        V = np.zeros((5, nx))
+        V[0] = 1.0
+        V[4] = 1.0
+        V[4, 7] = -0.5  # energy below the kinetic part: theta < 0
+        with pytest.raises(pr.PrError) as ei:
+            pr.pr_coarse_step(ctx, V, 0.01)
+        assert ei.value.code == pr.PR_ENONPHYS
+        V[4, 7] = 1.0
+        out = pr.pr_coarse_step(ctx, V, 0.01)
+        assert np.all(np.isfinite(out))
+    finally:
+        pr.pr_destroy(ctx)
