@@ -358,6 +358,7 @@ def run_ours(args):
     dv = 2 * L / NV
     dt = 0.5 * (1.0 / NX) / (L - 0.5 * dv)
     cells = len(EPSS) * NX * NV ** 3
+    upd = cells * NSTEPS
     U = W.smooth_periodic(NX)
     # conserved state for the device-side lift
     Vnp = np.stack([U[0], U[0] * U[1], U[0] * U[2], U[0] * U[3],
