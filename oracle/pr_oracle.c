@@ -409,9 +409,12 @@ static void rusanov(int nx, int bc, int sound, const double* V, int c, double* H
 }
 
 /* G over dT: explicit Rusanov updates, Eq. (15) with reading R2, local steps
- * dt = min(cfl dx / max S, remaining) until dT is reached (Sec. 2.2). */
-int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
-                  double dT, const double* Vin, double* Vout, int* nsub)
+ * dt = min(cfl dx / max S, remaining) until dT is reached (Sec. 2.2).  With an
+ * exterior force E [nx] (NULL: none) each local step adds dt S(V_i), the source
+ * S = (0, rho E_i, 0, 0, rho u_x E_i) of the Euler system Eq. (5) (reading R18:
+ * forward Euler, the force at the cell centre). */
+static int coarse_run_impl(int nx, double x0, double x1, int bc, double cfl, int sound,
+                           double dT, const double* E, const double* Vin, double* Vout, int* nsub)
 {
     if (nx < 1 || !(x1 > x0) || !(cfl > 0.0) || dT < 0.0) return OR_EINVAL;
     double dx = (x1 - x0) / nx;
@@ -449,6 +452,10 @@ int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
             rusanov(nx, bc, sound, V, i, Hr);
             rusanov(nx, bc, sound, V, i - 1, Hl);
             for (int q = 0; q < 5; ++q) W[q * nx + i] = V[q * nx + i] - dt / dx * (Hr[q] - Hl[q]);
+            if (E) {
+                W[1 * nx + i] += dt * V[0 * nx + i] * E[i];
+                W[4 * nx + i] += dt * V[1 * nx + i] * E[i];
+            }
         }
         memcpy(V, W, sizeof(double) * 5 * nx);
         ++steps;
@@ -460,6 +467,18 @@ int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
     free(V);
     free(W);
     return rc;
+}
+
+int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
+                  double dT, const double* Vin, double* Vout, int* nsub)
+{
+    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, NULL, Vin, Vout, nsub);
+}
+
+int or_coarse_run_force(int nx, double x0, double x1, int bc, double cfl, int sound,
+                        double dT, const double* E, const double* Vin, double* Vout, int* nsub)
+{
+    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, E, Vin, Vout, nsub);
 }
 
 /* ---------------- propagators and the parareal algorithms ---------------- */
@@ -499,14 +518,30 @@ int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout)
  * errs[k-1] is the Eq. (10) error of iteration k (reading R7).  With tol > 0
  * the loop stops after the first iteration whose error is below tol; levels
  * after *k_done are left as copies of level *k_done. */
+static int prop_fine(const void* p, const double* Vin, double* Vout)
+{
+    return or_fine_propagate((const or_pr*)p, Vin, Vout);
+}
+
+static int prop_coarse(const void* p, const double* Vin, double* Vout)
+{
+    return or_coarse_propagate((const or_pr*)p, Vin, Vout);
+}
+
 int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
                 double* Uall, double* errs, int* k_done)
 {
-    const or_kin* k0 = &p->kin;
-    int rc = check_kin(k0);
+    int rc = check_kin(&p->kin);
     if (rc) return rc;
-    if (p->N < 1 || K < 0 || (alg != 1 && alg != 2)) return OR_EINVAL;
-    int nx = k0->nx, N = p->N;
+    return or_parareal_core(p->kin.nx, p->N, prop_fine, prop_coarse, p, U0, K, tol, alg, Uall, errs, k_done);
+}
+
+/* The loop of Algorithms 1 and 2 over any pair of propagators PFL and G. */
+int or_parareal_core(int nx, int N, or_prop fine, or_prop coarse, const void* ctx, const double* U0,
+                     int K, double tol, int alg, double* Uall, double* errs, int* k_done)
+{
+    int rc = OR_OK;
+    if (nx < 1 || N < 1 || K < 0 || (alg != 1 && alg != 2)) return OR_EINVAL;
     long lvl = (long)(N + 1) * 5 * nx;
     double* D = malloc(sizeof(double) * lvl);  /* jumps Delta^n */
     double* a = malloc(sizeof(double) * 5 * nx);
@@ -519,19 +554,19 @@ int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
     }
 #define UL(kk, n) (Uall + (long)(kk) * lvl + (long)(n) * 5 * nx)
     or_prim_to_cons(nx, U0, UL(0, 0));
-    for (int n = 1; n <= N && !rc; ++n) rc = or_coarse_propagate(p, UL(0, n - 1), UL(0, n));
+    for (int n = 1; n <= N && !rc; ++n) rc = coarse(ctx, UL(0, n - 1), UL(0, n));
     int done = 0;
     for (int k = 1; k <= K && !rc; ++k) {
         int start = alg == 2 ? k : 1;
         if (start > N + 1) start = N + 1;
         for (int n = 0; n < start && n <= N; ++n) memcpy(UL(k, n), UL(k - 1, n), sizeof(double) * 5 * nx);
         for (int n = start; n <= N && !rc; ++n) {
-            rc = or_fine_propagate(p, UL(k - 1, n - 1), a);
-            if (!rc) rc = or_coarse_propagate(p, UL(k - 1, n - 1), b);
+            rc = fine(ctx, UL(k - 1, n - 1), a);
+            if (!rc) rc = coarse(ctx, UL(k - 1, n - 1), b);
             for (int q = 0; q < 5 * nx; ++q) D[(long)n * 5 * nx + q] = a[q] - b[q];
         }
         for (int n = start; n <= N && !rc; ++n) {
-            rc = or_coarse_propagate(p, UL(k, n - 1), b);
+            rc = coarse(ctx, UL(k, n - 1), b);
             for (int q = 0; q < 5 * nx; ++q) UL(k, n)[q] = b[q] + D[(long)n * 5 * nx + q];
         }
         double err = 0.0;

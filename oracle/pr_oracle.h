@@ -78,6 +78,54 @@ int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout);
 int or_parareal(const or_pr* p, const double* U0, int K, double tol, int alg,
                 double* Uall, double* errs, int* k_done);
 
+/* A propagator V(T^{n-1}) -> V(T^n) on conserved [5][nx] states. */
+typedef int (*or_prop)(const void* ctx, const double* Vin, double* Vout);
+
+/* The loop of Algorithms 1 and 2 over the propagators fine (P F L) and coarse (G);
+ * same conventions as or_parareal. */
+int or_parareal_core(int nx, int N, or_prop fine, or_prop coarse, const void* ctx, const double* U0,
+                     int K, double tol, int alg, double* Uall, double* errs, int* k_done);
+
+/* ---------------- exterior force E != 0 (pr_oracle_force.c) ----------------
+ * Eq. (11) with the force term E . grad_v f, the velocity flux G of Eq. (13)
+ * along v_x, and the Euler source of Eq. (5).  The velocity grid is
+ * anisotropic (Test 3): nvx cells along v_x and nvp along each of v_y, v_z,
+ * all on [-L, L].  f[i][j] with j = (jx*nvp + jy)*nvp + jz. */
+typedef struct {
+    int nx;
+    double x0, x1;
+    int bc;
+    int nvx;          /* velocity cells along v_x                              */
+    int nvp;          /* velocity cells along each of v_y and v_z              */
+    double L;
+    double eps;       /* Knudsen number; +inf means collisionless              */
+    int scheme;       /* x transport: OR_UPWIND or OR_MUSCL                    */
+    const double* E;  /* [nx] exterior force at the cell centres; NULL: E = 0  */
+} or_vkin;
+
+typedef struct {
+    or_vkin kin;
+    double T;
+    int N;
+    double cfl_f, cfl_g;
+    int sound;
+    int nf;
+} or_vpr;
+
+int or_coarse_run_force(int nx, double x0, double x1, int bc, double cfl, int sound,
+                        double dT, const double* E, const double* Vin, double* Vout, int* nsub);
+int or_v_lift(const or_vkin* k, const double* U, double* f);
+int or_v_project(const or_vkin* k, const double* f, double* U);
+int or_v_project_cons(const or_vkin* k, const double* f, double* V);
+double or_v_fine_dt_stab(const or_vkin* k, double cfl);
+int or_v_fine_nsteps(const or_vpr* p, double* dt_out);
+int or_v_fine_step(const or_vkin* k, double dt, const double* f, double* fout);
+int or_v_fine_run(const or_vkin* k, double dt, int nsteps, double* f);
+int or_v_fine_propagate(const or_vpr* p, const double* Vin, double* Vout);
+int or_v_coarse_propagate(const or_vpr* p, const double* Vin, double* Vout);
+int or_v_parareal(const or_vpr* p, const double* U0, int K, double tol, int alg,
+                  double* Uall, double* errs, int* k_done);
+
 /* Gradient of J(V(T)) w.r.t. the primitive initial state U0 [5][nx] and log eps,
  * given lamV = dJ/dV(T) [5][nx] (conserved final moments); upwind scheme. */
 int or_adjoint(const or_kin* k, double dt, int nsteps, const double* U0, const double* lamV,
