@@ -1,7 +1,8 @@
 /*
  * libpr — GB300 (sm_103a) kinetic-fluid parareal library for the collisional
- * Vlasov-BGK equation in the hyperbolic scaling (alpha = 0, E = 0), 1D in x and
- * 3D in v, after Laidin & Rey, arXiv 2502.02704.
+ * Vlasov-BGK equation in the hyperbolic scaling (alpha = 0), 1D in x and 3D in
+ * v, after Laidin & Rey, arXiv 2502.02704: without a force field (E = 0, the
+ * pr_init / pr_batch_* path) and with one (the pr_force_* / pr_init_force path).
  *
  * C ABI: every entry point takes plain pointers and sizes and returns an int
  * status (PR_OK = 0, negative on error).  Nothing aborts or exits.  Objects are
@@ -286,6 +287,101 @@ long long pr_kernel_launches(int reset);
  * the device status (PR_ENONPHYS for a non-physical state, PR_ECUDA on a
  * runtime error). */
 int pr_fine_step_noalloc(const pr_instance* inst, const double* f_in, double* f_out, void* stream);
+
+/* ============ exterior force E != 0 (Eqs. 5, 11-13; Test 3) ============ */
+
+/* The collisional Vlasov equation with a force field E(x) along x:
+ * d_t f + v_x d_x f + E d_{v_x} f = (M[f] - f)/eps, and the Euler system with
+ * the source (0, rho E, 0, 0, rho u_x E) of Eq. (5) as coarse model.
+ * Readings (the same as the oracle's): the force enters with the + sign of
+ * Eqs. (5), (11) and the flux of Eq. (13) (Eq. 1 prints -E.grad_v f); the v_x
+ * flux is the Rusanov flux G_{i,a+1/2} = E_i/2 (f_a + f_{a+1}) - E_max/2
+ * (f_{a+1} - f_a), E_max = max_i |E_i|, with no flux through v_x = -L or +L
+ * (Eq. 13 prints a viscosity term that vanishes identically); the 1/dv_x of the
+ * divergence is inserted; the coarse solver adds the source forward-Euler on
+ * the state before each local step; the stable fine step is
+ * dt_stab = cfl / (max|v_x| / dx + E_max / dv_x).
+ * Velocity grid: nvx cells along v_x and nvp along each of v_y and v_z, all on
+ * [-L, L] (Test 3 refines v_x only).  f[nx][nvx nvp^2], velocity index
+ * (jx*nvp + jy)*nvp + jz.  No 16-byte rule on nvp here.
+ * Each fine step is one kernel launch in which a cluster of CTAs owns one x
+ * column: transport in x and v_x, velocity moments exchanged through
+ * distributed shared memory, Maxwellian and implicit BGK. */
+
+typedef struct pr_force pr_force;  /* independent force-path instances        */
+
+typedef struct {
+    int nx;
+    double x0, x1;
+    int bc;            /* PR_BC_*                                              */
+    int nvx;           /* velocity cells along v_x (>= 2)                      */
+    int nvp;           /* velocity cells along each of v_y, v_z (1..64)        */
+    double L;          /* velocity box [-L, L]^3                               */
+    double eps;        /* Knudsen number > 0; +INFINITY = collisionless        */
+    double dt;         /* fine time step > 0                                   */
+    const double* E;   /* host [nx]: force at the cell centres, copied at
+                          creation; NULL means E = 0                           */
+} pr_force_instance;
+
+/* Create n instances that share nx, nvx, nvp (the other fields may differ),
+ * one x-transport scheme (PR_UPWIND or PR_MUSCL) and one precision.  Allocates
+ * two state buffers per instance.  A column of nvx nvp^2 cells is split over at
+ * most 16 CTAs, each staging its share of f* in shared memory; columns above
+ * 16 x 96 KiB (393,216 cells in PR_MIXED, 196,608 in PR_FP64) are rejected
+ * with PR_EINVAL.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
+int pr_force_create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int precision);
+
+int pr_force_destroy(pr_force* b);
+
+const char* pr_force_last_error(const pr_force* b);
+
+/* Lift instance i from host U[5][nx] (kind PR_PRIMITIVE or PR_CONSERVED):
+ * the pointwise Maxwellian of Eq. (17).  Synchronous.
+ * Errors: PR_EINVAL, PR_ENONPHYS, PR_ECUDA. */
+int pr_force_set_initial(pr_force* b, int i, const double* U, int kind);
+
+/* Load an arbitrary distribution f[nx][nvx nvp^2] (host float64, rounded to
+ * float32 in PR_MIXED), e.g. Test 3's two beams.  Synchronous. */
+int pr_force_set_f(pr_force* b, int i, const double* f);
+
+/* Advance every instance by nsteps fine steps (one launch per step), enqueued
+ * on stream (NULL: the object's stream). */
+int pr_force_run(pr_force* b, int nsteps, void* stream);
+
+/* Moments (Eq. 18) of instance i's current state into host out[5][nx].
+ * Synchronous; reports device-side errors of earlier runs. */
+int pr_force_moments(pr_force* b, int i, int kind, double* out);
+
+/* Instance i's distribution as float64 host f[nx][nvx nvp^2]. Synchronous. */
+int pr_force_get_f(pr_force* b, int i, double* out);
+
+/* Wait for the object's stream and report any device-side error. */
+int pr_force_sync(pr_force* b);
+
+/* CTAs per x column (the cluster size) and velocities per CTA in use. */
+int pr_force_config(const pr_force* b, int* cluster, int* chunk);
+
+/* Use `cluster` CTAs per x column (1..16) if the chunk fits shared memory;
+ * PR_EINVAL otherwise (the previous setting stays).  Synchronous. */
+int pr_force_set_cluster(pr_force* b, int cluster);
+
+/* Average duration in ms of one step launch over the runs since the last
+ * reset (CUDA events on the launching stream around each run, divided by its
+ * steps); reset = 1 clears the accumulator. */
+int pr_force_kernel_time(pr_force* b, double* avg_ms, int* steps, int reset);
+
+/* dt_stab of the reading above for inst (E read from the host array).
+ * Errors: PR_EINVAL. */
+int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt);
+
+/* A parareal problem with the force: as pr_init, with v->nv cells along v_y
+ * and v_z, nvx along v_x, and E (host [nx], copied; NULL = 0).  The fine
+ * propagator is the force path above (scheme and precision from t), the
+ * coarse propagator the Euler system with the source, n_f (t->nf = 0) from
+ * dt_stab with the force.  Every pr_* call on a parareal problem works on the
+ * result.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
+int pr_init_force(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t, int nvx,
+                  const double* E);
 
 #ifdef __cplusplus
 }

@@ -62,6 +62,13 @@ class pr_instance(C.Structure):
 
 _D = C.POINTER(C.c_double)
 _VP = C.c_void_p
+
+
+class pr_force_instance(C.Structure):
+    _fields_ = [("nx", C.c_int), ("x0", C.c_double), ("x1", C.c_double), ("bc", C.c_int), ("nvx", C.c_int),
+                ("nvp", C.c_int), ("L", C.c_double), ("eps", C.c_double), ("dt", C.c_double), ("E", _D)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -98,6 +105,21 @@ _SIGS = {
     "pr_kernel_launches": (C.c_longlong, [C.c_int]),
     "pr_batch_adjoint": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
     "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
+    "pr_force_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_force_instance), C.c_int, C.c_int, C.c_int]),
+    "pr_force_destroy": (C.c_int, [_VP]),
+    "pr_force_last_error": (C.c_char_p, [_VP]),
+    "pr_force_set_initial": (C.c_int, [_VP, C.c_int, _D, C.c_int]),
+    "pr_force_set_f": (C.c_int, [_VP, C.c_int, _D]),
+    "pr_force_run": (C.c_int, [_VP, C.c_int, _VP]),
+    "pr_force_moments": (C.c_int, [_VP, C.c_int, C.c_int, _D]),
+    "pr_force_get_f": (C.c_int, [_VP, C.c_int, _D]),
+    "pr_force_sync": (C.c_int, [_VP]),
+    "pr_force_config": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pr_force_set_cluster": (C.c_int, [_VP, C.c_int]),
+    "pr_force_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
+    "pr_force_dt_stab": (C.c_int, [C.POINTER(pr_force_instance), C.c_double, _D]),
+    "pr_init_force": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_grid), C.POINTER(pr_velocity), C.c_double,
+                                C.POINTER(pr_time), C.c_int, _D]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -223,7 +245,7 @@ def pr_fine_moments(ctx, slice_, kind=PR_CONSERVED):
 
 
 def pr_fine_get_f(ctx, slice_):
-    out = np.empty((ctx.nx, ctx.nv ** 3))
+    out = np.empty((ctx.nx, getattr(ctx, "nvx", ctx.nv) * ctx.nv ** 2))
     _ctx_check(ctx, lib().pr_fine_get_f(ctx.ptr, int(slice_), _p(out)))
     return out
 
@@ -384,6 +406,116 @@ def fine_dt(nx, nv, L, cfl=0.5, x0=0.0, x1=1.0) -> float:
     """dt_stab = cfl dx / max|v_x| of the x transport (Sec. 2.2)."""
     dv = 2.0 * L / nv
     return cfl * ((x1 - x0) / nx) / (L - 0.5 * dv)
+
+
+# ---------------------------------------------------------------- exterior force
+
+class ForceInstance:
+    """One force-path instance: pr_force_instance plus the force array it
+    points at (kept alive here; the library copies it at creation)."""
+
+    def __init__(self, nx, nvx, nvp, dt, L=8.0, x0=0.0, x1=1.0, bc=PR_BC_PERIODIC, eps=1e-2, E=None):
+        self.E = None if E is None else _f64(E, (nx,))
+        self.c = pr_force_instance(int(nx), float(x0), float(x1), int(bc), int(nvx), int(nvp), float(L),
+                                   float(eps), float(dt), _p(self.E) if self.E is not None else C.cast(None, _D))
+        self.nx, self.nvx, self.nvp = int(nx), int(nvx), int(nvp)
+
+
+def _force_check(b, rc):
+    if rc != PR_OK:
+        msg = lib().pr_force_last_error(b.ptr if b is not None else None)
+        raise PrError(rc, (msg or b"").decode())
+
+
+def pr_force_create(instances, scheme=PR_UPWIND, precision=PR_MIXED):
+    n = len(instances)
+    arr = (pr_force_instance * n)(*[d.c for d in instances])
+    out = _VP()
+    rc = lib().pr_force_create(C.byref(out), arr, n, int(scheme), int(precision))
+    if rc != PR_OK:
+        raise PrError(rc, (lib().pr_force_last_error(None) or b"").decode())
+    d = instances[0]
+    return _Handle(out, "pr_force", n=n, nx=d.nx, nvx=d.nvx, nvp=d.nvp, ncol=d.nvx * d.nvp ** 2)
+
+
+def pr_force_destroy(b):
+    if b is not None and b.ptr:
+        lib().pr_force_destroy(b.ptr)
+        b.ptr = _VP()
+
+
+def pr_force_last_error(b=None) -> str:
+    return (lib().pr_force_last_error(b.ptr if b is not None else None) or b"").decode()
+
+
+def pr_force_set_initial(b, i, U, kind=PR_PRIMITIVE):
+    U = _f64(U, (5, b.nx))
+    _force_check(b, lib().pr_force_set_initial(b.ptr, int(i), _p(U), int(kind)))
+
+
+def pr_force_set_f(b, i, f):
+    f = _f64(f, (b.nx, b.ncol))
+    _force_check(b, lib().pr_force_set_f(b.ptr, int(i), _p(f)))
+
+
+def pr_force_run(b, nsteps, stream=None):
+    _force_check(b, lib().pr_force_run(b.ptr, int(nsteps), _stream(stream)))
+
+
+def pr_force_moments(b, i, kind=PR_CONSERVED):
+    out = np.empty((5, b.nx))
+    _force_check(b, lib().pr_force_moments(b.ptr, int(i), int(kind), _p(out)))
+    return out
+
+
+def pr_force_get_f(b, i):
+    out = np.empty((b.nx, b.ncol))
+    _force_check(b, lib().pr_force_get_f(b.ptr, int(i), _p(out)))
+    return out
+
+
+def pr_force_sync(b):
+    _force_check(b, lib().pr_force_sync(b.ptr))
+
+
+def pr_force_config(b):
+    c, k = C.c_int(), C.c_int()
+    _force_check(b, lib().pr_force_config(b.ptr, C.byref(c), C.byref(k)))
+    return c.value, k.value
+
+
+def pr_force_set_cluster(b, cluster):
+    _force_check(b, lib().pr_force_set_cluster(b.ptr, int(cluster)))
+
+
+def pr_force_kernel_time(b, reset=False):
+    ms = C.c_double()
+    n = C.c_int()
+    _force_check(b, lib().pr_force_kernel_time(b.ptr, C.byref(ms), C.byref(n), int(bool(reset))))
+    return ms.value, n.value
+
+
+def pr_force_dt_stab(inst: ForceInstance, cfl=0.5) -> float:
+    dt = C.c_double()
+    rc = lib().pr_force_dt_stab(C.byref(inst.c), float(cfl), C.byref(dt))
+    if rc != PR_OK:
+        raise PrError(rc, "pr_force_dt_stab")
+    return dt.value
+
+
+def pr_init_force(nx, x0, x1, bc, nvx, nvp, L, eps, T, n_slices, E, cfl_f=0.5, cfl_g=0.5, scheme=PR_UPWIND,
+                  precision=PR_FP64, sound_speed=PR_SOUND_GAMMA53, max_batch=0, nf=0):
+    """Parareal problem with the exterior force E [nx] (host, copied)."""
+    g = pr_grid(nx, x0, x1, bc)
+    v = pr_velocity(nvp, L)
+    t = pr_time(T, n_slices, cfl_f, cfl_g, scheme, precision, sound_speed, max_batch, nf)
+    Ea = None if E is None else _f64(E, (nx,))
+    out = _VP()
+    rc = lib().pr_init_force(C.byref(out), C.byref(g), C.byref(v), float(eps), C.byref(t), int(nvx),
+                             _p(Ea) if Ea is not None else C.cast(None, _D))
+    if rc != PR_OK:
+        raise PrError(rc, (lib().pr_last_error(None) or b"").decode())
+    return _Handle(out, "pr_ctx", nx=nx, nv=nvp, nvx=nvx, N=n_slices)
 
 
 INF = math.inf

@@ -24,6 +24,8 @@ UNITS = {
     "runtime.cu": [],
     "noalloc.cu": [],
     "adjoint.cu": [],
+    "force.cu": [],
+    "force_runtime.cu": [],
 }
 
 

@@ -8,6 +8,8 @@
 //   printed sqrt(theta)), local steps dt = min(cfl dx / max S, remaining) until
 //   the coarse interval is covered (Sec. 2.2).  Ghost cells: periodic wrap,
 //   outflow copy, reflecting mirror with rho u_x negated.
+// With an exterior force E (Eq. 5) each local step adds dt (0, rho E_i, 0, 0,
+// rho u_x E_i) evaluated on the state before the step.
 // Sweep: Algorithm 2's sequential loop U^{n,k} = G(U^{n-1,k}) + jump^n for
 // n = k..N, with jump^n = PFL(U^{n-1,k-1}) - G(U^{n-1,k-1}) formed from the
 // stored G results of the previous sweep, and the Eq. (10) error
@@ -137,6 +139,10 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT,
             rusanov(A, nx, p.bc, p.sound, i - 1, Hl);
 #pragma unroll
             for (int q = 0; q < 5; ++q) B[q * nx + i] = A[q * nx + i] - dt / p.dx * (Hr[q] - Hl[q]);
+            if (p.E) {  // exterior force: forward-Euler source on the old state
+                B[1 * nx + i] += dt * A[0 * nx + i] * p.E[i];
+                B[4 * nx + i] += dt * A[1 * nx + i] * p.E[i];
+            }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < 5 * nx; i += blockDim.x) A[i] = B[i];

@@ -1,0 +1,64 @@
+// Internal interface between the force-path batch (force_runtime.cu) and the
+// parareal context (runtime.cu).  Internal to libpr.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "pr.h"
+#include "pr_kernels.h"
+
+struct pr_force {
+    int n = 0, precision = 0, scheme = 0, nx = 0, nvx = 0, nvp = 0;
+    prk::FGeom g{};
+    size_t smem = 0;
+    std::vector<prk::FInst> h;          // host copy of the descriptors
+    prk::FInst* d_inst = nullptr;
+    prk::Active* d_active = nullptr;
+    int* d_cur = nullptr;               // [n] buffer index of each instance's state
+    int* d_status = nullptr;
+    double* d_E = nullptr;              // [n][nx]
+    double* d_U = nullptr;              // [n][5][nx] moments of the current states
+    double* d_Ulift = nullptr;          // [n][5][nx] lift sources of pr_force_set_initial
+    void* d_vtab = nullptr;             // [n][nvx + 3 nvp^2] velocity tables (element type of f)
+    std::vector<void*> bufs;            // two state buffers per instance
+    double* d_tmp = nullptr;            // float64 staging of one instance's f (lazy)
+    cudaStream_t stream = nullptr;
+    // CUDA-event timing of the step launches
+    struct Pending {
+        cudaEvent_t a, b;
+        int steps;
+    };
+    std::vector<Pending> pending;
+    double step_ms_sum = 0.0;
+    int steps_timed = 0;
+    std::string err;
+};
+
+// Adds n to the library-wide kernel launch counter (runtime.cu).
+void pr_internal_count_launches(long long n);
+
+namespace prf {
+
+int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int precision, std::string& err);
+void destroy(pr_force* b);
+// Point instance b's lift source and projection target at device buffers.
+void bind(pr_force* b, int i, const double* Uin, double* Uout);
+cudaError_t upload(pr_force* b, int b0, int b1, cudaStream_t s);
+// Lift instances [b0, b1) from their Uin, run nsteps steps (the last writes
+// Ucur and Uout; with nsteps = 0 the moments of the lifted state go to Ucur),
+// advance their buffer indices.  Active range restored to all.
+int enqueue_lift_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool timing);
+// Run nsteps steps of instances [b0, b1) from their current states.
+int enqueue_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool timing);
+// The body of one graph-captured parareal iteration: active slices from the
+// device counter dk (slices max(k,1)..N on instances first_slice-1..), lift,
+// nsteps steps with projection, advance.
+cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cudaStream_t s);
+// Device status: 0 or a PR_* code (cleared).  Synchronises b->stream.
+int take_status(pr_force* b);
+double emax(const pr_force* b, int i);
+int launches_per_step();
+
+}  // namespace prf

@@ -1,0 +1,567 @@
+// Host runtime of the exterior-force path: the pr_force_* entry points of
+// include/pr.h and the helpers the parareal context uses (force_rt.h).
+// Owns the instances' state buffers, descriptors, velocity tables and the
+// per-run CUDA-event timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "force_rt.h"
+
+namespace {
+
+std::mutex g_fprep_mu;
+bool g_fprepared = false;
+std::mutex g_ferr_mu;
+std::string g_ferr;
+
+int dev_attr(cudaDeviceAttr a)
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, a, dev);
+    return v;
+}
+
+void prepare_once()
+{
+    std::lock_guard<std::mutex> lk(g_fprep_mu);
+    if (g_fprepared) return;
+    prk::prepare_force_kernels(dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin));
+    cudaGetLastError();
+    g_fprepared = true;
+}
+
+int ffail(pr_force* b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return code;
+}
+
+#define FCUDA(b, call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return ffail((b), PR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t elem(int precision) { return precision == PR_FP64 ? sizeof(double) : sizeof(float); }
+
+double dt_stab(const pr_force_instance& d, double cfl)
+{
+    double dx = (d.x1 - d.x0) / d.nx, dvx = 2.0 * d.L / d.nvx, vmax = d.L - 0.5 * dvx;
+    double em = 0.0;
+    if (d.E)
+        for (int i = 0; i < d.nx; ++i) em = std::max(em, std::fabs(d.E[i]));
+    if (em == 0.0) return cfl * dx / vmax;
+    return cfl / (vmax / dx + em / dvx);
+}
+
+// Geometry for cluster size C; false if the chunk does not fit shared memory.
+bool geometry(int precision, int nvx, int nvp, int C, prk::FGeom* g, size_t* smem)
+{
+    long long ncol = (long long)nvx * nvp * nvp;
+    if (C < 1 || C > prk::FORCE_MAX_CLUSTER) return false;
+    long long chunk = (ncol + C - 1) / C;
+    if (C > 1 && (long long)(C - 1) * chunk >= ncol) return false;  // an empty CTA
+    if ((size_t)chunk * elem(precision) > (size_t)prk::FORCE_MAX_CHUNK_BYTES) return false;
+    size_t sm = prk::force_step_smem(precision, nvx, nvp, (int)chunk);
+    if (sm > (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin) - 1024) return false;
+    g->nvx = nvx;
+    g->nvp = nvp;
+    g->ncol = ncol;
+    g->C = C;
+    g->chunk = (int)chunk;
+    *smem = sm;
+    return true;
+}
+
+// Default cluster size: the smallest whose chunk fits, raised (up to 8) while
+// the chunk stays above 8192 cells.
+int default_cluster(int precision, int nvx, int nvp)
+{
+    prk::FGeom g;
+    size_t sm;
+    int C = 1;
+    while (C <= prk::FORCE_MAX_CLUSTER && !geometry(precision, nvx, nvp, C, &g, &sm)) ++C;
+    if (C > prk::FORCE_MAX_CLUSTER) return 0;
+    while (C < 8 && g.chunk > 8192 && geometry(precision, nvx, nvp, C + 1, &g, &sm)) ++C;
+    return C;
+}
+
+template <typename T>
+void fill_vtab(std::vector<unsigned char>& out, int nvx, int nvp, double L)
+{
+    int nvp2 = nvp * nvp;
+    std::vector<T> t((size_t)nvx + 3 * nvp2);
+    double dvx = 2.0 * L / nvx, dvp = 2.0 * L / nvp;
+    for (int j = 0; j < nvx; ++j) t[j] = (T)(-L + (j + 0.5) * dvx);
+    for (int jp = 0; jp < nvp2; ++jp) {
+        int jy = jp / nvp, jz = jp % nvp;
+        double y = -L + (jy + 0.5) * dvp, z = -L + (jz + 0.5) * dvp;
+        t[nvx + jp] = (T)y;
+        t[nvx + nvp2 + jp] = (T)z;
+        t[nvx + 2 * nvp2 + jp] = (T)(y * y + z * z);
+    }
+    out.resize(t.size() * sizeof(T));
+    memcpy(out.data(), t.data(), out.size());
+}
+
+void fold_events(pr_force* b)
+{
+    for (auto& p : b->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            b->step_ms_sum += ms;
+            b->steps_timed += p.steps;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    b->pending.clear();
+    cudaGetLastError();
+}
+
+void prim_to_cons(int nx, const double* U, double* V)
+{
+    for (int i = 0; i < nx; ++i) {
+        double r = U[i], ux = U[nx + i], uy = U[2 * nx + i], uz = U[3 * nx + i], th = U[4 * nx + i];
+        V[i] = r;
+        V[nx + i] = r * ux;
+        V[2 * nx + i] = r * uy;
+        V[3 * nx + i] = r * uz;
+        V[4 * nx + i] = 0.5 * r * (ux * ux + uy * uy + uz * uz) + 1.5 * r * th;
+    }
+}
+
+int cons_to_prim(int nx, const double* V, double* U)
+{
+    int bad = 0;
+    for (int i = 0; i < nx; ++i) {
+        double r = V[i], ux = V[nx + i] / r, uy = V[2 * nx + i] / r, uz = V[3 * nx + i] / r;
+        double th = (2.0 * V[4 * nx + i] / r - (ux * ux + uy * uy + uz * uz)) / 3.0;
+        if (!(r > 0) || !(th > 0)) bad = 1;
+        U[i] = r;
+        U[nx + i] = ux;
+        U[2 * nx + i] = uy;
+        U[3 * nx + i] = uz;
+        U[4 * nx + i] = th;
+    }
+    return bad;
+}
+
+// Active instance range for the next launches (a copy from pageable memory:
+// the value is staged before the call returns).
+cudaError_t set_active(pr_force* b, int b0, int b1, cudaStream_t s)
+{
+    prk::Active a{b0, b1};
+    return cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+
+namespace prf {
+
+void destroy(pr_force* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    fold_events(b);
+    for (void* p : b->bufs) cudaFree(p);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_active);
+    cudaFree(b->d_cur);
+    cudaFree(b->d_status);
+    cudaFree(b->d_E);
+    cudaFree(b->d_U);
+    cudaFree(b->d_Ulift);
+    cudaFree(b->d_vtab);
+    cudaFree(b->d_tmp);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int precision, std::string& err)
+{
+    *out = nullptr;
+    auto fail = [&](int code, const std::string& m) {
+        err = m;
+        return code;
+    };
+    if (!inst || n < 1 || n > 65535) return fail(PR_EINVAL, "need 1..65535 instances");
+    if (scheme != PR_UPWIND && scheme != PR_MUSCL) return fail(PR_EINVAL, "bad scheme");
+    if (precision != PR_FP64 && precision != PR_MIXED) return fail(PR_EINVAL, "bad precision");
+    const pr_force_instance& d0 = inst[0];
+    for (int k = 0; k < n; ++k) {
+        const pr_force_instance& d = inst[k];
+        if (d.nx != d0.nx || d.nvx != d0.nvx || d.nvp != d0.nvp)
+            return fail(PR_EINVAL, "instances of one force batch share nx, nvx and nvp");
+        if (d.nx < 1 || d.nx > 65535 || d.nvx < 2 || d.nvp < 1 || d.nvp > 64 || d.nvx > 4096)
+            return fail(PR_EINVAL, "need 1 <= nx <= 65535, 2 <= nvx <= 4096, 1 <= nvp <= 64");
+        if (!(d.L > 0) || !(d.x1 > d.x0) || !(d.dt > 0) || !(d.eps > 0))
+            return fail(PR_EINVAL, "need L > 0, x1 > x0, dt > 0, eps > 0");
+        if (d.bc < PR_BC_PERIODIC || d.bc > PR_BC_REFLECT) return fail(PR_EINVAL, "bad boundary condition");
+        if (scheme == PR_MUSCL && d.bc == PR_BC_REFLECT && d.nx < 2)
+            return fail(PR_EINVAL, "MUSCL with reflecting walls needs nx >= 2");
+        if (d.E)
+            for (int i = 0; i < d.nx; ++i)
+                if (!std::isfinite(d.E[i])) return fail(PR_EINVAL, "E must be finite");
+    }
+    prepare_once();
+    int C = default_cluster(precision, d0.nvx, d0.nvp);
+    if (C == 0) return fail(PR_EINVAL, "velocity column too large for 16 CTAs of shared memory");
+    pr_force* b = new pr_force();
+    b->n = n;
+    b->precision = precision;
+    b->scheme = scheme;
+    b->nx = d0.nx;
+    b->nvx = d0.nvx;
+    b->nvp = d0.nvp;
+    geometry(precision, d0.nvx, d0.nvp, C, &b->g, &b->smem);
+    int clusters = 0;
+    if (prk::force_step_occupancy(precision, scheme, C, b->smem, &clusters) != 0 || clusters < 1) {
+        destroy(b);
+        return fail(PR_EINVAL, "no cluster of this shape fits the device");
+    }
+    const size_t es = elem(precision);
+    const int nx = b->nx, nvp2 = b->nvp * b->nvp;
+    const size_t state = (size_t)nx * b->g.ncol * es;
+    const size_t vt = ((size_t)b->nvx + 3 * nvp2) * es;
+    auto cm = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cm((void**)&b->d_inst, sizeof(prk::FInst) * n) && cm((void**)&b->d_active, sizeof(prk::Active)) &&
+              cm((void**)&b->d_cur, sizeof(int) * n) && cm((void**)&b->d_status, sizeof(int)) &&
+              cm((void**)&b->d_E, sizeof(double) * n * nx) && cm((void**)&b->d_U, sizeof(double) * n * 5 * nx) &&
+              cm((void**)&b->d_Ulift, sizeof(double) * n * 5 * nx) && cm(&b->d_vtab, vt * n);
+    for (int k = 0; ok && k < 2 * n; ++k) {
+        void* p = nullptr;
+        ok = cm(&p, state);
+        if (ok) b->bufs.push_back(p);
+    }
+    if (!ok) {
+        destroy(b);
+        cudaGetLastError();
+        return fail(PR_ENOMEM, "device allocation of the force batch");
+    }
+    std::vector<double> E((size_t)n * nx, 0.0);
+    std::vector<unsigned char> tabs(vt * n);
+    b->h.resize(n);
+    for (int k = 0; k < n; ++k) {
+        const pr_force_instance& d = inst[k];
+        prk::FInst& I = b->h[k];
+        memset(&I, 0, sizeof I);
+        if (d.E) memcpy(&E[(size_t)k * nx], d.E, sizeof(double) * nx);
+        double em = 0.0;
+        for (int i = 0; i < nx; ++i) em = std::max(em, std::fabs(E[(size_t)k * nx + i]));
+        I.nx = nx;
+        I.bc = d.bc;
+        I.collide = std::isfinite(d.eps) ? 1 : 0;
+        I.L = d.L;
+        I.dx = (d.x1 - d.x0) / nx;
+        I.dvx = 2.0 * d.L / b->nvx;
+        I.dvp = 2.0 * d.L / b->nvp;
+        I.dv3 = I.dvx * I.dvp * I.dvp;
+        I.dt = d.dt;
+        I.eps = d.eps;
+        I.a = I.collide ? d.eps / (d.eps + d.dt) : 1.0;
+        I.b = I.collide ? d.dt / (d.eps + d.dt) : 0.0;
+        I.nu = d.dt / I.dx;
+        I.nuv = d.dt / I.dvx;
+        I.Emax = em;
+        I.E = b->d_E + (size_t)k * nx;
+        I.f[0] = b->bufs[2 * k];
+        I.f[1] = b->bufs[2 * k + 1];
+        I.vtab = static_cast<unsigned char*>(b->d_vtab) + vt * k;
+        I.Uin = b->d_Ulift + (size_t)k * 5 * nx;
+        I.Uout = nullptr;
+        I.Ucur = b->d_U + (size_t)k * 5 * nx;
+        std::vector<unsigned char> t;
+        if (precision == PR_FP64) fill_vtab<double>(t, b->nvx, b->nvp, d.L);
+        else fill_vtab<float>(t, b->nvx, b->nvp, d.L);
+        memcpy(&tabs[vt * k], t.data(), vt);
+    }
+    prk::Active all{0, n};
+    ok = cudaMemcpy(b->d_E, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_vtab, tabs.data(), tabs.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_inst, b->h.data(), sizeof(prk::FInst) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemset(b->d_cur, 0, sizeof(int) * n) == cudaSuccess &&
+         cudaMemset(b->d_status, 0, sizeof(int)) == cudaSuccess &&
+         cudaMemset(b->d_U, 0, sizeof(double) * n * 5 * nx) == cudaSuccess &&
+         cudaMemset(b->d_Ulift, 0, sizeof(double) * n * 5 * nx) == cudaSuccess;
+    for (void* p : b->bufs) ok = ok && cudaMemset(p, 0, state) == cudaSuccess;
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+        err = std::string("force batch set-up: ") + cudaGetErrorString(cudaGetLastError());
+        destroy(b);
+        return PR_ECUDA;
+    }
+    *out = b;
+    return PR_OK;
+}
+
+void bind(pr_force* b, int i, const double* Uin, double* Uout)
+{
+    b->h[i].Uin = Uin;
+    b->h[i].Uout = Uout;
+}
+
+cudaError_t upload(pr_force* b, int b0, int b1, cudaStream_t s)
+{
+    if (b1 <= b0) return cudaSuccess;
+    return cudaMemcpyAsync(b->d_inst + b0, b->h.data() + b0, sizeof(prk::FInst) * (b1 - b0), cudaMemcpyHostToDevice,
+                           s);
+}
+
+static int enqueue_steps(pr_force* b, int n_inst, int nsteps, cudaStream_t s, bool timing)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timing && nsteps > 0) {
+        FCUDA(b, cudaEventCreate(&e0));
+        FCUDA(b, cudaEventCreate(&e1));
+        FCUDA(b, cudaEventRecord(e0, s));
+    }
+    for (int k = 0; k < nsteps; ++k)
+        FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx, n_inst,
+                                        b->d_active, b->d_cur, k, k == nsteps - 1, b->d_status, b->smem, s));
+    FCUDA(b, prk::launch_force_advance(b->d_active, b->d_cur, nsteps, n_inst, s));
+    pr_internal_count_launches(nsteps + (nsteps & 1));
+    if (e0) {
+        FCUDA(b, cudaEventRecord(e1, s));
+        b->pending.push_back({e0, e1, nsteps});
+    }
+    return PR_OK;
+}
+
+int enqueue_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool timing)
+{
+    if (nsteps <= 0 || b1 <= b0) return PR_OK;
+    FCUDA(b, set_active(b, b0, b1, s));
+    int rc = enqueue_steps(b, b->n, nsteps, s, timing);
+    FCUDA(b, set_active(b, 0, b->n, s));
+    return rc;
+}
+
+int enqueue_lift_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool timing)
+{
+    if (b1 <= b0) return PR_OK;
+    FCUDA(b, set_active(b, b0, b1, s));
+    const int p = b->precision == PR_FP64 ? 0 : 1;
+    FCUDA(b, prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s));
+    pr_internal_count_launches(1);
+    int rc = PR_OK;
+    if (nsteps > 0) {
+        rc = enqueue_steps(b, b->n, nsteps, s, timing);
+    } else {
+        FCUDA(b, prk::launch_force_moments(p, b->d_inst, b->g, b->nx, b0, b1, b->d_cur, s));
+        pr_internal_count_launches(1);
+    }
+    FCUDA(b, set_active(b, 0, b->n, s));
+    return rc;
+}
+
+cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cudaStream_t s)
+{
+    const int p = b->precision == PR_FP64 ? 0 : 1;
+    cudaError_t e = prk::launch_set_active(dk, b->d_active, 1, b->n, N, s);
+    if (e == cudaSuccess) e = prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s);
+    for (int k = 0; e == cudaSuccess && k < nsteps; ++k)
+        e = prk::launch_force_step(p, b->scheme, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, k,
+                                   k == nsteps - 1, b->d_status, b->smem, s);
+    if (e == cudaSuccess) e = prk::launch_force_advance(b->d_active, b->d_cur, nsteps, b->n, s);
+    return e;
+}
+
+int take_status(pr_force* b)
+{
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    fold_events(b);
+    int st = 0;
+    FCUDA(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        cudaMemset(b->d_status, 0, sizeof(int));
+        return ffail(b, st, st == PR_ENONPHYS ? "a density or temperature became non-positive" : "device status %d",
+                     st);
+    }
+    return PR_OK;
+}
+
+double emax(const pr_force* b, int i) { return b->h[i].Emax; }
+
+int launches_per_step() { return 1; }
+
+}  // namespace prf
+
+extern "C" {
+
+int pr_force_create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int precision)
+{
+    if (!out) return PR_EINVAL;
+    std::string err;
+    int rc = prf::create(out, inst, n, scheme, precision, err);
+    if (rc) {
+        std::lock_guard<std::mutex> lk(g_ferr_mu);
+        g_ferr = err;
+    }
+    return rc;
+}
+
+int pr_force_destroy(pr_force* b)
+{
+    prf::destroy(b);
+    return PR_OK;
+}
+
+const char* pr_force_last_error(const pr_force* b)
+{
+    if (!b) return g_ferr.c_str();
+    return b->err.c_str();
+}
+
+int pr_force_set_initial(pr_force* b, int i, const double* U, int kind)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !U) return ffail(b, PR_EINVAL, "bad instance index or null state");
+    if (kind != PR_PRIMITIVE && kind != PR_CONSERVED) return ffail(b, PR_EINVAL, "bad kind");
+    const int nx = b->nx;
+    std::vector<double> V(5 * nx), P(5 * nx);
+    if (kind == PR_PRIMITIVE) {
+        memcpy(P.data(), U, sizeof(double) * 5 * nx);
+        prim_to_cons(nx, U, V.data());
+    } else {
+        memcpy(V.data(), U, sizeof(double) * 5 * nx);
+    }
+    if (cons_to_prim(nx, V.data(), P.data())) return ffail(b, PR_ENONPHYS, "initial state has rho <= 0 or theta <= 0");
+    cudaStream_t s = b->stream;
+    FCUDA(b, cudaStreamSynchronize(s));
+    double* dst = b->d_Ulift + (size_t)i * 5 * nx;
+    FCUDA(b, cudaMemcpy(dst, V.data(), sizeof(double) * 5 * nx, cudaMemcpyHostToDevice));
+    prf::bind(b, i, dst, nullptr);
+    FCUDA(b, prf::upload(b, i, i + 1, s));
+    int rc = prf::enqueue_lift_run(b, i, i + 1, 0, s, false);
+    if (rc) return rc;
+    return prf::take_status(b);
+}
+
+int pr_force_set_f(pr_force* b, int i, const double* f)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !f) return ffail(b, PR_EINVAL, "bad instance index or null f");
+    const long long n = (long long)b->nx * b->g.ncol;
+    cudaStream_t s = b->stream;
+    FCUDA(b, cudaStreamSynchronize(s));
+    if (!b->d_tmp && cudaMalloc(&b->d_tmp, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        b->d_tmp = nullptr;
+        return ffail(b, PR_ENOMEM, "staging buffer");
+    }
+    FCUDA(b, cudaMemcpy(b->d_tmp, f, sizeof(double) * n, cudaMemcpyHostToDevice));
+    const int p = b->precision == PR_FP64 ? 0 : 1;
+    FCUDA(b, prk::launch_force_load(p, b->d_inst, i, b->d_cur, b->d_tmp, n, s));
+    FCUDA(b, prk::launch_force_moments(p, b->d_inst, b->g, b->nx, i, i + 1, b->d_cur, s));
+    pr_internal_count_launches(2);
+    return prf::take_status(b);
+}
+
+int pr_force_run(pr_force* b, int nsteps, void* stream)
+{
+    if (!b) return PR_EINVAL;
+    if (nsteps < 0) return ffail(b, PR_EINVAL, "nsteps must be >= 0");
+    cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : b->stream;
+    return prf::enqueue_run(b, 0, b->n, nsteps, s, true);
+}
+
+int pr_force_moments(pr_force* b, int i, int kind, double* out)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !out) return ffail(b, PR_EINVAL, "bad instance index or null output");
+    if (kind != PR_PRIMITIVE && kind != PR_CONSERVED) return ffail(b, PR_EINVAL, "bad kind");
+    FCUDA(b, cudaDeviceSynchronize());
+    std::vector<double> V(5 * b->nx);
+    FCUDA(b, cudaMemcpy(V.data(), b->d_U + (size_t)i * 5 * b->nx, sizeof(double) * V.size(), cudaMemcpyDeviceToHost));
+    int rc = prf::take_status(b);
+    if (kind == PR_CONSERVED) memcpy(out, V.data(), sizeof(double) * V.size());
+    else cons_to_prim(b->nx, V.data(), out);
+    return rc;
+}
+
+int pr_force_get_f(pr_force* b, int i, double* out)
+{
+    if (!b) return PR_EINVAL;
+    if (i < 0 || i >= b->n || !out) return ffail(b, PR_EINVAL, "bad instance index or null output");
+    const long long n = (long long)b->nx * b->g.ncol;
+    FCUDA(b, cudaDeviceSynchronize());
+    if (!b->d_tmp && cudaMalloc(&b->d_tmp, sizeof(double) * n) != cudaSuccess) {
+        cudaGetLastError();
+        b->d_tmp = nullptr;
+        return ffail(b, PR_ENOMEM, "staging buffer");
+    }
+    FCUDA(b, prk::launch_force_store(b->precision == PR_FP64 ? 0 : 1, b->d_inst, i, b->d_cur, b->d_tmp, n,
+                                     b->stream));
+    pr_internal_count_launches(1);
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    FCUDA(b, cudaMemcpy(out, b->d_tmp, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return prf::take_status(b);
+}
+
+int pr_force_sync(pr_force* b)
+{
+    if (!b) return PR_EINVAL;
+    return prf::take_status(b);
+}
+
+int pr_force_config(const pr_force* b, int* cluster, int* chunk)
+{
+    if (!b) return PR_EINVAL;
+    if (cluster) *cluster = b->g.C;
+    if (chunk) *chunk = b->g.chunk;
+    return PR_OK;
+}
+
+int pr_force_set_cluster(pr_force* b, int cluster)
+{
+    if (!b) return PR_EINVAL;
+    prk::FGeom g;
+    size_t sm;
+    if (!geometry(b->precision, b->nvx, b->nvp, cluster, &g, &sm))
+        return ffail(b, PR_EINVAL, "cluster size %d does not fit this column", cluster);
+    int clusters = 0;
+    if (prk::force_step_occupancy(b->precision, b->scheme, cluster, sm, &clusters) != 0 || clusters < 1)
+        return ffail(b, PR_EINVAL, "no cluster of %d CTAs fits the device", cluster);
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    b->g = g;
+    b->smem = sm;
+    return PR_OK;
+}
+
+int pr_force_kernel_time(pr_force* b, double* avg_ms, int* steps, int reset)
+{
+    if (!b) return PR_EINVAL;
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    fold_events(b);
+    if (avg_ms) *avg_ms = b->steps_timed ? b->step_ms_sum / b->steps_timed : 0.0;
+    if (steps) *steps = b->steps_timed;
+    if (reset) {
+        b->step_ms_sum = 0.0;
+        b->steps_timed = 0;
+    }
+    return PR_OK;
+}
+
+int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt)
+{
+    if (!inst || !dt || inst->nx < 1 || inst->nvx < 1 || !(inst->L > 0) || !(inst->x1 > inst->x0) || !(cfl > 0))
+        return PR_EINVAL;
+    *dt = dt_stab(*inst, cfl);
+    return PR_OK;
+}
+
+}  // extern "C"

@@ -94,10 +94,61 @@ cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const
 cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double* dU0, cudaStream_t s);
 cudaError_t adj_copy_state(const Inst* insts, const InstState* st, int b, double* dst, cudaStream_t s);
 
+// ---- fine propagator with an exterior force (force.cu) ----
+constexpr int FORCE_THREADS = 256;       // threads per CTA of the force kernels
+constexpr int FORCE_MAX_CLUSTER = 16;    // CTAs per x column (8 portable, 16 opt-in)
+constexpr int FORCE_MAX_CHUNK_BYTES = 96 * 1024;  // f* of one CTA's velocity chunk, staged in shared memory
+
+// One instance of the force path.  f[buf] is [nx][ncol] of T (float or double).
+struct FInst {
+    int nx, bc, collide, pad0;
+    double L, dx, dvx, dvp, dv3, dt, eps;
+    double a, b;               // f^{n+1} = a f* + b M
+    double nu, nuv;            // dt/dx, dt/dv_x
+    double Emax;               // max_i |E_i|
+    const double* E;           // [nx] exterior force at the cell centres (device)
+    void* f[2];                // ping-pong state
+    const void* vtab;          // T: v_x[nvx], v_y[nvp2], v_z[nvp2], v_y^2+v_z^2[nvp2]
+    const double* Uin;         // lift source, conserved [5][nx] (device) or null
+    double* Uout;              // projection destination after the last step (or null)
+    double* Ucur;              // conserved moments of the current state [5][nx]
+};
+
+// Geometry shared by the instances of one force batch.
+struct FGeom {
+    int nvx, nvp;
+    long long ncol;            // nvx * nvp^2
+    int C;                     // CTAs (cluster size) per x column
+    int chunk;                 // velocities per CTA
+};
+
+cudaError_t prepare_force_kernels(int max_smem);
+size_t force_step_smem(int precision, int nvx, int nvp, int chunk);
+size_t force_lift_smem(int precision, int nvx, int nvp);
+int force_step_occupancy(int precision, int scheme, int C, size_t smem, int* clusters);
+// One fine step of every active instance; input buffer cur[b] ^ (step & 1);
+// last != 0 also writes P(f^{n+1}) into Ucur (and Uout).
+cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                              const Active* act, int* cur, int step, int last, int* status, size_t smem,
+                              cudaStream_t s);
+// Lift Uin into f[0] of the active instances, cur <- 0.
+cudaError_t launch_force_lift(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                              const Active* act, int* cur, int* status, cudaStream_t s);
+cudaError_t launch_force_moments(int precision, const FInst* insts, const FGeom& g, int nx, int b0, int b1,
+                                 const int* cur, cudaStream_t s);
+cudaError_t launch_force_load(int precision, const FInst* insts, int b, const int* cur, const double* src,
+                              long long n, cudaStream_t s);
+cudaError_t launch_force_store(int precision, const FInst* insts, int b, const int* cur, double* dst,
+                               long long n, cudaStream_t s);
+// cur[b] ^= nsteps & 1 for the active instances (after a run of nsteps steps).
+cudaError_t launch_force_advance(const Active* act, int* cur, int nsteps, int n_inst, cudaStream_t s);
+cudaError_t launch_force_set_cur(int* cur, int b, int v, cudaStream_t s);
+
 // ---- coarse propagator and parareal sweep (coarse.cu) ----
 struct CoarseParams {
     int nx, bc, sound;
     double x0, x1, dx, cfl;
+    const double* E = nullptr; // exterior force [nx] (device) or null: source (0, rho E, 0, 0, rho u_x E)
 };
 
 // G over dT for one state (Vin/Vout device [5][nx], may alias).

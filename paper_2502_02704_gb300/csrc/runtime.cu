@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "force_rt.h"
 #include "pr.h"
 #include "pr_kernels.h"
 
@@ -492,6 +493,8 @@ static int lift_instances(pr_batch* b, int begin, int end, cudaStream_t s)
 }
 
 // Message for pr_batch_last_error(NULL) from entry points that own no object.
+void pr_internal_count_launches(long long n) { g_launches += n; }
+
 void pr_internal_set_global_error(const char* msg)
 {
     std::lock_guard<std::mutex> lk(g_init_mu);
@@ -868,7 +871,8 @@ struct pr_ctx {
     pr_time t;
     int nx = 0, N = 0, nf = 0, n_res = 0;
     double dtf = 0, dT = 0;
-    pr_batch* fine = nullptr;
+    pr_batch* fine = nullptr;   // E = 0 fine propagator (pr_init)
+    pr_force* ff = nullptr;     // force-path fine propagator (pr_init_force)
     double *dU = nullptr, *dPFL = nullptr, *dGs = nullptr, *derr = nullptr, *dwork = nullptr, *dtmp = nullptr;
     int* dk = nullptr;
     int* dstatus = nullptr;
@@ -906,6 +910,7 @@ static void free_ctx(pr_ctx* c)
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->fine) free_batch(c->fine);
+    if (c->ff) prf::destroy(c->ff);
     cudaFree(c->dU);
     cudaFree(c->dPFL);
     cudaFree(c->dGs);
@@ -918,31 +923,41 @@ static void free_ctx(pr_ctx* c)
     delete c;
 }
 
+static cudaStream_t ctx_stream(const pr_ctx* c) { return c->ff ? c->ff->stream : c->fine->stream; }
+
 // Point resident instance b at slice n (lift source U^{n-1}, projection PFL^n).
 static void bind_slice(pr_ctx* c, int b, int n)
 {
+    const double* uin = c->dU + (size_t)(n - 1) * 5 * c->nx;
+    double* uout = c->dPFL + (size_t)n * 5 * c->nx;
+    if (c->ff) {
+        prf::bind(c->ff, b, uin, uout);
+        return;
+    }
     Inst& I = c->fine->h[b];
-    I.Uin = c->dU + (size_t)(n - 1) * 5 * c->nx;
-    I.Uout = c->dPFL + (size_t)n * 5 * c->nx;
+    I.Uin = uin;
+    I.Uout = uout;
 }
 
 static int take_ctx_status(pr_ctx* c)
 {
-    CCUDA(c, cudaStreamSynchronize(c->fine->stream));
+    CCUDA(c, cudaStreamSynchronize(ctx_stream(c)));
     int st = 0;
     CCUDA(c, cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
-    int rc = take_status(c->fine, c->fine->stream);
+    int rc = c->ff ? prf::take_status(c->ff) : take_status(c->fine, c->fine->stream);
     if (st != 0) {
         cudaMemset(c->dstatus, 0, sizeof(int));
         return cfail(c, st, st == PR_ENONPHYS ? "coarse propagator met a non-physical state" : "coarse status %d", st);
     }
-    if (rc) return cfail(c, rc, "%s", c->fine->err.c_str());
+    if (rc) return cfail(c, rc, "%s", c->ff ? c->ff->err.c_str() : c->fine->err.c_str());
     return PR_OK;
 }
 
 extern "C" {
 
-int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t)
+// Shared by pr_init (E = 0, force = false) and pr_init_force.
+static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t,
+                      bool force, int nvx, const double* E)
 {
     auto init_fail = [](int code, const std::string& m) {
         std::lock_guard<std::mutex> lk(g_init_mu);
@@ -966,19 +981,38 @@ int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, co
     c->nx = g->nx;
     c->N = t->n_slices;
     c->dT = t->T / t->n_slices;
-    // fine steps per slice: n_f = ceil(dT / dt_stab), dt_stab = cfl dx / max|v_x| (Sec. 2.2)
-    double dx = (g->x1 - g->x0) / g->nx, dv = 2.0 * v->L / v->nv, vmax = v->L - 0.5 * dv;
+    // fine steps per slice: n_f = ceil(dT / dt_stab), dt_stab = cfl dx / max|v_x| (Sec. 2.2),
+    // with the force cfl / (max|v_x|/dx + E_max/dv_x)
+    double dx = (g->x1 - g->x0) / g->nx;
+    pr_force_instance fd{g->nx, g->x0, g->x1, g->bc, nvx, v->nv, v->L, eps, 1.0, E};
+    double dts = 0.0;
+    if (force) {
+        if (nvx < 2 || pr_force_dt_stab(&fd, t->cfl_f, &dts) != PR_OK) {
+            free_ctx(c);
+            return init_fail(PR_EINVAL, "bad force-path velocity grid");
+        }
+    } else {
+        double dv = 2.0 * v->L / v->nv, vmax = v->L - 0.5 * dv;
+        dts = t->cfl_f * dx / vmax;
+    }
     if (t->nf > 0) c->nf = t->nf;
     else {
-        double r = c->dT / (t->cfl_f * dx / vmax);
+        double r = c->dT / dts;
         c->nf = std::max(1, (int)std::ceil(r * (1.0 - 1e-9)));
     }
     c->dtf = c->dT / c->nf;
     c->n_res = t->max_batch > 0 ? std::min(t->max_batch, c->N) : c->N;
-    pr_instance d{g->nx, g->x0, g->x1, g->bc, v->nv, v->L, eps, c->dtf, t->scheme};
-    std::vector<pr_instance> descs(c->n_res, d);
     std::string err;
-    int rc = create_batch(&c->fine, descs.data(), c->n_res, t->precision, err);
+    int rc;
+    if (force) {
+        fd.dt = c->dtf;
+        std::vector<pr_force_instance> descs(c->n_res, fd);
+        rc = prf::create(&c->ff, descs.data(), c->n_res, t->scheme, t->precision, err);
+    } else {
+        pr_instance d{g->nx, g->x0, g->x1, g->bc, v->nv, v->L, eps, c->dtf, t->scheme};
+        std::vector<pr_instance> descs(c->n_res, d);
+        rc = create_batch(&c->fine, descs.data(), c->n_res, t->precision, err);
+    }
     if (rc) {
         free_ctx(c);
         return init_fail(rc, err);
@@ -1005,10 +1039,13 @@ int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, co
     c->cp.x1 = g->x1;
     c->cp.dx = dx;
     c->cp.cfl = t->cfl_g;
+    c->cp.E = force ? c->ff->d_E : nullptr;
     c->live.assign(c->n_res, 0);
     for (int b = 0; b < c->n_res; ++b) bind_slice(c, b, b + 1);
-    if (cudaMemcpy(c->fine->d_inst, c->fine->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess) {
+    cudaError_t ue = force ? prf::upload(c->ff, 0, c->n_res, c->ff->stream)
+                           : cudaMemcpy(c->fine->d_inst, c->fine->h.data(), sizeof(Inst) * c->n_res,
+                                        cudaMemcpyHostToDevice);
+    if (ue != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return init_fail(PR_ECUDA, "descriptor upload");
     }
@@ -1016,10 +1053,21 @@ int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, co
     return PR_OK;
 }
 
+int pr_init(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t)
+{
+    return ctx_create(out, g, v, eps, t, false, 0, nullptr);
+}
+
+int pr_init_force(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t, int nvx,
+                  const double* E)
+{
+    return ctx_create(out, g, v, eps, t, true, nvx, E);
+}
+
 int pr_destroy(pr_ctx* c)
 {
     if (c) {
-        cudaStreamSynchronize(c->fine->stream);
+        if (c->fine || c->ff) cudaStreamSynchronize(ctx_stream(c));
         free_ctx(c);
     }
     return PR_OK;
@@ -1053,7 +1101,7 @@ int pr_set_initial(pr_ctx* c, const double* U0)
     if (check_prim(U0, c->nx)) return cfail(c, PR_ENONPHYS, "initial state has rho <= 0 or theta <= 0");
     std::vector<double> V(5 * c->nx);
     prim_to_cons_host(c->nx, U0, V.data());
-    cudaStream_t s = c->fine->stream;
+    cudaStream_t s = ctx_stream(c);
     CCUDA(c, cudaStreamSynchronize(s));
     CCUDA(c, cudaMemcpy(c->dU, V.data(), sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice));
     CCUDA(c, cudaMemset(c->dk, 0, sizeof(int)));
@@ -1070,7 +1118,7 @@ int pr_coarse_step(pr_ctx* c, const double* Vin, double* Vout, double dT)
 {
     if (!c) return PR_EINVAL;
     if (!Vin || !Vout || !(dT >= 0)) return cfail(c, PR_EINVAL, "null state or negative dT");
-    cudaStream_t s = c->fine->stream;
+    cudaStream_t s = ctx_stream(c);
     CCUDA(c, cudaMemcpyAsync(c->dtmp, Vin, sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice, s));
     CCUDA(c, prk::launch_coarse(c->cp, c->dtmp, c->dtmp + 5 * c->nx, dT, c->dwork, c->dstatus, s));
     g_launches += 1;
@@ -1083,6 +1131,23 @@ int pr_fine_step(pr_ctx* c, int slice, int nsteps, void* stream)
     if (!c) return PR_EINVAL;
     if (!c->initialized) return cfail(c, PR_EINVAL, "call pr_set_initial first");
     if (slice < 1 || slice > c->N || nsteps < 0) return cfail(c, PR_EINVAL, "slice must be in 1..N and nsteps >= 0");
+    if (c->ff) {
+        pr_force* b = c->ff;
+        cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : b->stream;
+        int bi = (slice - 1) % c->n_res;
+        if (c->live[bi] != slice) {
+            bind_slice(c, bi, slice);
+            prf::bind(b, bi, b->h[bi].Uin, nullptr);  // a free-running slice does not overwrite the fine results
+            CCUDA(c, prf::upload(b, bi, bi + 1, s));
+            c->descs_dirty = true;
+            int rc = prf::enqueue_lift_run(b, bi, bi + 1, 0, s, false);
+            if (rc) return cfail(c, rc, "%s", b->err.c_str());
+            c->live[bi] = slice;
+        }
+        int rc = prf::enqueue_run(b, bi, bi + 1, nsteps, s, true);
+        if (rc) return cfail(c, rc, "%s", b->err.c_str());
+        return PR_OK;
+    }
     pr_batch* b = c->fine;
     cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : b->stream;
     int bi = (slice - 1) % c->n_res;
@@ -1112,6 +1177,11 @@ int pr_fine_moments(pr_ctx* c, int slice, int kind, double* out)
     if (slice < 1 || slice > c->N) return cfail(c, PR_EINVAL, "slice must be in 1..N");
     int bi = (slice - 1) % c->n_res;
     if (c->live[bi] != slice) return cfail(c, PR_EINVAL, "slice %d has no live distribution", slice);
+    if (c->ff) {
+        int rc = pr_force_moments(c->ff, bi, kind, out);
+        if (rc) return cfail(c, rc, "%s", c->ff->err.c_str());
+        return PR_OK;
+    }
     int rc = pr_batch_moments(c->fine, bi, kind, out);
     if (rc) return cfail(c, rc, "%s", c->fine->err.c_str());
     return PR_OK;
@@ -1123,6 +1193,11 @@ int pr_fine_get_f(pr_ctx* c, int slice, double* out)
     if (slice < 1 || slice > c->N) return cfail(c, PR_EINVAL, "slice must be in 1..N");
     int bi = (slice - 1) % c->n_res;
     if (c->live[bi] != slice) return cfail(c, PR_EINVAL, "slice %d has no live distribution", slice);
+    if (c->ff) {
+        int rc = pr_force_get_f(c->ff, bi, out);
+        if (rc) return cfail(c, rc, "%s", c->ff->err.c_str());
+        return PR_OK;
+    }
     int rc = pr_batch_get_f(c->fine, bi, out);
     if (rc) return cfail(c, rc, "%s", c->fine->err.c_str());
     return PR_OK;
@@ -1133,9 +1208,24 @@ int pr_fine_get_f(pr_ctx* c, int slice, double* out)
 // Enqueue one iteration (k = c->k + 1 on the device counter) without graphs.
 static int enqueue_iteration_plain(pr_ctx* c, int k)
 {
+    int first = std::max(k, 1);
+    if (c->ff) {
+        pr_force* b = c->ff;
+        cudaStream_t s = b->stream;
+        for (int w0 = first; w0 <= c->N; w0 += c->n_res) {
+            int cnt = std::min(c->n_res, c->N - w0 + 1);
+            for (int bi = 0; bi < cnt; ++bi) bind_slice(c, bi, w0 + bi);
+            CCUDA(c, prf::upload(b, 0, c->n_res, s));
+            int rc = prf::enqueue_lift_run(b, 0, cnt, c->nf, s, true);
+            if (rc) return cfail(c, rc, "%s", b->err.c_str());
+        }
+        CCUDA(c, prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus,
+                                   1, c->dk, s));
+        g_launches += 1;
+        return PR_OK;
+    }
     pr_batch* b = c->fine;
     cudaStream_t s = b->stream;
-    int first = std::max(k, 1);
     for (int w0 = first; w0 <= c->N; w0 += c->n_res) {
         int cnt = std::min(c->n_res, c->N - w0 + 1);
         for (int bi = 0; bi < cnt; ++bi) bind_slice(c, bi, w0 + bi);
@@ -1158,8 +1248,39 @@ static int enqueue_iteration_plain(pr_ctx* c, int k)
 // The graph of one iteration when all slices are resident: set the active
 // slices from the device counter k, lift them, run n_f fused fine steps in
 // one persistent launch, then the sequential correction sweep (which bumps k).
+static int build_graph_force(pr_ctx* c)
+{
+    pr_force* b = c->ff;
+    cudaStream_t s = b->stream;
+    for (int bi = 0; bi < c->n_res; ++bi) bind_slice(c, bi, bi + 1);
+    CCUDA(c, prf::upload(b, 0, c->n_res, s));
+    CCUDA(c, cudaStreamSynchronize(s));
+    c->descs_dirty = false;
+    CCUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = prf::enqueue_graph_body(b, c->dk, c->N, c->nf, s);
+    if (e == cudaSuccess)
+        e = prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
+                              c->dk, s);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return cfail(c, PR_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        return cfail(c, PR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    c->graph = gr;
+    c->gexec = ex;
+    return PR_OK;
+}
+
 static int build_graph(pr_ctx* c)
 {
+    if (c->ff) return build_graph_force(c);
     pr_batch* b = c->fine;
     cudaStream_t s = b->stream;
     for (int bi = 0; bi < c->n_res; ++bi) bind_slice(c, bi, bi + 1);
@@ -1198,12 +1319,12 @@ static int build_graph(pr_ctx* c)
 
 static int run_iterations(pr_ctx* c, int count, bool use_graph)
 {
-    pr_batch* b = c->fine;
+    cudaStream_t cs = ctx_stream(c);
     for (int it = 0; it < count; ++it) {
         int k = c->k + 1;
         if (k > c->N) {
             // every slice is already exact; the iteration changes nothing (error 0)
-            CCUDA(c, cudaMemsetAsync(c->derr + std::min(k, c->N + 1), 0, sizeof(double), b->stream));
+            CCUDA(c, cudaMemsetAsync(c->derr + std::min(k, c->N + 1), 0, sizeof(double), cs));
             c->k = k;
             continue;
         }
@@ -1218,8 +1339,8 @@ static int run_iterations(pr_ctx* c, int count, bool use_graph)
                 int rc = build_graph(c);
                 if (rc) return rc;
             }
-            CCUDA(c, cudaGraphLaunch(c->gexec, b->stream));
-            g_launches += 5;
+            CCUDA(c, cudaGraphLaunch(c->gexec, cs));
+            g_launches += c->ff ? 3 + c->nf + (c->nf & 1) : 5;
         } else {
             int rc = enqueue_iteration_plain(c, k);
             if (rc) return rc;
@@ -1240,7 +1361,7 @@ int pr_parareal_iter(pr_ctx* c, double* err_out)
     if (rc) return rc;
     if (err_out) {
         int k = std::min(c->k, c->N + 1);
-        CCUDA(c, cudaMemcpyAsync(c->h_pinned, c->derr + k, sizeof(double), cudaMemcpyDeviceToHost, c->fine->stream));
+        CCUDA(c, cudaMemcpyAsync(c->h_pinned, c->derr + k, sizeof(double), cudaMemcpyDeviceToHost, ctx_stream(c)));
         rc = take_ctx_status(c);
         *err_out = c->h_pinned[0];
         return rc;
@@ -1270,7 +1391,7 @@ int pr_parareal_run(pr_ctx* c, int K, double tol, int* k_done, double* errs)
         rc = run_iterations(c, K, true);
         if (rc == PR_OK) {
             CCUDA(c, cudaMemcpyAsync(c->h_pinned, c->derr, sizeof(double) * (c->N + 2), cudaMemcpyDeviceToHost,
-                                     c->fine->stream));
+                                     ctx_stream(c)));
             rc = take_ctx_status(c);
             for (int i = 0; i < K; ++i) {
                 int k = std::min(k0 + 1 + i, c->N + 1);
@@ -1293,7 +1414,7 @@ int pr_moments(pr_ctx* c, int n, int kind, double* out)
     if (kind != PR_PRIMITIVE && kind != PR_CONSERVED) return cfail(c, PR_EINVAL, "bad kind");
     std::vector<double> V(5 * c->nx);
     CCUDA(c, cudaMemcpyAsync(V.data(), c->dU + (size_t)n * 5 * c->nx, sizeof(double) * 5 * c->nx, cudaMemcpyDeviceToHost,
-                             c->fine->stream));
+                             ctx_stream(c)));
     int rc = take_ctx_status(c);
     if (kind == PR_CONSERVED) memcpy(out, V.data(), sizeof(double) * 5 * c->nx);
     else cons_to_prim_host(c->nx, V.data(), out);

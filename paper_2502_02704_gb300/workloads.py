@@ -14,6 +14,9 @@ variants used for measurement:
 * ``thirds``: two interacting shocks, rho = 1 / 0.2 / 1, theta = 2 / 0.5 / 2.
 * ``density_modes``: rho = 1 + a1 sin 2 pi x + a2 cos 4 pi x, u = 0, theta = 1.
 * ``ragged_instances``: Sod-type instances of uneven size and Knudsen number.
+* ``test3_force`` / ``test3_beams``: Test 3, the force E(x) = -5 x^4 (x-2)^4 (x-1)
+  sampled at the cell centres of [0, 2] and the two beams (1, +-1, 0, 0, 1)
+  whose Maxwellians sum to the initial distribution.
 """
 from __future__ import annotations
 
@@ -96,3 +99,15 @@ def random_positive_f(nx: int, nv: int, seed: int, lo: float = 0.05, hi: float =
     """Arbitrary positive distribution [nx, nv^3] (not a Maxwellian)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, (nx, nv ** 3))
+
+
+def test3_force(nx: int, x0: float = 0.0, x1: float = 2.0) -> np.ndarray:
+    """Test 3's exterior force E(x) = -5 x^4 (x-2)^4 (x-1) at the cell centres."""
+    x = cell_centres(nx, x0, x1)
+    return -5.0 * x ** 4 * (x - 2.0) ** 4 * (x - 1.0)
+
+
+def test3_beams(nx: int) -> tuple[np.ndarray, np.ndarray]:
+    """The two beams of Test 3 as primitive states: (1, 1, 0, 0, 1) and (1, -1, 0, 0, 1)."""
+    one, z = np.ones(nx), np.zeros(nx)
+    return np.stack([one, one, z, z, one]), np.stack([one, -one, z, z, one])
