@@ -315,7 +315,7 @@ typedef struct {
     double x0, x1;
     int bc;            /* PR_BC_*                                              */
     int nvx;           /* velocity cells along v_x (>= 2)                      */
-    int nvp;           /* velocity cells along each of v_y, v_z (1..64)        */
+    int nvp;           /* velocity cells along each of v_y, v_z (1..32)        */
     double L;          /* velocity box [-L, L]^3                               */
     double eps;        /* Knudsen number > 0; +INFINITY = collisionless        */
     double dt;         /* fine time step > 0                                   */
@@ -325,10 +325,11 @@ typedef struct {
 
 /* Create n instances that share nx, nvx, nvp (the other fields may differ),
  * one x-transport scheme (PR_UPWIND or PR_MUSCL) and one precision.  Allocates
- * two state buffers per instance.  A column of nvx nvp^2 cells is split over at
- * most 16 CTAs, each staging its share of f* in shared memory; columns above
- * 16 x 96 KiB (393,216 cells in PR_MIXED, 196,608 in PR_FP64) are rejected
- * with PR_EINVAL.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
+ * two state buffers per instance.  The v_x rows of a column are split over at
+ * most 16 CTAs of nvp^2 threads (rounded up to 32), each thread owning one
+ * (v_y, v_z) cell and each CTA staging its rows of f* in shared memory; columns
+ * above 16 x 96 KiB (393,216 cells in PR_MIXED, 196,608 in PR_FP64) are
+ * rejected with PR_EINVAL.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
 int pr_force_create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int precision);
 
 int pr_force_destroy(pr_force* b);
@@ -358,7 +359,8 @@ int pr_force_get_f(pr_force* b, int i, double* out);
 /* Wait for the object's stream and report any device-side error. */
 int pr_force_sync(pr_force* b);
 
-/* CTAs per x column (the cluster size) and velocities per CTA in use. */
+/* CTAs per x column (the cluster size) and velocities per CTA (v_x rows per
+ * CTA times nvp^2) in use. */
 int pr_force_config(const pr_force* b, int* cluster, int* chunk);
 
 /* Use `cluster` CTAs per x column (1..16) if the chunk fits shared memory;

@@ -23,7 +23,10 @@
 // Storage: f[b][buf][i][j], j = (jx*nvp + jy)*nvp + jz, float (mixed
 // precision, moments and Maxwellian parameters in double) or double.
 #include <cooperative_groups.h>
+
+#include <algorithm>
 #include <math.h>
+#include <stdint.h>
 
 #include "pr_kernels.h"
 
@@ -73,222 +76,583 @@ __device__ __forceinline__ T warp_sum_t(T v)
     return v;
 }
 
-// Shared-memory layout of the step kernel.
-struct FShared {
-    double red[FW][5];   // per-warp partial sums
-    double part[2][8];   // this CTA's partials, phase 0 (f*) and 1 (f^{n+1}); read by the cluster
-    double par[8];       // rho, u_x, u_y, u_z, theta, pref, ok
+// Accumulators of the cross-warp and cluster sums: double in the double
+// path; in the float path a double-float pair (hi + lo, error-free FP32
+// transformations: Knuth's TwoSum, Dekker's product with fmaf), which keeps
+// ~44 bits without touching the double pipe, slow on this part.
+struct DF {
+    float hi, lo;
 };
 
-// Sum of the CTA's 5 values s[] into sh.part[phase] (FP64 over warps).
-template <typename T>
-__device__ __forceinline__ void cta_partials(const T (&s)[5], FShared& sh, int phase)
+__device__ __forceinline__ DF df_add(DF a, DF b)
 {
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const float h = p + e;
+    return {h, e - (h - p)};
+}
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    using A = double;
+    static __device__ __forceinline__ A from(double x) { return x; }
+    static __device__ __forceinline__ A add(A a, A b) { return a + b; }
+    static __device__ __forceinline__ double to_double(A a) { return a; }
+};
+template <>
+struct Acc<float> {
+    using A = DF;
+    static __device__ __forceinline__ A from(float x) { return {x, 0.0f}; }
+    static __device__ __forceinline__ A add(A a, A b) { return df_add(a, b); }
+    static __device__ __forceinline__ double to_double(A a) { return (double)a.hi + (double)a.lo; }
+};
+
+// Shared-memory layout of the step kernel (the same size for both
+// accumulator types: 8 bytes each).
+template <typename A>
+struct FSharedT {
+    A red[32][5];     // per-warp partial sums (up to 1024 threads)
+    A part[2][8];     // this CTA's partials, phase 0 (f*) and 1 (f^{n+1}); read by the cluster
+    A gat[16][5];     // the cluster's partials, gathered (rank, quantity)
+    A tot[8];         // cluster totals (rank order)
+    double par[8];    // double path: rho, u_x, u_y, u_z, theta, pref, 1/(2 theta)
+    float fpar[8];    // float path: the same in float
+};
+using FShared = FSharedT<double>;
+static_assert(sizeof(FSharedT<DF>) == sizeof(FSharedT<double>), "layouts differ");
+
+// A per-instance scalar in the element type: the float copy in the float path
+// (a double-to-float conversion runs on the slow double pipe of this part).
+__device__ __forceinline__ float pick_t(double, float f, float*) { return f; }
+__device__ __forceinline__ double pick_t(double d, float, double*) { return d; }
+template <typename T>
+__device__ __forceinline__ T scal(double d, float f)
+{
+    return pick_t(d, f, static_cast<T*>(nullptr));
+}
+
+// Sum of the CTA's 5 values s[] into sh.part[phase] (accumulators over warps).
+template <typename T>
+__device__ __forceinline__ void cta_partials(const T (&s)[5], FSharedT<typename Acc<T>::A>& sh, int phase)
+{
+    using AC = Acc<T>;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         T v = warp_sum_t(s[q]);
-        if (lane == 0) sh.red[w][q] = (double)v;
+        if (lane == 0) sh.red[w][q] = AC::from(v);
     }
     __syncthreads();
     if (threadIdx.x < 5) {
-        double a = 0.0;
-        for (int k = 0; k < FW; ++k) a += sh.red[k][threadIdx.x];
+        typename AC::A a = AC::from(T(0));
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nw; ++k) a = AC::add(a, sh.red[k][threadIdx.x]);
         sh.part[phase][threadIdx.x] = a;
     }
 }
 
-// Cluster totals of part[phase], added in rank order (threads 0..4).
-__device__ __forceinline__ double cluster_total(cg::cluster_group& cl, FShared& sh, int phase, int C)
+// Copy the cluster's partials part[phase] of every rank into gat (one
+// distributed-shared-memory load per thread, all in flight at once).
+template <typename A>
+__device__ __forceinline__ void cluster_gather(cg::cluster_group& cl, FSharedT<A>& sh, int phase, int C)
 {
-    double a = 0.0;
-    for (int r = 0; r < C; ++r) {
-        const FShared* rs = cl.map_shared_rank(&sh, r);
-        a += rs->part[phase][threadIdx.x];
+    const int t = threadIdx.x;
+    if (t < 5 * C) {
+        const int r = t / 5, k = t - 5 * r;
+        const FSharedT<A>* rs = cl.map_shared_rank(&sh, r);
+        sh.gat[r][k] = rs->part[phase][k];
     }
-    return a;
 }
 
-template <typename T, int SCHEME>
-__global__ void __launch_bounds__(FT)
+// Sum of quantity k over the C ranks' gathered partials in a fixed pairwise
+// order (depth log2 C; every CTA of the cluster adds in the same order).
+template <typename T>
+__device__ __forceinline__ typename Acc<T>::A rank_sum(const FSharedT<typename Acc<T>::A>& sh, int k, int C)
+{
+    using AC = Acc<T>;
+    typename AC::A v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = r < C ? sh.gat[r][k] : AC::from(T(0));
+#pragma unroll
+    for (int w = 1; w < 16; w *= 2)
+#pragma unroll
+        for (int r = 0; r + w < 16; r += 2 * w) v[r] = AC::add(v[r], v[r + w]);
+    return v[0];
+}
+
+// Reciprocal and reciprocal square root in double precision by two
+// Newton-Raphson steps from a single-precision seed (each step squares the
+// relative error: 2^-23 -> 2^-46 -> below double rounding).
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    double y = (double)(1.0f / (float)x);
+    if (!(y != 0.0 && isfinite(y))) return 1.0 / x;  // outside the float range
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    if (!(y != 0.0 && isfinite(y))) return 1.0 / sqrt(x);
+    double e = fma(-x * y, y, 1.0);  // 1 - x y^2
+    y = fma(0.5 * y, e, y);
+    e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+
+// Maxwellian parameters from the cluster totals (one thread).  The double
+// path gets tot = (rho, rho u, 2E) with 2E = sum |v|^2 f dv and writes par =
+// (rho, u_x, u_y, u_z, theta, rho (2 pi theta)^(-3/2), 1/(2 theta)), the
+// reciprocals by Newton steps.  The float path gets the same sums without the
+// cell volume dv3 (double-float) and writes fpar: theta = (rho 2E - |rho u|^2)
+// / (3 rho^2) with the numerator, which cancels when |u|^2 >> theta, formed
+// in double-float; the divisions and the root in float.  A non-positive rho
+// or theta raises PR_ENONPHYS when report is set.
+__device__ __forceinline__ void maxwell_params(FSharedT<double>& sh, double, bool report, int* status)
+{
+    const double r = sh.tot[0], m1 = sh.tot[1], m2 = sh.tot[2], m3 = sh.tot[3], e2 = sh.tot[4];
+    const double num = fma(r, e2, -(fma(m1, m1, fma(m2, m2, m3 * m3))));  // 3 rho^2 theta
+    const bool ok = r > 0.0 && num > 0.0 && isfinite(r) && isfinite(num);
+    if (!ok && report) atomicCAS(status, 0, ST_NONPHYS);
+    const double ir = rcp_nr(r);
+    const double th = ok ? num * (ir * ir) * (1.0 / 3.0) : 1.0;
+    const double rs = ok ? rsqrt_nr(2.0 * 3.14159265358979323846 * th) : 0.0;
+    sh.par[0] = r;
+    sh.par[1] = m1 * ir;
+    sh.par[2] = m2 * ir;
+    sh.par[3] = m3 * ir;
+    sh.par[4] = th;
+    sh.par[5] = r * rs * rs * rs;
+    sh.par[6] = 0.5 * rcp_nr(th);
+}
+
+__device__ __forceinline__ void maxwell_params(FSharedT<DF>& sh, float dv3, bool report, int* status)
+{
+    const DF r = sh.tot[0], m1 = sh.tot[1], m2 = sh.tot[2], m3 = sh.tot[3], e2 = sh.tot[4];
+    const DF mm = df_add(df_mul(m1, m1), df_add(df_mul(m2, m2), df_mul(m3, m3)));
+    const DF nd = df_add(df_mul(r, e2), DF{-mm.hi, -mm.lo});  // 3 rho^2 theta (sums without dv3)
+    const float rf = r.hi + r.lo, num = nd.hi + nd.lo;
+    const bool ok = rf > 0.0f && num > 0.0f && isfinite(rf) && isfinite(num);
+    if (!ok && report) atomicCAS(status, 0, ST_NONPHYS);
+    const float irf = 1.0f / rf;
+    const float th = ok ? num * (irf * irf) * (1.0f / 3.0f) : 1.0f;
+    const float rs = ok ? rsqrtf(2.0f * 3.14159265f * th) : 0.0f;
+    sh.fpar[0] = rf * dv3;
+    sh.fpar[1] = (m1.hi + m1.lo) * irf;
+    sh.fpar[2] = (m2.hi + m2.lo) * irf;
+    sh.fpar[3] = (m3.hi + m3.lo) * irf;
+    sh.fpar[4] = th;
+    sh.fpar[5] = rf * dv3 * rs * rs * rs;
+    sh.fpar[6] = 0.5f / th;
+}
+
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+// Arrival without ordering: for a CTA whose remote reads have all returned.
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ long long gtimer()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (bounded by limit_ns) until the transaction count of the single-use
+// mbarrier at phase 0 completes; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, long long limit_ns)
+{
+    const long long t0 = gtimer();
+    for (int it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(0)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && gtimer() - t0 > limit_ns) return false;
+    }
+}
+
+// One contiguous run of v_x rows [a, b) of a (possibly ghost) x column, to be
+// placed at rows dst0.. of a shared-memory buffer.  Mirrored columns (a
+// reflecting wall reverses v_x) hold row r at stored row nvx-1-r.
+struct Seg {
+    const void* col;  // stored column base
+    int a, b;         // ghost-column rows
+    int dst0;         // buffer row of ghost row a
+    bool mir;
+};
+
+// Bulk copies of the non-mirrored segments (thread 0; completion on the
+// mbarrier, which thread 0 initialises here), when rows are 16-byte multiples.
+template <typename T>
+__device__ __forceinline__ void stage_bulk(const Seg* segs, int nseg, T* const* dst, int nvp2, uint32_t mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    uint32_t bytes = 0;
+    for (int k = 0; k < nseg; ++k)
+        if (!segs[k].mir && segs[k].b > segs[k].a) bytes += (uint32_t)(segs[k].b - segs[k].a) * nvp2 * sizeof(T);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+    for (int k = 0; k < nseg; ++k) {
+        const Seg& q = segs[k];
+        if (q.mir || q.b <= q.a) continue;
+        const T* src = static_cast<const T*>(q.col) + (size_t)q.a * nvp2;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_addr(dst[k] + (size_t)q.dst0 * nvp2)),
+            "l"(src), "r"((uint32_t)(q.b - q.a) * nvp2 * (uint32_t)sizeof(T)), "r"(mbar)
+            : "memory");
+    }
+}
+
+// The other segments (mirrored, or all when rows are not 16-byte multiples),
+// copied by all threads of the CTA element by element (a __syncthreads follows).
+template <typename T>
+__device__ __forceinline__ void stage_threads(const Seg* segs, int nseg, T* const* dst, int nvx, int nvp2, bool bulk)
+{
+    for (int k = 0; k < nseg; ++k) {
+        const Seg& q = segs[k];
+        if (bulk && !q.mir) continue;
+        const T* col = static_cast<const T*>(q.col);
+        const int n = (q.b - q.a) * nvp2;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int r = q.a + e / nvp2, j = e - (e / nvp2) * nvp2;
+            dst[k][(size_t)(q.dst0 + r - q.a) * nvp2 + j] = col[(size_t)(q.mir ? nvx - 1 - r : r) * nvp2 + j];
+        }
+    }
+}
+
+// VEC consecutive values of one shared-memory or global row (16 bytes when
+// VEC * sizeof(T) == 16).
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Pack {
+    T x[V];
+};
+
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ldv(const T* p)
+{
+    return *reinterpret_cast<const Pack<T, V>*>(p);
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* p, const Pack<T, V>& v)
+{
+    *reinterpret_cast<Pack<T, V>*>(p) = v;
+}
+
+// Thread layout of the step kernel: Lr = nvp^2 / VEC threads cover a v_x row
+// (thread q owns the VEC consecutive (v_y, v_z) cells q*VEC ..), G groups of
+// Lr threads split the CTA's rows into contiguous runs.
+template <typename T, int SCHEME, int VEC>
+__global__ void __launch_bounds__(VEC == 1 ? 1024 : 512, 1)
 k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
-             int step, int last, int* __restrict__ status)
+             int step, int last, int* __restrict__ status, long long wait_ns)
 {
     const int b = blockIdx.z;
     if (b < act->begin || b >= act->end) return;  // uniform over the cluster
     cg::cluster_group cl = cg::this_cluster();
     const FInst& I = insts[b];
     const int i = blockIdx.y, rank = blockIdx.x, C = gridDim.x;
-    const int nvx = g.nvx, nvp = g.nvp, nvp2 = nvp * nvp;
+    const int nvx = g.nvx, nvp2 = g.nvp * g.nvp;
     const long long ncol = g.ncol;
+    const int R = g.rows;
+    const int r0 = rank * R, r1 = min(r0 + R, nvx), nr = r1 - r0;
+    constexpr int NB = SCHEME == 0 ? 1 : 3;  // neighbour-column buffers
 
     extern __shared__ __align__(16) unsigned char fsm[];
-    FShared& sh = *reinterpret_cast<FShared*>(fsm);
-    T* vxs = reinterpret_cast<T*>(fsm + sizeof(FShared));  // velocity tables (copied from I.vtab)
-    T* vy = vxs + nvx;
-    T* vz = vy + nvp2;
-    T* vp2 = vz + nvp2;
-    T* eyz = vp2 + nvp2;  // Maxwellian tables
-    T* ex = eyz + nvp2;
-    T* st = ex + nvx;     // f* of this CTA's chunk
+    using AC = Acc<T>;
+    FSharedT<typename AC::A>& sh = *reinterpret_cast<FSharedT<typename AC::A>*>(fsm);
+    unsigned long long* mbar_p = reinterpret_cast<unsigned long long*>(fsm + sizeof(FShared));
+    T* vxs = reinterpret_cast<T*>(fsm + sizeof(FShared) + 16);  // v_x nodes
+    T* ex = vxs + nvx;                                           // Maxwellian factors: ex[nvx], ey[nvp], ez[nvp]
+    T* cen = reinterpret_cast<T*>(fsm + g.buf_off);              // rows r0-1 .. r1 of column i
+    T* nb = cen + (size_t)(R + 2) * nvp2;                        // NB x R rows of neighbour columns; f* into nb
+    const uint32_t mbar = smem_addr(mbar_p);
 
-    const T* vt = static_cast<const T*>(I.vtab);
-    for (int q = threadIdx.x; q < nvx + 3 * nvp2; q += FT) vxs[q] = vt[q];
-
-    const int c0 = rank * g.chunk;
-    const int c1 = (int)min((long long)c0 + g.chunk, ncol);
+    const int Lr = nvp2 / VEC;                       // threads per row
+    const int G = g.groups;                          // row groups
+    const int q = threadIdx.x % Lr, grp = threadIdx.x / Lr;
+    const int jp = q * VEC;
+    const int Rg = (nr + G - 1) / G;
+    const int ra = r0 + grp * Rg, rb = min(ra + Rg, r1);
+    const bool active = grp < G && ra < rb;
+    const bool bulk = g.bulk != 0;
     const int bufi = cur[b] ^ (step & 1);
     const T* __restrict__ fin = static_cast<const T*>(I.f[bufi]);
     T* __restrict__ fout = static_cast<T*>(I.f[bufi ^ 1]);
-    const T* col0 = fin + (size_t)i * ncol;
 
-    // neighbour columns i-2 .. i+2 under the boundary rule
-    const T* colp[5];
-    bool mir[5];
-    bool anymir = false;
-#pragma unroll
-    for (int d = -2; d <= 2; ++d) {
+    // segments: own column rows r0-1..r1 (clipped), then the neighbour rows each
+    // v_x row needs: upwind: i-1 where v_x > 0, i+1 where v_x < 0; MUSCL: i-1
+    // and i+1 everywhere plus i-2 / i+2 where v_x > 0 / < 0.  hpos: first row
+    // with v_x > 0.
+    const int hpos = I.hpos;
+    const int pa = max(r0, hpos), na = min(r1, hpos);
+    Seg segs[5];
+    T* dst[5];
+    int nseg = 0;
+    auto col = [&](int d, bool* m) { return static_cast<const void*>(fin + (size_t)ghost_col(i + d, I.nx, I.bc, m) * ncol); };
+    {
         bool m;
-        int cc = ghost_col(i + d, I.nx, I.bc, &m);
-        colp[d + 2] = fin + (size_t)cc * ncol;
-        mir[d + 2] = m;
-        anymir |= m;
+        const void* c0 = col(0, &m);
+        int a = max(r0 - 1, 0), e = min(r1 + 1, nvx);
+        segs[nseg] = {c0, a, e, a - (r0 - 1), false};
+        dst[nseg++] = cen;
     }
-    const T nu = (T)I.nu, nuv = (T)I.nuv;
-    const T Ei = (T)I.E[i], Em = (T)I.Emax, half = T(0.5);
+    if (SCHEME == 0) {
+        bool mm, mp;
+        const void* cm = col(-1, &mm);
+        const void* cp = col(1, &mp);
+        segs[nseg] = {cm, pa, r1, pa - r0, mm};
+        dst[nseg++] = nb;
+        segs[nseg] = {cp, r0, na, 0, mp};
+        dst[nseg++] = nb;
+    } else {
+        bool mm, mp, mm2, mp2;
+        const void* cm = col(-1, &mm);
+        const void* cp = col(1, &mp);
+        const void* cm2 = col(-2, &mm2);
+        const void* cp2 = col(2, &mp2);
+        segs[nseg] = {cm, r0, r1, 0, mm};
+        dst[nseg++] = nb;
+        segs[nseg] = {cp, r0, r1, 0, mp};
+        dst[nseg++] = nb + (size_t)R * nvp2;
+        segs[nseg] = {cm2, pa, r1, pa - r0, mm2};
+        dst[nseg++] = nb + (size_t)2 * R * nvp2;
+        segs[nseg] = {cp2, r0, na, 0, mp2};
+        dst[nseg++] = nb + (size_t)2 * R * nvp2;
+    }
+    // the bulk copies go out first; the tables load while they are in flight
+    if (bulk && threadIdx.x == 0) stage_bulk<T>(segs, nseg, dst, nvp2, mbar);
+    stage_threads<T>(segs, nseg, dst, nvx, nvp2, bulk);
+    const T* vt = static_cast<const T*>(I.vtab);
+    for (int k = threadIdx.x; k < nvx; k += blockDim.x) vxs[k] = vt[k];
+    T vy[VEC], vz[VEC], vp2[VEC];
+    int jy[VEC], jz[VEC];
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) {
+        vy[l] = active ? vt[nvx + jp + l] : T(0);
+        vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
+        vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
+        jy[l] = (jp + l) / g.nvp;
+        jz[l] = jp + l - jy[l] * g.nvp;
+    }
+    __syncthreads();  // mbarrier initialised; thread-staged rows visible
+    if (bulk && !mbar_wait(mbar, wait_ns)) {
+        atomicCAS(status, 0, ST_TIMEOUT);
+        mbar_wait(mbar, wait_ns);  // let copies in flight land before the buffers are reused
+    }
 
-    // this thread's cells e = c0 + t + k FT, (jx, jp) advanced without division
-    const int e0 = c0 + threadIdx.x;
-    const int dq = FT / nvp2, dr = FT - dq * nvp2;
-    int jx = e0 / nvp2, jp = e0 - jx * nvp2;
+    const T nu = scal<T>(I.nu, I.fnu), nuv = scal<T>(I.nuv, I.fnuv);
+    const T hE = T(0.5) * scal<T>(I.E[i], I.Ef[i]), hEm = T(0.5) * scal<T>(I.Emax, I.fEmax), half = T(0.5);
 
-    __syncthreads();
-    T s[5] = {T(0), T(0), T(0), T(0), T(0)};
+    // pass 1: f* of this thread's rows (written over the first neighbour
+    // buffer, each element by the thread that read it), with the sums
+    // sum f* per lane and sum v_x f*, sum v_x^2 f* over the lanes
+    T S0[VEC], S1 = T(0), S4 = T(0);
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) S0[l] = T(0);
+    if (active) {
+        T* nb1 = nb;
+        const T* nb2 = nb + (size_t)R * nvp2;
+        const T* nb3 = nb + (size_t)2 * R * nvp2;
+        Pack<T, VEC> dn, c;
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) dn.x[l] = T(0);
+        if (ra > 0) dn = ldv<T, VEC>(cen + (size_t)(ra - r0) * nvp2 + jp);
+        c = ldv<T, VEC>(cen + (size_t)(ra - r0 + 1) * nvp2 + jp);
 #pragma unroll 2
-    for (int e = e0; e < c1; e += FT) {
-        const T vx = vxs[jx];
-        const int jm = anymir ? (nvx - 1 - jx) * nvp2 + jp : e;
-        const T c = col0[e];
-        T Fr, Fl;
-        if (SCHEME == 0) {
-            if (vx > T(0)) {
-                Fr = vx * c;
-                Fl = vx * colp[1][mir[1] ? jm : e];
-            } else {
-                Fr = vx * colp[3][mir[3] ? jm : e];
-                Fl = vx * c;
+        for (int r = ra; r < rb; ++r) {
+            const size_t o = (size_t)(r - r0) * nvp2 + jp;
+            Pack<T, VEC> up;
+            if (r < nvx - 1) up = ldv<T, VEC>(cen + o + 2 * (size_t)nvp2);
+            else {
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) up.x[l] = T(0);
             }
-        } else {
-            const T m1 = colp[1][mir[1] ? jm : e], p1 = colp[3][mir[3] ? jm : e];
-            if (vx > T(0)) {
-                const T m2 = colp[0][mir[0] ? jm : e];
-                Fr = vx * (c + half * minmod(c - m1, p1 - c));
-                Fl = vx * (m1 + half * minmod(m1 - m2, c - m1));
-            } else {
-                const T p2 = colp[4][mir[4] ? jm : e];
-                Fr = vx * (p1 - half * minmod(p1 - c, p2 - p1));
-                Fl = vx * (c - half * minmod(c - m1, p1 - c));
+            const T vx = vxs[r];
+            const bool pos = vx > T(0);
+            const Pack<T, VEC> x1 = ldv<T, VEC>(nb1 + o);
+            Pack<T, VEC> x2, x3;
+            if (SCHEME == 1) {
+                x2 = ldv<T, VEC>(nb2 + o);
+                x3 = ldv<T, VEC>(nb3 + o);
             }
-        }
-        T Gr = T(0), Gl = T(0);
-        if (jx < nvx - 1) {
-            const T up = col0[e + nvp2];
-            Gr = half * Ei * (c + up) - half * Em * (up - c);
-        }
-        if (jx > 0) {
-            const T dn = col0[e - nvp2];
-            Gl = half * Ei * (dn + c) - half * Em * (c - dn);
-        }
-        const T v = c - nu * (Fr - Fl) - nuv * (Gr - Gl);
-        st[e - c0] = v;
-        s[0] += v;
-        s[1] += vx * v;
-        s[2] += vy[jp] * v;
-        s[3] += vz[jp] * v;
-        s[4] += (vx * vx + vp2[jp]) * v;
-        jp += dr;
-        jx += dq;
-        if (jp >= nvp2) {
-            jp -= nvp2;
-            ++jx;
+            const bool interior = r > 0 && r < nvx - 1;
+            Pack<T, VEC> out;
+            T vsum = T(0);
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+                const T cc = c.x[l], u = up.x[l], d = dn.x[l];
+                T Fd;  // F_{i+1/2} - F_{i-1/2}
+                if (SCHEME == 0) {
+                    Fd = vx * (pos ? cc - x1.x[l] : x1.x[l] - cc);
+                } else {
+                    const T m1 = x1.x[l], p1 = x2.x[l], far = x3.x[l];
+                    if (pos) Fd = vx * ((cc + half * minmod(cc - m1, p1 - cc)) - (m1 + half * minmod(m1 - far, cc - m1)));
+                    else Fd = vx * ((p1 - half * minmod(p1 - cc, far - p1)) - (cc - half * minmod(cc - m1, p1 - cc)));
+                }
+                T Gd;  // G_{j+1/2} - G_{j-1/2}, zero flux through the ends of the box
+                if (interior) Gd = hE * (u - d) - hEm * ((u + d) - (cc + cc));
+                else {
+                    const T Gr = r < nvx - 1 ? hE * (cc + u) - hEm * (u - cc) : T(0);
+                    const T Gl = r > 0 ? hE * (d + cc) - hEm * (cc - d) : T(0);
+                    Gd = Gr - Gl;
+                }
+                const T v = cc - nu * Fd - nuv * Gd;
+                out.x[l] = v;
+                S0[l] += v;
+                vsum += v;
+            }
+            stv<T, VEC>(nb1 + o, out);
+            S1 += vx * vsum;
+            S4 += (vx * vx) * vsum;
+            dn = c;
+            c = up;
         }
     }
-
-    cta_partials(s, sh, 0);
+    {
+        T s[5] = {T(0), S1, T(0), T(0), S4};
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+            s[0] += S0[l];
+            s[2] += vy[l] * S0[l];
+            s[3] += vz[l] * S0[l];
+            s[4] += vp2[l] * S0[l];
+        }
+        cta_partials(s, sh, 0);
+    }
     cl.sync();
-    if (threadIdx.x < 5) sh.red[0][threadIdx.x] = cluster_total(cl, sh, 0, C);
+    cluster_gather(cl, sh, 0, C);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double dv3 = I.dv3;
-        double rho = sh.red[0][0] * dv3;
-        double ux = sh.red[0][1] * dv3 / rho, uy = sh.red[0][2] * dv3 / rho, uz = sh.red[0][3] * dv3 / rho;
-        double th = (sh.red[0][4] * dv3 / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
-        bool ok = rho > 0.0 && th > 0.0 && isfinite(rho) && isfinite(th);
-        if (!ok && rank == 0 && I.collide) atomicCAS(status, 0, ST_NONPHYS);
-        sh.par[0] = rho;
-        sh.par[1] = ux;
-        sh.par[2] = uy;
-        sh.par[3] = uz;
-        sh.par[4] = ok ? th : 1.0;
-        sh.par[5] = ok ? rho * pow(2.0 * 3.14159265358979323846 * th, -1.5) : 0.0;
+    if (threadIdx.x < 5) {
+        // the same order in every CTA; the double path scales by dv3 here
+        const typename AC::A t = rank_sum<T>(sh, threadIdx.x, C);
+        if constexpr (sizeof(T) == sizeof(double)) sh.tot[threadIdx.x] = t * I.dv3;
+        else sh.tot[threadIdx.x] = t;
     }
+    cluster_arrive_relaxed();  // the peers' partials are read (the matching wait is at the end)
+    __syncthreads();
+    if (threadIdx.x == 0) maxwell_params(sh, scal<T>(I.dv3, I.fdv3), I.collide && rank == 0, status);
     __syncthreads();
 
-    const T a = (T)I.a, bb = (T)I.b;
+    const T a = scal<T>(I.a, I.fa), bb = scal<T>(I.b, I.fb);
     const bool collide = I.collide != 0;
+    T myz[VEC];  // b pref ey[jy] ez[jz] per lane
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) myz[l] = T(0);
     if (collide) {
-        // separable Maxwellian M = pref ex[jx] ey[jy] ez[jz], evaluated in T
-        // from the double parameters
-        const T ux = (T)sh.par[1], uy = (T)sh.par[2], uz = (T)sh.par[3];
-        const T inv2th = (T)(0.5 / sh.par[4]), pref = (T)sh.par[5];
-        for (int q = threadIdx.x; q < nvx; q += FT) {
-            T cx = vxs[q] - ux;
-            ex[q] = texp(-cx * cx * inv2th);
-        }
-        for (int q = threadIdx.x; q < nvp2; q += FT) {
-            T cy = vy[q] - uy, cz = vz[q] - uz;
-            eyz[q] = pref * texp(-cy * cy * inv2th) * texp(-cz * cz * inv2th);
+        // separable Maxwellian M = pref ex[jx] ey[jy] ez[jz], the three factor
+        // tables evaluated in T from the double parameters
+        T* ey = ex + nvx;
+        T* ez = ey + g.nvp;
+        const T ux = scal<T>(sh.par[1], sh.fpar[1]), uy = scal<T>(sh.par[2], sh.fpar[2]);
+        const T uz = scal<T>(sh.par[3], sh.fpar[3]), inv2th = scal<T>(sh.par[6], sh.fpar[6]);
+        const int nvp = g.nvp;
+        for (int k = threadIdx.x; k < nvx + 2 * nvp; k += blockDim.x) {
+            if (k < nvx) {
+                const T cx = vxs[k] - ux;
+                ex[k] = texp(-cx * cx * inv2th);
+            } else {
+                const int j = k - nvx < nvp ? k - nvx : k - nvx - nvp;
+                const T v = vt[nvx + j * nvp];  // v_y node j (v_y table, jz = 0)
+                const T cc = v - (k - nvx < nvp ? uy : uz);
+                ex[k] = texp(-cc * cc * inv2th);
+            }
         }
         __syncthreads();
+        const T pb = bb * scal<T>(sh.par[5], sh.fpar[5]);
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) myz[l] = pb * (ey[jy[l]] * ez[jz[l]]);
     }
 
-    T* out = fout + (size_t)i * ncol;
-    T s2[5] = {T(0), T(0), T(0), T(0), T(0)};
-    jx = e0 / nvp2;
-    jp = e0 - jx * nvp2;
+    // pass 2: relax and store; on the last step also the sums of f^{n+1}
+    T P0[VEC], P1 = T(0), P4 = T(0);
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) P0[l] = T(0);
+    if (active) {
+        T* out = fout + (size_t)i * ncol + jp;
 #pragma unroll 4
-    for (int e = e0; e < c1; e += FT) {
-        T v = st[e - c0];
-        if (collide) v = a * v + bb * (ex[jx] * eyz[jp]);
-        out[e] = v;
-        if (last) {
-            const T vx = vxs[jx];
-            s2[0] += v;
-            s2[1] += vx * v;
-            s2[2] += vy[jp] * v;
-            s2[3] += vz[jp] * v;
-            s2[4] += (vx * vx + vp2[jp]) * v;
-        }
-        jp += dr;
-        jx += dq;
-        if (jp >= nvp2) {
-            jp -= nvp2;
-            ++jx;
+        for (int r = ra; r < rb; ++r) {
+            Pack<T, VEC> v = ldv<T, VEC>(nb + (size_t)(r - r0) * nvp2 + jp);
+            if (collide) {
+                const T e = ex[r];
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) v.x[l] = a * v.x[l] + e * myz[l];
+            }
+            stv<T, VEC>(out + (size_t)r * nvp2, v);
+            if (last) {
+                const T vx = vxs[r];
+                T vsum = T(0);
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) {
+                    P0[l] += v.x[l];
+                    vsum += v.x[l];
+                }
+                P1 += vx * vsum;
+                P4 += (vx * vx) * vsum;
+            }
         }
     }
     if (last) {
-        cta_partials(s2, sh, 1);
-        cl.sync();
-        if (threadIdx.x < 5) {
-            double t = cluster_total(cl, sh, 1, C) * I.dv3;
-            if (threadIdx.x == 4) t *= 0.5;  // energy = 1/2 sum |v|^2 f dv
-            if (rank == 0) {
-                I.Ucur[threadIdx.x * I.nx + i] = t;
-                if (I.Uout) I.Uout[threadIdx.x * I.nx + i] = t;
-            }
+        T s[5] = {T(0), P1, T(0), T(0), P4};
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+            s[0] += P0[l];
+            s[2] += vy[l] * P0[l];
+            s[3] += vz[l] * P0[l];
+            s[4] += vp2[l] * P0[l];
         }
+        cta_partials(s, sh, 1);
+        cluster_wait();  // completes the barrier arrived at after the first exchange
+        cl.sync();       // every CTA's phase-1 partials are written
+        cluster_gather(cl, sh, 1, C);
+        __syncthreads();
+        if (rank == 0 && threadIdx.x < 5) {
+            double t = AC::to_double(rank_sum<T>(sh, threadIdx.x, C)) * I.dv3;
+            if (threadIdx.x == 4) t *= 0.5;  // energy = 1/2 sum |v|^2 f dv
+            I.Ucur[threadIdx.x * I.nx + i] = t;
+            if (I.Uout) I.Uout[threadIdx.x * I.nx + i] = t;
+        }
+        cluster_arrive();
     }
-    cl.sync();  // no CTA leaves while another may still read its shared memory
+    cluster_wait();  // no CTA leaves while another may still read its shared memory
 }
 
 // Lift (Eq. 17) of the conserved state Uin into buffer 0 of the active
@@ -332,8 +696,8 @@ k_force_lift(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
     }
     __syncthreads();
     T* out = static_cast<T*>(I.f[0]) + (size_t)i * g.ncol;
-    const int c0 = blockIdx.x * g.chunk;
-    const int c1 = min((long long)c0 + g.chunk, g.ncol);
+    const int c0 = blockIdx.x * g.rows * nvp2;
+    const int c1 = (int)min((long long)c0 + (long long)g.rows * nvp2, g.ncol);
     for (int e = c0 + threadIdx.x; e < c1; e += FT) {
         int jx = e / nvp2, jp = e - jx * nvp2;
         out[e] = ex[jx] * eyz[jp];
@@ -405,20 +769,46 @@ __global__ void k_force_advance(const Active* __restrict__ act, int* __restrict_
 
 __global__ void k_force_set_cur(int* cur, int b, int v) { cur[b] = v; }
 
-void* pick_step(int precision, int scheme)
+void* pick_step(int precision, int scheme, int vec)
 {
-    if (precision == 0) return scheme == 0 ? reinterpret_cast<void*>(&k_force_step<double, 0>)
-                                           : reinterpret_cast<void*>(&k_force_step<double, 1>);
-    return scheme == 0 ? reinterpret_cast<void*>(&k_force_step<float, 0>)
-                       : reinterpret_cast<void*>(&k_force_step<float, 1>);
+    if (precision == 0) {
+        if (vec == 2) return scheme == 0 ? reinterpret_cast<void*>(&k_force_step<double, 0, 2>)
+                                         : reinterpret_cast<void*>(&k_force_step<double, 1, 2>);
+        if (vec == 1) return scheme == 0 ? reinterpret_cast<void*>(&k_force_step<double, 0, 1>)
+                                         : reinterpret_cast<void*>(&k_force_step<double, 1, 1>);
+        return nullptr;
+    }
+    if (vec == 4) return scheme == 0 ? reinterpret_cast<void*>(&k_force_step<float, 0, 4>)
+                                     : reinterpret_cast<void*>(&k_force_step<float, 1, 4>);
+    if (vec == 1) return scheme == 0 ? reinterpret_cast<void*>(&k_force_step<float, 0, 1>)
+                                     : reinterpret_cast<void*>(&k_force_step<float, 1, 1>);
+    return nullptr;
 }
 
 }  // namespace
 
-size_t force_step_smem(int precision, int nvx, int nvp, int chunk)
+size_t force_step_buf_off(int precision, int nvx, int nvp)
 {
     size_t es = precision == 0 ? sizeof(double) : sizeof(float);
-    return sizeof(FShared) + ((size_t)4 * nvp * nvp + 2 * nvx + chunk) * es;
+    size_t off = sizeof(FShared) + 16 + (2 * (size_t)nvx + 2 * (size_t)nvp) * es;  // v_x nodes, ex, ey, ez
+    return (off + 127) / 128 * 128;
+}
+
+size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows)
+{
+    size_t es = precision == 0 ? sizeof(double) : sizeof(float);
+    size_t nbuf = (size_t)(rows + 2) + (size_t)(scheme == 0 ? 1 : 3) * rows;
+    return force_step_buf_off(precision, nvx, nvp) + nbuf * nvp * nvp * es;
+}
+
+// Row groups and threads for VEC values per thread: at most 256 threads,
+// a multiple of 32.
+void force_step_layout(int nvp, int vec, int rows, int* groups, int* threads)
+{
+    const int Lr = nvp * nvp / vec;
+    int G = std::max(1, std::min(rows, 256 / std::max(Lr, 1)));
+    *groups = G;
+    *threads = (Lr * G + 31) / 32 * 32;
 }
 
 size_t force_lift_smem(int precision, int nvx, int nvp)
@@ -429,14 +819,17 @@ size_t force_lift_smem(int precision, int nvx, int nvp)
 
 cudaError_t prepare_force_kernels(int max_smem)
 {
+    const int vecs[2][2] = {{1, 2}, {1, 4}};
     for (int p = 0; p < 2; ++p)
-        for (int sc = 0; sc < 2; ++sc) {
-            const void* fn = pick_step(p, sc);
-            cudaFuncAttributes fa;
-            if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
-                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
-            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        }
+        for (int sc = 0; sc < 2; ++sc)
+            for (int vi = 0; vi < 2; ++vi) {
+                const void* fn = pick_step(p, sc, vecs[p][vi]);
+                cudaFuncAttributes fa;
+                if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
+                    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_smem - (int)fa.sharedSizeBytes);
+                cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            }
     const void* lifts[2] = {reinterpret_cast<const void*>(&k_force_lift<double>),
                             reinterpret_cast<const void*>(&k_force_lift<float>)};
     for (const void* fn : lifts) {
@@ -447,13 +840,13 @@ cudaError_t prepare_force_kernels(int max_smem)
     return cudaGetLastError();
 }
 
-int force_step_occupancy(int precision, int scheme, int C, size_t smem, int* clusters)
+int force_step_occupancy(int precision, int scheme, int vec, int C, int threads, size_t smem, int* clusters)
 {
-    const void* fn = pick_step(precision, scheme);
+    const void* fn = pick_step(precision, scheme, vec);
     if (!fn) return -1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(FT, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -474,13 +867,13 @@ int force_step_occupancy(int precision, int scheme, int C, size_t smem, int* clu
 
 cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, int* cur, int step, int last, int* status, size_t smem,
-                              cudaStream_t s)
+                              cudaStream_t s, long long wait_ns)
 {
-    void* fn = pick_step(precision, scheme);
+    void* fn = pick_step(precision, scheme, g.vec);
     if (!fn) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(g.C, nx, n_inst);
-    cfg.blockDim = dim3(FT, 1, 1);
+    cfg.blockDim = dim3(g.threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -490,7 +883,8 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    void* args[] = {(void*)&insts, (void*)&g, (void*)&act, (void*)&cur, (void*)&step, (void*)&last, (void*)&status};
+    void* args[] = {(void*)&insts, (void*)&g,    (void*)&act,    (void*)&cur,
+                    (void*)&step,  (void*)&last, (void*)&status, (void*)&wait_ns};
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

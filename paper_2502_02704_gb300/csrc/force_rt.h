@@ -19,6 +19,7 @@ struct pr_force {
     int* d_cur = nullptr;               // [n] buffer index of each instance's state
     int* d_status = nullptr;
     double* d_E = nullptr;              // [n][nx]
+    float* d_Ef = nullptr;              // [n][nx] float copy
     double* d_U = nullptr;              // [n][5][nx] moments of the current states
     double* d_Ulift = nullptr;          // [n][5][nx] lift sources of pr_force_set_initial
     void* d_vtab = nullptr;             // [n][nvx + 3 nvp^2] velocity tables (element type of f)

@@ -66,35 +66,47 @@ double dt_stab(const pr_force_instance& d, double cfl)
     return cfl / (vmax / dx + em / dvx);
 }
 
-// Geometry for cluster size C; false if the chunk does not fit shared memory.
-bool geometry(int precision, int nvx, int nvp, int C, prk::FGeom* g, size_t* smem)
+// Geometry for cluster size C (the v_x rows split over C CTAs); false if a
+// CTA would be empty or its rows do not fit shared memory.
+bool geometry(int precision, int scheme, int nvx, int nvp, int C, prk::FGeom* g, size_t* smem)
 {
     long long ncol = (long long)nvx * nvp * nvp;
     if (C < 1 || C > prk::FORCE_MAX_CLUSTER) return false;
-    long long chunk = (ncol + C - 1) / C;
-    if (C > 1 && (long long)(C - 1) * chunk >= ncol) return false;  // an empty CTA
-    if ((size_t)chunk * elem(precision) > (size_t)prk::FORCE_MAX_CHUNK_BYTES) return false;
-    size_t sm = prk::force_step_smem(precision, nvx, nvp, (int)chunk);
+    int rows = (nvx + C - 1) / C;
+    if ((C - 1) * rows >= nvx) return false;  // an empty CTA
+    if ((size_t)rows * nvp * nvp * elem(precision) > (size_t)prk::FORCE_MAX_CHUNK_BYTES) return false;
+    size_t sm = prk::force_step_smem(precision, scheme, nvx, nvp, rows);
     if (sm > (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin) - 1024) return false;
     g->nvx = nvx;
     g->nvp = nvp;
     g->ncol = ncol;
     g->C = C;
-    g->chunk = (int)chunk;
+    g->rows = rows;
+    g->bulk = ((size_t)nvp * nvp * elem(precision)) % 16 == 0 ? 1 : 0;
+    g->vec = g->bulk ? (int)(16 / elem(precision)) : 1;
+    prk::force_step_layout(nvp, g->vec, rows, &g->groups, &g->threads);
+    if (g->threads > (g->vec == 1 ? 1024 : 512)) return false;
+    g->buf_off = (int)prk::force_step_buf_off(precision, nvx, nvp);
     *smem = sm;
     return true;
 }
 
-// Default cluster size: the smallest whose chunk fits, raised (up to 8) while
-// the chunk stays above 8192 cells.
-int default_cluster(int precision, int nvx, int nvp)
+// Default cluster size: the smallest that fits, raised (up to 8) while a CTA
+// holds more than 8192 cells.
+int default_cluster(int precision, int scheme, int nvx, int nvp)
 {
     prk::FGeom g;
     size_t sm;
     int C = 1;
-    while (C <= prk::FORCE_MAX_CLUSTER && !geometry(precision, nvx, nvp, C, &g, &sm)) ++C;
+    while (C <= prk::FORCE_MAX_CLUSTER && !geometry(precision, scheme, nvx, nvp, C, &g, &sm)) ++C;
     if (C > prk::FORCE_MAX_CLUSTER) return 0;
-    while (C < 8 && g.chunk > 8192 && geometry(precision, nvx, nvp, C + 1, &g, &sm)) ++C;
+    while (C < 8 && (long long)g.rows * nvp * nvp > 8192) {
+        int D = C + 1;
+        while (D <= 8 && !geometry(precision, scheme, nvx, nvp, D, &g, &sm)) ++D;
+        if (D > 8) break;
+        C = D;
+    }
+    geometry(precision, scheme, nvx, nvp, C, &g, &sm);
     return C;
 }
 
@@ -182,6 +194,7 @@ void destroy(pr_force* b)
     cudaFree(b->d_cur);
     cudaFree(b->d_status);
     cudaFree(b->d_E);
+    cudaFree(b->d_Ef);
     cudaFree(b->d_U);
     cudaFree(b->d_Ulift);
     cudaFree(b->d_vtab);
@@ -205,8 +218,8 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
         const pr_force_instance& d = inst[k];
         if (d.nx != d0.nx || d.nvx != d0.nvx || d.nvp != d0.nvp)
             return fail(PR_EINVAL, "instances of one force batch share nx, nvx and nvp");
-        if (d.nx < 1 || d.nx > 65535 || d.nvx < 2 || d.nvp < 1 || d.nvp > 64 || d.nvx > 4096)
-            return fail(PR_EINVAL, "need 1 <= nx <= 65535, 2 <= nvx <= 4096, 1 <= nvp <= 64");
+        if (d.nx < 1 || d.nx > 65535 || d.nvx < 2 || d.nvp < 1 || d.nvp > 32 || d.nvx > 4096)
+            return fail(PR_EINVAL, "need 1 <= nx <= 65535, 2 <= nvx <= 4096, 1 <= nvp <= 32");
         if (!(d.L > 0) || !(d.x1 > d.x0) || !(d.dt > 0) || !(d.eps > 0))
             return fail(PR_EINVAL, "need L > 0, x1 > x0, dt > 0, eps > 0");
         if (d.bc < PR_BC_PERIODIC || d.bc > PR_BC_REFLECT) return fail(PR_EINVAL, "bad boundary condition");
@@ -217,7 +230,7 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
                 if (!std::isfinite(d.E[i])) return fail(PR_EINVAL, "E must be finite");
     }
     prepare_once();
-    int C = default_cluster(precision, d0.nvx, d0.nvp);
+    int C = default_cluster(precision, scheme, d0.nvx, d0.nvp);
     if (C == 0) return fail(PR_EINVAL, "velocity column too large for 16 CTAs of shared memory");
     pr_force* b = new pr_force();
     b->n = n;
@@ -226,9 +239,10 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
     b->nx = d0.nx;
     b->nvx = d0.nvx;
     b->nvp = d0.nvp;
-    geometry(precision, d0.nvx, d0.nvp, C, &b->g, &b->smem);
+    geometry(precision, scheme, d0.nvx, d0.nvp, C, &b->g, &b->smem);
     int clusters = 0;
-    if (prk::force_step_occupancy(precision, scheme, C, b->smem, &clusters) != 0 || clusters < 1) {
+    if (prk::force_step_occupancy(precision, scheme, b->g.vec, C, b->g.threads, b->smem, &clusters) != 0 ||
+        clusters < 1) {
         destroy(b);
         return fail(PR_EINVAL, "no cluster of this shape fits the device");
     }
@@ -240,7 +254,8 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
     bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cm((void**)&b->d_inst, sizeof(prk::FInst) * n) && cm((void**)&b->d_active, sizeof(prk::Active)) &&
               cm((void**)&b->d_cur, sizeof(int) * n) && cm((void**)&b->d_status, sizeof(int)) &&
-              cm((void**)&b->d_E, sizeof(double) * n * nx) && cm((void**)&b->d_U, sizeof(double) * n * 5 * nx) &&
+              cm((void**)&b->d_E, sizeof(double) * n * nx) && cm((void**)&b->d_Ef, sizeof(float) * n * nx) &&
+              cm((void**)&b->d_U, sizeof(double) * n * 5 * nx) &&
               cm((void**)&b->d_Ulift, sizeof(double) * n * 5 * nx) && cm(&b->d_vtab, vt * n);
     for (int k = 0; ok && k < 2 * n; ++k) {
         void* p = nullptr;
@@ -278,6 +293,13 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
         I.nuv = d.dt / I.dvx;
         I.Emax = em;
         I.E = b->d_E + (size_t)k * nx;
+        I.Ef = b->d_Ef + (size_t)k * nx;
+        I.fa = (float)I.a;
+        I.fb = (float)I.b;
+        I.fnu = (float)I.nu;
+        I.fnuv = (float)I.nuv;
+        I.fEmax = (float)I.Emax;
+        I.fdv3 = (float)I.dv3;
         I.f[0] = b->bufs[2 * k];
         I.f[1] = b->bufs[2 * k + 1];
         I.vtab = static_cast<unsigned char*>(b->d_vtab) + vt * k;
@@ -288,9 +310,22 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
         if (precision == PR_FP64) fill_vtab<double>(t, b->nvx, b->nvp, d.L);
         else fill_vtab<float>(t, b->nvx, b->nvp, d.L);
         memcpy(&tabs[vt * k], t.data(), vt);
+        // first v_x row whose node, in the element type, is > 0 (the kernel
+        // takes the upwind side from the same comparison)
+        I.hpos = b->nvx;
+        for (int j = 0; j < b->nvx; ++j) {
+            bool pos = precision == PR_FP64 ? reinterpret_cast<const double*>(t.data())[j] > 0.0
+                                            : reinterpret_cast<const float*>(t.data())[j] > 0.0f;
+            if (pos) {
+                I.hpos = j;
+                break;
+            }
+        }
     }
     prk::Active all{0, n};
+    std::vector<float> Ef(E.begin(), E.end());
     ok = cudaMemcpy(b->d_E, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(b->d_Ef, Ef.data(), sizeof(float) * Ef.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->d_vtab, tabs.data(), tabs.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->d_inst, b->h.data(), sizeof(prk::FInst) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -522,7 +557,7 @@ int pr_force_config(const pr_force* b, int* cluster, int* chunk)
 {
     if (!b) return PR_EINVAL;
     if (cluster) *cluster = b->g.C;
-    if (chunk) *chunk = b->g.chunk;
+    if (chunk) *chunk = b->g.rows * b->nvp * b->nvp;
     return PR_OK;
 }
 
@@ -531,10 +566,11 @@ int pr_force_set_cluster(pr_force* b, int cluster)
     if (!b) return PR_EINVAL;
     prk::FGeom g;
     size_t sm;
-    if (!geometry(b->precision, b->nvx, b->nvp, cluster, &g, &sm))
+    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, cluster, &g, &sm))
         return ffail(b, PR_EINVAL, "cluster size %d does not fit this column", cluster);
     int clusters = 0;
-    if (prk::force_step_occupancy(b->precision, b->scheme, cluster, sm, &clusters) != 0 || clusters < 1)
+    if (prk::force_step_occupancy(b->precision, b->scheme, g.vec, cluster, g.threads, sm, &clusters) != 0 ||
+        clusters < 1)
         return ffail(b, PR_EINVAL, "no cluster of %d CTAs fits the device", cluster);
     FCUDA(b, cudaStreamSynchronize(b->stream));
     b->g = g;

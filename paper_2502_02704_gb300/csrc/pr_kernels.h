@@ -97,16 +97,19 @@ cudaError_t adj_copy_state(const Inst* insts, const InstState* st, int b, double
 // ---- fine propagator with an exterior force (force.cu) ----
 constexpr int FORCE_THREADS = 256;       // threads per CTA of the force kernels
 constexpr int FORCE_MAX_CLUSTER = 16;    // CTAs per x column (8 portable, 16 opt-in)
-constexpr int FORCE_MAX_CHUNK_BYTES = 96 * 1024;  // f* of one CTA's velocity chunk, staged in shared memory
+constexpr int FORCE_MAX_CHUNK_BYTES = 96 * 1024;  // f* of one CTA's v_x rows, staged in shared memory
 
 // One instance of the force path.  f[buf] is [nx][ncol] of T (float or double).
 struct FInst {
-    int nx, bc, collide, pad0;
+    int nx, bc, collide;
+    int hpos;                  // first v_x row whose node is > 0 (in the element type)
     double L, dx, dvx, dvp, dv3, dt, eps;
     double a, b;               // f^{n+1} = a f* + b M
     double nu, nuv;            // dt/dx, dt/dv_x
     double Emax;               // max_i |E_i|
     const double* E;           // [nx] exterior force at the cell centres (device)
+    const float* Ef;           // the same in float (the float path converts nothing per thread)
+    float fa, fb, fnu, fnuv, fEmax, fdv3;
     void* f[2];                // ping-pong state
     const void* vtab;          // T: v_x[nvx], v_y[nvp2], v_z[nvp2], v_y^2+v_z^2[nvp2]
     const double* Uin;         // lift source, conserved [5][nx] (device) or null
@@ -119,18 +122,27 @@ struct FGeom {
     int nvx, nvp;
     long long ncol;            // nvx * nvp^2
     int C;                     // CTAs (cluster size) per x column
-    int chunk;                 // velocities per CTA
+    int rows;                  // v_x rows per CTA (the last CTA may have fewer)
+    int vec;                   // (v_y, v_z) cells per thread: 16 bytes when bulk, else 1
+    int groups;                // row groups per CTA (nvp^2/vec threads each)
+    int threads;               // threads per CTA of the step kernel
+    int bulk;                  // rows are 16-byte multiples: stage them with bulk copies
+    int buf_off;               // shared-memory offset of the staging buffers
 };
 
 cudaError_t prepare_force_kernels(int max_smem);
-size_t force_step_smem(int precision, int nvx, int nvp, int chunk);
+size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows);
+size_t force_step_buf_off(int precision, int nvx, int nvp);
+void force_step_layout(int nvp, int vec, int rows, int* groups, int* threads);
 size_t force_lift_smem(int precision, int nvx, int nvp);
-int force_step_occupancy(int precision, int scheme, int C, size_t smem, int* clusters);
+int force_step_occupancy(int precision, int scheme, int vec, int C, int threads, size_t smem, int* clusters);
 // One fine step of every active instance; input buffer cur[b] ^ (step & 1);
 // last != 0 also writes P(f^{n+1}) into Ucur (and Uout).
+// Each CTA stages its input rows with bulk copies and waits on an mbarrier
+// for at most wait_ns (then PR_ETIMEOUT).
 cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, int* cur, int step, int last, int* status, size_t smem,
-                              cudaStream_t s);
+                              cudaStream_t s, long long wait_ns = WAIT_LIMIT_NS);
 // Lift Uin into f[0] of the active instances, cur <- 0.
 cudaError_t launch_force_lift(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, int* cur, int* status, cudaStream_t s);

@@ -49,10 +49,11 @@ def _beams_f_gpu(nx, nvx, nvp, L, dt):
 @pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
 @pytest.mark.parametrize("scheme", [pr.PR_UPWIND, pr.PR_MUSCL])
 @pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW, pr.PR_BC_REFLECT])
-@pytest.mark.parametrize("cluster", [1, 3, 8])
+@pytest.mark.parametrize("cluster", [1, 3, 7])
 def test_fine_steps_match_oracle(precision, scheme, bc, cluster):
-    # nvx = 25 (odd: a v_x = 0 node), nvp = 6 (36 < 256 threads: several v_x
-    # rows per thread stride); with 3 or 8 CTAs per column the last chunk is ragged
+    # nvx = 25 (odd: a v_x = 0 node) split over 1, 3 or 7 CTAs (9/9/7 and
+    # 4 x 6 + 1 rows: ragged last CTAs); nvp = 6: 36 (v_y, v_z) cells on a
+    # 64-thread CTA, so 28 threads only join the reductions
     nx, nvx, nvp, L, n = 14, 25, 6, 7.0, 5
     E = W.test3_force(nx)
     U = _profile(nx)
@@ -83,8 +84,8 @@ def test_fine_steps_match_oracle(precision, scheme, bc, cluster):
 
 @pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
 def test_wide_perpendicular_grid_and_several_instances(precision):
-    # nvp = 20 (400 > 256 threads: less than one row per stride), three
-    # instances with different eps, L, E and boundary in one launch
+    # nvp = 20 (400 threads, 13 warps), three instances with different eps,
+    # L, E and boundary in one launch
     nx, nvx, nvp, n = 9, 12, 20, 4
     specs = [(1e-3, 6.0, pr.PR_BC_PERIODIC, 1.0), (1.0, 7.0, pr.PR_BC_OUTFLOW, -0.5), (1e-5, 8.0, pr.PR_BC_REFLECT, 2.0)]
     insts, ks, dts = [], [], []
@@ -204,7 +205,7 @@ def test_free_running_slice_of_a_force_problem():
 def test_force_path_errors_are_reported():
     nx, nvx, nvp = 8, 8, 4
     ok = pr.ForceInstance(nx, nvx, nvp, 1e-3, E=np.ones(nx))
-    for bad in (pr.ForceInstance(nx, nvx, 65, 1e-3), pr.ForceInstance(nx, 1, nvp, 1e-3),
+    for bad in (pr.ForceInstance(nx, nvx, 33, 1e-3), pr.ForceInstance(nx, 1, nvp, 1e-3),
                 pr.ForceInstance(nx, nvx, nvp, -1.0), pr.ForceInstance(nx, nvx, nvp, 1e-3, E=np.full(nx, np.nan))):
         with pytest.raises(pr.PrError) as ei:
             pr.pr_force_create([bad], pr.PR_UPWIND, pr.PR_FP64)
@@ -213,9 +214,10 @@ def test_force_path_errors_are_reported():
         pr.pr_force_create([ok, pr.ForceInstance(nx + 1, nvx, nvp, 1e-3)])
     b = pr.pr_force_create([ok], pr.PR_UPWIND, pr.PR_FP64)
     try:
-        with pytest.raises(pr.PrError) as ei:
-            pr.pr_force_set_cluster(b, 17)
-        assert ei.value.code == pr.PR_EINVAL
+        for C in (17, 5):  # too many, or an empty CTA (8 rows over 5 CTAs of 2)
+            with pytest.raises(pr.PrError) as ei:
+                pr.pr_force_set_cluster(b, C)
+            assert ei.value.code == pr.PR_EINVAL
         bad_U = _profile(nx)
         bad_U[4, 3] = -1.0
         with pytest.raises(pr.PrError) as ei:
