@@ -333,6 +333,114 @@ def _large_section(pr, np, torch):
             "timing": "wall clock, parareal includes the first coarse guess and the moment readback"}
 
 
+def _moment_rel_err(np, V, Vref):
+    """max over the conserved components of max|V - Vref| / scale, the
+    momenta scaled by max(|rho u|, rho sqrt(theta)) (thermal momentum)."""
+    rho = Vref[0]
+    u2 = (Vref[1] ** 2 + Vref[2] ** 2 + Vref[3] ** 2) / rho ** 2
+    th = (2 * Vref[4] / rho - u2) / 3
+    thermal = np.max(np.abs(rho)) * np.sqrt(np.max(np.abs(th)))
+    sc = [np.max(np.abs(Vref[0]))] + [max(np.max(np.abs(Vref[q])), thermal) for q in (1, 2, 3)] + \
+         [np.max(np.abs(Vref[4]))]
+    return float(max(np.max(np.abs(V[q] - Vref[q])) / sc[q] for q in range(5)))
+
+
+def _test3_section(pr, np, torch):
+    """Test 3 (exterior force, Sec. 5.3): 100 x 256 x 16 x 16 cells on [0, 2] x
+    [-8, 8]^3, periodic, eps = 1e-5, two beams, E(x) = -5 x^4 (x-2)^4 (x-1),
+    T = 0.5, N_g = 200 slices of n_f = 4 fine steps (N_f = 800, the grids the
+    paper states for its other tests).  Serial kinetic runs, a 64-instance
+    batch for the HBM roofline, and Algorithm 2 at K = 3, 6, 9."""
+    from paper_2502_02704_gb300 import workloads as W
+
+    nx, nvx, nvp, L, eps, T, N, nf = 100, 256, 16, 8.0, 1e-5, 0.5, 200, 4
+    E = W.test3_force(nx)
+    dt = T / (N * nf)
+    ncell = nx * nvx * nvp * nvp
+    inst = pr.ForceInstance(nx, nvx, nvp, dt, L=L, x0=0.0, x1=2.0, eps=eps, E=E)
+    # the beams: each lifted by the library, summed on the host
+    tmp = pr.pr_force_create([inst, inst], pr.PR_UPWIND, pr.PR_FP64)
+    try:
+        for j, U in enumerate(W.test3_beams(nx)):
+            pr.pr_force_set_initial(tmp, j, U)
+        f0 = pr.pr_force_get_f(tmp, 0) + pr.pr_force_get_f(tmp, 1)
+        pr.pr_force_set_f(tmp, 0, f0)
+        U0 = pr.pr_force_moments(tmp, 0, pr.PR_PRIMITIVE)
+    finally:
+        pr.pr_force_destroy(tmp)
+    out = {"workload": "Test 3: 100 x 256 x 16 x 16, [0,2] x [-8,8]^3, periodic, eps=1e-5, two beams, "
+                       "E=-5x^4(x-2)^4(x-1), T=0.5, N_g=200, n_f=4 (800 fine steps), upwind",
+           "paper_context": {"hardware": "2 x Xeon 8268, 32 threads, FP64", "kinetic_s": 672.8,
+                             "parareal_s": {"3": 71.7, "6": 153.0, "9": 218.4},
+                             "successive_error": {"3": 1.387e-3, "6": 7.782e-6, "9": 2.421e-8}}}
+    kinetic = {}
+    for prec, name in ((pr.PR_MIXED, "mixed"), (pr.PR_FP64, "fp64")):
+        b = pr.pr_force_create([inst], pr.PR_UPWIND, prec)
+        try:
+            pr.pr_force_set_f(b, 0, f0)
+            pr.pr_force_run(b, 20)
+            pr.pr_force_sync(b)
+            pr.pr_force_kernel_time(b, reset=True)
+            pr.pr_force_set_f(b, 0, f0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pr.pr_force_run(b, N * nf)
+            V = pr.pr_force_moments(b, 0)
+            wall = time.perf_counter() - t0
+            kms, _ = pr.pr_force_kernel_time(b)
+            kinetic[name] = {"wall_ms": wall * 1e3, "step_us": kms * 1e3,
+                             "cell_updates_per_s": ncell / (kms * 1e-3), "V": V,
+                             "cluster": pr.pr_force_config(b)[0]}
+        finally:
+            pr.pr_force_destroy(b)
+    Vk = kinetic["fp64"].pop("V")
+    kinetic["mixed"]["max_rel_err_vs_fp64"] = _moment_rel_err(np, kinetic["mixed"].pop("V"), Vk)
+    out["kinetic"] = kinetic
+    # 64 independent instances in one launch per step: state 3.4 GB per buffer
+    nb, steps = 64, 20
+    b = pr.pr_force_create([inst] * nb, pr.PR_UPWIND, pr.PR_MIXED)
+    try:
+        for i in range(nb):
+            pr.pr_force_set_initial(b, i, U0)
+        pr.pr_force_run(b, 5)
+        pr.pr_force_sync(b)
+        pr.pr_force_kernel_time(b, reset=True)
+        pr.pr_force_run(b, steps)
+        kms, _ = pr.pr_force_kernel_time(b)
+    finally:
+        pr.pr_force_destroy(b)
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    ach = 8.0 * ncell * nb / (kms * 1e-3) / 1e9
+    out["batch64_mixed"] = {"step_ms": kms, "cell_updates_per_s": ncell * nb / (kms * 1e-3),
+                            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                         "frac": ach / hbm, "kernel": "k_force_step<float, upwind, 4>",
+                                         "bytes_per_cell_update": 8}}
+    # Algorithm 2
+    para = {}
+    for prec, name in ((pr.PR_MIXED, "mixed"), (pr.PR_FP64, "fp64")):
+        ctx = pr.pr_init_force(nx, 0.0, 2.0, pr.PR_BC_PERIODIC, nvx, nvp, L, eps, T, N, E, precision=prec, nf=nf)
+        try:
+            runs = []
+            for K in (3, 6, 9):
+                pr.pr_set_initial(ctx, U0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                pr.pr_set_initial(ctx, U0)
+                kd, errs = pr.pr_parareal_run(ctx, K)
+                UN = pr.pr_moments(ctx, N)
+                wall = time.perf_counter() - t0
+                rel = _moment_rel_err(np, UN, Vk)
+                runs.append({"K": K, "ms": wall * 1e3, "successive_error": float(errs[-1]),
+                             "max_rel_err_vs_fp64_kinetic": rel})
+            para[name] = runs
+        finally:
+            pr.pr_destroy(ctx)
+    out["parareal"] = para
+    out["timing"] = "kernel step times by CUDA events on the launching stream; wall clock around synchronous calls"
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -446,11 +554,16 @@ def run_ours(args):
         para = _parareal_speedup(pr, np)
     except Exception as e:  # reported, not hidden
         para = {"error": repr(e)}
-    ragged = large = None
+    ragged = large = test3 = None
     try:
         ragged = _ragged_section(pr, torch)
     except Exception as e:
         ragged = {"error": repr(e)}
+    if not args.no_test3:
+        try:
+            test3 = _test3_section(pr, np, torch)
+        except Exception as e:
+            test3 = {"error": repr(e)}
     if not args.no_large:
         try:
             large = _large_section(pr, np, torch)
@@ -478,6 +591,7 @@ def run_ours(args):
         "parareal": para,
         "ragged_batch": ragged,
         "parareal_large": large,
+        "test3_force": test3,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -495,6 +609,8 @@ def main():
                     help="omit the host-oracle timing (used only for profiler runs)")
     ap.add_argument("--no-large", action="store_true",
                     help="omit the 2048 x 48^3 parareal comparison (about 30 s, 120 GB)")
+    ap.add_argument("--no-test3", action="store_true",
+                    help="omit the Test 3 (exterior force) section (about 10 s)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

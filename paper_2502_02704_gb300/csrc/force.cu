@@ -290,7 +290,8 @@ __device__ __forceinline__ long long gtimer()
 }
 
 // Wait (bounded by limit_ns) until the transaction count of the single-use
-// mbarrier at phase 0 completes; false on time-out.
+// mbarrier at phase 0 completes; false on time-out.  Each try suspends the
+// thread for up to 100 us unless the phase completes first.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, long long limit_ns)
 {
     const long long t0 = gtimer();
@@ -298,10 +299,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, long long limit_ns)
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(mbar), "r"(0)
+            : "r"(mbar), "r"(0), "r"(100000)
             : "memory");
         if (done) return true;
         if ((it & 63) == 63 && gtimer() - t0 > limit_ns) return false;
@@ -465,13 +466,20 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
     for (int k = threadIdx.x; k < nvx; k += blockDim.x) vxs[k] = vt[k];
     T vy[VEC], vz[VEC], vp2[VEC];
     int jy[VEC], jz[VEC];
+    {
+        int y = jp / g.nvp, z = jp - (jp / g.nvp) * g.nvp;  // one division; the lanes step on
 #pragma unroll
-    for (int l = 0; l < VEC; ++l) {
-        vy[l] = active ? vt[nvx + jp + l] : T(0);
-        vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
-        vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
-        jy[l] = (jp + l) / g.nvp;
-        jz[l] = jp + l - jy[l] * g.nvp;
+        for (int l = 0; l < VEC; ++l) {
+            vy[l] = active ? vt[nvx + jp + l] : T(0);
+            vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
+            vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
+            jy[l] = y;
+            jz[l] = z;
+            if (++z == g.nvp) {
+                z = 0;
+                ++y;
+            }
+        }
     }
     __syncthreads();  // mbarrier initialised; thread-staged rows visible
     if (bulk && !mbar_wait(mbar, wait_ns)) {
