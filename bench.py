@@ -36,7 +36,9 @@ METRIC = "phase-space cell-updates/s (FP32 vs FP64) and parareal speedup on 1 GB
 UNIT = "cell-updates/s"
 WORKLOAD = "smooth periodic fine solve, Nx=512, 32^3 on [-8,8]^3, MUSCL-minmod, eps in {1,1e-2,1e-4} batched, 200 steps"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_run_traffic.txt")
+FORCE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_step_traffic.txt")
 FINE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "fine.cu")
+FORCE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "force.cu")
 
 
 def max_over_ranks(values, dist=None, device=None):
@@ -412,10 +414,19 @@ def _test3_section(pr, np, torch):
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     ach = 8.0 * ncell * nb / (kms * 1e-3) / 1e9
+    traffic = None
+    try:  # ncu DRAM bytes of one batch step, valid while the kernel source is unchanged
+        tj = json.load(open(FORCE_TRAFFIC_FILE))
+        if tj.get("force_cu_sha256_16") == _src_hash(FORCE_SRC):
+            traffic = tj["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
     out["batch64_mixed"] = {"step_ms": kms, "cell_updates_per_s": ncell * nb / (kms * 1e-3),
                             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                                         "frac": ach / hbm, "kernel": "k_force_step<float, upwind, 4>",
-                                         "bytes_per_cell_update": 8}}
+                                         "frac": ach / hbm, "traffic": traffic,
+                                         "algorithmic_bytes_per_launch": 8.0 * ncell * nb,
+                                         "kernel": "k_force_step<float, upwind, 4>", "bytes_per_cell_update": 8,
+                                         "peak_source": "measured" if peaks else "fallback"}}
     # Algorithm 2
     para = {}
     for prec, name in ((pr.PR_MIXED, "mixed"), (pr.PR_FP64, "fp64")):

@@ -372,6 +372,17 @@ int pr_force_set_cluster(pr_force* b, int cluster);
  * steps); reset = 1 clears the accumulator. */
 int pr_force_kernel_time(pr_force* b, double* avg_ms, int* steps, int reset);
 
+/* Failure-detection check (not in the paper): one fine step of every
+ * instance in which each CTA, besides its real staging copies, waits on a
+ * second mbarrier that expects bytes no copy delivers, with the wait limit
+ * shortened to wait_ms.  The waits run out, record PR_ETIMEOUT, then each CTA
+ * waits for its real copies before it leaves; the call returns that status
+ * after clearing it (PR_ETIMEOUT is the expected result).  The object stays
+ * usable; the instance states are unspecified until they are set again.
+ * PR_EINVAL when the rows are not staged by bulk copies (nvp^2 x element
+ * size not a multiple of 16 bytes).  No GPU fault is involved.  Synchronous. */
+int pr_force_inject_wait_timeout(pr_force* b, int wait_ms);
+
 /* dt_stab of the reading above for inst (E read from the host array).
  * Errors: PR_EINVAL. */
 int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt);

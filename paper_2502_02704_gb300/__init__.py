@@ -118,6 +118,7 @@ _SIGS = {
     "pr_force_set_cluster": (C.c_int, [_VP, C.c_int]),
     "pr_force_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_force_dt_stab": (C.c_int, [C.POINTER(pr_force_instance), C.c_double, _D]),
+    "pr_force_inject_wait_timeout": (C.c_int, [_VP, C.c_int]),
     "pr_init_force": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_grid), C.POINTER(pr_velocity), C.c_double,
                                 C.POINTER(pr_time), C.c_int, _D]),
 }
@@ -493,6 +494,12 @@ def pr_force_kernel_time(b, reset=False):
     n = C.c_int()
     _force_check(b, lib().pr_force_kernel_time(b.ptr, C.byref(ms), C.byref(n), int(bool(reset))))
     return ms.value, n.value
+
+
+def pr_force_inject_wait_timeout(b, wait_ms=50) -> int:
+    """Run the failure-detection step; returns the status it reported
+    (PR_ETIMEOUT expected) without raising."""
+    return int(lib().pr_force_inject_wait_timeout(b.ptr, int(wait_ms)))
 
 
 def pr_force_dt_stab(inst: ForceInstance, cfl=0.5) -> float:

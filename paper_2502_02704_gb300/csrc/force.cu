@@ -384,7 +384,7 @@ __device__ __forceinline__ void stv(T* p, const Pack<T, V>& v)
 template <typename T, int SCHEME, int VEC>
 __global__ void __launch_bounds__(VEC == 1 ? 1024 : 512, 1)
 k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
-             int step, int last, int* __restrict__ status, long long wait_ns)
+             int step, int last, int* __restrict__ status, long long wait_ns, int poison)
 {
     const int b = blockIdx.z;
     if (b < act->begin || b >= act->end) return;  // uniform over the cluster
@@ -459,8 +459,18 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
         segs[nseg] = {cp2, r0, na, 0, mp2};
         dst[nseg++] = nb + (size_t)2 * R * nvp2;
     }
-    // the bulk copies go out first; the tables load while they are in flight
-    if (bulk && threadIdx.x == 0) stage_bulk<T>(segs, nseg, dst, nvp2, mbar);
+    // the bulk copies go out first; the tables load while they are in flight.
+    // poison (failure-detection check): a second mbarrier expects 16 bytes
+    // that no copy delivers, so the wait on it runs out
+    const uint32_t mbar2 = mbar + 8;
+    if (bulk && threadIdx.x == 0) {
+        stage_bulk<T>(segs, nseg, dst, nvp2, mbar);
+        if (poison) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar2), "r"(1) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar2), "r"(16) : "memory");
+        }
+    }
     stage_threads<T>(segs, nseg, dst, nvx, nvp2, bulk);
     const T* vt = static_cast<const T*>(I.vtab);
     for (int k = threadIdx.x; k < nvx; k += blockDim.x) vxs[k] = vt[k];
@@ -482,6 +492,7 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
         }
     }
     __syncthreads();  // mbarrier initialised; thread-staged rows visible
+    if (bulk && poison && !mbar_wait(mbar2, wait_ns)) atomicCAS(status, 0, ST_TIMEOUT);
     if (bulk && !mbar_wait(mbar, wait_ns)) {
         atomicCAS(status, 0, ST_TIMEOUT);
         mbar_wait(mbar, wait_ns);  // let copies in flight land before the buffers are reused
@@ -875,7 +886,7 @@ int force_step_occupancy(int precision, int scheme, int vec, int C, int threads,
 
 cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, int* cur, int step, int last, int* status, size_t smem,
-                              cudaStream_t s, long long wait_ns)
+                              cudaStream_t s, long long wait_ns, int poison)
 {
     void* fn = pick_step(precision, scheme, g.vec);
     if (!fn) return cudaErrorInvalidValue;
@@ -891,8 +902,8 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    void* args[] = {(void*)&insts, (void*)&g,    (void*)&act,    (void*)&cur,
-                    (void*)&step,  (void*)&last, (void*)&status, (void*)&wait_ns};
+    void* args[] = {(void*)&insts, (void*)&g,      (void*)&act,     (void*)&cur,   (void*)&step,
+                    (void*)&last,  (void*)&status, (void*)&wait_ns, (void*)&poison};
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 

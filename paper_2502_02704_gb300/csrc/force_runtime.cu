@@ -423,7 +423,10 @@ int take_status(pr_force* b)
     FCUDA(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
         cudaMemset(b->d_status, 0, sizeof(int));
-        return ffail(b, st, st == PR_ENONPHYS ? "a density or temperature became non-positive" : "device status %d",
+        return ffail(b, st,
+                     st == PR_ENONPHYS   ? "a density or temperature became non-positive"
+                     : st == PR_ETIMEOUT ? "a staging wait timed out"
+                                         : "device status %d",
                      st);
     }
     return PR_OK;
@@ -590,6 +593,21 @@ int pr_force_kernel_time(pr_force* b, double* avg_ms, int* steps, int reset)
         b->steps_timed = 0;
     }
     return PR_OK;
+}
+
+int pr_force_inject_wait_timeout(pr_force* b, int wait_ms)
+{
+    if (!b) return PR_EINVAL;
+    if (!b->g.bulk || wait_ms < 1) return ffail(b, PR_EINVAL, "needs bulk-copy staging and wait_ms >= 1");
+    cudaStream_t s = b->stream;
+    FCUDA(b, cudaStreamSynchronize(s));
+    FCUDA(b, set_active(b, 0, b->n, s));
+    FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx, b->n,
+                                    b->d_active, b->d_cur, 0, 1, b->d_status, b->smem, s,
+                                    (long long)wait_ms * 1000000LL, 1));
+    FCUDA(b, prk::launch_force_advance(b->d_active, b->d_cur, 1, b->n, s));
+    pr_internal_count_launches(2);
+    return prf::take_status(b);
 }
 
 int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt)

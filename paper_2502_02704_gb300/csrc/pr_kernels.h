@@ -139,10 +139,11 @@ int force_step_occupancy(int precision, int scheme, int vec, int C, int threads,
 // One fine step of every active instance; input buffer cur[b] ^ (step & 1);
 // last != 0 also writes P(f^{n+1}) into Ucur (and Uout).
 // Each CTA stages its input rows with bulk copies and waits on an mbarrier
-// for at most wait_ns (then PR_ETIMEOUT).
+// for at most wait_ns (then PR_ETIMEOUT).  poison = 1 adds a wait on a second
+// mbarrier that no copy completes (failure-detection check: PR_ETIMEOUT).
 cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, int* cur, int step, int last, int* status, size_t smem,
-                              cudaStream_t s, long long wait_ns = WAIT_LIMIT_NS);
+                              cudaStream_t s, long long wait_ns = WAIT_LIMIT_NS, int poison = 0);
 // Lift Uin into f[0] of the active instances, cur <- 0.
 cudaError_t launch_force_lift(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, int* cur, int* status, cudaStream_t s);

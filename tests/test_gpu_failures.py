@@ -1,5 +1,6 @@
 """Failure detection on the device without a GPU fault: a dependency wait of
-the persistent launch that runs out (a flag nothing sets), non-physical
+the persistent launch that runs out (a flag nothing sets), a staging wait of
+the force path that runs out (an mbarrier no copy completes), non-physical
 states, and that each object stays usable afterwards."""
 import numpy as np
 import pytest
@@ -41,6 +42,34 @@ def test_dependency_wait_runs_out_and_batch_stays_usable():
     finally:
         pr.pr_batch_destroy(b)
     assert np.array_equal(V, _reference_run(5))
+
+
+def _force_run(b, steps):
+    pr.pr_force_set_initial(b, 0, W.smooth_periodic(8))
+    pr.pr_force_run(b, steps)
+    return pr.pr_force_moments(b, 0)
+
+
+def test_force_staging_wait_runs_out_and_object_stays_usable():
+    E = W.test3_force(8)
+    inst = pr.ForceInstance(8, 16, 4, 1e-3, E=E)  # 16 floats per row: bulk-copy staging
+    b = pr.pr_force_create([inst], pr.PR_UPWIND, pr.PR_MIXED)
+    fresh = pr.pr_force_create([inst], pr.PR_UPWIND, pr.PR_MIXED)
+    try:
+        pr.pr_force_set_initial(b, 0, W.smooth_periodic(8))
+        for wait_ms in (20, 50):
+            assert pr.pr_force_inject_wait_timeout(b, wait_ms) == pr.PR_ETIMEOUT
+            assert "timed out" in pr.pr_force_last_error(b)
+        assert np.array_equal(_force_run(b, 3), _force_run(fresh, 3))
+    finally:
+        pr.pr_force_destroy(b)
+        pr.pr_force_destroy(fresh)
+    # rows of 25 floats are staged by the threads: no staging wait to poison
+    b = pr.pr_force_create([pr.ForceInstance(8, 16, 5, 1e-3, E=E)], pr.PR_UPWIND, pr.PR_MIXED)
+    try:
+        assert pr.pr_force_inject_wait_timeout(b, 20) == pr.PR_EINVAL
+    finally:
+        pr.pr_force_destroy(b)
 
 
 def test_nonphysical_state_is_reported_and_cleared():
