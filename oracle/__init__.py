@@ -30,6 +30,7 @@ _lib = None
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT = 0, 1, 2
 UPWIND, MUSCL = 0, 1
 SOUND_GAMMA53, SOUND_SQRT_THETA = 0, 1
+COARSE_EULER, COARSE_CNS = 0, 1
 
 
 class OracleError(RuntimeError):
@@ -63,7 +64,7 @@ class _Kin(C.Structure):
 
 class _Pr(C.Structure):
     _fields_ = [("kin", _Kin), ("T", C.c_double), ("N", C.c_int), ("cfl_f", C.c_double),
-                ("cfl_g", C.c_double), ("sound", C.c_int), ("nf", C.c_int)]
+                ("cfl_g", C.c_double), ("sound", C.c_int), ("nf", C.c_int), ("coarse", C.c_int), ("lift", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -77,7 +78,7 @@ class _VKin(C.Structure):
 
 class _VPr(C.Structure):
     _fields_ = [("kin", _VKin), ("T", C.c_double), ("N", C.c_int), ("cfl_f", C.c_double),
-                ("cfl_g", C.c_double), ("sound", C.c_int), ("nf", C.c_int)]
+                ("cfl_g", C.c_double), ("sound", C.c_int), ("nf", C.c_int), ("coarse", C.c_int), ("lift", C.c_int)]
 
 
 def lib():
@@ -111,6 +112,10 @@ def lib():
                 "or_coarse_run_force": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double,
                                                   C.c_int, C.c_double, _D, _D, _D, C.POINTER(C.c_int)]),
                 "or_v_lift": (C.c_int, [pvk, _D, _D]),
+                "or_v_lift_ce": (C.c_int, [pvk, _D, _D]),
+                "or_lift_ce": (C.c_int, [pk, _D, _D]),
+                "or_coarse_run_cns": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
+                                                C.c_double, C.c_double, _D, _D, _D, C.POINTER(C.c_int)]),
                 "or_v_project": (C.c_int, [pvk, _D, _D]),
                 "or_v_project_cons": (C.c_int, [pvk, _D, _D]),
                 "or_v_fine_dt_stab": (C.c_double, [pvk, C.c_double]),
@@ -174,9 +179,11 @@ class Parareal:
     cfl_g: float = 0.5
     sound: int = SOUND_GAMMA53
     nf: int = 0
+    coarse: int = COARSE_EULER
+    lift: int = 0
 
     def c(self) -> _Pr:
-        return _Pr(self.kin.c(), self.T, self.N, self.cfl_f, self.cfl_g, self.sound, self.nf)
+        return _Pr(self.kin.c(), self.T, self.N, self.cfl_f, self.cfl_g, self.sound, self.nf, self.coarse, self.lift)
 
 
 def set_threads(n: int) -> None:
@@ -209,6 +216,29 @@ def lift(k: Kin, U: np.ndarray) -> np.ndarray:
     kc = k.c()
     _check(lib().or_lift(C.byref(kc), _ptr(U), _ptr(f)), "lift")
     return f
+
+
+def lift_ce(k: Kin, U: np.ndarray) -> np.ndarray:
+    """First-order (Chapman-Enskog) lifting L^(1) of Def. 3."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    f = np.empty((k.nx, k.nv3))
+    kc = k.c()
+    _check(lib().or_lift_ce(C.byref(kc), _ptr(U), _ptr(f)), "lift_ce")
+    return f
+
+
+def coarse_run_cns(nx: int, bc: int, cfl: float, dT: float, V: np.ndarray, eps: float, E=None, x0: float = 0.0,
+                   x1: float = 1.0, sound: int = SOUND_GAMMA53) -> tuple[np.ndarray, int]:
+    """Compressible Navier-Stokes coarse model (Eq. 8) over dT."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    out = np.empty_like(V)
+    ns = C.c_int()
+    Ep = _ptr(np.ascontiguousarray(E, dtype=np.float64)) if E is not None else C.cast(None, _D)
+    Ekeep = E
+    _check(lib().or_coarse_run_cns(nx, x0, x1, bc, cfl, sound, dT, eps, Ep, _ptr(V), _ptr(out), C.byref(ns)),
+           "coarse_run_cns")
+    del Ekeep
+    return out, ns.value
 
 
 def project(k: Kin, f: np.ndarray, conserved: bool = False) -> np.ndarray:
@@ -339,9 +369,12 @@ class VParareal:
     cfl_g: float = 0.5
     sound: int = SOUND_GAMMA53
     nf: int = 0
+    coarse: int = COARSE_EULER
+    lift: int = 0
 
     def c(self) -> _VPr:
-        return _VPr(self.kin.c(), self.T, self.N, self.cfl_f, self.cfl_g, self.sound, self.nf)
+        return _VPr(self.kin.c(), self.T, self.N, self.cfl_f, self.cfl_g, self.sound, self.nf, self.coarse,
+                    self.lift)
 
 
 def v_lift(k: VKin, U: np.ndarray) -> np.ndarray:
@@ -349,6 +382,14 @@ def v_lift(k: VKin, U: np.ndarray) -> np.ndarray:
     f = np.empty((k.nx, k.ncol))
     kc = k.c()
     _check(lib().or_v_lift(C.byref(kc), _ptr(U), _ptr(f)), "v_lift")
+    return f
+
+
+def v_lift_ce(k: VKin, U: np.ndarray) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    f = np.empty((k.nx, k.ncol))
+    kc = k.c()
+    _check(lib().or_v_lift_ce(C.byref(kc), _ptr(U), _ptr(f)), "v_lift_ce")
     return f
 
 

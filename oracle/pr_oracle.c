@@ -40,6 +40,23 @@
  *   R11 boundary ghosts: periodic wrap; outflow (the paper's "absorbing") copies the
  *       boundary cell; reflecting mirrors the cell and reverses v_x.
  *   R12 a non-positive density or temperature is an error (no clamping).
+ *
+ * Higher-order coupling (Eq. 8, Remark 1 / Def. 3 with L = 1), not run by the
+ * paper; readings:
+ *   R22 compressible Navier-Stokes coarse model of Eq. (8) for BGK with tau = 1:
+ *       mu = rho theta, kappa = 5 rho theta / 2 (the first-order Chapman-Enskog
+ *       moments of the BGK model, Prandtl number 1).  1-D in x: the viscous flux
+ *       of (rho u, E) is -eps (mu (4/3) du_x, mu du_y, mu du_z) and
+ *       -eps (mu (4/3) u_x du_x + mu u_y du_y + mu u_z du_z + kappa dtheta), with
+ *       the gradients (V_{i+1} - V_i)/dx and mu, kappa, u averaged over the two
+ *       cells of the face, added to the Rusanov flux; local steps
+ *       dt = cfl min(dx / max S, dx^2 / (2 eps (5/3) max theta)).
+ *   R23 first-order lifting f = M + eps g1, g1 = -(d_t + v d_x) M with the Euler
+ *       time derivatives: g1 = -M [ (c_x (c . du) - |c|^2 du_x / 3) / theta
+ *       + c_x (|c|^2 / (2 theta) - 5/2) dtheta / theta ], c = v - u; the
+ *       gradients of u and theta by central differences through the ghosts.
+ *       An exterior force cancels in g1 (its terms in d_t M and E d_v M are
+ *       opposite), so the force path lifts with the same formula.
  */
 #include "pr_oracle.h"
 
@@ -413,8 +430,30 @@ static void rusanov(int nx, int bc, int sound, const double* V, int c, double* H
  * exterior force E [nx] (NULL: none) each local step adds dt S(V_i), the source
  * S = (0, rho E_i, 0, 0, rho u_x E_i) of the Euler system Eq. (5) (reading R18:
  * forward Euler, the force at the cell centre). */
+/* Viscous flux D_{c+1/2} of Eq. (8) (reading R22), added to the Rusanov flux. */
+static void viscous(int nx, int bc, double dx, double eps, const double* V, int c, double* D)
+{
+    double a[5], b[5];
+    ext_state(nx, bc, V, c, a);
+    ext_state(nx, bc, V, c + 1, b);
+    double uxa, uya, uza, pa, tha, uxb, uyb, uzb, pb, thb;
+    euler_prim(a, &uxa, &uya, &uza, &pa, &tha);
+    euler_prim(b, &uxb, &uyb, &uzb, &pb, &thb);
+    double mu = 0.5 * (pa + pb);  /* rho theta averaged over the face */
+    double kappa = 2.5 * mu;
+    double dux = (uxb - uxa) / dx, duy = (uyb - uya) / dx, duz = (uzb - uza) / dx, dth = (thb - tha) / dx;
+    double ux = 0.5 * (uxa + uxb), uy = 0.5 * (uya + uyb), uz = 0.5 * (uza + uzb);
+    double sxx = -eps * mu * (4.0 / 3.0) * dux, sxy = -eps * mu * duy, sxz = -eps * mu * duz;
+    double q = -eps * kappa * dth;
+    D[0] = 0.0;
+    D[1] = sxx;
+    D[2] = sxy;
+    D[3] = sxz;
+    D[4] = sxx * ux + sxy * uy + sxz * uz + q;
+}
+
 static int coarse_run_impl(int nx, double x0, double x1, int bc, double cfl, int sound,
-                           double dT, const double* E, const double* Vin, double* Vout, int* nsub)
+                           double dT, double visc, const double* E, const double* Vin, double* Vout, int* nsub)
 {
     if (nx < 1 || !(x1 > x0) || !(cfl > 0.0) || dT < 0.0) return OR_EINVAL;
     double dx = (x1 - x0) / nx;
@@ -429,7 +468,7 @@ static int coarse_run_impl(int nx, double x0, double x1, int bc, double cfl, int
     double t = 0.0;
     int steps = 0, rc = OR_OK;
     while (t < dT) {
-        double smax = 0.0;
+        double smax = 0.0, thmax = 0.0;
         for (int i = 0; i < nx; ++i) {
             double Vc[5];
             for (int q = 0; q < 5; ++q) Vc[q] = V[q * nx + i];
@@ -438,10 +477,15 @@ static int coarse_run_impl(int nx, double x0, double x1, int bc, double cfl, int
             if (!(Vc[0] > 0.0) || !(th > 0.0)) rc = OR_ENONPHYS;
             double s = wave_speed(Vc, sound);
             if (s > smax) smax = s;
+            if (th > thmax) thmax = th;
         }
         if (rc) break;
         double rem = dT - t;
         double dt = cfl * dx / smax;
+        if (visc > 0.0) {
+            double dtv = cfl * dx * dx / (2.0 * visc * (5.0 / 3.0) * thmax);
+            if (dtv < dt) dt = dtv;
+        }
         int last = 0;
         if (dt >= rem) {
             dt = rem;
@@ -451,6 +495,15 @@ static int coarse_run_impl(int nx, double x0, double x1, int bc, double cfl, int
             double Hr[5], Hl[5];
             rusanov(nx, bc, sound, V, i, Hr);
             rusanov(nx, bc, sound, V, i - 1, Hl);
+            if (visc > 0.0) {
+                double Dr[5], Dl[5];
+                viscous(nx, bc, dx, visc, V, i, Dr);
+                viscous(nx, bc, dx, visc, V, i - 1, Dl);
+                for (int q = 0; q < 5; ++q) {
+                    Hr[q] += Dr[q];
+                    Hl[q] += Dl[q];
+                }
+            }
             for (int q = 0; q < 5; ++q) W[q * nx + i] = V[q * nx + i] - dt / dx * (Hr[q] - Hl[q]);
             if (E) {
                 W[1 * nx + i] += dt * V[0 * nx + i] * E[i];
@@ -472,13 +525,86 @@ static int coarse_run_impl(int nx, double x0, double x1, int bc, double cfl, int
 int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
                   double dT, const double* Vin, double* Vout, int* nsub)
 {
-    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, NULL, Vin, Vout, nsub);
+    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, 0.0, NULL, Vin, Vout, nsub);
 }
 
 int or_coarse_run_force(int nx, double x0, double x1, int bc, double cfl, int sound,
                         double dT, const double* E, const double* Vin, double* Vout, int* nsub)
 {
-    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, E, Vin, Vout, nsub);
+    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, 0.0, E, Vin, Vout, nsub);
+}
+
+int or_coarse_run_cns(int nx, double x0, double x1, int bc, double cfl, int sound, double dT, double eps,
+                      const double* E, const double* Vin, double* Vout, int* nsub)
+{
+    if (!(eps > 0.0) || !isfinite(eps)) return OR_EINVAL;
+    return coarse_run_impl(nx, x0, x1, bc, cfl, sound, dT, eps, E, Vin, Vout, nsub);
+}
+
+/* Gradients (d u_x, d u_y, d u_z, d theta) at cell i of a primitive state
+ * [5][nx] by central differences through the ghost cells (reading R23; a
+ * reflecting ghost negates u_x). */
+void or_prim_gradients(int nx, int bc, double dx, const double* U, int i, double* d)
+{
+    double g[2][5];
+    for (int s = 0; s < 2; ++s) {
+        int c = i + (s == 0 ? -1 : 1), cc = c, flip = 0;
+        if (c < 0 || c >= nx) {
+            if (bc == OR_BC_PERIODIC) cc = ((c % nx) + nx) % nx;
+            else if (bc == OR_BC_OUTFLOW) cc = c < 0 ? 0 : nx - 1;
+            else {
+                cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
+                flip = 1;
+            }
+        }
+        for (int q = 0; q < 5; ++q) g[s][q] = U[q * nx + cc];
+        if (flip) g[s][1] = -g[s][1];
+    }
+    for (int q = 0; q < 4; ++q) d[q] = (g[1][q + 1] - g[0][q + 1]) / (2.0 * dx);
+}
+
+/* One column of the first-order lifting (reading R23): f = M (1 - eps P(c))
+ * at the nodes vx[nvx] x vp[nvp] x vp[nvp], U5 primitive, d = gradients. */
+void or_ce_column(const double* vx, int nvx, const double* vp, int nvp, const double* U5, const double* d,
+                  double eps, double* fc)
+{
+    const double pi = 3.14159265358979323846;
+    double rho = U5[0], ux = U5[1], uy = U5[2], uz = U5[3], th = U5[4];
+    double pref = rho / pow(2.0 * pi * th, 1.5);
+    for (int jx = 0; jx < nvx; ++jx)
+        for (int jy = 0; jy < nvp; ++jy)
+            for (int jz = 0; jz < nvp; ++jz) {
+                double cx = vx[jx] - ux, cy = vp[jy] - uy, cz = vp[jz] - uz;
+                double c2 = cx * cx + cy * cy + cz * cz;
+                double M = pref * exp(-c2 / (2.0 * th));
+                double P = (cx * (cx * d[0] + cy * d[1] + cz * d[2]) - c2 * d[0] / 3.0) / th +
+                           cx * (c2 / (2.0 * th) - 2.5) * d[3] / th;
+                fc[((long)jx * nvp + jy) * nvp + jz] = M * (1.0 - eps * P);
+            }
+}
+
+/* First-order lifting L^(1) (Def. 3, reading R23) on the isotropic grid. */
+int or_lift_ce(const or_kin* k, const double* U, double* f)
+{
+    int rc = check_kin(k);
+    if (rc) return rc;
+    if (!isfinite(k->eps)) return OR_EINVAL;
+    int nx = k->nx, nv = k->nv;
+    long nv3 = (long)nv * nv * nv;
+    double dx = (k->x1 - k->x0) / nx;
+    double* v = malloc(sizeof(double) * nv);
+    if (!v) return OR_ENOMEM;
+    or_velocity_nodes(nv, k->L, v);
+    int bad = 0;
+    for (int i = 0; i < nx; ++i) {
+        double U5[5], d[4];
+        for (int q = 0; q < 5; ++q) U5[q] = U[q * nx + i];
+        if (!(U5[0] > 0.0) || !(U5[4] > 0.0)) bad = 1;
+        or_prim_gradients(nx, k->bc, dx, U, i, d);
+        or_ce_column(v, nv, v, nv, U5, d, k->eps, f + (long)i * nv3);
+    }
+    free(v);
+    return bad ? OR_ENONPHYS : OR_OK;
 }
 
 /* ---------------- propagators and the parareal algorithms ---------------- */
@@ -499,7 +625,7 @@ int or_fine_propagate(const or_pr* p, const double* Vin, double* Vout)
         return OR_ENOMEM;
     }
     int rc = or_cons_to_prim(nx, Vin, U);
-    if (!rc) rc = or_lift(k, U, f);
+    if (!rc) rc = p->lift == 1 ? or_lift_ce(k, U, f) : or_lift(k, U, f);
     if (!rc) rc = or_fine_run(k, dt, nf, f);
     if (!rc) rc = or_project_cons(k, f, Vout);
     free(U);
@@ -510,6 +636,9 @@ int or_fine_propagate(const or_pr* p, const double* Vin, double* Vout)
 int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout)
 {
     const or_kin* k = &p->kin;
+    if (p->coarse == OR_COARSE_CNS)
+        return or_coarse_run_cns(k->nx, k->x0, k->x1, k->bc, p->cfl_g, p->sound, p->T / p->N, k->eps, NULL, Vin,
+                                 Vout, 0);
     return or_coarse_run(k->nx, k->x0, k->x1, k->bc, p->cfl_g, p->sound, p->T / p->N, Vin, Vout, 0);
 }
 

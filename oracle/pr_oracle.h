@@ -33,6 +33,9 @@ extern "C" {
 #define OR_SOUND_GAMMA53 0
 #define OR_SOUND_SQRT_THETA 1
 
+#define OR_COARSE_EULER 0  /* Eqs. (14)-(16)                                   */
+#define OR_COARSE_CNS 1    /* Eq. (8), viscous terms of reading R22            */
+
 typedef struct {
     int nx;        /* x cells on [x0, x1]                                  */
     double x0, x1;
@@ -51,6 +54,8 @@ typedef struct {
     double cfl_g;  /* coarse CFL (Rusanov)                                 */
     int sound;     /* OR_SOUND_*                                           */
     int nf;        /* fine steps per slice; <= 0: derived from cfl_f       */
+    int coarse;    /* OR_COARSE_EULER or OR_COARSE_CNS                     */
+    int lift;      /* lifting order: 0 (Def. 2) or 1 (Def. 3, L = 1)       */
 } or_pr;
 
 void or_set_threads(int n);
@@ -71,6 +76,15 @@ int or_fine_run(const or_kin* k, double dt, int nsteps, double* f);
 
 int or_coarse_run(int nx, double x0, double x1, int bc, double cfl, int sound,
                   double dT, const double* Vin, double* Vout, int* nsub);
+/* The compressible Navier-Stokes coarse model of Eq. (8) (reading R22) with
+ * Knudsen number eps > 0 and an optional exterior force E [nx]. */
+int or_coarse_run_cns(int nx, double x0, double x1, int bc, double cfl, int sound, double dT, double eps,
+                      const double* E, const double* Vin, double* Vout, int* nsub);
+/* First-order lifting L^(1) of Def. 3 (reading R23). */
+int or_lift_ce(const or_kin* k, const double* U, double* f);
+void or_prim_gradients(int nx, int bc, double dx, const double* U, int i, double* d);
+void or_ce_column(const double* vx, int nvx, const double* vp, int nvp, const double* U5, const double* d,
+                  double eps, double* fc);
 
 int or_fine_propagate(const or_pr* p, const double* Vin, double* Vout);
 int or_coarse_propagate(const or_pr* p, const double* Vin, double* Vout);
@@ -110,11 +124,14 @@ typedef struct {
     double cfl_f, cfl_g;
     int sound;
     int nf;
+    int coarse;       /* OR_COARSE_EULER or OR_COARSE_CNS                   */
+    int lift;         /* lifting order 0 or 1                               */
 } or_vpr;
 
 int or_coarse_run_force(int nx, double x0, double x1, int bc, double cfl, int sound,
                         double dT, const double* E, const double* Vin, double* Vout, int* nsub);
 int or_v_lift(const or_vkin* k, const double* U, double* f);
+int or_v_lift_ce(const or_vkin* k, const double* U, double* f);
 int or_v_project(const or_vkin* k, const double* f, double* U);
 int or_v_project_cons(const or_vkin* k, const double* f, double* V);
 double or_v_fine_dt_stab(const or_vkin* k, double cfl);

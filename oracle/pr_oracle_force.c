@@ -105,6 +105,37 @@ int or_v_lift(const or_vkin* k, const double* U, double* f)
     return bad ? OR_ENONPHYS : OR_OK;
 }
 
+/* First-order lifting L^(1) (Def. 3, reading R23 of pr_oracle.c) on the
+ * anisotropic grid; the force does not enter g1. */
+int or_v_lift_ce(const or_vkin* k, const double* U, double* f)
+{
+    int rc = check_vkin(k);
+    if (rc) return rc;
+    if (!isfinite(k->eps)) return OR_EINVAL;
+    int nx = k->nx;
+    long nc = ncol(k);
+    double dx = (k->x1 - k->x0) / nx;
+    double* vx = malloc(sizeof(double) * k->nvx);
+    double* vp = malloc(sizeof(double) * k->nvp);
+    if (!vx || !vp) {
+        free(vx);
+        free(vp);
+        return OR_ENOMEM;
+    }
+    nodes(k, vx, vp);
+    int bad = 0;
+    for (int i = 0; i < nx; ++i) {
+        double U5[5], d[4];
+        for (int q = 0; q < 5; ++q) U5[q] = U[q * nx + i];
+        if (!(U5[0] > 0.0) || !(U5[4] > 0.0)) bad = 1;
+        or_prim_gradients(nx, k->bc, dx, U, i, d);
+        or_ce_column(vx, k->nvx, vp, k->nvp, U5, d, k->eps, f + (long)i * nc);
+    }
+    free(vx);
+    free(vp);
+    return bad ? OR_ENONPHYS : OR_OK;
+}
+
 /* Moments of one column by the quadrature of Eq. (18) (u first, then theta). */
 static void vcolumn_moments(const or_vkin* k, const double* vx, const double* vp, double dv3, const double* fc,
                             double* rho, double* u, double* th)
@@ -351,7 +382,7 @@ int or_v_fine_propagate(const or_vpr* p, const double* Vin, double* Vout)
         return OR_ENOMEM;
     }
     int rc = or_cons_to_prim(nx, Vin, U);
-    if (!rc) rc = or_v_lift(k, U, f);
+    if (!rc) rc = p->lift == 1 ? or_v_lift_ce(k, U, f) : or_v_lift(k, U, f);
     if (!rc) rc = or_v_fine_run(k, dt, nf, f);
     if (!rc) rc = or_v_project_cons(k, f, Vout);
     free(U);
@@ -363,6 +394,9 @@ int or_v_fine_propagate(const or_vpr* p, const double* Vin, double* Vout)
 int or_v_coarse_propagate(const or_vpr* p, const double* Vin, double* Vout)
 {
     const or_vkin* k = &p->kin;
+    if (p->coarse == OR_COARSE_CNS)
+        return or_coarse_run_cns(k->nx, k->x0, k->x1, k->bc, p->cfl_g, p->sound, p->T / p->N, k->eps, k->E, Vin,
+                                 Vout, 0);
     return or_coarse_run_force(k->nx, k->x0, k->x1, k->bc, p->cfl_g, p->sound, p->T / p->N, k->E, Vin, Vout, 0);
 }
 
