@@ -67,6 +67,14 @@ extern "C" {
 #define PR_PRIMITIVE 0
 #define PR_CONSERVED 1
 
+#define PR_COARSE_EULER 0      /* Euler system, Eqs. (14)-(16)                 */
+#define PR_COARSE_CNS 1        /* compressible Navier-Stokes, Eq. (8): the Euler
+                                  scheme plus viscous fluxes with mu = rho theta,
+                                  kappa = 5 rho theta / 2 (first-order
+                                  Chapman-Enskog coefficients of BGK, tau = 1),
+                                  central face gradients, local steps also
+                                  limited by dx^2 / (2 eps (5/3) max theta)    */
+
 /* ---- parameter blocks ---- */
 typedef struct {
     int nx;            /* x cells (>= 1)                                       */
@@ -90,6 +98,11 @@ typedef struct {
     int max_batch;     /* slices whose fine states are resident at once;
                           0 = all N (the fine phase runs in waves otherwise)  */
     int nf;            /* fine steps per slice; 0 = ceil(dT_g / dt_stab)       */
+    int coarse_model;  /* PR_COARSE_EULER (0) or PR_COARSE_CNS                 */
+    int lift_order;    /* 0: Maxwellian lifting (Def. 2); 1: first-order
+                          lifting L^(1) of Def. 3, f = M (1 - eps P(c)) with the
+                          Chapman-Enskog term of BGK, gradients of u and theta
+                          by central differences through the ghosts           */
 } pr_time;
 
 /* One fine-solve instance of a batch (independent problem). */
@@ -226,6 +239,12 @@ int pr_batch_inject_wait_timeout(pr_batch* b, int nsteps, int wait_ms);
 /* Wait for the batch stream and report any device-side error. */
 int pr_batch_sync(pr_batch* b);
 
+/* Lifting order of the batch's later lifts (pr_batch_set_initial*): 0
+ * (Maxwellian, Eq. 17) or 1 (first-order, Def. 3; every instance needs a
+ * finite eps).  The first-order lift writes f as a general state (one extra
+ * pass instead of the lift fused into the first step).  Errors: PR_EINVAL. */
+int pr_batch_set_lift_order(pr_batch* b, int order);
+
 /* Tile width (x cells per work item) used for instance i, and whether it came
  * from the autotuner (1) or the default (0). */
 int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned);
@@ -358,6 +377,10 @@ int pr_force_get_f(pr_force* b, int i, double* out);
 
 /* Wait for the object's stream and report any device-side error. */
 int pr_force_sync(pr_force* b);
+
+/* Lifting order of later pr_force_set_initial calls (0 or 1, as
+ * pr_batch_set_lift_order).  Errors: PR_EINVAL. */
+int pr_force_set_lift_order(pr_force* b, int order);
 
 /* CTAs per x column (the cluster size) and velocities per CTA (v_x rows per
  * CTA times nvp^2) in use. */

@@ -30,6 +30,7 @@ PR_UPWIND, PR_MUSCL = 0, 1
 PR_FP64, PR_MIXED = 0, 1
 PR_SOUND_GAMMA53, PR_SOUND_SQRT_THETA = 0, 1
 PR_PRIMITIVE, PR_CONSERVED = 0, 1
+PR_COARSE_EULER, PR_COARSE_CNS = 0, 1
 
 _CODES = {PR_EINVAL: "PR_EINVAL", PR_ENOMEM: "PR_ENOMEM", PR_ECUDA: "PR_ECUDA", PR_ETIMEOUT: "PR_ETIMEOUT",
           PR_ENONPHYS: "PR_ENONPHYS", PR_ENOTCONV: "PR_ENOTCONV"}
@@ -52,7 +53,7 @@ class pr_velocity(C.Structure):
 class pr_time(C.Structure):
     _fields_ = [("T", C.c_double), ("n_slices", C.c_int), ("cfl_f", C.c_double), ("cfl_g", C.c_double),
                 ("scheme", C.c_int), ("precision", C.c_int), ("sound_speed", C.c_int), ("max_batch", C.c_int),
-                ("nf", C.c_int)]
+                ("nf", C.c_int), ("coarse_model", C.c_int), ("lift_order", C.c_int)]
 
 
 class pr_instance(C.Structure):
@@ -97,6 +98,8 @@ _SIGS = {
     "pr_batch_moments_device": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "pr_batch_get_f": (C.c_int, [_VP, C.c_int, _D]),
     "pr_batch_sync": (C.c_int, [_VP]),
+    "pr_batch_set_lift_order": (C.c_int, [_VP, C.c_int]),
+    "pr_force_set_lift_order": (C.c_int, [_VP, C.c_int]),
     "pr_batch_inject_wait_timeout": (C.c_int, [_VP, C.c_int, C.c_int]),
     "pr_batch_tile": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pr_batch_autotune": (C.c_int, [_VP]),
@@ -202,10 +205,11 @@ def _batch_check(b, rc):
 # ---------------------------------------------------------------- parareal
 
 def pr_init(nx, x0, x1, bc, nv, L, eps, T, n_slices, cfl_f=0.5, cfl_g=0.5, scheme=PR_UPWIND,
-            precision=PR_FP64, sound_speed=PR_SOUND_GAMMA53, max_batch=0, nf=0):
+            precision=PR_FP64, sound_speed=PR_SOUND_GAMMA53, max_batch=0, nf=0, coarse_model=PR_COARSE_EULER,
+            lift_order=0):
     g = pr_grid(nx, x0, x1, bc)
     v = pr_velocity(nv, L)
-    t = pr_time(T, n_slices, cfl_f, cfl_g, scheme, precision, sound_speed, max_batch, nf)
+    t = pr_time(T, n_slices, cfl_f, cfl_g, scheme, precision, sound_speed, max_batch, nf, coarse_model, lift_order)
     out = _VP()
     rc = lib().pr_init(C.byref(out), C.byref(g), C.byref(v), float(eps), C.byref(t))
     if rc != PR_OK:
@@ -358,6 +362,10 @@ def pr_batch_sync(b):
     _batch_check(b, lib().pr_batch_sync(b.ptr))
 
 
+def pr_batch_set_lift_order(b, order):
+    _batch_check(b, lib().pr_batch_set_lift_order(b.ptr, int(order)))
+
+
 def pr_batch_tile(b, i):
     tx, tuned = C.c_int(), C.c_int()
     _batch_check(b, lib().pr_batch_tile(b.ptr, int(i), C.byref(tx), C.byref(tuned)))
@@ -479,6 +487,10 @@ def pr_force_sync(b):
     _force_check(b, lib().pr_force_sync(b.ptr))
 
 
+def pr_force_set_lift_order(b, order):
+    _force_check(b, lib().pr_force_set_lift_order(b.ptr, int(order)))
+
+
 def pr_force_config(b):
     c, k = C.c_int(), C.c_int()
     _force_check(b, lib().pr_force_config(b.ptr, C.byref(c), C.byref(k)))
@@ -511,11 +523,12 @@ def pr_force_dt_stab(inst: ForceInstance, cfl=0.5) -> float:
 
 
 def pr_init_force(nx, x0, x1, bc, nvx, nvp, L, eps, T, n_slices, E, cfl_f=0.5, cfl_g=0.5, scheme=PR_UPWIND,
-                  precision=PR_FP64, sound_speed=PR_SOUND_GAMMA53, max_batch=0, nf=0):
+                  precision=PR_FP64, sound_speed=PR_SOUND_GAMMA53, max_batch=0, nf=0, coarse_model=PR_COARSE_EULER,
+                  lift_order=0):
     """Parareal problem with the exterior force E [nx] (host, copied)."""
     g = pr_grid(nx, x0, x1, bc)
     v = pr_velocity(nvp, L)
-    t = pr_time(T, n_slices, cfl_f, cfl_g, scheme, precision, sound_speed, max_batch, nf)
+    t = pr_time(T, n_slices, cfl_f, cfl_g, scheme, precision, sound_speed, max_batch, nf, coarse_model, lift_order)
     Ea = None if E is None else _f64(E, (nx,))
     out = _VP()
     rc = lib().pr_init_force(C.byref(out), C.byref(g), C.byref(v), float(eps), C.byref(t), int(nvx),

@@ -26,6 +26,7 @@ UNITS = {
     "adjoint.cu": [],
     "force.cu": [],
     "force_runtime.cu": [],
+    "lift_ce.cu": [],
 }
 
 

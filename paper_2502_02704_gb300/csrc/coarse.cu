@@ -9,7 +9,10 @@
 //   the coarse interval is covered (Sec. 2.2).  Ghost cells: periodic wrap,
 //   outflow copy, reflecting mirror with rho u_x negated.
 // With an exterior force E (Eq. 5) each local step adds dt (0, rho E_i, 0, 0,
-// rho u_x E_i) evaluated on the state before the step.
+// rho u_x E_i) evaluated on the state before the step.  With visc = eps > 0
+// the model is the compressible Navier-Stokes system of Eq. (8): viscous
+// fluxes with mu = rho theta and kappa = 5 rho theta / 2 added to the Rusanov
+// flux, local steps also limited by dx^2 / (2 eps (5/3) max theta).
 // Sweep: Algorithm 2's sequential loop U^{n,k} = G(U^{n-1,k}) + jump^n for
 // n = k..N, with jump^n = PFL(U^{n-1,k-1}) - G(U^{n-1,k-1}) formed from the
 // stored G results of the previous sweep, and the Eq. (10) error
@@ -93,6 +96,28 @@ __device__ void rusanov(const double* V, int nx, int bc, int sound, int c, doubl
     for (int q = 0; q < 5; ++q) H[q] = 0.5 * (ha[q] + hb[q]) - 0.5 * S * (b[q] - a[q]);
 }
 
+// Viscous flux D_{c+1/2} of the compressible Navier-Stokes model (Eq. 8):
+// mu = rho theta, kappa = 5 rho theta / 2 (BGK, tau = 1), gradients
+// (V_{c+1} - V_c)/dx, coefficients and u averaged over the face.
+__device__ void viscous(const double* V, int nx, int bc, double dx, double eps, int c, double* D)
+{
+    double a[5], b[5];
+    cell(V, nx, bc, c, a);
+    cell(V, nx, bc, c + 1, b);
+    Prim pa = prim(a), pb = prim(b);
+    double mu = 0.5 * (pa.p + pb.p);
+    double kappa = 2.5 * mu;
+    double dux = (pb.ux - pa.ux) / dx, duy = (pb.uy - pa.uy) / dx, duz = (pb.uz - pa.uz) / dx, dth = (pb.th - pa.th) / dx;
+    double ux = 0.5 * (pa.ux + pb.ux), uy = 0.5 * (pa.uy + pb.uy), uz = 0.5 * (pa.uz + pb.uz);
+    double sxx = -eps * mu * (4.0 / 3.0) * dux, sxy = -eps * mu * duy, sxz = -eps * mu * duz;
+    double q = -eps * kappa * dth;
+    D[0] = 0.0;
+    D[1] = sxx;
+    D[2] = sxy;
+    D[3] = sxz;
+    D[4] = sxx * ux + sxy * uy + sxz * uz + q;
+}
+
 __device__ double block_max(double v, double* sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -112,7 +137,7 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT,
     const int nx = p.nx;
     double t = 0.0;
     while (t < dT) {
-        double smax = 0.0;
+        double smax = 0.0, thmax = 0.0;
         bool bad = false;
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             double v[5];
@@ -122,12 +147,18 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT,
             if (!(v[0] > 0.0) || !(pr.th > 0.0)) bad = true;
             double s = speed(v, p.sound);
             if (s > smax) smax = s;
+            if (pr.th > thmax) thmax = pr.th;
         }
         if (bad) atomicCAS(status, 0, ST_NONPHYS);
         smax = block_max(smax, sh);
         if (!(smax > 0.0) || isnan(smax)) return;
         double rem = dT - t;
         double dt = p.cfl * p.dx / smax;
+        if (p.visc > 0.0) {
+            thmax = block_max(thmax, sh);
+            double dtv = p.cfl * p.dx * p.dx / (2.0 * p.visc * (5.0 / 3.0) * thmax);
+            if (dtv < dt) dt = dtv;
+        }
         bool last = false;
         if (dt >= rem) {
             dt = rem;
@@ -137,6 +168,16 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT,
             double Hr[5], Hl[5];
             rusanov(A, nx, p.bc, p.sound, i, Hr);
             rusanov(A, nx, p.bc, p.sound, i - 1, Hl);
+            if (p.visc > 0.0) {  // compressible Navier-Stokes (Eq. 8)
+                double Dr[5], Dl[5];
+                viscous(A, nx, p.bc, p.dx, p.visc, i, Dr);
+                viscous(A, nx, p.bc, p.dx, p.visc, i - 1, Dl);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    Hr[q] += Dr[q];
+                    Hl[q] += Dl[q];
+                }
+            }
 #pragma unroll
             for (int q = 0; q < 5; ++q) B[q * nx + i] = A[q * nx + i] - dt / p.dx * (Hr[q] - Hl[q]);
             if (p.E) {  // exterior force: forward-Euler source on the old state

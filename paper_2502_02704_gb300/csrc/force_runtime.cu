@@ -390,7 +390,9 @@ int enqueue_lift_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bo
     if (b1 <= b0) return PR_OK;
     FCUDA(b, set_active(b, b0, b1, s));
     const int p = b->precision == PR_FP64 ? 0 : 1;
-    FCUDA(b, prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s));
+    FCUDA(b, b->lift_order == 1
+                 ? prk::launch_force_lift_ce(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s)
+                 : prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s));
     pr_internal_count_launches(1);
     int rc = PR_OK;
     if (nsteps > 0) {
@@ -407,7 +409,10 @@ cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cu
 {
     const int p = b->precision == PR_FP64 ? 0 : 1;
     cudaError_t e = prk::launch_set_active(dk, b->d_active, 1, b->n, N, s);
-    if (e == cudaSuccess) e = prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s);
+    if (e == cudaSuccess)
+        e = b->lift_order == 1
+                ? prk::launch_force_lift_ce(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s)
+                : prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s);
     for (int k = 0; e == cudaSuccess && k < nsteps; ++k)
         e = prk::launch_force_step(p, b->scheme, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, k,
                                    k == nsteps - 1, b->d_status, b->smem, s);
@@ -554,6 +559,17 @@ int pr_force_sync(pr_force* b)
 {
     if (!b) return PR_EINVAL;
     return prf::take_status(b);
+}
+
+int pr_force_set_lift_order(pr_force* b, int order)
+{
+    if (!b) return PR_EINVAL;
+    if (order != 0 && order != 1) return ffail(b, PR_EINVAL, "lift order must be 0 or 1");
+    if (order == 1)
+        for (const prk::FInst& I : b->h)
+            if (!I.collide) return ffail(b, PR_EINVAL, "the first-order lift needs a finite eps");
+    b->lift_order = order;
+    return PR_OK;
 }
 
 int pr_force_config(const pr_force* b, int* cluster, int* chunk)

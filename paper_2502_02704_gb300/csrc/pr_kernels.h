@@ -157,11 +157,22 @@ cudaError_t launch_force_store(int precision, const FInst* insts, int b, const i
 cudaError_t launch_force_advance(const Active* act, int* cur, int nsteps, int n_inst, cudaStream_t s);
 cudaError_t launch_force_set_cur(int* cur, int b, int v, cudaStream_t s);
 
+// ---- first-order (Chapman-Enskog) lifting, Def. 3 with L = 1 (lift_ce.cu) ----
+// E = 0 path: g[cur] = M (1 - eps P(c)) from Uin, tab[cur] = 0, a0 = 1 for
+// the active instances (grid over nx_max cells); with_moments also writes
+// P(f) into Ucur.
+cudaError_t launch_lift_ce(int precision, const Inst* insts, InstState* st, const Active* active, int nx_max,
+                           int n_inst_max, int with_moments, int* status, cudaStream_t s);
+// Force path: f[0] of the active instances, cur <- 0.
+cudaError_t launch_force_lift_ce(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                                 const Active* act, int* cur, int* status, cudaStream_t s);
+
 // ---- coarse propagator and parareal sweep (coarse.cu) ----
 struct CoarseParams {
     int nx, bc, sound;
     double x0, x1, dx, cfl;
     const double* E = nullptr; // exterior force [nx] (device) or null: source (0, rho E, 0, 0, rho u_x E)
+    double visc = 0.0;         // Knudsen number of the Navier-Stokes model (Eq. 8); 0: Euler
 };
 
 // G over dT for one state (Vin/Vout device [5][nx], may alias).

@@ -126,6 +126,8 @@ struct pr_batch {
     int grid = 0;
     size_t smem = 0, lift_smem = 0;
     int max_tiles = 1;
+    int nx_max = 1;
+    int lift_order = 0;  // 0: Maxwellian lift fused into the first step; 1: first-order lift (lift_ce.cu)
     std::string err;
     // kernel timing
     bool timing = false;
@@ -185,6 +187,7 @@ static int layout_tiles(pr_batch* b, const std::vector<int>& txs, std::vector<lo
         I.tx = txs[i];
         I.n_xt = (I.nx + I.tx - 1) / I.tx;
         b->max_tiles = std::max(b->max_tiles, I.n_xt);
+        b->nx_max = std::max(b->nx_max, I.nx);
         std::vector<int> deps;
         if (!build_deps(I.nx, I.tx, I.bc, b->H, deps))
             return bfail(b, PR_EINVAL, "instance %d: tile dependencies exceed %d", i, prk::MAXDEP);
@@ -484,9 +487,15 @@ static int lift_instances(pr_batch* b, int begin, int end, cudaStream_t s)
 {
     prk::Active a{begin, end};
     BCUDA(b, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
-    BCUDA(b, prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->max_tiles,
-                              end - begin, b->lift_smem, b->d_status, s));
-    g_launches += 1;
+    if (b->lift_order == 1) {
+        BCUDA(b, prk::launch_lift_ce(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->nx_max,
+                                     end - begin, 1, b->d_status, s));
+        g_launches += 2;
+    } else {
+        BCUDA(b, prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->max_tiles,
+                                  end - begin, b->lift_smem, b->d_status, s));
+        g_launches += 1;
+    }
     prk::Active all{0, b->n};
     BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
     return PR_OK;
@@ -591,6 +600,17 @@ int pr_batch_inject_wait_timeout(pr_batch* b, int nsteps, int wait_ms)
     int rc = enqueue_run(b, nsteps, 0, b->stream, false, (long long)wait_ms * 1000000LL, 1);
     if (rc) return rc;
     return take_status(b, b->stream);
+}
+
+int pr_batch_set_lift_order(pr_batch* b, int order)
+{
+    if (!b) return PR_EINVAL;
+    if (order != 0 && order != 1) return bfail(b, PR_EINVAL, "lift order must be 0 or 1");
+    if (order == 1)
+        for (const pr_instance& d : b->desc)
+            if (!std::isfinite(d.eps)) return bfail(b, PR_EINVAL, "the first-order lift needs a finite eps");
+    b->lift_order = order;
+    return PR_OK;
 }
 
 int pr_batch_sync(pr_batch* b)
@@ -973,6 +993,11 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
     if (t->sound_speed != PR_SOUND_GAMMA53 && t->sound_speed != PR_SOUND_SQRT_THETA)
         return init_fail(PR_EINVAL, "bad sound speed");
     if (t->nf < 0 || t->max_batch < 0) return init_fail(PR_EINVAL, "nf and max_batch must be >= 0");
+    if (t->coarse_model != PR_COARSE_EULER && t->coarse_model != PR_COARSE_CNS)
+        return init_fail(PR_EINVAL, "bad coarse model");
+    if (t->lift_order != 0 && t->lift_order != 1) return init_fail(PR_EINVAL, "lift order must be 0 or 1");
+    if ((t->coarse_model == PR_COARSE_CNS || t->lift_order == 1) && !(std::isfinite(eps) && eps > 0))
+        return init_fail(PR_EINVAL, "the Navier-Stokes model and the first-order lift need a finite eps > 0");
     pr_ctx* c = new pr_ctx();
     c->g = *g;
     c->v = *v;
@@ -1040,6 +1065,9 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
     c->cp.dx = dx;
     c->cp.cfl = t->cfl_g;
     c->cp.E = force ? c->ff->d_E : nullptr;
+    c->cp.visc = t->coarse_model == PR_COARSE_CNS ? eps : 0.0;
+    if (force) c->ff->lift_order = t->lift_order;
+    else c->fine->lift_order = t->lift_order;
     c->live.assign(c->n_res, 0);
     for (int b = 0; b < c->n_res; ++b) bind_slice(c, b, b + 1);
     cudaError_t ue = force ? prf::upload(c->ff, 0, c->n_res, c->ff->stream)
@@ -1290,8 +1318,11 @@ static int build_graph(pr_ctx* c)
     CCUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = prk::launch_set_active(c->dk, b->d_active, 1, c->n_res, c->N, s);
     if (e == cudaSuccess)
-        e = prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->max_tiles, b->n,
-                             b->lift_smem, b->d_status, s);
+        e = b->lift_order == 1
+                ? prk::launch_lift_ce(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->nx_max,
+                                      b->n, 0, b->d_status, s)
+                : prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->max_tiles,
+                                   b->n, b->lift_smem, b->d_status, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, b->sync_bytes, s);
     if (e == cudaSuccess)
         e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state, b->d_prefix,
