@@ -347,6 +347,42 @@ def _moment_rel_err(np, V, Vref):
     return float(max(np.max(np.abs(V[q] - Vref[q])) / sc[q] for q in range(5)))
 
 
+def _coarse_models_section(pr, np, torch):
+    """The higher-order coupling of Eq. 8 / Def. 3: Algorithm 2 on the smooth
+    periodic profile (Nx = 256, 24^3 on [-8, 8]^3, eps = 1e-2, MUSCL, T = 0.1,
+    N = 16 slices, FP64) with the Euler or Navier-Stokes coarse model and the
+    Maxwellian or first-order lifting; the error of U^{n,K} against the K = N
+    result (the serial fine chain of the same lifting), max over slices."""
+    from paper_2502_02704_gb300 import workloads as W
+
+    nx, nv, L, eps, T, N = 256, 24, 8.0, 1e-2, 0.1, 16
+    U0 = W.smooth_periodic(nx)
+    out = {"workload": "smooth periodic Nx=256, 24^3, eps=1e-2, MUSCL, T=0.1, N=16, FP64", "runs": []}
+    for coarse, lift in ((pr.PR_COARSE_EULER, 0), (pr.PR_COARSE_CNS, 0), (pr.PR_COARSE_EULER, 1),
+                         (pr.PR_COARSE_CNS, 1)):
+        ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_PERIODIC, nv, L, eps, T, N, scheme=pr.PR_MUSCL,
+                         precision=pr.PR_FP64, coarse_model=coarse, lift_order=lift)
+        try:
+            pr.pr_set_initial(ctx, U0)
+            pr.pr_parareal_run(ctx, N)
+            ref = [pr.pr_moments(ctx, n) for n in range(N + 1)]
+            errs, times = [], []
+            for K in range(0, 7):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                pr.pr_set_initial(ctx, U0)
+                if K:
+                    pr.pr_parareal_run(ctx, K)
+                U = [pr.pr_moments(ctx, n) for n in range(N + 1)]
+                times.append((time.perf_counter() - t0) * 1e3)
+                errs.append(max(_moment_rel_err(np, U[n], ref[n]) for n in range(1, N + 1)))
+        finally:
+            pr.pr_destroy(ctx)
+        out["runs"].append({"coarse": "cns" if coarse == pr.PR_COARSE_CNS else "euler", "lift_order": lift,
+                            "err_vs_fine_chain_K0_6": errs, "ms_K0_6": times})
+    return out
+
+
 def _test3_section(pr, np, torch):
     """Test 3 (exterior force, Sec. 5.3): 100 x 256 x 16 x 16 cells on [0, 2] x
     [-8, 8]^3, periodic, eps = 1e-5, two beams, E(x) = -5 x^4 (x-2)^4 (x-1),
@@ -565,7 +601,7 @@ def run_ours(args):
         para = _parareal_speedup(pr, np)
     except Exception as e:  # reported, not hidden
         para = {"error": repr(e)}
-    ragged = large = test3 = None
+    ragged = large = test3 = higher = None
     try:
         ragged = _ragged_section(pr, torch)
     except Exception as e:
@@ -575,6 +611,10 @@ def run_ours(args):
             test3 = _test3_section(pr, np, torch)
         except Exception as e:
             test3 = {"error": repr(e)}
+    try:
+        higher = _coarse_models_section(pr, np, torch)
+    except Exception as e:
+        higher = {"error": repr(e)}
     if not args.no_large:
         try:
             large = _large_section(pr, np, torch)
@@ -603,6 +643,7 @@ def run_ours(args):
         "ragged_batch": ragged,
         "parareal_large": large,
         "test3_force": test3,
+        "coarse_models": higher,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
