@@ -192,15 +192,14 @@ def _time_device(pr, torch, b, Vdev, outs, steps, warmup, stream):
     return ms / steps, kms, pr.pr_kernel_launches() - n0
 
 
-def _parareal_speedup(pr, np):
-    """Sod setup (Nx=64, 16^3, eps=1e-2, outflow, upwind, T=0.1, N=8): plain FP64
-    single-instance serial fine chain U^n = P F L(U^{n-1}) vs mixed-precision
-    batched parareal (Algorithm 2) for several K, with the error of each against
-    the FP64 serial chain."""
+def _parareal_speedup(pr, np, nx=64, nv=16, N=8, T=0.1, Ks=(1, 2, 3, 4, 8)):
+    """Sod setup (eps=1e-2, outflow, upwind on [-8, 8]^3; by default Nx=64,
+    16^3, T=0.1, N=8): plain FP64 single-instance serial fine chain
+    U^n = P F L(U^{n-1}) vs mixed-precision batched parareal (Algorithm 2) for
+    several K, with the error of each against the FP64 serial chain."""
     import torch
     from paper_2502_02704_gb300 import workloads as W
 
-    nx, nv, N, T = 64, 16, 8, 0.1
     U0 = W.sod(nx)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
@@ -232,14 +231,15 @@ def _parareal_speedup(pr, np):
         pr.pr_batch_sync(one)
         ref = chain.cpu().numpy()
         rows = []
-        for K in (1, 2, 3, 4, 8):
+        for K in Ks:
             parareal(K)
             t0 = time.perf_counter()
             got = parareal(K)
             t = time.perf_counter() - t0
             err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
             rows.append({"K": K, "ms": t * 1e3, "max_rel_err_vs_fp64_serial": err, "speedup": t_ser / t})
-        return {"workload": "Sod Nx=64, 16^3, eps=1e-2, outflow, upwind, T=0.1, N=8, 12 fine steps/slice",
+        return {"workload": f"Sod Nx={nx}, {nv}^3, eps=1e-2, outflow, upwind, T={T}, N={N}, "
+                            f"{nf} fine steps/slice",
                 "serial_fp64_ms": t_ser * 1e3, "parareal_mixed": rows,
                 "timing": "wall clock around synchronous calls, includes pr_set_initial (first coarse guess)"}
     finally:
@@ -596,11 +596,15 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         rate, cores, sample = _cpu_sample()
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-    para = None
+    para = para64 = None
     try:
         para = _parareal_speedup(pr, np)
     except Exception as e:  # reported, not hidden
         para = {"error": repr(e)}
+    try:  # the batched parareal configuration: 64 slices resident in one persistent launch
+        para64 = _parareal_speedup(pr, np, nx=256, nv=24, N=64, T=0.1, Ks=(1, 2, 3, 4, 5))
+    except Exception as e:
+        para64 = {"error": repr(e)}
     ragged = large = test3 = higher = None
     try:
         ragged = _ragged_section(pr, torch)
@@ -640,6 +644,7 @@ def run_ours(args):
                                           "achieved": None, "frac": None,
                                           "peak_source": "measured DFMA microbenchmark on this pool's GB300"}},
         "parareal": para,
+        "parareal_batched_n64": para64,
         "ragged_batch": ragged,
         "parareal_large": large,
         "test3_force": test3,
