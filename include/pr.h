@@ -390,6 +390,13 @@ int pr_force_config(const pr_force* b, int* cluster, int* chunk);
  * PR_EINVAL otherwise (the previous setting stays).  Synchronous. */
 int pr_force_set_cluster(pr_force* b, int cluster);
 
+/* Cap the threads of the step kernel's CTAs (32..1024, a multiple of 32;
+ * default 256): fewer threads per CTA means fewer row groups and more CTAs
+ * resident per SM.  A column row always gets its nvp^2 / vec threads.
+ * Applies to the current cluster size; PR_EINVAL when no layout fits.
+ * Synchronous. */
+int pr_force_set_threads(pr_force* b, int threads);
+
 /* Average duration in ms of one step launch over the runs since the last
  * reset (CUDA events on the launching stream around each run, divided by its
  * steps); reset = 1 clears the accumulator. */

@@ -119,6 +119,7 @@ _SIGS = {
     "pr_force_sync": (C.c_int, [_VP]),
     "pr_force_config": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pr_force_set_cluster": (C.c_int, [_VP, C.c_int]),
+    "pr_force_set_threads": (C.c_int, [_VP, C.c_int]),
     "pr_force_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_force_dt_stab": (C.c_int, [C.POINTER(pr_force_instance), C.c_double, _D]),
     "pr_force_inject_wait_timeout": (C.c_int, [_VP, C.c_int]),
@@ -499,6 +500,10 @@ def pr_force_config(b):
 
 def pr_force_set_cluster(b, cluster):
     _force_check(b, lib().pr_force_set_cluster(b.ptr, int(cluster)))
+
+
+def pr_force_set_threads(b, threads):
+    _force_check(b, lib().pr_force_set_threads(b.ptr, int(threads)))
 
 
 def pr_force_kernel_time(b, reset=False):

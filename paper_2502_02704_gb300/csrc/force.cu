@@ -820,12 +820,12 @@ size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows)
     return force_step_buf_off(precision, nvx, nvp) + nbuf * nvp * nvp * es;
 }
 
-// Row groups and threads for VEC values per thread: at most 256 threads,
-// a multiple of 32.
-void force_step_layout(int nvp, int vec, int rows, int* groups, int* threads)
+// Row groups and threads for VEC values per thread: at most max_threads
+// threads (at least one row of threads), a multiple of 32.
+void force_step_layout(int nvp, int vec, int rows, int max_threads, int* groups, int* threads)
 {
     const int Lr = nvp * nvp / vec;
-    int G = std::max(1, std::min(rows, 256 / std::max(Lr, 1)));
+    int G = std::max(1, std::min(rows, max_threads / std::max(Lr, 1)));
     *groups = G;
     *threads = (Lr * G + 31) / 32 * 32;
 }

@@ -12,6 +12,7 @@
 struct pr_force {
     int n = 0, precision = 0, scheme = 0, nx = 0, nvx = 0, nvp = 0;
     int lift_order = 0;                 // 0: Maxwellian lift; 1: first-order lift (lift_ce.cu)
+    int max_threads = 256;              // thread cap of the step kernel's CTAs
     prk::FGeom g{};
     size_t smem = 0;
     std::vector<prk::FInst> h;          // host copy of the descriptors

@@ -68,7 +68,7 @@ double dt_stab(const pr_force_instance& d, double cfl)
 
 // Geometry for cluster size C (the v_x rows split over C CTAs); false if a
 // CTA would be empty or its rows do not fit shared memory.
-bool geometry(int precision, int scheme, int nvx, int nvp, int C, prk::FGeom* g, size_t* smem)
+bool geometry(int precision, int scheme, int nvx, int nvp, int C, int max_threads, prk::FGeom* g, size_t* smem)
 {
     long long ncol = (long long)nvx * nvp * nvp;
     if (C < 1 || C > prk::FORCE_MAX_CLUSTER) return false;
@@ -84,7 +84,7 @@ bool geometry(int precision, int scheme, int nvx, int nvp, int C, prk::FGeom* g,
     g->rows = rows;
     g->bulk = ((size_t)nvp * nvp * elem(precision)) % 16 == 0 ? 1 : 0;
     g->vec = g->bulk ? (int)(16 / elem(precision)) : 1;
-    prk::force_step_layout(nvp, g->vec, rows, &g->groups, &g->threads);
+    prk::force_step_layout(nvp, g->vec, rows, max_threads, &g->groups, &g->threads);
     if (g->threads > (g->vec == 1 ? 1024 : 512)) return false;
     g->buf_off = (int)prk::force_step_buf_off(precision, nvx, nvp);
     *smem = sm;
@@ -98,15 +98,15 @@ int default_cluster(int precision, int scheme, int nvx, int nvp)
     prk::FGeom g;
     size_t sm;
     int C = 1;
-    while (C <= prk::FORCE_MAX_CLUSTER && !geometry(precision, scheme, nvx, nvp, C, &g, &sm)) ++C;
+    while (C <= prk::FORCE_MAX_CLUSTER && !geometry(precision, scheme, nvx, nvp, C, 256, &g, &sm)) ++C;
     if (C > prk::FORCE_MAX_CLUSTER) return 0;
     while (C < 8 && (long long)g.rows * nvp * nvp > 8192) {
         int D = C + 1;
-        while (D <= 8 && !geometry(precision, scheme, nvx, nvp, D, &g, &sm)) ++D;
+        while (D <= 8 && !geometry(precision, scheme, nvx, nvp, D, 256, &g, &sm)) ++D;
         if (D > 8) break;
         C = D;
     }
-    geometry(precision, scheme, nvx, nvp, C, &g, &sm);
+    geometry(precision, scheme, nvx, nvp, C, 256, &g, &sm);
     return C;
 }
 
@@ -239,7 +239,7 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
     b->nx = d0.nx;
     b->nvx = d0.nvx;
     b->nvp = d0.nvp;
-    geometry(precision, scheme, d0.nvx, d0.nvp, C, &b->g, &b->smem);
+    geometry(precision, scheme, d0.nvx, d0.nvp, C, b->max_threads, &b->g, &b->smem);
     int clusters = 0;
     if (prk::force_step_occupancy(precision, scheme, b->g.vec, C, b->g.threads, b->smem, &clusters) != 0 ||
         clusters < 1) {
@@ -585,13 +585,31 @@ int pr_force_set_cluster(pr_force* b, int cluster)
     if (!b) return PR_EINVAL;
     prk::FGeom g;
     size_t sm;
-    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, cluster, &g, &sm))
+    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, cluster, b->max_threads, &g, &sm))
         return ffail(b, PR_EINVAL, "cluster size %d does not fit this column", cluster);
     int clusters = 0;
     if (prk::force_step_occupancy(b->precision, b->scheme, g.vec, cluster, g.threads, sm, &clusters) != 0 ||
         clusters < 1)
         return ffail(b, PR_EINVAL, "no cluster of %d CTAs fits the device", cluster);
     FCUDA(b, cudaStreamSynchronize(b->stream));
+    b->g = g;
+    b->smem = sm;
+    return PR_OK;
+}
+
+int pr_force_set_threads(pr_force* b, int threads)
+{
+    if (!b) return PR_EINVAL;
+    if (threads < 32 || threads > 1024 || threads % 32) return ffail(b, PR_EINVAL, "threads must be 32..1024, a multiple of 32");
+    prk::FGeom g;
+    size_t sm;
+    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, b->g.C, threads, &g, &sm))
+        return ffail(b, PR_EINVAL, "no layout with %d threads for this column", threads);
+    int clusters = 0;
+    if (prk::force_step_occupancy(b->precision, b->scheme, g.vec, g.C, g.threads, sm, &clusters) != 0 || clusters < 1)
+        return ffail(b, PR_EINVAL, "no cluster of this shape fits the device");
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    b->max_threads = threads;
     b->g = g;
     b->smem = sm;
     return PR_OK;

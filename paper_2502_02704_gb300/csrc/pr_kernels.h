@@ -133,7 +133,7 @@ struct FGeom {
 cudaError_t prepare_force_kernels(int max_smem);
 size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows);
 size_t force_step_buf_off(int precision, int nvx, int nvp);
-void force_step_layout(int nvp, int vec, int rows, int* groups, int* threads);
+void force_step_layout(int nvp, int vec, int rows, int max_threads, int* groups, int* threads);
 size_t force_lift_smem(int precision, int nvx, int nvp);
 int force_step_occupancy(int precision, int scheme, int vec, int C, int threads, size_t smem, int* clusters);
 // One fine step of every active instance; input buffer cur[b] ^ (step & 1);

@@ -235,3 +235,27 @@ def test_force_path_errors_are_reported():
         pr.pr_force_sync(b)
     finally:
         pr.pr_force_destroy(b)
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+@pytest.mark.parametrize("threads", [32, 64, 512])
+def test_thread_caps_give_the_same_step(precision, threads):
+    # nvp = 8: 16 (float) / 32 (double) threads per v_x row, so the caps give
+    # 1 to 32 row groups per CTA; 3 CTAs per column (rows 14 / 14 / 12)
+    nx, nvx, nvp, L, n = 10, 40, 8, 7.0, 3
+    E = W.test3_force(nx)
+    U = _profile(nx)
+    k = _vkin(nx, nvx, nvp, L, pr.PR_BC_PERIODIC, 1e-2, pr.PR_MUSCL, E)
+    dt = O.v_fine_dt_stab(k, 0.5)
+    b = pr.pr_force_create([pr.ForceInstance(nx, nvx, nvp, dt, L=L, x0=0.0, x1=2.0, eps=1e-2, E=E)], pr.PR_MUSCL,
+                           precision)
+    try:
+        pr.pr_force_set_cluster(b, 3)
+        pr.pr_force_set_threads(b, threads)
+        pr.pr_force_set_initial(b, 0, U)
+        pr.pr_force_run(b, n)
+        V = pr.pr_force_moments(b, 0)
+    finally:
+        pr.pr_force_destroy(b)
+    Vo = O.v_project(k, O.v_fine_run(k, dt, n, O.v_lift(k, U)), conserved=True)
+    assert moment_rel_err(V, Vo) < TOL[precision]
