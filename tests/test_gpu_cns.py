@@ -136,3 +136,21 @@ def test_higher_order_options_need_collisions():
         assert ei.value.code == pr.PR_EINVAL
     finally:
         pr.pr_batch_destroy(b)
+
+
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW, pr.PR_BC_REFLECT])
+def test_first_order_lift_single_cell_and_two_cells(bc):
+    # nx = 1: every gradient is zero (periodic, outflow) or comes from the
+    # mirrored ghost (reflecting u_x); nx = 2 the smallest stencil
+    for nx in (1, 2):
+        U = _prof(max(nx, 2))[:, :nx].copy()
+        nv, L, eps = 8, 6.0, 3e-2
+        b = pr.pr_batch_create([pr.instance(nx, nv, 1e-3, L=L, bc=bc, eps=eps)], pr.PR_FP64)
+        try:
+            pr.pr_batch_set_lift_order(b, 1)
+            pr.pr_batch_set_initial(b, 0, U)
+            f = pr.pr_batch_get_f(b, 0)
+        finally:
+            pr.pr_batch_destroy(b)
+        k = O.Kin(nx=nx, nv=nv, L=L, bc=BC[bc], eps=eps)
+        assert f_rel_err(f, O.lift_ce(k, U)) < 1e-13, nx

@@ -259,3 +259,53 @@ def test_thread_caps_give_the_same_step(precision, threads):
         pr.pr_force_destroy(b)
     Vo = O.v_project(k, O.v_fine_run(k, dt, n, O.v_lift(k, U)), conserved=True)
     assert moment_rel_err(V, Vo) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", [pr.PR_FP64, pr.PR_MIXED])
+@pytest.mark.parametrize("nx,nvx,nvp,bc,scheme", [
+    (1, 8, 4, pr.PR_BC_PERIODIC, pr.PR_UPWIND),   # one x cell: every neighbour is itself
+    (2, 8, 4, pr.PR_BC_REFLECT, pr.PR_MUSCL),     # the smallest reflecting MUSCL column pair
+    (6, 2, 4, pr.PR_BC_OUTFLOW, pr.PR_MUSCL),     # two v_x rows: both are box ends
+    (6, 10, 1, pr.PR_BC_PERIODIC, pr.PR_UPWIND),  # one (v_y, v_z) cell per row
+    (6, 12, 5, pr.PR_BC_REFLECT, pr.PR_UPWIND),   # odd rows: staged by the threads, no bulk copies
+])
+def test_edge_geometries_match_oracle(precision, nx, nvx, nvp, bc, scheme):
+    L, n = 6.0, 3
+    E = np.linspace(-0.8, 0.6, nx)
+    x = W.cell_centres(nx, 0.0, 2.0)
+    U = np.stack([1 + 0.2 * np.cos(x), 0.1 * np.sin(x), 0 * x, 0 * x, 1 + 0.1 * x])
+    k = _vkin(nx, nvx, nvp, L, bc, 5e-2, scheme, E)
+    dt = O.v_fine_dt_stab(k, 0.5)
+    b = pr.pr_force_create([pr.ForceInstance(nx, nvx, nvp, dt, L=L, x0=0.0, x1=2.0, bc=bc, eps=5e-2, E=E)], scheme,
+                           precision)
+    try:
+        pr.pr_force_set_initial(b, 0, U)
+        pr.pr_force_run(b, n)
+        f = pr.pr_force_get_f(b, 0)
+        V = pr.pr_force_moments(b, 0)
+    finally:
+        pr.pr_force_destroy(b)
+    fo = O.v_fine_run(k, dt, n, O.v_lift(k, U))
+    assert f_rel_err(f, fo) < (1e-12 if precision == pr.PR_FP64 else 2e-6)
+    assert moment_rel_err(V, O.v_project(k, fo, conserved=True)) < TOL[precision]
+
+
+@pytest.mark.parametrize("scheme", [pr.PR_UPWIND, pr.PR_MUSCL])
+def test_zero_force_kernel_is_the_e0_kernel(scheme):
+    # two independent GPU kernels for the same scheme when E = 0 and the grid
+    # is isotropic: the clustered force step and the persistent E = 0 step
+    nx, nv, L, n = 48, 16, 8.0, 7
+    dt = pr.fine_dt(nx, nv, L)
+    U = W.smooth_periodic(nx)
+    a = pr.pr_batch_create([pr.instance(nx, nv, dt, L=L, eps=1e-2, scheme=scheme)], pr.PR_FP64)
+    b = pr.pr_force_create([pr.ForceInstance(nx, nv, nv, dt, L=L, x0=0.0, x1=1.0, eps=1e-2)], scheme, pr.PR_FP64)
+    try:
+        pr.pr_batch_set_initial(a, 0, U)
+        pr.pr_batch_run(a, n)
+        pr.pr_force_set_initial(b, 0, U)
+        pr.pr_force_run(b, n)
+        assert f_rel_err(pr.pr_force_get_f(b, 0), pr.pr_batch_get_f(a, 0)) < 1e-12
+        assert moment_rel_err(pr.pr_force_moments(b, 0), pr.pr_batch_moments(a, 0)) < 1e-12
+    finally:
+        pr.pr_batch_destroy(a)
+        pr.pr_force_destroy(b)
