@@ -358,3 +358,54 @@ def test_test3_force_concentrates_mass_towards_the_centre():
     assert np.all(U[0][centre] > rho0[centre]) and np.all(U[0][edges] < rho0[edges] + 1e-12)
     # the flow points towards x = 1 on both sides
     assert np.all(U[1][(x > 0.2) & (x < 0.9)] > 0) and np.all(U[1][(x > 1.1) & (x < 1.8)] < 0)
+
+
+# ------------------------------------------------- moments of f* from column sums
+def _column_sums(f, nvx, nvp, L):
+    """Per column: the five moments M, the upwind half sums A+ (v_x > 0) and
+    A- (v_x <= 0) of v_x f times each moment weight, and the densities of the
+    first and last v_x rows (plain numpy)."""
+    vx, _ = _nodes(nvx, L)
+    vp, _ = _nodes(nvp, L)
+    F = f.reshape(f.shape[0], nvx, nvp, nvp)
+    VX, VY, VZ = np.meshgrid(vx, vp, vp, indexing="ij")
+    phis = (np.ones_like(VX), VX, VY, VZ, VX ** 2 + VY ** 2 + VZ ** 2)
+    pos = VX > 0
+    M = np.stack([(F * p).sum(axis=(1, 2, 3)) for p in phis], axis=1)
+    Ap = np.stack([(F * np.where(pos, VX * p, 0)).sum(axis=(1, 2, 3)) for p in phis], axis=1)
+    An = np.stack([(F * np.where(pos, 0, VX * p)).sum(axis=(1, 2, 3)) for p in phis], axis=1)
+    return M, Ap, An, F[:, 0].sum(axis=(1, 2)), F[:, -1].sum(axis=(1, 2))
+
+
+@pytest.mark.parametrize("bc", [O.BC_PERIODIC, O.BC_OUTFLOW, O.BC_REFLECT])
+@pytest.mark.parametrize("nvx", [8, 9])
+def test_transport_moments_follow_from_column_sums(bc, nvx):
+    # With upwind x fluxes the sums of phi f* over a column are M - nu (A+_c -
+    # A+_{c-1} + A-_{c+1} - A-_c) - nuv Q, where the v_x Rusanov fluxes
+    # telescope (summation by parts, zero flux through +-L): Q vanishes for
+    # phi = 1, v_y, v_z and needs only the column density, sum v_x f and the
+    # end-row densities for phi = v_x, |v|^2.  A reflecting wall's ghost
+    # swaps A+ and A- with the sign of the even weights.
+    nx, nvp, L = 7, 4, 5.0
+    E = np.linspace(-0.6, 0.9, nx)
+    k = O.VKin(nx=nx, nvx=nvx, nvp=nvp, L=L, x0=0.0, x1=2.0, bc=bc, eps=math.inf, E=E)
+    f = np.random.default_rng(3).random((nx, k.ncol)) + 0.1
+    dt = O.v_fine_dt_stab(k, 0.5)
+    want = _column_sums(O.v_fine_run(k, dt, 1, f), nvx, nvp, L)[0]
+    M, Ap, An, r0, rn = _column_sums(f, nvx, nvp, L)
+    dvx, nu = 2 * L / nvx, dt / (2.0 / nx)
+    nuv, Em = dt / dvx, np.max(np.abs(E))
+    s = np.array([-1.0, 1.0, -1.0, -1.0, -1.0])
+    if bc == O.BC_PERIODIC:
+        Apg, Ang = Ap[nx - 1], An[0]
+    elif bc == O.BC_OUTFLOW:
+        Apg, Ang = Ap[0], An[nx - 1]
+    else:
+        Apg, Ang = s * An[0], s * Ap[nx - 1]
+    Ap_m = np.vstack([Apg, Ap[:-1]])   # A+ of column c-1
+    An_p = np.vstack([An[1:], Ang])    # A- of column c+1
+    Q = np.zeros((nx, 5))
+    Q[:, 1] = -dvx * (E * (M[:, 0] - 0.5 * (r0 + rn)) - Em * 0.5 * (rn - r0))
+    Q[:, 4] = -dvx * (E * (2 * M[:, 1] - L * (rn - r0)) - Em * (L * (r0 + rn) - dvx * M[:, 0]))
+    got = M - nu * (Ap - Ap_m + An_p - An) - nuv * Q
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
