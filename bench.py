@@ -36,7 +36,7 @@ METRIC = "phase-space cell-updates/s (FP32 vs FP64) and parareal speedup on 1 GB
 UNIT = "cell-updates/s"
 WORKLOAD = "smooth periodic fine solve, Nx=512, 32^3 on [-8,8]^3, MUSCL-minmod, eps in {1,1e-2,1e-4} batched, 200 steps"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_run_traffic.txt")
-FORCE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_step_traffic.txt")
+FORCE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_fused_traffic.txt")
 FINE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "fine.cu")
 FORCE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "force.cu")
 
@@ -445,15 +445,18 @@ def _test3_section(pr, np, torch):
         pr.pr_force_kernel_time(b, reset=True)
         pr.pr_force_run(b, steps)
         kms, _ = pr.pr_force_kernel_time(b)
+        walk, (cluster, _) = pr.pr_force_get_march(b), pr.pr_force_config(b)
     finally:
         pr.pr_force_destroy(b)
+    kname = (f"k_force_fused<16> (fused single pass, walks of {walk} columns, {cluster} CTAs per column)"
+             if walk > 0 else f"k_force_step<float, upwind, 4> (clusters of {cluster})")
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     ach = 8.0 * ncell * nb / (kms * 1e-3) / 1e9
     traffic = None
     try:  # ncu DRAM bytes of one batch step, valid while the kernel source is unchanged
         tj = json.load(open(FORCE_TRAFFIC_FILE))
-        if tj.get("force_cu_sha256_16") == _src_hash(FORCE_SRC):
+        if walk > 0 and tj.get("force_cu_sha256_16") == _src_hash(FORCE_SRC):
             traffic = tj["dram_bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         pass
@@ -461,7 +464,7 @@ def _test3_section(pr, np, torch):
                             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                                          "frac": ach / hbm, "traffic": traffic,
                                          "algorithmic_bytes_per_launch": 8.0 * ncell * nb,
-                                         "kernel": "k_force_step<float, upwind, 4>", "bytes_per_cell_update": 8,
+                                         "kernel": kname, "bytes_per_cell_update": 8,
                                          "peak_source": "measured" if peaks else "fallback"}}
     # Algorithm 2
     para = {}

@@ -397,6 +397,27 @@ int pr_force_set_cluster(pr_force* b, int cluster);
  * Synchronous. */
 int pr_force_set_threads(pr_force* b, int threads);
 
+/* Step kernel of the force path.  Two implementations give the same scheme:
+ * the clustered step (a cluster of CTAs per x column: transport, exchange of
+ * the moments of f* over distributed shared memory, relaxation) and, in mixed
+ * precision with the upwind scheme, the fused single-pass step: the moments
+ * of f* follow from 17 sums per column of f^n (upwind half sums of v_x f,
+ * end-row densities; the v_x fluxes telescope), which every step writes next
+ * to f^{n+1}, so each cell is read, relaxed and written in one pass and a CTA
+ * walks `columns` consecutive x columns with the next column's bulk copy in
+ * flight.  The fused step needs rows that are 16-byte multiples, at most 256
+ * threads per CTA, and no CTA whose rows straddle v_x = 0.  columns = -1:
+ * automatic (the default: the fused step where it applies, walks of about a
+ * quarter of the columns per resident CTA group, at most 32); 0: the
+ * clustered step; >= 1: the fused step with walks of about that length (the
+ * columns split into equal walks), PR_EINVAL where it does not apply (the
+ * previous setting stays).  Results agree to rounding (the moments of f* are
+ * summed in another order).  Synchronous. */
+int pr_force_set_march(pr_force* b, int columns);
+
+/* Walk length of the fused step in use (0: the clustered step). */
+int pr_force_get_march(const pr_force* b, int* columns);
+
 /* Average duration in ms of one step launch over the runs since the last
  * reset (CUDA events on the launching stream around each run, divided by its
  * steps); reset = 1 clears the accumulator. */

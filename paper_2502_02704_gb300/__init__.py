@@ -120,6 +120,8 @@ _SIGS = {
     "pr_force_config": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pr_force_set_cluster": (C.c_int, [_VP, C.c_int]),
     "pr_force_set_threads": (C.c_int, [_VP, C.c_int]),
+    "pr_force_set_march": (C.c_int, [_VP, C.c_int]),
+    "pr_force_get_march": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "pr_force_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_force_dt_stab": (C.c_int, [C.POINTER(pr_force_instance), C.c_double, _D]),
     "pr_force_inject_wait_timeout": (C.c_int, [_VP, C.c_int]),
@@ -504,6 +506,16 @@ def pr_force_set_cluster(b, cluster):
 
 def pr_force_set_threads(b, threads):
     _force_check(b, lib().pr_force_set_threads(b.ptr, int(threads)))
+
+
+def pr_force_set_march(b, columns):
+    _force_check(b, lib().pr_force_set_march(b.ptr, int(columns)))
+
+
+def pr_force_get_march(b) -> int:
+    n = C.c_int()
+    _force_check(b, lib().pr_force_get_march(b.ptr, C.byref(n)))
+    return n.value
 
 
 def pr_force_kernel_time(b, reset=False):

@@ -164,12 +164,12 @@ __device__ __forceinline__ void cta_partials(const T (&s)[5], FSharedT<typename 
 }
 
 // Copy the cluster's partials part[phase] of every rank into gat (one
-// distributed-shared-memory load per thread, all in flight at once).
+// distributed-shared-memory load per thread, all in flight at once; a CTA
+// of fewer than 5 C threads takes several).
 template <typename A>
 __device__ __forceinline__ void cluster_gather(cg::cluster_group& cl, FSharedT<A>& sh, int phase, int C)
 {
-    const int t = threadIdx.x;
-    if (t < 5 * C) {
+    for (int t = threadIdx.x; t < 5 * C; t += blockDim.x) {
         const int r = t / 5, k = t - 5 * r;
         const FSharedT<A>* rs = cl.map_shared_rank(&sh, r);
         sh.gat[r][k] = rs->part[phase][k];
@@ -241,9 +241,9 @@ __device__ __forceinline__ void maxwell_params(FSharedT<double>& sh, double, boo
     sh.par[6] = 0.5 * rcp_nr(th);
 }
 
-__device__ __forceinline__ void maxwell_params(FSharedT<DF>& sh, float dv3, bool report, int* status)
+__device__ __forceinline__ void maxwell_params_f(const DF* tot, float* fpar, float dv3, bool report, int* status)
 {
-    const DF r = sh.tot[0], m1 = sh.tot[1], m2 = sh.tot[2], m3 = sh.tot[3], e2 = sh.tot[4];
+    const DF r = tot[0], m1 = tot[1], m2 = tot[2], m3 = tot[3], e2 = tot[4];
     const DF mm = df_add(df_mul(m1, m1), df_add(df_mul(m2, m2), df_mul(m3, m3)));
     const DF nd = df_add(df_mul(r, e2), DF{-mm.hi, -mm.lo});  // 3 rho^2 theta (sums without dv3)
     const float rf = r.hi + r.lo, num = nd.hi + nd.lo;
@@ -252,13 +252,18 @@ __device__ __forceinline__ void maxwell_params(FSharedT<DF>& sh, float dv3, bool
     const float irf = 1.0f / rf;
     const float th = ok ? num * (irf * irf) * (1.0f / 3.0f) : 1.0f;
     const float rs = ok ? rsqrtf(2.0f * 3.14159265f * th) : 0.0f;
-    sh.fpar[0] = rf * dv3;
-    sh.fpar[1] = (m1.hi + m1.lo) * irf;
-    sh.fpar[2] = (m2.hi + m2.lo) * irf;
-    sh.fpar[3] = (m3.hi + m3.lo) * irf;
-    sh.fpar[4] = th;
-    sh.fpar[5] = rf * dv3 * rs * rs * rs;
-    sh.fpar[6] = 0.5f / th;
+    fpar[0] = rf * dv3;
+    fpar[1] = (m1.hi + m1.lo) * irf;
+    fpar[2] = (m2.hi + m2.lo) * irf;
+    fpar[3] = (m3.hi + m3.lo) * irf;
+    fpar[4] = th;
+    fpar[5] = rf * dv3 * rs * rs * rs;
+    fpar[6] = 0.5f / th;
+}
+
+__device__ __forceinline__ void maxwell_params(FSharedT<DF>& sh, float dv3, bool report, int* status)
+{
+    maxwell_params_f(sh.tot, sh.fpar, dv3, report, status);
 }
 
 __device__ __forceinline__ void cluster_arrive()
@@ -289,10 +294,10 @@ __device__ __forceinline__ long long gtimer()
     return t;
 }
 
-// Wait (bounded by limit_ns) until the transaction count of the single-use
-// mbarrier at phase 0 completes; false on time-out.  Each try suspends the
-// thread for up to 100 us unless the phase completes first.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, long long limit_ns)
+// Wait (bounded by limit_ns) until the phase of the mbarrier with the given
+// parity completes; false on time-out.  Each try suspends the thread for up
+// to 100 us unless the phase completes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, long long limit_ns, uint32_t parity = 0)
 {
     const long long t0 = gtimer();
     for (int it = 0;; ++it) {
@@ -302,7 +307,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, long long limit_ns)
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(mbar), "r"(0), "r"(100000)
+            : "r"(mbar), "r"(parity), "r"(100000)
             : "memory");
         if (done) return true;
         if ((it & 63) == 63 && gtimer() - t0 > limit_ns) return false;
@@ -395,7 +400,6 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
     const long long ncol = g.ncol;
     const int R = g.rows;
     const int r0 = rank * R, r1 = min(r0 + R, nvx), nr = r1 - r0;
-    constexpr int NB = SCHEME == 0 ? 1 : 3;  // neighbour-column buffers
 
     extern __shared__ __align__(16) unsigned char fsm[];
     using AC = Acc<T>;
@@ -674,6 +678,515 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
     cluster_wait();  // no CTA leaves while another may still read its shared memory
 }
 
+// ---- fused single-pass step (float, upwind): one CTA walks S columns ----
+//
+// With upwind x fluxes the sums of phi f* over a column (phi = 1, v, |v|^2)
+// are linear in sums of f^n over columns c-1, c, c+1 (summation by parts):
+//   P_phi(f*_c) = M_phi(c) - nu (A+_phi(c) - A+_phi(c-1) + A-_phi(c+1) - A-_phi(c)) - nuv Q_phi(c),
+// M_phi = sum phi f, A+-_phi = sum over v_x > 0 / v_x <= 0 of v_x phi f; the
+// v_x Rusanov fluxes telescope (zero flux through +-L), so Q vanishes for
+// phi = 1, v_y, v_z and, for phi = v_x, |v|^2, needs only M_1, M_v_x and the
+// densities rho_0, rho_{nvx-1} of the first and last v_x rows:
+//   Q_vx   = -dv_x [E (M_1 - (rho_0 + rho_last)/2) - E_max (rho_last - rho_0)/2]
+//   Q_|v|2 = -dv_x [E (2 M_vx - L (rho_last - rho_0)) - E_max (L (rho_0 + rho_last) - dv_x M_1)].
+// A reflecting wall's ghost column (v_x mirrored) has A+- = s A-+ of its
+// edge column, s = -1 for the even weights (1, v_y, v_z, |v|^2), +1 for v_x.
+// Each step therefore writes, next to f^{n+1}, these 17 sums of f^{n+1} per
+// (column, CTA) — the partials — and the next step knows every column's
+// Maxwellian before it reads f: one pass per cell (transport, relaxation,
+// store, sums), no exchange between CTAs and no f* kept anywhere.  A CTA owns
+// v_x rows [r0, r0+R) of the columns [i0, i0+S) of one instance: at the start
+// of its walk it adds the partials of columns i0-1 .. i0+S over the C CTAs of
+// a column in a fixed order and builds the parameters and factor tables of
+// all S columns while the first bulk copies land; then, per column, three
+// column slots rotate in shared memory as in a pipelined ring (rows with
+// v_x > 0 read columns c-1 and c, the others c and c+1; a CTA's rows never
+// straddle v_x = 0), the next column's copy in flight during the pass.
+constexpr int NQ = 17;  // per (column, CTA): M[5], A+[5], A-[5], rho_0, rho_{nvx-1}
+
+struct FuShared {
+    DF red[2][8][12];            // per-warp sums (<= 256 threads), by column parity
+    unsigned long long mbar[4];  // column slots 0..2; 3: failure-detection check
+};
+
+// Byte offsets of the walk's tables after FuShared (host and device).
+struct FuLayout {
+    size_t rs, tot, par, vxe, eyz, slots, total;
+};
+
+__host__ __device__ inline FuLayout fu_layout(int nvp, int R, int S)
+{
+    FuLayout L;
+    size_t o = sizeof(FuShared);
+    L.rs = o;                                          // DF [(S+2)][NQ]: rank sums of columns i0-1 .. i0+S
+    o += (size_t)(S + 2) * NQ * sizeof(DF);
+    L.tot = o;                                         // DF [S][5]: P(f*) of each column
+    o += (size_t)S * 5 * sizeof(DF);
+    L.par = o;                                         // float [S][8]: Maxwellian parameters
+    o += (size_t)S * 8 * sizeof(float);
+    L.vxe = o;                                         // float2 [S][R]: (v_x, ex) of the CTA's rows
+    o += (size_t)S * R * 2 * sizeof(float);
+    L.eyz = o;                                         // float [S][2 nvp]: ey, ez
+    o += (size_t)S * 2 * nvp * sizeof(float);
+    o = (o + 127) / 128 * 128;
+    L.slots = o;                                       // float [3][R+2][nvp^2]
+    o += (size_t)3 * (R + 2) * nvp * nvp * sizeof(float);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ DF df_scale(DF a, float s) { return df_mul(a, DF{s, 0.0f}); }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+
+// Sum over the C ranks (stride NQ) in the pairwise order of rank_sum.
+__device__ __forceinline__ DF part_rank_sum(const DF* __restrict__ p, int C)
+{
+    DF v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = r < C ? p[(size_t)r * NQ] : DF{0.0f, 0.0f};
+#pragma unroll
+    for (int w = 1; w < 16; w *= 2)
+#pragma unroll
+        for (int r = 0; r + w < 16; r += 2 * w) v[r] = df_add(v[r], v[r + w]);
+    return v[0];
+}
+
+// Per-thread sums of f^{n+1} over the thread's rows: per lane sum f and
+// sum v_x f; per row (vs = the row's lane sum) sum v_x vs, v_x^2 vs, v_x^3 vs
+// and the first / last row's vs.
+struct FuAcc {
+    float S0[4], T[4], R1, R2, R3, e0, en;
+};
+
+__device__ __forceinline__ void fu_clear(FuAcc& s)
+{
+#pragma unroll
+    for (int l = 0; l < 4; ++l) s.S0[l] = s.T[l] = 0.0f;
+    s.R1 = s.R2 = s.R3 = s.e0 = s.en = 0.0f;
+}
+
+// Row sums without the end-row densities (rows inside the box).
+__device__ __forceinline__ float fu_row_in(FuAcc& s, const Pack<float, 4>& v, float vx)
+{
+    float vs = 0.0f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        s.S0[l] += v.x[l];
+        s.T[l] = fmaf(vx, v.x[l], s.T[l]);
+        vs += v.x[l];
+    }
+    const float vx2 = vx * vx;
+    s.R1 = fmaf(vx, vs, s.R1);
+    s.R2 = fmaf(vx2, vs, s.R2);
+    s.R3 = fmaf(vx2 * vx, vs, s.R3);
+    return vs;
+}
+
+__device__ __forceinline__ void fu_row(FuAcc& s, const Pack<float, 4>& v, float vx, int r, int nvx)
+{
+    const float vs = fu_row_in(s, v, vx);
+    if (r == 0) s.e0 = vs;
+    if (r == nvx - 1) s.en = vs;
+}
+
+// CTA sums of the accumulators into the 17 partials of one column at dst
+// (threads < NQ write): M from every row; A into A+ (rows with v_x > 0) or A-
+// (the other CTAs); the end-row densities from the CTAs holding those rows.
+__device__ __forceinline__ void fu_reduce(const FuAcc& s, const float (&vy)[4], const float (&vz)[4],
+                                          const float (&vp2)[4], DF (*red)[12], bool posc, bool has0,
+                                          bool hasn, DF* __restrict__ dst)
+{
+    float val[12];
+    val[0] = val[2] = val[3] = val[4] = val[5] = val[7] = val[8] = val[9] = 0.0f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        val[0] += s.S0[l];
+        val[2] += vy[l] * s.S0[l];
+        val[3] += vz[l] * s.S0[l];
+        val[4] += vp2[l] * s.S0[l];
+        val[5] += s.T[l];
+        val[7] += vy[l] * s.T[l];
+        val[8] += vz[l] * s.T[l];
+        val[9] += vp2[l] * s.T[l];
+    }
+    val[1] = s.R1;
+    val[4] += s.R2;
+    val[6] = s.R2;
+    val[9] += s.R3;
+    val[10] = s.e0;
+    val[11] = s.en;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        if (q >= 10 && !(q == 10 ? has0 : hasn)) continue;  // uniform over the CTA
+        const float v = warp_sum_t(val[q]);
+        if (lane == 0) red[w][q] = DF{v, 0.0f};
+    }
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        const int q = threadIdx.x;
+        int src;
+        if (q < 5) src = q;
+        else if (q < 10) src = posc ? q : -1;
+        else if (q < 15) src = posc ? -1 : q - 5;
+        else src = q == 15 ? (has0 ? 10 : -1) : (hasn ? 11 : -1);
+        DF a{0.0f, 0.0f};
+        if (src >= 0) {
+            const int nw = (blockDim.x + 31) >> 5;
+            for (int k = 0; k < nw; ++k) a = df_add(a, red[k][src]);
+        }
+        dst[q] = a;
+    }
+}
+
+// Uniform per-column constants of the pass.
+struct FuCol {
+    float nu, gE, gM;   // dt/dx; dt/dv_x E/2 and dt/dv_x E_max/2
+    float a;            // f^{n+1} = a f* + ex ey ez (b M folded into the tables); 1 without collisions
+    float hE, hEm;      // E/2, E_max/2 (box-end rows)
+    float nuv;
+};
+
+// One column's pass over the thread's rows [ra, rb): f* (upwind x flux
+// against the neighbour slot, v_x Rusanov flux, combined on interior rows),
+// f^{n+1} stored with 16-byte stores, its sums accumulated.  POS: the rows
+// take the x flux from column c-1 (v_x > 0); BND: the CTA holds a box-end
+// row (zero v_x flux through +-L); NVPC: nvp^2 / 4 lanes per row when > 0.
+template <bool POS, bool BND, int NVPC>
+__device__ __forceinline__ void fu_pass(const float* __restrict__ cen, const float* __restrict__ nb,
+                                        float* __restrict__ out, const float2* __restrict__ vxe, int ra, int rb,
+                                        int r0, int nvx, int nvp2_rt, const FuCol& k, const float (&myz)[4],
+                                        FuAcc& acc)
+{
+    const int nvp2 = NVPC > 0 ? NVPC * NVPC : nvp2_rt;
+    Pack<float, 4> dnv, cv;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) dnv.x[l] = 0.0f;
+    if (!BND || ra > 0) dnv = ldv<float, 4>(cen + (size_t)(ra - r0) * nvp2);
+    cv = ldv<float, 4>(cen + (size_t)(ra - r0 + 1) * nvp2);
+    const float* cp = cen + (size_t)(ra - r0 + 2) * nvp2;  // row r+1
+    const float* np = nb + (size_t)(ra - r0 + 1) * nvp2;   // neighbour row r
+    float* op = out + (size_t)ra * nvp2;
+#pragma unroll 4
+    for (int r = ra; r < rb; ++r) {
+        Pack<float, 4> up;
+        if (!BND || r < nvx - 1) up = ldv<float, 4>(cp);
+        else {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) up.x[l] = 0.0f;
+        }
+        const float2 ve = vxe[r - r0];
+        const float vx = ve.x, nvx_ = k.nu * ve.x;
+        const Pack<float, 4> x1 = ldv<float, 4>(np);
+        Pack<float, 4> v;
+        if (!BND || (r > 0 && r < nvx - 1)) {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                float fs = fmaf(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
+                fs = fmaf(-k.gE, u - d, fs);
+                fs = fmaf(k.gM, fmaf(-2.0f, cc, u + d), fs);
+                v.x[l] = fmaf(k.a, fs, ve.y * myz[l]);
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                const float Gr = r < nvx - 1 ? k.hE * (cc + u) - k.hEm * (u - cc) : 0.0f;
+                const float Gl = r > 0 ? k.hE * (d + cc) - k.hEm * (cc - d) : 0.0f;
+                float fs = fmaf(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
+                fs = fmaf(-k.nuv, Gr - Gl, fs);
+                v.x[l] = fmaf(k.a, fs, ve.y * myz[l]);
+            }
+        }
+        stv<float, 4>(op, v);
+        if (BND) fu_row(acc, v, vx, r, nvx);
+        else fu_row_in(acc, v, vx);
+        dnv = cv;
+        cv = up;
+        cp += nvp2;
+        np += nvp2;
+        op += nvp2;
+    }
+}
+
+template <int NVPC>
+__global__ void __launch_bounds__(256, 3)
+k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
+              int step, int* __restrict__ status, long long wait_ns, int poison)
+{
+    using T = float;
+    constexpr int VEC = 4;
+    const int b = blockIdx.z;
+    if (b < act->begin || b >= act->end) return;
+    const FInst& I = insts[b];
+    const int S = g.march, nx = I.nx, bc = I.bc;
+    const int i0 = blockIdx.y * S, i1 = min(i0 + S, nx), W = i1 - i0;
+    const int rank = blockIdx.x, C = gridDim.x;
+    const int nvx = g.nvx, nvp = NVPC > 0 ? NVPC : g.nvp, nvp2 = nvp * nvp;
+    const long long ncol = g.ncol;
+    const int R = g.rows;
+    const int r0 = rank * R, r1 = min(r0 + R, nvx), nr = r1 - r0;
+    const bool posc = r0 >= I.hpos;  // all rows of this CTA have v_x > 0 (else all <= 0)
+    const int dn = posc ? -1 : 1;
+    const size_t slot_elems = (size_t)(R + 2) * nvp2;
+
+    extern __shared__ __align__(16) unsigned char fsm[];
+    FuShared& sh = *reinterpret_cast<FuShared*>(fsm);
+    const FuLayout lay = fu_layout(nvp, R, S);
+    DF* rs = reinterpret_cast<DF*>(fsm + lay.rs);
+    DF* tot = reinterpret_cast<DF*>(fsm + lay.tot);
+    float* par = reinterpret_cast<float*>(fsm + lay.par);
+    float2* vxe = reinterpret_cast<float2*>(fsm + lay.vxe);
+    float* eyz = reinterpret_cast<float*>(fsm + lay.eyz);
+    T* slots = reinterpret_cast<T*>(fsm + lay.slots);
+    const uint32_t mbar0 = smem_addr(&sh.mbar[0]);
+
+    const int Lr = nvp2 / VEC, G = g.groups;
+    const int q = threadIdx.x % Lr, grp = threadIdx.x / Lr;
+    const int jp = q * VEC;
+    const int Rg = (nr + G - 1) / G;
+    const int ra = r0 + grp * Rg, rb = min(ra + Rg, r1);
+    const bool active = grp < G && ra < rb;
+    const int bufi = cur[b] ^ (step & 1);
+    const T* __restrict__ fin = static_cast<const T*>(I.f[bufi]);
+    T* __restrict__ fout = static_cast<T*>(I.f[bufi ^ 1]);
+    const DF* __restrict__ pin = static_cast<const DF*>(I.part[bufi]);
+    DF* __restrict__ pout = static_cast<DF*>(I.part[bufi ^ 1]);
+    const int ha = max(r0 - 1, 0), hb = min(r1 + 1, nvx);
+
+    const int cfirst = posc ? i0 - 1 : i0, clast = posc ? i1 - 1 : i1;
+    auto slot_of = [&](int c) { return (c - i0 + 3) % 3; };
+    // column c (a ghost through the boundary rule) into its slot: one bulk
+    // copy by thread 0, or, for a mirrored ghost (only ever a neighbour),
+    // rows r0..r1-1 copied by all threads; true if the slot waits on its mbarrier
+    auto load = [&](int c) -> bool {
+        bool mir;
+        const int sc = ghost_col(c, nx, bc, &mir);
+        T* dst = slots + (size_t)slot_of(c) * slot_elems;
+        const T* col = fin + (size_t)sc * ncol;
+        if (!mir) {
+            if (threadIdx.x == 0) {
+                const uint32_t mb = mbar0 + 8u * (uint32_t)slot_of(c);
+                const uint32_t bytes = (uint32_t)(hb - ha) * nvp2 * (uint32_t)sizeof(T);
+                fence_proxy_async();
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_addr(dst + (size_t)(ha - (r0 - 1)) * nvp2)),
+                    "l"(col + (size_t)ha * nvp2), "r"(bytes), "r"(mb)
+                    : "memory");
+            }
+            return true;
+        }
+        for (int e = threadIdx.x; e < nr * nvp2; e += blockDim.x) {
+            const int r = r0 + e / nvp2, j = e - (e / nvp2) * nvp2;
+            dst[(size_t)(r - r0 + 1) * nvp2 + j] = col[(size_t)(nvx - 1 - r) * nvp2 + j];
+        }
+        fence_proxy_async();  // a later bulk copy into this slot comes after these stores
+        return false;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar0 + 8u * k), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (poison)  // 16 bytes that no copy delivers: the wait on it runs out
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar0 + 24u), "r"(16)
+                         : "memory");
+    }
+    __syncthreads();
+    uint32_t pend = 0, phase = 0;
+    for (int c = cfirst; c < cfirst + 3 && c <= clast; ++c)
+        if (load(c)) pend |= 1u << slot_of(c);
+
+    // the walk's Maxwellians, while the copies land: rank sums of the
+    // partials of columns i0-1 .. i1 (ghosts raw), then P(f*) per column
+    const T* vt = static_cast<const T*>(I.vtab);
+    for (int t = threadIdx.x; t < (W + 2) * NQ; t += blockDim.x) {
+        const int j = t / NQ, qq = t - j * NQ;
+        bool mir;
+        const int src = ghost_col(i0 - 1 + j, nx, bc, &mir);
+        rs[t] = part_rank_sum(pin + (size_t)src * C * NQ + qq, C);
+    }
+    __syncthreads();
+    const float nu = I.fnu, nuv = I.fnuv, Emax = I.fEmax;
+    for (int t5 = threadIdx.x; t5 < W * 5; t5 += blockDim.x) {
+        const int j = t5 / 5, k = t5 - 5 * j, c = i0 + j;
+        const DF* Mc = rs + (size_t)(j + 1) * NQ;
+        const DF* Lc = rs + (size_t)j * NQ;
+        const DF* Rc = rs + (size_t)(j + 2) * NQ;
+        const float sk = k == 1 ? 1.0f : -1.0f;
+        const bool mirL = bc == 2 && c == 0, mirR = bc == 2 && c == nx - 1;
+        const DF Apl = mirL ? df_scale(Lc[10 + k], sk) : Lc[5 + k];  // A+ of column c-1
+        const DF Amr = mirR ? df_scale(Rc[5 + k], sk) : Rc[10 + k];  // A- of column c+1
+        const DF fl = df_add(df_sub(Mc[5 + k], Apl), df_sub(Amr, Mc[10 + k]));
+        DF t = df_sub(Mc[k], df_scale(fl, nu));
+        if (k == 1 || k == 4) {
+            const float dvx = (float)I.dvx, Lb = (float)I.L, E = I.Ef[c];
+            const float M0 = Mc[0].hi + Mc[0].lo, M1 = Mc[1].hi + Mc[1].lo;
+            const float e0 = Mc[15].hi + Mc[15].lo, en = Mc[16].hi + Mc[16].lo;
+            const float Q = k == 1 ? -dvx * (E * (M0 - 0.5f * (e0 + en)) - Emax * 0.5f * (en - e0))
+                                   : -dvx * (E * (2.0f * M1 - Lb * (en - e0)) - Emax * (Lb * (e0 + en) - dvx * M0));
+            t = df_sub(t, DF{nuv * Q, 0.0f});
+        }
+        tot[j * 5 + k] = t;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < W; j += blockDim.x)
+        maxwell_params_f(tot + j * 5, par + j * 8, I.fdv3, I.collide && rank == 0, status);
+    __syncthreads();
+    // per column: (v_x, ex) of the rows and ey, ez, with b pref folded into
+    // ex; zero tables without collisions
+    const bool collide = I.collide != 0;
+    const T bb = I.fb;
+    for (int t = threadIdx.x; t < W * (nr + 2 * nvp); t += blockDim.x) {
+        const int j = t / (nr + 2 * nvp), k = t - j * (nr + 2 * nvp);
+        const float* pj = par + j * 8;
+        if (k < nr) {
+            const float vx = vt[r0 + k], cx = vx - pj[1];
+            vxe[j * R + k] = make_float2(vx, collide ? bb * pj[5] * texp(-cx * cx * pj[6]) : 0.0f);
+        } else {
+            const int m = k - nr < nvp ? k - nr : k - nr - nvp;
+            const float cc = vt[nvx + m * nvp] - (k - nr < nvp ? pj[2] : pj[3]);
+            eyz[j * 2 * nvp + (k - nr)] = collide ? texp(-cc * cc * pj[6]) : 0.0f;
+        }
+    }
+    T vy[VEC], vz[VEC], vp2[VEC];
+    int jy[VEC], jz[VEC];
+    {
+        int y = jp / nvp, z = jp - (jp / nvp) * nvp;
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+            vy[l] = active ? vt[nvx + jp + l] : T(0);
+            vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
+            vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
+            jy[l] = y;
+            jz[l] = z;
+            if (++z == nvp) {
+                z = 0;
+                ++y;
+            }
+        }
+    }
+    FuCol kc;
+    kc.nu = nu;
+    kc.nuv = nuv;
+    kc.hEm = T(0.5) * Emax;
+    kc.gM = nuv * kc.hEm;
+    kc.a = collide ? I.fa : 1.0f;
+    const bool has0 = r0 == 0, hasn = r1 == nvx, bnd = has0 || hasn;
+    __syncthreads();  // tables and thread-staged slots visible
+    if (poison && !mbar_wait(mbar0 + 24u, wait_ns)) atomicCAS(status, 0, ST_TIMEOUT);
+
+    for (int c = i0; c < i1; ++c) {
+        const int j = c - i0;
+        const int sc = slot_of(c), sn = slot_of(c + dn);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int s = k == 0 ? sc : sn;
+            if (pend & (1u << s)) {
+                const uint32_t mb = mbar0 + 8u * (uint32_t)s, ph = (phase >> s) & 1u;
+                if (!mbar_wait(mb, wait_ns, ph)) {
+                    atomicCAS(status, 0, ST_TIMEOUT);
+                    mbar_wait(mb, wait_ns, ph);  // let the copy land before the slot is reused
+                }
+                pend &= ~(1u << s);
+                phase ^= 1u << s;
+            }
+        }
+        const T* cen = slots + (size_t)sc * slot_elems + jp;
+        const T* nb = slots + (size_t)sn * slot_elems + jp;
+        kc.hE = T(0.5) * I.Ef[c];
+        kc.gE = nuv * kc.hE;
+        T myz[VEC];
+        {
+            const float* ey = eyz + j * 2 * nvp;
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) myz[l] = ey[jy[l]] * ey[nvp + jz[l]];
+        }
+        FuAcc acc;
+        fu_clear(acc);
+        if (active) {
+            T* out = fout + (size_t)c * ncol + jp;
+            const float2* ve = vxe + j * R;
+            if (posc) {
+                if (bnd) fu_pass<true, true, NVPC>(cen, nb, out, ve, ra, rb, r0, nvx, nvp2, kc, myz, acc);
+                else fu_pass<true, false, NVPC>(cen, nb, out, ve, ra, rb, r0, nvx, nvp2, kc, myz, acc);
+            } else {
+                if (bnd) fu_pass<false, true, NVPC>(cen, nb, out, ve, ra, rb, r0, nvx, nvp2, kc, myz, acc);
+                else fu_pass<false, false, NVPC>(cen, nb, out, ve, ra, rb, r0, nvx, nvp2, kc, myz, acc);
+            }
+        }
+        // the 17 sums of f^{n+1} of this column; the reduction's barrier ends
+        // every read of this column's slots
+        fu_reduce(acc, vy, vz, vp2, sh.red[c & 1], posc, has0, hasn, pout + ((size_t)c * C + rank) * NQ);
+        {
+            const int nc = posc ? c + 2 : c + 3;
+            if (nc <= clast && load(nc)) pend |= 1u << slot_of(nc);
+        }
+    }
+}
+
+// Partials (the 17 column sums of the fused step) of the current state of
+// the active instances: one CTA per (rank, column, instance), rows read
+// straight from memory with 16-byte loads.
+__global__ void __launch_bounds__(256)
+k_force_sums(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, const int* __restrict__ cur)
+{
+    const int b = blockIdx.z;
+    if (b < act->begin || b >= act->end) return;
+    const FInst& I = insts[b];
+    const int i = blockIdx.y, rank = blockIdx.x, C = gridDim.x;
+    const int nvx = g.nvx, nvp = g.nvp, nvp2 = nvp * nvp;
+    const int R = g.rows, r0 = rank * R, r1 = min(r0 + R, nvx), nr = r1 - r0;
+    const int Lr = nvp2 / 4, G = g.groups;
+    const int q = threadIdx.x % Lr, grp = threadIdx.x / Lr, jp = q * 4;
+    const int Rg = (nr + G - 1) / G;
+    const int ra = r0 + grp * Rg, rb = min(ra + Rg, r1);
+    const bool active = grp < G && ra < rb;
+    __shared__ DF red[8][12];
+    const int bi = cur[b];
+    const float* f = static_cast<const float*>(I.f[bi]) + (size_t)i * g.ncol + jp;
+    const float* vt = static_cast<const float*>(I.vtab);
+    float vy[4], vz[4], vp2[4];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        vy[l] = active ? vt[nvx + jp + l] : 0.0f;
+        vz[l] = active ? vt[nvx + nvp2 + jp + l] : 0.0f;
+        vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : 0.0f;
+    }
+    FuAcc acc;
+    fu_clear(acc);
+    if (active)
+        for (int r = ra; r < rb; ++r) fu_row(acc, ldv<float, 4>(f + (size_t)r * nvp2), vt[r], r, nvx);
+    fu_reduce(acc, vy, vz, vp2, red, r0 >= I.hpos, r0 == 0, r1 == nvx,
+              static_cast<DF*>(I.part[bi]) + ((size_t)i * C + rank) * NQ);
+}
+
+// Conserved moments (Eq. 18) of the current state from its partials, into
+// Ucur and Uout: one thread per (moment, column) of each active instance.
+__global__ void k_force_finalize(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act,
+                                 const int* __restrict__ cur, int nx)
+{
+    const int b = act->begin + blockIdx.y;
+    if (b >= act->end) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 5 * nx) return;
+    const FInst& I = insts[b];
+    const int k = t / nx, i = t - k * nx;
+    const DF s = part_rank_sum(static_cast<const DF*>(I.part[cur[b]]) + (size_t)i * g.C * NQ + k, g.C);
+    double u = ((double)s.hi + (double)s.lo) * I.dv3;
+    if (k == 4) u *= 0.5;  // energy = 1/2 sum |v|^2 f dv
+    I.Ucur[k * nx + i] = u;
+    if (I.Uout) I.Uout[k * nx + i] = u;
+}
+
 // Lift (Eq. 17) of the conserved state Uin into buffer 0 of the active
 // instances; cur <- 0.
 template <typename T>
@@ -806,6 +1319,15 @@ void* pick_step(int precision, int scheme, int vec)
 
 }  // namespace
 
+size_t force_fused_smem(int nvp, int rows, int walk) { return fu_layout(nvp, rows, walk).total; }
+
+bool force_fused_fits(int precision, int scheme, const FGeom& g)
+{
+    return precision == 1 && scheme == 0 && g.bulk && g.vec == 4 && g.threads <= 256 && g.C <= 16;
+}
+
+int force_partials_per_column(const FGeom& g) { return g.C * NQ; }
+
 size_t force_step_buf_off(int precision, int nvx, int nvp)
 {
     size_t es = precision == 0 ? sizeof(double) : sizeof(float);
@@ -849,6 +1371,11 @@ cudaError_t prepare_force_kernels(int max_smem)
                                          max_smem - (int)fa.sharedSizeBytes);
                 cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             }
+    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<0>), reinterpret_cast<const void*>(&k_force_fused<16>)}) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+    }
     const void* lifts[2] = {reinterpret_cast<const void*>(&k_force_lift<double>),
                             reinterpret_cast<const void*>(&k_force_lift<float>)};
     for (const void* fn : lifts) {
@@ -857,6 +1384,17 @@ cudaError_t prepare_force_kernels(int max_smem)
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
     }
     return cudaGetLastError();
+}
+
+int force_fused_occupancy(int threads, size_t smem, int* per_sm)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fused<0>, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    *per_sm = n;
+    return 0;
 }
 
 int force_step_occupancy(int precision, int scheme, int vec, int C, int threads, size_t smem, int* clusters)
@@ -888,6 +1426,12 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
                               const Active* act, int* cur, int step, int last, int* status, size_t smem,
                               cudaStream_t s, long long wait_ns, int poison)
 {
+    if (g.march > 0) {
+        dim3 grid(g.C, (nx + g.march - 1) / g.march, n_inst);
+        if (g.nvp == 16) k_force_fused<16><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+        else k_force_fused<0><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+        return cudaGetLastError();
+    }
     void* fn = pick_step(precision, scheme, g.vec);
     if (!fn) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
@@ -905,6 +1449,21 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
     void* args[] = {(void*)&insts, (void*)&g,      (void*)&act,     (void*)&cur,   (void*)&step,
                     (void*)&last,  (void*)&status, (void*)&wait_ns, (void*)&poison};
     return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_force_sums(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
+                              const int* cur, cudaStream_t s)
+{
+    k_force_sums<<<dim3(g.C, nx, n_inst), g.threads, 0, s>>>(insts, g, act, cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_finalize(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
+                                  const int* cur, cudaStream_t s)
+{
+    dim3 grid((5 * nx + 127) / 128, n_inst);
+    k_force_finalize<<<grid, 128, 0, s>>>(insts, g, act, cur, nx);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_force_lift(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,

@@ -13,6 +13,10 @@ struct pr_force {
     int n = 0, precision = 0, scheme = 0, nx = 0, nvx = 0, nvp = 0;
     int lift_order = 0;                 // 0: Maxwellian lift; 1: first-order lift (lift_ce.cu)
     int max_threads = 256;              // thread cap of the step kernel's CTAs
+    int march_req = -1;                 // fused step walk length: -1 automatic, 0 clustered step
+    void* d_part = nullptr;             // fused step partials, [2][n][nx][C][17] double-float
+    size_t part_bytes = 0;
+    std::vector<char> sums_ok;          // per instance: the partials match the current state
     prk::FGeom g{};
     size_t smem = 0;
     std::vector<prk::FInst> h;          // host copy of the descriptors

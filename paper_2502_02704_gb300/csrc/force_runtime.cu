@@ -87,6 +87,7 @@ bool geometry(int precision, int scheme, int nvx, int nvp, int C, int max_thread
     prk::force_step_layout(nvp, g->vec, rows, max_threads, &g->groups, &g->threads);
     if (g->threads > (g->vec == 1 ? 1024 : 512)) return false;
     g->buf_off = (int)prk::force_step_buf_off(precision, nvx, nvp);
+    g->march = 0;
     *smem = sm;
     return true;
 }
@@ -108,6 +109,95 @@ int default_cluster(int precision, int scheme, int nvx, int nvp)
     }
     geometry(precision, scheme, nvx, nvp, C, 256, &g, &sm);
     return C;
+}
+
+// Fused-step geometry with C CTAs per column (sets g.march to the walk
+// length, *smem): false when the fused step does not apply (precision,
+// scheme, row size, a CTA straddling v_x = 0, shared memory).  walk_req >= 1:
+// walks of about that length; -1 (automatic): a quarter of the columns per
+// resident CTA group, capped where the walk's tables would cost a resident
+// CTA per SM and at 32, and false below 2 (too few columns per group: the
+// clustered step is faster there).  The columns split into equal walks.
+bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk::FGeom* out, size_t* smem)
+{
+    prk::FGeom gg;
+    prk::FGeom* g = &gg;
+    size_t sm0;
+    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, C, max_threads, g, &sm0)) return false;
+    if (!prk::force_fused_fits(b->precision, b->scheme, *g)) return false;
+    for (const prk::FInst& I : b->h)
+        if (I.hpos < b->nvx && I.hpos % g->rows != 0) return false;
+    const size_t optin = (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin) - 1024;
+    auto resident = [&](int S) {
+        const size_t sm = prk::force_fused_smem(b->nvp, g->rows, S);
+        int per_sm = 0;
+        if (sm > optin || prk::force_fused_occupancy(g->threads, sm, &per_sm) != 0) return 0;
+        return per_sm;
+    };
+    const int per1 = resident(1);
+    if (per1 < 1) return false;
+    const int cap = std::min(32, b->nx);
+    long long S = walk_req;
+    if (S < 0) {
+        int scap = 1;
+        while (scap < cap && resident(scap + 1) == per1) ++scap;
+        const long long groups = std::max<long long>(1, (long long)per1 * dev_attr(cudaDevAttrMultiProcessorCount) / C);
+        S = std::min<long long>(scap, (long long)b->n * b->nx / (4 * groups));
+        if (S < 2) return false;
+    }
+    S = std::max<long long>(1, std::min<long long>(S, cap));
+    const long long walks = (b->nx + S - 1) / S;
+    S = (b->nx + walks - 1) / walks;
+    const size_t sm = prk::force_fused_smem(b->nvp, g->rows, (int)S);
+    if (resident((int)S) < 1) return false;
+    g->march = (int)S;
+    *out = gg;
+    *smem = sm;
+    return true;
+}
+
+// Cluster size of the fused step by default: the fewest CTAs per column for
+// which two CTAs of an 8-column walk share an SM, else the fewest that fit;
+// 0 if the fused step does not apply.  (Rows per thread amortise the
+// per-column reduction: on Test 3, 8 CTAs of 32 rows at two per SM beat 16 of
+// 16 rows at three per SM by a fifth.)
+int default_fused_cluster(const pr_force* b)
+{
+    const size_t half = (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerMultiprocessor) / 2 - 1024;
+    int any = 0;
+    for (int C = 1; C <= prk::FORCE_MAX_CLUSTER; ++C) {
+        prk::FGeom g;
+        size_t sm;
+        if (!fused_geometry(b, C, b->max_threads, 1, &g, &sm)) continue;
+        if (prk::force_fused_smem(b->nvp, g.rows, std::min(8, b->nx)) <= half) return C;
+        if (!any) any = C;
+    }
+    return any;
+}
+
+// Partials for the fused step's geometry (grown when needed; zeroed) and the
+// descriptors' pointers into them (host copies; the caller uploads).
+bool ensure_partials(pr_force* b)
+{
+    if (b->g.march <= 0) return true;
+    const size_t per = (size_t)b->nx * prk::force_partials_per_column(b->g) * 8;  // one state's partials
+    const size_t need = 2 * per * b->n;
+    if (need > b->part_bytes) {
+        cudaFree(b->d_part);
+        b->d_part = nullptr;
+        b->part_bytes = 0;
+        if (cudaMalloc(&b->d_part, need) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        b->part_bytes = need;
+    }
+    if (cudaMemset(b->d_part, 0, need) != cudaSuccess) return false;
+    for (int k = 0; k < b->n; ++k)
+        for (int j = 0; j < 2; ++j)
+            b->h[k].part[j] = static_cast<unsigned char*>(b->d_part) + ((size_t)2 * k + j) * per;
+    std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);
+    return true;
 }
 
 template <typename T>
@@ -199,6 +289,7 @@ void destroy(pr_force* b)
     cudaFree(b->d_Ulift);
     cudaFree(b->d_vtab);
     cudaFree(b->d_tmp);
+    cudaFree(b->d_part);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -322,6 +413,20 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
             }
         }
     }
+    b->sums_ok.assign(n, 0);
+    if (int Cf = default_fused_cluster(b)) {
+        prk::FGeom g;
+        size_t sm;
+        if (fused_geometry(b, Cf, b->max_threads, b->march_req, &g, &sm)) {
+            b->g = g;
+            b->smem = sm;
+        }
+    }
+    if (!ensure_partials(b)) {
+        err = "fused-step partials: out of device memory";
+        destroy(b);
+        return PR_ENOMEM;
+    }
     prk::Active all{0, n};
     std::vector<float> Ef(E.begin(), E.end());
     ok = cudaMemcpy(b->d_E, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -356,8 +461,17 @@ cudaError_t upload(pr_force* b, int b0, int b1, cudaStream_t s)
                            s);
 }
 
-static int enqueue_steps(pr_force* b, int n_inst, int nsteps, cudaStream_t s, bool timing)
+// Steps of the active window [b0, b1): the fused step first makes the
+// window's partials current (after a lift or a load) and ends with the
+// moments of the final state from its partials.
+static int enqueue_steps(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool timing)
 {
+    const int n_inst = b->n;
+    const bool fused = b->g.march > 0;
+    if (fused && nsteps > 0 && std::find(b->sums_ok.begin() + b0, b->sums_ok.begin() + b1, 0) != b->sums_ok.begin() + b1) {
+        FCUDA(b, prk::launch_force_sums(b->d_inst, b->g, b->nx, n_inst, b->d_active, b->d_cur, s));
+        pr_internal_count_launches(1);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timing && nsteps > 0) {
         FCUDA(b, cudaEventCreate(&e0));
@@ -373,6 +487,11 @@ static int enqueue_steps(pr_force* b, int n_inst, int nsteps, cudaStream_t s, bo
         FCUDA(b, cudaEventRecord(e1, s));
         b->pending.push_back({e0, e1, nsteps});
     }
+    if (fused && nsteps > 0) {
+        FCUDA(b, prk::launch_force_finalize(b->d_inst, b->g, b->nx, n_inst, b->d_active, b->d_cur, s));
+        pr_internal_count_launches(1);
+    }
+    std::fill(b->sums_ok.begin() + b0, b->sums_ok.begin() + b1, fused ? 1 : 0);
     return PR_OK;
 }
 
@@ -380,7 +499,7 @@ int enqueue_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool ti
 {
     if (nsteps <= 0 || b1 <= b0) return PR_OK;
     FCUDA(b, set_active(b, b0, b1, s));
-    int rc = enqueue_steps(b, b->n, nsteps, s, timing);
+    int rc = enqueue_steps(b, b0, b1, nsteps, s, timing);
     FCUDA(b, set_active(b, 0, b->n, s));
     return rc;
 }
@@ -394,9 +513,10 @@ int enqueue_lift_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bo
                  ? prk::launch_force_lift_ce(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s)
                  : prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s));
     pr_internal_count_launches(1);
+    std::fill(b->sums_ok.begin() + b0, b->sums_ok.begin() + b1, 0);
     int rc = PR_OK;
     if (nsteps > 0) {
-        rc = enqueue_steps(b, b->n, nsteps, s, timing);
+        rc = enqueue_steps(b, b0, b1, nsteps, s, timing);
     } else {
         FCUDA(b, prk::launch_force_moments(p, b->d_inst, b->g, b->nx, b0, b1, b->d_cur, s));
         pr_internal_count_launches(1);
@@ -413,10 +533,15 @@ cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cu
         e = b->lift_order == 1
                 ? prk::launch_force_lift_ce(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s)
                 : prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s);
+    const bool fused = b->g.march > 0 && nsteps > 0;
+    if (e == cudaSuccess && fused) e = prk::launch_force_sums(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
     for (int k = 0; e == cudaSuccess && k < nsteps; ++k)
         e = prk::launch_force_step(p, b->scheme, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, k,
                                    k == nsteps - 1, b->d_status, b->smem, s);
     if (e == cudaSuccess) e = prk::launch_force_advance(b->d_active, b->d_cur, nsteps, b->n, s);
+    if (e == cudaSuccess && fused)
+        e = prk::launch_force_finalize(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
+    std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);  // replays change the states behind the host's back
     return e;
 }
 
@@ -509,6 +634,7 @@ int pr_force_set_f(pr_force* b, int i, const double* f)
     FCUDA(b, cudaMemcpy(b->d_tmp, f, sizeof(double) * n, cudaMemcpyHostToDevice));
     const int p = b->precision == PR_FP64 ? 0 : 1;
     FCUDA(b, prk::launch_force_load(p, b->d_inst, i, b->d_cur, b->d_tmp, n, s));
+    b->sums_ok[i] = 0;
     FCUDA(b, prk::launch_force_moments(p, b->d_inst, b->g, b->nx, i, i + 1, b->d_cur, s));
     pr_internal_count_launches(2);
     return prf::take_status(b);
@@ -580,21 +706,59 @@ int pr_force_config(const pr_force* b, int* cluster, int* chunk)
     return PR_OK;
 }
 
+// Geometry for C CTAs per column with the requested walk (-1 automatic, 0
+// clustered step): the fused step where it applies, else the clustered one;
+// false (with a message) when neither fits.
+static bool pick_geometry(pr_force* b, int C, int max_threads, int walk_req, prk::FGeom* g, size_t* sm)
+{
+    if (walk_req != 0 && fused_geometry(b, C, max_threads, walk_req, g, sm)) return true;
+    if (walk_req >= 1) {
+        ffail(b, PR_EINVAL, "the fused step does not apply to this geometry");
+        return false;
+    }
+    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, C, max_threads, g, sm)) {
+        ffail(b, PR_EINVAL, "no layout with %d CTAs of at most %d threads for this column", C, max_threads);
+        return false;
+    }
+    int clusters = 0;
+    if (prk::force_step_occupancy(b->precision, b->scheme, g->vec, C, g->threads, *sm, &clusters) != 0 ||
+        clusters < 1) {
+        ffail(b, PR_EINVAL, "no cluster of %d CTAs fits the device", C);
+        return false;
+    }
+    return true;
+}
+
+// Switch to geometry g once the stream has drained: the partials follow the
+// fused step's geometry and the descriptors are uploaded again.
+static int apply_geometry(pr_force* b, const prk::FGeom& g, size_t sm)
+{
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    const prk::FGeom old = b->g;
+    const size_t old_sm = b->smem;
+    b->g = g;
+    b->smem = sm;
+    if (!ensure_partials(b)) {
+        b->g = old;
+        b->smem = old_sm;
+        return ffail(b, PR_ENOMEM, "fused-step partials: out of device memory");
+    }
+    std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);
+    FCUDA(b, prf::upload(b, 0, b->n, b->stream));
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    return PR_OK;
+}
+
 int pr_force_set_cluster(pr_force* b, int cluster)
 {
     if (!b) return PR_EINVAL;
     prk::FGeom g;
     size_t sm;
-    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, cluster, b->max_threads, &g, &sm))
-        return ffail(b, PR_EINVAL, "cluster size %d does not fit this column", cluster);
-    int clusters = 0;
-    if (prk::force_step_occupancy(b->precision, b->scheme, g.vec, cluster, g.threads, sm, &clusters) != 0 ||
-        clusters < 1)
-        return ffail(b, PR_EINVAL, "no cluster of %d CTAs fits the device", cluster);
-    FCUDA(b, cudaStreamSynchronize(b->stream));
-    b->g = g;
-    b->smem = sm;
-    return PR_OK;
+    // an explicit walk that does not apply to the new size falls back to the clustered step
+    if (!pick_geometry(b, cluster, b->max_threads, b->march_req, &g, &sm) &&
+        (b->march_req < 1 || !pick_geometry(b, cluster, b->max_threads, 0, &g, &sm)))
+        return PR_EINVAL;
+    return apply_geometry(b, g, sm);
 }
 
 int pr_force_set_threads(pr_force* b, int threads)
@@ -603,15 +767,30 @@ int pr_force_set_threads(pr_force* b, int threads)
     if (threads < 32 || threads > 1024 || threads % 32) return ffail(b, PR_EINVAL, "threads must be 32..1024, a multiple of 32");
     prk::FGeom g;
     size_t sm;
-    if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, b->g.C, threads, &g, &sm))
-        return ffail(b, PR_EINVAL, "no layout with %d threads for this column", threads);
-    int clusters = 0;
-    if (prk::force_step_occupancy(b->precision, b->scheme, g.vec, g.C, g.threads, sm, &clusters) != 0 || clusters < 1)
-        return ffail(b, PR_EINVAL, "no cluster of this shape fits the device");
-    FCUDA(b, cudaStreamSynchronize(b->stream));
-    b->max_threads = threads;
-    b->g = g;
-    b->smem = sm;
+    if (!pick_geometry(b, b->g.C, threads, b->march_req, &g, &sm) &&
+        (b->march_req < 1 || !pick_geometry(b, b->g.C, threads, 0, &g, &sm)))
+        return PR_EINVAL;
+    int rc = apply_geometry(b, g, sm);
+    if (rc == PR_OK) b->max_threads = threads;
+    return rc;
+}
+
+int pr_force_set_march(pr_force* b, int columns)
+{
+    if (!b) return PR_EINVAL;
+    if (columns < -1) return ffail(b, PR_EINVAL, "columns must be -1, 0 or a walk length");
+    prk::FGeom g;
+    size_t sm;
+    if (!pick_geometry(b, b->g.C, b->max_threads, columns, &g, &sm)) return PR_EINVAL;
+    int rc = apply_geometry(b, g, sm);
+    if (rc == PR_OK) b->march_req = columns;
+    return rc;
+}
+
+int pr_force_get_march(const pr_force* b, int* columns)
+{
+    if (!b || !columns) return PR_EINVAL;
+    *columns = b->g.march;
     return PR_OK;
 }
 
@@ -636,11 +815,16 @@ int pr_force_inject_wait_timeout(pr_force* b, int wait_ms)
     cudaStream_t s = b->stream;
     FCUDA(b, cudaStreamSynchronize(s));
     FCUDA(b, set_active(b, 0, b->n, s));
+    if (b->g.march > 0) {  // the fused step reads the partials of the current states
+        FCUDA(b, prk::launch_force_sums(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s));
+        pr_internal_count_launches(1);
+    }
     FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx, b->n,
                                     b->d_active, b->d_cur, 0, 1, b->d_status, b->smem, s,
                                     (long long)wait_ms * 1000000LL, 1));
     FCUDA(b, prk::launch_force_advance(b->d_active, b->d_cur, 1, b->n, s));
     pr_internal_count_launches(2);
+    std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);
     return prf::take_status(b);
 }
 

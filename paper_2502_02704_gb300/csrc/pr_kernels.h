@@ -111,6 +111,7 @@ struct FInst {
     const float* Ef;           // the same in float (the float path converts nothing per thread)
     float fa, fb, fnu, fnuv, fEmax, fdv3;
     void* f[2];                // ping-pong state
+    void* part[2];             // fused step: column sums of f[k], [nx][C][17] double-float (float path)
     const void* vtab;          // T: v_x[nvx], v_y[nvp2], v_z[nvp2], v_y^2+v_z^2[nvp2]
     const double* Uin;         // lift source, conserved [5][nx] (device) or null
     double* Uout;              // projection destination after the last step (or null)
@@ -128,13 +129,28 @@ struct FGeom {
     int threads;               // threads per CTA of the step kernel
     int bulk;                  // rows are 16-byte multiples: stage them with bulk copies
     int buf_off;               // shared-memory offset of the staging buffers
+    int march;                 // > 0: fused single-pass step, a CTA walks this many x columns; 0: clustered step
 };
 
 cudaError_t prepare_force_kernels(int max_smem);
 size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows);
 size_t force_step_buf_off(int precision, int nvx, int nvp);
+// The fused single-pass step (float, upwind, 16-byte lanes, <= 256 threads):
+// its shared memory for a walk of `walk` columns, whether geometry g can use
+// it, the partials it keeps per column, and its resident CTAs per SM.
+size_t force_fused_smem(int nvp, int rows, int walk);
+bool force_fused_fits(int precision, int scheme, const FGeom& g);
+int force_partials_per_column(const FGeom& g);
+int force_fused_occupancy(int threads, size_t smem, int* per_sm);
+// Partials of the current state of the active instances (fused step input).
+cudaError_t launch_force_sums(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
+                              const int* cur, cudaStream_t s);
+// Ucur / Uout of the active instances from the partials of their current state.
+cudaError_t launch_force_finalize(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
+                                  const int* cur, cudaStream_t s);
 void force_step_layout(int nvp, int vec, int rows, int max_threads, int* groups, int* threads);
 size_t force_lift_smem(int precision, int nvx, int nvp);
+// Resident clusters of C CTAs of the clustered step kernel.
 int force_step_occupancy(int precision, int scheme, int vec, int C, int threads, size_t smem, int* clusters);
 // One fine step of every active instance; input buffer cur[b] ^ (step & 1);
 // last != 0 also writes P(f^{n+1}) into Ucur (and Uout).
