@@ -446,24 +446,33 @@ def _test3_section(pr, np, torch):
         pr.pr_force_run(b, steps)
         kms, _ = pr.pr_force_kernel_time(b)
         walk, (cluster, _) = pr.pr_force_get_march(b), pr.pr_force_config(b)
+        persistent = pr.pr_force_get_persistent(b, steps)
     finally:
         pr.pr_force_destroy(b)
-    kname = (f"k_force_fused<16> (fused single pass, walks of {walk} columns, {cluster} CTAs per column)"
-             if walk > 0 else f"k_force_step<float, upwind, 4> (clusters of {cluster})")
+    if walk > 0 and persistent:
+        kname = (f"k_force_fused_run<16> (fused single pass, all {steps} steps in one persistent launch, "
+                 f"walks of {walk} columns, {cluster} CTAs per column)")
+    elif walk > 0:
+        kname = f"k_force_fused<16> (fused single pass, walks of {walk} columns, {cluster} CTAs per column)"
+    else:
+        kname = f"k_force_step<float, upwind, 4> (clusters of {cluster})"
     peaks = _peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     ach = 8.0 * ncell * nb / (kms * 1e-3) / 1e9
     traffic = None
     try:  # ncu DRAM bytes of one batch step, valid while the kernel source is unchanged
         tj = json.load(open(FORCE_TRAFFIC_FILE))
-        if walk > 0 and tj.get("force_cu_sha256_16") == _src_hash(FORCE_SRC):
-            traffic = tj["dram_bytes_per_launch"]
+        if walk > 0 and tj.get("kernel", "").split(" ")[0] == kname.split(" ")[0] \
+                and tj.get("force_cu_sha256_16") == _src_hash(FORCE_SRC):
+            traffic = tj["dram_bytes_per_step"]
     except (OSError, ValueError, KeyError):
         pass
     out["batch64_mixed"] = {"step_ms": kms, "cell_updates_per_s": ncell * nb / (kms * 1e-3),
                             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                                          "frac": ach / hbm, "traffic": traffic,
-                                         "algorithmic_bytes_per_launch": 8.0 * ncell * nb,
+                                         "algorithmic_bytes_per_step": 8.0 * ncell * nb,
+                                         "per": "step (a persistent launch runs all timed steps; bytes and time "
+                                                "per step)" if walk > 0 and persistent else "step (one launch)",
                                          "kernel": kname, "bytes_per_cell_update": 8,
                                          "peak_source": "measured" if peaks else "fallback"}}
     # Algorithm 2

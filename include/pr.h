@@ -407,13 +407,26 @@ int pr_force_set_threads(pr_force* b, int threads);
  * walks `columns` consecutive x columns with the next column's bulk copy in
  * flight.  The fused step needs rows that are 16-byte multiples, at most 256
  * threads per CTA, and no CTA whose rows straddle v_x = 0.  columns = -1:
- * automatic (the default: the fused step where it applies, walks of about a
- * quarter of the columns per resident CTA group, at most 32); 0: the
- * clustered step; >= 1: the fused step with walks of about that length (the
- * columns split into equal walks), PR_EINVAL where it does not apply (the
- * previous setting stays).  Results agree to rounding (the moments of f* are
+ * automatic (the default: the fused step where it applies and there are at
+ * least two columns per resident CTA group, walks of that many columns,
+ * capped where longer walks would cost a resident CTA per SM and at 32); 0:
+ * the clustered step; >= 1: the fused step with walks of about that length
+ * (the columns split into equal walks), PR_EINVAL where it does not apply
+ * (the previous setting stays).  Results agree to rounding (the moments of f* are
  * summed in another order).  Synchronous. */
 int pr_force_set_march(pr_force* b, int columns);
+
+/* Runs of the fused step in one persistent launch.  mode = 1: every run of
+ * the fused step is one launch whose CTAs take work items (step, instance,
+ * walk, CTA row block) in step order, each waiting (bounded; PR_ETIMEOUT)
+ * until its own and its two neighbour walks have finished the previous step;
+ * 0: one launch per step; -1 (the default): persistent for runs of two
+ * steps or more.  Same results bit for bit.  Synchronous. */
+int pr_force_set_persistent(pr_force* b, int mode);
+
+/* Whether a run of nsteps steps of all instances would take one persistent
+ * launch (*on = 1) under the current settings. */
+int pr_force_get_persistent(const pr_force* b, int nsteps, int* on);
 
 /* Walk length of the fused step in use (0: the clustered step). */
 int pr_force_get_march(const pr_force* b, int* columns);
@@ -430,8 +443,12 @@ int pr_force_kernel_time(pr_force* b, double* avg_ms, int* steps, int reset);
  * waits for its real copies before it leaves; the call returns that status
  * after clearing it (PR_ETIMEOUT is the expected result).  The object stays
  * usable; the instance states are unspecified until they are set again.
- * PR_EINVAL when the rows are not staged by bulk copies (nvp^2 x element
- * size not a multiple of 16 bytes).  No GPU fault is involved.  Synchronous. */
+ * With the fused step forced persistent (pr_force_set_persistent(b, 1)) the
+ * check is instead a two-step persistent run whose step-2 items wait for a
+ * completion count no walk reaches: those dependency waits run out the same
+ * way.  PR_EINVAL when the rows are not staged by bulk copies (nvp^2 x
+ * element size not a multiple of 16 bytes).  No GPU fault is involved.
+ * Synchronous. */
 int pr_force_inject_wait_timeout(pr_force* b, int wait_ms);
 
 /* dt_stab of the reading above for inst (E read from the host array).
@@ -446,6 +463,15 @@ int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt);
  * result.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
 int pr_init_force(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t, int nvx,
                   const double* E);
+
+/* Step kernel of a pr_init_force problem's fine propagator (its slices are
+ * the instances of an internal pr_force): cluster > 0 sets the CTAs per x
+ * column (pr_force_set_cluster; 0 keeps them), then columns and persistent as
+ * pr_force_set_march and pr_force_set_persistent.  The next iteration
+ * rebuilds its captured graph.  PR_EINVAL for a problem without a force or a
+ * setting that does not apply (earlier settings of the call stay).
+ * Synchronous. */
+int pr_set_force_step(pr_ctx* ctx, int cluster, int columns, int persistent);
 
 #ifdef __cplusplus
 }

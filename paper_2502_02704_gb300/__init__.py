@@ -121,10 +121,13 @@ _SIGS = {
     "pr_force_set_cluster": (C.c_int, [_VP, C.c_int]),
     "pr_force_set_threads": (C.c_int, [_VP, C.c_int]),
     "pr_force_set_march": (C.c_int, [_VP, C.c_int]),
+    "pr_force_set_persistent": (C.c_int, [_VP, C.c_int]),
+    "pr_force_get_persistent": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int)]),
     "pr_force_get_march": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "pr_force_kernel_time": (C.c_int, [_VP, _D, C.POINTER(C.c_int), C.c_int]),
     "pr_force_dt_stab": (C.c_int, [C.POINTER(pr_force_instance), C.c_double, _D]),
     "pr_force_inject_wait_timeout": (C.c_int, [_VP, C.c_int]),
+    "pr_set_force_step": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
     "pr_init_force": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_grid), C.POINTER(pr_velocity), C.c_double,
                                 C.POINTER(pr_time), C.c_int, _D]),
 }
@@ -512,6 +515,16 @@ def pr_force_set_march(b, columns):
     _force_check(b, lib().pr_force_set_march(b.ptr, int(columns)))
 
 
+def pr_force_set_persistent(b, mode):
+    _force_check(b, lib().pr_force_set_persistent(b.ptr, int(mode)))
+
+
+def pr_force_get_persistent(b, nsteps) -> int:
+    n = C.c_int()
+    _force_check(b, lib().pr_force_get_persistent(b.ptr, int(nsteps), C.byref(n)))
+    return n.value
+
+
 def pr_force_get_march(b) -> int:
     n = C.c_int()
     _force_check(b, lib().pr_force_get_march(b.ptr, C.byref(n)))
@@ -553,6 +566,11 @@ def pr_init_force(nx, x0, x1, bc, nvx, nvp, L, eps, T, n_slices, E, cfl_f=0.5, c
     if rc != PR_OK:
         raise PrError(rc, (lib().pr_last_error(None) or b"").decode())
     return _Handle(out, "pr_ctx", nx=nx, nv=nvp, nvx=nvx, N=n_slices)
+
+
+def pr_set_force_step(ctx, cluster=0, columns=-1, persistent=-1):
+    """Step kernel of a force problem's fine propagator (pr_set_force_step)."""
+    _ctx_check(ctx, lib().pr_set_force_step(ctx.ptr, int(cluster), int(columns), int(persistent)))
 
 
 INF = math.inf

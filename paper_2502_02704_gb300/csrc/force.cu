@@ -748,7 +748,13 @@ __device__ __forceinline__ DF part_rank_sum(const DF* __restrict__ p, int C)
 {
     DF v[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = r < C ? p[(size_t)r * NQ] : DF{0.0f, 0.0f};
+    for (int r = 0; r < 16; ++r) {
+        v[r] = DF{0.0f, 0.0f};
+        if (r < C) {  // past L1: written by other CTAs of the same launch in the persistent run
+            const float2 x = __ldcg(reinterpret_cast<const float2*>(p + (size_t)r * NQ));
+            v[r] = DF{x.x, x.y};
+        }
+    }
 #pragma unroll
     for (int w = 1; w < 16; w *= 2)
 #pragma unroll
@@ -915,19 +921,39 @@ __device__ __forceinline__ void fu_pass(const float* __restrict__ cen, const flo
     }
 }
 
+// mbarriers of the three column slots (and the failure-detection check's)
+// at the start of the CTA's shared memory; thread 0 initialises, all wait.
+__device__ __forceinline__ void fu_init_mbar(unsigned char* fsm, int poison)
+{
+    FuShared& sh = *reinterpret_cast<FuShared*>(fsm);
+    const uint32_t mbar0 = smem_addr(&sh.mbar[0]);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar0 + 8u * k), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (poison)  // 16 bytes that no copy delivers: the wait on it runs out
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar0 + 24u), "r"(16)
+                         : "memory");
+    }
+    __syncthreads();
+}
+
+// One walk of the fused step: columns [wk S, wk S + S) of instance b, the v_x
+// rows of CTA `rank` of C, step `step` of the run (state buffer
+// cur[b] ^ (step & 1)).  The slot mbarriers are initialised by the caller;
+// `phase` carries their parities from one walk to the next (every copy a walk
+// issues, it also waits for).  Ends after the last column's partials are
+// written by threads < 17 (no barrier after them).
 template <int NVPC>
-__global__ void __launch_bounds__(256, 3)
-k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
-              int step, int* __restrict__ status, long long wait_ns, int poison)
+__device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, const FGeom& g, const int* __restrict__ cur,
+                                           int b, int wk, int rank, int C, int step, int* __restrict__ status,
+                                           long long wait_ns, uint32_t& phase, unsigned char* fsm)
 {
     using T = float;
     constexpr int VEC = 4;
-    const int b = blockIdx.z;
-    if (b < act->begin || b >= act->end) return;
     const FInst& I = insts[b];
     const int S = g.march, nx = I.nx, bc = I.bc;
-    const int i0 = blockIdx.y * S, i1 = min(i0 + S, nx), W = i1 - i0;
-    const int rank = blockIdx.x, C = gridDim.x;
+    const int i0 = wk * S, i1 = min(i0 + S, nx), W = i1 - i0;
     const int nvx = g.nvx, nvp = NVPC > 0 ? NVPC : g.nvp, nvp2 = nvp * nvp;
     const long long ncol = g.ncol;
     const int R = g.rows;
@@ -936,7 +962,6 @@ k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict
     const int dn = posc ? -1 : 1;
     const size_t slot_elems = (size_t)(R + 2) * nvp2;
 
-    extern __shared__ __align__(16) unsigned char fsm[];
     FuShared& sh = *reinterpret_cast<FuShared*>(fsm);
     const FuLayout lay = fu_layout(nvp, R, S);
     DF* rs = reinterpret_cast<DF*>(fsm + lay.rs);
@@ -986,22 +1011,13 @@ k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict
         }
         for (int e = threadIdx.x; e < nr * nvp2; e += blockDim.x) {
             const int r = r0 + e / nvp2, j = e - (e / nvp2) * nvp2;
-            dst[(size_t)(r - r0 + 1) * nvp2 + j] = col[(size_t)(nvx - 1 - r) * nvp2 + j];
+            dst[(size_t)(r - r0 + 1) * nvp2 + j] = __ldcg(col + (size_t)(nvx - 1 - r) * nvp2 + j);
         }
         fence_proxy_async();  // a later bulk copy into this slot comes after these stores
         return false;
     };
 
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 4; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar0 + 8u * k), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (poison)  // 16 bytes that no copy delivers: the wait on it runs out
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar0 + 24u), "r"(16)
-                         : "memory");
-    }
-    __syncthreads();
-    uint32_t pend = 0, phase = 0;
+    uint32_t pend = 0;
     for (int c = cfirst; c < cfirst + 3 && c <= clast; ++c)
         if (load(c)) pend |= 1u << slot_of(c);
 
@@ -1082,7 +1098,6 @@ k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict
     kc.a = collide ? I.fa : 1.0f;
     const bool has0 = r0 == 0, hasn = r1 == nvx, bnd = has0 || hasn;
     __syncthreads();  // tables and thread-staged slots visible
-    if (poison && !mbar_wait(mbar0 + 24u, wait_ns)) atomicCAS(status, 0, ST_TIMEOUT);
 
     for (int c = i0; c < i1; ++c) {
         const int j = c - i0;
@@ -1129,6 +1144,97 @@ k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict
         {
             const int nc = posc ? c + 2 : c + 3;
             if (nc <= clast && load(nc)) pend |= 1u << slot_of(nc);
+        }
+    }
+}
+
+// One launch per step: CTA (rank, walk, instance).
+template <int NVPC>
+__global__ void __launch_bounds__(256, 3)
+k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
+              int step, int* __restrict__ status, long long wait_ns, int poison)
+{
+    const int b = blockIdx.z;
+    if (b < act->begin || b >= act->end) return;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    fu_init_mbar(fsm, poison);
+    if (poison) {
+        const uint32_t mb = smem_addr(&reinterpret_cast<FuShared*>(fsm)->mbar[3]);
+        if (!mbar_wait(mb, wait_ns)) atomicCAS(status, 0, ST_TIMEOUT);
+    }
+    uint32_t phase = 0;
+    fused_walk<NVPC>(insts, g, cur, b, blockIdx.y, blockIdx.x, gridDim.x, step, status, wait_ns, phase, fsm);
+}
+
+// Wait (bounded by limit_ns) until the counter reaches target; acquire
+// ordering, so the writes published before the count are visible.
+__device__ __forceinline__ bool wait_count(const int* p, int target, long long limit_ns)
+{
+    const long long t0 = gtimer();
+    for (int it = 0;; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= target) return true;
+        if ((it & 15) == 15 && gtimer() - t0 > limit_ns) return false;
+        __nanosleep(64);
+    }
+}
+
+// All steps of a run in one persistent launch.  Work items (step, instance,
+// walk, CTA row block) are taken by ticket in that order; an item of step
+// k > 0 waits until every CTA of its walk and of the walks holding its two
+// neighbour columns has finished step k-1 (done[walk] >= C k): their f^k and
+// partials are then written, and their reads of the buffer this item
+// overwrites are over.  An item only waits on smaller tickets, taken by
+// running CTAs, so the lowest unfinished ticket never waits.  sync: [0]
+// ticket, [1 + b walks + w] done counts (zeroed before the launch).
+// poison (failure-detection check): the waits of step 1 ask for a count no
+// walk reaches, so they run out after wait_ns.
+template <int NVPC>
+__global__ void __launch_bounds__(256, 3)
+k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
+                  int nsteps, int* __restrict__ sync, int* __restrict__ status, long long wait_ns, int poison)
+{
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ int s_t;
+    fu_init_mbar(fsm, 0);
+    const int b0 = act->begin, nact = act->end - act->begin;
+    const int nx0 = nact > 0 ? insts[b0].nx : 1;  // the instances share nx
+    const int C = g.C, walks = (nx0 + g.march - 1) / g.march;
+    const int per_walk_set = walks * C;
+    const long long per_step = (long long)nact * per_walk_set, total = per_step * nsteps;
+    int* done = sync + 1;
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(sync, 1);
+        __syncthreads();
+        const long long t = s_t;
+        if (t >= total) break;
+        const int k = (int)(t / per_step);
+        const int rem = (int)(t - (long long)k * per_step);
+        const int bl = rem / per_walk_set, rem2 = rem - bl * per_walk_set;
+        const int wk = rem2 / C, rank = rem2 - wk * C;
+        const int b = b0 + bl;
+        if (k > 0 && threadIdx.x == 0) {
+            const FInst& I = insts[b];
+            const int nx = I.nx, S = g.march;
+            bool m;
+            const int wl = ghost_col(wk * S - 1, nx, I.bc, &m) / S;
+            const int wr = ghost_col(min(wk * S + S, nx), nx, I.bc, &m) / S;
+            const int* d = done + (size_t)bl * walks;
+            const int target = C * k + (poison && k == 1 ? 1 << 28 : 0);
+            bool ok = wait_count(d + wk, target, wait_ns);
+            ok = ok && wait_count(d + wl, target, wait_ns);
+            ok = ok && wait_count(d + wr, target, wait_ns);
+            if (!ok) atomicCAS(status, 0, ST_TIMEOUT);
+            asm volatile("fence.proxy.async.global;" ::: "memory");  // the bulk copies read what others wrote
+        }
+        __syncthreads();
+        fused_walk<NVPC>(insts, g, cur, b, wk, rank, C, k, status, wait_ns, phase, fsm);
+        __syncthreads();  // every store of this walk issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + (size_t)bl * walks + wk, 1);
         }
     }
 }
@@ -1371,7 +1477,9 @@ cudaError_t prepare_force_kernels(int max_smem)
                                          max_smem - (int)fa.sharedSizeBytes);
                 cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             }
-    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<0>), reinterpret_cast<const void*>(&k_force_fused<16>)}) {
+    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<0>), reinterpret_cast<const void*>(&k_force_fused<16>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<16>)}) {
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
@@ -1449,6 +1557,18 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
     void* args[] = {(void*)&insts, (void*)&g,      (void*)&act,     (void*)&cur,   (void*)&step,
                     (void*)&last,  (void*)&status, (void*)&wait_ns, (void*)&poison};
     return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+cudaError_t launch_force_fused_run(const FInst* insts, const FGeom& g, int n_inst, const Active* act, int* cur,
+                                   int nsteps, int* sync, int sync_words, int* status, size_t smem, cudaStream_t s,
+                                   int ctas, long long wait_ns, int poison)
+{
+    cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * (size_t)sync_words, s);
+    if (e != cudaSuccess || nsteps <= 0) return e;
+    if (g.nvp == 16)
+        k_force_fused_run<16><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status, wait_ns, poison);
+    else k_force_fused_run<0><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status, wait_ns, poison);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_force_sums(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,

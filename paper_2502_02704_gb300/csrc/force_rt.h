@@ -17,6 +17,9 @@ struct pr_force {
     void* d_part = nullptr;             // fused step partials, [2][n][nx][C][17] double-float
     size_t part_bytes = 0;
     std::vector<char> sums_ok;          // per instance: the partials match the current state
+    int persist_req = -1;               // fused runs in one persistent launch: -1 automatic, 0 never, 1 always
+    int* d_fsync = nullptr;             // persistent run: ticket + done count per instance and walk
+    int fsync_words = 0;
     prk::FGeom g{};
     size_t smem = 0;
     std::vector<prk::FInst> h;          // host copy of the descriptors
@@ -64,6 +67,8 @@ int enqueue_run(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s, bool ti
 // nsteps steps with projection, advance.
 cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cudaStream_t s);
 // Device status: 0 or a PR_* code (cleared).  Synchronises b->stream.
+// Kernel launches enqueue_graph_body makes for a run of nsteps steps.
+int graph_body_launches(const pr_force* b, int nsteps);
 int take_status(pr_force* b);
 double emax(const pr_force* b, int i);
 int launches_per_step();

@@ -114,10 +114,11 @@ int default_cluster(int precision, int scheme, int nvx, int nvp)
 // Fused-step geometry with C CTAs per column (sets g.march to the walk
 // length, *smem): false when the fused step does not apply (precision,
 // scheme, row size, a CTA straddling v_x = 0, shared memory).  walk_req >= 1:
-// walks of about that length; -1 (automatic): a quarter of the columns per
-// resident CTA group, capped where the walk's tables would cost a resident
-// CTA per SM and at 32, and false below 2 (too few columns per group: the
-// clustered step is faster there).  The columns split into equal walks.
+// walks of about that length; -1 (automatic): the columns per resident CTA
+// group (so a step's items fill the resident CTAs once), capped where the
+// walk's tables would cost a resident CTA per SM and at 32, and false below 2
+// (too few columns: the clustered step is as fast there).  The columns split
+// into equal walks.
 bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk::FGeom* out, size_t* smem)
 {
     prk::FGeom gg;
@@ -142,7 +143,7 @@ bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk
         int scap = 1;
         while (scap < cap && resident(scap + 1) == per1) ++scap;
         const long long groups = std::max<long long>(1, (long long)per1 * dev_attr(cudaDevAttrMultiProcessorCount) / C);
-        S = std::min<long long>(scap, (long long)b->n * b->nx / (4 * groups));
+        S = std::min<long long>(scap, (long long)b->n * b->nx / groups);
         if (S < 2) return false;
     }
     S = std::max<long long>(1, std::min<long long>(S, cap));
@@ -175,6 +176,28 @@ int default_fused_cluster(const pr_force* b)
     return any;
 }
 
+// CTAs of the persistent fused run that fit the device at once (0: none).
+int fused_resident(const pr_force* b)
+{
+    int per_sm = 0;
+    if (prk::force_fused_occupancy(b->g.threads, b->smem, &per_sm) != 0) return 0;
+    return per_sm * dev_attr(cudaDevAttrMultiProcessorCount);
+}
+
+// Whether a fused run of nsteps steps over n_inst instances takes one
+// persistent launch: asked for, or (automatic) for every run of two steps or
+// more (Test 3: 15.4 instead of 20.5 us per step for one instance, 85 instead
+// of 83 % of the copy bandwidth for 64; steps overlap where a step's last
+// items would leave CTAs idle).
+bool fused_persistent(const pr_force* b, int n_inst, int nsteps)
+{
+    if (b->g.march <= 0 || b->persist_req == 0 || nsteps < 1) return false;
+    const long long walks = (b->nx + b->g.march - 1) / b->g.march;
+    const long long items = (long long)n_inst * walks * b->g.C;
+    if (items * nsteps >= (1LL << 30) || fused_resident(b) < 1) return false;  // ticket range
+    return b->persist_req == 1 || nsteps >= 2;
+}
+
 // Partials for the fused step's geometry (grown when needed; zeroed) and the
 // descriptors' pointers into them (host copies; the caller uploads).
 bool ensure_partials(pr_force* b)
@@ -193,6 +216,17 @@ bool ensure_partials(pr_force* b)
         b->part_bytes = need;
     }
     if (cudaMemset(b->d_part, 0, need) != cudaSuccess) return false;
+    const int words = 1 + b->n * ((b->nx + b->g.march - 1) / b->g.march);
+    if (words > b->fsync_words) {
+        cudaFree(b->d_fsync);
+        b->d_fsync = nullptr;
+        b->fsync_words = 0;
+        if (cudaMalloc(&b->d_fsync, sizeof(int) * words) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        b->fsync_words = words;
+    }
     for (int k = 0; k < b->n; ++k)
         for (int j = 0; j < 2; ++j)
             b->h[k].part[j] = static_cast<unsigned char*>(b->d_part) + ((size_t)2 * k + j) * per;
@@ -290,6 +324,7 @@ void destroy(pr_force* b)
     cudaFree(b->d_vtab);
     cudaFree(b->d_tmp);
     cudaFree(b->d_part);
+    cudaFree(b->d_fsync);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -478,11 +513,22 @@ static int enqueue_steps(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s
         FCUDA(b, cudaEventCreate(&e1));
         FCUDA(b, cudaEventRecord(e0, s));
     }
-    for (int k = 0; k < nsteps; ++k)
-        FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx, n_inst,
-                                        b->d_active, b->d_cur, k, k == nsteps - 1, b->d_status, b->smem, s));
+    if (fused_persistent(b, b1 - b0, nsteps)) {
+        const long long walks = (b->nx + b->g.march - 1) / b->g.march;
+        const long long items = (long long)(b1 - b0) * walks * b->g.C * nsteps;
+        const int ctas = (int)std::min<long long>(fused_resident(b), items);
+        FCUDA(b, prk::launch_force_fused_run(b->d_inst, b->g, n_inst, b->d_active, b->d_cur, nsteps, b->d_fsync,
+                                             b->fsync_words, b->d_status, b->smem, s, ctas));
+        pr_internal_count_launches(1);
+    } else {
+        for (int k = 0; k < nsteps; ++k)
+            FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx,
+                                            n_inst, b->d_active, b->d_cur, k, k == nsteps - 1, b->d_status, b->smem,
+                                            s));
+        pr_internal_count_launches(nsteps);
+    }
     FCUDA(b, prk::launch_force_advance(b->d_active, b->d_cur, nsteps, n_inst, s));
-    pr_internal_count_launches(nsteps + (nsteps & 1));
+    pr_internal_count_launches(nsteps & 1);
     if (e0) {
         FCUDA(b, cudaEventRecord(e1, s));
         b->pending.push_back({e0, e1, nsteps});
@@ -535,14 +581,31 @@ cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cu
                 : prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s);
     const bool fused = b->g.march > 0 && nsteps > 0;
     if (e == cudaSuccess && fused) e = prk::launch_force_sums(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
-    for (int k = 0; e == cudaSuccess && k < nsteps; ++k)
-        e = prk::launch_force_step(p, b->scheme, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, k,
-                                   k == nsteps - 1, b->d_status, b->smem, s);
+    if (fused && fused_persistent(b, b->n, nsteps)) {
+        const long long walks = (b->nx + b->g.march - 1) / b->g.march;
+        const long long items = (long long)b->n * walks * b->g.C * nsteps;
+        const int ctas = (int)std::min<long long>(fused_resident(b), items);
+        if (e == cudaSuccess)
+            e = prk::launch_force_fused_run(b->d_inst, b->g, b->n, b->d_active, b->d_cur, nsteps, b->d_fsync,
+                                            b->fsync_words, b->d_status, b->smem, s, ctas);
+    } else
+        for (int k = 0; e == cudaSuccess && k < nsteps; ++k)
+            e = prk::launch_force_step(p, b->scheme, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, k,
+                                       k == nsteps - 1, b->d_status, b->smem, s);
     if (e == cudaSuccess) e = prk::launch_force_advance(b->d_active, b->d_cur, nsteps, b->n, s);
     if (e == cudaSuccess && fused)
         e = prk::launch_force_finalize(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
     std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);  // replays change the states behind the host's back
     return e;
+}
+
+int graph_body_launches(const pr_force* b, int nsteps)
+{
+    const bool fused = b->g.march > 0 && nsteps > 0;
+    int n = 2 + (nsteps & 1);  // set-active, lift, advance
+    if (fused) n += 2 + (fused_persistent(b, b->n, nsteps) ? 1 : nsteps);  // partials, steps, moments
+    else n += nsteps;
+    return n;
 }
 
 int take_status(pr_force* b)
@@ -787,6 +850,22 @@ int pr_force_set_march(pr_force* b, int columns)
     return rc;
 }
 
+int pr_force_set_persistent(pr_force* b, int mode)
+{
+    if (!b) return PR_EINVAL;
+    if (mode < -1 || mode > 1) return ffail(b, PR_EINVAL, "mode must be -1, 0 or 1");
+    FCUDA(b, cudaStreamSynchronize(b->stream));
+    b->persist_req = mode;
+    return PR_OK;
+}
+
+int pr_force_get_persistent(const pr_force* b, int nsteps, int* on)
+{
+    if (!b || !on) return PR_EINVAL;
+    *on = fused_persistent(b, b->n, nsteps) ? 1 : 0;
+    return PR_OK;
+}
+
 int pr_force_get_march(const pr_force* b, int* columns)
 {
     if (!b || !columns) return PR_EINVAL;
@@ -819,11 +898,21 @@ int pr_force_inject_wait_timeout(pr_force* b, int wait_ms)
         FCUDA(b, prk::launch_force_sums(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s));
         pr_internal_count_launches(1);
     }
-    FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx, b->n,
-                                    b->d_active, b->d_cur, 0, 1, b->d_status, b->smem, s,
-                                    (long long)wait_ms * 1000000LL, 1));
-    FCUDA(b, prk::launch_force_advance(b->d_active, b->d_cur, 1, b->n, s));
-    pr_internal_count_launches(2);
+    if (b->g.march > 0 && b->persist_req == 1) {
+        // a two-step persistent run whose step-1 dependency waits run out
+        const long long walks = (b->nx + b->g.march - 1) / b->g.march;
+        const int ctas = (int)std::min<long long>(fused_resident(b), 2LL * b->n * walks * b->g.C);
+        FCUDA(b, prk::launch_force_fused_run(b->d_inst, b->g, b->n, b->d_active, b->d_cur, 2, b->d_fsync,
+                                             b->fsync_words, b->d_status, b->smem, s, ctas,
+                                             (long long)wait_ms * 1000000LL, 1));
+        pr_internal_count_launches(1);
+    } else {
+        FCUDA(b, prk::launch_force_step(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->d_inst, b->g, b->nx, b->n,
+                                        b->d_active, b->d_cur, 0, 1, b->d_status, b->smem, s,
+                                        (long long)wait_ms * 1000000LL, 1));
+        FCUDA(b, prk::launch_force_advance(b->d_active, b->d_cur, 1, b->n, s));
+        pr_internal_count_launches(2);
+    }
     std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);
     return prf::take_status(b);
 }

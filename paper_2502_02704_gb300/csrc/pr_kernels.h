@@ -142,6 +142,12 @@ size_t force_fused_smem(int nvp, int rows, int walk);
 bool force_fused_fits(int precision, int scheme, const FGeom& g);
 int force_partials_per_column(const FGeom& g);
 int force_fused_occupancy(int threads, size_t smem, int* per_sm);
+// All nsteps fused steps of the active instances in one persistent launch of
+// `ctas` CTAs (at most the resident count); sync (sync_words ints: a ticket
+// and one done count per instance and walk) is zeroed on the stream first.
+cudaError_t launch_force_fused_run(const FInst* insts, const FGeom& g, int n_inst, const Active* act, int* cur,
+                                   int nsteps, int* sync, int sync_words, int* status, size_t smem, cudaStream_t s,
+                                   int ctas, long long wait_ns = WAIT_LIMIT_NS, int poison = 0);
 // Partials of the current state of the active instances (fused step input).
 cudaError_t launch_force_sums(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
                               const int* cur, cudaStream_t s);

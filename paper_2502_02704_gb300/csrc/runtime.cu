@@ -1371,7 +1371,7 @@ static int run_iterations(pr_ctx* c, int count, bool use_graph)
                 if (rc) return rc;
             }
             CCUDA(c, cudaGraphLaunch(c->gexec, cs));
-            g_launches += c->ff ? 3 + c->nf + (c->nf & 1) : 5;
+            g_launches += c->ff ? 1 + prf::graph_body_launches(c->ff, c->nf) : 5;
         } else {
             int rc = enqueue_iteration_plain(c, k);
             if (rc) return rc;
@@ -1397,6 +1397,18 @@ int pr_parareal_iter(pr_ctx* c, double* err_out)
         *err_out = c->h_pinned[0];
         return rc;
     }
+    return PR_OK;
+}
+
+int pr_set_force_step(pr_ctx* c, int cluster, int columns, int persistent)
+{
+    if (!c) return PR_EINVAL;
+    if (!c->ff) return cfail(c, PR_EINVAL, "the problem has no exterior force (pr_init_force)");
+    int rc = cluster > 0 ? pr_force_set_cluster(c->ff, cluster) : PR_OK;
+    if (rc == PR_OK) rc = pr_force_set_march(c->ff, columns);
+    if (rc == PR_OK) rc = pr_force_set_persistent(c->ff, persistent);
+    if (rc) return cfail(c, rc, "%s", c->ff->err.c_str());
+    c->descs_dirty = true;  // the captured iteration holds the old launches
     return PR_OK;
 }
 

@@ -236,3 +236,84 @@ def test_cluster_wider_than_its_ctas_threads(precision):
         pr.pr_force_destroy(b)
     Vo = O.v_project(kin, O.v_fine_run(kin, dt, n, O.v_lift(kin, U)), conserved=True)
     assert moment_rel_err(V, Vo) < (1e-12 if precision == pr.PR_FP64 else TOL_MIXED)
+
+
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW, pr.PR_BC_REFLECT])
+@pytest.mark.parametrize("nvx,nvp,cluster,march", [(64, 16, 2, 1), (64, 16, 2, 6), (48, 8, 6, 4), (32, 4, 16, 23)])
+def test_persistent_run_is_bitwise_the_stepwise_run(bc, nvx, nvp, cluster, march):
+    # all steps of a run in one launch, items waiting on their neighbour
+    # walks, against one launch per step
+    nx, L, n = 23, 7.0, 7
+    insts, _, initial = _problem(nx, nvx, nvp, L, bc, 1e-3, n_inst=3)
+    out = []
+    for mode in (0, 1):
+        b = pr.pr_force_create(insts, pr.PR_UPWIND, pr.PR_MIXED)
+        try:
+            pr.pr_force_set_cluster(b, cluster)
+            pr.pr_force_set_march(b, march)
+            pr.pr_force_set_persistent(b, mode)
+            for i, U in enumerate(initial):
+                pr.pr_force_set_initial(b, i, U)
+            pr.pr_force_run(b, 1)
+            pr.pr_force_run(b, n - 1)
+            out.append([(pr.pr_force_get_f(b, i), pr.pr_force_moments(b, i)) for i in range(3)])
+        finally:
+            pr.pr_force_destroy(b)
+    for (f, V), (fr, Vr) in zip(out[1], out[0]):
+        assert np.array_equal(f, fr)
+        assert np.array_equal(V, Vr)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_force_parareal_on_the_fused_step_matches_oracle(persistent):
+    # Algorithm 2 with the fused step for the fine propagator (one launch per
+    # slice run, or one persistent launch): the slices are the instances
+    nx, nvx, nvp, L, eps, T, N, K = 16, 32, 8, 6.0, 1e-2, 0.05, 6, 3
+    E = W.test3_force(nx)
+    U0 = _profile(nx)
+    k = O.VKin(nx=nx, nvx=nvx, nvp=nvp, L=L, x0=0.0, x1=2.0, eps=eps, E=E)
+    Uo, errs_o, _ = O.v_parareal(O.VParareal(kin=k, T=T, N=N), U0, K=K)
+    ctx = pr.pr_init_force(nx, 0.0, 2.0, pr.PR_BC_PERIODIC, nvx, nvp, L, eps, T, N, E, precision=pr.PR_MIXED)
+    try:
+        pr.pr_set_force_step(ctx, 2, 4, persistent)
+        pr.pr_set_initial(ctx, U0)
+        kd, errs = pr.pr_parareal_run(ctx, K)
+        for n in range(N + 1):
+            assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < TOL_MIXED, n
+    finally:
+        pr.pr_destroy(ctx)
+
+
+def test_persistent_dependency_wait_runs_out_and_object_stays_usable():
+    nx = 16
+    E = W.test3_force(nx)
+    inst = pr.ForceInstance(nx, 32, 8, 1e-3, E=E)
+    b = pr.pr_force_create([inst], pr.PR_UPWIND, pr.PR_MIXED)
+    fresh = pr.pr_force_create([inst], pr.PR_UPWIND, pr.PR_MIXED)
+    try:
+        for o in (b, fresh):
+            pr.pr_force_set_cluster(o, 2)
+            pr.pr_force_set_march(o, 4)
+            pr.pr_force_set_persistent(o, 1)
+        pr.pr_force_set_initial(b, 0, W.smooth_periodic(nx))
+        assert pr.pr_force_inject_wait_timeout(b, 20) == pr.PR_ETIMEOUT
+        assert "timed out" in pr.pr_force_last_error(b)
+        runs = []
+        for o in (b, fresh):
+            pr.pr_force_set_initial(o, 0, W.smooth_periodic(nx))
+            pr.pr_force_run(o, 3)
+            runs.append(pr.pr_force_moments(o, 0))
+        assert np.array_equal(runs[0], runs[1])
+    finally:
+        pr.pr_force_destroy(b)
+        pr.pr_force_destroy(fresh)
+
+
+def test_force_step_setting_needs_a_force_problem():
+    ctx = pr.pr_init(8, 0.0, 1.0, pr.PR_BC_PERIODIC, 4, 8.0, 1e-2, 0.1, 2)
+    try:
+        with pytest.raises(pr.PrError) as ei:
+            pr.pr_set_force_step(ctx, 0, 4, 1)
+        assert ei.value.code == pr.PR_EINVAL
+    finally:
+        pr.pr_destroy(ctx)
