@@ -513,7 +513,10 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
     const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
     T* outp = gout + (size_t)c0 * ldv + v0;
-#pragma unroll 1
+    // float64 steps two x cells per loop body (the window rotation becomes
+    // register renaming: +2 % measured); float32 one (unrolling spills there)
+    constexpr int XUNROLL = sizeof(T) == 8 ? 2 : 1;
+#pragma unroll XUNROLL
     for (int i = 0; i < ncols; ++i, outp += ldv) {
         T fs[V];
         if (H == 2) {
