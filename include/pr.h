@@ -399,8 +399,8 @@ int pr_force_set_threads(pr_force* b, int threads);
 
 /* Step kernel of the force path.  Two implementations give the same scheme:
  * the clustered step (a cluster of CTAs per x column: transport, exchange of
- * the moments of f* over distributed shared memory, relaxation) and, in mixed
- * precision with the upwind scheme, the fused single-pass step: the moments
+ * the moments of f* over distributed shared memory, relaxation) and, with
+ * the upwind scheme (either precision), the fused single-pass step: the moments
  * of f* follow from 17 sums per column of f^n (upwind half sums of v_x f,
  * end-row densities; the v_x fluxes telescope), which every step writes next
  * to f^{n+1}, so each cell is read, relaxed and written in one pass and a CTA

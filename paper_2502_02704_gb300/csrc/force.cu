@@ -223,22 +223,27 @@ __device__ __forceinline__ double rsqrt_nr(double x)
 // / (3 rho^2) with the numerator, which cancels when |u|^2 >> theta, formed
 // in double-float; the divisions and the root in float.  A non-positive rho
 // or theta raises PR_ENONPHYS when report is set.
-__device__ __forceinline__ void maxwell_params(FSharedT<double>& sh, double, bool report, int* status)
+__device__ __forceinline__ void maxwell_params_d(const double* tot, double* par, bool report, int* status)
 {
-    const double r = sh.tot[0], m1 = sh.tot[1], m2 = sh.tot[2], m3 = sh.tot[3], e2 = sh.tot[4];
+    const double r = tot[0], m1 = tot[1], m2 = tot[2], m3 = tot[3], e2 = tot[4];
     const double num = fma(r, e2, -(fma(m1, m1, fma(m2, m2, m3 * m3))));  // 3 rho^2 theta
     const bool ok = r > 0.0 && num > 0.0 && isfinite(r) && isfinite(num);
     if (!ok && report) atomicCAS(status, 0, ST_NONPHYS);
     const double ir = rcp_nr(r);
     const double th = ok ? num * (ir * ir) * (1.0 / 3.0) : 1.0;
     const double rs = ok ? rsqrt_nr(2.0 * 3.14159265358979323846 * th) : 0.0;
-    sh.par[0] = r;
-    sh.par[1] = m1 * ir;
-    sh.par[2] = m2 * ir;
-    sh.par[3] = m3 * ir;
-    sh.par[4] = th;
-    sh.par[5] = r * rs * rs * rs;
-    sh.par[6] = 0.5 * rcp_nr(th);
+    par[0] = r;
+    par[1] = m1 * ir;
+    par[2] = m2 * ir;
+    par[3] = m3 * ir;
+    par[4] = th;
+    par[5] = r * rs * rs * rs;
+    par[6] = 0.5 * rcp_nr(th);
+}
+
+__device__ __forceinline__ void maxwell_params(FSharedT<double>& sh, double, bool report, int* status)
+{
+    maxwell_params_d(sh.tot, sh.par, report, status);
 }
 
 __device__ __forceinline__ void maxwell_params_f(const DF* tot, float* fpar, float dv3, bool report, int* status)
@@ -678,7 +683,7 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
     cluster_wait();  // no CTA leaves while another may still read its shared memory
 }
 
-// ---- fused single-pass step (float, upwind): one CTA walks S columns ----
+// ---- fused single-pass step (upwind; float or double): one CTA walks S columns ----
 //
 // With upwind x fluxes the sums of phi f* over a column (phi = 1, v, |v|^2)
 // are linear in sums of f^n over columns c-1, c, c+1 (summation by parts):
@@ -704,33 +709,73 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
 // straddle v_x = 0), the next column's copy in flight during the pass.
 constexpr int NQ = 17;  // per (column, CTA): M[5], A+[5], A-[5], rho_0, rho_{nvx-1}
 
+// The partials and the moments of f* are accumulated in FuOps<T>::A: a
+// double-float pair in the float path (44 bits without the double pipe),
+// double in the double path; both 8 bytes, so one layout serves both.
+template <typename T>
+struct FuOps;
+template <>
+struct FuOps<float> {
+    using A = DF;
+    using T2 = float2;
+    static __device__ __forceinline__ A from(float x) { return DF{x, 0.0f}; }
+    static __device__ __forceinline__ A add(A a, A b) { return df_add(a, b); }
+    static __device__ __forceinline__ A sub(A a, A b) { return df_add(a, DF{-b.hi, -b.lo}); }
+    static __device__ __forceinline__ A scale(A a, float s) { return df_mul(a, DF{s, 0.0f}); }
+    static __device__ __forceinline__ float val(A a) { return a.hi + a.lo; }
+    static __device__ __forceinline__ double dval(A a) { return (double)a.hi + (double)a.lo; }
+    static __device__ __forceinline__ A ldcg(const A* p)
+    {
+        const float2 x = __ldcg(reinterpret_cast<const float2*>(p));
+        return DF{x.x, x.y};
+    }
+};
+template <>
+struct FuOps<double> {
+    using A = double;
+    using T2 = double2;
+    static __device__ __forceinline__ A from(double x) { return x; }
+    static __device__ __forceinline__ A add(A a, A b) { return a + b; }
+    static __device__ __forceinline__ A sub(A a, A b) { return a - b; }
+    static __device__ __forceinline__ A scale(A a, double s) { return a * s; }
+    static __device__ __forceinline__ double val(A a) { return a; }
+    static __device__ __forceinline__ double dval(A a) { return a; }
+    static __device__ __forceinline__ A ldcg(const A* p) { return __ldcg(p); }
+};
+
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+
 struct FuShared {
-    DF red[2][8][12];            // per-warp sums (<= 256 threads), by column parity
+    DF red[2][8][12];            // per-warp sums (<= 256 threads), by column parity (8-byte A)
     unsigned long long mbar[4];  // column slots 0..2; 3: failure-detection check
 };
 
-// Byte offsets of the walk's tables after FuShared (host and device).
+// Byte offsets of the walk's tables after FuShared (host and device); es is
+// the element size of f (4 or 8).
 struct FuLayout {
     size_t rs, tot, par, vxe, eyz, slots, total;
 };
 
-__host__ __device__ inline FuLayout fu_layout(int nvp, int R, int S)
+__host__ __device__ inline size_t fu_al16(size_t x) { return (x + 15) / 16 * 16; }
+
+__host__ __device__ inline FuLayout fu_layout(int nvp, int R, int S, int es)
 {
     FuLayout L;
-    size_t o = sizeof(FuShared);
-    L.rs = o;                                          // DF [(S+2)][NQ]: rank sums of columns i0-1 .. i0+S
-    o += (size_t)(S + 2) * NQ * sizeof(DF);
-    L.tot = o;                                         // DF [S][5]: P(f*) of each column
-    o += (size_t)S * 5 * sizeof(DF);
-    L.par = o;                                         // float [S][8]: Maxwellian parameters
-    o += (size_t)S * 8 * sizeof(float);
-    L.vxe = o;                                         // float2 [S][R]: (v_x, ex) of the CTA's rows
-    o += (size_t)S * R * 2 * sizeof(float);
-    L.eyz = o;                                         // float [S][2 nvp]: ey, ez
-    o += (size_t)S * 2 * nvp * sizeof(float);
+    size_t o = fu_al16(sizeof(FuShared));
+    L.rs = o;                                          // A [(S+2)][NQ]: rank sums of columns i0-1 .. i0+S
+    o = fu_al16(o + (size_t)(S + 2) * NQ * 8);
+    L.tot = o;                                         // A [S][5]: P(f*) of each column
+    o = fu_al16(o + (size_t)S * 5 * 8);
+    L.par = o;                                         // T [S][8]: Maxwellian parameters
+    o = fu_al16(o + (size_t)S * 8 * es);
+    L.vxe = o;                                         // T2 [S][R]: (v_x, b pref ex) of the CTA's rows
+    o = fu_al16(o + (size_t)S * R * 2 * es);
+    L.eyz = o;                                         // T [S][2 nvp]: ey, ez
+    o += (size_t)S * 2 * nvp * es;
     o = (o + 127) / 128 * 128;
-    L.slots = o;                                       // float [3][R+2][nvp^2]
-    o += (size_t)3 * (R + 2) * nvp * nvp * sizeof(float);
+    L.slots = o;                                       // T [3][R+2][nvp^2]
+    o += (size_t)3 * (R + 2) * nvp * nvp * es;
     L.total = o;
     return L;
 }
@@ -740,62 +785,74 @@ __device__ __forceinline__ void fence_proxy_async()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ DF df_scale(DF a, float s) { return df_mul(a, DF{s, 0.0f}); }
-__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
-
-// Sum over the C ranks (stride NQ) in the pairwise order of rank_sum.
-__device__ __forceinline__ DF part_rank_sum(const DF* __restrict__ p, int C)
+// Sum over the C ranks (stride NQ) in the pairwise order of rank_sum, read
+// past L1 (written by other CTAs of the same launch in the persistent run).
+template <typename T>
+__device__ __forceinline__ typename FuOps<T>::A part_rank_sum(const typename FuOps<T>::A* __restrict__ p, int C)
 {
-    DF v[16];
+    using O = FuOps<T>;
+    typename O::A v[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        v[r] = DF{0.0f, 0.0f};
-        if (r < C) {  // past L1: written by other CTAs of the same launch in the persistent run
-            const float2 x = __ldcg(reinterpret_cast<const float2*>(p + (size_t)r * NQ));
-            v[r] = DF{x.x, x.y};
-        }
-    }
+    for (int r = 0; r < 16; ++r) v[r] = r < C ? O::ldcg(p + (size_t)r * NQ) : O::from(T(0));
 #pragma unroll
     for (int w = 1; w < 16; w *= 2)
 #pragma unroll
-        for (int r = 0; r + w < 16; r += 2 * w) v[r] = df_add(v[r], v[r + w]);
+        for (int r = 0; r + w < 16; r += 2 * w) v[r] = O::add(v[r], v[r + w]);
     return v[0];
+}
+
+// Maxwellian parameters of a column from its P(f*) sums (without dv3): the
+// float path's double-float function, or the double path's.
+__device__ __forceinline__ void fu_params(const DF* tot, float* par, const FInst& I, bool report, int* status)
+{
+    maxwell_params_f(tot, par, I.fdv3, report, status);
+}
+__device__ __forceinline__ void fu_params(const double* tot, double* par, const FInst& I, bool report, int* status)
+{
+    double t[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) t[k] = tot[k] * I.dv3;
+    maxwell_params_d(t, par, report, status);
 }
 
 // Per-thread sums of f^{n+1} over the thread's rows: per lane sum f and
 // sum v_x f; per row (vs = the row's lane sum) sum v_x vs, v_x^2 vs, v_x^3 vs
 // and the first / last row's vs.
+template <typename T, int VEC>
 struct FuAcc {
-    float S0[4], T[4], R1, R2, R3, e0, en;
+    T S0[VEC], Tx[VEC], R1, R2, R3, e0, en;
 };
 
-__device__ __forceinline__ void fu_clear(FuAcc& s)
+template <typename T, int VEC>
+__device__ __forceinline__ void fu_clear(FuAcc<T, VEC>& s)
 {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) s.S0[l] = s.T[l] = 0.0f;
-    s.R1 = s.R2 = s.R3 = s.e0 = s.en = 0.0f;
+    for (int l = 0; l < VEC; ++l) s.S0[l] = s.Tx[l] = T(0);
+    s.R1 = s.R2 = s.R3 = s.e0 = s.en = T(0);
 }
 
 // Row sums without the end-row densities (rows inside the box).
-__device__ __forceinline__ float fu_row_in(FuAcc& s, const Pack<float, 4>& v, float vx)
+template <typename T, int VEC>
+__device__ __forceinline__ T fu_row_in(FuAcc<T, VEC>& s, const Pack<T, VEC>& v, T vx)
 {
-    float vs = 0.0f;
+    T vs = T(0);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < VEC; ++l) {
         s.S0[l] += v.x[l];
-        s.T[l] = fmaf(vx, v.x[l], s.T[l]);
+        s.Tx[l] = tfma(vx, v.x[l], s.Tx[l]);
         vs += v.x[l];
     }
-    const float vx2 = vx * vx;
-    s.R1 = fmaf(vx, vs, s.R1);
-    s.R2 = fmaf(vx2, vs, s.R2);
-    s.R3 = fmaf(vx2 * vx, vs, s.R3);
+    const T vx2 = vx * vx;
+    s.R1 = tfma(vx, vs, s.R1);
+    s.R2 = tfma(vx2, vs, s.R2);
+    s.R3 = tfma(vx2 * vx, vs, s.R3);
     return vs;
 }
 
-__device__ __forceinline__ void fu_row(FuAcc& s, const Pack<float, 4>& v, float vx, int r, int nvx)
+template <typename T, int VEC>
+__device__ __forceinline__ void fu_row(FuAcc<T, VEC>& s, const Pack<T, VEC>& v, T vx, int r, int nvx)
 {
-    const float vs = fu_row_in(s, v, vx);
+    const T vs = fu_row_in(s, v, vx);
     if (r == 0) s.e0 = vs;
     if (r == nvx - 1) s.en = vs;
 }
@@ -803,22 +860,24 @@ __device__ __forceinline__ void fu_row(FuAcc& s, const Pack<float, 4>& v, float 
 // CTA sums of the accumulators into the 17 partials of one column at dst
 // (threads < NQ write): M from every row; A into A+ (rows with v_x > 0) or A-
 // (the other CTAs); the end-row densities from the CTAs holding those rows.
-__device__ __forceinline__ void fu_reduce(const FuAcc& s, const float (&vy)[4], const float (&vz)[4],
-                                          const float (&vp2)[4], DF (*red)[12], bool posc, bool has0,
-                                          bool hasn, DF* __restrict__ dst)
+template <typename T, int VEC>
+__device__ __forceinline__ void fu_reduce(const FuAcc<T, VEC>& s, const T (&vy)[VEC], const T (&vz)[VEC],
+                                          const T (&vp2)[VEC], typename FuOps<T>::A (*red)[12], bool posc,
+                                          bool has0, bool hasn, typename FuOps<T>::A* __restrict__ dst)
 {
-    float val[12];
-    val[0] = val[2] = val[3] = val[4] = val[5] = val[7] = val[8] = val[9] = 0.0f;
+    using O = FuOps<T>;
+    T val[12];
+    val[0] = val[2] = val[3] = val[4] = val[5] = val[7] = val[8] = val[9] = T(0);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < VEC; ++l) {
         val[0] += s.S0[l];
         val[2] += vy[l] * s.S0[l];
         val[3] += vz[l] * s.S0[l];
         val[4] += vp2[l] * s.S0[l];
-        val[5] += s.T[l];
-        val[7] += vy[l] * s.T[l];
-        val[8] += vz[l] * s.T[l];
-        val[9] += vp2[l] * s.T[l];
+        val[5] += s.Tx[l];
+        val[7] += vy[l] * s.Tx[l];
+        val[8] += vz[l] * s.Tx[l];
+        val[9] += vp2[l] * s.Tx[l];
     }
     val[1] = s.R1;
     val[4] += s.R2;
@@ -830,8 +889,8 @@ __device__ __forceinline__ void fu_reduce(const FuAcc& s, const float (&vy)[4], 
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
         if (q >= 10 && !(q == 10 ? has0 : hasn)) continue;  // uniform over the CTA
-        const float v = warp_sum_t(val[q]);
-        if (lane == 0) red[w][q] = DF{v, 0.0f};
+        const T v = warp_sum_t(val[q]);
+        if (lane == 0) red[w][q] = O::from(v);
     }
     __syncthreads();
     if (threadIdx.x < NQ) {
@@ -841,76 +900,77 @@ __device__ __forceinline__ void fu_reduce(const FuAcc& s, const float (&vy)[4], 
         else if (q < 10) src = posc ? q : -1;
         else if (q < 15) src = posc ? -1 : q - 5;
         else src = q == 15 ? (has0 ? 10 : -1) : (hasn ? 11 : -1);
-        DF a{0.0f, 0.0f};
+        typename O::A a = O::from(T(0));
         if (src >= 0) {
             const int nw = (blockDim.x + 31) >> 5;
-            for (int k = 0; k < nw; ++k) a = df_add(a, red[k][src]);
+            for (int k = 0; k < nw; ++k) a = O::add(a, red[k][src]);
         }
         dst[q] = a;
     }
 }
 
 // Uniform per-column constants of the pass.
+template <typename T>
 struct FuCol {
-    float nu, gE, gM;   // dt/dx; dt/dv_x E/2 and dt/dv_x E_max/2
-    float a;            // f^{n+1} = a f* + ex ey ez (b M folded into the tables); 1 without collisions
-    float hE, hEm;      // E/2, E_max/2 (box-end rows)
-    float nuv;
+    T nu, gE, gM;   // dt/dx; dt/dv_x E/2 and dt/dv_x E_max/2
+    T a;            // f^{n+1} = a f* + ex ey ez (b M folded into the tables); 1 without collisions
+    T hE, hEm;      // E/2, E_max/2 (box-end rows)
+    T nuv;
 };
 
 // One column's pass over the thread's rows [ra, rb): f* (upwind x flux
 // against the neighbour slot, v_x Rusanov flux, combined on interior rows),
 // f^{n+1} stored with 16-byte stores, its sums accumulated.  POS: the rows
 // take the x flux from column c-1 (v_x > 0); BND: the CTA holds a box-end
-// row (zero v_x flux through +-L); NVPC: nvp^2 / 4 lanes per row when > 0.
-template <bool POS, bool BND, int NVPC>
-__device__ __forceinline__ void fu_pass(const float* __restrict__ cen, const float* __restrict__ nb,
-                                        float* __restrict__ out, const float2* __restrict__ vxe, int ra, int rb,
-                                        int r0, int nvx, int nvp2_rt, const FuCol& k, const float (&myz)[4],
-                                        FuAcc& acc)
+// row (zero v_x flux through +-L); NVPC: nvp when > 0.
+template <bool POS, bool BND, int NVPC, typename T, int VEC>
+__device__ __forceinline__ void fu_pass(const T* __restrict__ cen, const T* __restrict__ nb, T* __restrict__ out,
+                                        const typename FuOps<T>::T2* __restrict__ vxe, int ra, int rb, int r0,
+                                        int nvx, int nvp2_rt, const FuCol<T>& k, const T (&myz)[VEC],
+                                        FuAcc<T, VEC>& acc)
 {
     const int nvp2 = NVPC > 0 ? NVPC * NVPC : nvp2_rt;
-    Pack<float, 4> dnv, cv;
+    Pack<T, VEC> dnv, cv;
 #pragma unroll
-    for (int l = 0; l < 4; ++l) dnv.x[l] = 0.0f;
-    if (!BND || ra > 0) dnv = ldv<float, 4>(cen + (size_t)(ra - r0) * nvp2);
-    cv = ldv<float, 4>(cen + (size_t)(ra - r0 + 1) * nvp2);
-    const float* cp = cen + (size_t)(ra - r0 + 2) * nvp2;  // row r+1
-    const float* np = nb + (size_t)(ra - r0 + 1) * nvp2;   // neighbour row r
-    float* op = out + (size_t)ra * nvp2;
+    for (int l = 0; l < VEC; ++l) dnv.x[l] = T(0);
+    if (!BND || ra > 0) dnv = ldv<T, VEC>(cen + (size_t)(ra - r0) * nvp2);
+    cv = ldv<T, VEC>(cen + (size_t)(ra - r0 + 1) * nvp2);
+    const T* cp = cen + (size_t)(ra - r0 + 2) * nvp2;  // row r+1
+    const T* np = nb + (size_t)(ra - r0 + 1) * nvp2;   // neighbour row r
+    T* op = out + (size_t)ra * nvp2;
 #pragma unroll 4
     for (int r = ra; r < rb; ++r) {
-        Pack<float, 4> up;
-        if (!BND || r < nvx - 1) up = ldv<float, 4>(cp);
+        Pack<T, VEC> up;
+        if (!BND || r < nvx - 1) up = ldv<T, VEC>(cp);
         else {
 #pragma unroll
-            for (int l = 0; l < 4; ++l) up.x[l] = 0.0f;
+            for (int l = 0; l < VEC; ++l) up.x[l] = T(0);
         }
-        const float2 ve = vxe[r - r0];
-        const float vx = ve.x, nvx_ = k.nu * ve.x;
-        const Pack<float, 4> x1 = ldv<float, 4>(np);
-        Pack<float, 4> v;
+        const typename FuOps<T>::T2 ve = vxe[r - r0];
+        const T vx = ve.x, nvx_ = k.nu * ve.x;
+        const Pack<T, VEC> x1 = ldv<T, VEC>(np);
+        Pack<T, VEC> v;
         if (!BND || (r > 0 && r < nvx - 1)) {
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float cc = cv.x[l], u = up.x[l], d = dnv.x[l];
-                float fs = fmaf(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
-                fs = fmaf(-k.gE, u - d, fs);
-                fs = fmaf(k.gM, fmaf(-2.0f, cc, u + d), fs);
-                v.x[l] = fmaf(k.a, fs, ve.y * myz[l]);
+            for (int l = 0; l < VEC; ++l) {
+                const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                T fs = tfma(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
+                fs = tfma(-k.gE, u - d, fs);
+                fs = tfma(k.gM, tfma(T(-2), cc, u + d), fs);
+                v.x[l] = tfma(k.a, fs, ve.y * myz[l]);
             }
         } else {
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float cc = cv.x[l], u = up.x[l], d = dnv.x[l];
-                const float Gr = r < nvx - 1 ? k.hE * (cc + u) - k.hEm * (u - cc) : 0.0f;
-                const float Gl = r > 0 ? k.hE * (d + cc) - k.hEm * (cc - d) : 0.0f;
-                float fs = fmaf(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
-                fs = fmaf(-k.nuv, Gr - Gl, fs);
-                v.x[l] = fmaf(k.a, fs, ve.y * myz[l]);
+            for (int l = 0; l < VEC; ++l) {
+                const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                const T Gr = r < nvx - 1 ? k.hE * (cc + u) - k.hEm * (u - cc) : T(0);
+                const T Gl = r > 0 ? k.hE * (d + cc) - k.hEm * (cc - d) : T(0);
+                T fs = tfma(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
+                fs = tfma(-k.nuv, Gr - Gl, fs);
+                v.x[l] = tfma(k.a, fs, ve.y * myz[l]);
             }
         }
-        stv<float, 4>(op, v);
+        stv<T, VEC>(op, v);
         if (BND) fu_row(acc, v, vx, r, nvx);
         else fu_row_in(acc, v, vx);
         dnv = cv;
@@ -944,13 +1004,15 @@ __device__ __forceinline__ void fu_init_mbar(unsigned char* fsm, int poison)
 // `phase` carries their parities from one walk to the next (every copy a walk
 // issues, it also waits for).  Ends after the last column's partials are
 // written by threads < 17 (no barrier after them).
-template <int NVPC>
+template <typename T, int NVPC>
 __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, const FGeom& g, const int* __restrict__ cur,
                                            int b, int wk, int rank, int C, int step, int* __restrict__ status,
                                            long long wait_ns, uint32_t& phase, unsigned char* fsm)
 {
-    using T = float;
-    constexpr int VEC = 4;
+    using O = FuOps<T>;
+    using A = typename O::A;
+    using T2 = typename O::T2;
+    constexpr int VEC = 16 / (int)sizeof(T);
     const FInst& I = insts[b];
     const int S = g.march, nx = I.nx, bc = I.bc;
     const int i0 = wk * S, i1 = min(i0 + S, nx), W = i1 - i0;
@@ -963,12 +1025,13 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
     const size_t slot_elems = (size_t)(R + 2) * nvp2;
 
     FuShared& sh = *reinterpret_cast<FuShared*>(fsm);
-    const FuLayout lay = fu_layout(nvp, R, S);
-    DF* rs = reinterpret_cast<DF*>(fsm + lay.rs);
-    DF* tot = reinterpret_cast<DF*>(fsm + lay.tot);
-    float* par = reinterpret_cast<float*>(fsm + lay.par);
-    float2* vxe = reinterpret_cast<float2*>(fsm + lay.vxe);
-    float* eyz = reinterpret_cast<float*>(fsm + lay.eyz);
+    A (*red)[8][12] = reinterpret_cast<A (*)[8][12]>(&sh.red[0][0][0]);
+    const FuLayout lay = fu_layout(nvp, R, S, (int)sizeof(T));
+    A* rs = reinterpret_cast<A*>(fsm + lay.rs);
+    A* tot = reinterpret_cast<A*>(fsm + lay.tot);
+    T* par = reinterpret_cast<T*>(fsm + lay.par);
+    T2* vxe = reinterpret_cast<T2*>(fsm + lay.vxe);
+    T* eyz = reinterpret_cast<T*>(fsm + lay.eyz);
     T* slots = reinterpret_cast<T*>(fsm + lay.slots);
     const uint32_t mbar0 = smem_addr(&sh.mbar[0]);
 
@@ -981,8 +1044,8 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
     const int bufi = cur[b] ^ (step & 1);
     const T* __restrict__ fin = static_cast<const T*>(I.f[bufi]);
     T* __restrict__ fout = static_cast<T*>(I.f[bufi ^ 1]);
-    const DF* __restrict__ pin = static_cast<const DF*>(I.part[bufi]);
-    DF* __restrict__ pout = static_cast<DF*>(I.part[bufi ^ 1]);
+    const A* __restrict__ pin = static_cast<const A*>(I.part[bufi]);
+    A* __restrict__ pout = static_cast<A*>(I.part[bufi ^ 1]);
     const int ha = max(r0 - 1, 0), hb = min(r1 + 1, nvx);
 
     const int cfirst = posc ? i0 - 1 : i0, clast = posc ? i1 - 1 : i1;
@@ -1028,49 +1091,51 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
         const int j = t / NQ, qq = t - j * NQ;
         bool mir;
         const int src = ghost_col(i0 - 1 + j, nx, bc, &mir);
-        rs[t] = part_rank_sum(pin + (size_t)src * C * NQ + qq, C);
+        rs[t] = part_rank_sum<T>(pin + (size_t)src * C * NQ + qq, C);
     }
     __syncthreads();
-    const float nu = I.fnu, nuv = I.fnuv, Emax = I.fEmax;
+    const T nu = scal<T>(I.nu, I.fnu), nuv = scal<T>(I.nuv, I.fnuv), Emax = scal<T>(I.Emax, I.fEmax);
     for (int t5 = threadIdx.x; t5 < W * 5; t5 += blockDim.x) {
         const int j = t5 / 5, k = t5 - 5 * j, c = i0 + j;
-        const DF* Mc = rs + (size_t)(j + 1) * NQ;
-        const DF* Lc = rs + (size_t)j * NQ;
-        const DF* Rc = rs + (size_t)(j + 2) * NQ;
-        const float sk = k == 1 ? 1.0f : -1.0f;
+        const A* Mc = rs + (size_t)(j + 1) * NQ;
+        const A* Lc = rs + (size_t)j * NQ;
+        const A* Rc = rs + (size_t)(j + 2) * NQ;
+        const T sk = k == 1 ? T(1) : T(-1);
         const bool mirL = bc == 2 && c == 0, mirR = bc == 2 && c == nx - 1;
-        const DF Apl = mirL ? df_scale(Lc[10 + k], sk) : Lc[5 + k];  // A+ of column c-1
-        const DF Amr = mirR ? df_scale(Rc[5 + k], sk) : Rc[10 + k];  // A- of column c+1
-        const DF fl = df_add(df_sub(Mc[5 + k], Apl), df_sub(Amr, Mc[10 + k]));
-        DF t = df_sub(Mc[k], df_scale(fl, nu));
+        const A Apl = mirL ? O::scale(Lc[10 + k], sk) : Lc[5 + k];  // A+ of column c-1
+        const A Amr = mirR ? O::scale(Rc[5 + k], sk) : Rc[10 + k];  // A- of column c+1
+        const A fl = O::add(O::sub(Mc[5 + k], Apl), O::sub(Amr, Mc[10 + k]));
+        A t = O::sub(Mc[k], O::scale(fl, nu));
         if (k == 1 || k == 4) {
-            const float dvx = (float)I.dvx, Lb = (float)I.L, E = I.Ef[c];
-            const float M0 = Mc[0].hi + Mc[0].lo, M1 = Mc[1].hi + Mc[1].lo;
-            const float e0 = Mc[15].hi + Mc[15].lo, en = Mc[16].hi + Mc[16].lo;
-            const float Q = k == 1 ? -dvx * (E * (M0 - 0.5f * (e0 + en)) - Emax * 0.5f * (en - e0))
-                                   : -dvx * (E * (2.0f * M1 - Lb * (en - e0)) - Emax * (Lb * (e0 + en) - dvx * M0));
-            t = df_sub(t, DF{nuv * Q, 0.0f});
+            const T dvx = (T)I.dvx, Lb = (T)I.L, E = scal<T>(I.E[c], I.Ef[c]);
+            const T M0 = O::val(Mc[0]), M1 = O::val(Mc[1]);
+            const T e0 = O::val(Mc[15]), en = O::val(Mc[16]);
+            const T Q = k == 1 ? -dvx * (E * (M0 - T(0.5) * (e0 + en)) - Emax * T(0.5) * (en - e0))
+                               : -dvx * (E * (T(2) * M1 - Lb * (en - e0)) - Emax * (Lb * (e0 + en) - dvx * M0));
+            t = O::sub(t, O::from(nuv * Q));
         }
         tot[j * 5 + k] = t;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < W; j += blockDim.x)
-        maxwell_params_f(tot + j * 5, par + j * 8, I.fdv3, I.collide && rank == 0, status);
+    for (int j = threadIdx.x; j < W; j += blockDim.x) fu_params(tot + j * 5, par + j * 8, I, I.collide && rank == 0, status);
     __syncthreads();
-    // per column: (v_x, ex) of the rows and ey, ez, with b pref folded into
-    // ex; zero tables without collisions
+    // per column: (v_x, b pref ex) of the rows and ey, ez; zero tables
+    // without collisions
     const bool collide = I.collide != 0;
-    const T bb = I.fb;
+    const T bb = scal<T>(I.b, I.fb);
     for (int t = threadIdx.x; t < W * (nr + 2 * nvp); t += blockDim.x) {
         const int j = t / (nr + 2 * nvp), k = t - j * (nr + 2 * nvp);
-        const float* pj = par + j * 8;
+        const T* pj = par + j * 8;
         if (k < nr) {
-            const float vx = vt[r0 + k], cx = vx - pj[1];
-            vxe[j * R + k] = make_float2(vx, collide ? bb * pj[5] * texp(-cx * cx * pj[6]) : 0.0f);
+            const T vx = vt[r0 + k], cx = vx - pj[1];
+            T2 e;
+            e.x = vx;
+            e.y = collide ? bb * pj[5] * texp(-cx * cx * pj[6]) : T(0);
+            vxe[j * R + k] = e;
         } else {
             const int m = k - nr < nvp ? k - nr : k - nr - nvp;
-            const float cc = vt[nvx + m * nvp] - (k - nr < nvp ? pj[2] : pj[3]);
-            eyz[j * 2 * nvp + (k - nr)] = collide ? texp(-cc * cc * pj[6]) : 0.0f;
+            const T cc = vt[nvx + m * nvp] - (k - nr < nvp ? pj[2] : pj[3]);
+            eyz[j * 2 * nvp + (k - nr)] = collide ? texp(-cc * cc * pj[6]) : T(0);
         }
     }
     T vy[VEC], vz[VEC], vp2[VEC];
@@ -1090,12 +1155,12 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
             }
         }
     }
-    FuCol kc;
+    FuCol<T> kc;
     kc.nu = nu;
     kc.nuv = nuv;
     kc.hEm = T(0.5) * Emax;
     kc.gM = nuv * kc.hEm;
-    kc.a = collide ? I.fa : 1.0f;
+    kc.a = collide ? scal<T>(I.a, I.fa) : T(1);
     const bool has0 = r0 == 0, hasn = r1 == nvx, bnd = has0 || hasn;
     __syncthreads();  // tables and thread-staged slots visible
 
@@ -1117,19 +1182,19 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
         }
         const T* cen = slots + (size_t)sc * slot_elems + jp;
         const T* nb = slots + (size_t)sn * slot_elems + jp;
-        kc.hE = T(0.5) * I.Ef[c];
+        kc.hE = T(0.5) * scal<T>(I.E[c], I.Ef[c]);
         kc.gE = nuv * kc.hE;
         T myz[VEC];
         {
-            const float* ey = eyz + j * 2 * nvp;
+            const T* ey = eyz + j * 2 * nvp;
 #pragma unroll
             for (int l = 0; l < VEC; ++l) myz[l] = ey[jy[l]] * ey[nvp + jz[l]];
         }
-        FuAcc acc;
+        FuAcc<T, VEC> acc;
         fu_clear(acc);
         if (active) {
             T* out = fout + (size_t)c * ncol + jp;
-            const float2* ve = vxe + j * R;
+            const T2* ve = vxe + j * R;
             if (posc) {
                 if (bnd) fu_pass<true, true, NVPC>(cen, nb, out, ve, ra, rb, r0, nvx, nvp2, kc, myz, acc);
                 else fu_pass<true, false, NVPC>(cen, nb, out, ve, ra, rb, r0, nvx, nvp2, kc, myz, acc);
@@ -1140,7 +1205,7 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
         }
         // the 17 sums of f^{n+1} of this column; the reduction's barrier ends
         // every read of this column's slots
-        fu_reduce(acc, vy, vz, vp2, sh.red[c & 1], posc, has0, hasn, pout + ((size_t)c * C + rank) * NQ);
+        fu_reduce(acc, vy, vz, vp2, red[c & 1], posc, has0, hasn, pout + ((size_t)c * C + rank) * NQ);
         {
             const int nc = posc ? c + 2 : c + 3;
             if (nc <= clast && load(nc)) pend |= 1u << slot_of(nc);
@@ -1149,8 +1214,8 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
 }
 
 // One launch per step: CTA (rank, walk, instance).
-template <int NVPC>
-__global__ void __launch_bounds__(256, 3)
+template <typename T, int NVPC>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
               int step, int* __restrict__ status, long long wait_ns, int poison)
 {
@@ -1163,7 +1228,7 @@ k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict
         if (!mbar_wait(mb, wait_ns)) atomicCAS(status, 0, ST_TIMEOUT);
     }
     uint32_t phase = 0;
-    fused_walk<NVPC>(insts, g, cur, b, blockIdx.y, blockIdx.x, gridDim.x, step, status, wait_ns, phase, fsm);
+    fused_walk<T, NVPC>(insts, g, cur, b, blockIdx.y, blockIdx.x, gridDim.x, step, status, wait_ns, phase, fsm);
 }
 
 // Wait (bounded by limit_ns) until the counter reaches target; acquire
@@ -1190,8 +1255,8 @@ __device__ __forceinline__ bool wait_count(const int* p, int target, long long l
 // ticket, [1 + b walks + w] done counts (zeroed before the launch).
 // poison (failure-detection check): the waits of step 1 ask for a count no
 // walk reaches, so they run out after wait_ns.
-template <int NVPC>
-__global__ void __launch_bounds__(256, 3)
+template <typename T, int NVPC>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
                   int nsteps, int* __restrict__ sync, int* __restrict__ status, long long wait_ns, int poison)
 {
@@ -1230,7 +1295,7 @@ k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __rest
             asm volatile("fence.proxy.async.global;" ::: "memory");  // the bulk copies read what others wrote
         }
         __syncthreads();
-        fused_walk<NVPC>(insts, g, cur, b, wk, rank, C, k, status, wait_ns, phase, fsm);
+        fused_walk<T, NVPC>(insts, g, cur, b, wk, rank, C, k, status, wait_ns, phase, fsm);
         __syncthreads();  // every store of this walk issued
         if (threadIdx.x == 0) {
             __threadfence();
@@ -1242,52 +1307,58 @@ k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __rest
 // Partials (the 17 column sums of the fused step) of the current state of
 // the active instances: one CTA per (rank, column, instance), rows read
 // straight from memory with 16-byte loads.
+template <typename T>
 __global__ void __launch_bounds__(256)
 k_force_sums(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, const int* __restrict__ cur)
 {
+    using O = FuOps<T>;
+    constexpr int VEC = 16 / (int)sizeof(T);
     const int b = blockIdx.z;
     if (b < act->begin || b >= act->end) return;
     const FInst& I = insts[b];
     const int i = blockIdx.y, rank = blockIdx.x, C = gridDim.x;
     const int nvx = g.nvx, nvp = g.nvp, nvp2 = nvp * nvp;
     const int R = g.rows, r0 = rank * R, r1 = min(r0 + R, nvx), nr = r1 - r0;
-    const int Lr = nvp2 / 4, G = g.groups;
-    const int q = threadIdx.x % Lr, grp = threadIdx.x / Lr, jp = q * 4;
+    const int Lr = nvp2 / VEC, G = g.groups;
+    const int q = threadIdx.x % Lr, grp = threadIdx.x / Lr, jp = q * VEC;
     const int Rg = (nr + G - 1) / G;
     const int ra = r0 + grp * Rg, rb = min(ra + Rg, r1);
     const bool active = grp < G && ra < rb;
-    __shared__ DF red[8][12];
+    __shared__ typename O::A red[8][12];
     const int bi = cur[b];
-    const float* f = static_cast<const float*>(I.f[bi]) + (size_t)i * g.ncol + jp;
-    const float* vt = static_cast<const float*>(I.vtab);
-    float vy[4], vz[4], vp2[4];
+    const T* f = static_cast<const T*>(I.f[bi]) + (size_t)i * g.ncol + jp;
+    const T* vt = static_cast<const T*>(I.vtab);
+    T vy[VEC], vz[VEC], vp2[VEC];
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        vy[l] = active ? vt[nvx + jp + l] : 0.0f;
-        vz[l] = active ? vt[nvx + nvp2 + jp + l] : 0.0f;
-        vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : 0.0f;
+    for (int l = 0; l < VEC; ++l) {
+        vy[l] = active ? vt[nvx + jp + l] : T(0);
+        vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
+        vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
     }
-    FuAcc acc;
+    FuAcc<T, VEC> acc;
     fu_clear(acc);
     if (active)
-        for (int r = ra; r < rb; ++r) fu_row(acc, ldv<float, 4>(f + (size_t)r * nvp2), vt[r], r, nvx);
+        for (int r = ra; r < rb; ++r) fu_row(acc, ldv<T, VEC>(f + (size_t)r * nvp2), vt[r], r, nvx);
     fu_reduce(acc, vy, vz, vp2, red, r0 >= I.hpos, r0 == 0, r1 == nvx,
-              static_cast<DF*>(I.part[bi]) + ((size_t)i * C + rank) * NQ);
+              static_cast<typename O::A*>(I.part[bi]) + ((size_t)i * C + rank) * NQ);
 }
 
 // Conserved moments (Eq. 18) of the current state from its partials, into
 // Ucur and Uout: one thread per (moment, column) of each active instance.
+template <typename T>
 __global__ void k_force_finalize(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act,
                                  const int* __restrict__ cur, int nx)
 {
+    using O = FuOps<T>;
     const int b = act->begin + blockIdx.y;
     if (b >= act->end) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 5 * nx) return;
     const FInst& I = insts[b];
     const int k = t / nx, i = t - k * nx;
-    const DF s = part_rank_sum(static_cast<const DF*>(I.part[cur[b]]) + (size_t)i * g.C * NQ + k, g.C);
-    double u = ((double)s.hi + (double)s.lo) * I.dv3;
+    const typename O::A s =
+        part_rank_sum<T>(static_cast<const typename O::A*>(I.part[cur[b]]) + (size_t)i * g.C * NQ + k, g.C);
+    double u = O::dval(s) * I.dv3;
     if (k == 4) u *= 0.5;  // energy = 1/2 sum |v|^2 f dv
     I.Ucur[k * nx + i] = u;
     if (I.Uout) I.Uout[k * nx + i] = u;
@@ -1425,11 +1496,14 @@ void* pick_step(int precision, int scheme, int vec)
 
 }  // namespace
 
-size_t force_fused_smem(int nvp, int rows, int walk) { return fu_layout(nvp, rows, walk).total; }
+size_t force_fused_smem(int precision, int nvp, int rows, int walk)
+{
+    return fu_layout(nvp, rows, walk, precision == 0 ? 8 : 4).total;
+}
 
 bool force_fused_fits(int precision, int scheme, const FGeom& g)
 {
-    return precision == 1 && scheme == 0 && g.bulk && g.vec == 4 && g.threads <= 256 && g.C <= 16;
+    return scheme == 0 && g.bulk && g.vec == (precision == 0 ? 2 : 4) && g.threads <= 256 && g.C <= 16;
 }
 
 int force_partials_per_column(const FGeom& g) { return g.C * NQ; }
@@ -1477,9 +1551,14 @@ cudaError_t prepare_force_kernels(int max_smem)
                                          max_smem - (int)fa.sharedSizeBytes);
                 cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             }
-    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<0>), reinterpret_cast<const void*>(&k_force_fused<16>),
-                           reinterpret_cast<const void*>(&k_force_fused_run<0>),
-                           reinterpret_cast<const void*>(&k_force_fused_run<16>)}) {
+    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<float, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused<float, 16>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<float, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<float, 16>),
+                           reinterpret_cast<const void*>(&k_force_fused<double, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused<double, 16>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<double, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<double, 16>)}) {
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
@@ -1494,10 +1573,13 @@ cudaError_t prepare_force_kernels(int max_smem)
     return cudaGetLastError();
 }
 
-int force_fused_occupancy(int threads, size_t smem, int* per_sm)
+int force_fused_occupancy(int precision, int threads, size_t smem, int* per_sm)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fused<0>, threads, smem) != cudaSuccess) {
+    const cudaError_t e =
+        precision == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fused<double, 0>, threads, smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fused<float, 0>, threads, smem);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
@@ -1536,8 +1618,15 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
 {
     if (g.march > 0) {
         dim3 grid(g.C, (nx + g.march - 1) / g.march, n_inst);
-        if (g.nvp == 16) k_force_fused<16><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
-        else k_force_fused<0><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+        if (precision == 0) {
+            if (g.nvp == 16)
+                k_force_fused<double, 16><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+            else k_force_fused<double, 0><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+        } else {
+            if (g.nvp == 16)
+                k_force_fused<float, 16><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+            else k_force_fused<float, 0><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+        }
         return cudaGetLastError();
     }
     void* fn = pick_step(precision, scheme, g.vec);
@@ -1559,30 +1648,44 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-cudaError_t launch_force_fused_run(const FInst* insts, const FGeom& g, int n_inst, const Active* act, int* cur,
-                                   int nsteps, int* sync, int sync_words, int* status, size_t smem, cudaStream_t s,
-                                   int ctas, long long wait_ns, int poison)
+cudaError_t launch_force_fused_run(int precision, const FInst* insts, const FGeom& g, int n_inst, const Active* act,
+                                   int* cur, int nsteps, int* sync, int sync_words, int* status, size_t smem,
+                                   cudaStream_t s, int ctas, long long wait_ns, int poison)
 {
     cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * (size_t)sync_words, s);
     if (e != cudaSuccess || nsteps <= 0) return e;
-    if (g.nvp == 16)
-        k_force_fused_run<16><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status, wait_ns, poison);
-    else k_force_fused_run<0><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status, wait_ns, poison);
+    if (precision == 0) {
+        if (g.nvp == 16)
+            k_force_fused_run<double, 16><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
+                                                                       wait_ns, poison);
+        else
+            k_force_fused_run<double, 0><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
+                                                                      wait_ns, poison);
+    } else {
+        if (g.nvp == 16)
+            k_force_fused_run<float, 16><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
+                                                                      wait_ns, poison);
+        else
+            k_force_fused_run<float, 0><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
+                                                                     wait_ns, poison);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_force_sums(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
-                              const int* cur, cudaStream_t s)
+cudaError_t launch_force_sums(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                              const Active* act, const int* cur, cudaStream_t s)
 {
-    k_force_sums<<<dim3(g.C, nx, n_inst), g.threads, 0, s>>>(insts, g, act, cur);
+    if (precision == 0) k_force_sums<double><<<dim3(g.C, nx, n_inst), g.threads, 0, s>>>(insts, g, act, cur);
+    else k_force_sums<float><<<dim3(g.C, nx, n_inst), g.threads, 0, s>>>(insts, g, act, cur);
     return cudaGetLastError();
 }
 
-cudaError_t launch_force_finalize(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
-                                  const int* cur, cudaStream_t s)
+cudaError_t launch_force_finalize(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                                  const Active* act, const int* cur, cudaStream_t s)
 {
     dim3 grid((5 * nx + 127) / 128, n_inst);
-    k_force_finalize<<<grid, 128, 0, s>>>(insts, g, act, cur, nx);
+    if (precision == 0) k_force_finalize<double><<<grid, 128, 0, s>>>(insts, g, act, cur, nx);
+    else k_force_finalize<float><<<grid, 128, 0, s>>>(insts, g, act, cur, nx);
     return cudaGetLastError();
 }
 

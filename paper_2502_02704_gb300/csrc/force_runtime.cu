@@ -130,9 +130,9 @@ bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk
         if (I.hpos < b->nvx && I.hpos % g->rows != 0) return false;
     const size_t optin = (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin) - 1024;
     auto resident = [&](int S) {
-        const size_t sm = prk::force_fused_smem(b->nvp, g->rows, S);
+        const size_t sm = prk::force_fused_smem(b->precision, b->nvp, g->rows, S);
         int per_sm = 0;
-        if (sm > optin || prk::force_fused_occupancy(g->threads, sm, &per_sm) != 0) return 0;
+        if (sm > optin || prk::force_fused_occupancy(b->precision, g->threads, sm, &per_sm) != 0) return 0;
         return per_sm;
     };
     const int per1 = resident(1);
@@ -149,7 +149,7 @@ bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk
     S = std::max<long long>(1, std::min<long long>(S, cap));
     const long long walks = (b->nx + S - 1) / S;
     S = (b->nx + walks - 1) / walks;
-    const size_t sm = prk::force_fused_smem(b->nvp, g->rows, (int)S);
+    const size_t sm = prk::force_fused_smem(b->precision, b->nvp, g->rows, (int)S);
     if (resident((int)S) < 1) return false;
     g->march = (int)S;
     *out = gg;
@@ -170,7 +170,7 @@ int default_fused_cluster(const pr_force* b)
         prk::FGeom g;
         size_t sm;
         if (!fused_geometry(b, C, b->max_threads, 1, &g, &sm)) continue;
-        if (prk::force_fused_smem(b->nvp, g.rows, std::min(8, b->nx)) <= half) return C;
+        if (prk::force_fused_smem(b->precision, b->nvp, g.rows, std::min(8, b->nx)) <= half) return C;
         if (!any) any = C;
     }
     return any;
@@ -180,7 +180,7 @@ int default_fused_cluster(const pr_force* b)
 int fused_resident(const pr_force* b)
 {
     int per_sm = 0;
-    if (prk::force_fused_occupancy(b->g.threads, b->smem, &per_sm) != 0) return 0;
+    if (prk::force_fused_occupancy(b->precision, b->g.threads, b->smem, &per_sm) != 0) return 0;
     return per_sm * dev_attr(cudaDevAttrMultiProcessorCount);
 }
 
@@ -504,7 +504,7 @@ static int enqueue_steps(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s
     const int n_inst = b->n;
     const bool fused = b->g.march > 0;
     if (fused && nsteps > 0 && std::find(b->sums_ok.begin() + b0, b->sums_ok.begin() + b1, 0) != b->sums_ok.begin() + b1) {
-        FCUDA(b, prk::launch_force_sums(b->d_inst, b->g, b->nx, n_inst, b->d_active, b->d_cur, s));
+        FCUDA(b, prk::launch_force_sums(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->nx, n_inst, b->d_active, b->d_cur, s));
         pr_internal_count_launches(1);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -517,7 +517,7 @@ static int enqueue_steps(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s
         const long long walks = (b->nx + b->g.march - 1) / b->g.march;
         const long long items = (long long)(b1 - b0) * walks * b->g.C * nsteps;
         const int ctas = (int)std::min<long long>(fused_resident(b), items);
-        FCUDA(b, prk::launch_force_fused_run(b->d_inst, b->g, n_inst, b->d_active, b->d_cur, nsteps, b->d_fsync,
+        FCUDA(b, prk::launch_force_fused_run(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, n_inst, b->d_active, b->d_cur, nsteps, b->d_fsync,
                                              b->fsync_words, b->d_status, b->smem, s, ctas));
         pr_internal_count_launches(1);
     } else {
@@ -534,7 +534,7 @@ static int enqueue_steps(pr_force* b, int b0, int b1, int nsteps, cudaStream_t s
         b->pending.push_back({e0, e1, nsteps});
     }
     if (fused && nsteps > 0) {
-        FCUDA(b, prk::launch_force_finalize(b->d_inst, b->g, b->nx, n_inst, b->d_active, b->d_cur, s));
+        FCUDA(b, prk::launch_force_finalize(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->nx, n_inst, b->d_active, b->d_cur, s));
         pr_internal_count_launches(1);
     }
     std::fill(b->sums_ok.begin() + b0, b->sums_ok.begin() + b1, fused ? 1 : 0);
@@ -580,13 +580,13 @@ cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cu
                 ? prk::launch_force_lift_ce(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s)
                 : prk::launch_force_lift(p, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, b->d_status, s);
     const bool fused = b->g.march > 0 && nsteps > 0;
-    if (e == cudaSuccess && fused) e = prk::launch_force_sums(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
+    if (e == cudaSuccess && fused) e = prk::launch_force_sums(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
     if (fused && fused_persistent(b, b->n, nsteps)) {
         const long long walks = (b->nx + b->g.march - 1) / b->g.march;
         const long long items = (long long)b->n * walks * b->g.C * nsteps;
         const int ctas = (int)std::min<long long>(fused_resident(b), items);
         if (e == cudaSuccess)
-            e = prk::launch_force_fused_run(b->d_inst, b->g, b->n, b->d_active, b->d_cur, nsteps, b->d_fsync,
+            e = prk::launch_force_fused_run(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->n, b->d_active, b->d_cur, nsteps, b->d_fsync,
                                             b->fsync_words, b->d_status, b->smem, s, ctas);
     } else
         for (int k = 0; e == cudaSuccess && k < nsteps; ++k)
@@ -594,7 +594,7 @@ cudaError_t enqueue_graph_body(pr_force* b, const int* dk, int N, int nsteps, cu
                                        k == nsteps - 1, b->d_status, b->smem, s);
     if (e == cudaSuccess) e = prk::launch_force_advance(b->d_active, b->d_cur, nsteps, b->n, s);
     if (e == cudaSuccess && fused)
-        e = prk::launch_force_finalize(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
+        e = prk::launch_force_finalize(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s);
     std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);  // replays change the states behind the host's back
     return e;
 }
@@ -895,14 +895,14 @@ int pr_force_inject_wait_timeout(pr_force* b, int wait_ms)
     FCUDA(b, cudaStreamSynchronize(s));
     FCUDA(b, set_active(b, 0, b->n, s));
     if (b->g.march > 0) {  // the fused step reads the partials of the current states
-        FCUDA(b, prk::launch_force_sums(b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s));
+        FCUDA(b, prk::launch_force_sums(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->nx, b->n, b->d_active, b->d_cur, s));
         pr_internal_count_launches(1);
     }
     if (b->g.march > 0 && b->persist_req == 1) {
         // a two-step persistent run whose step-1 dependency waits run out
         const long long walks = (b->nx + b->g.march - 1) / b->g.march;
         const int ctas = (int)std::min<long long>(fused_resident(b), 2LL * b->n * walks * b->g.C);
-        FCUDA(b, prk::launch_force_fused_run(b->d_inst, b->g, b->n, b->d_active, b->d_cur, 2, b->d_fsync,
+        FCUDA(b, prk::launch_force_fused_run(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->g, b->n, b->d_active, b->d_cur, 2, b->d_fsync,
                                              b->fsync_words, b->d_status, b->smem, s, ctas,
                                              (long long)wait_ms * 1000000LL, 1));
         pr_internal_count_launches(1);

@@ -111,7 +111,7 @@ struct FInst {
     const float* Ef;           // the same in float (the float path converts nothing per thread)
     float fa, fb, fnu, fnuv, fEmax, fdv3;
     void* f[2];                // ping-pong state
-    void* part[2];             // fused step: column sums of f[k], [nx][C][17] double-float (float path)
+    void* part[2];             // fused step: column sums of f[k], [nx][C][17], double-float (float) or double
     const void* vtab;          // T: v_x[nvx], v_y[nvp2], v_z[nvp2], v_y^2+v_z^2[nvp2]
     const double* Uin;         // lift source, conserved [5][nx] (device) or null
     double* Uout;              // projection destination after the last step (or null)
@@ -135,25 +135,26 @@ struct FGeom {
 cudaError_t prepare_force_kernels(int max_smem);
 size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows);
 size_t force_step_buf_off(int precision, int nvx, int nvp);
-// The fused single-pass step (float, upwind, 16-byte lanes, <= 256 threads):
-// its shared memory for a walk of `walk` columns, whether geometry g can use
-// it, the partials it keeps per column, and its resident CTAs per SM.
-size_t force_fused_smem(int nvp, int rows, int walk);
+// The fused single-pass step (upwind, 16-byte lanes, <= 256 threads; float
+// or double): its shared memory for a walk of `walk` columns, whether
+// geometry g can use it, the partials it keeps per column (8 bytes each), and
+// its resident CTAs per SM.
+size_t force_fused_smem(int precision, int nvp, int rows, int walk);
 bool force_fused_fits(int precision, int scheme, const FGeom& g);
 int force_partials_per_column(const FGeom& g);
-int force_fused_occupancy(int threads, size_t smem, int* per_sm);
+int force_fused_occupancy(int precision, int threads, size_t smem, int* per_sm);
 // All nsteps fused steps of the active instances in one persistent launch of
 // `ctas` CTAs (at most the resident count); sync (sync_words ints: a ticket
 // and one done count per instance and walk) is zeroed on the stream first.
-cudaError_t launch_force_fused_run(const FInst* insts, const FGeom& g, int n_inst, const Active* act, int* cur,
-                                   int nsteps, int* sync, int sync_words, int* status, size_t smem, cudaStream_t s,
-                                   int ctas, long long wait_ns = WAIT_LIMIT_NS, int poison = 0);
+cudaError_t launch_force_fused_run(int precision, const FInst* insts, const FGeom& g, int n_inst, const Active* act,
+                                   int* cur, int nsteps, int* sync, int sync_words, int* status, size_t smem,
+                                   cudaStream_t s, int ctas, long long wait_ns = WAIT_LIMIT_NS, int poison = 0);
 // Partials of the current state of the active instances (fused step input).
-cudaError_t launch_force_sums(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
-                              const int* cur, cudaStream_t s);
+cudaError_t launch_force_sums(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                              const Active* act, const int* cur, cudaStream_t s);
 // Ucur / Uout of the active instances from the partials of their current state.
-cudaError_t launch_force_finalize(const FInst* insts, const FGeom& g, int nx, int n_inst, const Active* act,
-                                  const int* cur, cudaStream_t s);
+cudaError_t launch_force_finalize(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
+                                  const Active* act, const int* cur, cudaStream_t s);
 void force_step_layout(int nvp, int vec, int rows, int max_threads, int* groups, int* threads);
 size_t force_lift_smem(int precision, int nvx, int nvp);
 // Resident clusters of C CTAs of the clustered step kernel.

@@ -12,11 +12,13 @@ import pytest
 import oracle as O
 import paper_2502_02704_gb300 as pr
 from paper_2502_02704_gb300 import workloads as W
-from helpers import TOL_MIXED, f_rel_err, moment_rel_err
+from helpers import TOL_FP64, TOL_MIXED, f_rel_err, moment_rel_err
 
 pytestmark = pytest.mark.gpu
 
 BC = {pr.PR_BC_PERIODIC: O.BC_PERIODIC, pr.PR_BC_OUTFLOW: O.BC_OUTFLOW, pr.PR_BC_REFLECT: O.BC_REFLECT}
+TOL = {pr.PR_FP64: TOL_FP64, pr.PR_MIXED: TOL_MIXED}
+FTOL = {pr.PR_FP64: 1e-12, pr.PR_MIXED: 2e-6}   # f against the oracle
 
 
 def _profile(nx, phase=0.0):
@@ -37,10 +39,10 @@ def _problem(nx, nvx, nvp, L, bc, eps, n_inst=2):
     return insts, kins, initial
 
 
-def _run(insts, cluster, march, splits, initial):
+def _run(insts, cluster, march, splits, initial, precision=pr.PR_MIXED):
     """Run the step counts in `splits` one after the other; every instance's f
     and moments and the walk length in use."""
-    b = pr.pr_force_create(insts, pr.PR_UPWIND, pr.PR_MIXED)
+    b = pr.pr_force_create(insts, pr.PR_UPWIND, precision)
     try:
         pr.pr_force_set_cluster(b, cluster)
         pr.pr_force_set_march(b, march)
@@ -63,36 +65,38 @@ def _run(insts, cluster, march, splits, initial):
     (32, 4, 16),   # 2 rows per CTA, 32-thread CTAs
 ])
 @pytest.mark.parametrize("eps", [1e-2, math.inf])
-def test_fused_step_matches_oracle_and_clustered_step(bc, nvx, nvp, cluster, eps):
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_fused_step_matches_oracle_and_clustered_step(bc, nvx, nvp, cluster, eps, precision):
     nx, L, n = 20, 7.0, 5
     insts, kins, initial = _problem(nx, nvx, nvp, L, bc, eps)
-    got, used = _run(insts, cluster, 7, (2, n - 2), initial)
-    ref, used0 = _run(insts, cluster, 0, (n,), initial)
+    got, used = _run(insts, cluster, 7, (2, n - 2), initial, precision)
+    ref, used0 = _run(insts, cluster, 0, (n,), initial, precision)
     assert used == 7 and used0 == 0
     for k, ((f, V), (fr, Vr)) in enumerate(zip(got, ref)):
         fo = O.v_fine_run(kins[k], insts[k].c.dt, n, O.v_lift(kins[k], initial[k]))
-        assert f_rel_err(f, fo) < 2e-6
-        assert moment_rel_err(V, O.v_project(kins[k], fo, conserved=True)) < TOL_MIXED
-        assert f_rel_err(f, fr) < 2e-6   # the clustered step sums f* itself
-        assert moment_rel_err(V, Vr) < TOL_MIXED
+        assert f_rel_err(f, fo) < FTOL[precision]
+        assert moment_rel_err(V, O.v_project(kins[k], fo, conserved=True)) < TOL[precision]
+        assert f_rel_err(f, fr) < FTOL[precision]   # the clustered step sums f* itself
+        assert moment_rel_err(V, Vr) < TOL[precision]
 
 
 @pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_REFLECT])
-def test_walk_length_and_run_splits_give_the_same_bits(bc):
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_walk_length_and_run_splits_give_the_same_bits(bc, precision):
     # each column's arithmetic does not depend on how columns group into
     # walks, and the partials kernel sums in the step's order
     nx, nvx, nvp, L = 23, 64, 16, 7.0
     insts, _, initial = _problem(nx, nvx, nvp, L, bc, 1e-3, n_inst=3)
-    ref, _ = _run(insts, 4, 1, (6,), initial)
+    ref, _ = _run(insts, 4, 1, (6,), initial, precision)
     for march, splits in ((3, (6,)), (8, (1, 1, 4)), (23, (2, 4)), (32, (6,))):
-        got, used = _run(insts, 4, march, splits, initial)
+        got, used = _run(insts, 4, march, splits, initial, precision)
         assert used == min(march, nx) or (march, used) == (8, 8)
         for (f, V), (fr, Vr) in zip(got, ref):
             assert np.array_equal(f, fr)
             assert np.array_equal(V, Vr)
     # a new walk length drops the partials: the partials kernel recomputes
     # them from the stored f^n, bit for bit those the step wrote
-    b = pr.pr_force_create(insts, pr.PR_UPWIND, pr.PR_MIXED)
+    b = pr.pr_force_create(insts, pr.PR_UPWIND, precision)
     try:
         pr.pr_force_set_cluster(b, 4)
         pr.pr_force_set_march(b, 1)
@@ -165,7 +169,15 @@ def test_fused_selection_rules():
         assert pr.pr_force_get_march(b) == 0
     finally:
         pr.pr_force_destroy(b)
-    for scheme, precision, nv in ((pr.PR_UPWIND, pr.PR_FP64, nvp), (pr.PR_MUSCL, pr.PR_MIXED, nvp),
+    # FP64 upwind has the fused step too (16-byte lanes of two doubles)
+    b = pr.pr_force_create([inst], pr.PR_UPWIND, pr.PR_FP64)
+    try:
+        pr.pr_force_set_cluster(b, 2)
+        pr.pr_force_set_march(b, 4)
+        assert pr.pr_force_get_march(b) == 4
+    finally:
+        pr.pr_force_destroy(b)
+    for scheme, precision, nv in ((pr.PR_MUSCL, pr.PR_MIXED, nvp), (pr.PR_MUSCL, pr.PR_FP64, nvp),
                                   (pr.PR_UPWIND, pr.PR_MIXED, 5)):  # 25-float rows: no bulk copies
         b = pr.pr_force_create([pr.ForceInstance(nx, nvx, nv, 1e-3, L=8.0, x0=0.0, x1=2.0, E=E)], scheme, precision)
         try:
@@ -240,14 +252,15 @@ def test_cluster_wider_than_its_ctas_threads(precision):
 
 @pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW, pr.PR_BC_REFLECT])
 @pytest.mark.parametrize("nvx,nvp,cluster,march", [(64, 16, 2, 1), (64, 16, 2, 6), (48, 8, 6, 4), (32, 4, 16, 23)])
-def test_persistent_run_is_bitwise_the_stepwise_run(bc, nvx, nvp, cluster, march):
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_persistent_run_is_bitwise_the_stepwise_run(bc, nvx, nvp, cluster, march, precision):
     # all steps of a run in one launch, items waiting on their neighbour
     # walks, against one launch per step
     nx, L, n = 23, 7.0, 7
     insts, _, initial = _problem(nx, nvx, nvp, L, bc, 1e-3, n_inst=3)
     out = []
     for mode in (0, 1):
-        b = pr.pr_force_create(insts, pr.PR_UPWIND, pr.PR_MIXED)
+        b = pr.pr_force_create(insts, pr.PR_UPWIND, precision)
         try:
             pr.pr_force_set_cluster(b, cluster)
             pr.pr_force_set_march(b, march)
@@ -265,7 +278,8 @@ def test_persistent_run_is_bitwise_the_stepwise_run(bc, nvx, nvp, cluster, march
 
 
 @pytest.mark.parametrize("persistent", [0, 1])
-def test_force_parareal_on_the_fused_step_matches_oracle(persistent):
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_force_parareal_on_the_fused_step_matches_oracle(persistent, precision):
     # Algorithm 2 with the fused step for the fine propagator (one launch per
     # slice run, or one persistent launch): the slices are the instances
     nx, nvx, nvp, L, eps, T, N, K = 16, 32, 8, 6.0, 1e-2, 0.05, 6, 3
@@ -273,13 +287,13 @@ def test_force_parareal_on_the_fused_step_matches_oracle(persistent):
     U0 = _profile(nx)
     k = O.VKin(nx=nx, nvx=nvx, nvp=nvp, L=L, x0=0.0, x1=2.0, eps=eps, E=E)
     Uo, errs_o, _ = O.v_parareal(O.VParareal(kin=k, T=T, N=N), U0, K=K)
-    ctx = pr.pr_init_force(nx, 0.0, 2.0, pr.PR_BC_PERIODIC, nvx, nvp, L, eps, T, N, E, precision=pr.PR_MIXED)
+    ctx = pr.pr_init_force(nx, 0.0, 2.0, pr.PR_BC_PERIODIC, nvx, nvp, L, eps, T, N, E, precision=precision)
     try:
         pr.pr_set_force_step(ctx, 2, 4, persistent)
         pr.pr_set_initial(ctx, U0)
         kd, errs = pr.pr_parareal_run(ctx, K)
         for n in range(N + 1):
-            assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < TOL_MIXED, n
+            assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < TOL[precision], n
     finally:
         pr.pr_destroy(ctx)
 
