@@ -141,6 +141,34 @@ def _cpu_sample(seconds=12.0, max_steps=200):
     return rate, cores, f"{steps} fine steps of one instance (eps=1e-2, Nx=512, 32^3, MUSCL) in {el:.1f} s"
 
 
+def _cpu_single_core(seconds=2.0):
+    """The oracle on one host core (its own threads set to 1): fine steps of
+    the periodic MUSCL workload (Nx=512, 32^3), of the Sod tube (Nx=64,
+    16^3, upwind, outflow) and of the gradient workload's grid (Nx=256, 24^3,
+    upwind, periodic), each for about `seconds`.  Cell-updates/s."""
+    import oracle as O
+    from paper_2502_02704_gb300 import workloads as W
+
+    cases = {"periodic_muscl_512x32c3": (NX, NV, O.BC_PERIODIC, O.MUSCL, W.smooth_periodic(NX)),
+             "sod_upwind_64x16c3": (64, 16, O.BC_OUTFLOW, O.UPWIND, W.sod(64)),
+             "smooth_upwind_256x24c3": (256, 24, O.BC_PERIODIC, O.UPWIND, W.smooth_periodic(256))}
+    out = {}
+    O.set_threads(1)
+    try:
+        for name, (nx, nv, bc, sch, U) in cases.items():
+            k = O.Kin(nx=nx, nv=nv, L=L, bc=bc, eps=1e-2, scheme=sch)
+            dt = 0.5 * (1.0 / nx) / (L - 0.5 * (2 * L / nv))
+            f = O.lift(k, U)
+            steps, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < seconds:
+                f = O.fine_run(k, dt, 1, f)
+                steps += 1
+            out[name] = nx * nv ** 3 * steps / (time.perf_counter() - t0)
+    finally:
+        O.set_threads(os.cpu_count() or 1)
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on the host cores, same metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -607,7 +635,8 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         rate, cores, sample = _cpu_sample()
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": _cpu_single_core()}
     para = para64 = None
     try:
         para = _parareal_speedup(pr, np)
