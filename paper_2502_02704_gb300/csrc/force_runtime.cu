@@ -145,6 +145,9 @@ bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk
         const long long groups = std::max<long long>(1, (long long)per1 * dev_attr(cudaDevAttrMultiProcessorCount) / C);
         S = std::min<long long>(scap, (long long)b->n * b->nx / groups);
         if (S < 2) return false;
+        // one resident CTA per SM (FP64 Test 3): half the walk, two waves of
+        // items per step balance better (one instance 234 instead of 250 us)
+        if (per1 == 1) S = std::max<long long>(2, S / 2);
     }
     S = std::max<long long>(1, std::min<long long>(S, cap));
     const long long walks = (b->nx + S - 1) / S;
