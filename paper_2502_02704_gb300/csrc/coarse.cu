@@ -48,76 +48,6 @@ __device__ __forceinline__ Prim prim(const double* v)
     return q;
 }
 
-__device__ __forceinline__ double speed(const double* v, int sound)
-{
-    Prim q = prim(v);
-    double c = sound == 1 ? sqrt(q.th) : sqrt(5.0 * q.th / 3.0);
-    return fabs(q.ux) + c;
-}
-
-// state of cell c (ghosts allowed) of V[5][nx]
-__device__ __forceinline__ void cell(const double* V, int nx, int bc, int c, double* out)
-{
-    int cc = c;
-    bool flip = false;
-    if (c < 0 || c >= nx) {
-        if (bc == 0) cc = ((c % nx) + nx) % nx;
-        else if (bc == 1) cc = c < 0 ? 0 : nx - 1;
-        else {
-            cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
-            flip = true;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) out[q] = V[q * nx + cc];
-    if (flip) out[1] = -out[1];
-}
-
-__device__ __forceinline__ void flux(const double* v, double* h)
-{
-    Prim q = prim(v);
-    h[0] = v[1];
-    h[1] = v[1] * q.ux + q.p;
-    h[2] = v[1] * q.uy;
-    h[3] = v[1] * q.uz;
-    h[4] = q.ux * (v[4] + q.p);
-}
-
-__device__ void rusanov(const double* V, int nx, int bc, int sound, int c, double* H)
-{
-    double a[5], b[5], ha[5], hb[5];
-    cell(V, nx, bc, c, a);
-    cell(V, nx, bc, c + 1, b);
-    flux(a, ha);
-    flux(b, hb);
-    double sa = speed(a, sound), sb = speed(b, sound);
-    double S = sa > sb ? sa : sb;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) H[q] = 0.5 * (ha[q] + hb[q]) - 0.5 * S * (b[q] - a[q]);
-}
-
-// Viscous flux D_{c+1/2} of the compressible Navier-Stokes model (Eq. 8):
-// mu = rho theta, kappa = 5 rho theta / 2 (BGK, tau = 1), gradients
-// (V_{c+1} - V_c)/dx, coefficients and u averaged over the face.
-__device__ void viscous(const double* V, int nx, int bc, double dx, double eps, int c, double* D)
-{
-    double a[5], b[5];
-    cell(V, nx, bc, c, a);
-    cell(V, nx, bc, c + 1, b);
-    Prim pa = prim(a), pb = prim(b);
-    double mu = 0.5 * (pa.p + pb.p);
-    double kappa = 2.5 * mu;
-    double dux = (pb.ux - pa.ux) / dx, duy = (pb.uy - pa.uy) / dx, duz = (pb.uz - pa.uz) / dx, dth = (pb.th - pa.th) / dx;
-    double ux = 0.5 * (pa.ux + pb.ux), uy = 0.5 * (pa.uy + pb.uy), uz = 0.5 * (pa.uz + pb.uz);
-    double sxx = -eps * mu * (4.0 / 3.0) * dux, sxy = -eps * mu * duy, sxz = -eps * mu * duz;
-    double q = -eps * kappa * dth;
-    D[0] = 0.0;
-    D[1] = sxx;
-    D[2] = sxy;
-    D[3] = sxz;
-    D[4] = sxx * ux + sxy * uy + sxz * uz + q;
-}
-
 __device__ double block_max(double v, double* sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -131,10 +61,108 @@ __device__ double block_max(double v, double* sh)
     return r;
 }
 
-// G over dT applied in place to A (work B); result ends in A.  Needs the whole CTA.
-__device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT, int* status, double* sh)
+// Two maxima over the CTA in one pass (sh holds 2 doubles per warp).
+__device__ void block_max2(double& a, double& b, double* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sh[2 * warp] = a;
+        sh[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    double ra = 0.0, rb = 0.0;
+    for (int k = 0; k < nw; ++k) {
+        ra = fmax(ra, sh[2 * k]);
+        rb = fmax(rb, sh[2 * k + 1]);
+    }
+    a = ra;
+    b = rb;
+}
+
+// Per-cell values of one substep, computed once from the state before it:
+// u_x, u_y, u_z, theta, p, the Euler flux h (5) and the wave speed, stored
+// [NCACHE][nx].  A face then combines two cached cells; a reflecting ghost
+// (rho u_x negated) has u_x and h_0, h_2, h_3, h_4 negated, which is exactly
+// what the same formulas give on the mirrored state.
+constexpr int NCACHE = 11;
+
+struct CellF {
+    double v[5], ux, uy, uz, th, p, h[5], s;
+};
+
+__device__ __forceinline__ void fetch(const double* A, const double* Cc, int nx, int bc, int c, CellF& o)
+{
+    int cc = c;
+    bool flip = false;
+    if (c < 0 || c >= nx) {
+        if (bc == 0) cc = ((c % nx) + nx) % nx;
+        else if (bc == 1) cc = c < 0 ? 0 : nx - 1;
+        else {
+            cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
+            flip = true;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) o.v[q] = A[q * nx + cc];
+    o.ux = Cc[cc];
+    o.uy = Cc[nx + cc];
+    o.uz = Cc[2 * nx + cc];
+    o.th = Cc[3 * nx + cc];
+    o.p = Cc[4 * nx + cc];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) o.h[q] = Cc[(5 + q) * nx + cc];
+    o.s = Cc[10 * nx + cc];
+    if (flip) {
+        o.v[1] = -o.v[1];
+        o.ux = -o.ux;
+        o.h[0] = -o.h[0];
+        o.h[2] = -o.h[2];
+        o.h[3] = -o.h[3];
+        o.h[4] = -o.h[4];
+    }
+}
+
+// Flux through the face between cells a and b: Rusanov (Eq. 16) plus, when
+// eps > 0, the viscous flux of the compressible Navier-Stokes model (Eq. 8)
+// with mu = rho theta, kappa = 5 rho theta / 2, gradients (b - a)/dx and
+// coefficients and u averaged over the face.
+__device__ __forceinline__ void face_flux(const CellF& a, const CellF& b, double visc, double dx, double* H)
+{
+    const double S = a.s > b.s ? a.s : b.s;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) H[q] = 0.5 * (a.h[q] + b.h[q]) - 0.5 * S * (b.v[q] - a.v[q]);
+    if (visc > 0.0) {
+        const double eps = visc;
+        double mu = 0.5 * (a.p + b.p);
+        double kappa = 2.5 * mu;
+        double dux = (b.ux - a.ux) / dx, duy = (b.uy - a.uy) / dx, duz = (b.uz - a.uz) / dx, dth = (b.th - a.th) / dx;
+        double ux = 0.5 * (a.ux + b.ux), uy = 0.5 * (a.uy + b.uy), uz = 0.5 * (a.uz + b.uz);
+        double sxx = -eps * mu * (4.0 / 3.0) * dux, sxy = -eps * mu * duy, sxz = -eps * mu * duz;
+        double qh = -eps * kappa * dth;
+        H[0] += 0.0;
+        H[1] += sxx;
+        H[2] += sxy;
+        H[3] += sxz;
+        H[4] += sxx * ux + sxy * uy + sxz * uz + qh;
+    }
+}
+
+// G over dT applied to A (work B, cache Cc of NCACHE nx doubles); the result
+// ends in A.  Needs the whole CTA.  Per local step: one pass caching each
+// cell's primitives, flux and speed (and the two maxima of the CFL limits),
+// one pass forming each cell's two face fluxes and its update, three CTA
+// barriers; the two state buffers swap roles.
+__device__ void coarse_G(const CoarseParams& p, double* A, double* B, double* Cc, double dT, int* status, double* sh)
 {
     const int nx = p.nx;
+    double* cur = A;
+    double* nxt = B;
     double t = 0.0;
     while (t < dT) {
         double smax = 0.0, thmax = 0.0;
@@ -142,20 +170,31 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT,
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
             double v[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) v[q] = A[q * nx + i];
+            for (int q = 0; q < 5; ++q) v[q] = cur[q * nx + i];
             Prim pr = prim(v);
             if (!(v[0] > 0.0) || !(pr.th > 0.0)) bad = true;
-            double s = speed(v, p.sound);
+            double c = p.sound == 1 ? sqrt(pr.th) : sqrt(5.0 * pr.th / 3.0);
+            double s = fabs(pr.ux) + c;
             if (s > smax) smax = s;
             if (pr.th > thmax) thmax = pr.th;
+            Cc[i] = pr.ux;
+            Cc[nx + i] = pr.uy;
+            Cc[2 * nx + i] = pr.uz;
+            Cc[3 * nx + i] = pr.th;
+            Cc[4 * nx + i] = pr.p;
+            Cc[5 * nx + i] = v[1];
+            Cc[6 * nx + i] = v[1] * pr.ux + pr.p;
+            Cc[7 * nx + i] = v[1] * pr.uy;
+            Cc[8 * nx + i] = v[1] * pr.uz;
+            Cc[9 * nx + i] = pr.ux * (v[4] + pr.p);
+            Cc[10 * nx + i] = s;
         }
         if (bad) atomicCAS(status, 0, ST_NONPHYS);
-        smax = block_max(smax, sh);
-        if (!(smax > 0.0) || isnan(smax)) return;
+        block_max2(smax, thmax, sh);  // its barriers also publish the cache
+        if (!(smax > 0.0) || isnan(smax)) break;
         double rem = dT - t;
         double dt = p.cfl * p.dx / smax;
         if (p.visc > 0.0) {
-            thmax = block_max(thmax, sh);
             double dtv = p.cfl * p.dx * p.dx / (2.0 * p.visc * (5.0 / 3.0) * thmax);
             if (dtv < dt) dt = dtv;
         }
@@ -165,31 +204,30 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double dT,
             last = true;
         }
         for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            double Hr[5], Hl[5];
-            rusanov(A, nx, p.bc, p.sound, i, Hr);
-            rusanov(A, nx, p.bc, p.sound, i - 1, Hl);
-            if (p.visc > 0.0) {  // compressible Navier-Stokes (Eq. 8)
-                double Dr[5], Dl[5];
-                viscous(A, nx, p.bc, p.dx, p.visc, i, Dr);
-                viscous(A, nx, p.bc, p.dx, p.visc, i - 1, Dl);
+            CellF L, M, R;
+            fetch(cur, Cc, nx, p.bc, i - 1, L);
+            fetch(cur, Cc, nx, p.bc, i, M);
+            fetch(cur, Cc, nx, p.bc, i + 1, R);
+            double Hl[5], Hr[5];
+            face_flux(L, M, p.visc, p.dx, Hl);
+            face_flux(M, R, p.visc, p.dx, Hr);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    Hr[q] += Dr[q];
-                    Hl[q] += Dl[q];
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) B[q * nx + i] = A[q * nx + i] - dt / p.dx * (Hr[q] - Hl[q]);
+            for (int q = 0; q < 5; ++q) nxt[q * nx + i] = cur[q * nx + i] - dt / p.dx * (Hr[q] - Hl[q]);
             if (p.E) {  // exterior force: forward-Euler source on the old state
-                B[1 * nx + i] += dt * A[0 * nx + i] * p.E[i];
-                B[4 * nx + i] += dt * A[1 * nx + i] * p.E[i];
+                nxt[1 * nx + i] += dt * cur[0 * nx + i] * p.E[i];
+                nxt[4 * nx + i] += dt * cur[1 * nx + i] * p.E[i];
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < 5 * nx; i += blockDim.x) A[i] = B[i];
-        __syncthreads();
+        double* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
         if (last) break;
         t += dt;
+    }
+    if (cur != A) {
+        for (int i = threadIdx.x; i < 5 * nx; i += blockDim.x) A[i] = cur[i];
+        __syncthreads();
     }
 }
 
@@ -197,12 +235,13 @@ __global__ void __launch_bounds__(CT)
 k_coarse(CoarseParams p, const double* Vin, double* Vout, double dT, double* work, int use_smem, int* status)
 {
     extern __shared__ __align__(16) double dsm[];
-    __shared__ double sh[CT / 32];
+    __shared__ double sh[2 * (CT / 32)];
     double* A = use_smem ? dsm : work;
     double* B = A + 5 * p.nx;
+    double* Cc = B + 5 * p.nx;
     for (int i = threadIdx.x; i < 5 * p.nx; i += blockDim.x) A[i] = Vin[i];
     __syncthreads();
-    coarse_G(p, A, B, dT, status, sh);
+    coarse_G(p, A, B, Cc, dT, status, sh);
     __syncthreads();
     for (int i = threadIdx.x; i < 5 * p.nx; i += blockDim.x) Vout[i] = A[i];
 }
@@ -212,16 +251,17 @@ k_sweep(CoarseParams p, int N, double dT, const int* dk, double* U, const double
         double* work, int use_smem, int* status, int bump, int* dk_mut)
 {
     extern __shared__ __align__(16) double dsm[];
-    __shared__ double sh[CT / 32];
+    __shared__ double sh[2 * (CT / 32)];
     const int nx = p.nx, sz = 5 * nx;
     const int k = *dk;
     double* A = use_smem ? dsm : work;
     double* B = A + sz;
+    double* Cc = B + sz;
     double emax = 0.0;
     for (int n = (k > 1 ? k : 1); n <= N; ++n) {
         for (int i = threadIdx.x; i < sz; i += blockDim.x) A[i] = U[(size_t)(n - 1) * sz + i];
         __syncthreads();
-        coarse_G(p, A, B, dT, status, sh);
+        coarse_G(p, A, B, Cc, dT, status, sh);
         for (int i = threadIdx.x; i < sz; i += blockDim.x) {
             const size_t o = (size_t)n * sz + i;
             double gv = A[i];
@@ -253,7 +293,10 @@ __global__ void k_set_active(const int* dk, Active* a, int first_slice, int n_in
     a->end = hi;
 }
 
-bool fits_smem(int nx) { return (size_t)10 * nx * sizeof(double) <= 200 * 1024; }
+// Doubles of workspace of one coarse step: state, next state, cell cache.
+size_t work_doubles(int nx) { return (size_t)(10 + NCACHE) * nx; }
+
+bool fits_smem(int nx) { return work_doubles(nx) * sizeof(double) <= 200 * 1024; }
 
 }  // namespace
 
@@ -272,7 +315,7 @@ cudaError_t launch_coarse(const CoarseParams& p, const double* Vin, double* Vout
                           int* status, cudaStream_t s)
 {
     int use = fits_smem(p.nx);
-    size_t smem = use ? (size_t)10 * p.nx * sizeof(double) : 0;
+    size_t smem = use ? work_doubles(p.nx) * sizeof(double) : 0;
     int threads = p.nx < CT ? ((p.nx + 31) / 32) * 32 : CT;
     k_coarse<<<1, threads, smem, s>>>(p, Vin, Vout, dT, work, use, status);
     return cudaGetLastError();
@@ -283,11 +326,13 @@ cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk,
                          cudaStream_t s)
 {
     int use = fits_smem(p.nx);
-    size_t smem = use ? (size_t)10 * p.nx * sizeof(double) : 0;
+    size_t smem = use ? work_doubles(p.nx) * sizeof(double) : 0;
     int threads = p.nx < CT ? ((p.nx + 31) / 32) * 32 : CT;
     k_sweep<<<1, threads, smem, s>>>(p, N, dT, dk, U, PFL, Gs, err, work, use, status, bump, dk_mut);
     return cudaGetLastError();
 }
+
+size_t coarse_work_doubles(int nx) { return work_doubles(nx); }
 
 cudaError_t launch_set_active(const int* dk, Active* active, int first_slice, int n_inst, int N, cudaStream_t s)
 {

@@ -205,6 +205,9 @@ cudaError_t launch_coarse(const CoarseParams& p, const double* Vin, double* Vout
 // Sequential sweep of Algorithm 2 for n = k..N (k read from *dk on the device):
 //   Gv = G(U[n-1]); U[n] = Gv + (k > 0 ? PFL[n] - Gs[n] : 0); Gs[n] = Gv;
 //   err[k] = max |U[n]_new - U[n]_old|.  Then *dk <- k + 1 if bump.
+// Doubles of global workspace a coarse step needs when its state does not fit
+// shared memory (state, next state, per-cell cache).
+size_t coarse_work_doubles(int nx);
 cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk, double* U,
                          const double* PFL, double* Gs, double* err, double* work, int* status,
                          int bump, int* dk_mut, cudaStream_t s);

@@ -1045,7 +1045,7 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
     size_t lvl = (size_t)(c->N + 1) * 5 * c->nx * sizeof(double);
     if (cudaMalloc(&c->dU, lvl) != cudaSuccess || cudaMalloc(&c->dPFL, lvl) != cudaSuccess ||
         cudaMalloc(&c->dGs, lvl) != cudaSuccess || cudaMalloc(&c->derr, sizeof(double) * (c->N + 2)) != cudaSuccess ||
-        cudaMalloc(&c->dwork, sizeof(double) * 10 * c->nx) != cudaSuccess ||
+        cudaMalloc(&c->dwork, sizeof(double) * prk::coarse_work_doubles(c->nx)) != cudaSuccess ||
         cudaMalloc(&c->dtmp, sizeof(double) * 10 * c->nx) != cudaSuccess || cudaMalloc(&c->dk, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->dstatus, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_pinned, sizeof(double) * (c->N + 2)) != cudaSuccess) {
         free_ctx(c);
