@@ -2,7 +2,7 @@
 
 Each translation unit is compiled by nvcc in parallel and linked into
 ``paper_2502_02704_gb300/libpr.so``.  The coarse propagator is compiled with
-``-fmad=false`` so its Rusanov arithmetic is the plain IEEE sequence of the
+``-fmad=false`` so its Rusanov arithmetic is the plain IEEE sequence of its
 formulas (no fused multiply-add contraction).
 """
 from __future__ import annotations

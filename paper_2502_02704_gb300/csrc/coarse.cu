@@ -18,33 +18,41 @@
 // stored G results of the previous sweep, and the Eq. (10) error
 // max |U^{n,k} - U^{n,k-1}| reduced in the same pass.
 //
-// One CTA runs the whole sweep (the loop over n is sequential by nature);
-// the state lives in shared memory when it fits.  This file is compiled
-// without floating-point contraction so that the arithmetic is the plain
-// IEEE sequence of the formulas above.
+// One thread-block cluster runs the whole sweep (the loop over n is
+// sequential by nature), its CTAs owning contiguous blocks of cells in their
+// shared memory (or global regions when the blocks do not fit).  This file
+// is compiled without floating-point contraction so that the arithmetic is
+// the plain IEEE sequence of the formulas above (with rho's reciprocal times
+// the momenta for the primitive variables).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "pr_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace prk {
 
 namespace {
 
-constexpr int CT = 1024;  // threads of the coarse CTA
+constexpr int CT = 256;  // threads per coarse CTA at most (cells beyond loop)
 
 struct Prim {
     double ux, uy, uz, p, th;
 };
 
+// Primitive variables of a conserved state with one reciprocal of rho (the
+// quotients v/rho as products with 1/rho: within an ulp of the divisions,
+// and a much shorter dependent chain on this part's FP64 pipe).
 __device__ __forceinline__ Prim prim(const double* v)
 {
     Prim q;
-    double rho = v[0];
-    q.ux = v[1] / rho;
-    q.uy = v[2] / rho;
-    q.uz = v[3] / rho;
-    q.th = (2.0 * v[4] / rho - (q.ux * q.ux + q.uy * q.uy + q.uz * q.uz)) / 3.0;
-    q.p = rho * q.th;
+    const double rinv = 1.0 / v[0];
+    q.ux = v[1] * rinv;
+    q.uy = v[2] * rinv;
+    q.uz = v[3] * rinv;
+    q.th = (2.0 * v[4] * rinv - (q.ux * q.ux + q.uy * q.uy + q.uz * q.uz)) * (1.0 / 3.0);
+    q.p = v[0] * q.th;
     return q;
 }
 
@@ -96,7 +104,30 @@ struct CellF {
     double v[5], ux, uy, uz, th, p, h[5], s;
 };
 
-__device__ __forceinline__ void fetch(const double* A, const double* Cc, int nx, int bc, int c, CellF& o)
+// Region of one cluster CTA (m cells): state A[5][m], next state B[5][m],
+// cell cache [NCACHE][m], then 2 doubles of the CTA's CFL maxima.  Lives in
+// the CTA's shared memory, or in a global workspace (one region per CTA)
+// when m cells do not fit; peers read it through distributed shared memory
+// or plainly, ordered by the cluster barriers.
+__host__ __device__ inline size_t region_doubles(int m) { return (size_t)(10 + NCACHE) * m + 2; }
+
+struct Peers {
+    double* base;      // this CTA's region
+    double* gbase;     // global regions (when not in shared memory)
+    size_t region;     // doubles per region
+    int rank, m;
+    bool smem;
+    __device__ __forceinline__ double* of(cg::cluster_group& cl, int r) const
+    {
+        if (r == rank) return base;
+        return smem ? cl.map_shared_rank(base, r) : gbase + (size_t)r * region;
+    }
+};
+
+// Cell c of the whole domain (ghosts through the boundary rule) from the
+// state at offset cur_off and the cache of its owner.
+__device__ __forceinline__ void fetch(cg::cluster_group& cl, const Peers& P, int cur_off, int nx, int bc, int c,
+                                      CellF& o)
 {
     int cc = c;
     bool flip = false;
@@ -108,16 +139,25 @@ __device__ __forceinline__ void fetch(const double* A, const double* Cc, int nx,
             flip = true;
         }
     }
+    const int m = P.m, b0 = P.rank * m;
+    int owner, li;
+    if (cc >= b0 && cc < b0 + m) owner = P.rank, li = cc - b0;              // own block
+    else if (cc == b0 - 1) owner = P.rank - 1, li = m - 1;                  // left neighbour block
+    else if (cc == b0 + m) owner = P.rank + 1, li = 0;                      // right neighbour block
+    else owner = cc / m, li = cc - owner * m;                               // a wrapped or mirrored ghost
+    const double* R = P.of(cl, owner);
+    const double* V = R + cur_off;
+    const double* Cc = R + 10 * m;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) o.v[q] = A[q * nx + cc];
-    o.ux = Cc[cc];
-    o.uy = Cc[nx + cc];
-    o.uz = Cc[2 * nx + cc];
-    o.th = Cc[3 * nx + cc];
-    o.p = Cc[4 * nx + cc];
+    for (int q = 0; q < 5; ++q) o.v[q] = V[q * m + li];
+    o.ux = Cc[li];
+    o.uy = Cc[m + li];
+    o.uz = Cc[2 * m + li];
+    o.th = Cc[3 * m + li];
+    o.p = Cc[4 * m + li];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) o.h[q] = Cc[(5 + q) * nx + cc];
-    o.s = Cc[10 * nx + cc];
+    for (int q = 0; q < 5; ++q) o.h[q] = Cc[(5 + q) * m + li];
+    o.s = Cc[10 * m + li];
     if (flip) {
         o.v[1] = -o.v[1];
         o.ux = -o.ux;
@@ -130,9 +170,9 @@ __device__ __forceinline__ void fetch(const double* A, const double* Cc, int nx,
 
 // Flux through the face between cells a and b: Rusanov (Eq. 16) plus, when
 // eps > 0, the viscous flux of the compressible Navier-Stokes model (Eq. 8)
-// with mu = rho theta, kappa = 5 rho theta / 2, gradients (b - a)/dx and
-// coefficients and u averaged over the face.
-__device__ __forceinline__ void face_flux(const CellF& a, const CellF& b, double visc, double dx, double* H)
+// with mu = rho theta, kappa = 5 rho theta / 2, gradients (b - a)/dx (idx =
+// 1/dx) and coefficients and u averaged over the face.
+__device__ __forceinline__ void face_flux(const CellF& a, const CellF& b, double visc, double idx, double* H)
 {
     const double S = a.s > b.s ? a.s : b.s;
 #pragma unroll
@@ -141,7 +181,7 @@ __device__ __forceinline__ void face_flux(const CellF& a, const CellF& b, double
         const double eps = visc;
         double mu = 0.5 * (a.p + b.p);
         double kappa = 2.5 * mu;
-        double dux = (b.ux - a.ux) / dx, duy = (b.uy - a.uy) / dx, duz = (b.uz - a.uz) / dx, dth = (b.th - a.th) / dx;
+        double dux = (b.ux - a.ux) * idx, duy = (b.uy - a.uy) * idx, duz = (b.uz - a.uz) * idx, dth = (b.th - a.th) * idx;
         double ux = 0.5 * (a.ux + b.ux), uy = 0.5 * (a.uy + b.uy), uz = 0.5 * (a.uz + b.uz);
         double sxx = -eps * mu * (4.0 / 3.0) * dux, sxy = -eps * mu * duy, sxz = -eps * mu * duz;
         double qh = -eps * kappa * dth;
@@ -153,45 +193,64 @@ __device__ __forceinline__ void face_flux(const CellF& a, const CellF& b, double
     }
 }
 
-// G over dT applied to A (work B, cache Cc of NCACHE nx doubles); the result
-// ends in A.  Needs the whole CTA.  Per local step: one pass caching each
-// cell's primitives, flux and speed (and the two maxima of the CFL limits),
-// one pass forming each cell's two face fluxes and its update, three CTA
-// barriers; the two state buffers swap roles.
-__device__ void coarse_G(const CoarseParams& p, double* A, double* B, double* Cc, double dT, int* status, double* sh)
+// G over dT applied to this CTA's cells [c0, c1) of the state at region
+// offset 0 (A), with the other CTAs of the cluster doing theirs; the result
+// ends in A.  Per local step: one pass caching each own cell's primitives,
+// flux and speed and its CTA's two CFL maxima, a cluster barrier, the
+// cluster maxima, one pass forming each own cell's two face fluxes (peer
+// cells through the owners' regions) and its update into B, a cluster
+// barrier; A and B swap roles.  Every CTA takes the same local steps.
+// (Forming each face once into a face array, with one more CTA barrier,
+// measured no faster: the step is a chain of dependent FP64 operations.)
+__device__ void coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peers& P, int C, int c0, int c1,
+                         double dT, int* status, double* sh)
 {
-    const int nx = p.nx;
-    double* cur = A;
-    double* nxt = B;
+    const int nx = p.nx, m = P.m, mc = c1 - c0;
+    double* R = P.base;
+    double* Cc = R + 10 * m;
+    double* red = R + (10 + NCACHE) * m;
+    int cur_off = 0, nxt_off = 5 * m;
+    const double idx = 1.0 / p.dx;
     double t = 0.0;
     while (t < dT) {
+        const double* cur = R + cur_off;
         double smax = 0.0, thmax = 0.0;
         bool bad = false;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        for (int li = threadIdx.x; li < mc; li += blockDim.x) {
             double v[5];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) v[q] = cur[q * nx + i];
+            for (int q = 0; q < 5; ++q) v[q] = cur[q * m + li];
             Prim pr = prim(v);
             if (!(v[0] > 0.0) || !(pr.th > 0.0)) bad = true;
-            double c = p.sound == 1 ? sqrt(pr.th) : sqrt(5.0 * pr.th / 3.0);
+            double c = p.sound == 1 ? sqrt(pr.th) : sqrt(pr.th * (5.0 / 3.0));
             double s = fabs(pr.ux) + c;
             if (s > smax) smax = s;
             if (pr.th > thmax) thmax = pr.th;
-            Cc[i] = pr.ux;
-            Cc[nx + i] = pr.uy;
-            Cc[2 * nx + i] = pr.uz;
-            Cc[3 * nx + i] = pr.th;
-            Cc[4 * nx + i] = pr.p;
-            Cc[5 * nx + i] = v[1];
-            Cc[6 * nx + i] = v[1] * pr.ux + pr.p;
-            Cc[7 * nx + i] = v[1] * pr.uy;
-            Cc[8 * nx + i] = v[1] * pr.uz;
-            Cc[9 * nx + i] = pr.ux * (v[4] + pr.p);
-            Cc[10 * nx + i] = s;
+            Cc[li] = pr.ux;
+            Cc[m + li] = pr.uy;
+            Cc[2 * m + li] = pr.uz;
+            Cc[3 * m + li] = pr.th;
+            Cc[4 * m + li] = pr.p;
+            Cc[5 * m + li] = v[1];
+            Cc[6 * m + li] = v[1] * pr.ux + pr.p;
+            Cc[7 * m + li] = v[1] * pr.uy;
+            Cc[8 * m + li] = v[1] * pr.uz;
+            Cc[9 * m + li] = pr.ux * (v[4] + pr.p);
+            Cc[10 * m + li] = s;
         }
         if (bad) atomicCAS(status, 0, ST_NONPHYS);
-        block_max2(smax, thmax, sh);  // its barriers also publish the cache
-        if (!(smax > 0.0) || isnan(smax)) break;
+        block_max2(smax, thmax, sh);
+        if (threadIdx.x == 0) {
+            red[0] = smax;
+            red[1] = thmax;
+        }
+        cl.sync();  // caches, states and CTA maxima of every rank visible
+        for (int r = 0; r < C; ++r) {
+            const double* rr = P.of(cl, r) + (10 + NCACHE) * m;
+            smax = fmax(smax, rr[0]);
+            thmax = fmax(thmax, rr[1]);
+        }
+        if (!(smax > 0.0) || isnan(smax)) break;  // the same on every rank
         double rem = dT - t;
         double dt = p.cfl * p.dx / smax;
         if (p.visc > 0.0) {
@@ -203,81 +262,119 @@ __device__ void coarse_G(const CoarseParams& p, double* A, double* B, double* Cc
             dt = rem;
             last = true;
         }
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-            CellF L, M, R;
-            fetch(cur, Cc, nx, p.bc, i - 1, L);
-            fetch(cur, Cc, nx, p.bc, i, M);
-            fetch(cur, Cc, nx, p.bc, i + 1, R);
+        double* nxt = R + nxt_off;
+        const double dtdx = dt / p.dx;
+        for (int li = threadIdx.x; li < mc; li += blockDim.x) {
+            const int i = c0 + li;
+            CellF L, M, Rt;
+            fetch(cl, P, cur_off, nx, p.bc, i - 1, L);
+            fetch(cl, P, cur_off, nx, p.bc, i, M);
+            fetch(cl, P, cur_off, nx, p.bc, i + 1, Rt);
             double Hl[5], Hr[5];
-            face_flux(L, M, p.visc, p.dx, Hl);
-            face_flux(M, R, p.visc, p.dx, Hr);
+            face_flux(L, M, p.visc, idx, Hl);
+            face_flux(M, Rt, p.visc, idx, Hr);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) nxt[q * nx + i] = cur[q * nx + i] - dt / p.dx * (Hr[q] - Hl[q]);
+            for (int q = 0; q < 5; ++q) nxt[q * m + li] = cur[q * m + li] - dtdx * (Hr[q] - Hl[q]);
             if (p.E) {  // exterior force: forward-Euler source on the old state
-                nxt[1 * nx + i] += dt * cur[0 * nx + i] * p.E[i];
-                nxt[4 * nx + i] += dt * cur[1 * nx + i] * p.E[i];
+                nxt[1 * m + li] += dt * cur[0 * m + li] * p.E[i];
+                nxt[4 * m + li] += dt * cur[1 * m + li] * p.E[i];
             }
         }
-        __syncthreads();
-        double* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+        cl.sync();  // every rank's reads of the old states and caches are over
+        const int tmp = cur_off;
+        cur_off = nxt_off;
+        nxt_off = tmp;
         if (last) break;
         t += dt;
     }
-    if (cur != A) {
-        for (int i = threadIdx.x; i < 5 * nx; i += blockDim.x) A[i] = cur[i];
+    if (cur_off != 0) {
+        for (int li = threadIdx.x; li < mc; li += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) R[q * m + li] = R[cur_off + q * m + li];
         __syncthreads();
     }
 }
 
+__device__ __forceinline__ Peers make_peers(double* dsm, double* work, int use_smem, int m)
+{
+    Peers P;
+    P.region = region_doubles(m);
+    P.rank = (int)blockIdx.x;
+    P.m = m;
+    P.smem = use_smem != 0;
+    P.gbase = work;
+    P.base = P.smem ? dsm : work + (size_t)blockIdx.x * P.region;
+    return P;
+}
+
+// One G over dT of Vin (device [5][nx]) into Vout; one cluster of C CTAs.
 __global__ void __launch_bounds__(CT)
 k_coarse(CoarseParams p, const double* Vin, double* Vout, double dT, double* work, int use_smem, int* status)
 {
     extern __shared__ __align__(16) double dsm[];
     __shared__ double sh[2 * (CT / 32)];
-    double* A = use_smem ? dsm : work;
-    double* B = A + 5 * p.nx;
-    double* Cc = B + 5 * p.nx;
-    for (int i = threadIdx.x; i < 5 * p.nx; i += blockDim.x) A[i] = Vin[i];
+    cg::cluster_group cl = cg::this_cluster();
+    const int nx = p.nx, C = gridDim.x, m = (nx + C - 1) / C;
+    const int c0 = (int)blockIdx.x * m, c1 = min(nx, c0 + m);
+    const Peers P = make_peers(dsm, work, use_smem, m);
+    for (int li = threadIdx.x; li < c1 - c0; li += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) P.base[q * m + li] = Vin[q * nx + c0 + li];
     __syncthreads();
-    coarse_G(p, A, B, Cc, dT, status, sh);
-    __syncthreads();
-    for (int i = threadIdx.x; i < 5 * p.nx; i += blockDim.x) Vout[i] = A[i];
+    coarse_G(p, cl, P, C, c0, c1, dT, status, sh);
+    for (int li = threadIdx.x; li < c1 - c0; li += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Vout[q * nx + c0 + li] = P.base[q * m + li];
+    cl.sync();  // no CTA leaves while another may still read its region
 }
 
+// Algorithm 2's sequential sweep over n = max(k,1)..N on one cluster of C
+// CTAs, each owning a contiguous block of cells.
 __global__ void __launch_bounds__(CT)
 k_sweep(CoarseParams p, int N, double dT, const int* dk, double* U, const double* PFL, double* Gs, double* err,
         double* work, int use_smem, int* status, int bump, int* dk_mut)
 {
     extern __shared__ __align__(16) double dsm[];
     __shared__ double sh[2 * (CT / 32)];
-    const int nx = p.nx, sz = 5 * nx;
+    cg::cluster_group cl = cg::this_cluster();
+    const int nx = p.nx, sz = 5 * nx, C = gridDim.x, m = (nx + C - 1) / C;
+    const int c0 = (int)blockIdx.x * m, c1 = min(nx, c0 + m), mc = c1 - c0;
     const int k = *dk;
-    double* A = use_smem ? dsm : work;
-    double* B = A + sz;
-    double* Cc = B + sz;
+    const Peers P = make_peers(dsm, work, use_smem, m);
+    double* A = P.base;
     double emax = 0.0;
     for (int n = (k > 1 ? k : 1); n <= N; ++n) {
-        for (int i = threadIdx.x; i < sz; i += blockDim.x) A[i] = U[(size_t)(n - 1) * sz + i];
+        for (int li = threadIdx.x; li < mc; li += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) A[q * m + li] = U[(size_t)(n - 1) * sz + q * nx + c0 + li];
         __syncthreads();
-        coarse_G(p, A, B, Cc, dT, status, sh);
-        for (int i = threadIdx.x; i < sz; i += blockDim.x) {
-            const size_t o = (size_t)n * sz + i;
-            double gv = A[i];
-            double nv = k > 0 ? gv + (PFL[o] - Gs[o]) : gv;
-            double d = fabs(nv - U[o]);
-            if (d > emax) emax = d;
-            U[o] = nv;
-            Gs[o] = gv;
-        }
+        coarse_G(p, cl, P, C, c0, c1, dT, status, sh);
+        for (int li = threadIdx.x; li < mc; li += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const size_t o = (size_t)n * sz + q * nx + c0 + li;
+                double gv = A[q * m + li];
+                double nv = k > 0 ? gv + (PFL[o] - Gs[o]) : gv;
+                double d = fabs(nv - U[o]);
+                if (d > emax) emax = d;
+                U[o] = nv;
+                Gs[o] = gv;
+            }
         __syncthreads();
     }
-    emax = block_max(emax, sh);
-    if (threadIdx.x == 0) {
-        err[k] = emax;
+    // the error of the iteration: max over the cluster
+    double dummy = 0.0;
+    block_max2(emax, dummy, sh);
+    double* red = P.base + (10 + NCACHE) * m;
+    if (threadIdx.x == 0) red[0] = emax;
+    cl.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double e = 0.0;
+        for (int r = 0; r < C; ++r) e = fmax(e, P.of(cl, r)[(10 + NCACHE) * m]);
+        err[k] = e;
         if (bump) *dk_mut = k + 1;
     }
+    cl.sync();  // no CTA leaves while another may still read its region
 }
 
 __global__ void k_set_active(const int* dk, Active* a, int first_slice, int n_inst, int N)
@@ -293,10 +390,49 @@ __global__ void k_set_active(const int* dk, Active* a, int first_slice, int n_in
     a->end = hi;
 }
 
-// Doubles of workspace of one coarse step: state, next state, cell cache.
-size_t work_doubles(int nx) { return (size_t)(10 + NCACHE) * nx; }
+// CTAs of the coarse cluster: blocks of about 32 cells (one warp each; the
+// local steps are chains of dependent FP64 operations, so a block's cells
+// share an SM's FP64 pipe with no other warp), at most 16 CTAs, none empty
+// (C = ceil(nx / m) for the block size m).
+int coarse_ctas(int nx)
+{
+    const int C0 = nx >= 512 ? 16 : nx > 32 ? (nx + 31) / 32 : 1;
+    const int m = (nx + C0 - 1) / C0;
+    return (nx + m - 1) / m;
+}
 
-bool fits_smem(int nx) { return work_doubles(nx) * sizeof(double) <= 200 * 1024; }
+// Doubles of global workspace of a coarse step (one region per CTA).
+size_t work_doubles(int nx)
+{
+    const int C = coarse_ctas(nx), m = (nx + C - 1) / C;
+    return (size_t)C * region_doubles(m);
+}
+
+bool fits_smem(int nx)
+{
+    const int C = coarse_ctas(nx), m = (nx + C - 1) / C;
+    return region_doubles(m) * sizeof(double) <= 200 * 1024;
+}
+
+template <typename... Args>
+cudaError_t launch_cluster(void (*fn)(Args...), int nx, cudaStream_t s, Args... args)
+{
+    const int C = coarse_ctas(nx), m = (nx + C - 1) / C;
+    const int use = fits_smem(nx);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(m < CT ? (m + 31) / 32 * 32 : CT, 1, 1);
+    cfg.dynamicSmemBytes = use ? region_doubles(m) * sizeof(double) : 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, args...);
+}
 
 }  // namespace
 
@@ -307,6 +443,7 @@ void prepare_coarse_kernels(int max_smem)
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaGetLastError();
     }
 }
@@ -314,22 +451,15 @@ void prepare_coarse_kernels(int max_smem)
 cudaError_t launch_coarse(const CoarseParams& p, const double* Vin, double* Vout, double dT, double* work,
                           int* status, cudaStream_t s)
 {
-    int use = fits_smem(p.nx);
-    size_t smem = use ? work_doubles(p.nx) * sizeof(double) : 0;
-    int threads = p.nx < CT ? ((p.nx + 31) / 32) * 32 : CT;
-    k_coarse<<<1, threads, smem, s>>>(p, Vin, Vout, dT, work, use, status);
-    return cudaGetLastError();
+    return launch_cluster(k_coarse, p.nx, s, p, Vin, Vout, dT, work, (int)fits_smem(p.nx), status);
 }
 
 cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk, double* U, const double* PFL,
                          double* Gs, double* err, double* work, int* status, int bump, int* dk_mut,
                          cudaStream_t s)
 {
-    int use = fits_smem(p.nx);
-    size_t smem = use ? work_doubles(p.nx) * sizeof(double) : 0;
-    int threads = p.nx < CT ? ((p.nx + 31) / 32) * 32 : CT;
-    k_sweep<<<1, threads, smem, s>>>(p, N, dT, dk, U, PFL, Gs, err, work, use, status, bump, dk_mut);
-    return cudaGetLastError();
+    return launch_cluster(k_sweep, p.nx, s, p, N, dT, dk, U, PFL, Gs, err, work, (int)fits_smem(p.nx), status,
+                          bump, dk_mut);
 }
 
 size_t coarse_work_doubles(int nx) { return work_doubles(nx); }

@@ -40,15 +40,26 @@ def test_coarse_step_matches_oracle(bc, sound):
         pr.pr_destroy(ctx)
 
 
-def test_coarse_step_large_grid_uses_global_work():
-    nx = 3000  # state does not fit shared memory
-    V = O.prim_to_cons(W.sod(nx))
-    ctx = _ctx(nx=nx, nv=4, N=1)
+@pytest.mark.parametrize("nx,bc", [
+    (1, pr.PR_BC_PERIODIC), (2, pr.PR_BC_REFLECT),   # one CTA
+    (17, pr.PR_BC_PERIODIC),                          # 2 CTAs of 9 and 8 cells
+    (130, pr.PR_BC_REFLECT),                          # 15 CTAs of 9 cells, the last of 4
+    (3000, pr.PR_BC_OUTFLOW),                         # 16 CTAs, blocks in shared memory
+    (40000, pr.PR_BC_PERIODIC),                       # 16 CTAs, blocks in the global workspace
+])
+def test_coarse_step_on_cluster_blocks_matches_oracle(nx, bc):
+    # the coarse step runs on a cluster of CTAs owning contiguous blocks of
+    # cells; neighbours across blocks and the boundary ghosts come from the
+    # owners' regions
+    V = O.prim_to_cons(W.sod(nx) if nx > 2 else np.array([[1.0, 0.9][:nx], [0.1, -0.2][:nx], [0.0] * nx,
+                                                          [0.0] * nx, [1.0, 1.2][:nx]]))
+    ctx = _ctx(nx=nx, nv=4, N=1, bc=bc)
+    dT = 2e-3 if nx < 10000 else 2e-4
     try:
-        out = pr.pr_coarse_step(ctx, V, 2e-3)
+        out = pr.pr_coarse_step(ctx, V, dT)
     finally:
         pr.pr_destroy(ctx)
-    ref, _ = O.coarse_run(nx, O.BC_OUTFLOW, 0.5, 2e-3, V)
+    ref, _ = O.coarse_run(nx, BC[bc], 0.5, dT, V)
     assert moment_rel_err(out, ref) < 1e-14
 
 
