@@ -246,7 +246,9 @@ int pr_batch_sync(pr_batch* b);
 int pr_batch_set_lift_order(pr_batch* b, int order);
 
 /* Tile width (x cells per work item) used for instance i, and whether it came
- * from the autotuner (1) or the default (0). */
+ * from the autotuner (1) or the default (0).  The default is 32 cells (capped at
+ * nx), narrowed to 16 and then 8 while the batch has fewer work items than the
+ * fine kernel has resident CTAs. */
 int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned);
 
 /* Set the tile width (x cells per work item, 1..64; capped at each instance's

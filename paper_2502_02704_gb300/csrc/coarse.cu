@@ -24,6 +24,7 @@
 // is compiled without floating-point contraction so that the arithmetic is
 // the plain IEEE sequence of the formulas above (with rho's reciprocal times
 // the momenta for the primitive variables).
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -56,19 +57,6 @@ __device__ __forceinline__ Prim prim(const double* v)
     return q;
 }
 
-__device__ double block_max(double v, double* sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    for (int k = 0; k < nw; ++k) r = fmax(r, sh[k]);
-    return r;
-}
-
 // Two maxima over the CTA in one pass (sh holds 2 doubles per warp).
 __device__ void block_max2(double& a, double& b, double* sh)
 {
@@ -94,22 +82,24 @@ __device__ void block_max2(double& a, double& b, double* sh)
 }
 
 // Per-cell values of one substep, computed once from the state before it:
-// u_x, u_y, u_z, theta, p, the Euler flux h (5) and the wave speed, stored
-// [NCACHE][nx].  A face then combines two cached cells; a reflecting ghost
-// (rho u_x negated) has u_x and h_0, h_2, h_3, h_4 negated, which is exactly
-// what the same formulas give on the mirrored state.
+// the Euler flux h (5) and the wave speed s, then for the Navier-Stokes
+// model u_x, u_y, u_z, theta and p, stored [NCACHE][m].  A face combines two
+// cells; a reflecting ghost (rho u_x negated) has u_x and h_0, h_2, h_3, h_4
+// negated, which is exactly what the same formulas give on the mirrored
+// state.  Substeps alternate between two caches (and two slots of CFL
+// maxima), so a CTA fills the next cache while its peers may still read the
+// current one: one cluster barrier per substep orders everything.
 constexpr int NCACHE = 11;
+constexpr int NRED = 4;  // (max speed, max theta) for each of the two caches
+constexpr unsigned long long SIGN = 0x8000000000000000ull;
 
-struct CellF {
-    double v[5], ux, uy, uz, th, p, h[5], s;
-};
-
-// Region of one cluster CTA (m cells): state A[5][m], next state B[5][m],
-// cell cache [NCACHE][m], then 2 doubles of the CTA's CFL maxima.  Lives in
-// the CTA's shared memory, or in a global workspace (one region per CTA)
-// when m cells do not fit; peers read it through distributed shared memory
-// or plainly, ordered by the cluster barriers.
-__host__ __device__ inline size_t region_doubles(int m) { return (size_t)(10 + NCACHE) * m + 2; }
+// Region of one cluster CTA (m cells): states A[5][m] and B[5][m], caches
+// K0 and K1 [NCACHE][m], the CFL maxima of K0 and K1, then the CTA's face
+// fluxes [5][m+1].  Lives in the CTA's shared memory, or in a global
+// workspace (one region per CTA) when m cells do not fit; peers read states
+// and caches through distributed shared memory or plainly, ordered by the
+// cluster barriers.
+__host__ __device__ inline size_t region_doubles(int m) { return (size_t)(15 + 2 * NCACHE) * m + NRED + 5; }
 
 struct Peers {
     double* base;      // this CTA's region
@@ -124,169 +114,236 @@ struct Peers {
     }
 };
 
-// Cell c of the whole domain (ghosts through the boundary rule) from the
-// state at offset cur_off and the cache of its owner.
-__device__ __forceinline__ void fetch(cg::cluster_group& cl, const Peers& P, int cur_off, int nx, int bc, int c,
-                                      CellF& o)
+__device__ __forceinline__ double flip_sign(double x, unsigned long long mask)
 {
-    int cc = c;
-    bool flip = false;
-    if (c < 0 || c >= nx) {
-        if (bc == 0) cc = ((c % nx) + nx) % nx;
-        else if (bc == 1) cc = c < 0 ? 0 : nx - 1;
-        else {
-            cc = c < 0 ? -1 - c : 2 * nx - 1 - c;
-            flip = true;
-        }
-    }
-    const int m = P.m, b0 = P.rank * m;
-    int owner, li;
-    if (cc >= b0 && cc < b0 + m) owner = P.rank, li = cc - b0;              // own block
-    else if (cc == b0 - 1) owner = P.rank - 1, li = m - 1;                  // left neighbour block
-    else if (cc == b0 + m) owner = P.rank + 1, li = 0;                      // right neighbour block
-    else owner = cc / m, li = cc - owner * m;                               // a wrapped or mirrored ghost
-    const double* R = P.of(cl, owner);
-    const double* V = R + cur_off;
-    const double* Cc = R + 10 * m;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) o.v[q] = V[q * m + li];
-    o.ux = Cc[li];
-    o.uy = Cc[m + li];
-    o.uz = Cc[2 * m + li];
-    o.th = Cc[3 * m + li];
-    o.p = Cc[4 * m + li];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) o.h[q] = Cc[(5 + q) * m + li];
-    o.s = Cc[10 * m + li];
-    if (flip) {
-        o.v[1] = -o.v[1];
-        o.ux = -o.ux;
-        o.h[0] = -o.h[0];
-        o.h[2] = -o.h[2];
-        o.h[3] = -o.h[3];
-        o.h[4] = -o.h[4];
-    }
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)mask);
 }
 
-// Flux through the face between cells a and b: Rusanov (Eq. 16) plus, when
-// eps > 0, the viscous flux of the compressible Navier-Stokes model (Eq. 8)
-// with mu = rho theta, kappa = 5 rho theta / 2, gradients (b - a)/dx (idx =
-// 1/dx) and coefficients and u averaged over the face.
-__device__ __forceinline__ void face_flux(const CellF& a, const CellF& b, double visc, double idx, double* H)
+// x > 0 (and not NaN) from the bit pattern of x, on the integer pipe.
+__device__ __forceinline__ bool positive(long long b) { return b > 0 && b <= 0x7ff0000000000000ll; }
+
+// The CFL maxima are taken over speeds and temperatures, non-negative in
+// every physical state, where the order of the IEEE bit patterns as unsigned
+// 64-bit integers is the order of the values: integer maxima keep them off
+// this part's narrow FP64 pipe.  Values with the sign bit set (a negative
+// theta, already flagged non-physical) count as 0; a NaN maps above every
+// number and stops G.  The warp maximum of a 64-bit pattern: the maximum high
+// word, then the maximum low word among the lanes holding it.
+__device__ __forceinline__ unsigned long long clamp_sign(long long b) { return b < 0 ? 0ull : (unsigned long long)b; }
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
 {
-    const double S = a.s > b.s ? a.s : b.s;
-#pragma unroll
-    for (int q = 0; q < 5; ++q) H[q] = 0.5 * (a.h[q] + b.h[q]) - 0.5 * S * (b.v[q] - a.v[q]);
-    if (visc > 0.0) {
-        const double eps = visc;
-        double mu = 0.5 * (a.p + b.p);
-        double kappa = 2.5 * mu;
-        double dux = (b.ux - a.ux) * idx, duy = (b.uy - a.uy) * idx, duz = (b.uz - a.uz) * idx, dth = (b.th - a.th) * idx;
-        double ux = 0.5 * (a.ux + b.ux), uy = 0.5 * (a.uy + b.uy), uz = 0.5 * (a.uz + b.uz);
-        double sxx = -eps * mu * (4.0 / 3.0) * dux, sxy = -eps * mu * duy, sxz = -eps * mu * duz;
-        double qh = -eps * kappa * dth;
-        H[0] += 0.0;
-        H[1] += sxx;
-        H[2] += sxy;
-        H[3] += sxz;
-        H[4] += sxx * ux + sxy * uy + sxz * uz + qh;
+    const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(x >> 32));
+    const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(x >> 32) == hi ? (unsigned)x : 0u);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// The cell beyond this CTA's block on one side (side -1: left of its first
+// cell, +1: right of its last): the owner's region, the local index there and
+// the mirror mask.  Interior block edges read the neighbouring rank; the
+// domain ends follow the boundary rule (periodic: the opposite end; outflow:
+// a copy of the end cell; reflecting: the end cell mirrored).
+__device__ __forceinline__ const double* beyond_block(cg::cluster_group& cl, const Peers& P, int C, int nx, int bc,
+                                                      int side, int& lj, unsigned long long& mask)
+{
+    const int last_lj = nx - 1 - (C - 1) * P.m;  // local index of cell nx-1 on rank C-1
+    int r;
+    mask = 0ull;
+    if (side < 0) {
+        if (P.rank > 0) r = P.rank - 1, lj = P.m - 1;
+        else if (bc == 0) r = C - 1, lj = last_lj;
+        else r = 0, lj = 0, mask = bc == 2 ? SIGN : 0ull;
+    } else {
+        if (P.rank < C - 1) r = P.rank + 1, lj = 0;
+        else if (bc == 0) r = 0, lj = 0;
+        else r = C - 1, lj = last_lj, mask = bc == 2 ? SIGN : 0ull;
     }
+    return P.of(cl, r);
 }
 
 // G over dT applied to this CTA's cells [c0, c1) of the state at region
 // offset 0 (A), with the other CTAs of the cluster doing theirs; the result
-// ends in A.  Per local step: one pass caching each own cell's primitives,
-// flux and speed and its CTA's two CFL maxima, a cluster barrier, the
-// cluster maxima, one pass forming each own cell's two face fluxes (peer
-// cells through the owners' regions) and its update into B, a cluster
-// barrier; A and B swap roles.  Every CTA takes the same local steps.
-// (Forming each face once into a face array, with one more CTA barrier,
-// measured no faster: the step is a chain of dependent FP64 operations.)
+// ends in A.  Per local step:
+//   1. one thread per own cell: primitives, flux h, speed (and the
+//      Navier-Stokes primitives) into the cache, the CTA's CFL maxima;
+//   2. one cluster barrier; the cluster maxima (one rank per lane), dt;
+//   3. one thread per (face, component) of the block's mc + 1 faces: the
+//      Rusanov flux of Eq. (16) (plus the viscous flux of Eq. (8)), the
+//      cells beyond the block through their owners' regions;
+//   4. one thread per (cell, component): the update of Eq. (15) into the
+//      other state (plus the force source).
+// Spreading steps 3 and 4 over all warps of the CTA keeps the FP64
+// instructions of any one warp few: this part's FP64 pipe takes tens of
+// cycles per warp instruction, and the local step is a chain of them.  A
+// cluster barrier after the last local step ends every peer read before the
+// caller reuses A.  Every CTA takes the same local steps.
+template <bool VISC>
 __device__ void coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peers& P, int C, int c0, int c1,
-                         double dT, int* status, double* sh)
+                         double dT, int* status, unsigned long long* sh)
 {
-    const int nx = p.nx, m = P.m, mc = c1 - c0;
+    const int nx = p.nx, m = P.m, mc = c1 - c0, nf = mc + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int cell_warps = (min(mc, (int)blockDim.x) + 31) >> 5;
+    // the face pass runs on every warp but the last (which takes dt) when
+    // the CTA has more than one
+    const int face_threads = nw > 1 ? (nw - 1) * 32 : 32;
+    const int face_thread = nw > 1 && warp == nw - 1 ? 5 * nf : (int)threadIdx.x;
     double* R = P.base;
-    double* Cc = R + 10 * m;
-    double* red = R + (10 + NCACHE) * m;
-    int cur_off = 0, nxt_off = 5 * m;
+    const int red_off = (10 + 2 * NCACHE) * m;
+    double* F = R + red_off + NRED;  // face fluxes [5][m + 1]
+    int lL, lR;
+    unsigned long long mL, mR;
+    const double* RL = beyond_block(cl, P, C, nx, p.bc, -1, lL, mL);
+    const double* RR = beyond_block(cl, P, C, nx, p.bc, +1, lR, mR);
+    int cur_off = 0, nxt_off = 5 * m, buf = 0;
     const double idx = 1.0 / p.dx;
     double t = 0.0;
     while (t < dT) {
         const double* cur = R + cur_off;
-        double smax = 0.0, thmax = 0.0;
+        const int ko = (10 + buf * NCACHE) * m;  // this substep's cache
+        double* K = R + ko;
+        unsigned long long smax = 0, thmax = 0;
         bool bad = false;
         for (int li = threadIdx.x; li < mc; li += blockDim.x) {
             double v[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) v[q] = cur[q * m + li];
             Prim pr = prim(v);
-            if (!(v[0] > 0.0) || !(pr.th > 0.0)) bad = true;
+            const long long rb = __double_as_longlong(v[0]), tb = __double_as_longlong(pr.th);
+            if (!positive(rb) || !positive(tb)) bad = true;
             double c = p.sound == 1 ? sqrt(pr.th) : sqrt(pr.th * (5.0 / 3.0));
             double s = fabs(pr.ux) + c;
-            if (s > smax) smax = s;
-            if (pr.th > thmax) thmax = pr.th;
-            Cc[li] = pr.ux;
-            Cc[m + li] = pr.uy;
-            Cc[2 * m + li] = pr.uz;
-            Cc[3 * m + li] = pr.th;
-            Cc[4 * m + li] = pr.p;
-            Cc[5 * m + li] = v[1];
-            Cc[6 * m + li] = v[1] * pr.ux + pr.p;
-            Cc[7 * m + li] = v[1] * pr.uy;
-            Cc[8 * m + li] = v[1] * pr.uz;
-            Cc[9 * m + li] = pr.ux * (v[4] + pr.p);
-            Cc[10 * m + li] = s;
-        }
-        if (bad) atomicCAS(status, 0, ST_NONPHYS);
-        block_max2(smax, thmax, sh);
-        if (threadIdx.x == 0) {
-            red[0] = smax;
-            red[1] = thmax;
-        }
-        cl.sync();  // caches, states and CTA maxima of every rank visible
-        for (int r = 0; r < C; ++r) {
-            const double* rr = P.of(cl, r) + (10 + NCACHE) * m;
-            smax = fmax(smax, rr[0]);
-            thmax = fmax(thmax, rr[1]);
-        }
-        if (!(smax > 0.0) || isnan(smax)) break;  // the same on every rank
-        double rem = dT - t;
-        double dt = p.cfl * p.dx / smax;
-        if (p.visc > 0.0) {
-            double dtv = p.cfl * p.dx * p.dx / (2.0 * p.visc * (5.0 / 3.0) * thmax);
-            if (dtv < dt) dt = dtv;
-        }
-        bool last = false;
-        if (dt >= rem) {
-            dt = rem;
-            last = true;
-        }
-        double* nxt = R + nxt_off;
-        const double dtdx = dt / p.dx;
-        for (int li = threadIdx.x; li < mc; li += blockDim.x) {
-            const int i = c0 + li;
-            CellF L, M, Rt;
-            fetch(cl, P, cur_off, nx, p.bc, i - 1, L);
-            fetch(cl, P, cur_off, nx, p.bc, i, M);
-            fetch(cl, P, cur_off, nx, p.bc, i + 1, Rt);
-            double Hl[5], Hr[5];
-            face_flux(L, M, p.visc, idx, Hl);
-            face_flux(M, Rt, p.visc, idx, Hr);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) nxt[q * m + li] = cur[q * m + li] - dtdx * (Hr[q] - Hl[q]);
-            if (p.E) {  // exterior force: forward-Euler source on the old state
-                nxt[1 * m + li] += dt * cur[0 * m + li] * p.E[i];
-                nxt[4 * m + li] += dt * cur[1 * m + li] * p.E[i];
+            smax = max(smax, clamp_sign(__double_as_longlong(s)));
+            thmax = max(thmax, clamp_sign(tb));
+            K[li] = v[1];
+            K[m + li] = v[1] * pr.ux + pr.p;
+            K[2 * m + li] = v[1] * pr.uy;
+            K[3 * m + li] = v[1] * pr.uz;
+            K[4 * m + li] = pr.ux * (v[4] + pr.p);
+            K[5 * m + li] = s;
+            if (VISC) {
+                K[6 * m + li] = pr.ux;
+                K[7 * m + li] = pr.uy;
+                K[8 * m + li] = pr.uz;
+                K[9 * m + li] = pr.th;
+                K[10 * m + li] = pr.p;
             }
         }
-        cl.sync();  // every rank's reads of the old states and caches are over
+        if (bad) atomicCAS(status, 0, ST_NONPHYS);
+        smax = warp_max_u64(smax);
+        thmax = warp_max_u64(thmax);
+        double* red = R + red_off + 2 * buf;
+        if (cell_warps == 1) {  // only warp 0 holds cells
+            if (threadIdx.x == 0) red[0] = __longlong_as_double(smax), red[1] = __longlong_as_double(thmax);
+        } else {
+            if (lane == 0) sh[2 * warp] = smax, sh[2 * warp + 1] = thmax;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long a = 0, b = 0;
+                for (int w = 0; w < cell_warps; ++w) a = max(a, sh[2 * w]), b = max(b, sh[2 * w + 1]);
+                red[0] = __longlong_as_double(a);
+                red[1] = __longlong_as_double(b);
+            }
+        }
+        cl.sync();  // caches, states and CTA maxima of every rank visible
+        // 2. the last warp (the fewest face items) takes the cluster maxima
+        // and dt while the others start on the faces, which need neither
+        if (warp == nw - 1) {
+            smax = 0;
+            thmax = 0;
+            if (lane < C) {
+                const double* rr = P.of(cl, lane) + red_off + 2 * buf;
+                smax = __double_as_longlong(rr[0]);
+                thmax = __double_as_longlong(rr[1]);
+            }
+            smax = warp_max_u64(smax);
+            thmax = warp_max_u64(thmax);
+            const double sm = __longlong_as_double(smax);
+            unsigned long long flags = 0;  // 1: last local step, 2: stop (degenerate speeds)
+            double dt = 0.0;
+            if (!(sm > 0.0) || isnan(sm)) {
+                flags = 2;
+            } else {
+                const double rem = dT - t;
+                dt = p.cfl * p.dx / sm;
+                if (VISC) {
+                    double dtv = p.cfl * p.dx * p.dx / (2.0 * p.visc * (5.0 / 3.0) * __longlong_as_double(thmax));
+                    if (dtv < dt) dt = dtv;
+                }
+                if (dt >= rem) {
+                    dt = rem;
+                    flags = 1;
+                }
+            }
+            if (lane == 0) sh[0] = __double_as_longlong(dt), sh[1] = flags;
+        }
+        // 3. face f of the block lies between its cells f - 1 and f
+        for (int w = face_thread; w < 5 * nf; w += face_threads) {
+            const int q = w / nf, f = w - q * nf;
+            const double* Ra = f > 0 ? R : RL;
+            const double* Rb = f < mc ? R : RR;
+            const int ia = f > 0 ? f - 1 : lL, ib = f < mc ? f : lR;
+            const unsigned long long ma = f > 0 ? 0ull : mL, mb = f < mc ? 0ull : mR;
+            // mirrored: rho u_x (q = 1) of the state, every flux component but h_1
+            const unsigned long long va_m = q == 1 ? ma : 0ull, ha_m = q == 1 ? 0ull : ma;
+            const unsigned long long vb_m = q == 1 ? mb : 0ull, hb_m = q == 1 ? 0ull : mb;
+            const double va = flip_sign(Ra[cur_off + q * m + ia], va_m);
+            const double vb = flip_sign(Rb[cur_off + q * m + ib], vb_m);
+            const double ha = flip_sign(Ra[ko + q * m + ia], ha_m);
+            const double hb = flip_sign(Rb[ko + q * m + ib], hb_m);
+            const long long sa = __double_as_longlong(Ra[ko + 5 * m + ia]);
+            const long long sb = __double_as_longlong(Rb[ko + 5 * m + ib]);
+            const double S = __longlong_as_double(sa > sb ? sa : sb);
+            double H = 0.5 * (ha + hb) - 0.5 * S * (vb - va);
+            if (VISC && q > 0) {
+                const double eps = p.visc;
+                const double* Ka = Ra + ko + ia;
+                const double* Kb = Rb + ko + ib;
+                const double mu = 0.5 * (Ka[10 * m] + Kb[10 * m]);
+                const double uxa = flip_sign(Ka[6 * m], ma), uxb = flip_sign(Kb[6 * m], mb);
+                const double dux = (uxb - uxa) * idx;
+                const double sxx = -eps * mu * (4.0 / 3.0) * dux;
+                if (q == 1) {
+                    H += sxx;
+                } else if (q == 2) {
+                    H += -eps * mu * ((Kb[7 * m] - Ka[7 * m]) * idx);
+                } else if (q == 3) {
+                    H += -eps * mu * ((Kb[8 * m] - Ka[8 * m]) * idx);
+                } else {
+                    const double duy = (Kb[7 * m] - Ka[7 * m]) * idx, duz = (Kb[8 * m] - Ka[8 * m]) * idx;
+                    const double dth = (Kb[9 * m] - Ka[9 * m]) * idx;
+                    const double ux = 0.5 * (uxa + uxb), uy = 0.5 * (Ka[7 * m] + Kb[7 * m]);
+                    const double uz = 0.5 * (Ka[8 * m] + Kb[8 * m]);
+                    const double sxy = -eps * mu * duy, sxz = -eps * mu * duz;
+                    const double qh = -eps * (2.5 * mu) * dth;
+                    H += sxx * ux + sxy * uy + sxz * uz + qh;
+                }
+            }
+            F[q * (m + 1) + f] = H;
+        }
+        __syncthreads();
+        const double dt = __longlong_as_double(sh[0]);
+        const unsigned long long flags = sh[1];
+        if (flags & 2) break;  // the same on every rank
+        const bool last = flags & 1;
+        // 4. update of Eq. (15), forward-Euler force source on the old state
+        double* nxt = R + nxt_off;
+        const double dtdx = dt * idx;
+        for (int w = threadIdx.x; w < 5 * mc; w += blockDim.x) {
+            const int q = w / mc, li = w - q * mc;
+            double u = cur[q * m + li] - dtdx * (F[q * (m + 1) + li + 1] - F[q * (m + 1) + li]);
+            if (p.E && (q == 1 || q == 4)) u += dt * cur[(q == 1 ? 0 : 1) * m + li] * p.E[c0 + li];
+            nxt[q * m + li] = u;
+        }
+        __syncthreads();  // the next local step reads nxt by cell
         const int tmp = cur_off;
         cur_off = nxt_off;
         nxt_off = tmp;
+        buf ^= 1;
         if (last) break;
         t += dt;
     }
+    cl.sync();  // every rank's reads of this region are over
     if (cur_off != 0) {
         for (int li = threadIdx.x; li < mc; li += blockDim.x)
 #pragma unroll
@@ -308,11 +365,12 @@ __device__ __forceinline__ Peers make_peers(double* dsm, double* work, int use_s
 }
 
 // One G over dT of Vin (device [5][nx]) into Vout; one cluster of C CTAs.
+template <bool VISC>
 __global__ void __launch_bounds__(CT)
 k_coarse(CoarseParams p, const double* Vin, double* Vout, double dT, double* work, int use_smem, int* status)
 {
     extern __shared__ __align__(16) double dsm[];
-    __shared__ double sh[2 * (CT / 32)];
+    __shared__ unsigned long long sh[2 * (CT / 32)];
     cg::cluster_group cl = cg::this_cluster();
     const int nx = p.nx, C = gridDim.x, m = (nx + C - 1) / C;
     const int c0 = (int)blockIdx.x * m, c1 = min(nx, c0 + m);
@@ -321,7 +379,7 @@ k_coarse(CoarseParams p, const double* Vin, double* Vout, double dT, double* wor
 #pragma unroll
         for (int q = 0; q < 5; ++q) P.base[q * m + li] = Vin[q * nx + c0 + li];
     __syncthreads();
-    coarse_G(p, cl, P, C, c0, c1, dT, status, sh);
+    coarse_G<VISC>(p, cl, P, C, c0, c1, dT, status, sh);
     for (int li = threadIdx.x; li < c1 - c0; li += blockDim.x)
 #pragma unroll
         for (int q = 0; q < 5; ++q) Vout[q * nx + c0 + li] = P.base[q * m + li];
@@ -330,12 +388,13 @@ k_coarse(CoarseParams p, const double* Vin, double* Vout, double dT, double* wor
 
 // Algorithm 2's sequential sweep over n = max(k,1)..N on one cluster of C
 // CTAs, each owning a contiguous block of cells.
+template <bool VISC>
 __global__ void __launch_bounds__(CT)
 k_sweep(CoarseParams p, int N, double dT, const int* dk, double* U, const double* PFL, double* Gs, double* err,
         double* work, int use_smem, int* status, int bump, int* dk_mut)
 {
     extern __shared__ __align__(16) double dsm[];
-    __shared__ double sh[2 * (CT / 32)];
+    __shared__ unsigned long long sh[2 * (CT / 32)];
     cg::cluster_group cl = cg::this_cluster();
     const int nx = p.nx, sz = 5 * nx, C = gridDim.x, m = (nx + C - 1) / C;
     const int c0 = (int)blockIdx.x * m, c1 = min(nx, c0 + m), mc = c1 - c0;
@@ -348,7 +407,7 @@ k_sweep(CoarseParams p, int N, double dT, const int* dk, double* U, const double
 #pragma unroll
             for (int q = 0; q < 5; ++q) A[q * m + li] = U[(size_t)(n - 1) * sz + q * nx + c0 + li];
         __syncthreads();
-        coarse_G(p, cl, P, C, c0, c1, dT, status, sh);
+        coarse_G<VISC>(p, cl, P, C, c0, c1, dT, status, sh);
         for (int li = threadIdx.x; li < mc; li += blockDim.x)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
@@ -364,13 +423,13 @@ k_sweep(CoarseParams p, int N, double dT, const int* dk, double* U, const double
     }
     // the error of the iteration: max over the cluster
     double dummy = 0.0;
-    block_max2(emax, dummy, sh);
-    double* red = P.base + (10 + NCACHE) * m;
-    if (threadIdx.x == 0) red[0] = emax;
+    block_max2(emax, dummy, reinterpret_cast<double*>(sh));
+    const int red_off = (10 + 2 * NCACHE) * m;
+    if (threadIdx.x == 0) P.base[red_off] = emax;
     cl.sync();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double e = 0.0;
-        for (int r = 0; r < C; ++r) e = fmax(e, P.of(cl, r)[(10 + NCACHE) * m]);
+        for (int r = 0; r < C; ++r) e = fmax(e, P.of(cl, r)[red_off]);
         err[k] = e;
         if (bump) *dk_mut = k + 1;
     }
@@ -390,9 +449,10 @@ __global__ void k_set_active(const int* dk, Active* a, int first_slice, int n_in
     a->end = hi;
 }
 
-// CTAs of the coarse cluster: blocks of about 32 cells (one warp each; the
-// local steps are chains of dependent FP64 operations, so a block's cells
-// share an SM's FP64 pipe with no other warp), at most 16 CTAs, none empty
+// CTAs of the coarse cluster: blocks of about 32 cells (the per-cell pass of
+// a local step is then one warp per CTA, the face and update passes a few
+// warps; more CTAs would shorten no warp's chain of FP64 instructions and
+// only add participants to the cluster barrier), at most 16 CTAs, none empty
 // (C = ceil(nx / m) for the block size m).
 int coarse_ctas(int nx)
 {
@@ -421,7 +481,8 @@ cudaError_t launch_cluster(void (*fn)(Args...), int nx, cudaStream_t s, Args... 
     const int use = fits_smem(nx);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(m < CT ? (m + 31) / 32 * 32 : CT, 1, 1);
+    // a thread per face component, and one more warp for the local step dt
+    cfg.blockDim = dim3(std::min(CT, (5 * (m + 1) + 31) / 32 * 32 + 32), 1, 1);
     cfg.dynamicSmemBytes = use ? region_doubles(m) * sizeof(double) : 0;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -438,7 +499,8 @@ cudaError_t launch_cluster(void (*fn)(Args...), int nx, cudaStream_t s, Args... 
 
 void prepare_coarse_kernels(int max_smem)
 {
-    const void* fns[2] = {reinterpret_cast<const void*>(&k_coarse), reinterpret_cast<const void*>(&k_sweep)};
+    const void* fns[4] = {reinterpret_cast<const void*>(&k_coarse<false>), reinterpret_cast<const void*>(&k_coarse<true>),
+                          reinterpret_cast<const void*>(&k_sweep<false>), reinterpret_cast<const void*>(&k_sweep<true>)};
     for (const void* fn : fns) {
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
@@ -451,15 +513,16 @@ void prepare_coarse_kernels(int max_smem)
 cudaError_t launch_coarse(const CoarseParams& p, const double* Vin, double* Vout, double dT, double* work,
                           int* status, cudaStream_t s)
 {
-    return launch_cluster(k_coarse, p.nx, s, p, Vin, Vout, dT, work, (int)fits_smem(p.nx), status);
+    return launch_cluster(p.visc > 0.0 ? k_coarse<true> : k_coarse<false>, p.nx, s, p, Vin, Vout, dT, work,
+                          (int)fits_smem(p.nx), status);
 }
 
 cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk, double* U, const double* PFL,
                          double* Gs, double* err, double* work, int* status, int bump, int* dk_mut,
                          cudaStream_t s)
 {
-    return launch_cluster(k_sweep, p.nx, s, p, N, dT, dk, U, PFL, Gs, err, work, (int)fits_smem(p.nx), status,
-                          bump, dk_mut);
+    return launch_cluster(p.visc > 0.0 ? k_sweep<true> : k_sweep<false>, p.nx, s, p, N, dT, dk, U, PFL, Gs, err, work,
+                          (int)fits_smem(p.nx), status, bump, dk_mut);
 }
 
 size_t coarse_work_doubles(int nx) { return work_doubles(nx); }

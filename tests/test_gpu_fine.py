@@ -192,6 +192,25 @@ def test_full_size_smooth_periodic_three_knudsen_numbers(precision):
     O.set_threads(1)
 
 
+def test_default_tile_width_follows_batch_size():
+    # a batch with fewer items than resident CTAs takes narrower tiles; one
+    # that fills the GPU keeps 32 columns; widths never exceed nx
+    def default_tiles(insts):
+        b = pr.pr_batch_create(insts, pr.PR_MIXED)
+        try:
+            return [pr.pr_batch_tile(b, i) for i in range(len(insts))]
+        finally:
+            pr.pr_batch_destroy(b)
+
+    small = default_tiles([pr.instance(64, 16, pr.fine_dt(64, 16, 8.0), eps=1e-2)])
+    assert small == [(8, False)]
+    tiny = default_tiles([pr.instance(5, 8, pr.fine_dt(5, 8, 8.0), eps=1e-2)])
+    assert tiny == [(5, False)]
+    big = default_tiles([pr.instance(512, 32, pr.fine_dt(512, 32, 8.0), eps=e, scheme=pr.PR_MUSCL)
+                         for e in (1.0, 1e-2, 1e-4)])
+    assert big == [(32, False)] * 3
+
+
 @pytest.mark.parametrize("tx", [8, 13, 64])
 def test_manual_tile_widths_keep_results(tx):
     # tile width 13 leaves a ragged last tile; widths below 8 are raised to 8
