@@ -40,27 +40,52 @@ def test_coarse_step_matches_oracle(bc, sound):
         pr.pr_destroy(ctx)
 
 
-@pytest.mark.parametrize("nx,bc", [
-    (1, pr.PR_BC_PERIODIC), (2, pr.PR_BC_REFLECT),   # one CTA
-    (17, pr.PR_BC_PERIODIC),                          # 2 CTAs of 9 and 8 cells
-    (130, pr.PR_BC_REFLECT),                          # 15 CTAs of 9 cells, the last of 4
-    (3000, pr.PR_BC_OUTFLOW),                         # 16 CTAs, blocks in shared memory
-    (40000, pr.PR_BC_PERIODIC),                       # 16 CTAs, blocks in the global workspace
+def _block_profile(nx):
+    # smooth part plus a jump at x = 0.4: every component moves, so the
+    # reflecting ghost's flip of rho u_x and the viscous terms all matter
+    x = W.cell_centres(nx, 0.0, 1.0)
+    w = 2 * np.pi * x
+    jump = np.where(x < 0.4, 0.0, 1.0)
+    return np.stack([1 + 0.3 * np.sin(w) - 0.4 * jump, 0.2 * np.cos(w) + 0.1 * jump, 0.1 * np.sin(2 * w),
+                     -0.05 * np.cos(w), 1 + 0.25 * np.sin(w + 0.3) - 0.2 * jump])
+
+
+@pytest.mark.parametrize("model", ["euler", "cns", "euler+E", "cns+E"])
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW, pr.PR_BC_REFLECT])
+@pytest.mark.parametrize("nx", [
+    1, 2, 17,      # one CTA
+    97,            # 4 CTAs of 25 cells, the last of 22
+    130,           # 5 CTAs of 26 cells
+    3000,          # 16 CTAs, blocks in shared memory, the last ragged
+    40000,         # 16 CTAs, blocks in the global workspace
 ])
-def test_coarse_step_on_cluster_blocks_matches_oracle(nx, bc):
+def test_coarse_step_on_cluster_blocks_matches_oracle(nx, bc, model):
     # the coarse step runs on a cluster of CTAs owning contiguous blocks of
-    # cells; neighbours across blocks and the boundary ghosts come from the
-    # owners' regions
-    V = O.prim_to_cons(W.sod(nx) if nx > 2 else np.array([[1.0, 0.9][:nx], [0.1, -0.2][:nx], [0.0] * nx,
-                                                          [0.0] * nx, [1.0, 1.2][:nx]]))
-    ctx = _ctx(nx=nx, nv=4, N=1, bc=bc)
-    dT = 2e-3 if nx < 10000 else 2e-4
+    # cells: faces across blocks and the boundary ghosts come from the
+    # owners' regions; the Navier-Stokes terms and the force source ride on
+    # the same face and update passes
+    eps = 1e-4
+    cns = model.startswith("cns")
+    V = O.prim_to_cons(_block_profile(nx))
+    dT = 2.0 / nx  # about six hyperbolic local steps (more where the viscous limit binds)
+    cm = pr.PR_COARSE_CNS if cns else pr.PR_COARSE_EULER
+    E = 0.5 * np.sin(2 * np.pi * W.cell_centres(nx, 0.0, 1.0)) if model.endswith("+E") else None
+    if E is None:
+        ctx = pr.pr_init(nx, 0.0, 1.0, bc, 4, 8.0, eps, 0.1, 1, coarse_model=cm)
+    else:
+        ctx = pr.pr_init_force(nx, 0.0, 1.0, bc, 4, 4, 8.0, eps, 0.1, 1, E, coarse_model=cm)
     try:
         out = pr.pr_coarse_step(ctx, V, dT)
     finally:
         pr.pr_destroy(ctx)
-    ref, _ = O.coarse_run(nx, BC[bc], 0.5, dT, V)
-    assert moment_rel_err(out, ref) < 1e-14
+    if cns:
+        ref, ns = O.coarse_run_cns(nx, BC[bc], 0.5, dT, V, eps, E=E)
+    elif E is not None:
+        ref, ns = O.coarse_run_force(nx, BC[bc], 0.5, dT, V, E)
+    else:
+        ref, ns = O.coarse_run(nx, BC[bc], 0.5, dT, V)
+    assert ns >= 2
+    assert moment_rel_err(out, ref) < 1e-13
 
 
 @pytest.mark.parametrize("precision,tol", [(pr.PR_FP64, TOL_FP64), (pr.PR_MIXED, TOL_MIXED)])
