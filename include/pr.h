@@ -75,6 +75,13 @@ extern "C" {
                                   central face gradients, local steps also
                                   limited by dx^2 / (2 eps (5/3) max theta)    */
 
+#define PR_FINE_AUTO 0         /* fine phase of a parareal iteration: chosen   */
+#define PR_FINE_TILED 1        /* the persistent tiled kernel (any instance)   */
+#define PR_FINE_CLUSTER 2      /* one thread-block cluster per slice, the slice
+                                  kept in shared memory for all its steps
+                                  (mixed precision, Maxwellian lifting, no
+                                  force, nv = 8 or 16, small nx)               */
+
 /* ---- parameter blocks ---- */
 typedef struct {
     int nx;            /* x cells (>= 1)                                       */
@@ -465,6 +472,27 @@ int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt);
  * result.  Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
 int pr_init_force(pr_ctx** out, const pr_grid* g, const pr_velocity* v, double eps, const pr_time* t, int nvx,
                   const double* E);
+
+/* Kernel of the fine phase of a parareal iteration (pr_init problems):
+ * PR_FINE_AUTO takes the cluster-resident run when it applies (mixed
+ * precision, Maxwellian lifting, nv = 8 or 16, a slice's cells fit the
+ * shared memory of a cluster of <= 16 CTAs) and the resident slices'
+ * clusters run in at most two waves, else the tiled persistent kernel; PR_FINE_TILED and
+ * PR_FINE_CLUSTER force one (PR_EINVAL when the cluster run does not apply or
+ * the problem has a force).  The cluster run lifts, steps and projects a
+ * slice without the batch's global state: it serves pr_parareal_iter / _run;
+ * pr_fine_step always uses the tiled kernel.  The next iteration rebuilds its
+ * captured graph.  Synchronous. */
+int pr_set_fine_path(pr_ctx* ctx, int mode);
+
+/* The kernel the fine phase of an iteration uses: PR_FINE_TILED or
+ * PR_FINE_CLUSTER (never PR_FINE_AUTO). */
+int pr_get_fine_path(const pr_ctx* ctx, int* path);
+
+/* Layout of the cluster-resident fine run for this problem's slices: CTAs
+ * per cluster, x cells per CTA and how many clusters (slices) the device runs
+ * at once; all 0 (and PR_OK) when the run does not apply. */
+int pr_fine_cluster_shape(const pr_ctx* ctx, int* cluster, int* cells_per_cta, int* resident);
 
 /* Step kernel of a pr_init_force problem's fine propagator (its slices are
  * the instances of an internal pr_force): cluster > 0 sets the CTAs per x

@@ -31,6 +31,7 @@ PR_FP64, PR_MIXED = 0, 1
 PR_SOUND_GAMMA53, PR_SOUND_SQRT_THETA = 0, 1
 PR_PRIMITIVE, PR_CONSERVED = 0, 1
 PR_COARSE_EULER, PR_COARSE_CNS = 0, 1
+PR_FINE_AUTO, PR_FINE_TILED, PR_FINE_CLUSTER = 0, 1, 2
 
 _CODES = {PR_EINVAL: "PR_EINVAL", PR_ENOMEM: "PR_ENOMEM", PR_ECUDA: "PR_ECUDA", PR_ETIMEOUT: "PR_ETIMEOUT",
           PR_ENONPHYS: "PR_ENONPHYS", PR_ENOTCONV: "PR_ENOTCONV"}
@@ -128,6 +129,9 @@ _SIGS = {
     "pr_force_dt_stab": (C.c_int, [C.POINTER(pr_force_instance), C.c_double, _D]),
     "pr_force_inject_wait_timeout": (C.c_int, [_VP, C.c_int]),
     "pr_set_force_step": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
+    "pr_set_fine_path": (C.c_int, [_VP, C.c_int]),
+    "pr_get_fine_path": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+    "pr_fine_cluster_shape": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "pr_init_force": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_grid), C.POINTER(pr_velocity), C.c_double,
                                 C.POINTER(pr_time), C.c_int, _D]),
 }
@@ -566,6 +570,26 @@ def pr_init_force(nx, x0, x1, bc, nvx, nvp, L, eps, T, n_slices, E, cfl_f=0.5, c
     if rc != PR_OK:
         raise PrError(rc, (lib().pr_last_error(None) or b"").decode())
     return _Handle(out, "pr_ctx", nx=nx, nv=nvp, nvx=nvx, N=n_slices)
+
+
+def pr_set_fine_path(ctx, mode):
+    """Kernel of the fine phase of a parareal iteration (PR_FINE_AUTO / _TILED / _CLUSTER)."""
+    _ctx_check(ctx, lib().pr_set_fine_path(ctx.ptr, int(mode)))
+
+
+def pr_get_fine_path(ctx):
+    """The kernel the fine phase of an iteration uses (PR_FINE_TILED or PR_FINE_CLUSTER)."""
+    v = C.c_int()
+    _ctx_check(ctx, lib().pr_get_fine_path(ctx.ptr, C.byref(v)))
+    return v.value
+
+
+def pr_fine_cluster_shape(ctx):
+    """(CTAs per cluster, x cells per CTA, clusters resident at once) of the
+    cluster-resident fine run, zeros when it does not apply."""
+    a, b, r = C.c_int(), C.c_int(), C.c_int()
+    _ctx_check(ctx, lib().pr_fine_cluster_shape(ctx.ptr, C.byref(a), C.byref(b), C.byref(r)))
+    return a.value, b.value, r.value
 
 
 def pr_set_force_step(ctx, cluster=0, columns=-1, persistent=-1):

@@ -32,9 +32,12 @@
 // step s-1 (bounded spin on a flag; a time-out aborts the launch with a status
 // code).  Tickets are taken only by running CTAs and an item waits only on
 // smaller tickets, so the lowest unfinished ticket never waits.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "pr_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace prk {
 
@@ -321,7 +324,7 @@ __device__ bool wait_tiles(const Inst& I, int xt, unsigned target, int* status, 
                     break;
                 }
                 __nanosleep(ns);
-                if (ns < 1024) ns <<= 1;
+                if (ns < 128) ns <<= 1;
             }
         }
     }
@@ -797,6 +800,261 @@ k_state_moments(const Inst* __restrict__ insts, InstState* st, int b)
     if (c == 0 && threadIdx.x == 0) st[b].a0 = 1.0;
 }
 
+// ---- cluster-resident fine run ----
+// For instances small enough to live in the shared memory of one thread-block
+// cluster: CTA r of the cluster owns x cells [r w, r w + w) with all nv^3
+// velocities, as the storage form above (g and the factor tables, two
+// buffers each).  A step reconstructs f of its cells and of 2H halo cells --
+// the neighbouring CTAs' cells (or the boundary ghosts) read from their
+// shared memory through the cluster's distributed shared memory -- marches
+// along x as the tiled kernel does, sums the moments of its own cells over
+// all velocities in the CTA, and builds the tables of the next state; one
+// cluster barrier per step publishes both buffers.  Lift, n steps and the
+// projection run in one launch with no global-memory traffic in between, so
+// a step costs a few microseconds instead of the dependency chain of global
+// flags, partial sums and tile finalisers of the tiled kernel (which a
+// batch too small to fill the GPU exposes).  float32 f, 8 v_z nodes per
+// thread, nv^3 / 8 threads per CTA.
+constexpr int CLV = 8;
+
+__host__ __device__ inline size_t cl_floats_offset(int w, int nv, int nt)
+{
+    const size_t nv3 = (size_t)nv * nv * nv, tw = 3 * (size_t)nv;
+    return align16((2 * (size_t)w * nv3 + 2 * (size_t)w * tw + (size_t)w * (nt / 32) * 5) * sizeof(float));
+}
+
+__host__ __device__ inline size_t cl_smem_bytes(int w, int nv, int nt)
+{
+    return align16(cl_floats_offset(w, nv, nt) + (size_t)w * 5 * sizeof(double) + (size_t)w * 5 * sizeof(float));
+}
+
+// Table parameters (u_x, u_y, u_z, 1/(2 theta), weight rho (2 pi theta)^{-3/2})
+// of the Maxwellian with moment sums s = (f, v f, |v|^2 f summed, no dv^3):
+// rho, u and theta in float64 (theta's numerator cancels at high Mach
+// numbers), 1/(2 theta) and the prefactor in float32 like the tables they
+// feed.  This chain runs on the FP64 pipe between two steps of the cluster
+// run, where each FP64 warp instruction costs tens of cycles.
+__device__ __forceinline__ void cl_params(const double* s, double dv3, double weight, float* pf, int* status)
+{
+    const double rho = s[0] * dv3, inv = 1.0 / s[0];
+    const double ux = s[1] * inv, uy = s[2] * inv, uz = s[3] * inv;
+    const double th = (s[4] * inv - (ux * ux + uy * uy + uz * uz)) * (1.0 / 3.0);
+    if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
+    const float thf = (float)th, tpf = 2.0f * (float)PI * thf;
+    pf[0] = (float)ux;
+    pf[1] = (float)uy;
+    pf[2] = (float)uz;
+    pf[3] = 0.5f / thf;
+    pf[4] = (float)(weight * rho) / (tpf * sqrtf(tpf));
+}
+
+// Factor tables of ncols cells from their float32 parameters pf[i*5 + 0..4],
+// into shared memory only.
+__device__ void cl_tables(const Inst& I, int ncols, const float* pf, float* tb)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, nv = I.nv, tw = 3 * nv;
+    const float Lf = (float)I.L, dvf = (float)I.dv;
+    for (int idx = tid; idx < ncols * tw; idx += nt) {
+        int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
+        const int jm = j < nv - 1 - j ? j : nv - 1 - j;
+        const float vlow = -Lf + ((float)jm + 0.5f) * dvf;
+        float vj = j == jm ? vlow : -vlow;
+        float dvu = vj - pf[i * 5 + d];
+        float val = expf(-(dvu * dvu) * pf[i * 5 + 3]);
+        if (d == 0) val *= pf[i * 5 + 4];
+        tb[idx] = val;
+    }
+}
+
+__device__ __forceinline__ void ld8(const float* p, float (&o)[CLV])
+{
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w, o[4] = b.x, o[5] = b.y, o[6] = b.z, o[7] = b.w;
+}
+
+template <int SCHEME, int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_fine_cluster(const Inst* __restrict__ insts, const Active* __restrict__ active, int nsteps, int w, int* status)
+{
+    constexpr int H = SCHEME == 1 ? 2 : 1, V = CLV, NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int b = active->begin + (int)blockIdx.x / C;  // one cluster per instance
+    if (b >= active->end) return;                       // the same for every CTA of the cluster
+    const Inst& I = insts[b];
+    const int nx = I.nx, nv = I.nv, nv3 = I.nv3, tw = 3 * nv, bc = I.bc;
+    const int c0 = rank * w, ncols = min(nx, c0 + w) - c0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    float* g = reinterpret_cast<float*>(smem);  // [2][w][nv3]
+    float* tab = g + 2 * (size_t)w * nv3;        // [2][w][tw]
+    float* red = tab + 2 * (size_t)w * tw;       // [w][NW][5] warp totals
+    double* mom = reinterpret_cast<double*>(smem + cl_floats_offset(w, nv, NT));  // [w][5]
+    float* pf = reinterpret_cast<float*>(mom + 5 * w);                              // [w][5]
+
+    // lift (Eq. 17) of the own cells into tables buffer 0: the conserved
+    // moments as sums (rho, m, 2E) / dv^3
+    for (int i = tid; i < ncols; i += NT) {
+        const int c = c0 + i;
+        const double id3 = 1.0 / I.dv3;
+        const double sm[5] = {I.Uin[c] * id3, I.Uin[nx + c] * id3, I.Uin[2 * nx + c] * id3, I.Uin[3 * nx + c] * id3,
+                              2.0 * I.Uin[4 * nx + c] * id3};
+        cl_params(sm, I.dv3, 1.0, pf + i * 5, status);
+    }
+    __syncthreads();
+    cl_tables(I, ncols, pf, tab);
+    if (nsteps <= 0) {  // the projection of the lifted state
+        __syncthreads();
+        project_columns<float, NT>(I, c0, ncols, mom, 0.0, tab, I.Uout);
+        cl.sync();
+        return;
+    }
+    cl.sync();  // every rank's lifted tables visible
+
+    const int v0 = tid * V;  // NT * V == nv3
+    const int jz = v0 % nv, jy = (v0 / nv) % nv, jx = v0 / (nv * nv);
+    const int jxf = nv - 1 - jx, v0f = (jxf * nv + jy) * nv + jz;
+    const double vxd = -I.L + (jx + 0.5) * I.dv, vyd = -I.L + (jy + 0.5) * I.dv;
+    const double vzd = -I.L + (jz + 0.5) * I.dv;
+    const bool pos = vxd > 0.0;
+    const float cour = (float)(I.nu * vxd);
+    const float vx = (float)vxd, vy = (float)vyd, vxy2 = (float)(vxd * vxd + vyd * vyd);
+    const float vz0 = (float)vzd, dvz = (float)I.dv, zz0 = (float)(vzd * vzd), zz1 = (float)(2.0 * vzd * I.dv),
+                zz2 = (float)(I.dv * I.dv);
+    const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
+    const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
+
+    for (int s = 1; s <= nsteps; ++s) {
+        const int p = (s - 1) & 1;
+        const float wg = s == 1 ? 0.f : (float)I.a;  // the lifted state has no g part
+        // f of extended cell e (x cell c0 - H + e) at this thread's velocities
+        auto recon = [&](int e, float (&o)[V]) {
+            bool fl;
+            const int cc = map_col(c0 - H + e, nx, bc, fl);
+            const int owner = cc / w, lc = cc - owner * w;
+            const float* gp = g + ((size_t)p * w + lc) * nv3;
+            const float* tp = tab + ((size_t)p * w + lc) * tw;
+            if (owner != rank) {
+                gp = cl.map_shared_rank(const_cast<float*>(gp), owner);
+                tp = cl.map_shared_rank(const_cast<float*>(tp), owner);
+            }
+            const float txy = tp[fl ? jxf : jx] * tp[nv + jy];
+            float tz[V];
+            ld8(tp + 2 * nv + jz, tz);
+            if (wg != 0.f) {
+                float gv[V];
+                ld8(gp + (fl ? v0f : v0), gv);
+#pragma unroll
+                for (int q = 0; q < V; ++q) o[q] = wg * gv[q] + txy * tz[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < V; ++q) o[q] = txy * tz[q];
+            }
+        };
+        float fc[V], fn[V], dm[V], dp[V], sp[V];
+        if (H == 2) {
+            float f0[V], f1[V];
+            recon(0, f0);
+            recon(1, f1);
+            recon(2, fc);
+            recon(3, fn);
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                float d0 = f1[q] - f0[q];
+                dm[q] = fc[q] - f1[q];
+                dp[q] = fn[q] - fc[q];
+                sp[q] = pos ? f1[q] + 0.5f * minmod2(d0, dm[q]) : fc[q] - 0.5f * minmod2(dm[q], dp[q]);
+            }
+        } else {
+            float f0[V];
+            recon(0, f0);
+            recon(1, fc);
+#pragma unroll
+            for (int q = 0; q < V; ++q) sp[q] = pos ? f0[q] : fc[q];
+        }
+        float* outp = g + (size_t)(p ^ 1) * w * nv3 + v0;
+        for (int i = 0; i < ncols; ++i, outp += nv3) {
+            float fs[V];
+            if (H == 2) {
+                float fnn[V];
+                recon(i + 4, fnn);
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    float dpp = fnn[q] - fn[q];
+                    float face = pos ? fc[q] + 0.5f * minmod2(dm[q], dp[q]) : fn[q] - 0.5f * minmod2(dp[q], dpp);
+                    fs[q] = fc[q] - cour * (face - sp[q]);
+                    sp[q] = face;
+                    fc[q] = fn[q];
+                    fn[q] = fnn[q];
+                    dm[q] = dp[q];
+                    dp[q] = dpp;
+                }
+            } else {
+                recon(i + 2, fn);
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    float face = pos ? fc[q] : fn[q];
+                    fs[q] = fc[q] - cour * (face - sp[q]);
+                    sp[q] = face;
+                    fc[q] = fn[q];
+                }
+            }
+            reinterpret_cast<float4*>(outp)[0] = make_float4(fs[0], fs[1], fs[2], fs[3]);
+            reinterpret_cast<float4*>(outp)[1] = make_float4(fs[4], fs[5], fs[6], fs[7]);
+            float s0 = fs[0], t1 = 0.f, t2 = 0.f;
+#pragma unroll
+            for (int q = 1; q < V; ++q) {
+                s0 += fs[q];
+                t1 += float(q) * fs[q];
+                t2 += float(q * q) * fs[q];
+            }
+            float r[5];
+            r[0] = s0;
+            r[1] = vx * s0;
+            r[2] = vy * s0;
+            r[3] = vz0 * s0 + dvz * t1;
+            r[4] = (vxy2 + zz0) * s0 + zz1 * t1 + zz2 * t2;
+            float tot = warp_sum5(r, lane);
+            if (writer) red[(i * NW + warp) * 5 + qsel] = tot;
+        }
+        __syncthreads();
+        // moment sums of the own cells: half a warp per (cell, moment), lane
+        // k adding warp k's total, in float64 (NW <= 16)
+        for (int vb = 2 * warp; vb < ncols * 5; vb += 2 * NW) {
+            const int vi = vb + (lane >> 4), k = lane & 15;
+            const bool on = vi < ncols * 5;
+            double x = on && k < NW ? (double)red[((vi / 5) * NW + k) * 5 + vi % 5] : 0.0;
+#pragma unroll
+            for (int o = 8; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (on && k == 0) mom[vi] = x;
+        }
+        __syncthreads();
+        for (int i = tid; i < ncols; i += NT) cl_params(mom + i * 5, I.dv3, I.b, pf + i * 5, status);
+        __syncthreads();
+        float* tnext = tab + (size_t)(p ^ 1) * w * tw;
+        cl_tables(I, ncols, pf, tnext);
+        if (s == nsteps) {  // projection (Eq. 18) of f = a g + M
+            __syncthreads();
+            project_columns<float, NT>(I, c0, ncols, mom, I.a, tnext, I.Uout);
+        }
+        cl.sync();  // the next state of every rank visible; no rank still reads this one
+    }
+}
+
+template <int SCHEME, int NT>
+void* fine_cluster_ptr()
+{
+    return reinterpret_cast<void*>(&k_fine_cluster<SCHEME, NT>);
+}
+
+void* fine_cluster_kernel(int scheme, int nv)
+{
+    if (nv == 8) return scheme == 1 ? fine_cluster_ptr<1, 64>() : fine_cluster_ptr<0, 64>();
+    if (nv == 16) return scheme == 1 ? fine_cluster_ptr<1, 512>() : fine_cluster_ptr<0, 512>();
+    return nullptr;
+}
+
 template <typename T, int SCHEME, int V>
 void* fine_kernel_ptr()
 {
@@ -844,6 +1102,13 @@ void prepare_fine_kernels(int max_smem)
         for (int sch = 0; sch < 2; ++sch) raise_smem(fine_kernel(c[0], sch, c[1]), max_smem);
     raise_smem(reinterpret_cast<const void*>(&k_lift<double>), max_smem);
     raise_smem(reinterpret_cast<const void*>(&k_lift<float>), max_smem);
+    for (int nv : {8, 16})
+        for (int sch = 0; sch < 2; ++sch) {
+            const void* fn = fine_cluster_kernel(sch, nv);
+            raise_smem(fn, max_smem);
+            cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaGetLastError();
+        }
 }
 
 int fine_run_occupancy(int precision, int scheme, int vpt, size_t smem, int* blocks_per_sm)
@@ -907,6 +1172,65 @@ cudaError_t launch_set_f(int precision, const Inst* insts, InstState* st, int b,
         k_state_moments<float><<<h.nx, THREADS, 0, s>>>(insts, st, b);
     }
     return cudaGetLastError();
+}
+
+// Cluster-resident fine run: the cells per CTA w (the fewest that keep the
+// cluster at <= 16 CTAs) and the shared memory of a CTA; false when nv has no
+// instantiation (8 or 16) or the cells do not fit.
+bool fine_cluster_plan(int nx, int nv, int max_smem, int* C, int* w, size_t* smem)
+{
+    const void* fn = fine_cluster_kernel(0, nv);
+    if (!fn || nx < 1) return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int ww = (nx + 15) / 16;
+    const size_t sm = cl_smem_bytes(ww, nv, nv * nv * nv / CLV);
+    if (sm + fa.sharedSizeBytes > (size_t)max_smem) return false;
+    *w = ww;
+    *C = (nx + ww - 1) / ww;
+    *smem = sm;
+    return true;
+}
+
+static cudaLaunchConfig_t cluster_config(int nv, int n_inst, int C, size_t smem, cudaStream_t s,
+                                         cudaLaunchAttribute* at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_inst * C, 1, 1);
+    cfg.blockDim = dim3(nv * nv * nv / CLV, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int fine_cluster_resident(int scheme, int nv, int C, size_t smem)
+{
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_config(nv, 1, C, smem, 0, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fine_cluster_kernel(scheme, nv), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+cudaError_t launch_fine_cluster(int scheme, int nv, const Inst* insts, const Active* active, int n_inst_max,
+                                int nsteps, int C, int w, size_t smem, int* status, cudaStream_t s)
+{
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_config(nv, n_inst_max, C, smem, s, at);
+    void* args[] = {(void*)&insts, (void*)&active, (void*)&nsteps, (void*)&w, (void*)&status};
+    return cudaLaunchKernelExC(&cfg, fine_cluster_kernel(scheme, nv), args);
 }
 
 }  // namespace prk

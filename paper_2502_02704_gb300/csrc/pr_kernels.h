@@ -65,6 +65,15 @@ cudaError_t launch_fine_run(int precision, int scheme, int vpt, const Inst* inst
 int fine_run_occupancy(int precision, int scheme, int vpt, size_t smem, int* blocks_per_sm);
 size_t fine_run_smem(int precision, int vpt, int tx, int nv, int H);
 
+// Cluster-resident fine run (float32 f, nv = 8 or 16): one thread-block
+// cluster of C CTAs per active instance, w x cells per CTA, keeps the
+// instance in shared memory for lift (from Uin), nsteps steps and the
+// projection into Uout (and Ucur).  The batch's g, tab and state are not used.
+bool fine_cluster_plan(int nx, int nv, int max_smem, int* C, int* w, size_t* smem);
+int fine_cluster_resident(int scheme, int nv, int C, size_t smem);  // co-resident clusters
+cudaError_t launch_fine_cluster(int scheme, int nv, const Inst* insts, const Active* active, int n_inst_max,
+                                int nsteps, int C, int w, size_t smem, int* status, cudaStream_t s);
+
 // Set the dynamic shared-memory limit of the kernels (called once).
 void prepare_fine_kernels(int max_smem);
 void prepare_coarse_kernels(int max_smem);

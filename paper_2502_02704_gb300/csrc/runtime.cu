@@ -923,6 +923,11 @@ struct pr_ctx {
     int k = 0;
     bool initialized = false;
     std::vector<int> live;  // slice whose live f each resident instance holds (0 = none)
+    int fpath_req = PR_FINE_AUTO;
+    bool use_cluster = false;  // fine phase on the cluster-resident kernel
+    int cl_C = 0, cl_w = 0;    // its CTAs per cluster and x cells per CTA
+    size_t cl_smem = 0;
+    int cl_resident = 0;       // clusters of that shape the device runs at once
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool descs_dirty = false;
@@ -979,6 +984,37 @@ static void bind_slice(pr_ctx* c, int b, int n)
     Inst& I = c->fine->h[b];
     I.Uin = uin;
     I.Uout = uout;
+}
+
+// The fine phase of an iteration runs on the cluster-resident kernel when
+// the slices are mixed precision with the Maxwellian lifting, their shape has
+// an instantiation and fits one cluster's shared memory, and the resident
+// slices' clusters run in at most two waves (clusters that finish free their
+// SMs for the next); else on the tiled persistent kernel, which a batch that
+// fills the GPU runs near the HBM roofline.
+static int choose_fine_path(pr_ctx* c)
+{
+    c->use_cluster = false;
+    if (c->ff) return PR_OK;
+    pr_batch* b = c->fine;
+    int C = 0, w = 0;
+    size_t sm = 0;
+    const bool fits = b->precision == PR_MIXED && b->lift_order == 0 &&
+                      prk::fine_cluster_plan(c->nx, c->v.nv, max_optin_smem(), &C, &w, &sm);
+    const int resident = fits ? prk::fine_cluster_resident(b->scheme, c->v.nv, C, sm) : 0;
+    if (c->fpath_req == PR_FINE_CLUSTER) {
+        if (!fits || resident < 1)
+            return cfail(c, PR_EINVAL, "the cluster-resident fine run needs mixed precision, the Maxwellian lifting, "
+                                       "nv = 8 or 16 and a slice that fits a cluster's shared memory");
+        c->use_cluster = true;
+    } else if (c->fpath_req == PR_FINE_AUTO) {
+        c->use_cluster = fits && resident > 0 && c->n_res <= 2 * resident;
+    }
+    c->cl_C = fits ? C : 0;
+    c->cl_w = fits ? w : 0;
+    c->cl_smem = sm;
+    c->cl_resident = resident;
+    return PR_OK;
 }
 
 static int take_ctx_status(pr_ctx* c)
@@ -1099,6 +1135,7 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
         free_ctx(c);
         return init_fail(PR_ECUDA, "descriptor upload");
     }
+    choose_fine_path(c);
     *out = c;
     return PR_OK;
 }
@@ -1280,6 +1317,16 @@ static int enqueue_iteration_plain(pr_ctx* c, int k)
         int cnt = std::min(c->n_res, c->N - w0 + 1);
         for (int bi = 0; bi < cnt; ++bi) bind_slice(c, bi, w0 + bi);
         CCUDA(c, cudaMemcpyAsync(b->d_inst, b->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice, s));
+        if (c->use_cluster) {  // lift, n_f steps and projection of the wave's slices in one launch
+            prk::Active a{0, cnt};
+            CCUDA(c, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
+            CCUDA(c, prk::launch_fine_cluster(b->scheme, c->v.nv, b->d_inst, b->d_active, cnt, c->nf, c->cl_C,
+                                              c->cl_w, c->cl_smem, b->d_status, s));
+            g_launches += 1;
+            prk::Active all{0, b->n};
+            CCUDA(c, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+            continue;
+        }
         int rc = lift_instances(b, 0, cnt, s);
         if (rc) return cfail(c, rc, "%s", b->err.c_str());
         prk::Active a{0, cnt};
@@ -1339,6 +1386,11 @@ static int build_graph(pr_ctx* c)
     c->descs_dirty = false;
     CCUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = prk::launch_set_active(c->dk, b->d_active, 1, c->n_res, c->N, s);
+    if (c->use_cluster) {
+        if (e == cudaSuccess)
+            e = prk::launch_fine_cluster(b->scheme, c->v.nv, b->d_inst, b->d_active, c->n_res, c->nf, c->cl_C,
+                                         c->cl_w, c->cl_smem, b->d_status, s);
+    } else {
     if (e == cudaSuccess)
         e = b->lift_order == 1
                 ? prk::launch_lift_ce(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, b->d_active, b->nx_max,
@@ -1350,6 +1402,7 @@ static int build_graph(pr_ctx* c)
         e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state, b->d_prefix,
                                  b->d_active, c->nf, reinterpret_cast<unsigned long long*>(b->d_sync), b->d_status,
                                  c->nf > 1 ? prk::WAIT_LIMIT_NS : 0, b->grid, b->smem, s);
+    }
     if (e == cudaSuccess)
         e = prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
                               c->dk, s);
@@ -1393,7 +1446,7 @@ static int run_iterations(pr_ctx* c, int count, bool use_graph)
                 if (rc) return rc;
             }
             CCUDA(c, cudaGraphLaunch(c->gexec, cs));
-            g_launches += c->ff ? 1 + prf::graph_body_launches(c->ff, c->nf) : 5;
+            g_launches += c->ff ? 1 + prf::graph_body_launches(c->ff, c->nf) : c->use_cluster ? 3 : 5;
         } else {
             int rc = enqueue_iteration_plain(c, k);
             if (rc) return rc;
@@ -1419,6 +1472,41 @@ int pr_parareal_iter(pr_ctx* c, double* err_out)
         *err_out = c->h_pinned[0];
         return rc;
     }
+    return PR_OK;
+}
+
+int pr_set_fine_path(pr_ctx* c, int mode)
+{
+    if (!c) return PR_EINVAL;
+    if (mode < PR_FINE_AUTO || mode > PR_FINE_CLUSTER) return cfail(c, PR_EINVAL, "unknown fine path %d", mode);
+    if (c->ff && mode == PR_FINE_CLUSTER)
+        return cfail(c, PR_EINVAL, "the cluster-resident fine run has no exterior force");
+    CCUDA(c, cudaStreamSynchronize(ctx_stream(c)));
+    const int old = c->fpath_req;
+    c->fpath_req = mode;
+    int rc = choose_fine_path(c);
+    if (rc) {
+        c->fpath_req = old;
+        choose_fine_path(c);
+        return rc;
+    }
+    c->descs_dirty = true;  // the captured iteration holds the old launches
+    return PR_OK;
+}
+
+int pr_get_fine_path(const pr_ctx* c, int* path)
+{
+    if (!c || !path) return PR_EINVAL;
+    *path = c->use_cluster ? PR_FINE_CLUSTER : PR_FINE_TILED;
+    return PR_OK;
+}
+
+int pr_fine_cluster_shape(const pr_ctx* c, int* cluster, int* cells_per_cta, int* resident)
+{
+    if (!c) return PR_EINVAL;
+    if (cluster) *cluster = c->cl_C;
+    if (cells_per_cta) *cells_per_cta = c->cl_w;
+    if (resident) *resident = c->cl_resident;
     return PR_OK;
 }
 
