@@ -162,8 +162,9 @@ __device__ __forceinline__ const double* beyond_block(cg::cluster_group& cl, con
 }
 
 // G over dT applied to this CTA's cells [c0, c1) of the state at region
-// offset 0 (A), with the other CTAs of the cluster doing theirs; the result
-// ends in A.  Per local step:
+// offset 0 (A), with the other CTAs of the cluster doing theirs; returns the
+// region offset of the result (A, or B after an odd number of local steps).
+// Per local step:
 //   1. one thread per own cell: primitives, flux h, speed (and the
 //      Navier-Stokes primitives) into the cache, the CTA's CFL maxima;
 //   2. one cluster barrier; the cluster maxima (one rank per lane), dt;
@@ -176,9 +177,9 @@ __device__ __forceinline__ const double* beyond_block(cg::cluster_group& cl, con
 // instructions of any one warp few: this part's FP64 pipe takes tens of
 // cycles per warp instruction, and the local step is a chain of them.  A
 // cluster barrier after the last local step ends every peer read before the
-// caller reuses A.  Every CTA takes the same local steps.
+// caller reuses the region.  Every CTA takes the same local steps.
 template <bool VISC>
-__device__ void coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peers& P, int C, int c0, int c1,
+__device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peers& P, int C, int c0, int c1,
                          double dT, int* status, unsigned long long* sh)
 {
     const int nx = p.nx, m = P.m, mc = c1 - c0, nf = mc + 1;
@@ -344,12 +345,7 @@ __device__ void coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Pee
         t += dt;
     }
     cl.sync();  // every rank's reads of this region are over
-    if (cur_off != 0) {
-        for (int li = threadIdx.x; li < mc; li += blockDim.x)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) R[q * m + li] = R[cur_off + q * m + li];
-        __syncthreads();
-    }
+    return cur_off;
 }
 
 __device__ __forceinline__ Peers make_peers(double* dsm, double* work, int use_smem, int m)
@@ -379,10 +375,10 @@ k_coarse(CoarseParams p, const double* Vin, double* Vout, double dT, double* wor
 #pragma unroll
         for (int q = 0; q < 5; ++q) P.base[q * m + li] = Vin[q * nx + c0 + li];
     __syncthreads();
-    coarse_G<VISC>(p, cl, P, C, c0, c1, dT, status, sh);
+    const int off = coarse_G<VISC>(p, cl, P, C, c0, c1, dT, status, sh);
     for (int li = threadIdx.x; li < c1 - c0; li += blockDim.x)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Vout[q * nx + c0 + li] = P.base[q * m + li];
+        for (int q = 0; q < 5; ++q) Vout[q * nx + c0 + li] = P.base[off + q * m + li];
     cl.sync();  // no CTA leaves while another may still read its region
 }
 
@@ -402,22 +398,40 @@ k_sweep(CoarseParams p, int N, double dT, const int* dk, double* U, const double
     const Peers P = make_peers(dsm, work, use_smem, m);
     double* A = P.base;
     double emax = 0.0;
-    for (int n = (k > 1 ? k : 1); n <= N; ++n) {
+    const int n0 = k > 1 ? k : 1;
+    // one cell per thread: the slice's jump and old iterate are prefetched
+    // into registers while G runs (they do not depend on it)
+    const bool pre = mc <= (int)blockDim.x;
+    if (n0 <= N) {
         for (int li = threadIdx.x; li < mc; li += blockDim.x)
 #pragma unroll
-            for (int q = 0; q < 5; ++q) A[q * m + li] = U[(size_t)(n - 1) * sz + q * nx + c0 + li];
+            for (int q = 0; q < 5; ++q) A[q * m + li] = U[(size_t)(n0 - 1) * sz + q * nx + c0 + li];
         __syncthreads();
-        coarse_G<VISC>(p, cl, P, C, c0, c1, dT, status, sh);
+    }
+    for (int n = n0; n <= N; ++n) {
+        double jp[5], uo[5];
+        if (pre && (int)threadIdx.x < mc) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const size_t o = (size_t)n * sz + q * nx + c0 + threadIdx.x;
+                jp[q] = k > 0 ? PFL[o] - Gs[o] : 0.0;
+                uo[q] = U[o];
+            }
+        }
+        const int off = coarse_G<VISC>(p, cl, P, C, c0, c1, dT, status, sh);
+        // correction; the new iterate also stays in A as the next slice's start
         for (int li = threadIdx.x; li < mc; li += blockDim.x)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 const size_t o = (size_t)n * sz + q * nx + c0 + li;
-                double gv = A[q * m + li];
-                double nv = k > 0 ? gv + (PFL[o] - Gs[o]) : gv;
-                double d = fabs(nv - U[o]);
+                const double gv = P.base[off + q * m + li];
+                const double jump = pre ? jp[q] : (k > 0 ? PFL[o] - Gs[o] : 0.0);
+                const double nv = k > 0 ? gv + jump : gv;
+                const double d = fabs(nv - (pre ? uo[q] : U[o]));
                 if (d > emax) emax = d;
                 U[o] = nv;
                 Gs[o] = gv;
+                A[q * m + li] = nv;
             }
         __syncthreads();
     }
