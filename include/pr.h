@@ -170,7 +170,8 @@ int pr_fine_moments(pr_ctx* ctx, int slice, int kind, double* out);
 int pr_fine_get_f(pr_ctx* ctx, int slice, double* out);
 
 /* One iteration of Algorithm 2 (k <- k+1): lift U^{n-1,k-1}, run n_f fine steps
- * and project for every slice n = k..N in one batched persistent launch, form
+ * and project for every slice n = k..N in one launch (the tiled persistent
+ * kernel, or one cluster per slice: pr_set_fine_path), form
  * the jumps P F L(U^{n-1,k-1}) - G(U^{n-1,k-1}), then the sequential correction
  * U^{n,k} = G(U^{n-1,k}) + jump for n = k..N on the device.  *err_out (may be
  * NULL) receives max_n |U^{n,k} - U^{n,k-1}| over cells and the 5 conserved
