@@ -972,6 +972,12 @@ static void free_ctx(pr_ctx* c)
 
 static cudaStream_t ctx_stream(const pr_ctx* c) { return c->ff ? c->ff->stream : c->fine->stream; }
 
+// Pinned host memory of a problem: the iteration errors [N + 2], a staging
+// copy of the conserved initial state [5][nx], then two status words.
+static size_t pinned_doubles(const pr_ctx* c) { return (size_t)(c->N + 2) + 5 * (size_t)c->nx + 1; }
+static double* pinned_state(pr_ctx* c) { return c->h_pinned + (c->N + 2); }
+static int* pinned_status(pr_ctx* c) { return reinterpret_cast<int*>(c->h_pinned + (c->N + 2) + 5 * (size_t)c->nx); }
+
 // Point resident instance b at slice n (lift source U^{n-1}, projection PFL^n).
 static void bind_slice(pr_ctx* c, int b, int n)
 {
@@ -1019,6 +1025,14 @@ static int choose_fine_path(pr_ctx* c)
 
 static int take_ctx_status(pr_ctx* c)
 {
+    if (!c->ff) {  // both status words in one round trip; the slow path below on an error
+        int* hs = pinned_status(c);
+        cudaStream_t s = ctx_stream(c);
+        CCUDA(c, cudaMemcpyAsync(hs, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CCUDA(c, cudaMemcpyAsync(hs + 1, c->fine->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CCUDA(c, cudaStreamSynchronize(s));
+        if (hs[0] == 0 && hs[1] == 0) return PR_OK;
+    }
     CCUDA(c, cudaStreamSynchronize(ctx_stream(c)));
     int st = 0;
     CCUDA(c, cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1105,7 +1119,7 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
         cudaMalloc(&c->dGs, lvl) != cudaSuccess || cudaMalloc(&c->derr, sizeof(double) * (c->N + 2)) != cudaSuccess ||
         cudaMalloc(&c->dwork, sizeof(double) * prk::coarse_work_doubles(c->nx)) != cudaSuccess ||
         cudaMalloc(&c->dtmp, sizeof(double) * 10 * c->nx) != cudaSuccess || cudaMalloc(&c->dk, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->dstatus, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_pinned, sizeof(double) * (c->N + 2)) != cudaSuccess) {
+        cudaMalloc(&c->dstatus, sizeof(int)) != cudaSuccess || cudaMallocHost(&c->h_pinned, sizeof(double) * pinned_doubles(c)) != cudaSuccess) {
         free_ctx(c);
         return init_fail(PR_ENOMEM, "parareal iterate buffers");
     }
@@ -1186,12 +1200,13 @@ int pr_set_initial(pr_ctx* c, const double* U0)
     if (!c) return PR_EINVAL;
     if (!U0) return cfail(c, PR_EINVAL, "null initial state");
     if (check_prim(U0, c->nx)) return cfail(c, PR_ENONPHYS, "initial state has rho <= 0 or theta <= 0");
-    std::vector<double> V(5 * c->nx);
-    prim_to_cons_host(c->nx, U0, V.data());
+    // stream-ordered after any enqueued iteration; the staging copy is free
+    // (every call that fills it ends synchronised)
+    double* hV = pinned_state(c);
+    prim_to_cons_host(c->nx, U0, hV);
     cudaStream_t s = ctx_stream(c);
-    CCUDA(c, cudaStreamSynchronize(s));
-    CCUDA(c, cudaMemcpy(c->dU, V.data(), sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice));
-    CCUDA(c, cudaMemset(c->dk, 0, sizeof(int)));
+    CCUDA(c, cudaMemcpyAsync(c->dU, hV, sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice, s));
+    CCUDA(c, cudaMemsetAsync(c->dk, 0, sizeof(int), s));
     CCUDA(c, prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
                                c->dk, s));
     g_launches += 1;
