@@ -830,22 +830,22 @@ __host__ __device__ inline size_t cl_smem_bytes(int w, int nv, int nt)
 
 // Table parameters (u_x, u_y, u_z, 1/(2 theta), weight rho (2 pi theta)^{-3/2})
 // of the Maxwellian with moment sums s = (f, v f, |v|^2 f summed, no dv^3):
-// rho, u and theta in float64 (theta's numerator cancels at high Mach
-// numbers), 1/(2 theta) and the prefactor in float32 like the tables they
-// feed.  This chain runs on the FP64 pipe between two steps of the cluster
-// run, where each FP64 warp instruction costs tens of cycles.
+// theta's numerator s_4 s_0 - |s_1..3|^2 = 3 theta s_0^2 in float64 (it
+// cancels at high Mach numbers), the rest in float32 like the tables it
+// feeds.  This chain sits between two steps of the cluster run, where each
+// FP64 warp instruction costs tens of cycles.
 __device__ __forceinline__ void cl_params(const double* s, double dv3, double weight, float* pf, int* status)
 {
-    const double rho = s[0] * dv3, inv = 1.0 / s[0];
-    const double ux = s[1] * inv, uy = s[2] * inv, uz = s[3] * inv;
-    const double th = (s[4] * inv - (ux * ux + uy * uy + uz * uz)) * (1.0 / 3.0);
-    if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
-    const float thf = (float)th, tpf = 2.0f * (float)PI * thf;
-    pf[0] = (float)ux;
-    pf[1] = (float)uy;
-    pf[2] = (float)uz;
+    const double num = s[4] * s[0] - (s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
+    const float s0 = (float)s[0], numf = (float)num;
+    if (!(s0 > 0.f) || !(numf > 0.f)) atomicCAS(status, 0, ST_NONPHYS);
+    const float is0 = 1.0f / s0;
+    const float thf = numf * (is0 * is0) * (1.0f / 3.0f), tpf = 2.0f * (float)PI * thf;
+    pf[0] = (float)s[1] * is0;
+    pf[1] = (float)s[2] * is0;
+    pf[2] = (float)s[3] * is0;
     pf[3] = 0.5f / thf;
-    pf[4] = (float)(weight * rho) / (tpf * sqrtf(tpf));
+    pf[4] = (float)weight * (s0 * (float)dv3) / (tpf * sqrtf(tpf));
 }
 
 // Factor tables of ncols cells from their float32 parameters pf[i*5 + 0..4],
