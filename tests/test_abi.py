@@ -33,3 +33,15 @@ def test_binding_covers_the_abi():
     assert declared == set(pr.EXPORTED)
     for name in declared:
         assert callable(getattr(pr, name)), name
+
+
+def test_null_problem_is_rejected_without_a_device():
+    # entry points validate their handle before any CUDA call
+    import ctypes as C
+    L = pr.lib()
+    v = C.c_int()
+    assert L.pr_set_fine_path(None, pr.PR_FINE_CLUSTER) == pr.PR_EINVAL
+    assert L.pr_get_fine_path(None, C.byref(v)) == pr.PR_EINVAL
+    assert L.pr_fine_cluster_shape(None, C.byref(v), C.byref(v), C.byref(v)) == pr.PR_EINVAL
+    assert L.pr_set_force_step(None, 0, -1, -1) == pr.PR_EINVAL
+    assert L.pr_parareal_iter(None, None) == pr.PR_EINVAL
