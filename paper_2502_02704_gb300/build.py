@@ -1,9 +1,7 @@
 """Build libpr.so (the CUDA library behind include/pr.h) in-tree for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel and linked into
-``paper_2502_02704_gb300/libpr.so``.  The coarse propagator is compiled with
-``-fmad=false`` so its Rusanov arithmetic is the plain IEEE sequence of its
-formulas (no fused multiply-add contraction).
+``paper_2502_02704_gb300/libpr.so``.
 """
 from __future__ import annotations
 
@@ -20,7 +18,7 @@ LIB = os.path.join(HERE, "libpr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
     "fine.cu": [],
-    "coarse.cu": ["-fmad=false"],
+    "coarse.cu": [],
     "runtime.cu": [],
     "noalloc.cu": [],
     "adjoint.cu": [],
