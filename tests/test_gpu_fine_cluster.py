@@ -139,3 +139,16 @@ def test_fine_path_selection_rules():
         pr.pr_set_fine_path(ctx, pr.PR_FINE_TILED)
     finally:
         pr.pr_destroy(ctx)
+
+
+def test_cluster_run_is_the_same_from_the_graph_and_in_waves():
+    # each slice's cluster computes the same bits whether all slices run from
+    # the captured iteration or in waves without a graph
+    nx, nv, N, K, T = 48, 8, 7, 3, 0.06
+    _, Ug, eg = _run(nx, nv, pr.PR_BC_PERIODIC, pr.PR_MUSCL, N, K, T, pr.PR_FINE_CLUSTER,
+                     U0=W.smooth_periodic(nx))
+    _, Uw, ew = _run(nx, nv, pr.PR_BC_PERIODIC, pr.PR_MUSCL, N, K, T, pr.PR_FINE_CLUSTER, max_batch=3,
+                     U0=W.smooth_periodic(nx))
+    for n in range(N + 1):
+        assert np.array_equal(Ug[n], Uw[n]), n
+    assert np.array_equal(eg, ew)

@@ -217,3 +217,22 @@ def test_errors_are_reported_not_raised_on_device():
     with pytest.raises(pr.PrError) as ei:
         pr.pr_batch_create([pr.instance(10, 6, 1e-3)])
     assert ei.value.code == pr.PR_EINVAL
+
+
+def test_parareal_on_a_grid_larger_than_the_sweep_threads():
+    # 5000 cells: 16 sweep CTAs of 313 cells, more cells than threads, so the
+    # sweep's correction loads its inputs after G instead of prefetching them,
+    # and the face and update passes loop over their items
+    nx, nv, T, N, K = 5000, 4, 0.002, 2, 2
+    U0 = W.sod(nx)
+    p = _oracle_pr(nx=nx, nv=nv, T=T, N=N)
+    Uo, errs_o, _ = O.parareal(p, U0, K=K)
+    ctx = _ctx(nx=nx, nv=nv, T=T, N=N)
+    try:
+        pr.pr_set_initial(ctx, U0)
+        kd, errs = pr.pr_parareal_run(ctx, K)
+        for n in range(N + 1):
+            assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < TOL_FP64, n
+        assert np.allclose(errs, errs_o, rtol=1e-6, atol=0)
+    finally:
+        pr.pr_destroy(ctx)
