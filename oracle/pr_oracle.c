@@ -152,37 +152,38 @@ int or_lift(const or_kin* k, const double* U, double* f)
     return bad ? OR_ENONPHYS : OR_OK;
 }
 
-/* Moments of one x column by the first-order quadrature of Eq. (18), summed in
- * lexicographic (jx, jy, jz) order: rho = sum f dv^3, rho u = sum v f dv^3,
+/* Moments of one x column by the first-order quadrature of Eq. (18), the
+ * terms taken in lexicographic (jx, jy, jz) order and summed with
+ * compensation (or_cadd): rho = sum f dv^3, rho u = sum v f dv^3,
  * 3 rho theta = sum |v - u|^2 f dv^3 (two passes: u first, then theta). */
 static void column_moments(int nv, const double* v, double dv3, const double* fc,
                            double* rho, double* u, double* th)
 {
-    double s0 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    or_csum s0 = {0, 0}, sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
     for (int jx = 0; jx < nv; ++jx)
         for (int jy = 0; jy < nv; ++jy)
             for (int jz = 0; jz < nv; ++jz) {
                 double fv = fc[((long)jx * nv + jy) * nv + jz];
-                s0 += fv * dv3;
-                sx += v[jx] * fv * dv3;
-                sy += v[jy] * fv * dv3;
-                sz += v[jz] * fv * dv3;
+                or_cadd(&s0, fv * dv3);
+                or_cadd(&sx, v[jx] * fv * dv3);
+                or_cadd(&sy, v[jy] * fv * dv3);
+                or_cadd(&sz, v[jz] * fv * dv3);
             }
-    double r = s0;
-    double ux = sx / r, uy = sy / r, uz = sz / r;
-    double s2 = 0.0;
+    double r = or_cval(&s0);
+    double ux = or_cval(&sx) / r, uy = or_cval(&sy) / r, uz = or_cval(&sz) / r;
+    or_csum s2 = {0, 0};
     for (int jx = 0; jx < nv; ++jx)
         for (int jy = 0; jy < nv; ++jy)
             for (int jz = 0; jz < nv; ++jz) {
                 double fv = fc[((long)jx * nv + jy) * nv + jz];
                 double cx = v[jx] - ux, cy = v[jy] - uy, cz = v[jz] - uz;
-                s2 += (cx * cx + cy * cy + cz * cz) * fv * dv3;
+                or_cadd(&s2, (cx * cx + cy * cy + cz * cz) * fv * dv3);
             }
     *rho = r;
     u[0] = ux;
     u[1] = uy;
     u[2] = uz;
-    *th = s2 / (3.0 * r);
+    *th = or_cval(&s2) / (3.0 * r);
 }
 
 /* Discrete projection P, Def. 1 / Eq. (18), primitive output [5][nx]. */

@@ -18,6 +18,26 @@
 extern "C" {
 #endif
 
+/* Compensated summation (Neumaier 1974, the improved Kahan-Babuska sum) for the
+ * velocity sums of Eq. (18).  The moments are defined as exact sums over the
+ * nv^3 cells; a plain running sum of that many terms drifts by ~sqrt(n) ulps
+ * (about 1e-14 relative at 24^3), while s + c below is the exact sum of the
+ * terms to within a couple of ulps in any order.  Each addition's rounding
+ * error is recovered exactly (Knuth's two-sum, ordered by magnitude). */
+typedef struct {
+    double s, c;
+} or_csum;
+
+static inline void or_cadd(or_csum* a, double x)
+{
+    double t = a->s + x;
+    if ((a->s < 0 ? -a->s : a->s) >= (x < 0 ? -x : x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static inline double or_cval(const or_csum* a) { return a->s + a->c; }
+
 #define OR_OK 0
 #define OR_EINVAL -1
 #define OR_ENOMEM -2

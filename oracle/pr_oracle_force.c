@@ -136,36 +136,37 @@ int or_v_lift_ce(const or_vkin* k, const double* U, double* f)
     return bad ? OR_ENONPHYS : OR_OK;
 }
 
-/* Moments of one column by the quadrature of Eq. (18) (u first, then theta). */
+/* Moments of one column by the quadrature of Eq. (18) (u first, then theta),
+ * summed with compensation (or_cadd) as the E = 0 oracle does. */
 static void vcolumn_moments(const or_vkin* k, const double* vx, const double* vp, double dv3, const double* fc,
                             double* rho, double* u, double* th)
 {
     int nvx = k->nvx, nvp = k->nvp;
-    double s0 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    or_csum s0 = {0, 0}, sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
     for (int jx = 0; jx < nvx; ++jx)
         for (int jy = 0; jy < nvp; ++jy)
             for (int jz = 0; jz < nvp; ++jz) {
                 double fv = fc[((long)jx * nvp + jy) * nvp + jz];
-                s0 += fv * dv3;
-                sx += vx[jx] * fv * dv3;
-                sy += vp[jy] * fv * dv3;
-                sz += vp[jz] * fv * dv3;
+                or_cadd(&s0, fv * dv3);
+                or_cadd(&sx, vx[jx] * fv * dv3);
+                or_cadd(&sy, vp[jy] * fv * dv3);
+                or_cadd(&sz, vp[jz] * fv * dv3);
             }
-    double r = s0;
-    double ux = sx / r, uy = sy / r, uz = sz / r;
-    double s2 = 0.0;
+    double r = or_cval(&s0);
+    double ux = or_cval(&sx) / r, uy = or_cval(&sy) / r, uz = or_cval(&sz) / r;
+    or_csum s2 = {0, 0};
     for (int jx = 0; jx < nvx; ++jx)
         for (int jy = 0; jy < nvp; ++jy)
             for (int jz = 0; jz < nvp; ++jz) {
                 double fv = fc[((long)jx * nvp + jy) * nvp + jz];
                 double cx = vx[jx] - ux, cy = vp[jy] - uy, cz = vp[jz] - uz;
-                s2 += (cx * cx + cy * cy + cz * cz) * fv * dv3;
+                or_cadd(&s2, (cx * cx + cy * cy + cz * cz) * fv * dv3);
             }
     *rho = r;
     u[0] = ux;
     u[1] = uy;
     u[2] = uz;
-    *th = s2 / (3.0 * r);
+    *th = or_cval(&s2) / (3.0 * r);
 }
 
 int or_v_project(const or_vkin* k, const double* f, double* U)

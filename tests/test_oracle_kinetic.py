@@ -71,6 +71,29 @@ def test_lift_project_roundtrip_resolved_grid():
     assert np.allclose(Up, U, rtol=0, atol=1e-12)
 
 
+def test_projection_sums_are_exact_to_rounding():
+    # Eq. (18) defines the moments as exact sums over the nv^3 velocity cells.
+    # math.fsum gives the correctly rounded sum of the same terms, so the
+    # oracle's projection (which is then converted to conserved variables)
+    # must agree with the exact sums to a few ulps, at a grid with as many
+    # cells as the batched parareal workload (24^3) and at 32^3.
+    for nv, nx in ((24, 3), (32, 2)):
+        k = O.Kin(nx=nx, nv=nv, L=8.0)
+        rng = np.random.default_rng(nv)
+        f = rng.uniform(0.1, 1.0, (nx, nv ** 3)) * O.lift(k, np.tile([[1.0], [0.3], [0.0], [-0.2], [0.9]], (1, nx)))
+        V = O.project(k, f, conserved=True)
+        v = O.velocity_nodes(nv, 8.0)
+        dv3 = (16.0 / nv) ** 3
+        vx, vy, vz = (g.ravel() for g in np.meshgrid(v, v, v, indexing="ij"))
+        for i in range(nx):
+            fc = f[i]
+            ex = [math.fsum(fc * dv3), math.fsum(vx * fc * dv3), math.fsum(vy * fc * dv3),
+                  math.fsum(vz * fc * dv3), 0.5 * math.fsum((vx * vx + vy * vy + vz * vz) * fc * dv3)]
+            scale = [ex[0], ex[0], ex[0], ex[0], ex[4]]
+            for q in range(5):
+                assert abs(V[q, i] - ex[q]) <= 4e-16 * scale[q], (nv, i, q, V[q, i], ex[q])
+
+
 def _beams(k, rng):
     """x-uniform, far-from-equilibrium f0: two drifting Maxwellians (as in Test 3)."""
     nx = k.nx
