@@ -289,6 +289,13 @@ int pr_batch_kernel_time(pr_batch* b, double* avg_ms, int* launches, int reset);
 int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int checkpoint, const double* lamV, double* dU0,
                      double* dlogeps);
 
+/* Stable fine step of the E = 0 propagator for the grid of *inst (Sec. 2.2):
+ * dt_stab = cfl dx / max|v_x|, dx = (x1 - x0)/nx, max|v_x| = L - dv/2 (the
+ * outermost velocity node).  inst->eps, inst->dt and inst->scheme are not
+ * read.  Errors: PR_EINVAL (null pointers, nx < 1, x1 <= x0, L <= 0, nv < 1,
+ * cfl not finite and > 0). */
+int pr_fine_dt_stab(const pr_instance* inst, double cfl, double* dt);
+
 /* Number of kernels the library launched since the last reset (any object). */
 long long pr_kernel_launches(int reset);
 
@@ -307,14 +314,18 @@ long long pr_kernel_launches(int reset);
  * tables, moment partials, counters, status) lives in one static device array
  * of 4 MiB that every GPU which loads libpr holds until the process exits;
  * instances needing more (about nx * (6 nv + 5 ceil(nv^3/1024)) * 8 bytes plus
- * a few KiB) are rejected with PR_EINVAL.  The first call on a device looks up
- * that array's device address (with the device current), so make the first
- * call before any stream capture.  Each call clears what must start at zero;
- * calls share the array, so calls that overlap on the GPU (other streams,
- * other host threads) race and must be serialised by the caller.  Enqueued on
- * stream (NULL: the legacy default stream), then synchronises it and returns
- * the device status (PR_ENONPHYS for a non-physical state, PR_ECUDA on a
- * runtime error). */
+ * a few KiB), or more shared memory per CTA than the device allows, are
+ * rejected with PR_EINVAL and a message.  The first call on each device does a
+ * one-time set-up there: with that device current it looks up the array's
+ * device address and sets the fine kernel's shared-memory limit; make that
+ * first call before any stream capture.  Every call copies its small
+ * descriptors from host memory into the array, clears what must start at
+ * zero, and ends by reading the device status back and synchronising the
+ * stream.  Calls share the array, so calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Enqueued on stream (NULL: the legacy default stream); returns the device
+ * status (PR_ENONPHYS for a non-physical state, PR_ECUDA on a runtime error;
+ * the message is in pr_batch_last_error(NULL)). */
 int pr_fine_step_noalloc(const pr_instance* inst, const double* f_in, double* f_out, void* stream);
 
 /* ============ exterior force E != 0 (Eqs. 5, 11-13; Test 3) ============ */

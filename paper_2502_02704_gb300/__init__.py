@@ -109,6 +109,7 @@ _SIGS = {
     "pr_kernel_launches": (C.c_longlong, [C.c_int]),
     "pr_batch_adjoint": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
     "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
+    "pr_fine_dt_stab": (C.c_int, [C.POINTER(pr_instance), C.c_double, _D]),
     "pr_force_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_force_instance), C.c_int, C.c_int, C.c_int]),
     "pr_force_destroy": (C.c_int, [_VP]),
     "pr_force_last_error": (C.c_char_p, [_VP]),
@@ -421,10 +422,17 @@ def pr_fine_step_noalloc(inst, f_in_dev, f_out_dev, stream=None):
         raise PrError(rc, (lib().pr_batch_last_error(None) or b"").decode() or "pr_fine_step_noalloc failed")
 
 
+def pr_fine_dt_stab(inst, cfl=0.5) -> float:
+    out = C.c_double()
+    rc = lib().pr_fine_dt_stab(C.byref(inst), float(cfl), C.byref(out))
+    if rc != PR_OK:
+        raise PrError(rc, "pr_fine_dt_stab: invalid grid or cfl")
+    return out.value
+
+
 def fine_dt(nx, nv, L, cfl=0.5, x0=0.0, x1=1.0) -> float:
-    """dt_stab = cfl dx / max|v_x| of the x transport (Sec. 2.2)."""
-    dv = 2.0 * L / nv
-    return cfl * ((x1 - x0) / nx) / (L - 0.5 * dv)
+    """dt_stab = cfl dx / max|v_x| of the x transport (Sec. 2.2), from the library."""
+    return pr_fine_dt_stab(instance(nx, nv, 1.0, L=L, x0=x0, x1=x1), cfl)
 
 
 # ---------------------------------------------------------------- exterior force

@@ -120,8 +120,14 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long mask)
     return __longlong_as_double(__double_as_longlong(x) ^ (long long)mask);
 }
 
-// x > 0 (and not NaN) from the bit pattern of x, on the integer pipe.
-__device__ __forceinline__ bool positive(long long b) { return b > 0 && b <= 0x7ff0000000000000ll; }
+// x > 0 and finite (not NaN, not +inf) from the bit pattern of x, on the
+// integer pipe.
+__device__ __forceinline__ bool positive(long long b) { return b > 0 && b < 0x7ff0000000000000ll; }
+
+// A guard on the local steps of one G: no physical run needs this many, and
+// a run that reaches it (a degenerate state the checks above let through)
+// stops with PR_ENONPHYS instead of spinning.
+constexpr int MAX_LOCAL_STEPS = 1 << 24;
 
 // The CFL maxima are taken over speeds and temperatures, non-negative in
 // every physical state, where the order of the IEEE bit patterns as unsigned
@@ -200,6 +206,7 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
     int cur_off = 0, nxt_off = 5 * m, buf = 0;
     const double idx = 1.0 / p.dx;
     double t = 0.0;
+    int nloc = 0;
     while (t < dT) {
         const double* cur = R + cur_off;
         const int ko = (10 + buf * NCACHE) * m;  // this substep's cache
@@ -231,7 +238,12 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
                 K[10 * m + li] = pr.p;
             }
         }
-        if (bad) atomicCAS(status, 0, ST_NONPHYS);
+        if (bad) {
+            atomicCAS(status, 0, ST_NONPHYS);
+            // a NaN pattern orders above every speed: the cluster maximum
+            // becomes NaN on every rank and all of them stop together
+            smax = 0x7ff8000000000000ull;
+        }
         smax = warp_max_u64(smax);
         thmax = warp_max_u64(thmax);
         double* red = R + red_off + 2 * buf;
@@ -261,9 +273,9 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
             smax = warp_max_u64(smax);
             thmax = warp_max_u64(thmax);
             const double sm = __longlong_as_double(smax);
-            unsigned long long flags = 0;  // 1: last local step, 2: stop (degenerate speeds)
+            unsigned long long flags = 0;  // 1: last local step, 2: stop (degenerate state or steps)
             double dt = 0.0;
-            if (!(sm > 0.0) || isnan(sm)) {
+            if (!(sm > 0.0) || !isfinite(sm) || nloc >= MAX_LOCAL_STEPS) {
                 flags = 2;
             } else {
                 const double rem = dT - t;
@@ -272,11 +284,16 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
                     double dtv = p.cfl * p.dx * p.dx / (2.0 * p.visc * (5.0 / 3.0) * __longlong_as_double(thmax));
                     if (dtv < dt) dt = dtv;
                 }
-                if (dt >= rem) {
+                if (!(dt > 0.0)) {
+                    flags = 2;
+                } else if (dt >= rem) {
                     dt = rem;
                     flags = 1;
+                } else if (!(t + dt > t)) {
+                    flags = 2;  // no progress: the step is below the resolution of t
                 }
             }
+            if (flags == 2 && lane == 0) atomicCAS(status, 0, ST_NONPHYS);
             if (lane == 0) sh[0] = __double_as_longlong(dt), sh[1] = flags;
         }
         // 3. face f of the block lies between its cells f - 1 and f
@@ -344,6 +361,7 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
         buf ^= 1;
         if (last) break;
         t += dt;
+        ++nloc;
     }
     cl.sync();  // every rank's reads of this region are over
     return cur_off;

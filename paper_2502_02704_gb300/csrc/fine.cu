@@ -35,6 +35,7 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include "maxwell_tab.h"
 #include "pr_kernels.h"
 
 namespace cg = cooperative_groups;
@@ -145,36 +146,22 @@ __device__ __forceinline__ T face_value(T fm, T f0, T f1, T f2, bool pos)
 // Shared-memory layout helpers.
 __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Factor tables of the Maxwellians of ncols x cells.  par[i*8 + 0..4] =
-// (u_x, u_y, u_z, theta, weight*rho*(2 pi theta)^{-3/2}) in float64.  The
-// float32 tables are evaluated in float32 from the float64 parameters (the
-// FP64 pipe of this GPU is ~1/64 rate); the float64 tables in float64.
+// Factor tables of the Maxwellians of ncols x cells.  float64: par[i*8 + 0..4]
+// = (u_x, u_y, u_z, theta, weight*rho*(2 pi theta)^{-3/2}), the tables
+// evaluated in float64.  float32: tp[i] holds the same parameters as float
+// pairs in grid units (tabpar_from_sums) and each entry is evaluated to about
+// 1e-9 before its one rounding (tab_entry, float32 pipes only: this GPU's
+// FP64 pipe is ~1/64 of their rate).  Grid coordinates k_j = j + 1/2 - nv/2
+// are exact, so the tables keep the grid's mirror symmetry.
 template <typename T, int NT>
-__device__ void write_tables(const Inst& I, int c0, int ncols, const double* par, T* tout, T* tb)
+__device__ void write_tables(const Inst& I, int c0, int ncols, const double* par, const TabPar* tp, T* tout, T* tb)
 {
     const int tid = threadIdx.x;
     const int nv = I.nv, tw = 3 * nv;
     if (sizeof(T) == 4) {
-        float* pf = reinterpret_cast<float*>(tb + ncols * tw);  // [ncols][5]: u_x, u_y, u_z, 1/(2 theta), weight*C
-        for (int i = tid; i < ncols; i += NT) {
-            pf[i * 5 + 0] = (float)par[i * 8 + 0];
-            pf[i * 5 + 1] = (float)par[i * 8 + 1];
-            pf[i * 5 + 2] = (float)par[i * 8 + 2];
-            pf[i * 5 + 3] = (float)(0.5 / par[i * 8 + 3]);
-            pf[i * 5 + 4] = (float)par[i * 8 + 4];
-        }
-        __syncthreads();
-        const float Lf = (float)I.L, dvf = (float)I.dv;
         for (int idx = tid; idx < ncols * tw; idx += NT) {
             int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
-            // nodes of the upper half are the exact negatives of the lower half,
-            // so the float32 tables keep the grid's mirror symmetry
-            const int jm = j < nv - 1 - j ? j : nv - 1 - j;
-            const float vlow = -Lf + ((float)jm + 0.5f) * dvf;
-            float vj = j == jm ? vlow : -vlow;
-            float dvu = vj - pf[i * 5 + d];
-            float val = expf(-(dvu * dvu) * pf[i * 5 + 3]);
-            if (d == 0) val *= pf[i * 5 + 4];
+            const float val = tab_entry(tp[i], d, node_k(j, nv));
             tb[idx] = (T)val;
             tout[(size_t)(c0 + i) * tw + rem] = (T)val;
         }
@@ -193,8 +180,9 @@ __device__ void write_tables(const Inst& I, int c0, int ncols, const double* par
 }
 
 // Conserved moments (Eq. 18) of f = wg g + M_tab for ncols x cells, from the
-// g sums mom[i*5 + 0..4] = (g, v_x g, v_y g, v_z g, |v|^2 g) (no dv^3) and the
-// 1-D sums of the tables tb (separable M): written to Ucur (and Uout).
+// g sums in grid units mom[i*5 + 0..4] = (g, k_x g, k_y g, k_z g, |k|^2 g),
+// v = k dv (no dv^3), and the 1-D sums of the tables tb (separable M):
+// written to Ucur (and Uout).
 template <typename T, int NT>
 __device__ void project_columns(const Inst& I, int c0, int ncols, const double* mom, double wg, const T* tb,
                                 double* Uout)
@@ -231,11 +219,12 @@ __device__ void project_columns(const Inst& I, int c0, int ncols, const double* 
             V[3] = dv3 * x0 * y0 * gs[2][1];
             V[4] = 0.5 * dv3 * (gs[0][2] * y0 * z0 + x0 * gs[1][2] * z0 + x0 * y0 * gs[2][2]);
             if (wg != 0.0) {
+                const double w1 = wg * dv3 * I.dv;
                 V[0] += wg * mom[i * 5 + 0] * dv3;
-                V[1] += wg * mom[i * 5 + 1] * dv3;
-                V[2] += wg * mom[i * 5 + 2] * dv3;
-                V[3] += wg * mom[i * 5 + 3] * dv3;
-                V[4] += wg * 0.5 * mom[i * 5 + 4] * dv3;
+                V[1] += w1 * mom[i * 5 + 1];
+                V[2] += w1 * mom[i * 5 + 2];
+                V[3] += w1 * mom[i * 5 + 3];
+                V[4] += 0.5 * w1 * I.dv * mom[i * 5 + 4];
             }
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
@@ -246,22 +235,56 @@ __device__ void project_columns(const Inst& I, int c0, int ncols, const double* 
     }
 }
 
-// Maxwellian parameters from moment sums (rho, m, |v|^2 sums without dv^3):
-// u = m/rho, theta = (sum|v|^2 f / rho - |u|^2)/3 (= Eq. 18's 3 rho theta).
-__device__ __forceinline__ void prim_from_sums(const double* s, double dv3, double weight, double* par,
+// Maxwellian parameters from moment sums in grid units s = (f, k f, |k|^2 f
+// summed, v = k dv, no dv^3): u = dv s_{1..3}/s_0, theta = dv^2 (s_4/s_0 -
+// |s_{1..3}/s_0|^2)/3 (= Eq. 18's 3 rho theta), rho = s_0 dv^3.
+__device__ __forceinline__ void prim_from_sums(const double* s, double dv, double dv3, double weight, double* par,
                                                int* status)
 {
     double rho = s[0] * dv3;
-    double ir = 1.0 / rho;
-    double ux = s[1] * dv3 * ir, uy = s[2] * dv3 * ir, uz = s[3] * dv3 * ir;
-    double th = (s[4] * dv3 * ir - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    double is0 = 1.0 / s[0];
+    double kx = s[1] * is0, ky = s[2] * is0, kz = s[3] * is0;
+    double th = dv * dv * (s[4] * is0 - (kx * kx + ky * ky + kz * kz)) / 3.0;
     if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
     double tp = 2.0 * PI * th;
-    par[0] = ux;
-    par[1] = uy;
-    par[2] = uz;
+    par[0] = kx * dv;
+    par[1] = ky * dv;
+    par[2] = kz * dv;
     par[3] = th;
     par[4] = weight * rho / (tp * sqrt(tp));
+}
+
+// The same Maxwellian as float pairs in grid units, for the float32 tables:
+// u_d/dv = s_d/s_0, tau = s_4/s_0 - |u/dv|^2 = 3 theta/dv^2, so the exponent
+// (k_j - u_d/dv)^2 dv^2/(2 theta) has w = 3/(2 tau) and the prefactor
+// weight rho (2 pi theta)^{-3/2} = weight s_0 (2 pi tau/3)^{-3/2}: dv drops
+// out.  Parameters in float64 (Eq. 18's moments and the Maxwellian of Eq. 4),
+// then split into pairs.
+__device__ __forceinline__ TabPar tabpar_from_sums(const double* s, double weight, int* status)
+{
+    TabPar P;
+    const double is0 = 1.0 / s[0];
+    const double k[3] = {s[1] * is0, s[2] * is0, s[3] * is0};
+    const double tau = s[4] * is0 - (k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    if (!(s[0] > 0.0) || !(tau > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
+    const double tq = (2.0 * PI / 3.0) * tau;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) split_pair(k[d], P.uh[d], P.ul[d]);
+    split_pair(1.5 / tau, P.wh, P.wl);
+    split_pair(weight * s[0] / (tq * sqrt(tq)), P.ph, P.pl);
+    return P;
+}
+
+// Grid-unit sums (f, k f, |k|^2 f without dv^3) of the conserved state V
+// (rho, rho u, E) of cell c (the lift source).
+__device__ __forceinline__ void sums_from_state(const double* V, int nx, int c, double dv, double dv3, double* s)
+{
+    const double id3 = 1.0 / dv3, id4 = id3 / dv;
+    s[0] = V[c] * id3;
+    s[1] = V[nx + c] * id4;
+    s[2] = V[2 * nx + c] * id4;
+    s[3] = V[3 * nx + c] * id4;
+    s[4] = 2.0 * V[4 * nx + c] * (id4 / dv);
 }
 
 // Last CTA of a tile: sum the chunk partials of step s (fixed order, one
@@ -274,7 +297,8 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
     const int tid = threadIdx.x;
     double* mom = reinterpret_cast<double*>(smem);  // [MAX_TX][5]
     double* par = mom + MAX_TX * 5;                  // [MAX_TX][8]
-    T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);   // [MAX_TX][3][nv] (+ float parameters)
+    TabPar* tp = reinterpret_cast<TabPar*>(par);     // float32: the pairs in place of par
+    T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);   // [MAX_TX][3][nv]
     const int n_vc = I.n_vc;
     for (int idx = tid; idx < ncols * 5; idx += NT) {
         const int i = idx / 5, q = idx - i * 5;
@@ -284,10 +308,13 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
         mom[idx] = acc;
     }
     __syncthreads();
-    for (int i = tid; i < ncols; i += NT) prim_from_sums(mom + i * 5, I.dv3, I.b, par + i * 8, status);
+    for (int i = tid; i < ncols; i += NT) {
+        if (sizeof(T) == 4) tp[i] = tabpar_from_sums(mom + i * 5, I.b, status);
+        else prim_from_sums(mom + i * 5, I.dv, I.dv3, I.b, par + i * 8, status);
+    }
     __syncthreads();
     T* tout = reinterpret_cast<T*>(I.tab[pout]);
-    write_tables<T, NT>(I, c0, ncols, par, tout, tb);
+    write_tables<T, NT>(I, c0, ncols, par, tp, tout, tb);
     if (s == nsteps) {
         __syncthreads();
         project_columns<T, NT>(I, c0, ncols, mom, I.a, tb, I.Uout);
@@ -455,14 +482,17 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     cp_async_wait<RING>();
     __syncthreads();
 
-    const double vxd = -I.L + (jx + 0.5) * I.dv, vyd = -I.L + (jy + 0.5) * I.dv;
-    const double vzd = -I.L + (jz + 0.5) * I.dv;
+    const double vxd = -I.L + (jx + 0.5) * I.dv;
     const bool pos = vxd > 0.0;
     const T cour = (T)(I.nu * vxd);
-    const T vx = (T)vxd, vy = (T)vyd, vxy2 = (T)(vxd * vxd + vyd * vyd);
-    // v_z of node q of this thread = vz0 + q dv:  sum vz f = vz0 s0 + dv t1,
-    // sum vz^2 f = vz0^2 s0 + 2 vz0 dv t1 + dv^2 t2, t1 = sum q f_q, t2 = sum q^2 f_q
-    const T vz0 = (T)vzd, dvz = (T)I.dv, zz0 = (T)(vzd * vzd), zz1 = (T)(2.0 * vzd * I.dv), zz2 = (T)(I.dv * I.dv);
+    // moment weights in grid units, v = k dv with k = j + 1/2 - nv/2 (half
+    // integers, exact in float32, so no weight carries a rounding error into
+    // the sums): node q of this thread has k_z = kz0 + q, so sum k_z f =
+    // kz0 s0 + t1 and sum k_z^2 f = kz0^2 s0 + 2 kz0 t1 + t2 with t1 = sum q f_q,
+    // t2 = sum q^2 f_q; dv and dv^2 are applied in float64 after the reduction
+    const T kx = T(0.5) * T(2 * jx + 1 - nv), ky = T(0.5) * T(2 * jy + 1 - nv);
+    const T kz0 = T(0.5) * T(2 * jz + 1 - nv), kz1 = T(2 * jz + 1 - nv);
+    const T kk0 = kx * kx + ky * ky + kz0 * kz0;
 
     // value of the current state at extended column e for this thread's V velocities
     auto recon = [&](int e, T (&o)[V]) {
@@ -574,10 +604,10 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
                 t2 += T(q * q) * fs[q];
             }
             r[0] = s0;
-            r[1] = vx * s0;
-            r[2] = vy * s0;
-            r[3] = vz0 * s0 + dvz * t1;
-            r[4] = (vxy2 + zz0) * s0 + zz1 * t1 + zz2 * t2;
+            r[1] = kx * s0;
+            r[2] = ky * s0;
+            r[3] = kz0 * s0 + t1;
+            r[4] = kk0 * s0 + kz1 * t1 + t2;
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) r[q] = T(0);
@@ -692,25 +722,18 @@ k_lift(const Inst* __restrict__ insts, InstState* st, const Active* __restrict__
     const int c0 = xt * I.tx, ncols = min(I.nx, c0 + I.tx) - c0;
     double* mom = reinterpret_cast<double*>(smem);
     double* par = mom + MAX_TX * 5;
+    TabPar* tp = reinterpret_cast<TabPar*>(par);
     T* tb = reinterpret_cast<T*>(par + MAX_TX * 8);
     for (int i = threadIdx.x; i < ncols; i += THREADS) {
-        const int c = c0 + i, nx = I.nx;
-        double rho = I.Uin[c], mx = I.Uin[nx + c], my = I.Uin[2 * nx + c], mz = I.Uin[3 * nx + c];
-        double E = I.Uin[4 * nx + c];
-        double ux = mx / rho, uy = my / rho, uz = mz / rho;
-        double th = (2.0 * E / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
-        if (!(rho > 0.0) || !(th > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
-        double tp = 2.0 * PI * th;
-        par[i * 8 + 0] = ux;
-        par[i * 8 + 1] = uy;
-        par[i * 8 + 2] = uz;
-        par[i * 8 + 3] = th;
-        par[i * 8 + 4] = rho / (tp * sqrt(tp));
+        double sm[5];
+        sums_from_state(I.Uin, I.nx, c0 + i, I.dv, I.dv3, sm);
+        if (sizeof(T) == 4) tp[i] = tabpar_from_sums(sm, 1.0, status);
+        else prim_from_sums(sm, I.dv, I.dv3, 1.0, par + i * 8, status);
     }
     __syncthreads();
     InstState S = st[b];
     T* tout = reinterpret_cast<T*>(I.tab[S.cur]);
-    write_tables<T, THREADS>(I, c0, ncols, par, tout, tb);
+    write_tables<T, THREADS>(I, c0, ncols, par, tp, tout, tb);
     __syncthreads();
     project_columns<T, THREADS>(I, c0, ncols, mom, 0.0, tb, nullptr);
     if (xt == 0 && threadIdx.x == 0) st[b].a0 = 0.0;
@@ -825,44 +848,17 @@ __host__ __device__ inline size_t cl_floats_offset(int w, int nv, int nt)
 
 __host__ __device__ inline size_t cl_smem_bytes(int w, int nv, int nt)
 {
-    return align16(cl_floats_offset(w, nv, nt) + (size_t)w * 5 * sizeof(double) + (size_t)w * 5 * sizeof(float));
+    return align16(cl_floats_offset(w, nv, nt) + (size_t)w * 5 * sizeof(double) + (size_t)w * sizeof(TabPar));
 }
 
-// Table parameters (u_x, u_y, u_z, 1/(2 theta), weight rho (2 pi theta)^{-3/2})
-// of the Maxwellian with moment sums s = (f, v f, |v|^2 f summed, no dv^3):
-// theta's numerator s_4 s_0 - |s_1..3|^2 = 3 theta s_0^2 in float64 (it
-// cancels at high Mach numbers), the rest in float32 like the tables it
-// feeds.  This chain sits between two steps of the cluster run, where each
-// FP64 warp instruction costs tens of cycles.
-__device__ __forceinline__ void cl_params(const double* s, double dv3, double weight, float* pf, int* status)
-{
-    const double num = s[4] * s[0] - (s[1] * s[1] + s[2] * s[2] + s[3] * s[3]);
-    const float s0 = (float)s[0], numf = (float)num;
-    if (!(s0 > 0.f) || !(numf > 0.f)) atomicCAS(status, 0, ST_NONPHYS);
-    const float is0 = 1.0f / s0;
-    const float thf = numf * (is0 * is0) * (1.0f / 3.0f), tpf = 2.0f * (float)PI * thf;
-    pf[0] = (float)s[1] * is0;
-    pf[1] = (float)s[2] * is0;
-    pf[2] = (float)s[3] * is0;
-    pf[3] = 0.5f / thf;
-    pf[4] = (float)weight * (s0 * (float)dv3) / (tpf * sqrtf(tpf));
-}
-
-// Factor tables of ncols cells from their float32 parameters pf[i*5 + 0..4],
-// into shared memory only.
-__device__ void cl_tables(const Inst& I, int ncols, const float* pf, float* tb)
+// Factor tables of ncols cells from their parameter pairs tp[i], into
+// shared memory only.
+__device__ void cl_tables(const Inst& I, int ncols, const TabPar* tp, float* tb)
 {
     const int tid = threadIdx.x, nt = blockDim.x, nv = I.nv, tw = 3 * nv;
-    const float Lf = (float)I.L, dvf = (float)I.dv;
     for (int idx = tid; idx < ncols * tw; idx += nt) {
         int i = idx / tw, rem = idx - i * tw, d = rem / nv, j = rem - d * nv;
-        const int jm = j < nv - 1 - j ? j : nv - 1 - j;
-        const float vlow = -Lf + ((float)jm + 0.5f) * dvf;
-        float vj = j == jm ? vlow : -vlow;
-        float dvu = vj - pf[i * 5 + d];
-        float val = expf(-(dvu * dvu) * pf[i * 5 + 3]);
-        if (d == 0) val *= pf[i * 5 + 4];
-        tb[idx] = val;
+        tb[idx] = tab_entry(tp[i], d, node_k(j, nv));
     }
 }
 
@@ -891,19 +887,17 @@ k_fine_cluster(const Inst* __restrict__ insts, const Active* __restrict__ active
     float* tab = g + 2 * (size_t)w * nv3;        // [2][w][tw]
     float* red = tab + 2 * (size_t)w * tw;       // [w][NW][5] warp totals
     double* mom = reinterpret_cast<double*>(smem + cl_floats_offset(w, nv, NT));  // [w][5]
-    float* pf = reinterpret_cast<float*>(mom + 5 * w);                              // [w][5]
+    TabPar* tp = reinterpret_cast<TabPar*>(mom + 5 * w);                            // [w]
 
     // lift (Eq. 17) of the own cells into tables buffer 0: the conserved
-    // moments as sums (rho, m, 2E) / dv^3
+    // moments as grid-unit sums, the Maxwellian parameters in float64
     for (int i = tid; i < ncols; i += NT) {
-        const int c = c0 + i;
-        const double id3 = 1.0 / I.dv3;
-        const double sm[5] = {I.Uin[c] * id3, I.Uin[nx + c] * id3, I.Uin[2 * nx + c] * id3, I.Uin[3 * nx + c] * id3,
-                              2.0 * I.Uin[4 * nx + c] * id3};
-        cl_params(sm, I.dv3, 1.0, pf + i * 5, status);
+        double sm[5];
+        sums_from_state(I.Uin, nx, c0 + i, I.dv, I.dv3, sm);
+        tp[i] = tabpar_from_sums(sm, 1.0, status);
     }
     __syncthreads();
-    cl_tables(I, ncols, pf, tab);
+    cl_tables(I, ncols, tp, tab);
     if (nsteps <= 0) {  // the projection of the lifted state
         __syncthreads();
         project_columns<float, NT>(I, c0, ncols, mom, 0.0, tab, I.Uout);
@@ -915,13 +909,13 @@ k_fine_cluster(const Inst* __restrict__ insts, const Active* __restrict__ active
     const int v0 = tid * V;  // NT * V == nv3
     const int jz = v0 % nv, jy = (v0 / nv) % nv, jx = v0 / (nv * nv);
     const int jxf = nv - 1 - jx, v0f = (jxf * nv + jy) * nv + jz;
-    const double vxd = -I.L + (jx + 0.5) * I.dv, vyd = -I.L + (jy + 0.5) * I.dv;
-    const double vzd = -I.L + (jz + 0.5) * I.dv;
+    const double vxd = -I.L + (jx + 0.5) * I.dv;
     const bool pos = vxd > 0.0;
     const float cour = (float)(I.nu * vxd);
-    const float vx = (float)vxd, vy = (float)vyd, vxy2 = (float)(vxd * vxd + vyd * vyd);
-    const float vz0 = (float)vzd, dvz = (float)I.dv, zz0 = (float)(vzd * vzd), zz1 = (float)(2.0 * vzd * I.dv),
-                zz2 = (float)(I.dv * I.dv);
+    // moment weights in grid units, as in the tiled kernel
+    const float kx = 0.5f * (float)(2 * jx + 1 - nv), ky = 0.5f * (float)(2 * jy + 1 - nv);
+    const float kz0 = 0.5f * (float)(2 * jz + 1 - nv), kz1 = (float)(2 * jz + 1 - nv);
+    const float kk0 = kx * kx + ky * ky + kz0 * kz0;
     const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
     const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
 
@@ -1011,10 +1005,10 @@ k_fine_cluster(const Inst* __restrict__ insts, const Active* __restrict__ active
             }
             float r[5];
             r[0] = s0;
-            r[1] = vx * s0;
-            r[2] = vy * s0;
-            r[3] = vz0 * s0 + dvz * t1;
-            r[4] = (vxy2 + zz0) * s0 + zz1 * t1 + zz2 * t2;
+            r[1] = kx * s0;
+            r[2] = ky * s0;
+            r[3] = kz0 * s0 + t1;
+            r[4] = kk0 * s0 + kz1 * t1 + t2;
             float tot = warp_sum5(r, lane);
             if (writer) red[(i * NW + warp) * 5 + qsel] = tot;
         }
@@ -1030,10 +1024,10 @@ k_fine_cluster(const Inst* __restrict__ insts, const Active* __restrict__ active
             if (on && k == 0) mom[vi] = x;
         }
         __syncthreads();
-        for (int i = tid; i < ncols; i += NT) cl_params(mom + i * 5, I.dv3, I.b, pf + i * 5, status);
+        for (int i = tid; i < ncols; i += NT) tp[i] = tabpar_from_sums(mom + i * 5, I.b, status);
         __syncthreads();
         float* tnext = tab + (size_t)(p ^ 1) * w * tw;
-        cl_tables(I, ncols, pf, tnext);
+        cl_tables(I, ncols, tp, tnext);
         if (s == nsteps) {  // projection (Eq. 18) of f = a g + M
             __syncthreads();
             project_columns<float, NT>(I, c0, ncols, mom, I.a, tnext, I.Uout);
@@ -1076,14 +1070,14 @@ size_t fine_run_smem(int precision, int vpt, int tx, int nv, int H)
     int nw = CHUNK / vpt / 32;
     size_t ring = (size_t)(precision == 0 ? Ring<double>::SLOTS : Ring<float>::SLOTS) * CHUNK * es;
     size_t item = ring + align16((size_t)(tx + 2 * H) * 3 * nv * es) + (size_t)tx * nw * 5 * es;
-    size_t fin = (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es + (size_t)tx * 5 * sizeof(float);
+    size_t fin = (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es;
     return item > fin ? item : fin;
 }
 
 size_t lift_smem(int precision, int tx, int nv)
 {
     size_t es = precision == 0 ? sizeof(double) : sizeof(float);
-    return (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es + (size_t)tx * 5 * sizeof(float);
+    return (size_t)MAX_TX * 13 * sizeof(double) + (size_t)tx * 3 * nv * es;
 }
 
 // Dynamic shared memory may use what the static allocation leaves of the opt-in limit.

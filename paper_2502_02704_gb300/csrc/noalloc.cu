@@ -58,10 +58,18 @@ extern "C" int pr_fine_step_noalloc(const pr_instance* d, const double* f_in, do
         pr_internal_set_global_error(why);
         return PR_EINVAL;
     };
+    auto cuda_fail = [](cudaError_t e) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "pr_fine_step_noalloc: %s", cudaGetErrorString(e));
+        pr_internal_set_global_error(msg);
+        return PR_ECUDA;
+    };
     if (!d || !f_in || !f_out || f_in == f_out) return reject("pr_fine_step_noalloc: null or aliased arguments");
-    if (d->nx < 1 || d->nv < 4 || d->nv % 4 || !(d->x1 > d->x0) || !(d->L > 0) || !(d->eps > 0) || !(d->dt > 0) ||
-        d->bc < 0 || d->bc > 2 || d->scheme < 0 || d->scheme > 1 || (d->scheme == PR_MUSCL && d->bc == PR_BC_REFLECT && d->nx < 2))
-        return reject("pr_fine_step_noalloc: invalid instance parameters");
+    if (d->nx < 1 || d->nv < 4 || d->nv % 4 || !(d->x1 > d->x0) || !std::isfinite(d->x0) || !std::isfinite(d->x1) ||
+        !(d->L > 0) || !std::isfinite(d->L) || !(d->eps > 0) || !(d->dt > 0) || !std::isfinite(d->dt) || d->bc < 0 ||
+        d->bc > 2 || d->scheme < 0 || d->scheme > 1 || (d->scheme == PR_MUSCL && d->bc == PR_BC_REFLECT && d->nx < 2))
+        return reject("pr_fine_step_noalloc: invalid instance parameters (sizes, domain, L, eps > 0, finite dt > 0, "
+                      "bc, scheme)");
     if ((reinterpret_cast<uintptr_t>(f_in) | reinterpret_cast<uintptr_t>(f_out)) & 15)
         return reject("pr_fine_step_noalloc: f_in and f_out must be 16-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -113,9 +121,30 @@ extern "C" int pr_fine_step_noalloc(const pr_instance* d, const double* f_in, do
         return reject(msg);
     }
 
+    // the fine kernel's shared memory for this instance against the device's limit
+    const int H = d->scheme == PR_MUSCL ? 2 : 1;
+    const size_t smem = prk::fine_run_smem(0, 4, I.tx, I.nv, H);
+    int dev = 0, smax = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        pr_internal_set_global_error("pr_fine_step_noalloc: no usable CUDA device");
+        return PR_ECUDA;
+    }
+    if (smem > (size_t)smax) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "pr_fine_step_noalloc: instance needs %zu bytes of shared memory per CTA, the "
+                 "device allows %d", smem, smax);
+        return reject(msg);
+    }
+
     unsigned char* base = nullptr;
     int rc = scratch_address(&base);
-    if (rc) return rc;
+    if (rc) {
+        pr_internal_set_global_error("pr_fine_step_noalloc: looking up the static scratch array failed");
+        return rc;
+    }
     unsigned* sync = reinterpret_cast<unsigned*>(base + o_sync + 8);
     I.g[0] = const_cast<double*>(f_in);
     I.g[1] = f_out;
@@ -138,18 +167,17 @@ extern "C" int pr_fine_step_noalloc(const pr_instance* d, const double* f_in, do
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_sync, 0, 8 + 2 * sizeof(unsigned) * I.n_xt, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_tab0, 0, tab, s);
-    if (e != cudaSuccess) return PR_ECUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
 
     const prk::Inst* dI = reinterpret_cast<const prk::Inst*>(base + o_inst);
     prk::InstState* dS = reinterpret_cast<prk::InstState*>(base + o_state);
     const prk::Active* dA = reinterpret_cast<const prk::Active*>(base + o_active);
     int* dstatus = reinterpret_cast<int*>(base + o_status);
-    const int H = d->scheme == PR_MUSCL ? 2 : 1;
-    size_t smem = prk::fine_run_smem(0, 4, I.tx, I.nv, H);
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (prk::fine_run_occupancy(0, d->scheme, 4, smem, &per_sm) != 0 || per_sm < 1) return PR_EINVAL;
+    int per_sm = 0;
+    if (prk::fine_run_occupancy(0, d->scheme, 4, smem, &per_sm) != 0 || per_sm < 1) {
+        cudaGetLastError();
+        return reject("pr_fine_step_noalloc: the fine kernel cannot be resident with this instance's shared memory");
+    }
     long long items = prefix[1];
     int grid = (int)(items < (long long)per_sm * sms ? items : (long long)per_sm * sms);
     e = prk::launch_fine_run(0, d->scheme, 4, dI, dS, reinterpret_cast<const long long*>(base + o_prefix), dA, 1,
@@ -157,10 +185,11 @@ extern "C" int pr_fine_step_noalloc(const pr_instance* d, const double* f_in, do
     // f_out now holds f*; apply the implicit relaxation in place: f = a f* + b M
     if (e == cudaSuccess) e = prk::launch_advance(dI, dS, dA, 1, 1, s);
     if (e == cudaSuccess) e = prk::launch_materialize(0, dI, dS, 0, I, f_out, s);
-    if (e != cudaSuccess) return PR_ECUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
     int status = 0;
-    if (cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return PR_ECUDA;
+    e = cudaMemcpyAsync(&status, dstatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (status == PR_ENONPHYS) pr_internal_set_global_error("pr_fine_step_noalloc: a density or temperature became <= 0");
     return status;
 }

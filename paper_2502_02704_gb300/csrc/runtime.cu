@@ -337,6 +337,13 @@ static int create_batch(pr_batch** out, const pr_instance* inst, int n, int prec
         if (std::isinf(d.eps)) {
             I.a = 1.0;
             I.b = 0.0;
+        } else if (precision == PR_MIXED) {
+            // the float32 steps scale g by float(a) (Eq. 7: f = a f* + b M):
+            // with a = float(eps/(eps+dt)) and b = 1 - a the weights the
+            // kernels use sum to 1, so the relaxation keeps the moments (the
+            // relaxation rate moves by less than 1e-6 relative)
+            I.a = (double)(float)(d.eps / (d.eps + d.dt));
+            I.b = 1.0 - I.a;
         } else {
             I.a = d.eps / (d.eps + d.dt);
             I.b = d.dt / (d.eps + d.dt);
@@ -493,10 +500,25 @@ static void cons_to_prim_host(int nx, const double* V, double* U)
 
 static int check_prim(const double* U, int nx)
 {
-    for (int i = 0; i < nx; ++i)
-        if (!(U[i] > 0.0) || !(U[4 * nx + i] > 0.0) || !std::isfinite(U[nx + i]) || !std::isfinite(U[2 * nx + i]) ||
-            !std::isfinite(U[3 * nx + i]))
-            return PR_ENONPHYS;
+    for (int i = 0; i < nx; ++i) {
+        if (!(U[i] > 0.0) || !(U[4 * nx + i] > 0.0)) return PR_ENONPHYS;
+        for (int q = 0; q < 5; ++q)
+            if (!std::isfinite(U[q * nx + i])) return PR_ENONPHYS;
+    }
+    return PR_OK;
+}
+
+// Conserved state: every component finite, rho > 0 and a positive temperature.
+static int check_cons(const double* V, int nx)
+{
+    for (int i = 0; i < nx; ++i) {
+        for (int q = 0; q < 5; ++q)
+            if (!std::isfinite(V[q * nx + i])) return PR_ENONPHYS;
+        const double rho = V[i];
+        if (!(rho > 0.0)) return PR_ENONPHYS;
+        const double m2 = V[nx + i] * V[nx + i] + V[2 * nx + i] * V[2 * nx + i] + V[3 * nx + i] * V[3 * nx + i];
+        if (!(2.0 * V[4 * nx + i] - m2 / rho > 0.0)) return PR_ENONPHYS;
+    }
     return PR_OK;
 }
 
@@ -515,6 +537,17 @@ static int lift_instances(pr_batch* b, int begin, int end, cudaStream_t s)
     }
     prk::Active all{0, b->n};
     BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+    return PR_OK;
+}
+
+int pr_fine_dt_stab(const pr_instance* d, double cfl, double* dt)
+{
+    if (!d || !dt) return PR_EINVAL;
+    if (d->nx < 1 || d->nv < 1 || !(d->x1 > d->x0) || !std::isfinite(d->x1 - d->x0) || !(d->L > 0) ||
+        !std::isfinite(d->L) || !(cfl > 0) || !std::isfinite(cfl))
+        return PR_EINVAL;
+    const double dx = (d->x1 - d->x0) / d->nx, dv = 2.0 * d->L / d->nv;
+    *dt = cfl * dx / (d->L - 0.5 * dv);
     return PR_OK;
 }
 
@@ -1060,7 +1093,9 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
     *out = nullptr;
     if (!g || !v || !t) return init_fail(PR_EINVAL, "null parameter block");
     if (t->n_slices < 1) return init_fail(PR_EINVAL, "n_slices must be >= 1");
-    if (!(t->T > 0) || !(t->cfl_f > 0) || !(t->cfl_g > 0)) return init_fail(PR_EINVAL, "T, cfl_f and cfl_g must be > 0");
+    if (!(t->T > 0) || !(t->cfl_f > 0) || !(t->cfl_g > 0) || !std::isfinite(t->T) || !std::isfinite(t->cfl_f) ||
+        !std::isfinite(t->cfl_g))
+        return init_fail(PR_EINVAL, "T, cfl_f and cfl_g must be finite and > 0");
     if (t->precision != PR_FP64 && t->precision != PR_MIXED) return init_fail(PR_EINVAL, "bad precision");
     if (t->sound_speed != PR_SOUND_GAMMA53 && t->sound_speed != PR_SOUND_SQRT_THETA)
         return init_fail(PR_EINVAL, "bad sound speed");
@@ -1089,8 +1124,11 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
             return init_fail(PR_EINVAL, "bad force-path velocity grid");
         }
     } else {
-        double dv = 2.0 * v->L / v->nv, vmax = v->L - 0.5 * dv;
-        dts = t->cfl_f * dx / vmax;
+        pr_instance gi{g->nx, g->x0, g->x1, g->bc, v->nv, v->L, eps, 1.0, t->scheme};
+        if (pr_fine_dt_stab(&gi, t->cfl_f, &dts) != PR_OK) {
+            free_ctx(c);
+            return init_fail(PR_EINVAL, "bad grid or velocity box");
+        }
     }
     if (t->nf > 0) c->nf = t->nf;
     else {
@@ -1219,7 +1257,10 @@ int pr_set_initial(pr_ctx* c, const double* U0)
 int pr_coarse_step(pr_ctx* c, const double* Vin, double* Vout, double dT)
 {
     if (!c) return PR_EINVAL;
-    if (!Vin || !Vout || !(dT >= 0)) return cfail(c, PR_EINVAL, "null state or negative dT");
+    if (!Vin || !Vout || !(dT >= 0) || !std::isfinite(dT))
+        return cfail(c, PR_EINVAL, "null state, or dT negative or not finite");
+    if (check_cons(Vin, c->nx))
+        return cfail(c, PR_ENONPHYS, "state has a non-finite component, rho <= 0 or theta <= 0");
     cudaStream_t s = ctx_stream(c);
     CCUDA(c, cudaMemcpyAsync(c->dtmp, Vin, sizeof(double) * 5 * c->nx, cudaMemcpyHostToDevice, s));
     CCUDA(c, prk::launch_coarse(c->cp, c->dtmp, c->dtmp + 5 * c->nx, dT, c->dwork, c->dstatus, s));

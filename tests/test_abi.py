@@ -45,3 +45,23 @@ def test_null_problem_is_rejected_without_a_device():
     assert L.pr_fine_cluster_shape(None, C.byref(v), C.byref(v), C.byref(v)) == pr.PR_EINVAL
     assert L.pr_set_force_step(None, 0, -1, -1) == pr.PR_EINVAL
     assert L.pr_parareal_iter(None, None) == pr.PR_EINVAL
+
+
+def test_fine_dt_stab_needs_no_device():
+    # Sec. 2.2: dt_stab = cfl dx / max|v_x|, max|v_x| the outermost node
+    # L - dv/2 (cube centres); computed by the library, not by the binding.
+    dt = pr.pr_fine_dt_stab(pr.instance(64, 16, 1.0, L=8.0), 0.5)
+    assert dt == 0.5 * (1.0 / 64) / 7.5
+    assert pr.fine_dt(256, 24, 8.0) == pr.pr_fine_dt_stab(pr.instance(256, 24, 1.0), 0.5)
+    for bad in (pr.instance(0, 16, 1.0), pr.instance(8, 16, 1.0, L=-1.0), pr.instance(8, 16, 1.0, x0=1.0, x1=1.0)):
+        try:
+            pr.pr_fine_dt_stab(bad, 0.5)
+            raise AssertionError("accepted an invalid grid")
+        except pr.PrError as e:
+            assert e.code == pr.PR_EINVAL
+    for cfl in (0.0, float("inf"), float("nan")):
+        try:
+            pr.pr_fine_dt_stab(pr.instance(8, 16, 1.0), cfl)
+            raise AssertionError("accepted an invalid cfl")
+        except pr.PrError as e:
+            assert e.code == pr.PR_EINVAL

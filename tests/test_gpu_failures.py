@@ -2,6 +2,8 @@
 the persistent launch that runs out (a flag nothing sets), a staging wait of
 the force path that runs out (an mbarrier no copy completes), non-physical
 states, and that each object stays usable afterwards."""
+import math
+
 import numpy as np
 import pytest
 
@@ -106,3 +108,31 @@ def test_coarse_solver_reports_negative_temperature():
         assert np.all(np.isfinite(out))
     finally:
         pr.pr_destroy(ctx)
+
+
+def test_coarse_step_rejects_non_finite_inputs():
+    # G's local-step loop must end: a non-finite interval or state is refused
+    # on the host before any launch, and the object stays usable.
+    nx = 32
+    ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, 4, 8.0, 1e-2, 0.1, 2)
+    try:
+        V = np.zeros((5, nx))
+        V[0] = 1.0
+        V[4] = 1.5
+        for dT in (math.inf, math.nan, -1.0):
+            with pytest.raises(pr.PrError) as ei:
+                pr.pr_coarse_step(ctx, V, dT)
+            assert ei.value.code == pr.PR_EINVAL
+        for q, bad in ((0, math.inf), (4, math.inf), (1, math.nan), (0, 0.0)):
+            W2 = V.copy()
+            W2[q, 5] = bad
+            with pytest.raises(pr.PrError) as ei:
+                pr.pr_coarse_step(ctx, W2, 0.01)
+            assert ei.value.code == pr.PR_ENONPHYS, (q, bad)
+        out = pr.pr_coarse_step(ctx, V, 0.01)
+        assert np.allclose(out, V, rtol=0, atol=1e-15)  # a constant state stays
+    finally:
+        pr.pr_destroy(ctx)
+    with pytest.raises(pr.PrError) as ei:
+        pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, 4, 8.0, 1e-2, math.inf, 2)
+    assert ei.value.code == pr.PR_EINVAL

@@ -113,15 +113,13 @@ def test_batched_parareal_64_slices_full_size():
     # the batched-parareal configuration at its size: Sod on [0, 1], Nx = 256,
     # 24^3 on [-8, 8]^3, eps = 1e-2, outflow, upwind, T = 0.1, N = 64 slices
     # resident in one persistent launch; K = 2 against the oracle (both
-    # precisions), the successive errors too.
-    # FP64 tolerance: the coarse chain is bitwise the oracle's (-fmad=false)
-    # and one fine propagation P F L agrees to ~4e-14 (checked below at 1e-13);
-    # the correction U^n = G(U^{n-1}) + PFL - G adds each slice's difference
-    # along the sequential chain, so slice n differs by up to n times that:
-    # the bound at N = 64 is N x 5e-14 = 3.2e-12 (measured 2.0e-12 at n = 64,
-    # growing linearly from 3.9e-14 at n = 1).  Mixed precision composes the
-    # same way from its per-propagation float32 difference (checked below at
-    # 1.5e-6): bound N x 1.5e-6 (measured 4.3e-5 at n = 64).
+    # precisions), the successive errors too.  The correction
+    # U^n = G(U^{n-1}) + PFL - G adds each slice's fine-propagation
+    # difference along the sequential chain, so the composed bars 1e-12 /
+    # 1e-5 need one P F L to agree well: checked first (measured 7.8e-16 and
+    # 2.0e-7; composed over 64 slices 3.8e-14 and 1.1e-6 -- the float32
+    # differences left are rounding that does not keep one sign from slice to
+    # slice, so they grow far slower than 64 times the per-slice figure).
     nx, nv, N, K = 256, 24, 64, 2
     U0 = W.sod(nx)
     k = O.Kin(nx=nx, nv=nv, L=8.0, bc=O.BC_OUTFLOW, eps=1e-2, scheme=O.UPWIND)
@@ -134,15 +132,16 @@ def test_batched_parareal_64_slices_full_size():
     finally:
         O.set_threads(1)
     nf, dt = O.fine_nsteps(p)
-    for precision, one in ((pr.PR_FP64, 1e-13), (pr.PR_MIXED, 1.5e-6)):
+    for precision, one in ((pr.PR_FP64, 1e-14), (pr.PR_MIXED, 3e-7)):
         b = pr.pr_batch_create([pr.instance(nx, nv, dt, L=8.0, bc=pr.PR_BC_OUTFLOW, eps=1e-2)], precision)
         try:
             pr.pr_batch_set_initial(b, 0, V, pr.PR_CONSERVED)
             pr.pr_batch_run(b, nf)
-            assert moment_rel_err(pr.pr_batch_moments(b, 0), pfl) < one, precision
+            e1 = moment_rel_err(pr.pr_batch_moments(b, 0), pfl)
+            assert e1 < one, (precision, e1)
         finally:
             pr.pr_batch_destroy(b)
-    for precision, tol in ((pr.PR_FP64, N * 5e-14), (pr.PR_MIXED, N * 1.5e-6)):
+    for precision, tol in ((pr.PR_FP64, TOL_FP64), (pr.PR_MIXED, TOL_MIXED)):
         ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, nv, 8.0, 1e-2, 0.1, N, 0.5, 0.5, pr.PR_UPWIND, precision)
         try:
             pr.pr_set_initial(ctx, U0)

@@ -1,5 +1,5 @@
 """The allocation-free fine step (pr_fine_step_noalloc) gives the same result
-as the regular batch path.
+as the regular batch path and as the CPU oracle's fine step.
 
 Some callers cannot allocate GPU memory through this library (their device
 memory belongs to another allocator, or they must not allocate once set up);
@@ -7,9 +7,12 @@ for them pr_fine_step_noalloc takes caller-owned input and output arrays and
 keeps all its scratch in a static device array.  This file is collected last
 so that a failure here does not hide the other tests; it also runs alone.
 """
+import math
+
 import numpy as np
 import pytest
 
+import oracle as O
 import paper_2502_02704_gb300 as pr
 from paper_2502_02704_gb300 import workloads as W
 from helpers import TOL_FP64, f_rel_err
@@ -45,6 +48,12 @@ def test_noalloc_step_matches_batch_step_twice(scheme, bc):
     assert f_rel_err(out1.cpu().numpy(), r1) < TOL_FP64
     assert f_rel_err(out2.cpu().numpy(), r2) < TOL_FP64
     assert f_rel_err(r1, f0) > 1e-3
+    # and the oracle's fine step (Eqs. 11-13) directly, twice
+    k = O.Kin(nx=nx, nv=nv, L=8.0, bc=bc, eps=1e-2, scheme=scheme)
+    o1 = O.fine_step(k, inst.dt, f0)
+    o2 = O.fine_step(k, inst.dt, o1)
+    assert f_rel_err(out1.cpu().numpy(), o1) < TOL_FP64
+    assert f_rel_err(out2.cpu().numpy(), o2) < TOL_FP64
 
 
 def test_noalloc_rejects_instances_beyond_the_static_scratch():
@@ -56,3 +65,14 @@ def test_noalloc_rejects_instances_beyond_the_static_scratch():
         pr.pr_fine_step_noalloc(inst, x, x.clone())
     assert ei.value.code == pr.PR_EINVAL
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_rejects_non_finite_step_with_a_message():
+    import torch
+
+    x = torch.empty(8 * 4 ** 3, dtype=torch.float64, device="cuda")
+    for dt in (math.inf, math.nan, 0.0):
+        with pytest.raises(pr.PrError) as ei:
+            pr.pr_fine_step_noalloc(pr.instance(8, 4, dt), x, x.clone())
+        assert ei.value.code == pr.PR_EINVAL
+        assert "dt" in str(ei.value)
