@@ -38,6 +38,7 @@ WORKLOAD = "smooth periodic fine solve, Nx=512, 32^3 on [-8,8]^3, MUSCL-minmod, 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fine_run_traffic.txt")
 FORCE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_fused_traffic.txt")
 FINE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "fine.cu")
+FP64_ALG_FLOPS = 14  # algorithmic FP64 flops per cell-update of the MUSCL fine step (see run_ours)
 FORCE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "force.cu")
 
 
@@ -220,64 +221,168 @@ def _time_device(pr, torch, b, Vdev, outs, steps, warmup, stream):
     return ms / steps, kms, pr.pr_kernel_launches() - n0
 
 
-def _parareal_speedup(pr, np, nx=64, nv=16, N=8, T=0.1, Ks=(1, 2, 3, 4, 8)):
-    """Sod setup (eps=1e-2, outflow, upwind on [-8, 8]^3; by default Nx=64,
-    16^3, T=0.1, N=8): plain FP64 single-instance serial fine chain
-    U^n = P F L(U^{n-1}) vs mixed-precision batched parareal (Algorithm 2) for
-    several K, with the error of each against the FP64 serial chain."""
-    import torch
-    from paper_2502_02704_gb300 import workloads as W
+def _cons(np, U0):
+    """Conserved state (rho, rho u, E) of a primitive profile (host arithmetic
+    of the input only; E = rho |u|^2 / 2 + 3 rho theta / 2)."""
+    return np.stack([U0[0], U0[0] * U0[1], U0[0] * U0[2], U0[0] * U0[3],
+                     0.5 * U0[0] * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) + 1.5 * U0[0] * U0[4]])
 
-    U0 = W.sod(nx)
+
+def _median_s(f, reps):
+    f()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        f()
+        ts.append(time.perf_counter() - t0)
+    return sorted(ts)[len(ts) // 2]
+
+
+def _serial_chain(pr, np, torch, inst, V0, N, nf, precision, reps):
+    """The serial fine chain U^n = P F L(U^{n-1}), n = 1..N (what parareal
+    converges to at K = N), on one instance of the batch path in the given
+    precision.  Returns (seconds, median of reps; chain [N+1, 5, nx])."""
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
-    par = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, nv, 8.0, 1e-2, T, N, 0.5, 0.5, pr.PR_UPWIND, pr.PR_MIXED)
-    nf, dtf = pr.pr_fine_steps_per_slice(par)
-    one = pr.pr_batch_create([pr.instance(nx, nv, dtf, L=8.0, bc=pr.PR_BC_OUTFLOW, eps=1e-2, scheme=pr.PR_UPWIND)],
-                             pr.PR_FP64)
-    V0 = np.stack([U0[0], U0[0] * U0[1], U0[0] * U0[2], U0[0] * U0[3],
-                   0.5 * U0[0] * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) + 1.5 * U0[0] * U0[4]])
-    chain = torch.zeros((N + 1, 5, nx), dtype=torch.float64, device=dev)
+    one = pr.pr_batch_create([inst], precision)
+    chain = torch.zeros((N + 1, 5, inst.nx), dtype=torch.float64, device=dev)
     chain[0] = torch.tensor(V0, device=dev)
     try:
-        def serial():
+        def run():
             for n in range(1, N + 1):
                 pr.pr_batch_set_initial_device(one, 0, chain[n - 1], pr.PR_CONSERVED, stream)
                 pr.pr_batch_run(one, nf, stream)
                 pr.pr_batch_moments_device(one, 0, chain[n], stream)
             torch.cuda.synchronize()
 
-        def parareal(K):
-            pr.pr_set_initial(par, U0)
-            pr.pr_parareal_run(par, K)  # returns after the iterate is complete on the device
-
-        def median_s(f, reps=5):
-            f()
-            ts = []
-            for _ in range(reps):
-                t0 = time.perf_counter()
-                f()
-                ts.append(time.perf_counter() - t0)
-            return sorted(ts)[reps // 2]
-
-        t_ser = median_s(serial)
+        t = _median_s(run, reps)
         pr.pr_batch_sync(one)
-        ref = chain.cpu().numpy()
-        rows = []
-        for K in Ks:
-            t = median_s(lambda: parareal(K))
-            got = np.stack([pr.pr_moments(par, n) for n in range(N + 1)])
-            err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
-            rows.append({"K": K, "ms": t * 1e3, "max_rel_err_vs_fp64_serial": err, "speedup": t_ser / t})
-        return {"workload": f"Sod Nx={nx}, {nv}^3, eps=1e-2, outflow, upwind, T={T}, N={N}, "
-                            f"{nf} fine steps/slice",
-                "serial_fp64_ms": t_ser * 1e3, "parareal_mixed": rows,
-                "timing": "wall clock around synchronous calls, median of 5; parareal: pr_set_initial (the "
-                          "first coarse guess) + pr_parareal_run, serial: the N fine runs; both end with "
-                          "the moments in device memory, read back after the clock"}
+        return t, chain.cpu().numpy()
     finally:
-        pr.pr_destroy(par)
         pr.pr_batch_destroy(one)
+
+
+def _stage_times(pr, torch, inst, V0, nf, reps=5):
+    """Device times (ms, CUDA events on the launching stream, median) of the
+    pieces of one fine propagation P F L of one slice in mixed precision: the
+    lift L (Eq. 17), the n_f fine steps F and the projection P (Eq. 18) --
+    the T_Lift, T_Kin and T_Proj of the paper's cost estimate (Sec. 4)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    b = pr.pr_batch_create([inst], pr.PR_MIXED)
+    Vd = torch.tensor(V0, device=dev)
+    out = torch.empty_like(Vd)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    lift, kin, proj = [], [], []
+    try:
+        for r in range(reps + 1):
+            ev[0].record(stream)
+            pr.pr_batch_set_initial_device(b, 0, Vd, pr.PR_CONSERVED, stream)
+            ev[1].record(stream)
+            pr.pr_batch_run(b, nf, stream)
+            ev[2].record(stream)
+            pr.pr_batch_moments_device(b, 0, out, stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            if r:
+                lift.append(ev[0].elapsed_time(ev[1]))
+                kin.append(ev[1].elapsed_time(ev[2]))
+                proj.append(ev[2].elapsed_time(ev[3]))
+        pr.pr_batch_sync(b)
+    finally:
+        pr.pr_batch_destroy(b)
+    med = lambda x: sorted(x)[len(x) // 2]
+    return med(lift), med(kin), med(proj)
+
+
+def _parareal_section(pr, np, torch, workload, nx, nv, L, bc, scheme, eps, T, N, U0, Ks, reps=5, reps64=3,
+                      per_iter=False):
+    """Mixed-precision batched parareal (Algorithm 2) against two serial fine
+    chains of the same slices -- plain FP64 and mixed precision -- at matched
+    moment accuracy, with the paper's ideal cost estimate (Sec. 4) evaluated
+    from measured pieces.  Errors: max over slices n >= 1 of the moment error
+    (per conserved component, scaled by its field maximum, the momenta by the
+    thermal momentum) against the FP64 serial chain."""
+    ctx = pr.pr_init(nx, 0.0, 1.0, bc, nv, L, eps, T, N, 0.5, 0.5, scheme, pr.PR_MIXED)
+    try:
+        nf, dtf = pr.pr_fine_steps_per_slice(ctx)
+        inst = pr.instance(nx, nv, dtf, L=L, bc=bc, eps=eps, scheme=scheme)
+        V0 = _cons(np, U0)
+        t64, ref = _serial_chain(pr, np, torch, inst, V0, N, nf, pr.PR_FP64, reps64)
+        t32, ch32 = _serial_chain(pr, np, torch, inst, V0, N, nf, pr.PR_MIXED, reps)
+
+        def err(U):
+            return max(_moment_rel_err(np, U[n], ref[n]) for n in range(1, N + 1))
+
+        def iterates():
+            return np.stack([pr.pr_moments(ctx, n) for n in range(N + 1)])
+
+        e32 = err(ch32)
+        t_init = _median_s(lambda: pr.pr_set_initial(ctx, U0), reps)
+        rows = []
+        if per_iter:
+            pr.pr_set_initial(ctx, U0)
+            acc = t_init
+            for k in range(1, max(Ks) + 1):
+                t0 = time.perf_counter()
+                succ = pr.pr_parareal_iter(ctx)
+                acc += time.perf_counter() - t0
+                if k in Ks:
+                    rows.append({"K": k, "ms": acc * 1e3, "err_vs_fp64_serial": err(iterates()),
+                                 "successive_error": float(succ)})
+        else:
+            for K in Ks:
+                def run():
+                    pr.pr_set_initial(ctx, U0)
+                    return pr.pr_parareal_run(ctx, K)
+
+                t = _median_s(run, reps)
+                _, errs = run()
+                rows.append({"K": K, "ms": t * 1e3, "err_vs_fp64_serial": err(iterates()),
+                             "successive_error": float(errs[-1])})
+        path = pr.pr_get_fine_path(ctx)
+    finally:
+        pr.pr_destroy(ctx)
+    for r in rows:
+        r["speedup_vs_fp64_serial"] = t64 * 1e3 / r["ms"]
+        r["speedup_vs_mixed_serial"] = t32 * 1e3 / r["ms"]
+
+    def first(ok):
+        for r in rows:
+            if ok(r["err_vs_fp64_serial"]):
+                return {k: r[k] for k in ("K", "ms", "err_vs_fp64_serial", "speedup_vs_fp64_serial",
+                                          "speedup_vs_mixed_serial")}
+        return {"reached": False, "K_max": max(Ks)}
+
+    # the paper's ideal estimate T_par = T_Fl + N k ((T_L + T_P + T_Kin + T_Fl)/N_p + T_Fl)
+    tl, tk, tp = _stage_times(pr, torch, inst, V0, nf)
+    tf = t_init * 1e3 / N
+    piece = tl + tp + tk + tf
+    model = {"T_Lift_ms": tl, "T_Kin_ms": tk, "T_Proj_ms": tp, "T_Fluid_ms": tf,
+             "pieces": "T_Lift, T_Kin (n_f fine steps), T_Proj: device times of one slice's lift, fine run "
+                       "and projection (mixed); T_Fluid: the first coarse guess / N",
+             "rows": []}
+    for r in rows:
+        K = r["K"]
+        pred = tf + N * K * (piece / N + tf)
+        rest = r["ms"] - tf - N * K * tf
+        model["rows"].append({"K": K, "predicted_ms_Np_eq_N": pred, "measured_ms": r["ms"],
+                              "effective_Np": N * K * piece / rest if rest > 0 else None})
+    kopt = math.ceil((N * tk - tf) / (N * (piece / N + tf)))
+    model["k_opt_Np_eq_N"] = kopt
+    return {"workload": workload + f", N={N} slices of {nf} fine steps",
+            "fine_path": "cluster" if path == pr.PR_FINE_CLUSTER else "tiled",
+            "serial_fp64_ms": t64 * 1e3, "serial_mixed_ms": t32 * 1e3,
+            "serial_mixed_err_vs_fp64": e32,
+            "precision_gain": t64 / t32,
+            "parareal_mixed": rows,
+            "equal_accuracy": {
+                "at_mixed_serial_accuracy": first(lambda e: e <= e32),
+                "at_1e-5": first(lambda e: e <= 1e-5)},
+            "cost_model_sec4": model,
+            "timing": "wall clock around synchronous calls (median of the repetitions); parareal: the first "
+                      "coarse guess + K iterations; serial: N lift + fine run + projection in a row; all end "
+                      "with the moments in device memory, read back after the clock"}
 
 
 def _ragged_section(pr, torch):
@@ -318,55 +423,74 @@ def _ragged_section(pr, torch):
         pr.pr_batch_destroy(b)
 
 
-def _large_section(pr, np, torch):
-    """Two interacting shocks: Nx = 2048, 48^3 on [-10, 10]^3, thirds profile,
-    reflecting walls, eps = 1e-4, MUSCL, T = 0.05, N = 128 slices (16 fine steps
-    each), K = 6: mixed-precision batched parareal vs the plain FP64
-    single-instance serial fine chain, wall clock, with the error of each
-    parareal iterate against the FP64 chain."""
+def _adjoint_section(pr, np, torch, cpu=True):
+    """The gradient workload: Nx = 256, 24^3 on [-8, 8]^3, periodic, upwind,
+    FP64, eps = 1e-3, rho = 1 + a1 sin 2 pi x + a2 cos 4 pi x (seeded), T = 0.05
+    (197 steps), J = sum (rho(T) - rho_target)^2 dx, checkpoint every 16 steps.
+    Wall clock of the forward run alone and of one gradient (pr_batch_adjoint:
+    its own forward pass storing checkpoints, then per segment a recomputed
+    forward and the reverse sweep), and the oracle's hand adjoint on the host
+    cores on a bounded number of steps."""
     from paper_2502_02704_gb300 import workloads as W
 
-    nx, nv, L, N, T, eps, K = 2048, 48, 10.0, 128, 0.05, 1e-4, 6
-    U0 = W.thirds(nx)
-    ctx = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_REFLECT, nv, L, eps, T, N, 0.5, 0.5, pr.PR_MUSCL, pr.PR_MIXED)
+    nx, nv, L, T, eps, ckpt = 256, 24, 8.0, 0.05, 1e-3, 16
+    n = math.ceil(T / pr.fine_dt(nx, nv, L) * (1 - 1e-9))
+    dt = T / n
+    a1, a2 = W.draw_modes(1)
+    t1, t2 = W.draw_modes(2)
+    U0 = W.density_modes(nx, a1, a2)
+    target = W.density_modes(nx, t1, t2)[0]
+    cells = nx * nv ** 3
+    b = pr.pr_batch_create([pr.instance(nx, nv, dt, L=L, bc=pr.PR_BC_PERIODIC, eps=eps)], pr.PR_FP64)
     try:
-        nf, dtf = pr.pr_fine_steps_per_slice(ctx)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        pr.pr_set_initial(ctx, U0)
-        kd, errs = pr.pr_parareal_run(ctx, K)
-        t_par = time.perf_counter() - t0
-        par = np.stack([pr.pr_moments(ctx, n) for n in range(N + 1)])
+        def fwd():
+            pr.pr_batch_set_initial(b, 0, U0)
+            pr.pr_batch_run(b, n)
+            return pr.pr_batch_moments(b, 0)
+
+        t_fwd = _median_s(fwd, 3)
+        V = fwd()
+        lamV = np.zeros((5, nx))
+        lamV[0] = 2.0 * (V[0] - target) / nx  # dJ/drho(T) of the misfit
+
+        def grad():
+            pr.pr_batch_set_initial(b, 0, U0)
+            return pr.pr_batch_adjoint(b, 0, n, lamV, ckpt)
+
+        t_grad = _median_s(grad, 3)
     finally:
-        pr.pr_destroy(ctx)
-    one = pr.pr_batch_create([pr.instance(nx, nv, dtf, L=L, bc=pr.PR_BC_REFLECT, eps=eps, scheme=pr.PR_MUSCL)],
-                             pr.PR_FP64)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.current_stream(dev)
-    V0 = np.stack([U0[0], U0[0] * U0[1], U0[0] * U0[2], U0[0] * U0[3],
-                   0.5 * U0[0] * (U0[1] ** 2 + U0[2] ** 2 + U0[3] ** 2) + 1.5 * U0[0] * U0[4]])
-    chain = torch.zeros((N + 1, 5, nx), dtype=torch.float64, device=dev)
-    chain[0] = torch.tensor(V0, device=dev)
-    try:
-        torch.cuda.synchronize()
+        pr.pr_batch_destroy(b)
+    # algorithmic bytes per cell and step of one gradient: the forward pass
+    # (read f, write f*: 16), the recomputed forward (16), and the reverse
+    # step (read lambda^{n+1} and the step's stored f*, write lambda^n: 24)
+    alg = 56.0 * cells * n
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    ach = alg / t_grad / 1e9
+    out = {"workload": f"gradient: Nx={nx}, {nv}^3, periodic, upwind, FP64, eps=1e-3, T=0.05 ({n} steps), "
+                       f"checkpoint {ckpt}, J = sum (rho(T) - rho_target)^2 dx",
+           "forward_ms": t_fwd * 1e3, "gradient_ms": t_grad * 1e3, "gradient_over_forward": t_grad / t_fwd,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "algorithmic_bytes_per_cell_step": 56,
+                        "bytes": "forward 16 + recomputed forward 16 + reverse step 24 (lambda in, stored f* in, "
+                                 "lambda out) per cell and step, float64",
+                        "peak_source": "measured" if peaks else "fallback"},
+           "timing": "wall clock around the synchronous calls, median of 3"}
+    if cpu:
+        import oracle as O
+
+        cores = os.cpu_count() or 1
+        O.set_threads(cores)
+        k = O.Kin(nx=nx, nv=nv, L=L, bc=O.BC_PERIODIC, eps=eps, scheme=O.UPWIND)
+        ns = 8
         t0 = time.perf_counter()
-        for n in range(1, N + 1):
-            pr.pr_batch_set_initial_device(one, 0, chain[n - 1], pr.PR_CONSERVED, stream)
-            pr.pr_batch_run(one, nf, stream)
-            pr.pr_batch_moments_device(one, 0, chain[n], stream)
-        torch.cuda.synchronize()
-        pr.pr_batch_sync(one)
-        t_ser = time.perf_counter() - t0
-    finally:
-        pr.pr_batch_destroy(one)
-    ref = chain.cpu().numpy()
-    err = float(np.max(np.abs(par - ref)) / np.max(np.abs(ref)))
-    return {"workload": "two shocks, Nx=2048, 48^3 on [-10,10]^3, reflecting, eps=1e-4, MUSCL, T=0.05, "
-                        "N=128 (16 fine steps/slice), K=6",
-            "parareal_mixed_s": t_par, "serial_fp64_s": t_ser, "speedup": t_ser / t_par,
-            "successive_errors": [float(e) for e in errs], "max_rel_err_vs_fp64_serial": err,
-            "timing": "wall clock; parareal: the first coarse guess + K iterations, serial: the N fine runs; "
-                      "both end with the moments in device memory, read back after the clock"}
+        O.adjoint(k, dt, ns, U0, lamV)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": el / ns * 1e3, "unit": "ms per step of the gradient", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"oracle forward + hand adjoint over {ns} steps in {el:.1f} s"}
+        out["gpu_ms_per_step_of_the_gradient"] = t_grad * 1e3 / n
+    return out
 
 
 def _moment_rel_err(np, V, Vref):
@@ -624,32 +748,50 @@ def run_ours(args):
             traffic = tj["dram_bytes_per_launch"]
     except Exception:
         traffic = None
-    # plain FP64: bound by the FP64 pipe on GB300 (measured DFMA rate); FP64
-    # flops per cell-update from the committed ncu counter summary
-    fp64_peak_tflops = 1.01
+    # plain FP64: bound by the FP64 pipe on GB300.  Peak: the library's DFMA
+    # probe on this device (pr_probe_fp64_peak).  Achieved: algorithmic FP64
+    # flops of the MUSCL step, FP64_ALG_FLOPS per cell-update (reconstruction
+    # a g + (T0 T1) T2: 3; MUSCL transport: one new difference, the half-slope
+    # FMA, the flux difference and its FMA: 6; the five moment accumulations
+    # s0 += f, t1 += q f, t2 += q^2 f: 5); the executed count from the
+    # committed ncu summary is reported beside it while the source matches.
+    fp64_peak_tflops = None
+    try:
+        fp64_peak_tflops = pr.pr_probe_fp64_peak()
+    except Exception:
+        fp64_peak_tflops = None
     value64 = upd / (ms64 * 1e-3)
-    fp64_alu = None
+    ach_alg = FP64_ALG_FLOPS * upd / (kms64 * 1e-3) / 1e12
+    fp64_alu = {"bound": "alu", "achieved": ach_alg, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": ach_alg / fp64_peak_tflops if fp64_peak_tflops else None,
+                "flops_per_cell_update": FP64_ALG_FLOPS, "flops_kind": "algorithmic (counted from the scheme)",
+                "peak_source": "measured in this run: DFMA chains on every SM (pr_probe_fp64_peak)"}
     try:
         fj = json.load(open(os.path.join(ROOT, "profiles", "fine_run_fp64_flops.txt")))
         if fj.get("fine_cu_sha256_16") == _src_hash(FINE_SRC):
-            ach = fj["fp64_flops_per_cell_update"] * upd / (kms64 * 1e-3) / 1e12
-            fp64_alu = {"bound": "alu", "achieved": ach, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                        "frac": ach / fp64_peak_tflops, "flops_per_cell_update": fj["fp64_flops_per_cell_update"],
-                        "peak_source": "measured DFMA microbenchmark on this pool's GB300"}
+            ex = fj["fp64_flops_per_cell_update"]
+            fp64_alu["executed"] = {"flops_per_cell_update": ex, "source": "ncu DADD + DMUL + 2 DFMA",
+                                    "achieved": ex * upd / (kms64 * 1e-3) / 1e12}
     except Exception:
-        fp64_alu = None
+        pass
     cpu = None
     if not args.no_cpu_baseline:
         rate, cores, sample = _cpu_sample()
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "single_core": _cpu_single_core()}
+    from paper_2502_02704_gb300 import workloads as W2
+
     para = para64 = None
-    try:
-        para = _parareal_speedup(pr, np)
+    try:  # configs: Sod tube, N = 8 (the small parareal problem)
+        para = _parareal_section(pr, np, torch, "Sod Nx=64, 16^3 on [-8,8]^3, eps=1e-2, outflow, upwind, T=0.1",
+                                 64, 16, 8.0, pr.PR_BC_OUTFLOW, pr.PR_UPWIND, 1e-2, 0.1, 8, W2.sod(64),
+                                 Ks=(1, 2, 3, 4, 5, 6, 7, 8))
     except Exception as e:  # reported, not hidden
         para = {"error": repr(e)}
     try:  # the batched parareal configuration: 64 slices resident in one persistent launch
-        para64 = _parareal_speedup(pr, np, nx=256, nv=24, N=64, T=0.1, Ks=(1, 2, 3, 4, 5))
+        para64 = _parareal_section(pr, np, torch, "Sod Nx=256, 24^3 on [-8,8]^3, eps=1e-2, outflow, upwind, T=0.1",
+                                   256, 24, 8.0, pr.PR_BC_OUTFLOW, pr.PR_UPWIND, 1e-2, 0.1, 64, W2.sod(256),
+                                   Ks=(1, 2, 3, 4, 5, 64), reps=3)
     except Exception as e:
         para64 = {"error": repr(e)}
     ragged = large = test3 = higher = None
@@ -666,9 +808,17 @@ def run_ours(args):
         higher = _coarse_models_section(pr, np, torch)
     except Exception as e:
         higher = {"error": repr(e)}
+    adjoint = None
+    try:
+        adjoint = _adjoint_section(pr, np, torch, cpu=not args.no_cpu_baseline)
+    except Exception as e:
+        adjoint = {"error": repr(e)}
     if not args.no_large:
-        try:
-            large = _large_section(pr, np, torch)
+        try:  # two interacting shocks, 128 slices resident, K <= 6
+            large = _parareal_section(pr, np, torch, "two shocks, Nx=2048, 48^3 on [-10,10]^3, reflecting, "
+                                      "eps=1e-4, MUSCL, T=0.05", 2048, 48, 10.0, pr.PR_BC_REFLECT, pr.PR_MUSCL,
+                                      1e-4, 0.05, 128, W2.thirds(2048), Ks=(1, 2, 3, 4, 5, 6), reps=1, reps64=1,
+                                      per_iter=True)
         except Exception as e:
             large = {"error": repr(e)}
     line = {
@@ -686,16 +836,14 @@ def run_ours(args):
                 "h2d_bytes_per_step": len(EPSS) * 5 * NX * 8, "d2h_bytes_per_step": len(EPSS) * 5 * NX * 8},
         "gpu_launches": launches,
         "clocks": clocks,
-        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "kernel_ms": kms64,
-                 "roofline": fp64_alu or {"bound": "alu", "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                                          "achieved": None, "frac": None,
-                                          "peak_source": "measured DFMA microbenchmark on this pool's GB300"}},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64, "kernel_ms": kms64, "roofline": fp64_alu},
         "parareal": para,
         "parareal_batched_n64": para64,
         "ragged_batch": ragged,
         "parareal_large": large,
         "test3_force": test3,
         "coarse_models": higher,
+        "adjoint": adjoint,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

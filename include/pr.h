@@ -296,6 +296,14 @@ int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int checkpoint, const doubl
  * cfl not finite and > 0). */
 int pr_fine_dt_stab(const pr_instance* inst, double cfl, double* dt);
 
+/* Measured FP64 fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per DFMA): independent DFMA chains on every SM, best of
+ * five launches timed with CUDA events after a warm-up.  Not in the paper:
+ * the denominator of the plain-FP64 fine step's roofline, which this part's
+ * FP64 pipe bounds.  Allocates and frees 8 bytes and a stream; synchronous.
+ * Errors: PR_EINVAL (null out), PR_ECUDA. */
+int pr_probe_fp64_peak(double* tflops);
+
 /* Number of kernels the library launched since the last reset (any object). */
 long long pr_kernel_launches(int reset);
 

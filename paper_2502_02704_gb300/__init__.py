@@ -110,6 +110,7 @@ _SIGS = {
     "pr_batch_adjoint": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
     "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
     "pr_fine_dt_stab": (C.c_int, [C.POINTER(pr_instance), C.c_double, _D]),
+    "pr_probe_fp64_peak": (C.c_int, [_D]),
     "pr_force_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_force_instance), C.c_int, C.c_int, C.c_int]),
     "pr_force_destroy": (C.c_int, [_VP]),
     "pr_force_last_error": (C.c_char_p, [_VP]),
@@ -427,6 +428,15 @@ def pr_fine_dt_stab(inst, cfl=0.5) -> float:
     rc = lib().pr_fine_dt_stab(C.byref(inst), float(cfl), C.byref(out))
     if rc != PR_OK:
         raise PrError(rc, "pr_fine_dt_stab: invalid grid or cfl")
+    return out.value
+
+
+def pr_probe_fp64_peak() -> float:
+    """Measured FP64 FMA throughput of the current device, TFLOP/s."""
+    out = C.c_double()
+    rc = lib().pr_probe_fp64_peak(C.byref(out))
+    if rc != PR_OK:
+        raise PrError(rc, "pr_probe_fp64_peak failed")
     return out.value
 
 

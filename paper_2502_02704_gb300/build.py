@@ -25,6 +25,7 @@ UNITS = {
     "force.cu": [],
     "force_runtime.cu": [],
     "lift_ce.cu": [],
+    "probe.cu": [],
 }
 
 
