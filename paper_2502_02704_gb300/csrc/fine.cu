@@ -113,10 +113,11 @@ __device__ __forceinline__ T minmod(T a, T b)
 }
 
 // minmod without branches: the argument of smaller magnitude when both have
-// the same sign, else 0 (max(0, min(a,b)) + min(0, max(a,b))).
+// the same sign, else 0 -- b clamped to the interval between 0 and a (four
+// min/max operations, no addition).
 __device__ __forceinline__ float minmod2(float a, float b)
 {
-    return fmaxf(0.f, fminf(a, b)) + fminf(0.f, fmaxf(a, b));
+    return fminf(fmaxf(b, fminf(a, 0.f)), fmaxf(a, 0.f));
 }
 // float64: the same selection on the IEEE bit patterns with integer
 // operations only (sign bits equal -> the smaller magnitude, else 0), which
