@@ -33,27 +33,6 @@ __device__ __forceinline__ void node(const Inst& I, int v, double& vx, double& v
     vz = -I.L + (jz + 0.5) * I.dv;
 }
 
-template <int NV>
-__device__ void block_sum(double (&x)[NV], double* sh)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-#pragma unroll
-        for (int o = 16; o; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) sh[warp * NV + q] = x[q];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double t = 0.0;
-        for (int w = 0; w < AT / 32; ++w) t += sh[w * NV + q];
-        x[q] = t;
-    }
-}
-
 // seed: lam[c][v] = dv^3 (l0 + l1 vx + l2 vy + l3 vz + l4 |v|^2/2), l = dJ/dV(T)[.][c]
 __global__ void k_adj_seed(Inst I, const double* lamV, double* lam)
 {
@@ -66,132 +45,244 @@ __global__ void k_adj_seed(Inst I, const double* lamV, double* lam)
                                          lamV[4 * nx + c] * 0.5 * (vx * vx + vy * vy + vz * vz));
 }
 
-// conserved moments of g (stride ldv) per x cell: m[5][nx]
-__global__ void __launch_bounds__(AT) k_adj_moments(Inst I, const double* g, double* m)
+// Per x cell c, one CTA: the conserved moments m(g) of the transported
+// state g (the step's f*), the Maxwellian of m(g) in its separable form
+// M = rho (2 pi theta)^{-3/2} e_x[jx] e_y[jy] e_z[jz] (1-D factors in shared
+// memory, 3 nv exponentials per cell instead of nv^3), then the sums A_rho,
+// A_u, A_theta and the log-eps term, folded into the five coefficients of the
+// BGK part of lam_g.  Threads own (jy, jz) pairs of the velocity plane and
+// walk jx, so node indices come without divisions and each jx plane is read
+// coalesced.
+constexpr int ACT = 512;
+
+template <int NV>
+__device__ void block_sum_n(double (&x)[NV], double* sh)
 {
-    __shared__ double sh[(AT / 32) * 5];
-    const int c = blockIdx.x;
-    double s[5] = {0, 0, 0, 0, 0};
-    for (int v = threadIdx.x; v < I.nv3; v += AT) {
-        double vx, vy, vz;
-        node(I, v, vx, vy, vz);
-        double f = g[(size_t)c * I.ldv + v];
-        s[0] += f;
-        s[1] += vx * f;
-        s[2] += vy * f;
-        s[3] += vz * f;
-        s[4] += 0.5 * (vx * vx + vy * vy + vz * vz) * f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sh[warp * NV + q] = x[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh[w * NV + q];
+        x[q] = t;
     }
-    block_sum<5>(s, sh);
-    if (threadIdx.x < 5) m[(size_t)threadIdx.x * I.nx + c] = s[threadIdx.x] * I.dv3;
+    __syncthreads();
 }
 
-// per x cell: coefficients of the BGK part of lam_g and the log-eps term
-__global__ void __launch_bounds__(AT) k_adj_coef(Inst I, const double* lam, const double* g, const double* m,
-                                                double* coef, double* eps_acc)
+// 1-D Maxwellian factors of (u, theta) into e[3][nv] (e[0] carries pref).
+__device__ void maxwell_factors(const Inst& I, double ux, double uy, double uz, double th, double pref, double* e)
 {
-    __shared__ double sh[(AT / 32) * 6];
-    const int c = blockIdx.x, nx = I.nx;
-    const double rho = m[c], ux = m[nx + c] / rho, uy = m[2 * nx + c] / rho, uz = m[3 * nx + c] / rho;
-    const double th = (2.0 * m[4 * nx + c] / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
-    const double tp = 2.0 * PI * th, pref = rho / (tp * sqrt(tp));
-    double s[6] = {0, 0, 0, 0, 0, 0};  // A_rho, A_u (3), A_theta, eps term
-    for (int v = threadIdx.x; v < I.nv3; v += AT) {
-        double vx, vy, vz;
-        node(I, v, vx, vy, vz);
-        double cx = vx - ux, cy = vy - uy, cz = vz - uz, c2 = cx * cx + cy * cy + cz * cz;
-        double M = pref * exp(-c2 / (2.0 * th));
-        double l = lam[(size_t)c * I.nv3 + v], lM = l * M;
-        s[0] += lM / rho;
-        s[1] += lM * cx / th;
-        s[2] += lM * cy / th;
-        s[3] += lM * cz / th;
-        s[4] += lM * (c2 / (2.0 * th * th) - 1.5 / th);
-        s[5] += l * (g[(size_t)c * I.ldv + v] - M);
+    const int nv = I.nv;
+    const double i2t = 0.5 / th;
+    for (int k = threadIdx.x; k < 3 * nv; k += blockDim.x) {
+        const int d = k / nv, j = k - d * nv;
+        const double c = -I.L + (j + 0.5) * I.dv - (d == 0 ? ux : d == 1 ? uy : uz);
+        const double x = exp(-c * c * i2t);
+        e[k] = d == 0 ? pref * x : x;
     }
-    block_sum<6>(s, sh);
+}
+
+__global__ void __launch_bounds__(ACT) k_adj_coef(Inst I, const double* lam, const double* g, double* coef,
+                                                 double* eps_acc)
+{
+    extern __shared__ double ash[];  // e[3][nv], tx[2][nv], then the block-sum scratch
+    const int c = blockIdx.x, nv = I.nv, np = nv * nv;
+    double* e = ash;
+    double* tx = ash + 3 * nv;  // v_x, then v_x - u_x
+    double* sh = ash + 5 * nv;
+    const double* gc = g + (size_t)c * I.ldv;
+    const double* lc = lam + (size_t)c * I.nv3;
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) tx[j] = -I.L + (j + 0.5) * I.dv;
+    __syncthreads();
+    // moments of g (sums over the plane, then over jx)
+    double m[5] = {0, 0, 0, 0, 0};
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const int jy = p / nv, jz = p - jy * nv;
+        const double vy = -I.L + (jy + 0.5) * I.dv, vz = -I.L + (jz + 0.5) * I.dv;
+        double s0 = 0, sx = 0, sxx = 0;
+        for (int jx = 0; jx < nv; ++jx) {
+            const double vx = tx[jx], f = gc[(size_t)jx * np + p];
+            s0 += f;
+            sx += vx * f;
+            sxx += vx * vx * f;
+        }
+        m[0] += s0;
+        m[1] += sx;
+        m[2] += vy * s0;
+        m[3] += vz * s0;
+        m[4] += sxx + (vy * vy + vz * vz) * s0;
+    }
+    block_sum_n<5>(m, sh);
+    const double rho = m[0] * I.dv3, ir = 1.0 / rho;
+    const double u[3] = {m[1] * I.dv3 * ir, m[2] * I.dv3 * ir, m[3] * I.dv3 * ir};
+    const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const double th = (m[4] * I.dv3 * ir - u2) / 3.0, ith = 1.0 / th;
+    const double tp = 2.0 * PI * th, pref = rho / (tp * sqrt(tp));
+    maxwell_factors(I, u[0], u[1], u[2], th, pref, e);
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) tx[nv + j] = tx[j] - u[0];
+    __syncthreads();
+    double s[6] = {0, 0, 0, 0, 0, 0};  // A_rho, A_u (3), A_theta, eps term
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const int jy = p / nv, jz = p - jy * nv;
+        const double cy = -I.L + (jy + 0.5) * I.dv - u[1], cz = -I.L + (jz + 0.5) * I.dv - u[2];
+        const double eyz = e[nv + jy] * e[2 * nv + jz], cyz2 = cy * cy + cz * cz;
+        double a0 = 0, ax = 0, axx = 0, ae = 0;
+        for (int jx = 0; jx < nv; ++jx) {
+            const double cx = tx[nv + jx];
+            const double M = e[jx] * eyz, l = lc[(size_t)jx * np + p], lM = l * M;
+            a0 += lM;
+            ax += lM * cx;
+            axx += lM * cx * cx;
+            ae += l * (gc[(size_t)jx * np + p] - M);
+        }
+        s[0] += a0;
+        s[1] += ax;
+        s[2] += a0 * cy;
+        s[3] += a0 * cz;
+        s[4] += axx + a0 * cyz2;  // sum lM |v - u|^2
+        s[5] += ae;
+    }
+    block_sum_n<6>(s, sh);
     if (threadIdx.x == 0) {
-        const double Ar = s[0], Ax = s[1], Ay = s[2], Az = s[3], At = s[4];
-        const double u2 = ux * ux + uy * uy + uz * uz, k3 = 1.0 / (3.0 * rho), w = I.b * I.dv3;
-        coef[c * 5 + 0] = w * (Ar - (Ax * ux + Ay * uy + Az * uz) / rho + At * (u2 - 3.0 * th) * k3);
-        coef[c * 5 + 1] = w * (Ax / rho - 2.0 * At * ux * k3);
-        coef[c * 5 + 2] = w * (Ay / rho - 2.0 * At * uy * k3);
-        coef[c * 5 + 3] = w * (Az / rho - 2.0 * At * uz * k3);
+        // A_rho = sum lM / rho, A_u = sum lM c / theta, A_theta = sum lM (|c|^2/(2 theta^2) - 3/(2 theta))
+        const double Ar = s[0] * ir, Ax = s[1] * ith, Ay = s[2] * ith, Az = s[3] * ith;
+        const double At = 0.5 * s[4] * ith * ith - 1.5 * s[0] * ith;
+        const double k3 = 1.0 / (3.0 * rho), w = I.b * I.dv3;
+        coef[c * 5 + 0] = w * (Ar - (Ax * u[0] + Ay * u[1] + Az * u[2]) * ir + At * (u2 - 3.0 * th) * k3);
+        coef[c * 5 + 1] = w * (Ax * ir - 2.0 * At * u[0] * k3);
+        coef[c * 5 + 2] = w * (Ay * ir - 2.0 * At * u[1] * k3);
+        coef[c * 5 + 3] = w * (Az * ir - 2.0 * At * u[2] * k3);
         coef[c * 5 + 4] = w * At * k3;
         eps_acc[c] += I.a * I.b * s[5];
     }
 }
 
-__device__ __forceinline__ double lam_g(const Inst& I, const double* lam, const double* coef, int c, int v, double vx,
-                                        double vy, double vz)
-{
-    const double* k = coef + c * 5;
-    return I.a * lam[(size_t)c * I.nv3 + v] + k[0] + k[1] * vx + k[2] * vy + k[3] * vz +
-           k[4] * (vx * vx + vy * vy + vz * vz);
-}
+// lam_out = T^T lam_g for the upwind transport (periodic or outflow ghosts),
+// lam_g = a lam + P_c(v), P_c(v) = k0 + k1 v_x + k2 v_y + k3 v_z + k4 |v|^2
+// with cell c's coefficients.  For v_x > 0 the step reads
+// g_i = (1 - cr) f_i + cr f_{i-1}, so lam_i = (1 - cr) lam_g,i + cr lam_g,i+1;
+// for v_x < 0, g_i = (1 + cr) f_i - cr f_{i+1}, so lam_i = (1 + cr) lam_g,i -
+// cr lam_g,i-1 (cr = v_x dt/dx with sign); an outflow ghost copies the end
+// cell, which adds its weight to the end cell itself.  One CTA per (cell,
+// part of the (v_y, v_z) plane); each thread walks v_x.  The per-v_x weights
+// and the v_x parts of P for the cell and for its upwind neighbour come from
+// shared-memory tables.
+constexpr int APT = 256;
 
-// lam_out = T^T lam_g for the upwind transport (periodic or outflow ghosts)
-__global__ void k_adj_apply(Inst I, const double* lam, const double* coef, double* out)
+__global__ void __launch_bounds__(APT) k_adj_apply(Inst I, const double* lam, const double* coef, double* out)
 {
-    const int c = blockIdx.x, v = blockIdx.y * AT + threadIdx.x;
-    if (v >= I.nv3) return;
-    double vx, vy, vz;
-    node(I, v, vx, vy, vz);
-    const int nx = I.nx;
-    const double cr = I.nu * vx;  // Courant number with sign
-    double r;
-    if (vx > 0.0) {
-        // g_i = (1 - cr) f_i + cr f_{i-1}
-        int up = c + 1;
-        bool has_up = true;
-        if (up >= nx) {
-            if (I.bc == 0) up -= nx;
-            else has_up = false;
-        }
-        double self = (1.0 - cr);
-        if (I.bc == 1 && c == 0) self += cr;  // outflow ghost f_{-1} = f_0
-        r = self * lam_g(I, lam, coef, c, v, vx, vy, vz);
-        if (has_up) r += cr * lam_g(I, lam, coef, up, v, vx, vy, vz);
-    } else if (vx < 0.0) {
-        // g_i = (1 + cr) f_i - cr f_{i+1}
-        int dn = c - 1;
-        bool has_dn = true;
-        if (dn < 0) {
-            if (I.bc == 0) dn += nx;
-            else has_dn = false;
-        }
-        double self = (1.0 + cr);
-        if (I.bc == 1 && c == nx - 1) self -= cr;  // outflow ghost f_{nx} = f_{nx-1}
-        r = self * lam_g(I, lam, coef, c, v, vx, vy, vz);
-        if (has_dn) r -= cr * lam_g(I, lam, coef, dn, v, vx, vy, vz);
-    } else {
-        r = lam_g(I, lam, coef, c, v, vx, vy, vz);
+    extern __shared__ double ap[];  // [nv] each: self weight, neighbour weight, P_x of c, P_x of the neighbour
+    const int c = blockIdx.x, nx = I.nx, nv = I.nv, np = nv * nv;
+    double* ws = ap;
+    double* wn = ap + nv;
+    double* pc = ap + 2 * nv;
+    double* pn = ap + 3 * nv;
+    int up = c + 1, dn = c - 1;
+    bool has_up = true, has_dn = true;
+    if (up >= nx) {
+        if (I.bc == 0) up -= nx;
+        else has_up = false;
     }
-    out[(size_t)c * I.nv3 + v] = r;
+    if (dn < 0) {
+        if (I.bc == 0) dn += nx;
+        else has_dn = false;
+    }
+    const double* kc = coef + c * 5;
+    const double* ku = coef + (has_up ? up : c) * 5;
+    const double* kd = coef + (has_dn ? dn : c) * 5;
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+        const double vx = -I.L + (j + 0.5) * I.dv, cr = I.nu * vx;
+        pc[j] = vx * (kc[1] + kc[4] * vx);
+        if (vx > 0.0) {
+            double self = 1.0 - cr;
+            if (I.bc == 1 && c == 0) self += cr;  // outflow ghost f_{-1} = f_0
+            ws[j] = self;
+            wn[j] = has_up ? cr : 0.0;
+            pn[j] = vx * (ku[1] + ku[4] * vx);
+        } else if (vx < 0.0) {
+            double self = 1.0 + cr;
+            if (I.bc == 1 && c == nx - 1) self -= cr;  // outflow ghost f_{nx} = f_{nx-1}
+            ws[j] = self;
+            wn[j] = has_dn ? -cr : 0.0;
+            pn[j] = vx * (kd[1] + kd[4] * vx);
+        } else {
+            ws[j] = 1.0;
+            wn[j] = 0.0;
+            pn[j] = 0.0;
+        }
+    }
+    __syncthreads();
+    const int p = blockIdx.y * APT + threadIdx.x;
+    if (p >= np) return;
+    const int jy = p / nv, jz = p - jy * nv;
+    const double vy = -I.L + (jy + 0.5) * I.dv, vz = -I.L + (jz + 0.5) * I.dv, vyz2 = vy * vy + vz * vz;
+    const double bc_ = kc[0] + kc[2] * vy + kc[3] * vz + kc[4] * vyz2;
+    const double bu = ku[0] + ku[2] * vy + ku[3] * vz + ku[4] * vyz2;
+    const double bd = kd[0] + kd[2] * vy + kd[3] * vz + kd[4] * vyz2;
+    const double a = I.a;
+    const double* lc = lam + (size_t)c * I.nv3 + p;
+    const double* lu = lam + (size_t)(has_up ? up : c) * I.nv3 + p;
+    const double* ld = lam + (size_t)(has_dn ? dn : c) * I.nv3 + p;
+    double* o = out + (size_t)c * I.nv3 + p;
+    const int half = nv / 2;  // v_x < 0 for jx < nv/2 (cube centres, even nv)
+    for (int jx = 0; jx < nv; ++jx) {
+        const size_t k = (size_t)jx * np;
+        const double gself = a * lc[k] + bc_ + pc[jx];
+        const double gn = jx < half ? a * ld[k] + bd + pn[jx] : a * lu[k] + bu + pn[jx];
+        o[k] = ws[jx] * gself + wn[jx] * gn;
+    }
 }
 
-// dJ/dU0[q][c] = sum_v lam^0 dM/dU_q with U = (rho, u, theta) from the conserved Uin
-__global__ void __launch_bounds__(AT) k_adj_lift(Inst I, const double* lam, const double* Uin, double* dU0)
+// dJ/dU0[q][c] = sum_v lam^0 dM/dU_q with U = (rho, u, theta) from the
+// conserved Uin (the separable Maxwellian, as in k_adj_coef)
+__global__ void __launch_bounds__(ACT) k_adj_lift(Inst I, const double* lam, const double* Uin, double* dU0)
 {
-    __shared__ double sh[(AT / 32) * 5];
-    const int c = blockIdx.x, nx = I.nx;
-    const double rho = Uin[c], ux = Uin[nx + c] / rho, uy = Uin[2 * nx + c] / rho, uz = Uin[3 * nx + c] / rho;
-    const double th = (2.0 * Uin[4 * nx + c] / rho - (ux * ux + uy * uy + uz * uz)) / 3.0;
+    extern __shared__ double ash[];
+    const int c = blockIdx.x, nx = I.nx, nv = I.nv, np = nv * nv;
+    double* e = ash;
+    double* sh = ash + 3 * nv;
+    const double rho = Uin[c], ir = 1.0 / rho;
+    const double u[3] = {Uin[nx + c] * ir, Uin[2 * nx + c] * ir, Uin[3 * nx + c] * ir};
+    const double th = (2.0 * Uin[4 * nx + c] * ir - (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])) / 3.0, ith = 1.0 / th;
     const double tp = 2.0 * PI * th, pref = rho / (tp * sqrt(tp));
+    maxwell_factors(I, u[0], u[1], u[2], th, pref, e);
+    __syncthreads();
+    const double* lc = lam + (size_t)c * I.nv3;
     double s[5] = {0, 0, 0, 0, 0};
-    for (int v = threadIdx.x; v < I.nv3; v += AT) {
-        double vx, vy, vz;
-        node(I, v, vx, vy, vz);
-        double cx = vx - ux, cy = vy - uy, cz = vz - uz, c2 = cx * cx + cy * cy + cz * cz;
-        double lM = lam[(size_t)c * I.nv3 + v] * pref * exp(-c2 / (2.0 * th));
-        s[0] += lM / rho;
-        s[1] += lM * cx / th;
-        s[2] += lM * cy / th;
-        s[3] += lM * cz / th;
-        s[4] += lM * (c2 / (2.0 * th * th) - 1.5 / th);
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const int jy = p / nv, jz = p - jy * nv;
+        const double cy = -I.L + (jy + 0.5) * I.dv - u[1], cz = -I.L + (jz + 0.5) * I.dv - u[2];
+        const double eyz = e[nv + jy] * e[2 * nv + jz], cyz2 = cy * cy + cz * cz;
+        double a0 = 0, ax = 0, axx = 0;
+        for (int jx = 0; jx < nv; ++jx) {
+            const double cx = -I.L + (jx + 0.5) * I.dv - u[0];
+            const double lM = lc[(size_t)jx * np + p] * e[jx] * eyz;
+            a0 += lM;
+            ax += lM * cx;
+            axx += lM * cx * cx;
+        }
+        s[0] += a0;
+        s[1] += ax;
+        s[2] += a0 * cy;
+        s[3] += a0 * cz;
+        s[4] += axx + a0 * cyz2;
     }
-    block_sum<5>(s, sh);
-    if (threadIdx.x < 5) dU0[(size_t)threadIdx.x * nx + c] = s[threadIdx.x];
+    block_sum_n<5>(s, sh);
+    if (threadIdx.x == 0) {
+        dU0[c] = s[0] * ir;
+        dU0[(size_t)nx + c] = s[1] * ith;
+        dU0[(size_t)2 * nx + c] = s[2] * ith;
+        dU0[(size_t)3 * nx + c] = s[3] * ith;
+        dU0[(size_t)4 * nx + c] = 0.5 * s[4] * ith * ith - 1.5 * s[0] * ith;
+    }
 }
 
 // copy the float64 stored state g[cur] of instance b into dst [nx][ldv]
@@ -212,23 +303,20 @@ cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t adj_moments(const Inst& I, const double* g, double* m, cudaStream_t s)
-{
-    k_adj_moments<<<I.nx, AT, 0, s>>>(I, g, m);
-    return cudaGetLastError();
-}
+static size_t adj_smem(const Inst& I) { return (5 * (size_t)I.nv + (ACT / 32) * 6) * sizeof(double); }
 
-cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const double* m, double* coef,
-                     double* eps_acc, double* lam_out, cudaStream_t s)
+cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, double* coef, double* eps_acc,
+                     double* lam_out, cudaStream_t s)
 {
-    k_adj_coef<<<I.nx, AT, 0, s>>>(I, lam_in, g, m, coef, eps_acc);
-    k_adj_apply<<<dim3(I.nx, (I.nv3 + AT - 1) / AT), AT, 0, s>>>(I, lam_in, coef, lam_out);
+    k_adj_coef<<<I.nx, ACT, adj_smem(I), s>>>(I, lam_in, g, coef, eps_acc);
+    k_adj_apply<<<dim3(I.nx, (I.nv * I.nv + APT - 1) / APT), APT, 4 * (size_t)I.nv * sizeof(double), s>>>(
+        I, lam_in, coef, lam_out);
     return cudaGetLastError();
 }
 
 cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double* dU0, cudaStream_t s)
 {
-    k_adj_lift<<<I.nx, AT, 0, s>>>(I, lam, Uin, dU0);
+    k_adj_lift<<<I.nx, ACT, adj_smem(I), s>>>(I, lam, Uin, dU0);
     return cudaGetLastError();
 }
 

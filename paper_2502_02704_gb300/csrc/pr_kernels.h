@@ -97,9 +97,10 @@ cudaError_t launch_set_f(int precision, const Inst* insts, InstState* st, int b,
 
 // ---- adjoint of the float64 upwind fine run (adjoint.cu) ----
 cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_t s);
-cudaError_t adj_moments(const Inst& I, const double* g, double* m, cudaStream_t s);
-cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const double* m, double* coef,
-                     double* eps_acc, double* lam_out, cudaStream_t s);
+// One reverse step: lam_out = T^T (a lam_in + b dv^3 (c0 + c.v + c4 |v|^2)),
+// the coefficients from the moments of the step's transported state g.
+cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, double* coef, double* eps_acc,
+                     double* lam_out, cudaStream_t s);
 cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double* dU0, cudaStream_t s);
 cudaError_t adj_copy_state(const Inst* insts, const InstState* st, int b, double* dst, cudaStream_t s);
 

@@ -768,40 +768,43 @@ extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const 
     const size_t st = (size_t)I.nx * I.ldv, sv = (size_t)I.nx * I.nv3, m5 = (size_t)5 * I.nx;
     const int nck = nsteps > 0 ? (nsteps + ckpt - 1) / ckpt : 0;
     const int seg = std::min(ckpt, std::max(nsteps, 1));
-    // work: checkpoints, segment states and moments, two adjoint buffers, small vectors
-    size_t need = ((size_t)nck * sv + (size_t)seg * st + (size_t)seg * m5 + 2 * sv + 5 * I.nx + I.nx + 2 * m5) * sizeof(double);
+    // work: checkpoints, segment states, two adjoint buffers, small vectors
+    size_t need = ((size_t)nck * sv + (size_t)seg * st + 2 * sv + 5 * I.nx + I.nx + 2 * m5) * sizeof(double);
     double* w = nullptr;
     if (cudaMalloc(&w, need) != cudaSuccess) return bfail(b, PR_ENOMEM, "adjoint work buffers (%zu bytes)", need);
     double* ck = w;
     double* sg = ck + (size_t)nck * sv;
-    double* sm = sg + (size_t)seg * st;
-    double* la = sm + (size_t)seg * m5;
+    double* la = sg + (size_t)seg * st;
     double* lb = la + sv;
     double* coef = lb + sv;
     double* eps = coef + 5 * I.nx;
     double* dv = eps + I.nx;   // lamV on the device
     double* du = dv + m5;      // dU0 on the device
     int rc = PR_OK;
-    auto run1 = [&]() -> int {
+    // one fine step of instance i alone (a batch of one needs no change of
+    // the active range)
+    const bool solo = b->n == 1;
+    auto runk = [&](int k) -> int {
+        if (solo) return enqueue_run(b, k, 0, s, false);
         prk::Active a{i, i + 1};
         BCUDA(b, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
-        int r = enqueue_run(b, 1, 0, s, false);
+        int r = enqueue_run(b, k, 0, s, false);
         prk::Active all{0, b->n};
         BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
         return r;
     };
+    auto run1 = [&]() -> int { return runk(1); };
     do {
-        // forward from the lifted state, storing f every ckpt steps
+        // forward from the lifted state, storing f every ckpt steps: one
+        // persistent launch per segment (the same bits as single steps)
         if ((rc = lift_instances(b, i, i + 1, s))) break;
-        for (int t = 0; t < nsteps && !rc; ++t) {
-            if (t % ckpt == 0) {
-                if (prk::launch_materialize(0, b->d_inst, b->d_state, i, I, ck + (size_t)(t / ckpt) * sv, s) != cudaSuccess) {
-                    rc = bfail(b, PR_ECUDA, "checkpoint");
-                    break;
-                }
-                g_launches += 1;
+        for (int t = 0; t < nsteps && !rc; t += ckpt) {
+            if (prk::launch_materialize(0, b->d_inst, b->d_state, i, I, ck + (size_t)(t / ckpt) * sv, s) != cudaSuccess) {
+                rc = bfail(b, PR_ECUDA, "checkpoint");
+                break;
             }
-            rc = run1();
+            g_launches += 1;
+            rc = runk(std::min(ckpt, nsteps - t));
         }
         if (rc) break;
         if (cudaMemcpyAsync(dv, lamV, sizeof(double) * m5, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -819,14 +822,12 @@ extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const 
             else g_launches += 2;
             for (int t = s0; t < s1 && !rc; ++t) {
                 if ((rc = run1())) break;
-                if (prk::adj_copy_state(b->d_inst, b->d_state, i, sg + (size_t)(t - s0) * st, s) != cudaSuccess ||
-                    prk::adj_moments(I, sg + (size_t)(t - s0) * st, sm + (size_t)(t - s0) * m5, s) != cudaSuccess)
+                if (prk::adj_copy_state(b->d_inst, b->d_state, i, sg + (size_t)(t - s0) * st, s) != cudaSuccess)
                     rc = bfail(b, PR_ECUDA, "segment store");
-                g_launches += 2;
+                g_launches += 1;
             }
             for (int t = s1 - 1; t >= s0 && !rc; --t) {
-                if (prk::adj_step(I, la, sg + (size_t)(t - s0) * st, sm + (size_t)(t - s0) * m5, coef, eps, lb, s) !=
-                    cudaSuccess)
+                if (prk::adj_step(I, la, sg + (size_t)(t - s0) * st, coef, eps, lb, s) != cudaSuccess)
                     rc = bfail(b, PR_ECUDA, "adjoint step");
                 g_launches += 2;
                 std::swap(la, lb);
