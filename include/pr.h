@@ -226,6 +226,13 @@ int pr_batch_set_f(pr_batch* b, int i, const double* f);
  * wait on neighbouring tiles of the previous step only.  Enqueued on stream. */
 int pr_batch_run(pr_batch* b, int nsteps, void* stream);
 
+/* The same for the instances [first, first + count) only (the others keep
+ * their state): one persistent launch over that range, e.g. the slices a
+ * rank holds at a late parareal iteration (Algorithm 2 recomputes fewer
+ * slices each iteration).  Enqueued on stream.  Errors: PR_EINVAL (range
+ * outside the batch, nsteps < 0), PR_ECUDA. */
+int pr_batch_run_range(pr_batch* b, int first, int count, int nsteps, void* stream);
+
 /* Moments (Eq. 18) of instance i into host out[5][nx_i]. Synchronous. */
 int pr_batch_moments(pr_batch* b, int i, int kind, double* out);
 

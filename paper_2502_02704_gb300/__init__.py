@@ -110,6 +110,7 @@ _SIGS = {
     "pr_batch_adjoint": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _D, _D, _D]),
     "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
     "pr_fine_dt_stab": (C.c_int, [C.POINTER(pr_instance), C.c_double, _D]),
+    "pr_batch_run_range": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP]),
     "pr_probe_fp64_peak": (C.c_int, [_D]),
     "pr_force_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_force_instance), C.c_int, C.c_int, C.c_int]),
     "pr_force_destroy": (C.c_int, [_VP]),
@@ -345,6 +346,10 @@ def pr_batch_set_f(b, i, f):
 
 def pr_batch_run(b, nsteps, stream=None):
     _batch_check(b, lib().pr_batch_run(b.ptr, int(nsteps), _stream(stream)))
+
+
+def pr_batch_run_range(b, first, count, nsteps, stream=None):
+    _batch_check(b, lib().pr_batch_run_range(b.ptr, int(first), int(count), int(nsteps), _stream(stream)))
 
 
 def pr_batch_moments(b, i, kind=PR_CONSERVED):

@@ -642,6 +642,22 @@ int pr_batch_run(pr_batch* b, int nsteps, void* stream)
     return enqueue_run(b, nsteps, 0, pick(b, stream), true);
 }
 
+int pr_batch_run_range(pr_batch* b, int first, int count, int nsteps, void* stream)
+{
+    if (!b) return PR_EINVAL;
+    if (first < 0 || count < 1 || first > b->n - count || nsteps < 0)
+        return bfail(b, PR_EINVAL, "instances [first, first + count) must lie in the batch and nsteps >= 0");
+    if (nsteps == 0) return PR_OK;
+    cudaStream_t s = pick(b, stream);
+    if (count == b->n) return enqueue_run(b, nsteps, 0, s, true);
+    prk::Active a{first, first + count};
+    BCUDA(b, cudaMemcpyAsync(b->d_active, &a, sizeof a, cudaMemcpyHostToDevice, s));
+    const int rc = enqueue_run(b, nsteps, 0, s, true);
+    prk::Active all{0, b->n};
+    BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+    return rc;
+}
+
 int pr_batch_inject_wait_timeout(pr_batch* b, int nsteps, int wait_ms)
 {
     if (!b) return PR_EINVAL;
