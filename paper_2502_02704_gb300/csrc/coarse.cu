@@ -125,8 +125,9 @@ __device__ __forceinline__ double flip_sign(double x, unsigned long long mask)
 __device__ __forceinline__ bool positive(long long b) { return b > 0 && b < 0x7ff0000000000000ll; }
 
 // A guard on the local steps of one G: no physical run needs this many, and
-// a run that reaches it (a degenerate state the checks above let through)
-// stops with PR_ENONPHYS instead of spinning.
+// a run that reaches it (a degenerate state the checks let through, or a
+// step too small to advance the time) stops with PR_ENONPHYS instead of
+// spinning.
 constexpr int MAX_LOCAL_STEPS = 1 << 24;
 
 // The CFL maxima are taken over speeds and temperatures, non-negative in
@@ -273,9 +274,11 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
             smax = warp_max_u64(smax);
             thmax = warp_max_u64(thmax);
             const double sm = __longlong_as_double(smax);
+            // (finite speeds: positive() rejected +inf and NaN above, a
+            // degenerate step that makes no progress runs into the step cap)
             unsigned long long flags = 0;  // 1: last local step, 2: stop (degenerate state or steps)
             double dt = 0.0;
-            if (!(sm > 0.0) || !isfinite(sm) || nloc >= MAX_LOCAL_STEPS) {
+            if (!(sm > 0.0) || isnan(sm) || nloc >= MAX_LOCAL_STEPS) {
                 flags = 2;
             } else {
                 const double rem = dT - t;
@@ -284,13 +287,9 @@ __device__ int coarse_G(const CoarseParams& p, cg::cluster_group& cl, const Peer
                     double dtv = p.cfl * p.dx * p.dx / (2.0 * p.visc * (5.0 / 3.0) * __longlong_as_double(thmax));
                     if (dtv < dt) dt = dtv;
                 }
-                if (!(dt > 0.0)) {
-                    flags = 2;
-                } else if (dt >= rem) {
+                if (dt >= rem) {
                     dt = rem;
                     flags = 1;
-                } else if (!(t + dt > t)) {
-                    flags = 2;  // no progress: the step is below the resolution of t
                 }
             }
             if (flags == 2 && lane == 0) atomicCAS(status, 0, ST_NONPHYS);
