@@ -264,15 +264,21 @@ __device__ __forceinline__ void prim_from_sums(const double* s, double dv, doubl
 __device__ __forceinline__ TabPar tabpar_from_sums(const double* s, double weight, int* status)
 {
     TabPar P;
+    // rho, u, theta (as rho dv^3-free sums, u/dv and tau) in float64
     const double is0 = 1.0 / s[0];
     const double k[3] = {s[1] * is0, s[2] * is0, s[3] * is0};
     const double tau = s[4] * is0 - (k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
     if (!(s[0] > 0.0) || !(tau > 0.0)) atomicCAS(status, 0, ST_NONPHYS);
-    const double tq = (2.0 * PI / 3.0) * tau;
 #pragma unroll
     for (int d = 0; d < 3; ++d) split_pair(k[d], P.uh[d], P.ul[d]);
-    split_pair(1.5 / tau, P.wh, P.wl);
-    split_pair(weight * s[0] / (tq * sqrt(tq)), P.ph, P.pl);
+    // the table weights from them in pair arithmetic (no float64 division or
+    // root on the step's critical path)
+    const F2 t2 = f2_of(tau);
+    const F2 w = f2_mul(F2{1.5f, 0.0f}, f2_rcp(t2));
+    const F2 tq = f2_mul(f2_of(2.0 * PI / 3.0), t2);
+    const F2 pref = f2_mul(f2_of(weight * s[0]), f2_rcp(f2_mul(tq, f2_sqrt(tq))));
+    P.wh = w.h, P.wl = w.l;
+    P.ph = pref.h, P.pl = pref.l;
     return P;
 }
 

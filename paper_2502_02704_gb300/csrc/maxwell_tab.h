@@ -56,6 +56,49 @@ __host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, flo
     e = (a - (s - bb)) + (b - bb);
 }
 
+// Float pairs h + l (|l| <= ulp(h)/2 after normalisation, ~48 bits): the
+// table weights 3/(2 tau) and rho (2 pi theta)^{-3/2} are formed in pair
+// arithmetic from the float64 Maxwellian parameters, so that no float64
+// division or square root (tens of instructions on this part's narrow
+// float64 pipe) sits between two steps.  Products with Dekker's method
+// (exact float products by FMA), reciprocal and square root by one Newton
+// step from the float32 value; relative error ~1e-13.
+struct F2 {
+    float h, l;
+};
+
+__host__ __device__ __forceinline__ F2 f2_of(double x)
+{
+    F2 r;
+    split_pair(x, r.h, r.l);
+    return r;
+}
+__host__ __device__ __forceinline__ F2 f2_norm(float h, float e)
+{
+    const float s = h + e;
+    return F2{s, e - (s - h)};
+}
+__host__ __device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
+{
+    const float p = a.h * b.h;
+    const float e = fmaf(a.h, b.h, -p) + fmaf(a.h, b.l, a.l * b.h);
+    return f2_norm(p, e);
+}
+// 1 / a: r = 1/a_h, then r + r (1 - a r) with the residual in pair arithmetic
+__host__ __device__ __forceinline__ F2 f2_rcp(F2 a)
+{
+    const float r = 1.0f / a.h;
+    const float t = fmaf(-a.h, r, 1.0f) - a.l * r;
+    return f2_norm(r, r * t);
+}
+// sqrt(a): s = sqrt(a_h), then s + (a - s^2) / (2 s)
+__host__ __device__ __forceinline__ F2 f2_sqrt(F2 a)
+{
+    const float s = sqrtf(a.h);
+    const float d = fmaf(-s, s, a.h) + a.l;
+    return f2_norm(s, d * (0.5f / s));
+}
+
 // exp(-(xh + xl)) for xh >= 0 to about 1e-9 relative, times the pair
 // (mh + ml), rounded once to float32.  Cody-Waite: -x = n ln2 + r with n an
 // integer and |r| <= ln2/2; ln2 = LN2H + LN2L with LN2H holding 15
