@@ -28,6 +28,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "maxwell_tab.h"
 #include "pr_kernels.h"
 
 namespace cg = cooperative_groups;
@@ -128,7 +129,7 @@ struct FSharedT {
     A gat[16][5];     // the cluster's partials, gathered (rank, quantity)
     A tot[8];         // cluster totals (rank order)
     double par[8];    // double path: rho, u_x, u_y, u_z, theta, pref, 1/(2 theta)
-    float fpar[8];    // float path: the same in float
+    float fpar[8];    // (unused: the float path's pairs FPar replace tot once read)
 };
 using FShared = FSharedT<double>;
 static_assert(sizeof(FSharedT<DF>) == sizeof(FSharedT<double>), "layouts differ");
@@ -219,10 +220,17 @@ __device__ __forceinline__ double rsqrt_nr(double x)
 // path gets tot = (rho, rho u, 2E) with 2E = sum |v|^2 f dv and writes par =
 // (rho, u_x, u_y, u_z, theta, rho (2 pi theta)^(-3/2), 1/(2 theta)), the
 // reciprocals by Newton steps.  The float path gets the same sums without the
-// cell volume dv3 (double-float) and writes fpar: theta = (rho 2E - |rho u|^2)
-// / (3 rho^2) with the numerator, which cancels when |u|^2 >> theta, formed
-// in double-float; the divisions and the root in float.  A non-positive rho
-// or theta raises PR_ENONPHYS when report is set.
+// cell volume dv3 (double-float) and writes FPar: u, 1/(2 theta) and the
+// prefactor rho dv3 (2 pi theta)^{-3/2} as float pairs, in pair arithmetic
+// (~1e-13; theta = (rho 2E - |rho u|^2) / (3 rho^2) with the numerator, which
+// cancels when |u|^2 >> theta, formed in double-float), so that the float32
+// factor tables come out within about 1e-9 before their one rounding.  A
+// non-positive rho or theta raises PR_ENONPHYS when report is set.
+struct FPar {
+    F2 u[3], i2t, pref;
+};
+static_assert(sizeof(FPar) == 5 * sizeof(DF), "FPar takes the place of the five double-float totals");
+
 __device__ __forceinline__ void maxwell_params_d(const double* tot, double* par, bool report, int* status)
 {
     const double r = tot[0], m1 = tot[1], m2 = tot[2], m3 = tot[3], e2 = tot[4];
@@ -246,7 +254,7 @@ __device__ __forceinline__ void maxwell_params(FSharedT<double>& sh, double, boo
     maxwell_params_d(sh.tot, sh.par, report, status);
 }
 
-__device__ __forceinline__ void maxwell_params_f(const DF* tot, float* fpar, float dv3, bool report, int* status)
+__device__ __forceinline__ void maxwell_params_f(const DF* tot, float* fpar, double dv3, bool report, int* status)
 {
     const DF r = tot[0], m1 = tot[1], m2 = tot[2], m3 = tot[3], e2 = tot[4];
     const DF mm = df_add(df_mul(m1, m1), df_add(df_mul(m2, m2), df_mul(m3, m3)));
@@ -254,21 +262,39 @@ __device__ __forceinline__ void maxwell_params_f(const DF* tot, float* fpar, flo
     const float rf = r.hi + r.lo, num = nd.hi + nd.lo;
     const bool ok = rf > 0.0f && num > 0.0f && isfinite(rf) && isfinite(num);
     if (!ok && report) atomicCAS(status, 0, ST_NONPHYS);
-    const float irf = 1.0f / rf;
-    const float th = ok ? num * (irf * irf) * (1.0f / 3.0f) : 1.0f;
-    const float rs = ok ? rsqrtf(2.0f * 3.14159265f * th) : 0.0f;
-    fpar[0] = rf * dv3;
-    fpar[1] = (m1.hi + m1.lo) * irf;
-    fpar[2] = (m2.hi + m2.lo) * irf;
-    fpar[3] = (m3.hi + m3.lo) * irf;
-    fpar[4] = th;
-    fpar[5] = rf * dv3 * rs * rs * rs;
-    fpar[6] = 0.5f / th;
+    FPar P;
+    if (ok) {
+        const F2 R = f2_norm(r.hi, r.lo), ir = f2_rcp(R);
+        P.u[0] = f2_mul(f2_norm(m1.hi, m1.lo), ir);
+        P.u[1] = f2_mul(f2_norm(m2.hi, m2.lo), ir);
+        P.u[2] = f2_mul(f2_norm(m3.hi, m3.lo), ir);
+        const F2 th = f2_mul(f2_mul(f2_norm(nd.hi, nd.lo), f2_mul(ir, ir)), f2_of(1.0 / 3.0));
+        P.i2t = f2_mul(F2{0.5f, 0.0f}, f2_rcp(th));
+        const F2 tp = f2_mul(f2_of(2.0 * 3.14159265358979323846), th);
+        P.pref = f2_mul(f2_mul(R, f2_of(dv3)), f2_rcp(f2_mul(tp, f2_sqrt(tp))));
+    } else {
+        P.u[0] = P.u[1] = P.u[2] = F2{0.0f, 0.0f};
+        P.i2t = F2{0.5f, 0.0f};
+        P.pref = F2{0.0f, 0.0f};
+    }
+    *reinterpret_cast<FPar*>(fpar) = P;
 }
 
-__device__ __forceinline__ void maxwell_params(FSharedT<DF>& sh, float dv3, bool report, int* status)
+__device__ __forceinline__ void maxwell_params(FSharedT<DF>& sh, double dv3, bool report, int* status)
 {
-    maxwell_params_f(sh.tot, sh.fpar, dv3, report, status);
+    maxwell_params_f(sh.tot, reinterpret_cast<float*>(sh.tot), dv3, report, status);  // FPar over tot
+}
+
+// exp(-(v - u)^2 / (2 theta)) times m, from the float-pair node v, mean u and
+// 1/(2 theta): the exponent in pair arithmetic, exp_neg_pair for the rest.
+__device__ __forceinline__ float gauss_f2(F2 v, F2 u, F2 i2t, F2 m)
+{
+    float ch, cl;
+    two_sum(v.h, -u.h, ch, cl);
+    cl += v.l - u.l;
+    const F2 c = f2_norm(ch, cl);
+    const F2 x = f2_mul(f2_mul(c, c), i2t);
+    return exp_neg_pair(x.h, x.l, m.h, m.l);
 }
 
 __device__ __forceinline__ void cluster_arrive()
@@ -597,7 +623,7 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
     }
     cluster_arrive_relaxed();  // the peers' partials are read (the matching wait is at the end)
     __syncthreads();
-    if (threadIdx.x == 0) maxwell_params(sh, scal<T>(I.dv3, I.fdv3), I.collide && rank == 0, status);
+    if (threadIdx.x == 0) maxwell_params(sh, I.dv3, I.collide && rank == 0, status);
     __syncthreads();
 
     const T a = scal<T>(I.a, I.fa), bb = scal<T>(I.b, I.fb);
@@ -606,28 +632,47 @@ k_force_step(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
 #pragma unroll
     for (int l = 0; l < VEC; ++l) myz[l] = T(0);
     if (collide) {
-        // separable Maxwellian M = pref ex[jx] ey[jy] ez[jz], the three factor
-        // tables evaluated in T from the double parameters
+        // separable Maxwellian b M = (b pref ex[jx]) ey[jy] ez[jz]: in float64
+        // from the double parameters; in float32 each factor within ~1e-9 of
+        // its exact value before one rounding (the exponent in pair
+        // arithmetic from the pair parameters and nodes), b pref folded into
+        // ex with the same single rounding
         T* ey = ex + nvx;
         T* ez = ey + g.nvp;
-        const T ux = scal<T>(sh.par[1], sh.fpar[1]), uy = scal<T>(sh.par[2], sh.fpar[2]);
-        const T uz = scal<T>(sh.par[3], sh.fpar[3]), inv2th = scal<T>(sh.par[6], sh.fpar[6]);
         const int nvp = g.nvp;
-        for (int k = threadIdx.x; k < nvx + 2 * nvp; k += blockDim.x) {
-            if (k < nvx) {
-                const T cx = vxs[k] - ux;
-                ex[k] = texp(-cx * cx * inv2th);
-            } else {
-                const int j = k - nvx < nvp ? k - nvx : k - nvx - nvp;
-                const T v = vt[nvx + j * nvp];  // v_y node j (v_y table, jz = 0)
-                const T cc = v - (k - nvx < nvp ? uy : uz);
-                ex[k] = texp(-cc * cc * inv2th);
+        if constexpr (sizeof(T) == sizeof(float)) {
+            const FPar& P = *reinterpret_cast<const FPar*>(sh.tot);
+            const F2 m = f2_mul(F2{(float)bb, 0.0f}, P.pref), one{1.0f, 0.0f};
+            const F2* vp = reinterpret_cast<const F2*>(I.vpair);
+            for (int k = threadIdx.x; k < nvx + 2 * nvp; k += blockDim.x) {
+                if (k < nvx) {
+                    ex[k] = gauss_f2(vp[k], P.u[0], P.i2t, m);
+                } else {
+                    const int j = k - nvx < nvp ? k - nvx : k - nvx - nvp;
+                    ex[k] = gauss_f2(vp[nvx + j], P.u[k - nvx < nvp ? 1 : 2], P.i2t, one);
+                }
             }
-        }
-        __syncthreads();
-        const T pb = bb * scal<T>(sh.par[5], sh.fpar[5]);
+            __syncthreads();
 #pragma unroll
-        for (int l = 0; l < VEC; ++l) myz[l] = pb * (ey[jy[l]] * ez[jz[l]]);
+            for (int l = 0; l < VEC; ++l) myz[l] = ey[jy[l]] * ez[jz[l]];
+        } else {
+            const T ux = sh.par[1], uy = sh.par[2], uz = sh.par[3], inv2th = sh.par[6];
+            for (int k = threadIdx.x; k < nvx + 2 * nvp; k += blockDim.x) {
+                if (k < nvx) {
+                    const T cx = vxs[k] - ux;
+                    ex[k] = texp(-cx * cx * inv2th);
+                } else {
+                    const int j = k - nvx < nvp ? k - nvx : k - nvx - nvp;
+                    const T v = vt[nvx + j * nvp];  // v_y node j (v_y table, jz = 0)
+                    const T cc = v - (k - nvx < nvp ? uy : uz);
+                    ex[k] = texp(-cc * cc * inv2th);
+                }
+            }
+            __syncthreads();
+            const T pb = bb * sh.par[5];
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) myz[l] = pb * (ey[jy[l]] * ez[jz[l]]);
+        }
     }
 
     // pass 2: relax and store; on the last step also the sums of f^{n+1}
@@ -767,7 +812,7 @@ __host__ __device__ inline FuLayout fu_layout(int nvp, int R, int S, int es)
     o = fu_al16(o + (size_t)(S + 2) * NQ * 8);
     L.tot = o;                                         // A [S][5]: P(f*) of each column
     o = fu_al16(o + (size_t)S * 5 * 8);
-    L.par = o;                                         // T [S][8]: Maxwellian parameters
+    L.par = o;                                         // T [S][8]: Maxwellian parameters (double path)
     o = fu_al16(o + (size_t)S * 8 * es);
     L.vxe = o;                                         // T2 [S][R]: (v_x, b pref ex) of the CTA's rows
     o = fu_al16(o + (size_t)S * R * 2 * es);
@@ -803,9 +848,9 @@ __device__ __forceinline__ typename FuOps<T>::A part_rank_sum(const typename FuO
 
 // Maxwellian parameters of a column from its P(f*) sums (without dv3): the
 // float path's double-float function, or the double path's.
-__device__ __forceinline__ void fu_params(const DF* tot, float* par, const FInst& I, bool report, int* status)
+__device__ __forceinline__ void fu_params(DF* tot, float*, const FInst& I, bool report, int* status)
 {
-    maxwell_params_f(tot, par, I.fdv3, report, status);
+    maxwell_params_f(tot, reinterpret_cast<float*>(tot), I.dv3, report, status);  // FPar over tot
 }
 __device__ __forceinline__ void fu_params(const double* tot, double* par, const FInst& I, bool report, int* status)
 {
@@ -1117,25 +1162,43 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
         tot[j * 5 + k] = t;
     }
     __syncthreads();
+    // (float path: each column's parameter pairs FPar replace its five
+    // double-float totals, read first; double path: par [8] per column)
     for (int j = threadIdx.x; j < W; j += blockDim.x) fu_params(tot + j * 5, par + j * 8, I, I.collide && rank == 0, status);
     __syncthreads();
-    // per column: (v_x, b pref ex) of the rows and ey, ez; zero tables
-    // without collisions
+    // per column: (v_x, b pref ex) of the rows and ey, ez (float32: each
+    // factor from the pair parameters within ~1e-9 before its rounding, as in
+    // the clustered step); zero tables without collisions
     const bool collide = I.collide != 0;
     const T bb = scal<T>(I.b, I.fb);
     for (int t = threadIdx.x; t < W * (nr + 2 * nvp); t += blockDim.x) {
         const int j = t / (nr + 2 * nvp), k = t - j * (nr + 2 * nvp);
         const T* pj = par + j * 8;
         if (k < nr) {
-            const T vx = vt[r0 + k], cx = vx - pj[1];
+            const T vx = vt[r0 + k];
             T2 e;
             e.x = vx;
-            e.y = collide ? bb * pj[5] * texp(-cx * cx * pj[6]) : T(0);
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const FPar& P = *reinterpret_cast<const FPar*>(tot + j * 5);
+                const F2* vp = reinterpret_cast<const F2*>(I.vpair);
+                e.y = collide ? gauss_f2(vp[r0 + k], P.u[0], P.i2t, f2_mul(F2{(float)bb, 0.0f}, P.pref)) : T(0);
+            } else {
+                const T cx = vx - pj[1];
+                e.y = collide ? bb * pj[5] * texp(-cx * cx * pj[6]) : T(0);
+            }
             vxe[j * R + k] = e;
         } else {
             const int m = k - nr < nvp ? k - nr : k - nr - nvp;
-            const T cc = vt[nvx + m * nvp] - (k - nr < nvp ? pj[2] : pj[3]);
-            eyz[j * 2 * nvp + (k - nr)] = collide ? texp(-cc * cc * pj[6]) : T(0);
+            T val;
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const FPar& P = *reinterpret_cast<const FPar*>(tot + j * 5);
+                const F2* vp = reinterpret_cast<const F2*>(I.vpair);
+                val = gauss_f2(vp[nvx + m], P.u[k - nr < nvp ? 1 : 2], P.i2t, F2{1.0f, 0.0f});
+            } else {
+                const T cc = vt[nvx + m * nvp] - (k - nr < nvp ? pj[2] : pj[3]);
+                val = texp(-cc * cc * pj[6]);
+            }
+            eyz[j * 2 * nvp + (k - nr)] = collide ? val : T(0);
         }
     }
     T vy[VEC], vz[VEC], vp2[VEC];
@@ -1394,14 +1457,27 @@ k_force_lift(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
         if (i == 0 && blockIdx.x == 0) cur[b] = 0;
     }
     __syncthreads();
-    const T ux = (T)par[1], uy = (T)par[2], uz = (T)par[3], inv2th = (T)(0.5 / par[4]), pref = (T)par[5];
-    for (int q = threadIdx.x; q < nvx; q += FT) {
-        T cx = vt[q] - ux;
-        ex[q] = texp(-cx * cx * inv2th);
-    }
-    for (int q = threadIdx.x; q < nvp2; q += FT) {
-        T cy = vt[nvx + q] - uy, cz = vt[nvx + nvp2 + q] - uz;
-        eyz[q] = pref * texp(-cy * cy * inv2th) * texp(-cz * cz * inv2th);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // factors within ~1e-9 before their one rounding, the prefactor
+        // folded into ex (float pairs from the float64 parameters)
+        const F2 u0 = f2_of(par[1]), u1 = f2_of(par[2]), u2 = f2_of(par[3]);
+        const F2 i2t = f2_of(0.5 / par[4]), pref = f2_of(par[5]), one{1.0f, 0.0f};
+        const F2* vp = reinterpret_cast<const F2*>(I.vpair);
+        for (int q = threadIdx.x; q < nvx; q += FT) ex[q] = gauss_f2(vp[q], u0, i2t, pref);
+        for (int q = threadIdx.x; q < nvp2; q += FT) {
+            const int jy = q / nvp, jz = q - jy * nvp;
+            eyz[q] = gauss_f2(vp[nvx + jy], u1, i2t, one) * gauss_f2(vp[nvx + jz], u2, i2t, one);
+        }
+    } else {
+        const T ux = (T)par[1], uy = (T)par[2], uz = (T)par[3], inv2th = (T)(0.5 / par[4]), pref = (T)par[5];
+        for (int q = threadIdx.x; q < nvx; q += FT) {
+            T cx = vt[q] - ux;
+            ex[q] = texp(-cx * cx * inv2th);
+        }
+        for (int q = threadIdx.x; q < nvp2; q += FT) {
+            T cy = vt[nvx + q] - uy, cz = vt[nvx + nvp2 + q] - uz;
+            eyz[q] = pref * texp(-cy * cy * inv2th) * texp(-cz * cz * inv2th);
+        }
     }
     __syncthreads();
     T* out = static_cast<T*>(I.f[0]) + (size_t)i * g.ncol;

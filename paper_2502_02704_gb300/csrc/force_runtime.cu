@@ -237,6 +237,17 @@ bool ensure_partials(pr_force* b)
     return true;
 }
 
+// Byte size of an instance's node tables: v_x, v_y, v_z, v_y^2 + v_z^2 in the
+// element type, then (float path) the nodes as float pairs hi + lo (v_x, then
+// v_y = v_z), from which the float32 Maxwellian factors are evaluated.
+static size_t vtab_bytes(int nvx, int nvp, size_t es)
+{
+    const size_t base = ((size_t)nvx + 3 * (size_t)nvp * nvp) * es;
+    return es == sizeof(float) ? (base + 15) / 16 * 16 + 2 * ((size_t)nvx + nvp) * sizeof(float) : base;
+}
+
+static size_t vpair_offset(int nvx, int nvp, size_t es) { return (((size_t)nvx + 3 * (size_t)nvp * nvp) * es + 15) / 16 * 16; }
+
 template <typename T>
 void fill_vtab(std::vector<unsigned char>& out, int nvx, int nvp, double L)
 {
@@ -251,8 +262,18 @@ void fill_vtab(std::vector<unsigned char>& out, int nvx, int nvp, double L)
         t[nvx + nvp2 + jp] = (T)z;
         t[nvx + 2 * nvp2 + jp] = (T)(y * y + z * z);
     }
-    out.resize(t.size() * sizeof(T));
-    memcpy(out.data(), t.data(), out.size());
+    out.assign(vtab_bytes(nvx, nvp, sizeof(T)), 0);
+    memcpy(out.data(), t.data(), t.size() * sizeof(T));
+    if (sizeof(T) == sizeof(float)) {
+        float* pp = reinterpret_cast<float*>(out.data() + vpair_offset(nvx, nvp, sizeof(T)));
+        auto put = [&](int k, double v) {
+            const float h = (float)v;
+            pp[2 * k] = h;
+            pp[2 * k + 1] = (float)(v - (double)h);
+        };
+        for (int j = 0; j < nvx; ++j) put(j, -L + (j + 0.5) * dvx);
+        for (int j = 0; j < nvp; ++j) put(nvx + j, -L + (j + 0.5) * dvp);
+    }
 }
 
 void fold_events(pr_force* b)
@@ -378,7 +399,7 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
     const size_t es = elem(precision);
     const int nx = b->nx, nvp2 = b->nvp * b->nvp;
     const size_t state = (size_t)nx * b->g.ncol * es;
-    const size_t vt = ((size_t)b->nvx + 3 * nvp2) * es;
+    const size_t vt = (vtab_bytes(b->nvx, b->nvp, es) + 255) / 256 * 256;
     auto cm = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cm((void**)&b->d_inst, sizeof(prk::FInst) * n) && cm((void**)&b->d_active, sizeof(prk::Active)) &&
@@ -423,8 +444,17 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
         I.Emax = em;
         I.E = b->d_E + (size_t)k * nx;
         I.Ef = b->d_Ef + (size_t)k * nx;
-        I.fa = (float)I.a;
-        I.fb = (float)I.b;
+        // the float32 step forms a f* + b M with float weights: the larger one
+        // rounded to float32 and the smaller one 1 - larger (exact by
+        // Sterbenz, the larger lying in [1/2, 1]), so that a + b = 1 holds for
+        // the weights in use and the relaxation keeps the moments (Eq. 7)
+        if (I.a >= I.b) {
+            I.fa = (float)I.a;
+            I.fb = 1.0f - I.fa;
+        } else {
+            I.fb = (float)I.b;
+            I.fa = 1.0f - I.fb;
+        }
         I.fnu = (float)I.nu;
         I.fnuv = (float)I.nuv;
         I.fEmax = (float)I.Emax;
@@ -432,13 +462,17 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
         I.f[0] = b->bufs[2 * k];
         I.f[1] = b->bufs[2 * k + 1];
         I.vtab = static_cast<unsigned char*>(b->d_vtab) + vt * k;
+        I.vpair = es == sizeof(float)
+                      ? reinterpret_cast<const float*>(static_cast<unsigned char*>(b->d_vtab) + vt * k +
+                                                       vpair_offset(b->nvx, b->nvp, es))
+                      : nullptr;
         I.Uin = b->d_Ulift + (size_t)k * 5 * nx;
         I.Uout = nullptr;
         I.Ucur = b->d_U + (size_t)k * 5 * nx;
         std::vector<unsigned char> t;
         if (precision == PR_FP64) fill_vtab<double>(t, b->nvx, b->nvp, d.L);
         else fill_vtab<float>(t, b->nvx, b->nvp, d.L);
-        memcpy(&tabs[vt * k], t.data(), vt);
+        memcpy(&tabs[vt * k], t.data(), t.size());
         // first v_x row whose node, in the element type, is > 0 (the kernel
         // takes the upwind side from the same comparison)
         I.hpos = b->nvx;

@@ -123,6 +123,7 @@ struct FInst {
     void* f[2];                // ping-pong state
     void* part[2];             // fused step: column sums of f[k], [nx][C][17], double-float (float) or double
     const void* vtab;          // T: v_x[nvx], v_y[nvp2], v_z[nvp2], v_y^2+v_z^2[nvp2]
+    const float* vpair;        // float path: the nodes as float pairs, v_x[nvx][2], v_p[nvp][2]
     const double* Uin;         // lift source, conserved [5][nx] (device) or null
     double* Uout;              // projection destination after the last step (or null)
     double* Ucur;              // conserved moments of the current state [5][nx]
