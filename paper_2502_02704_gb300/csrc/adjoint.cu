@@ -90,8 +90,8 @@ __device__ void maxwell_factors(const Inst& I, double ux, double uy, double uz, 
     }
 }
 
-__global__ void __launch_bounds__(ACT) k_adj_coef(Inst I, const double* lam, const double* g, double* coef,
-                                                 double* eps_acc)
+__global__ void __launch_bounds__(ACT) k_adj_coef(Inst I, const double* lam, const double* g, const double* msum,
+                                                 double* coef, double* eps_acc)
 {
     extern __shared__ double ash[];  // e[3][nv], tx[2][nv], then the block-sum scratch
     const int c = blockIdx.x, nv = I.nv, np = nv * nv;
@@ -102,25 +102,35 @@ __global__ void __launch_bounds__(ACT) k_adj_coef(Inst I, const double* lam, con
     const double* lc = lam + (size_t)c * I.nv3;
     for (int j = threadIdx.x; j < nv; j += blockDim.x) tx[j] = -I.L + (j + 0.5) * I.dv;
     __syncthreads();
-    // moments of g (sums over the plane, then over jx)
+    // moments of g: recorded by the forward kernel (sums in grid units,
+    // v = k dv), or summed here (over the plane, then over jx)
     double m[5] = {0, 0, 0, 0, 0};
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        const int jy = p / nv, jz = p - jy * nv;
-        const double vy = -I.L + (jy + 0.5) * I.dv, vz = -I.L + (jz + 0.5) * I.dv;
-        double s0 = 0, sx = 0, sxx = 0;
-        for (int jx = 0; jx < nv; ++jx) {
-            const double vx = tx[jx], f = gc[(size_t)jx * np + p];
-            s0 += f;
-            sx += vx * f;
-            sxx += vx * vx * f;
+    if (msum) {
+        const double* q = msum + (size_t)c * 5;
+        m[0] = q[0];
+        m[1] = q[1] * I.dv;
+        m[2] = q[2] * I.dv;
+        m[3] = q[3] * I.dv;
+        m[4] = q[4] * I.dv * I.dv;
+    } else {
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+            const int jy = p / nv, jz = p - jy * nv;
+            const double vy = -I.L + (jy + 0.5) * I.dv, vz = -I.L + (jz + 0.5) * I.dv;
+            double s0 = 0, sx = 0, sxx = 0;
+            for (int jx = 0; jx < nv; ++jx) {
+                const double vx = tx[jx], f = gc[(size_t)jx * np + p];
+                s0 += f;
+                sx += vx * f;
+                sxx += vx * vx * f;
+            }
+            m[0] += s0;
+            m[1] += sx;
+            m[2] += vy * s0;
+            m[3] += vz * s0;
+            m[4] += sxx + (vy * vy + vz * vz) * s0;
         }
-        m[0] += s0;
-        m[1] += sx;
-        m[2] += vy * s0;
-        m[3] += vz * s0;
-        m[4] += sxx + (vy * vy + vz * vz) * s0;
+        block_sum_n<5>(m, sh);
     }
-    block_sum_n<5>(m, sh);
     const double rho = m[0] * I.dv3, ir = 1.0 / rho;
     const double u[3] = {m[1] * I.dv3 * ir, m[2] * I.dv3 * ir, m[3] * I.dv3 * ir};
     const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -285,16 +295,6 @@ __global__ void __launch_bounds__(ACT) k_adj_lift(Inst I, const double* lam, con
     }
 }
 
-// copy the float64 stored state g[cur] of instance b into dst [nx][ldv]
-__global__ void k_copy_state(const Inst* insts, const InstState* st, int b, double* dst)
-{
-    const Inst& I = insts[b];
-    const double* src = reinterpret_cast<const double*>(I.g[st[b].cur]);
-    const size_t n = (size_t)I.nx * I.ldv;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-        dst[k] = src[k];
-}
-
 }  // namespace
 
 cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_t s)
@@ -305,10 +305,10 @@ cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_
 
 static size_t adj_smem(const Inst& I) { return (5 * (size_t)I.nv + (ACT / 32) * 6) * sizeof(double); }
 
-cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, double* coef, double* eps_acc,
-                     double* lam_out, cudaStream_t s)
+cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const double* msum, double* coef,
+                     double* eps_acc, double* lam_out, cudaStream_t s)
 {
-    k_adj_coef<<<I.nx, ACT, adj_smem(I), s>>>(I, lam_in, g, coef, eps_acc);
+    k_adj_coef<<<I.nx, ACT, adj_smem(I), s>>>(I, lam_in, g, msum, coef, eps_acc);
     k_adj_apply<<<dim3(I.nx, (I.nv * I.nv + APT - 1) / APT), APT, 4 * (size_t)I.nv * sizeof(double), s>>>(
         I, lam_in, coef, lam_out);
     return cudaGetLastError();
@@ -320,10 +320,5 @@ cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double
     return cudaGetLastError();
 }
 
-cudaError_t adj_copy_state(const Inst* insts, const InstState* st, int b, double* dst, cudaStream_t s)
-{
-    k_copy_state<<<512, 256, 0, s>>>(insts, st, b, dst);
-    return cudaGetLastError();
-}
 
 }  // namespace prk

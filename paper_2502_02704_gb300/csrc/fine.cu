@@ -315,6 +315,8 @@ __device__ void finalize_tile(const Inst& I, int s, int nsteps, int xt, int c0, 
         mom[idx] = acc;
     }
     __syncthreads();
+    if (sizeof(T) == sizeof(double) && I.trace_m)  // the recorded step's moment sums
+        for (int idx = tid; idx < ncols * 5; idx += NT) I.trace_m[((size_t)(s - 1) * I.nx + c0) * 5 + idx] = mom[idx];
     for (int i = tid; i < ncols; i += NT) {
         if (sizeof(T) == 4) tp[i] = tabpar_from_sums(mom + i * 5, I.b, status);
         else prim_from_sums(mom + i * 5, I.dv, I.dv3, I.b, par + i * 8, status);
@@ -601,6 +603,14 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
         if (act) {
 #pragma unroll
             for (int k = 0; k < NV4; ++k) st4(outp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
+            if constexpr (sizeof(T) == sizeof(double)) {
+                // the reverse sweep of the gradient records every step's f*
+                if (I.trace) {
+                    double* tp = I.trace + ((size_t)(s - 1) * nx + c0 + i) * ldv + v0;
+#pragma unroll
+                    for (int k = 0; k < NV4; ++k) st4(tp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
+                }
+            }
             // the q = 0 terms of t1, t2 vanish (started at q = 1: the same
             // bits for finite values, two operations fewer per column)
             T s0 = fs[0], t1 = T(0), t2 = T(0);

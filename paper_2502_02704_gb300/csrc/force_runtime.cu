@@ -397,7 +397,7 @@ int create(pr_force** out, const pr_force_instance* inst, int n, int scheme, int
         return fail(PR_EINVAL, "no cluster of this shape fits the device");
     }
     const size_t es = elem(precision);
-    const int nx = b->nx, nvp2 = b->nvp * b->nvp;
+    const int nx = b->nx;
     const size_t state = (size_t)nx * b->g.ncol * es;
     const size_t vt = (vtab_bytes(b->nvx, b->nvp, es) + 255) / 256 * 256;
     auto cm = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };

@@ -37,6 +37,8 @@ struct Inst {
     unsigned int* arrive;      // [n_xt] arrivals of v chunks in the current step
     const int* deps;           // [n_xt][MAXDEP] tiles an item must wait on (-1 padded)
     long long item0;           // prefix: first item of this instance within a step
+    double* trace;             // float64 only, or null: f* of step s of a launch at [s-1][nx][ldv]
+    double* trace_m;           // float64 only, or null: its moment sums (grid units) at [s-1][nx][5]
 };
 
 // Per-instance dynamic state, updated on the device between launches.
@@ -99,10 +101,9 @@ cudaError_t launch_set_f(int precision, const Inst* insts, InstState* st, int b,
 cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_t s);
 // One reverse step: lam_out = T^T (a lam_in + b dv^3 (c0 + c.v + c4 |v|^2)),
 // the coefficients from the moments of the step's transported state g.
-cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, double* coef, double* eps_acc,
-                     double* lam_out, cudaStream_t s);
+cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const double* msum, double* coef,
+                     double* eps_acc, double* lam_out, cudaStream_t s);
 cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double* dU0, cudaStream_t s);
-cudaError_t adj_copy_state(const Inst* insts, const InstState* st, int b, double* dst, cudaStream_t s);
 
 // ---- fine propagator with an exterior force (force.cu) ----
 constexpr int FORCE_THREADS = 256;       // threads per CTA of the force kernels

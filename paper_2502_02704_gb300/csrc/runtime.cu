@@ -784,13 +784,16 @@ extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const 
     const size_t st = (size_t)I.nx * I.ldv, sv = (size_t)I.nx * I.nv3, m5 = (size_t)5 * I.nx;
     const int nck = nsteps > 0 ? (nsteps + ckpt - 1) / ckpt : 0;
     const int seg = std::min(ckpt, std::max(nsteps, 1));
-    // work: checkpoints, segment states, two adjoint buffers, small vectors
-    size_t need = ((size_t)nck * sv + (size_t)seg * st + 2 * sv + 5 * I.nx + I.nx + 2 * m5) * sizeof(double);
+    // work: checkpoints, segment states and their moment sums, two adjoint
+    // buffers, small vectors
+    size_t need =
+        ((size_t)nck * sv + (size_t)seg * st + (size_t)seg * m5 + 2 * sv + 5 * I.nx + I.nx + 2 * m5) * sizeof(double);
     double* w = nullptr;
     if (cudaMalloc(&w, need) != cudaSuccess) return bfail(b, PR_ENOMEM, "adjoint work buffers (%zu bytes)", need);
     double* ck = w;
     double* sg = ck + (size_t)nck * sv;
-    double* la = sg + (size_t)seg * st;
+    double* smm = sg + (size_t)seg * st;
+    double* la = smm + (size_t)seg * m5;
     double* lb = la + sv;
     double* coef = lb + sv;
     double* eps = coef + 5 * I.nx;
@@ -809,7 +812,6 @@ extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const 
         BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
         return r;
     };
-    auto run1 = [&]() -> int { return runk(1); };
     do {
         // forward from the lifted state, storing f every ckpt steps: one
         // persistent launch per segment (the same bits as single steps)
@@ -836,14 +838,18 @@ extern "C" int pr_batch_adjoint(pr_batch* b, int i, int nsteps, int ckpt, const 
             else if (prk::launch_set_f(0, b->d_inst, b->d_state, i, I, ck + (size_t)k * sv, s) != cudaSuccess)
                 rc = bfail(b, PR_ECUDA, "reload checkpoint");
             else g_launches += 2;
-            for (int t = s0; t < s1 && !rc; ++t) {
-                if ((rc = run1())) break;
-                if (prk::adj_copy_state(b->d_inst, b->d_state, i, sg + (size_t)(t - s0) * st, s) != cudaSuccess)
-                    rc = bfail(b, PR_ECUDA, "segment store");
-                g_launches += 1;
-            }
+            if (rc) break;
+            // the segment recomputed in one persistent launch that records each
+            // step's f* and its moment sums (the same bits as single steps)
+            Inst tr = b->h[i];
+            tr.trace = sg;
+            tr.trace_m = smm;
+            BCUDA(b, cudaMemcpyAsync(b->d_inst + i, &tr, sizeof(Inst), cudaMemcpyHostToDevice, s));
+            rc = runk(s1 - s0);
+            BCUDA(b, cudaMemcpyAsync(b->d_inst + i, &b->h[i], sizeof(Inst), cudaMemcpyHostToDevice, s));
             for (int t = s1 - 1; t >= s0 && !rc; --t) {
-                if (prk::adj_step(I, la, sg + (size_t)(t - s0) * st, coef, eps, lb, s) != cudaSuccess)
+                if (prk::adj_step(I, la, sg + (size_t)(t - s0) * st, smm + (size_t)(t - s0) * m5, coef, eps, lb, s) !=
+                    cudaSuccess)
                     rc = bfail(b, PR_ECUDA, "adjoint step");
                 g_launches += 2;
                 std::swap(la, lb);
