@@ -409,3 +409,68 @@ def test_transport_moments_follow_from_column_sums(bc, nvx):
     Q[:, 4] = -dvx * (E * (2 * M[:, 1] - L * (rn - r0)) - Em * (L * (r0 + rn) - dvx * M[:, 0]))
     got = M - nu * (Ap - Ap_m + An_p - An) - nuv * Q
     assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def _ghost_x(f, c, bc, nvx, nvp):
+    """Column c of f [nx, ncol] through the boundary rule (a reflecting wall
+    mirrors the column and reverses v_x)."""
+    nx = f.shape[0]
+    if 0 <= c < nx:
+        return f[c]
+    if bc == O.BC_PERIODIC:
+        return f[c % nx]
+    if bc == O.BC_OUTFLOW:
+        return f[0 if c < 0 else nx - 1]
+    m = -1 - c if c < 0 else 2 * nx - 1 - c
+    return f[m].reshape(nvx, nvp * nvp)[::-1].reshape(-1)
+
+
+def _minmod(a, b):
+    return np.where(a * b <= 0, 0.0, np.where(np.abs(a) < np.abs(b), a, b))
+
+
+@pytest.mark.parametrize("bc", [O.BC_PERIODIC, O.BC_OUTFLOW, O.BC_REFLECT])
+@pytest.mark.parametrize("nvx", [8, 9])
+def test_muscl_transport_moments_follow_from_limited_column_sums(bc, nvx):
+    # With MUSCL-minmod x fluxes the interface value on the upwind side of
+    # face c+1/2 is f_c + s_c/2 (v_x > 0) or f_{c+1} - s_{c+1}/2 (v_x <= 0),
+    # s_c = minmod(f_c - f_{c-1}, f_{c+1} - f_c), so the upwind identity holds
+    # with A+ and A- taken of f + s/2 and f - s/2: each column's limited sums
+    # need only that column and its two neighbours.  Ghosts: an outflow edge
+    # column has s = 0 (its ghost repeats it), so the ghost's sums are the
+    # edge column's; a reflecting ghost has s_ghost(v) = -s_edge(-v) (minmod
+    # is odd), so it swaps A+ and A- with the sign of the even weights as
+    # the upwind sums do.
+    nx, nvp, L = 7, 4, 5.0
+    E = np.linspace(-0.6, 0.9, nx)
+    k = O.VKin(nx=nx, nvx=nvx, nvp=nvp, L=L, x0=0.0, x1=2.0, bc=bc, eps=math.inf, scheme=O.MUSCL, E=E)
+    f = np.random.default_rng(5).random((nx, k.ncol)) + 0.1
+    dt = O.v_fine_dt_stab(k, 0.5)
+    want = _column_sums(O.v_fine_run(k, dt, 1, f), nvx, nvp, L)[0]
+    ext = np.stack([_ghost_x(f, c, bc, nvx, nvp) for c in range(-1, nx + 1)])  # columns -1 .. nx
+    s = _minmod(ext[1:-1] - ext[:-2], ext[2:] - ext[1:-1])                     # slopes of columns 0 .. nx-1
+    M, _, _, r0, rn = _column_sums(f, nvx, nvp, L)
+    _, Ap, _, _, _ = _column_sums(f + 0.5 * s, nvx, nvp, L)
+    _, _, An, _, _ = _column_sums(f - 0.5 * s, nvx, nvp, L)
+    dvx, nu = 2 * L / nvx, dt / (2.0 / nx)
+    nuv, Em = dt / dvx, np.max(np.abs(E))
+    if bc == O.BC_OUTFLOW:  # the edge columns' slopes vanish
+        assert np.all(s[0] == 0) and np.all(s[nx - 1] == 0)
+    Q = np.zeros((nx, 5))
+    Q[:, 1] = -dvx * (E * (M[:, 0] - 0.5 * (r0 + rn)) - Em * 0.5 * (rn - r0))
+    Q[:, 4] = -dvx * (E * (2 * M[:, 1] - L * (rn - r0)) - Em * (L * (r0 + rn) - dvx * M[:, 0]))
+
+    def predict(Ap, An):
+        sg = np.array([-1.0, 1.0, -1.0, -1.0, -1.0])
+        if bc == O.BC_PERIODIC:
+            Apg, Ang = Ap[nx - 1], An[0]
+        elif bc == O.BC_OUTFLOW:
+            Apg, Ang = Ap[0], An[nx - 1]
+        else:
+            Apg, Ang = sg * An[0], sg * Ap[nx - 1]
+        return M - nu * (Ap - np.vstack([Apg, Ap[:-1]]) + np.vstack([An[1:], Ang]) - An) - nuv * Q
+
+    assert np.max(np.abs(predict(Ap, An) - want)) < 1e-13 * np.max(np.abs(want))
+    # the limiter matters here: the unlimited (upwind) sums give another answer
+    _, Ap0, An0, _, _ = _column_sums(f, nvx, nvp, L)
+    assert np.max(np.abs(predict(Ap0, An0) - want)) > 1e-6 * np.max(np.abs(want))
