@@ -790,36 +790,42 @@ struct FuOps<double> {
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 
+constexpr int MB_CHECK = 5;     // mbarrier of the failure-detection check
+constexpr int MU_SLOTS = 5;     // column slots of the MUSCL walk (upwind: 3)
+
 struct FuShared {
     DF red[2][8][12];            // per-warp sums (<= 256 threads), by column parity (8-byte A)
-    unsigned long long mbar[4];  // column slots 0..2; 3: failure-detection check
+    unsigned long long mbar[6];  // column slots 0..4; MB_CHECK: failure-detection check
 };
 
 // Byte offsets of the walk's tables after FuShared (host and device); es is
-// the element size of f (4 or 8).
+// the element size of f (4 or 8).  A MUSCL walk of S columns computes S + 2
+// (its neighbours on both sides too) and keeps five column slots.
 struct FuLayout {
     size_t rs, tot, par, vxe, eyz, slots, total;
 };
 
 __host__ __device__ inline size_t fu_al16(size_t x) { return (x + 15) / 16 * 16; }
 
-__host__ __device__ inline FuLayout fu_layout(int nvp, int R, int S, int es)
+__host__ __device__ inline FuLayout fu_layout(int nvp, int R, int S, int es, int scheme = 0)
 {
     FuLayout L;
+    const int Wc = scheme ? S + 2 : S;                 // computed columns
+    const int nslot = scheme ? MU_SLOTS : 3;
     size_t o = fu_al16(sizeof(FuShared));
-    L.rs = o;                                          // A [(S+2)][NQ]: rank sums of columns i0-1 .. i0+S
-    o = fu_al16(o + (size_t)(S + 2) * NQ * 8);
-    L.tot = o;                                         // A [S][5]: P(f*) of each column
-    o = fu_al16(o + (size_t)S * 5 * 8);
-    L.par = o;                                         // T [S][8]: Maxwellian parameters (double path)
-    o = fu_al16(o + (size_t)S * 8 * es);
-    L.vxe = o;                                         // T2 [S][R]: (v_x, b pref ex) of the CTA's rows
-    o = fu_al16(o + (size_t)S * R * 2 * es);
-    L.eyz = o;                                         // T [S][2 nvp]: ey, ez
-    o += (size_t)S * 2 * nvp * es;
+    L.rs = o;                                          // A [(Wc+2)][NQ]: rank sums of the computed columns and one each side
+    o = fu_al16(o + (size_t)(Wc + 2) * NQ * 8);
+    L.tot = o;                                         // A [Wc][5]: P(f*) of each column
+    o = fu_al16(o + (size_t)Wc * 5 * 8);
+    L.par = o;                                         // T [Wc][8]: Maxwellian parameters (double path)
+    o = fu_al16(o + (size_t)Wc * 8 * es);
+    L.vxe = o;                                         // T2 [Wc][R]: (v_x, b pref ex) of the CTA's rows
+    o = fu_al16(o + (size_t)Wc * R * 2 * es);
+    L.eyz = o;                                         // T [Wc][2 nvp]: ey, ez
+    o += (size_t)Wc * 2 * nvp * es;
     o = (o + 127) / 128 * 128;
-    L.slots = o;                                       // T [3][R+2][nvp^2]
-    o += (size_t)3 * (R + 2) * nvp * nvp * es;
+    L.slots = o;                                       // T [nslot][R+2][nvp^2]
+    o += (size_t)nslot * (R + 2) * nvp * nvp * es;
     L.total = o;
     return L;
 }
@@ -901,41 +907,66 @@ __device__ __forceinline__ void fu_row(FuAcc<T, VEC>& s, const Pack<T, VEC>& v, 
     if (r == nvx - 1) s.en = vs;
 }
 
+// One exchange of the transposed butterfly over lane bit w: lanes with the
+// bit clear keep values 0..n-1 and send n..2n-1 (the others the reverse); each
+// keeps the sum of its half with its partner's.
+template <int n, typename T>
+__device__ __forceinline__ void fu_xchg(T (&x)[16], int lane, int w)
+{
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        const T send = up ? x[j] : x[j + n];
+        const T keep = up ? x[j + n] : x[j];
+        x[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+}
+
 // CTA sums of the accumulators into the 17 partials of one column at dst
 // (threads < NQ write): M from every row; A into A+ (rows with v_x > 0) or A-
 // (the other CTAs); the end-row densities from the CTAs holding those rows.
+// S0, R1, R2: sum f, sum v_x vs, sum v_x^2 vs; Tx, RA2, RA3: sum v_x g,
+// sum v_x^2 gs, sum v_x^3 gs of the values g the half sums A take (f for
+// upwind fluxes, f +- s/2 for MUSCL).
 template <typename T, int VEC>
-__device__ __forceinline__ void fu_reduce(const FuAcc<T, VEC>& s, const T (&vy)[VEC], const T (&vz)[VEC],
-                                          const T (&vp2)[VEC], typename FuOps<T>::A (*red)[12], bool posc,
-                                          bool has0, bool hasn, typename FuOps<T>::A* __restrict__ dst)
+__device__ __forceinline__ void fu_reduce_sums(const T (&S0)[VEC], const T (&Tx)[VEC], T R1, T R2, T RA2, T RA3,
+                                               T e0, T en, const T (&vy)[VEC], const T (&vz)[VEC],
+                                               const T (&vp2)[VEC], typename FuOps<T>::A (*red)[12], bool posc,
+                                               bool has0, bool hasn, typename FuOps<T>::A* __restrict__ dst)
 {
     using O = FuOps<T>;
     T val[12];
     val[0] = val[2] = val[3] = val[4] = val[5] = val[7] = val[8] = val[9] = T(0);
 #pragma unroll
     for (int l = 0; l < VEC; ++l) {
-        val[0] += s.S0[l];
-        val[2] += vy[l] * s.S0[l];
-        val[3] += vz[l] * s.S0[l];
-        val[4] += vp2[l] * s.S0[l];
-        val[5] += s.Tx[l];
-        val[7] += vy[l] * s.Tx[l];
-        val[8] += vz[l] * s.Tx[l];
-        val[9] += vp2[l] * s.Tx[l];
+        val[0] += S0[l];
+        val[2] += vy[l] * S0[l];
+        val[3] += vz[l] * S0[l];
+        val[4] += vp2[l] * S0[l];
+        val[5] += Tx[l];
+        val[7] += vy[l] * Tx[l];
+        val[8] += vz[l] * Tx[l];
+        val[9] += vp2[l] * Tx[l];
     }
-    val[1] = s.R1;
-    val[4] += s.R2;
-    val[6] = s.R2;
-    val[9] += s.R3;
-    val[10] = s.e0;
-    val[11] = s.en;
+    val[1] = R1;
+    val[4] += R2;
+    val[6] = RA2;
+    val[9] += RA3;
+    val[10] = e0;
+    val[11] = en;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // transposed butterfly: each exchange halves the values a lane keeps, so
+    // 8 + 4 + 2 + 1 + 1 shuffles leave lanes 2q, 2q+1 with the warp sum of
+    // value q (12..15 are padding)
+    T x[16];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-        if (q >= 10 && !(q == 10 ? has0 : hasn)) continue;  // uniform over the CTA
-        const T v = warp_sum_t(val[q]);
-        if (lane == 0) red[w][q] = O::from(v);
-    }
+    for (int q = 0; q < 16; ++q) x[q] = q < 12 ? val[q] : T(0);
+    fu_xchg<8>(x, lane, 16);
+    fu_xchg<4>(x, lane, 8);
+    fu_xchg<2>(x, lane, 4);
+    fu_xchg<1>(x, lane, 2);
+    x[0] += __shfl_xor_sync(0xffffffffu, x[0], 1);
+    if (!(lane & 1) && lane < 24) red[w][lane >> 1] = O::from(x[0]);
     __syncthreads();
     if (threadIdx.x < NQ) {
         const int q = threadIdx.x;
@@ -951,6 +982,14 @@ __device__ __forceinline__ void fu_reduce(const FuAcc<T, VEC>& s, const T (&vy)[
         }
         dst[q] = a;
     }
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void fu_reduce(const FuAcc<T, VEC>& s, const T (&vy)[VEC], const T (&vz)[VEC],
+                                          const T (&vp2)[VEC], typename FuOps<T>::A (*red)[12], bool posc,
+                                          bool has0, bool hasn, typename FuOps<T>::A* __restrict__ dst)
+{
+    fu_reduce_sums(s.S0, s.Tx, s.R1, s.R2, s.R2, s.R3, s.e0, s.en, vy, vz, vp2, red, posc, has0, hasn, dst);
 }
 
 // Uniform per-column constants of the pass.
@@ -1032,11 +1071,12 @@ __device__ __forceinline__ void fu_init_mbar(unsigned char* fsm, int poison)
     FuShared& sh = *reinterpret_cast<FuShared*>(fsm);
     const uint32_t mbar0 = smem_addr(&sh.mbar[0]);
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k <= MB_CHECK; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar0 + 8u * k), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (poison)  // 16 bytes that no copy delivers: the wait on it runs out
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar0 + 24u), "r"(16)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar0 + 8u * MB_CHECK),
+                         "r"(16)
                          : "memory");
     }
     __syncthreads();
@@ -1275,9 +1315,449 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
     }
 }
 
+// ---- fused single-pass step with MUSCL-minmod x fluxes ----
+//
+// The interface value on the upwind side of face c+1/2 is f_c + s_c/2
+// (v_x > 0) or f_{c+1} - s_{c+1}/2 (v_x <= 0), s_c = minmod(f_c - f_{c-1},
+// f_{c+1} - f_c), so the column-sum identity of the upwind step holds with
+// A+ and A- taken of f + s/2 and f - s/2 (v_x Rusanov fluxes unchanged).  The
+// 17 partials keep their layout; the slope of f^{n+1} in column c needs
+// f^{n+1} of columns c-1 and c+1, so a walk also computes (without storing
+// them) the column on each side of its own, keeps each lane's last two
+// outputs in registers, and writes the sums of column c-1 once column c is
+// computed.  The transport of column c reads f^n of columns c-2 .. c+1
+// (v_x > 0) or c-1 .. c+2 (v_x <= 0): five column slots rotate, four in use
+// and the next copy in flight.  Periodic and outflow boundaries: an outflow
+// edge column's slope is zero (its ghost repeats it), so a wall's outside
+// neighbour is not computed; a reflecting wall keeps the clustered step.
+
+// Branch-free minmod: the value of smaller magnitude when a and b have the
+// same sign, else 0 (equal to minmod() for every finite pair).
+__device__ __forceinline__ float mm2(float a, float b) { return fminf(fmaxf(b, fminf(a, 0.0f)), fmaxf(a, 0.0f)); }
+__device__ __forceinline__ double mm2(double a, double b) { return fmin(fmax(b, fmin(a, 0.0)), fmax(a, 0.0)); }
+__device__ __forceinline__ float mmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float mmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double mmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ double mmax(double a, double b) { return fmax(a, b); }
+
+// Sums of one column of f^{n+1} (values h of its rows) with the limited
+// half-sum values g = h +- s/2 (sign + for rows with v_x > 0).
+template <typename T, int VEC>
+struct FuAccM {
+    T S0[VEC], Tx[VEC], R1, R2, RA2, RA3, e0, en;
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ void fu_clear(FuAccM<T, VEC>& s)
+{
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) s.S0[l] = s.Tx[l] = T(0);
+    s.R1 = s.R2 = s.RA2 = s.RA3 = s.e0 = s.en = T(0);
+}
+
+// One row of a column's sums: h its values, g the limited values.
+template <bool BND, typename T, int VEC>
+__device__ __forceinline__ void fu_row_m(FuAccM<T, VEC>& s, const T (&h)[VEC], const T (&g)[VEC], T vx, int r,
+                                         int nvx)
+{
+    T vs = T(0), gs = T(0);
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) {
+        s.S0[l] += h[l];
+        s.Tx[l] = tfma(vx, g[l], s.Tx[l]);
+        vs += h[l];
+        gs += g[l];
+    }
+    const T vx2 = vx * vx;
+    s.R1 = tfma(vx, vs, s.R1);
+    s.R2 = tfma(vx2, vs, s.R2);
+    s.RA2 = tfma(vx2, gs, s.RA2);
+    s.RA3 = tfma(vx2 * vx, gs, s.RA3);
+    if (BND) {
+        if (r == 0) s.e0 = vs;
+        if (r == nvx - 1) s.en = vs;
+    }
+}
+
+// One computed column's pass over the thread's rows [ra, rb) (at most RG):
+// f* from the limited x fluxes and the v_x Rusanov flux, f^{n+1} = a f* + b M
+// stored when `out` is set.  cen: this column's slot with its row halo; x1,
+// xf: the upwind neighbour and the one beyond it; xd: the downwind
+// neighbour; sgn = +1 for rows with v_x > 0, -1 otherwise.  With the
+// differences e = f_c - f_x1, d1 = f_xd - f_c, d2 = f_x1 - f_xf the flux
+// difference over v_x is sgn (e + (minmod(e, d1) - minmod(e, d2)) / 2) for
+// either sign (minmod is odd), so one formula serves both.  With `sums`, the
+// sums of the previous computed column h1 (slope from dd = h1 - its own
+// predecessor and this column's f^{n+1} - h1); then dd <- f^{n+1} - h1 (0 when
+// `dup`: the first column next to an outflow wall) and h1 <- f^{n+1}.
+template <bool BND, int NVPC, int RG, typename T, int VEC>
+__device__ __forceinline__ void fu_pass_m(const T* __restrict__ cen, const T* __restrict__ x1s,
+                                          const T* __restrict__ xfs, const T* __restrict__ xds, T* __restrict__ out,
+                                          const typename FuOps<T>::T2* __restrict__ vxe, int ra, int rb, int r0,
+                                          int nvx, int nvp2_rt, const FuCol<T>& k, T sgn, const T (&myz)[VEC],
+                                          bool sums, bool dup, T (&h1)[RG][VEC], T (&dd)[RG][VEC],
+                                          FuAccM<T, VEC>& acc)
+{
+    const int nvp2 = NVPC > 0 ? NVPC * NVPC : nvp2_rt;
+    const T nus = sgn * k.nu, hs = T(0.5) * sgn;
+    Pack<T, VEC> dnv, cv;
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) dnv.x[l] = T(0);
+    if (!BND || ra > 0) dnv = ldv<T, VEC>(cen + (size_t)(ra - r0) * nvp2);
+    cv = ldv<T, VEC>(cen + (size_t)(ra - r0 + 1) * nvp2);
+    const size_t o = (size_t)(ra - r0 + 1) * nvp2;  // row ra in a slot
+#pragma unroll
+    for (int i = 0; i < RG; ++i) {
+        const int r = ra + i;
+        if (r < rb) {
+            Pack<T, VEC> up;
+            if (!BND || r < nvx - 1) up = ldv<T, VEC>(cen + o + (size_t)(i + 1) * nvp2);
+            else {
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) up.x[l] = T(0);
+            }
+            const typename FuOps<T>::T2 ve = vxe[r - r0];
+            const T vx = ve.x, nvx_ = nus * ve.x;
+            const Pack<T, VEC> a1 = ldv<T, VEC>(x1s + o + (size_t)i * nvp2);
+            const Pack<T, VEC> af = ldv<T, VEC>(xfs + o + (size_t)i * nvp2);
+            const Pack<T, VEC> ad = ldv<T, VEC>(xds + o + (size_t)i * nvp2);
+            T v[VEC];
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+                const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                const T e = cc - a1.x[l], d1 = ad.x[l] - cc, d2 = a1.x[l] - af.x[l];
+                const T lo = mmin(e, T(0)), hi = mmax(e, T(0));  // minmod(e, x) = x clamped to [lo, hi]
+                const T D = tfma(T(0.5), mmin(mmax(d1, lo), hi) - mmin(mmax(d2, lo), hi), e);
+                T fs = tfma(-nvx_, D, cc);
+                if (!BND || (r > 0 && r < nvx - 1)) {
+                    fs = tfma(-k.gE, u - d, fs);
+                    fs = tfma(k.gM, tfma(T(-2), cc, u + d), fs);
+                } else {
+                    const T Gr = r < nvx - 1 ? k.hE * (cc + u) - k.hEm * (u - cc) : T(0);
+                    const T Gl = r > 0 ? k.hE * (d + cc) - k.hEm * (cc - d) : T(0);
+                    fs = tfma(-k.nuv, Gr - Gl, fs);
+                }
+                v[l] = tfma(k.a, fs, ve.y * myz[l]);
+            }
+            if (out) {
+                Pack<T, VEC> pv;
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) pv.x[l] = v[l];
+                stv<T, VEC>(out + (size_t)r * nvp2, pv);
+            }
+            T dn[VEC];
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) dn[l] = v[l] - h1[i][l];
+            if (sums) {
+                T g[VEC];
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) g[l] = tfma(hs, mm2(dd[i][l], dn[l]), h1[i][l]);
+                fu_row_m<BND>(acc, h1[i], g, vx, r, nvx);
+            }
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+                dd[i][l] = dn[l];
+                h1[i][l] = v[l];
+            }
+            dnv = cv;
+            cv = up;
+        }
+    }
+    if (dup)
+#pragma unroll
+        for (int i = 0; i < RG; ++i)
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) dd[i][l] = T(0);
+}
+
+// Sums of the last computed column h1 next to an outflow wall (slope zero).
+template <bool BND, int RG, typename T, int VEC>
+__device__ __forceinline__ void fu_sums_edge(const typename FuOps<T>::T2* __restrict__ vxe, int ra, int rb, int r0,
+                                             int nvx, const T (&h1)[RG][VEC], FuAccM<T, VEC>& acc)
+{
+#pragma unroll
+    for (int i = 0; i < RG; ++i) {
+        const int r = ra + i;
+        if (r < rb) fu_row_m<BND>(acc, h1[i], h1[i], vxe[r - r0].x, r, nvx);
+    }
+}
+
+// One MUSCL walk: columns [wk S, wk S + S) of instance b, as fused_walk
+// (same arguments, partials and completion rule).
+template <typename T, int NVPC, int RG>
+__device__ __forceinline__ void fused_walk_m(const FInst* __restrict__ insts, const FGeom& g,
+                                             const int* __restrict__ cur, int b, int wk, int rank, int C, int step,
+                                             int* __restrict__ status, long long wait_ns, uint32_t& phase,
+                                             unsigned char* fsm)
+{
+    using O = FuOps<T>;
+    using A = typename O::A;
+    using T2 = typename O::T2;
+    constexpr int VEC = 16 / (int)sizeof(T);
+    const FInst& I = insts[b];
+    const int S = g.march, nx = I.nx, bc = I.bc;
+    const int i0 = wk * S, i1 = min(i0 + S, nx);
+    const int nvx = g.nvx, nvp = NVPC > 0 ? NVPC : g.nvp, nvp2 = nvp * nvp;
+    const long long ncol = g.ncol;
+    const int R = g.rows;
+    const int r0 = rank * R, r1 = min(r0 + R, nvx), nr = r1 - r0;
+    const bool posc = r0 >= I.hpos;  // all rows of this CTA have v_x > 0 (else all <= 0)
+    const size_t slot_elems = (size_t)(R + 2) * nvp2;
+    // computed columns cs..ce: the walk's own and its neighbours, except
+    // outside an outflow wall
+    const bool wallL = bc != 0 && i0 == 0, wallR = bc != 0 && i1 == nx;
+    const int cs = wallL ? i0 : i0 - 1, ce = wallR ? i1 - 1 : i1, Wc = ce - cs + 1;
+    const int back = posc ? 2 : 1;  // column c reads columns c-back .. c-back+3
+    const int L0 = cs - back, Lend = ce - back + 3;
+
+    FuShared& sh = *reinterpret_cast<FuShared*>(fsm);
+    A (*red)[8][12] = reinterpret_cast<A (*)[8][12]>(&sh.red[0][0][0]);
+    const FuLayout lay = fu_layout(nvp, R, S, (int)sizeof(T), 1);
+    A* rs = reinterpret_cast<A*>(fsm + lay.rs);
+    A* tot = reinterpret_cast<A*>(fsm + lay.tot);
+    T* par = reinterpret_cast<T*>(fsm + lay.par);
+    T2* vxe = reinterpret_cast<T2*>(fsm + lay.vxe);
+    T* eyz = reinterpret_cast<T*>(fsm + lay.eyz);
+    T* slots = reinterpret_cast<T*>(fsm + lay.slots);
+    const uint32_t mbar0 = smem_addr(&sh.mbar[0]);
+
+    const int Lr = nvp2 / VEC, G = g.groups;
+    const int q = threadIdx.x % Lr, grp = threadIdx.x / Lr;
+    const int jp = q * VEC;
+    const int Rg = (nr + G - 1) / G;
+    const int ra = r0 + grp * Rg, rb = min(ra + Rg, r1);
+    const bool active = grp < G && ra < rb;
+    const int bufi = cur[b] ^ (step & 1);
+    const T* __restrict__ fin = static_cast<const T*>(I.f[bufi]);
+    T* __restrict__ fout = static_cast<T*>(I.f[bufi ^ 1]);
+    const A* __restrict__ pin = static_cast<const A*>(I.part[bufi]);
+    A* __restrict__ pout = static_cast<A*>(I.part[bufi ^ 1]);
+    const int ha = max(r0 - 1, 0), hb = min(r1 + 1, nvx);
+
+    auto slot_of = [&](int c) { return (c - L0) % MU_SLOTS; };
+    // column c (through the boundary rule: periodic wrap or outflow repeat)
+    // into its slot with one bulk copy by thread 0
+    auto load = [&](int c) {
+        bool mir;
+        const int sc = ghost_col(c, nx, bc, &mir);
+        if (threadIdx.x == 0) {
+            T* dst = slots + (size_t)slot_of(c) * slot_elems;
+            const T* col = fin + (size_t)sc * ncol;
+            const uint32_t mb = mbar0 + 8u * (uint32_t)slot_of(c);
+            const uint32_t bytes = (uint32_t)(hb - ha) * nvp2 * (uint32_t)sizeof(T);
+            fence_proxy_async();
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(dst + (size_t)(ha - (r0 - 1)) * nvp2)),
+                "l"(col + (size_t)ha * nvp2), "r"(bytes), "r"(mb)
+                : "memory");
+        }
+    };
+
+    uint32_t pend = 0;
+    for (int c = L0; c < L0 + MU_SLOTS && c <= Lend; ++c) {
+        load(c);
+        pend |= 1u << slot_of(c);
+    }
+
+    // the Maxwellians of the computed columns, while the copies land: rank
+    // sums of the partials of columns cs-1 .. ce+1, then P(f*) per column
+    const T* vt = static_cast<const T*>(I.vtab);
+    for (int t = threadIdx.x; t < (Wc + 2) * NQ; t += blockDim.x) {
+        const int j = t / NQ, qq = t - j * NQ;
+        bool mir;
+        const int src = ghost_col(cs - 1 + j, nx, bc, &mir);
+        rs[t] = part_rank_sum<T>(pin + (size_t)src * C * NQ + qq, C);
+    }
+    __syncthreads();
+    const T nu = scal<T>(I.nu, I.fnu), nuv = scal<T>(I.nuv, I.fnuv), Emax = scal<T>(I.Emax, I.fEmax);
+    for (int t5 = threadIdx.x; t5 < Wc * 5; t5 += blockDim.x) {
+        const int j = t5 / 5, k = t5 - 5 * j;
+        bool mir;
+        const int c = ghost_col(cs + j, nx, bc, &mir);
+        const A* Mc = rs + (size_t)(j + 1) * NQ;
+        const A* Lc = rs + (size_t)j * NQ;
+        const A* Rc = rs + (size_t)(j + 2) * NQ;
+        const A fl = O::add(O::sub(Mc[5 + k], Lc[5 + k]), O::sub(Rc[10 + k], Mc[10 + k]));
+        A t = O::sub(Mc[k], O::scale(fl, nu));
+        if (k == 1 || k == 4) {
+            const T dvx = (T)I.dvx, Lb = (T)I.L, E = scal<T>(I.E[c], I.Ef[c]);
+            const T M0 = O::val(Mc[0]), M1 = O::val(Mc[1]);
+            const T e0 = O::val(Mc[15]), en = O::val(Mc[16]);
+            const T Q = k == 1 ? -dvx * (E * (M0 - T(0.5) * (e0 + en)) - Emax * T(0.5) * (en - e0))
+                               : -dvx * (E * (T(2) * M1 - Lb * (en - e0)) - Emax * (Lb * (e0 + en) - dvx * M0));
+            t = O::sub(t, O::from(nuv * Q));
+        }
+        tot[j * 5 + k] = t;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < Wc; j += blockDim.x) {
+        const int c = cs + j;
+        fu_params(tot + j * 5, par + j * 8, I, I.collide && rank == 0 && c >= i0 && c < i1, status);
+    }
+    __syncthreads();
+    const bool collide = I.collide != 0;
+    const T bb = scal<T>(I.b, I.fb);
+    for (int t = threadIdx.x; t < Wc * (nr + 2 * nvp); t += blockDim.x) {
+        const int j = t / (nr + 2 * nvp), k = t - j * (nr + 2 * nvp);
+        const T* pj = par + j * 8;
+        if (k < nr) {
+            const T vx = vt[r0 + k];
+            T2 e;
+            e.x = vx;
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const FPar& P = *reinterpret_cast<const FPar*>(tot + j * 5);
+                const F2* vp = reinterpret_cast<const F2*>(I.vpair);
+                e.y = collide ? gauss_f2(vp[r0 + k], P.u[0], P.i2t, f2_mul(F2{(float)bb, 0.0f}, P.pref)) : T(0);
+            } else {
+                const T cx = vx - pj[1];
+                e.y = collide ? bb * pj[5] * texp(-cx * cx * pj[6]) : T(0);
+            }
+            vxe[j * R + k] = e;
+        } else {
+            const int m = k - nr < nvp ? k - nr : k - nr - nvp;
+            T val;
+            if constexpr (sizeof(T) == sizeof(float)) {
+                const FPar& P = *reinterpret_cast<const FPar*>(tot + j * 5);
+                const F2* vp = reinterpret_cast<const F2*>(I.vpair);
+                val = gauss_f2(vp[nvx + m], P.u[k - nr < nvp ? 1 : 2], P.i2t, F2{1.0f, 0.0f});
+            } else {
+                const T cc = vt[nvx + m * nvp] - (k - nr < nvp ? pj[2] : pj[3]);
+                val = texp(-cc * cc * pj[6]);
+            }
+            eyz[j * 2 * nvp + (k - nr)] = collide ? val : T(0);
+        }
+    }
+    T vy[VEC], vz[VEC], vp2[VEC];
+    int jy[VEC], jz[VEC];
+    {
+        int y = jp / nvp, z = jp - (jp / nvp) * nvp;
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+            vy[l] = active ? vt[nvx + jp + l] : T(0);
+            vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
+            vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
+            jy[l] = y;
+            jz[l] = z;
+            if (++z == nvp) {
+                z = 0;
+                ++y;
+            }
+        }
+    }
+    FuCol<T> kc;
+    kc.nu = nu;
+    kc.nuv = nuv;
+    kc.hEm = T(0.5) * Emax;
+    kc.gM = nuv * kc.hEm;
+    kc.a = collide ? scal<T>(I.a, I.fa) : T(1);
+    const bool has0 = r0 == 0, hasn = r1 == nvx, bnd = has0 || hasn;
+    T h1[RG][VEC], dd[RG][VEC];
+#pragma unroll
+    for (int i = 0; i < RG; ++i)
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) h1[i][l] = dd[i][l] = T(0);
+    const T sgn = posc ? T(1) : T(-1);
+    __syncthreads();  // tables visible
+
+    for (int c = cs; c <= ce; ++c) {
+        const int j = c - cs;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int s = slot_of(c - back + k);
+            if (pend & (1u << s)) {
+                const uint32_t mb = mbar0 + 8u * (uint32_t)s, ph = (phase >> s) & 1u;
+                if (!mbar_wait(mb, wait_ns, ph)) {
+                    atomicCAS(status, 0, ST_TIMEOUT);
+                    mbar_wait(mb, wait_ns, ph);  // let the copy land before the slot is reused
+                }
+                pend &= ~(1u << s);
+                phase ^= 1u << s;
+            }
+        }
+        const int dn = posc ? -1 : 1;  // the upwind side
+        const T* cen = slots + (size_t)slot_of(c) * slot_elems + jp;
+        const T* x1s = slots + (size_t)slot_of(c + dn) * slot_elems + jp;
+        const T* xfs = slots + (size_t)slot_of(c + 2 * dn) * slot_elems + jp;
+        const T* xds = slots + (size_t)slot_of(c - dn) * slot_elems + jp;
+        bool mir;
+        const int ec = ghost_col(c, nx, bc, &mir);
+        kc.hE = T(0.5) * scal<T>(I.E[ec], I.Ef[ec]);
+        kc.gE = nuv * kc.hE;
+        T myz[VEC];
+        {
+            const T* ey = eyz + j * 2 * nvp;
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) myz[l] = ey[jy[l]] * ey[nvp + jz[l]];
+        }
+        const bool own = c >= i0 && c < i1, sums = c - 1 >= i0 && c - 1 < i1, dup = c == cs && wallL;
+        FuAccM<T, VEC> acc;
+        fu_clear(acc);
+        if (active) {
+            T* out = own ? fout + (size_t)c * ncol + jp : nullptr;
+            const T2* ve = vxe + j * R;
+            if (bnd)
+                fu_pass_m<true, NVPC, RG>(cen, x1s, xfs, xds, out, ve, ra, rb, r0, nvx, nvp2, kc, sgn, myz, sums, dup,
+                                          h1, dd, acc);
+            else
+                fu_pass_m<false, NVPC, RG>(cen, x1s, xfs, xds, out, ve, ra, rb, r0, nvx, nvp2, kc, sgn, myz, sums,
+                                           dup, h1, dd, acc);
+        }
+        // the 17 sums of column c-1; the barrier ends every read of column
+        // c-back's slot, which the next copy overwrites
+        if (sums)
+            fu_reduce_sums(acc.S0, acc.Tx, acc.R1, acc.R2, acc.RA2, acc.RA3, acc.e0, acc.en, vy, vz, vp2,
+                           red[(c - 1) & 1], posc, has0, hasn, pout + ((size_t)(c - 1) * C + rank) * NQ);
+        else
+            __syncthreads();
+        {
+            const int nc = c - back + MU_SLOTS;
+            if (nc <= Lend) {
+                load(nc);
+                pend |= 1u << slot_of(nc);
+            }
+        }
+    }
+    if (wallR) {  // the last column's sums: its outside neighbour repeats it
+        FuAccM<T, VEC> acc;
+        fu_clear(acc);
+        if (active) {
+            const T2* ve = vxe + (ce - cs) * R;
+            if (bnd) fu_sums_edge<true>(ve, ra, rb, r0, nvx, h1, acc);
+            else fu_sums_edge<false>(ve, ra, rb, r0, nvx, h1, acc);
+        }
+        fu_reduce_sums(acc.S0, acc.Tx, acc.R1, acc.R2, acc.RA2, acc.RA3, acc.e0, acc.en, vy, vz, vp2,
+                       red[(i1 - 1) & 1], posc, has0, hasn, pout + ((size_t)(i1 - 1) * C + rank) * NQ);
+    }
+}
+
+// Walk of either scheme: MU = 0 upwind, MU > 0 MUSCL with at most MU v_x
+// rows per thread.
+template <typename T, int NVPC, int MU>
+__device__ __forceinline__ void fused_walk_any(const FInst* __restrict__ insts, const FGeom& g,
+                                               const int* __restrict__ cur, int b, int wk, int rank, int C, int step,
+                                               int* __restrict__ status, long long wait_ns, uint32_t& phase,
+                                               unsigned char* fsm)
+{
+    if constexpr (MU > 0) fused_walk_m<T, NVPC, MU>(insts, g, cur, b, wk, rank, C, step, status, wait_ns, phase, fsm);
+    else fused_walk<T, NVPC>(insts, g, cur, b, wk, rank, C, step, status, wait_ns, phase, fsm);
+}
+
+// Resident CTAs per SM the fused kernels are built for.
+template <typename T, int MU>
+constexpr int fu_min_blocks()
+{
+    return MU > 0 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 3 : 2);
+}
+
+// MUSCL rows per thread of the instantiated kernels (float: 4 lanes of 4
+// rows, double: 2 lanes of 8 rows; 32 registers of outputs either way).
+constexpr int MU_ROWS_F = 4, MU_ROWS_D = 8;
+
 // One launch per step: CTA (rank, walk, instance).
-template <typename T, int NVPC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+template <typename T, int NVPC, int MU>
+__global__ void __launch_bounds__(256, fu_min_blocks<T, MU>())
 k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
               int step, int* __restrict__ status, long long wait_ns, int poison)
 {
@@ -1286,11 +1766,12 @@ k_force_fused(const FInst* __restrict__ insts, FGeom g, const Active* __restrict
     extern __shared__ __align__(16) unsigned char fsm[];
     fu_init_mbar(fsm, poison);
     if (poison) {
-        const uint32_t mb = smem_addr(&reinterpret_cast<FuShared*>(fsm)->mbar[3]);
+        const uint32_t mb = smem_addr(&reinterpret_cast<FuShared*>(fsm)->mbar[MB_CHECK]);
         if (!mbar_wait(mb, wait_ns)) atomicCAS(status, 0, ST_TIMEOUT);
     }
     uint32_t phase = 0;
-    fused_walk<T, NVPC>(insts, g, cur, b, blockIdx.y, blockIdx.x, gridDim.x, step, status, wait_ns, phase, fsm);
+    fused_walk_any<T, NVPC, MU>(insts, g, cur, b, blockIdx.y, blockIdx.x, gridDim.x, step, status, wait_ns, phase,
+                                fsm);
 }
 
 // Wait (bounded by limit_ns) until the counter reaches target; acquire
@@ -1312,13 +1793,15 @@ __device__ __forceinline__ bool wait_count(const int* p, int target, long long l
 // k > 0 waits until every CTA of its walk and of the walks holding its two
 // neighbour columns has finished step k-1 (done[walk] >= C k): their f^k and
 // partials are then written, and their reads of the buffer this item
-// overwrites are over.  An item only waits on smaller tickets, taken by
+// overwrites are over.  (A MUSCL walk reads up to three columns past its
+// ends; every walk then has at least three columns, so those are still the
+// neighbour walks'.)  An item only waits on smaller tickets, taken by
 // running CTAs, so the lowest unfinished ticket never waits.  sync: [0]
 // ticket, [1 + b walks + w] done counts (zeroed before the launch).
 // poison (failure-detection check): the waits of step 1 ask for a count no
 // walk reaches, so they run out after wait_ns.
-template <typename T, int NVPC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+template <typename T, int NVPC, int MU>
+__global__ void __launch_bounds__(256, fu_min_blocks<T, MU>())
 k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, int* __restrict__ cur,
                   int nsteps, int* __restrict__ sync, int* __restrict__ status, long long wait_ns, int poison)
 {
@@ -1357,7 +1840,7 @@ k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __rest
             asm volatile("fence.proxy.async.global;" ::: "memory");  // the bulk copies read what others wrote
         }
         __syncthreads();
-        fused_walk<T, NVPC>(insts, g, cur, b, wk, rank, C, k, status, wait_ns, phase, fsm);
+        fused_walk_any<T, NVPC, MU>(insts, g, cur, b, wk, rank, C, k, status, wait_ns, phase, fsm);
         __syncthreads();  // every store of this walk issued
         if (threadIdx.x == 0) {
             __threadfence();
@@ -1369,7 +1852,7 @@ k_force_fused_run(const FInst* __restrict__ insts, FGeom g, const Active* __rest
 // Partials (the 17 column sums of the fused step) of the current state of
 // the active instances: one CTA per (rank, column, instance), rows read
 // straight from memory with 16-byte loads.
-template <typename T>
+template <typename T, bool MUSCL>
 __global__ void __launch_bounds__(256)
 k_force_sums(const FInst* __restrict__ insts, FGeom g, const Active* __restrict__ act, const int* __restrict__ cur)
 {
@@ -1397,12 +1880,38 @@ k_force_sums(const FInst* __restrict__ insts, FGeom g, const Active* __restrict_
         vz[l] = active ? vt[nvx + nvp2 + jp + l] : T(0);
         vp2[l] = active ? vt[nvx + 2 * nvp2 + jp + l] : T(0);
     }
-    FuAcc<T, VEC> acc;
-    fu_clear(acc);
-    if (active)
-        for (int r = ra; r < rb; ++r) fu_row(acc, ldv<T, VEC>(f + (size_t)r * nvp2), vt[r], r, nvx);
-    fu_reduce(acc, vy, vz, vp2, red, r0 >= I.hpos, r0 == 0, r1 == nvx,
-              static_cast<typename O::A*>(I.part[bi]) + ((size_t)i * C + rank) * NQ);
+    typename O::A* dst = static_cast<typename O::A*>(I.part[bi]) + ((size_t)i * C + rank) * NQ;
+    const bool posc = r0 >= I.hpos;
+    if constexpr (MUSCL) {
+        // the half sums of f +- s/2, s the minmod slope from the neighbour
+        // columns (periodic wrap or outflow repeat)
+        bool mir;
+        const T* fl = static_cast<const T*>(I.f[bi]) + (size_t)ghost_col(i - 1, I.nx, I.bc, &mir) * g.ncol + jp;
+        const T* fr = static_cast<const T*>(I.f[bi]) + (size_t)ghost_col(i + 1, I.nx, I.bc, &mir) * g.ncol + jp;
+        FuAccM<T, VEC> acc;
+        fu_clear(acc);
+        if (active)
+            for (int r = ra; r < rb; ++r) {
+                const Pack<T, VEC> c = ldv<T, VEC>(f + (size_t)r * nvp2);
+                const Pack<T, VEC> a = ldv<T, VEC>(fl + (size_t)r * nvp2);
+                const Pack<T, VEC> d = ldv<T, VEC>(fr + (size_t)r * nvp2);
+                T h[VEC], gv[VEC];
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) {
+                    h[l] = c.x[l];
+                    gv[l] = tfma(posc ? T(0.5) : T(-0.5), mm2(c.x[l] - a.x[l], d.x[l] - c.x[l]), c.x[l]);
+                }
+                fu_row_m<true>(acc, h, gv, vt[r], r, nvx);
+            }
+        fu_reduce_sums(acc.S0, acc.Tx, acc.R1, acc.R2, acc.RA2, acc.RA3, acc.e0, acc.en, vy, vz, vp2, red, posc,
+                       r0 == 0, r1 == nvx, dst);
+    } else {
+        FuAcc<T, VEC> acc;
+        fu_clear(acc);
+        if (active)
+            for (int r = ra; r < rb; ++r) fu_row(acc, ldv<T, VEC>(f + (size_t)r * nvp2), vt[r], r, nvx);
+        fu_reduce(acc, vy, vz, vp2, red, posc, r0 == 0, r1 == nvx, dst);
+    }
 }
 
 // Conserved moments (Eq. 18) of the current state from its partials, into
@@ -1571,14 +2080,19 @@ void* pick_step(int precision, int scheme, int vec)
 
 }  // namespace
 
-size_t force_fused_smem(int precision, int nvp, int rows, int walk)
+size_t force_fused_smem(int precision, int scheme, int nvp, int rows, int walk)
 {
-    return fu_layout(nvp, rows, walk, precision == 0 ? 8 : 4).total;
+    return fu_layout(nvp, rows, walk, precision == 0 ? 8 : 4, scheme).total;
 }
+
+int force_fused_muscl_rows(int precision) { return precision == 0 ? MU_ROWS_D : MU_ROWS_F; }
 
 bool force_fused_fits(int precision, int scheme, const FGeom& g)
 {
-    return scheme == 0 && g.bulk && g.vec == (precision == 0 ? 2 : 4) && g.threads <= 256 && g.C <= 16;
+    if (!(g.bulk && g.vec == (precision == 0 ? 2 : 4) && g.threads <= 256 && g.C <= 16)) return false;
+    if (scheme == 0) return true;
+    const int nr = std::min(g.rows, g.nvx), G = std::max(g.groups, 1);
+    return scheme == 1 && (nr + G - 1) / G <= force_fused_muscl_rows(precision);
 }
 
 int force_partials_per_column(const FGeom& g) { return g.C * NQ; }
@@ -1626,14 +2140,22 @@ cudaError_t prepare_force_kernels(int max_smem)
                                          max_smem - (int)fa.sharedSizeBytes);
                 cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             }
-    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<float, 0>),
-                           reinterpret_cast<const void*>(&k_force_fused<float, 16>),
-                           reinterpret_cast<const void*>(&k_force_fused_run<float, 0>),
-                           reinterpret_cast<const void*>(&k_force_fused_run<float, 16>),
-                           reinterpret_cast<const void*>(&k_force_fused<double, 0>),
-                           reinterpret_cast<const void*>(&k_force_fused<double, 16>),
-                           reinterpret_cast<const void*>(&k_force_fused_run<double, 0>),
-                           reinterpret_cast<const void*>(&k_force_fused_run<double, 16>)}) {
+    for (const void* fn : {reinterpret_cast<const void*>(&k_force_fused<float, 0, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused<float, 16, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<float, 0, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<float, 16, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused<double, 0, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused<double, 16, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<double, 0, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<double, 16, 0>),
+                           reinterpret_cast<const void*>(&k_force_fused<float, 0, MU_ROWS_F>),
+                           reinterpret_cast<const void*>(&k_force_fused<float, 16, MU_ROWS_F>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<float, 0, MU_ROWS_F>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<float, 16, MU_ROWS_F>),
+                           reinterpret_cast<const void*>(&k_force_fused<double, 0, MU_ROWS_D>),
+                           reinterpret_cast<const void*>(&k_force_fused<double, 16, MU_ROWS_D>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<double, 0, MU_ROWS_D>),
+                           reinterpret_cast<const void*>(&k_force_fused_run<double, 16, MU_ROWS_D>)}) {
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - (int)fa.sharedSizeBytes);
@@ -1648,12 +2170,14 @@ cudaError_t prepare_force_kernels(int max_smem)
     return cudaGetLastError();
 }
 
-int force_fused_occupancy(int precision, int threads, size_t smem, int* per_sm)
+int force_fused_occupancy(int precision, int scheme, int threads, size_t smem, int* per_sm)
 {
     int n = 0;
-    const cudaError_t e =
-        precision == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fused<double, 0>, threads, smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_force_fused<float, 0>, threads, smem);
+    const void* fn = precision == 0 ? (scheme ? reinterpret_cast<const void*>(&k_force_fused_run<double, 0, MU_ROWS_D>)
+                                              : reinterpret_cast<const void*>(&k_force_fused_run<double, 0, 0>))
+                                    : (scheme ? reinterpret_cast<const void*>(&k_force_fused_run<float, 0, MU_ROWS_F>)
+                                              : reinterpret_cast<const void*>(&k_force_fused_run<float, 0, 0>));
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return -1;
@@ -1693,15 +2217,16 @@ cudaError_t launch_force_step(int precision, int scheme, const FInst* insts, con
 {
     if (g.march > 0) {
         dim3 grid(g.C, (nx + g.march - 1) / g.march, n_inst);
+        const bool n16 = g.nvp == 16, mu = g.scheme != 0;
+#define FU_STEP(T, N, M) k_force_fused<T, N, M><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison)
         if (precision == 0) {
-            if (g.nvp == 16)
-                k_force_fused<double, 16><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
-            else k_force_fused<double, 0><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+            if (mu) n16 ? FU_STEP(double, 16, MU_ROWS_D) : FU_STEP(double, 0, MU_ROWS_D);
+            else n16 ? FU_STEP(double, 16, 0) : FU_STEP(double, 0, 0);
         } else {
-            if (g.nvp == 16)
-                k_force_fused<float, 16><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
-            else k_force_fused<float, 0><<<grid, g.threads, smem, s>>>(insts, g, act, cur, step, status, wait_ns, poison);
+            if (mu) n16 ? FU_STEP(float, 16, MU_ROWS_F) : FU_STEP(float, 0, MU_ROWS_F);
+            else n16 ? FU_STEP(float, 16, 0) : FU_STEP(float, 0, 0);
         }
+#undef FU_STEP
         return cudaGetLastError();
     }
     void* fn = pick_step(precision, scheme, g.vec);
@@ -1729,29 +2254,31 @@ cudaError_t launch_force_fused_run(int precision, const FInst* insts, const FGeo
 {
     cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * (size_t)sync_words, s);
     if (e != cudaSuccess || nsteps <= 0) return e;
+    const bool n16 = g.nvp == 16, mu = g.scheme != 0;
+#define FU_RUN(T, N, M) \
+    k_force_fused_run<T, N, M><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status, wait_ns, poison)
     if (precision == 0) {
-        if (g.nvp == 16)
-            k_force_fused_run<double, 16><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
-                                                                       wait_ns, poison);
-        else
-            k_force_fused_run<double, 0><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
-                                                                      wait_ns, poison);
+        if (mu) n16 ? FU_RUN(double, 16, MU_ROWS_D) : FU_RUN(double, 0, MU_ROWS_D);
+        else n16 ? FU_RUN(double, 16, 0) : FU_RUN(double, 0, 0);
     } else {
-        if (g.nvp == 16)
-            k_force_fused_run<float, 16><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
-                                                                      wait_ns, poison);
-        else
-            k_force_fused_run<float, 0><<<ctas, g.threads, smem, s>>>(insts, g, act, cur, nsteps, sync, status,
-                                                                     wait_ns, poison);
+        if (mu) n16 ? FU_RUN(float, 16, MU_ROWS_F) : FU_RUN(float, 0, MU_ROWS_F);
+        else n16 ? FU_RUN(float, 16, 0) : FU_RUN(float, 0, 0);
     }
+#undef FU_RUN
     return cudaGetLastError();
 }
 
 cudaError_t launch_force_sums(int precision, const FInst* insts, const FGeom& g, int nx, int n_inst,
                               const Active* act, const int* cur, cudaStream_t s)
 {
-    if (precision == 0) k_force_sums<double><<<dim3(g.C, nx, n_inst), g.threads, 0, s>>>(insts, g, act, cur);
-    else k_force_sums<float><<<dim3(g.C, nx, n_inst), g.threads, 0, s>>>(insts, g, act, cur);
+    const dim3 grid(g.C, nx, n_inst);
+    if (precision == 0) {
+        if (g.scheme) k_force_sums<double, true><<<grid, g.threads, 0, s>>>(insts, g, act, cur);
+        else k_force_sums<double, false><<<grid, g.threads, 0, s>>>(insts, g, act, cur);
+    } else {
+        if (g.scheme) k_force_sums<float, true><<<grid, g.threads, 0, s>>>(insts, g, act, cur);
+        else k_force_sums<float, false><<<grid, g.threads, 0, s>>>(insts, g, act, cur);
+    }
     return cudaGetLastError();
 }
 

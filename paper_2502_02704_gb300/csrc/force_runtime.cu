@@ -88,6 +88,7 @@ bool geometry(int precision, int scheme, int nvx, int nvp, int C, int max_thread
     if (g->threads > (g->vec == 1 ? 1024 : 512)) return false;
     g->buf_off = (int)prk::force_step_buf_off(precision, nvx, nvp);
     g->march = 0;
+    g->scheme = scheme;
     *smem = sm;
     return true;
 }
@@ -126,13 +127,15 @@ bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk
     size_t sm0;
     if (!geometry(b->precision, b->scheme, b->nvx, b->nvp, C, max_threads, g, &sm0)) return false;
     if (!prk::force_fused_fits(b->precision, b->scheme, *g)) return false;
-    for (const prk::FInst& I : b->h)
+    for (const prk::FInst& I : b->h) {
         if (I.hpos < b->nvx && I.hpos % g->rows != 0) return false;
+        if (b->scheme != 0 && I.bc == 2) return false;  // MUSCL: periodic and outflow only
+    }
     const size_t optin = (size_t)dev_attr(cudaDevAttrMaxSharedMemoryPerBlockOptin) - 1024;
     auto resident = [&](int S) {
-        const size_t sm = prk::force_fused_smem(b->precision, b->nvp, g->rows, S);
+        const size_t sm = prk::force_fused_smem(b->precision, b->scheme, b->nvp, g->rows, S);
         int per_sm = 0;
-        if (sm > optin || prk::force_fused_occupancy(b->precision, g->threads, sm, &per_sm) != 0) return 0;
+        if (sm > optin || prk::force_fused_occupancy(b->precision, b->scheme, g->threads, sm, &per_sm) != 0) return 0;
         return per_sm;
     };
     const int per1 = resident(1);
@@ -150,9 +153,20 @@ bool fused_geometry(const pr_force* b, int C, int max_threads, int walk_req, prk
         if (per1 == 1) S = std::max<long long>(2, S / 2);
     }
     S = std::max<long long>(1, std::min<long long>(S, cap));
-    const long long walks = (b->nx + S - 1) / S;
+    long long walks = (b->nx + S - 1) / S;
     S = (b->nx + walks - 1) / walks;
-    const size_t sm = prk::force_fused_smem(b->precision, b->nvp, g->rows, (int)S);
+    if (b->scheme != 0) {
+        // a MUSCL walk reads three columns past each end: every walk needs
+        // at least three so that those belong to its neighbour walks (the
+        // next longer walk whose last walk is long enough)
+        for (S = std::max<long long>(S, 3); S < b->nx; ++S) {
+            walks = (b->nx + S - 1) / S;
+            if (b->nx - (walks - 1) * S >= 3) break;
+        }
+        S = std::min<long long>(S, b->nx);
+        walks = (b->nx + S - 1) / S;
+    }
+    const size_t sm = prk::force_fused_smem(b->precision, b->scheme, b->nvp, g->rows, (int)S);
     if (resident((int)S) < 1) return false;
     g->march = (int)S;
     *out = gg;
@@ -173,7 +187,7 @@ int default_fused_cluster(const pr_force* b)
         prk::FGeom g;
         size_t sm;
         if (!fused_geometry(b, C, b->max_threads, 1, &g, &sm)) continue;
-        if (prk::force_fused_smem(b->precision, b->nvp, g.rows, std::min(8, b->nx)) <= half) return C;
+        if (prk::force_fused_smem(b->precision, b->scheme, b->nvp, g.rows, std::min(8, b->nx)) <= half) return C;
         if (!any) any = C;
     }
     return any;
@@ -183,7 +197,7 @@ int default_fused_cluster(const pr_force* b)
 int fused_resident(const pr_force* b)
 {
     int per_sm = 0;
-    if (prk::force_fused_occupancy(b->precision, b->g.threads, b->smem, &per_sm) != 0) return 0;
+    if (prk::force_fused_occupancy(b->precision, b->scheme, b->g.threads, b->smem, &per_sm) != 0) return 0;
     return per_sm * dev_attr(cudaDevAttrMultiProcessorCount);
 }
 

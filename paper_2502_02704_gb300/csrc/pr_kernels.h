@@ -142,19 +142,22 @@ struct FGeom {
     int bulk;                  // rows are 16-byte multiples: stage them with bulk copies
     int buf_off;               // shared-memory offset of the staging buffers
     int march;                 // > 0: fused single-pass step, a CTA walks this many x columns; 0: clustered step
+    int scheme;                // x fluxes: 0 upwind, 1 MUSCL-minmod
 };
 
 cudaError_t prepare_force_kernels(int max_smem);
 size_t force_step_smem(int precision, int scheme, int nvx, int nvp, int rows);
 size_t force_step_buf_off(int precision, int nvx, int nvp);
-// The fused single-pass step (upwind, 16-byte lanes, <= 256 threads; float
-// or double): its shared memory for a walk of `walk` columns, whether
-// geometry g can use it, the partials it keeps per column (8 bytes each), and
-// its resident CTAs per SM.
-size_t force_fused_smem(int precision, int nvp, int rows, int walk);
+// The fused single-pass step (upwind or MUSCL, 16-byte lanes, <= 256
+// threads; float or double): its shared memory for a walk of `walk` columns,
+// whether geometry g can use it (MUSCL: at most force_fused_muscl_rows v_x
+// rows per thread), the partials it keeps per column (8 bytes each), and its
+// resident CTAs per SM.
+size_t force_fused_smem(int precision, int scheme, int nvp, int rows, int walk);
 bool force_fused_fits(int precision, int scheme, const FGeom& g);
+int force_fused_muscl_rows(int precision);
 int force_partials_per_column(const FGeom& g);
-int force_fused_occupancy(int precision, int threads, size_t smem, int* per_sm);
+int force_fused_occupancy(int precision, int scheme, int threads, size_t smem, int* per_sm);
 // All nsteps fused steps of the active instances in one persistent launch of
 // `ctas` CTAs (at most the resident count); sync (sync_words ints: a ticket
 // and one done count per instance and walk) is zeroed on the stream first.

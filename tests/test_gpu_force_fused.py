@@ -39,13 +39,14 @@ def _problem(nx, nvx, nvp, L, bc, eps, n_inst=2):
     return insts, kins, initial
 
 
-def _run(insts, cluster, march, splits, initial, precision=pr.PR_MIXED):
+def _run(insts, cluster, march, splits, initial, precision=pr.PR_MIXED, scheme=pr.PR_UPWIND, persistent=-1):
     """Run the step counts in `splits` one after the other; every instance's f
     and moments and the walk length in use."""
-    b = pr.pr_force_create(insts, pr.PR_UPWIND, precision)
+    b = pr.pr_force_create(insts, scheme, precision)
     try:
         pr.pr_force_set_cluster(b, cluster)
         pr.pr_force_set_march(b, march)
+        pr.pr_force_set_persistent(b, persistent)
         used = pr.pr_force_get_march(b)
         for i, U in enumerate(initial):
             pr.pr_force_set_initial(b, i, U)
@@ -329,5 +330,184 @@ def test_force_step_setting_needs_a_force_problem():
         with pytest.raises(pr.PrError) as ei:
             pr.pr_set_force_step(ctx, 0, 4, 1)
         assert ei.value.code == pr.PR_EINVAL
+    finally:
+        pr.pr_destroy(ctx)
+
+
+# ------------------------------------------------------------ MUSCL fused step
+# Periodic and outflow boundaries; a CTA's rows per thread at most 4 (float)
+# or 8 (double).
+MU_GEOMS = [
+    (64, 16, 4),   # 16 rows per CTA: float 4 groups of 4 rows, double 2 of 8
+    (60, 16, 4),   # 15 rows: groups of 4, 4, 4, 3 (double 8, 7)
+    (48, 8, 6),    # 8 rows per CTA, one row per thread
+    (32, 4, 16),   # 2 rows per CTA, 32-thread CTAs
+]
+
+
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW])
+@pytest.mark.parametrize("nvx,nvp,cluster", MU_GEOMS)
+@pytest.mark.parametrize("eps", [1e-2, math.inf])
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_muscl_fused_step_matches_oracle_and_clustered_step(bc, nvx, nvp, cluster, eps, precision):
+    nx, L, n = 20, 7.0, 5
+    insts, kins, initial = _problem(nx, nvx, nvp, L, bc, eps)
+    for k in kins:
+        k.scheme = O.MUSCL
+    got, used = _run(insts, cluster, 7, (2, n - 2), initial, precision, pr.PR_MUSCL)
+    ref, used0 = _run(insts, cluster, 0, (n,), initial, precision, pr.PR_MUSCL)
+    assert used == 7 and used0 == 0
+    for k, ((f, V), (fr, Vr)) in enumerate(zip(got, ref)):
+        fo = O.v_fine_run(kins[k], insts[k].c.dt, n, O.v_lift(kins[k], initial[k]))
+        assert f_rel_err(f, fo) < FTOL[precision]
+        assert moment_rel_err(V, O.v_project(kins[k], fo, conserved=True)) < TOL[precision]
+        assert f_rel_err(f, fr) < FTOL[precision]
+        assert moment_rel_err(V, Vr) < TOL[precision]
+
+
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW])
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_muscl_walk_length_and_run_splits_give_the_same_bits(bc, precision):
+    # a walk's neighbour columns are computed with the arithmetic of the walk
+    # that owns them, and the partials kernel sums the limited values in the
+    # step's order
+    nx, nvx, nvp, L = 23, 64, 16, 7.0
+    insts, _, initial = _problem(nx, nvx, nvp, L, bc, 1e-3, n_inst=3)
+    ref, used = _run(insts, 4, 3, (6,), initial, precision, pr.PR_MUSCL)
+    assert used == 4   # walks of 3 would leave a last walk of 2 columns
+    for march, splits in ((1, (6,)), (5, (1, 1, 4)), (8, (2, 4)), (23, (6,)), (32, (3, 3))):
+        got, used = _run(insts, 4, march, splits, initial, precision, pr.PR_MUSCL)
+        assert used >= 3
+        for (f, V), (fr, Vr) in zip(got, ref):
+            assert np.array_equal(f, fr)
+            assert np.array_equal(V, Vr)
+    b = pr.pr_force_create(insts, pr.PR_MUSCL, precision)
+    try:
+        pr.pr_force_set_cluster(b, 4)
+        pr.pr_force_set_march(b, 3)
+        for i, U in enumerate(initial):
+            pr.pr_force_set_initial(b, i, U)
+        pr.pr_force_run(b, 2)
+        pr.pr_force_set_march(b, 7)   # the partials kernel recomputes the limited sums
+        pr.pr_force_run(b, 4)
+        for i, (fr, Vr) in enumerate(ref):
+            assert np.array_equal(pr.pr_force_get_f(b, i), fr)
+            assert np.array_equal(pr.pr_force_moments(b, i), Vr)
+    finally:
+        pr.pr_force_destroy(b)
+
+
+@pytest.mark.parametrize("bc", [pr.PR_BC_PERIODIC, pr.PR_BC_OUTFLOW])
+@pytest.mark.parametrize("nvx,nvp,cluster,march", [(64, 16, 4, 3), (64, 16, 4, 6), (48, 8, 6, 4), (32, 4, 16, 23)])
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_muscl_persistent_run_is_bitwise_the_stepwise_run(bc, nvx, nvp, cluster, march, precision):
+    nx, L, n = 23, 7.0, 7
+    insts, _, initial = _problem(nx, nvx, nvp, L, bc, 1e-3, n_inst=3)
+    out = [_run(insts, cluster, march, (1, n - 1), initial, precision, pr.PR_MUSCL, mode)[0] for mode in (0, 1)]
+    for (f, V), (fr, Vr) in zip(out[1], out[0]):
+        assert np.array_equal(f, fr)
+        assert np.array_equal(V, Vr)
+
+
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_muscl_fused_step_from_a_loaded_state_matches_oracle(precision):
+    # a rough state (the limiter active everywhere), outflow walls, and one
+    # walk over all columns next to walks of three
+    nx, nvx, nvp, L, n = 12, 64, 8, 8.0, 4
+    E = W.test3_force(nx)
+    kin = O.VKin(nx=nx, nvx=nvx, nvp=nvp, L=L, x0=0.0, x1=2.0, bc=O.BC_OUTFLOW, eps=1e-3, scheme=O.MUSCL, E=E)
+    dt = O.v_fine_dt_stab(kin, 0.5)
+    f0 = np.random.default_rng(7).random((nx, kin.ncol)) * O.v_lift(kin, _profile(nx))
+    fo = O.v_fine_run(kin, dt, n, f0)
+    for march in (3, 12):
+        b = pr.pr_force_create([pr.ForceInstance(nx, nvx, nvp, dt, L=L, x0=0.0, x1=2.0, bc=pr.PR_BC_OUTFLOW,
+                                                 eps=1e-3, E=E)], pr.PR_MUSCL, precision)
+        try:
+            pr.pr_force_set_cluster(b, 8)
+            pr.pr_force_set_march(b, march)
+            assert pr.pr_force_get_march(b) == march
+            pr.pr_force_set_f(b, 0, f0)
+            pr.pr_force_run(b, n)
+            f = pr.pr_force_get_f(b, 0)
+            V = pr.pr_force_moments(b, 0)
+        finally:
+            pr.pr_force_destroy(b)
+        assert f_rel_err(f, fo) < FTOL[precision]
+        assert moment_rel_err(V, O.v_project(kin, fo, conserved=True)) < TOL[precision]
+
+
+def test_muscl_fused_selection_rules():
+    nx, nvx, nvp = 12, 64, 16
+    E = W.test3_force(nx)
+    for precision in (pr.PR_MIXED, pr.PR_FP64):
+        inst = pr.ForceInstance(nx, nvx, nvp, 1e-3, L=8.0, x0=0.0, x1=2.0, E=E)
+        b = pr.pr_force_create([inst], pr.PR_MUSCL, precision)
+        try:
+            if precision == pr.PR_MIXED:
+                # 2 CTAs of 32 rows: more rows per thread than the kernel
+                # keeps (FP64 has no layout of 2 CTAs for this column at all)
+                pr.pr_force_set_cluster(b, 2)
+                with pytest.raises(pr.PrError) as ei:
+                    pr.pr_force_set_march(b, 4)
+                assert ei.value.code == pr.PR_EINVAL
+            pr.pr_force_set_cluster(b, 4)
+            pr.pr_force_set_march(b, 4)
+            assert pr.pr_force_get_march(b) == 4
+            pr.pr_force_set_march(b, 2)   # a walk reads three columns past its ends
+            assert pr.pr_force_get_march(b) == 3
+            pr.pr_force_set_march(b, 11)
+            assert pr.pr_force_get_march(b) == 6    # two equal walks
+        finally:
+            pr.pr_force_destroy(b)
+        # 10 columns: walks of 3 or 4 would leave a last walk of 1 or 2
+        b = pr.pr_force_create([pr.ForceInstance(10, nvx, nvp, 1e-3, L=8.0, x0=0.0, x1=2.0, E=E[:10])],
+                               pr.PR_MUSCL, precision)
+        try:
+            pr.pr_force_set_cluster(b, 4)
+            pr.pr_force_set_march(b, 3)
+            assert pr.pr_force_get_march(b) == 5
+        finally:
+            pr.pr_force_destroy(b)
+    # a reflecting wall keeps the clustered step
+    inst = pr.ForceInstance(nx, nvx, nvp, 1e-3, L=8.0, x0=0.0, x1=2.0, bc=pr.PR_BC_REFLECT, E=E)
+    b = pr.pr_force_create([inst], pr.PR_MUSCL, pr.PR_MIXED)
+    try:
+        pr.pr_force_set_cluster(b, 4)
+        assert pr.pr_force_get_march(b) == 0
+        with pytest.raises(pr.PrError) as ei:
+            pr.pr_force_set_march(b, 4)
+        assert ei.value.code == pr.PR_EINVAL
+    finally:
+        pr.pr_force_destroy(b)
+
+
+def test_muscl_test3_batch_uses_the_fused_step_by_default():
+    nx = 100
+    E = W.test3_force(nx)
+    insts = [pr.ForceInstance(nx, 256, 16, 6.25e-4, L=8.0, x0=0.0, x1=2.0, eps=1e-5, E=E) for _ in range(64)]
+    for precision in (pr.PR_MIXED, pr.PR_FP64):
+        b = pr.pr_force_create(insts, pr.PR_MUSCL, precision)
+        try:
+            assert pr.pr_force_config(b) == (16, 4096)   # 16 CTAs of 16 rows
+            assert pr.pr_force_get_march(b) >= 3
+        finally:
+            pr.pr_force_destroy(b)
+
+
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_muscl_force_parareal_on_the_fused_step_matches_oracle(precision):
+    nx, nvx, nvp, L, eps, T, N, K = 16, 32, 8, 6.0, 1e-2, 0.05, 6, 3
+    E = W.test3_force(nx)
+    U0 = _profile(nx)
+    k = O.VKin(nx=nx, nvx=nvx, nvp=nvp, L=L, x0=0.0, x1=2.0, eps=eps, scheme=O.MUSCL, E=E)
+    Uo, errs_o, _ = O.v_parareal(O.VParareal(kin=k, T=T, N=N), U0, K=K)
+    ctx = pr.pr_init_force(nx, 0.0, 2.0, pr.PR_BC_PERIODIC, nvx, nvp, L, eps, T, N, E, scheme=pr.PR_MUSCL,
+                           precision=precision)
+    try:
+        pr.pr_set_force_step(ctx, 4, 4, 1)
+        pr.pr_set_initial(ctx, U0)
+        kd, errs = pr.pr_parareal_run(ctx, K)
+        for n in range(N + 1):
+            assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < TOL[precision], n
     finally:
         pr.pr_destroy(ctx)
