@@ -435,14 +435,19 @@ int pr_force_set_threads(pr_force* b, int threads);
 
 /* Step kernel of the force path.  Two implementations give the same scheme:
  * the clustered step (a cluster of CTAs per x column: transport, exchange of
- * the moments of f* over distributed shared memory, relaxation) and, with
- * the upwind scheme (either precision), the fused single-pass step: the moments
- * of f* follow from 17 sums per column of f^n (upwind half sums of v_x f,
- * end-row densities; the v_x fluxes telescope), which every step writes next
- * to f^{n+1}, so each cell is read, relaxed and written in one pass and a CTA
- * walks `columns` consecutive x columns with the next column's bulk copy in
- * flight.  The fused step needs rows that are 16-byte multiples, at most 256
- * threads per CTA, and no CTA whose rows straddle v_x = 0.  columns = -1:
+ * the moments of f* over distributed shared memory, relaxation) and the fused
+ * single-pass step (either precision): the moments of f* follow from 17 sums
+ * per column of f^n (the upwind-side half sums of v_x f, end-row densities;
+ * the v_x fluxes telescope), which every step writes next to f^{n+1}, so each
+ * cell is read, relaxed and written in one pass and a CTA walks `columns`
+ * consecutive x columns with the next column's bulk copy in flight.  With
+ * MUSCL the half sums are of f +- s/2 (s the minmod slope, Eq. 13 with the
+ * limiter): a walk also computes, without storing, the column next to each
+ * of its ends to form the slopes of f^{n+1}, every walk has at least three
+ * columns, a thread holds at most 4 (float) or 8 (double) v_x rows, and a
+ * reflecting wall keeps the clustered step.  The fused step needs rows that
+ * are 16-byte multiples, at most 256 threads per CTA, and no CTA whose rows
+ * straddle v_x = 0.  columns = -1:
  * automatic (the default: the fused step where it applies and there are at
  * least two columns per resident CTA group, walks of that many columns,
  * capped where longer walks would cost a resident CTA per SM and at 32); 0:
