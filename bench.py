@@ -40,6 +40,8 @@ FORCE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_fused_traffic.txt")
 FINE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "fine.cu")
 FP64_ALG_FLOPS = 14  # algorithmic FP64 flops per cell-update of the MUSCL fine step (see run_ours)
 FORCE_SRC = os.path.join(ROOT, "paper_2502_02704_gb300", "csrc", "force.cu")
+FORCE_MUSCL_FILE = os.path.join(ROOT, "profiles", "force_fused_muscl_counters.txt")
+SM_ISSUE_PER_CLOCK = 4 * 32  # thread-instructions an SM issues per clock (4 schedulers, one warp-instruction each)
 
 
 def max_over_ranks(values, dist=None, device=None):
@@ -69,6 +71,32 @@ def _peaks():
 
 def _src_hash(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _issue_peak():
+    """Thread-instructions per second the GPU can issue (T/s): SMs x 4
+    schedulers x 32 lanes x the maximum SM clock (nvidia-smi; 2070 MHz, the
+    GB300's, if it cannot be read)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = 2070.0
+    try:
+        r = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits", "-i", "0"],
+                           capture_output=True, text=True, timeout=20)
+        mhz = float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        pass
+    return sms * SM_ISSUE_PER_CLOCK * mhz * 1e6 / 1e12
+
+
+def _counters(path, src):
+    """An ncu counter summary (JSON) if it was taken on the current source."""
+    try:
+        tj = json.load(open(path))
+        return tj if tj.get("force_cu_sha256_16") == _src_hash(src) else None
+    except (OSError, ValueError):
+        return None
 
 
 class Clocks:
@@ -594,19 +622,23 @@ def _test3_section(pr, np, torch):
     out["kinetic"] = kinetic
     # 64 independent instances in one launch per step: state 3.4 GB per buffer
     nb, steps = 64, 20
-    b = pr.pr_force_create([inst] * nb, pr.PR_UPWIND, pr.PR_MIXED)
-    try:
-        for i in range(nb):
-            pr.pr_force_set_initial(b, i, U0)
-        pr.pr_force_run(b, 5)
-        pr.pr_force_sync(b)
-        pr.pr_force_kernel_time(b, reset=True)
-        pr.pr_force_run(b, steps)
-        kms, _ = pr.pr_force_kernel_time(b)
-        walk, (cluster, _) = pr.pr_force_get_march(b), pr.pr_force_config(b)
-        persistent = pr.pr_force_get_persistent(b, steps)
-    finally:
-        pr.pr_force_destroy(b)
+
+    def batch(scheme, march=-1):
+        b = pr.pr_force_create([inst] * nb, scheme, pr.PR_MIXED)
+        try:
+            pr.pr_force_set_march(b, march)
+            for i in range(nb):
+                pr.pr_force_set_initial(b, i, U0)
+            pr.pr_force_run(b, 5)
+            pr.pr_force_sync(b)
+            pr.pr_force_kernel_time(b, reset=True)
+            pr.pr_force_run(b, steps)
+            kms, _ = pr.pr_force_kernel_time(b)
+            return kms, pr.pr_force_get_march(b), pr.pr_force_config(b)[0], pr.pr_force_get_persistent(b, steps)
+        finally:
+            pr.pr_force_destroy(b)
+
+    kms, walk, cluster, persistent = batch(pr.PR_UPWIND)
     if walk > 0 and persistent:
         kname = (f"k_force_fused_run<16> (fused single pass, all {steps} steps in one persistent launch, "
                  f"walks of {walk} columns, {cluster} CTAs per column)")
@@ -633,6 +665,28 @@ def _test3_section(pr, np, torch):
                                                 "per step)" if walk > 0 and persistent else "step (one launch)",
                                          "kernel": kname, "bytes_per_cell_update": 8,
                                          "peak_source": "measured" if peaks else "fallback"}}
+    # the same batch with MUSCL-minmod x fluxes (the limiter of Eq. 13): the
+    # fused step against the clustered one
+    mkms, mwalk, mcluster, _ = batch(pr.PR_MUSCL)
+    ckms, _, ccluster, _ = batch(pr.PR_MUSCL, 0)
+    mach = 8.0 * ncell * nb / (mkms * 1e-3) / 1e9
+    issue = _issue_peak()
+    mc = _counters(FORCE_MUSCL_FILE, FORCE_SRC)
+    ipc = mc["thread_instructions_per_cell_update"] if mc else None
+    out["batch64_mixed_muscl"] = {
+        "step_ms": mkms, "cell_updates_per_s": ncell * nb / (mkms * 1e-3),
+        "roofline": {"bound": "hbm", "achieved": mach, "peak": hbm, "unit": "GB/s", "frac": mach / hbm,
+                     "traffic": mc["dram_bytes_per_step"] if mc else None,
+                     "algorithmic_bytes_per_step": 8.0 * ncell * nb, "bytes_per_cell_update": 8,
+                     "kernel": f"k_force_fused_run<float, 16, 4> (MUSCL, walks of {mwalk} columns, "
+                               f"{mcluster} CTAs per column)",
+                     "peak_source": "measured" if peaks else "fallback"},
+        # the limiter is the instruction issue rate, not HBM: the measured
+        # instructions per cell-update over the GPU's issue rate
+        "issue": {"thread_instructions_per_cell_update": ipc, "issue_rate_T_per_s": issue,
+                  "frac": (ipc * ncell * nb / (mkms * 1e-3) / (issue * 1e12)) if ipc else None,
+                  "source": "ncu smsp__inst_executed.sum x 32 / cell-updates, profiles/force_fused_muscl_counters.txt"},
+        "clustered_step_ms": ckms, "clustered_cluster": ccluster, "speedup_over_clustered": ckms / mkms}
     # Algorithm 2
     para = {}
     for prec, name in ((pr.PR_MIXED, "mixed"), (pr.PR_FP64, "fp64")):
