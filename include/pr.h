@@ -196,6 +196,21 @@ int pr_fine_steps_per_slice(const pr_ctx* ctx, int* nf, double* dt);
 /* Iterations completed since pr_set_initial. */
 int pr_iterations(const pr_ctx* ctx, int* k);
 
+/* Parareal resume.  pr_save writes the state Algorithm 2 carries from one
+ * iteration to the next (Sec. 2.2): the iterates U^{n,k} (n = 0..N), the
+ * coarse values G(U^{n-1,k}) the next correction reuses, k and the errors of
+ * the iterations run, with a header of the problem's sizes and settings (and
+ * its force field), to the file at path (binary, host byte order; about
+ * 80 (N+1) nx bytes).  pr_load reads such a file into a problem created with
+ * the same sizes and settings (max_batch may differ): the next
+ * pr_parareal_iter continues with iteration k+1 and gives the bits the
+ * uninterrupted run gives.  Synchronous.  Errors: PR_EINVAL (called before
+ * pr_set_initial (save), a file that cannot be opened or written, another
+ * problem's file, a truncated file), PR_ENONPHYS (a loaded iterate with
+ * rho <= 0, theta <= 0 or a non-finite value: nothing is changed), PR_ECUDA. */
+int pr_save(pr_ctx* ctx, const char* path);
+int pr_load(pr_ctx* ctx, const char* path);
+
 /* ================== batched fine solves (many instances) ================== */
 
 /* Create a batch of n independent fine-solve instances of uneven sizes, all in

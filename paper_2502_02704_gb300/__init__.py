@@ -88,6 +88,8 @@ _SIGS = {
     "pr_moments": (C.c_int, [_VP, C.c_int, C.c_int, _D]),
     "pr_fine_steps_per_slice": (C.c_int, [_VP, C.POINTER(C.c_int), _D]),
     "pr_iterations": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+    "pr_save": (C.c_int, [_VP, C.c_char_p]),
+    "pr_load": (C.c_int, [_VP, C.c_char_p]),
     "pr_batch_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_instance), C.c_int, C.c_int]),
     "pr_batch_destroy": (C.c_int, [_VP]),
     "pr_batch_last_error": (C.c_char_p, [_VP]),
@@ -300,6 +302,16 @@ def pr_iterations(ctx) -> int:
     k = C.c_int()
     _ctx_check(ctx, lib().pr_iterations(ctx.ptr, C.byref(k)))
     return k.value
+
+
+def pr_save(ctx, path):
+    """Write the parareal iteration state to path (pr_save)."""
+    _ctx_check(ctx, lib().pr_save(ctx.ptr, os.fsencode(path)))
+
+
+def pr_load(ctx, path):
+    """Continue a parareal run from a state written by pr_save (pr_load)."""
+    _ctx_check(ctx, lib().pr_load(ctx.ptr, os.fsencode(path)))
 
 
 # ---------------------------------------------------------------- batches

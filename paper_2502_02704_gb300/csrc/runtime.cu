@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -1253,6 +1254,117 @@ int pr_iterations(const pr_ctx* c, int* k)
 {
     if (!c || !k) return PR_EINVAL;
     *k = c->k;
+    return PR_OK;
+}
+
+// ---- parareal resume: the iteration state in a file ----
+//
+// Layout (host byte order): "PRPARA01"; 16 int32 (nx, bc, nv, N, nf, scheme,
+// precision, sound speed, coarse model, lift order, force, nvx, k, 0, 0, 0);
+// 12 doubles (x0, x1, L, eps, T, cfl_f, cfl_g, dt_f, dT, 0, 0, 0); with the
+// force, E [nx]; the errors [N+2]; U^{n,k} and the coarse values
+// G(U^{n-1,k}) the next correction reuses, each [N+1][5][nx] conserved.
+static const char kStateMagic[8] = {'P', 'R', 'P', 'A', 'R', 'A', '0', '1'};
+
+static void state_header(const pr_ctx* c, int32_t* hi, double* hd)
+{
+    std::memset(hi, 0, 16 * sizeof(int32_t));
+    std::memset(hd, 0, 12 * sizeof(double));
+    const int32_t v[13] = {c->nx, c->g.bc, c->v.nv, c->N, c->nf, c->t.scheme, c->t.precision, c->t.sound_speed,
+                           c->t.coarse_model, c->t.lift_order, c->ff ? 1 : 0, c->ff ? c->ff->nvx : 0, c->k};
+    std::memcpy(hi, v, sizeof v);
+    const double d[9] = {c->g.x0, c->g.x1, c->v.L, c->eps, c->t.T, c->t.cfl_f, c->t.cfl_g, c->dtf, c->dT};
+    std::memcpy(hd, d, sizeof d);
+}
+
+// The problem's force field from the device (empty without one).
+static int state_force(pr_ctx* c, std::vector<double>& E)
+{
+    E.clear();
+    if (!c->ff) return PR_OK;
+    E.resize(c->nx);
+    CCUDA(c, cudaMemcpy(E.data(), c->ff->d_E, sizeof(double) * c->nx, cudaMemcpyDeviceToHost));
+    return PR_OK;
+}
+
+int pr_save(pr_ctx* c, const char* path)
+{
+    if (!c) return PR_EINVAL;
+    if (!path) return cfail(c, PR_EINVAL, "null path");
+    if (!c->initialized) return cfail(c, PR_EINVAL, "call pr_set_initial first");
+    CCUDA(c, cudaStreamSynchronize(ctx_stream(c)));
+    int rc = take_ctx_status(c);
+    if (rc) return rc;
+    const size_t lvl = (size_t)(c->N + 1) * 5 * c->nx;
+    std::vector<double> U(lvl), G(lvl), err(c->N + 2), E;
+    CCUDA(c, cudaMemcpy(U.data(), c->dU, sizeof(double) * lvl, cudaMemcpyDeviceToHost));
+    CCUDA(c, cudaMemcpy(G.data(), c->dGs, sizeof(double) * lvl, cudaMemcpyDeviceToHost));
+    CCUDA(c, cudaMemcpy(err.data(), c->derr, sizeof(double) * (c->N + 2), cudaMemcpyDeviceToHost));
+    if ((rc = state_force(c, E))) return rc;
+    int32_t hi[16];
+    double hd[12];
+    state_header(c, hi, hd);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return cfail(c, PR_EINVAL, "cannot open %s for writing", path);
+    bool ok = std::fwrite(kStateMagic, 1, 8, f) == 8 && std::fwrite(hi, sizeof hi, 1, f) == 1 &&
+              std::fwrite(hd, sizeof hd, 1, f) == 1 && (E.empty() || std::fwrite(E.data(), sizeof(double), E.size(), f) == E.size()) &&
+              std::fwrite(err.data(), sizeof(double), err.size(), f) == err.size() &&
+              std::fwrite(U.data(), sizeof(double), lvl, f) == lvl && std::fwrite(G.data(), sizeof(double), lvl, f) == lvl;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return cfail(c, PR_EINVAL, "writing %s failed", path);
+    return PR_OK;
+}
+
+int pr_load(pr_ctx* c, const char* path)
+{
+    if (!c) return PR_EINVAL;
+    if (!path) return cfail(c, PR_EINVAL, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return cfail(c, PR_EINVAL, "cannot open %s", path);
+    char magic[8];
+    int32_t hi[16], want_i[16];
+    double hd[12], want_d[12];
+    std::vector<double> E, Ew;
+    int rc = state_force(c, Ew);
+    if (rc) {
+        std::fclose(f);
+        return rc;
+    }
+    state_header(c, want_i, want_d);
+    const size_t lvl = (size_t)(c->N + 1) * 5 * c->nx;
+    std::vector<double> U(lvl), G(lvl), err(c->N + 2);
+    E.resize(Ew.size());
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kStateMagic, 8) == 0 &&
+              std::fread(hi, sizeof hi, 1, f) == 1 && std::fread(hd, sizeof hd, 1, f) == 1;
+    // every size and setting but k must be this problem's, bit for bit
+    bool same = ok && std::memcmp(hi, want_i, 12 * sizeof(int32_t)) == 0 && std::memcmp(hd, want_d, sizeof hd) == 0;
+    ok = same && (E.empty() || std::fread(E.data(), sizeof(double), E.size(), f) == E.size()) &&
+         std::fread(err.data(), sizeof(double), err.size(), f) == err.size() &&
+         std::fread(U.data(), sizeof(double), lvl, f) == lvl && std::fread(G.data(), sizeof(double), lvl, f) == lvl;
+    char extra;
+    const bool at_end = ok && std::fread(&extra, 1, 1, f) == 0;
+    std::fclose(f);
+    if (!same) return cfail(c, PR_EINVAL, "%s is not a state of this problem (sizes, settings or format differ)", path);
+    if (!ok || !at_end) return cfail(c, PR_EINVAL, "%s is truncated or has trailing bytes", path);
+    if (!E.empty() && std::memcmp(E.data(), Ew.data(), sizeof(double) * E.size()) != 0)
+        return cfail(c, PR_EINVAL, "%s was saved with another force field", path);
+    const int k = hi[12];
+    if (k < 0 || k > c->N + 1) return cfail(c, PR_EINVAL, "%s holds an iteration count outside 0..N+1", path);
+    for (int n = 0; n <= c->N; ++n)
+        if (check_cons(U.data() + (size_t)n * 5 * c->nx, c->nx))
+            return cfail(c, PR_ENONPHYS, "%s holds a non-physical iterate (slice %d)", path, n);
+    for (double e : err)
+        if (!std::isfinite(e)) return cfail(c, PR_EINVAL, "%s holds a non-finite error", path);
+    cudaStream_t s = ctx_stream(c);
+    CCUDA(c, cudaStreamSynchronize(s));
+    CCUDA(c, cudaMemcpy(c->dU, U.data(), sizeof(double) * lvl, cudaMemcpyHostToDevice));
+    CCUDA(c, cudaMemcpy(c->dGs, G.data(), sizeof(double) * lvl, cudaMemcpyHostToDevice));
+    CCUDA(c, cudaMemcpy(c->derr, err.data(), sizeof(double) * err.size(), cudaMemcpyHostToDevice));
+    const int next = k + 1;  // the device counter holds the iteration the next sweep runs
+    CCUDA(c, cudaMemcpy(c->dk, &next, sizeof(int), cudaMemcpyHostToDevice));
+    c->k = k;
+    c->initialized = true;
+    std::fill(c->live.begin(), c->live.end(), 0);
     return PR_OK;
 }
 
