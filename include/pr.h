@@ -126,6 +126,7 @@ typedef struct {
 
 typedef struct pr_ctx pr_ctx;      /* one parareal problem (Algorithm 2)       */
 typedef struct pr_batch pr_batch;  /* independent fine-solve instances         */
+typedef struct pr_multi pr_multi;  /* problems iterated together in one launch  */
 
 /* ======================= parareal problem (Sec. 2) ======================= */
 
@@ -210,6 +211,39 @@ int pr_iterations(const pr_ctx* ctx, int* k);
  * rho <= 0, theta <= 0 or a non-finite value: nothing is changed), PR_ECUDA. */
 int pr_save(pr_ctx* ctx, const char* path);
 int pr_load(pr_ctx* ctx, const char* path);
+
+/* ============ several parareal problems and instances per launch ============ */
+
+/* Algorithm 2 for several problems at once (the batching of Sec. 2.2 across
+ * problems): every slice of every problem (pr_init problems, no exterior
+ * force; one precision, scheme, lifting order and n_f, other sizes, eps and
+ * boundaries free) and n_extra independent instances (pr_instance, the same
+ * scheme and precision, each with its own dt) become instances of one batch,
+ * so one persistent launch per iteration runs the lift, the n_f fine steps
+ * and the projection of every active slice together with n_f steps of every
+ * independent instance; then each problem's sequential correction sweep
+ * (Eq. 10) runs on a stream of its own, concurrently with the others.  One
+ * iteration is one replay of a captured CUDA graph.  The problems are
+ * borrowed (they must outlive the object) and iterate in lockstep.  *out is
+ * NULL on failure (message: pr_multi_last_error(NULL)).
+ * Errors: PR_EINVAL, PR_ENOMEM, PR_ECUDA. */
+int pr_multi_create(pr_multi** out, pr_ctx* const* ctxs, int n_ctx, const pr_instance* extra, int n_extra);
+int pr_multi_destroy(pr_multi* m);
+const char* pr_multi_last_error(const pr_multi* m);
+
+/* The batch that holds the instances: instances 0 .. *first_independent - 1
+ * are the problems' slices (owned by the object), the rest the independent
+ * instances in the order given, which the pr_batch_* calls set and read
+ * (pr_batch_set_initial, pr_batch_get_f, pr_batch_moments ...). */
+int pr_multi_batch(pr_multi* m, pr_batch** batch, int* first_independent);
+
+/* count iterations (k <- k + count) of every problem, each initialised
+ * (pr_set_initial, or pr_load) and all at the same k, with k + count at most
+ * the smallest N; the independent instances advance count x n_f steps.
+ * errs (may be NULL) receives errs[it * n_ctx + p], the error of Eq. 10 of
+ * problem p in iteration it.  Synchronous.
+ * Errors: PR_EINVAL, PR_ETIMEOUT, PR_ENONPHYS, PR_ECUDA. */
+int pr_multi_iterate(pr_multi* m, int count, double* errs);
 
 /* ================== batched fine solves (many instances) ================== */
 

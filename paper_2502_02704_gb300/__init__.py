@@ -89,6 +89,11 @@ _SIGS = {
     "pr_fine_steps_per_slice": (C.c_int, [_VP, C.POINTER(C.c_int), _D]),
     "pr_iterations": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "pr_save": (C.c_int, [_VP, C.c_char_p]),
+    "pr_multi_create": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.c_int, C.POINTER(pr_instance), C.c_int]),
+    "pr_multi_destroy": (C.c_int, [_VP]),
+    "pr_multi_last_error": (C.c_char_p, [_VP]),
+    "pr_multi_batch": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(C.c_int)]),
+    "pr_multi_iterate": (C.c_int, [_VP, C.c_int, _D]),
     "pr_load": (C.c_int, [_VP, C.c_char_p]),
     "pr_batch_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_instance), C.c_int, C.c_int]),
     "pr_batch_destroy": (C.c_int, [_VP]),
@@ -328,6 +333,56 @@ def pr_batch_create(instances, precision=PR_MIXED):
     if rc != PR_OK:
         raise PrError(rc, (lib().pr_batch_last_error(None) or b"").decode())
     return _Handle(out, "pr_batch", shapes=[(d.nx, d.nv) for d in instances], n=n)
+
+
+def pr_multi_create(ctxs, extra=()):
+    """Several parareal problems (and independent instances) iterated
+    together, one persistent launch per iteration (pr_multi_create)."""
+    n = len(ctxs)
+    arr = (_VP * n)(*[c.ptr for c in ctxs])
+    ex = (pr_instance * max(len(extra), 1))(*extra)
+    out = _VP()
+    rc = lib().pr_multi_create(C.byref(out), arr, n, ex, len(extra))
+    if rc != PR_OK:
+        raise PrError(rc, (lib().pr_multi_last_error(None) or b"").decode())
+    shapes = []
+    for n_ in range(1, max(c.N for c in ctxs) + 1):
+        shapes += [(c.nx, c.nv) for c in ctxs if n_ <= c.N]
+    shapes += [(d.nx, d.nv) for d in extra]
+    b = _VP()
+    first = C.c_int()
+    lib().pr_multi_batch(out, C.byref(b), C.byref(first))
+    batch = _Handle(b, "pr_batch (of a pr_multi)", shapes=shapes, n=len(shapes))
+    return _Handle(out, "pr_multi", n_ctx=n, batch=batch, first_independent=first.value)
+
+
+def pr_multi_batch(m):
+    """The batch of a pr_multi and the index of its first independent
+    instance (pr_multi_batch); pr_multi_create keeps both on the handle."""
+    return m.batch, m.first_independent
+
+
+def pr_multi_last_error(m=None) -> str:
+    return (lib().pr_multi_last_error(m.ptr if m is not None else None) or b"").decode()
+
+
+def _multi_check(m, rc):
+    if rc != PR_OK:
+        msg = lib().pr_multi_last_error(m.ptr if m is not None else None)
+        raise PrError(rc, (msg or b"").decode())
+
+
+def pr_multi_iterate(m, count=1):
+    """count lockstep iterations; the errors of Eq. 10, [count, n_problems]."""
+    errs = np.zeros((max(int(count), 1), m.n_ctx))
+    _multi_check(m, lib().pr_multi_iterate(m.ptr, int(count), _p(errs)))
+    return errs[: int(count)]
+
+
+def pr_multi_destroy(m):
+    if m is not None and m.ptr:
+        lib().pr_multi_destroy(m.ptr)
+        m.ptr = _VP()
 
 
 def pr_batch_destroy(b):

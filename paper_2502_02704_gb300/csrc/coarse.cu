@@ -559,6 +559,31 @@ cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk,
 
 size_t coarse_work_doubles(int nx) { return work_doubles(nx); }
 
+// Several problems iterated in lockstep (one k): instances 0..n_sl-1 run
+// slices nidx[i] (ascending), the rest are independent instances.  Slices
+// n >= max(k,1) run and are lifted: run = [lo, n_inst), lift = [lo, n_sl).
+__global__ void k_set_active_multi(const int* dk, const int* nidx, int n_sl, int n_inst, Active* run, Active* lift)
+{
+    const int k = *dk, first = k > 1 ? k : 1;
+    int lo = 0, hi = n_sl;  // first instance whose slice is >= first
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (nidx[mid] >= first) hi = mid;
+        else lo = mid + 1;
+    }
+    run->begin = lo;
+    run->end = n_inst;
+    lift->begin = lo;
+    lift->end = n_sl;
+}
+
+cudaError_t launch_set_active_multi(const int* dk, const int* nidx, int n_sl, int n_inst, Active* run, Active* lift,
+                                    cudaStream_t s)
+{
+    k_set_active_multi<<<1, 1, 0, s>>>(dk, nidx, n_sl, n_inst, run, lift);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_active(const int* dk, Active* active, int first_slice, int n_inst, int N, cudaStream_t s)
 {
     k_set_active<<<1, 1, 0, s>>>(dk, active, first_slice, n_inst, N);

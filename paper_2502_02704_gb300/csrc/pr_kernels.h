@@ -230,5 +230,9 @@ cudaError_t launch_sweep(const CoarseParams& p, int N, double dT, const int* dk,
 // Active range for the parareal fine phase: instances [k-1, N) -> wave window.
 cudaError_t launch_set_active(const int* dk, Active* active, int first_slice, int n_inst,
                               int N, cudaStream_t s);
+// Lockstep problems sharing one batch: slices nidx[i] (ascending) for
+// i < n_sl, independent instances after them; run / lift ranges from k.
+cudaError_t launch_set_active_multi(const int* dk, const int* nidx, int n_sl, int n_inst, Active* run, Active* lift,
+                                    cudaStream_t s);
 
 }  // namespace prk

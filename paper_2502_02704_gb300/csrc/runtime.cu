@@ -1766,3 +1766,264 @@ int pr_moments(pr_ctx* c, int n, int kind, double* out)
 }
 
 }  // extern "C"
+
+// ======================= several problems in one launch =======================
+//
+// The batching of Algorithm 2 across problems: every slice of every problem
+// and a set of independent instances are instances of one batch, so one
+// persistent launch per iteration runs the fine propagations of all of them;
+// each problem's correction sweep then runs on a stream of its own (the sweeps
+// are sequential inside a problem, independent across problems).  The
+// problems iterate in lockstep (one k); the slices are ordered by slice index,
+// so the slices n >= k of every problem and the independent instances after
+// them form one contiguous active range.
+struct pr_multi {
+    std::vector<pr_ctx*> ctx;
+    pr_batch* b = nullptr;
+    int n_sl = 0, n_extra = 0, nf = 0, Nmin = 0;
+    int* d_n = nullptr;             // slice index of each slice instance
+    prk::Active* d_act = nullptr;   // [0] lift range, [1] the independent instances
+    std::vector<std::pair<int, int>> owner;  // (problem, slice) of each slice instance
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;    // fork, then one join per problem
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+};
+
+static int mfail(pr_multi* m, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (m) m->err = buf;
+    return code;
+}
+
+#define MCUDA(m, call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return mfail((m), PR_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Failure of pr_multi_create (no object yet): the message goes where
+// pr_multi_last_error(NULL) reads it.
+static int minit_fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    g_init_error = buf;
+    return code;
+}
+
+static void free_multi(pr_multi* m)
+{
+    if (!m) return;
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->graph) cudaGraphDestroy(m->graph);
+    for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+    for (cudaStream_t s : m->side) cudaStreamDestroy(s);
+    if (m->b) free_batch(m->b);
+    cudaFree(m->d_n);
+    cudaFree(m->d_act);
+    delete m;
+}
+
+// The graph of one lockstep iteration: active ranges from k, lift of the
+// active slices, one persistent run of n_f steps over slices and independent
+// instances, the independent instances' state advance, and every problem's
+// correction sweep on its own stream (fork and join through events).
+static int build_multi_graph(pr_multi* m)
+{
+    pr_batch* b = m->b;
+    cudaStream_t s = b->stream;
+    const int n = b->n, np = (int)m->ctx.size();
+    MCUDA(m, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = prk::launch_set_active_multi(m->ctx[0]->dk, m->d_n, m->n_sl, n, b->d_active, m->d_act, s);
+    if (e == cudaSuccess)
+        e = b->lift_order == 1
+                ? prk::launch_lift_ce(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, m->d_act, b->nx_max, n,
+                                      0, b->d_status, s)
+                : prk::launch_lift(b->precision == PR_FP64 ? 0 : 1, b->d_inst, b->d_state, m->d_act, b->max_tiles, n,
+                                   b->lift_smem, b->d_status, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_sync, 0, b->sync_bytes, s);
+    if (e == cudaSuccess)
+        e = prk::launch_fine_run(b->precision == PR_FP64 ? 0 : 1, b->scheme, b->vpt, b->d_inst, b->d_state,
+                                 b->d_prefix, b->d_active, m->nf, reinterpret_cast<unsigned long long*>(b->d_sync),
+                                 b->d_status, m->nf > 1 ? prk::WAIT_LIMIT_NS : 0, b->grid, b->smem, s);
+    if (e == cudaSuccess && m->n_extra > 0) e = prk::launch_advance(b->d_inst, b->d_state, m->d_act + 1, m->nf, n, s);
+    if (e == cudaSuccess) e = cudaEventRecord(m->ev[0], s);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+        pr_ctx* c = m->ctx[p];
+        e = cudaStreamWaitEvent(m->side[p], m->ev[0], 0);
+        if (e == cudaSuccess)
+            e = prk::launch_sweep(c->cp, c->N, c->dT, c->dk, c->dU, c->dPFL, c->dGs, c->derr, c->dwork, c->dstatus, 1,
+                                  c->dk, m->side[p]);
+        if (e == cudaSuccess) e = cudaEventRecord(m->ev[1 + p], m->side[p]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->ev[1 + p], 0);
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return mfail(m, PR_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        return mfail(m, PR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    m->graph = gr;
+    m->gexec = ex;
+    return PR_OK;
+}
+
+extern "C" {
+
+int pr_multi_create(pr_multi** out, pr_ctx* const* ctxs, int n_ctx, const pr_instance* extra, int n_extra)
+{
+    if (!out) return PR_EINVAL;
+    *out = nullptr;
+    if (!ctxs || n_ctx < 1 || n_extra < 0 || (n_extra > 0 && !extra))
+        return minit_fail(PR_EINVAL, "need at least one problem, and the independent instances when n_extra > 0");
+    const pr_ctx* c0 = ctxs[0];
+    std::set<const pr_ctx*> seen;
+    for (int p = 0; p < n_ctx; ++p) {
+        const pr_ctx* c = ctxs[p];
+        if (!c) return minit_fail(PR_EINVAL, "problem %d is null", p);
+        if (!seen.insert(c).second) return minit_fail(PR_EINVAL, "problem %d is given twice", p);
+        if (c->ff) return minit_fail(PR_EINVAL, "problem %d has an exterior force (pr_init_force): not supported here", p);
+        if (c->t.precision != c0->t.precision || c->t.scheme != c0->t.scheme || c->nf != c0->nf ||
+            c->fine->lift_order != c0->fine->lift_order)
+            return minit_fail(PR_EINVAL, "problem %d differs from problem 0 in precision, scheme, fine steps per slice "
+                                        "or lifting order", p);
+    }
+    for (int i = 0; i < n_extra; ++i)
+        if (extra[i].scheme != c0->t.scheme)
+            return minit_fail(PR_EINVAL, "independent instance %d has another scheme than the problems", i);
+    pr_multi* m = new pr_multi();
+    m->ctx.assign(ctxs, ctxs + n_ctx);
+    m->nf = c0->nf;
+    m->n_extra = n_extra;
+    m->Nmin = c0->N;
+    for (const pr_ctx* c : m->ctx) m->Nmin = std::min(m->Nmin, c->N);
+    // slice instances by slice index (then problem), the independent ones after them
+    for (int n = 1;; ++n) {
+        bool any = false;
+        for (int p = 0; p < n_ctx; ++p)
+            if (n <= ctxs[p]->N) {
+                m->owner.push_back({p, n});
+                any = true;
+            }
+        if (!any) break;
+    }
+    m->n_sl = (int)m->owner.size();
+    std::vector<pr_instance> descs;
+    descs.reserve(m->n_sl + n_extra);
+    std::vector<int> nidx;
+    for (auto [p, n] : m->owner) {
+        const pr_ctx* c = ctxs[p];
+        descs.push_back(pr_instance{c->nx, c->g.x0, c->g.x1, c->g.bc, c->v.nv, c->v.L, c->eps, c->dtf, c->t.scheme});
+        nidx.push_back(n);
+    }
+    descs.insert(descs.end(), extra, extra + n_extra);
+    std::string err;
+    int rc = create_batch(&m->b, descs.data(), (int)descs.size(), c0->t.precision, err);
+    if (rc) {
+        free_multi(m);
+        return minit_fail(rc, "%s", err.c_str());
+    }
+    m->b->lift_order = c0->fine->lift_order;
+    for (int i = 0; i < m->n_sl; ++i) {  // lift from U^{n-1}, project into P F L^n of the owning problem
+        const pr_ctx* c = ctxs[m->owner[i].first];
+        const int n = m->owner[i].second;
+        m->b->h[i].Uin = c->dU + (size_t)(n - 1) * 5 * c->nx;
+        m->b->h[i].Uout = c->dPFL + (size_t)n * 5 * c->nx;
+    }
+    const prk::Active act[2] = {{0, m->n_sl}, {m->n_sl, m->n_sl + n_extra}};
+    bool ok = cudaMalloc(&m->d_n, sizeof(int) * std::max(1, m->n_sl)) == cudaSuccess &&
+              cudaMalloc(&m->d_act, sizeof act) == cudaSuccess &&
+              cudaMemcpy(m->d_n, nidx.data(), sizeof(int) * m->n_sl, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(m->d_act, act, sizeof act, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(m->b->d_inst, m->b->h.data(), sizeof(Inst) * m->b->n, cudaMemcpyHostToDevice) == cudaSuccess;
+    m->side.assign(n_ctx, nullptr);
+    m->ev.assign(n_ctx + 1, nullptr);
+    for (int p = 0; p < n_ctx && ok; ++p) ok = cudaStreamCreateWithFlags(&m->side[p], cudaStreamNonBlocking) == cudaSuccess;
+    for (auto& e : m->ev)
+        if (ok) ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok || cudaDeviceSynchronize() != cudaSuccess) {
+        free_multi(m);
+        return minit_fail(PR_ECUDA, "multi-problem set-up");
+    }
+    *out = m;
+    return PR_OK;
+}
+
+int pr_multi_destroy(pr_multi* m)
+{
+    if (!m) return PR_EINVAL;
+    cudaStreamSynchronize(m->b->stream);
+    free_multi(m);
+    return PR_OK;
+}
+
+const char* pr_multi_last_error(const pr_multi* m) { return m ? m->err.c_str() : g_init_error.c_str(); }
+
+int pr_multi_batch(pr_multi* m, pr_batch** batch, int* first_independent)
+{
+    if (!m) return PR_EINVAL;
+    if (batch) *batch = m->b;
+    if (first_independent) *first_independent = m->n_sl;
+    return PR_OK;
+}
+
+int pr_multi_iterate(pr_multi* m, int count, double* errs)
+{
+    if (!m) return PR_EINVAL;
+    if (count < 0) return mfail(m, PR_EINVAL, "count must be >= 0");
+    const int np = (int)m->ctx.size(), k = m->ctx[0]->k;
+    for (int p = 0; p < np; ++p) {
+        const pr_ctx* c = m->ctx[p];
+        if (!c->initialized) return mfail(m, PR_EINVAL, "problem %d: call pr_set_initial first", p);
+        if (c->k != k) return mfail(m, PR_EINVAL, "the problems must be at the same iteration (problem %d: k = %d, "
+                                                  "problem 0: k = %d)", p, c->k, k);
+    }
+    if (k + count > m->Nmin)
+        return mfail(m, PR_EINVAL, "k + count = %d exceeds the smallest N (%d): the slices of that problem are exact",
+                     k + count, m->Nmin);
+    cudaStream_t s = m->b->stream;
+    for (int p = 0; p < np; ++p) MCUDA(m, cudaStreamSynchronize(ctx_stream(m->ctx[p])));  // their own work first
+    if (!m->gexec) {
+        int rc = build_multi_graph(m);
+        if (rc) return rc;
+    }
+    for (int it = 0; it < count; ++it) {
+        MCUDA(m, cudaGraphLaunch(m->gexec, s));
+        g_launches += 4 + (m->n_extra > 0 ? 1 : 0) + np;
+    }
+    MCUDA(m, cudaStreamSynchronize(s));
+    int rc = take_status(m->b, s);
+    if (rc) return mfail(m, rc, "%s", m->b->err.c_str());
+    for (int p = 0; p < np; ++p) {
+        pr_ctx* c = m->ctx[p];
+        c->k = k + count;
+        std::fill(c->live.begin(), c->live.end(), 0);
+        const int rc2 = take_ctx_status(c);
+        if (rc2) return mfail(m, rc2, "problem %d: %s", p, c->err.c_str());
+        if (errs && count > 0) {
+            std::vector<double> e(count);
+            MCUDA(m, cudaMemcpy(e.data(), c->derr + k + 1, sizeof(double) * count, cudaMemcpyDeviceToHost));
+            for (int it = 0; it < count; ++it) errs[(size_t)it * np + p] = e[it];
+        }
+    }
+    return PR_OK;
+}
+
+}  // extern "C"
