@@ -413,6 +413,92 @@ def _parareal_section(pr, np, torch, workload, nx, nv, L, bc, scheme, eps, T, N,
                       "with the moments in device memory, read back after the clock"}
 
 
+def _multi_section(pr, np, torch):
+    """Several parareal problems and independent instances per launch
+    (pr_multi) against the same work run one object after another: four
+    Sod-type problems of different sizes and eps (N = 8, outflow, upwind,
+    mixed precision, one shared n_f) and 16 seeded ragged instances advanced
+    with them, K = 4 iterations; wall clock around the synchronous calls,
+    median of 3 after a warm-up."""
+    from paper_2502_02704_gb300 import workloads as W
+
+    specs = [(64, 16, 1e-2), (128, 16, 1e-3), (96, 24, 1e-2), (256, 16, 1e-4)]  # nx, nv, eps
+    N, T, K = 8, 0.1, 4
+    nf = 0
+    for nx, nv, eps in specs:  # the shared n_f: the largest the problems' CFL needs
+        c = pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, nv, 8.0, eps, T, N, precision=pr.PR_MIXED)
+        try:
+            nf = max(nf, pr.pr_fine_steps_per_slice(c)[0])
+        finally:
+            pr.pr_destroy(c)
+    extras, ext_U = [], []
+    for r in W.ragged_instances(16, seed=5, nx_range=(64, 256)):
+        nx = r["nx"]
+        extras.append(pr.instance(nx, r["nv"], pr.fine_dt(nx, r["nv"], r["L"]), L=r["L"], bc=pr.PR_BC_OUTFLOW,
+                                  eps=r["eps"]))
+        ext_U.append(r["U"])
+    cells_slices = sum(nx * nv ** 3 for nx, nv, _ in specs) * N
+    cells_extra = sum(d.nx * d.nv ** 3 for d in extras)
+
+    def problems():
+        ctxs = [pr.pr_init(nx, 0.0, 1.0, pr.PR_BC_OUTFLOW, nv, 8.0, eps, T, N, precision=pr.PR_MIXED, nf=nf)
+                for nx, nv, eps in specs]
+        return ctxs
+
+    def start(ctxs, b, first):
+        for c, (nx, _, _) in zip(ctxs, specs):
+            pr.pr_set_initial(c, W.sod(nx))
+        for j, U in enumerate(ext_U):
+            pr.pr_batch_set_initial(b, first + j, U)
+        pr.pr_batch_sync(b)
+
+    # one object after another: each problem's K iterations, then the instances
+    ctxs = problems()
+    b = pr.pr_batch_create(extras, pr.PR_MIXED)
+    sep = []
+    try:
+        for rep in range(4):
+            start(ctxs, b, 0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for c in ctxs:
+                pr.pr_parareal_run(c, K)
+            pr.pr_batch_run(b, K * nf)
+            pr.pr_batch_sync(b)
+            sep.append(time.perf_counter() - t0)
+        U_sep = [np.stack([pr.pr_moments(c, n) for n in range(N + 1)]) for c in ctxs]
+    finally:
+        pr.pr_batch_destroy(b)
+        for c in ctxs:
+            pr.pr_destroy(c)
+    # together: one persistent launch per iteration
+    ctxs = problems()
+    m = None
+    tog = []
+    try:
+        m = pr.pr_multi_create(ctxs, extras)
+        for rep in range(4):
+            start(ctxs, m.batch, m.first_independent)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pr.pr_multi_iterate(m, K)
+            tog.append(time.perf_counter() - t0)
+        U_tog = [np.stack([pr.pr_moments(c, n) for n in range(N + 1)]) for c in ctxs]
+    finally:
+        pr.pr_multi_destroy(m)
+        for c in ctxs:
+            pr.pr_destroy(c)
+    t_sep, t_tog = statistics.median(sep[1:]), statistics.median(tog[1:])
+    diff = max(_moment_rel_err(np, a[n], b_[n]) for a, b_ in zip(U_tog, U_sep) for n in range(N + 1))
+    return {"workload": f"4 Sod-type problems (Nx x Nv^3 = 64x16^3, 128x16^3, 96x24^3, 256x16^3; eps 1e-2..1e-4; "
+                        f"N={N}, T={T}, n_f={nf}, outflow, upwind, mixed) + 16 ragged independent instances "
+                        f"(Nx 64..256, 16^3..32^3) advanced n_f steps per iteration, K={K}",
+            "cell_updates_per_iteration": (cells_slices + cells_extra) * nf,
+            "separate_ms": t_sep * 1e3, "one_launch_per_iteration_ms": t_tog * 1e3, "speedup": t_sep / t_tog,
+            "max_rel_err_between_the_two": diff,
+            "timing": "wall clock around the synchronous calls, median of 3 after a warm-up"}
+
+
 def _ragged_section(pr, torch):
     """32 seeded ragged Sod-type instances (Nx in [128, 1024], 16^3/24^3/32^3,
     log10 eps in [-5, 0], MUSCL, outflow), mixed precision, one persistent
@@ -862,6 +948,11 @@ def run_ours(args):
         higher = _coarse_models_section(pr, np, torch)
     except Exception as e:
         higher = {"error": repr(e)}
+    multi = None
+    try:
+        multi = _multi_section(pr, np, torch)
+    except Exception as e:
+        multi = {"error": repr(e)}
     adjoint = None
     try:
         adjoint = _adjoint_section(pr, np, torch, cpu=not args.no_cpu_baseline)
@@ -894,6 +985,7 @@ def run_ours(args):
         "parareal": para,
         "parareal_batched_n64": para64,
         "ragged_batch": ragged,
+        "multi_problem": multi,
         "parareal_large": large,
         "test3_force": test3,
         "coarse_models": higher,
