@@ -89,6 +89,7 @@ _SIGS = {
     "pr_fine_steps_per_slice": (C.c_int, [_VP, C.POINTER(C.c_int), _D]),
     "pr_iterations": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "pr_save": (C.c_int, [_VP, C.c_char_p]),
+    "pr_batch_vpt": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "pr_multi_create": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.c_int, C.POINTER(pr_instance), C.c_int]),
     "pr_multi_destroy": (C.c_int, [_VP]),
     "pr_multi_last_error": (C.c_char_p, [_VP]),
@@ -383,6 +384,13 @@ def pr_multi_destroy(m):
     if m is not None and m.ptr:
         lib().pr_multi_destroy(m.ptr)
         m.ptr = _VP()
+
+
+def pr_batch_vpt(b) -> int:
+    """Velocities per thread of the fine kernel in use (pr_batch_vpt)."""
+    v = C.c_int()
+    _batch_check(b, lib().pr_batch_vpt(b.ptr, C.byref(v)))
+    return v.value
 
 
 def pr_batch_destroy(b):

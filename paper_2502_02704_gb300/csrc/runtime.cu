@@ -106,6 +106,7 @@ static void prepare_kernels_once()
 struct pr_batch {
     int n = 0, precision = PR_MIXED, scheme = PR_UPWIND, H = 1;
     int vpt = 4;  // velocities per thread of the fine kernel
+    int vpt_req = 0;  // 0: 8 in float32 when every nv allows it, else 4; 4: always 4 (autotuner's choice)
     size_t es = 4;
     std::vector<pr_instance> desc;
     std::vector<Inst> h;
@@ -220,7 +221,7 @@ static int upload_layout(pr_batch* b, const std::vector<int>& txs)
     // eight v_z nodes per thread in float32 when every row allows it
     bool all8 = true;
     for (auto& I : b->h) all8 = all8 && I.nv % 8 == 0;
-    b->vpt = (b->precision == PR_MIXED && all8) ? 8 : 4;
+    b->vpt = (b->precision == PR_MIXED && all8 && b->vpt_req != 4) ? 8 : 4;
     b->smem = prk::fine_run_smem(b->precision == PR_FP64 ? 0 : 1, b->vpt, maxtx, maxnv, b->H);
     b->lift_smem = prk::lift_smem(b->precision == PR_FP64 ? 0 : 1, maxtx, maxnv);
     if ((int)b->smem > max_optin_smem() || (int)b->lift_smem > max_optin_smem())
@@ -730,6 +731,13 @@ int pr_batch_tile(const pr_batch* b, int i, int* tx, int* tuned)
     return PR_OK;
 }
 
+int pr_batch_vpt(const pr_batch* b, int* vpt)
+{
+    if (!b || !vpt) return PR_EINVAL;
+    *vpt = b->vpt;
+    return PR_OK;
+}
+
 int pr_batch_set_tile(pr_batch* b, int tx)
 {
     if (!b) return PR_EINVAL;
@@ -909,17 +917,22 @@ extern "C" int pr_batch_autotune(pr_batch* b)
         }
     };
     copy_all(true);
+    // candidates: tile widths x velocities per thread (8 and 4 where every
+    // nv allows 8 in float32, else 4 only)
     const int cands[4] = {8, 16, 32, 64};
-    std::vector<int> best(b->n), cur(b->n);
-    for (int i = 0; i < b->n; ++i) best[i] = cur[i] = b->h[i].tx;
+    bool all8 = b->precision == PR_MIXED;
+    for (auto& I : b->h) all8 = all8 && I.nv % 8 == 0;
+    const int nvpt = all8 ? 2 : 1, vpts[2] = {0, 4};
     double best_ms = 1e300;
-    int best_c = -1;
+    int best_c = -1, best_v = 0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int steps = 16;  // long enough for the steady state of the persistent launch
     int rc = PR_OK;
-    for (int ci = 0; ci < 4 && rc == PR_OK; ++ci) {
+    for (int cv = 0; cv < 4 * nvpt && rc == PR_OK; ++cv) {
+        const int ci = cv % 4;
+        b->vpt_req = vpts[cv / 4];
         std::vector<int> txs(b->n);
         for (int i = 0; i < b->n; ++i) txs[i] = std::min(cands[ci], b->h[i].nx);
         rc = upload_layout(b, txs);
@@ -940,11 +953,13 @@ extern "C" int pr_batch_autotune(pr_batch* b)
         if (rc == PR_OK && ms_sum < best_ms) {
             best_ms = ms_sum;
             best_c = ci;
+            best_v = b->vpt_req;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     int rc2;
+    b->vpt_req = best_c >= 0 ? best_v : 0;
     if (best_c >= 0) {
         std::vector<int> txs(b->n);
         for (int i = 0; i < b->n; ++i) txs[i] = std::min(cands[best_c], b->h[i].nx);

@@ -231,3 +231,36 @@ def test_manual_tile_widths_keep_results(tx):
     k = _kin(nx, nv, 8.0, pr.PR_BC_PERIODIC, 1e-2, pr.PR_MUSCL)
     Vo = O.project(k, O.fine_run(k, dt, 6, O.lift(k, W.smooth_periodic(nx))), conserved=True)
     assert moment_rel_err(V, Vo) < TOL_FP64
+
+
+def test_autotuned_layout_in_float32_keeps_results():
+    # nv = 16: the search covers 8 and 4 velocities per thread in float32
+    nx, nv = 160, 16
+    dt = pr.fine_dt(nx, nv, 8.0)
+    inst = [pr.instance(nx, nv, dt, bc=pr.PR_BC_PERIODIC, eps=1e-2, scheme=pr.PR_MUSCL),
+            pr.instance(96, nv, dt, bc=pr.PR_BC_OUTFLOW, eps=1e-4, scheme=pr.PR_MUSCL)]
+    U = [W.smooth_periodic(nx), W.sod(96)]
+    b = pr.pr_batch_create(inst, pr.PR_MIXED)
+    try:
+        assert pr.pr_batch_vpt(b) == 8      # the default where every nv allows it
+        for i, u in enumerate(U):
+            pr.pr_batch_set_initial(b, i, u)
+        pr.pr_batch_autotune(b)
+        assert pr.pr_batch_vpt(b) in (4, 8)
+        assert all(pr.pr_batch_tile(b, i)[1] for i in range(2))
+        pr.pr_batch_run(b, 6)
+        V = [pr.pr_batch_moments(b, i) for i in range(2)]
+    finally:
+        pr.pr_batch_destroy(b)
+    for i, d in enumerate(inst):
+        k = _kin(d.nx, nv, 8.0, d.bc, d.eps, pr.PR_MUSCL)
+        Vo = O.project(k, O.fine_run(k, dt, 6, O.lift(k, U[i])), conserved=True)
+        assert moment_rel_err(V[i], Vo) < TOL_MIXED
+    # with nv = 12 only 4 velocities per thread exist
+    b = pr.pr_batch_create([pr.instance(64, 12, dt, eps=1e-2)], pr.PR_MIXED)
+    try:
+        pr.pr_batch_set_initial(b, 0, W.smooth_periodic(64))
+        pr.pr_batch_autotune(b)
+        assert pr.pr_batch_vpt(b) == 4
+    finally:
+        pr.pr_batch_destroy(b)
