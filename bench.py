@@ -709,13 +709,15 @@ def _test3_section(pr, np, torch):
     # 64 independent instances in one launch per step: state 3.4 GB per buffer
     nb, steps = 64, 20
 
-    def batch(scheme, march=-1):
+    def batch(scheme, march=-1, tune=False):
         b = pr.pr_force_create([inst] * nb, scheme, pr.PR_MIXED)
         try:
             pr.pr_force_set_march(b, march)
             for i in range(nb):
                 pr.pr_force_set_initial(b, i, U0)
             pr.pr_force_run(b, 5)
+            if tune:  # the library's layout search on the live states
+                pr.pr_force_autotune(b, 4)
             pr.pr_force_sync(b)
             pr.pr_force_kernel_time(b, reset=True)
             pr.pr_force_run(b, steps)
@@ -773,6 +775,13 @@ def _test3_section(pr, np, torch):
                   "frac": (ipc * ncell * nb / (mkms * 1e-3) / (issue * 1e12)) if ipc else None,
                   "source": "ncu smsp__inst_executed.sum x 32 / cell-updates, profiles/force_fused_muscl_counters.txt"},
         "clustered_step_ms": ckms, "clustered_cluster": ccluster, "speedup_over_clustered": ckms / mkms}
+    tuned = {}
+    for name, sch in (("upwind", pr.PR_UPWIND), ("muscl", pr.PR_MUSCL)):
+        tkms, twalk, tcluster, _ = batch(sch, tune=True)
+        tuned[name] = {"step_ms": tkms, "cluster": tcluster, "walk": twalk}
+    out["batch64_autotuned"] = {"note": "pr_force_autotune(4 steps per candidate) on the live states, then the "
+                                        "same 20 timed steps; the heuristic layout's times are the entries above",
+                                **tuned}
     # Algorithm 2
     para = {}
     for prec, name in ((pr.PR_MIXED, "mixed"), (pr.PR_FP64, "fp64")):

@@ -525,6 +525,17 @@ int pr_force_get_persistent(const pr_force* b, int nsteps, int* on);
 /* Walk length of the fused step in use (0: the clustered step). */
 int pr_force_get_march(const pr_force* b, int* columns);
 
+/* Time candidate step layouts on the current states with CUDA events and
+ * keep the fastest: every CTA count per column for which the fused step
+ * applies, each with its automatic walk length and half and twice it, and
+ * the clustered step at its default cluster size (each candidate runs nsteps
+ * >= 1 steps twice from the saved states; the second run counts).  The
+ * states and moments are restored; the chosen cluster size and walk stay
+ * set (pr_force_config, pr_force_get_march).  Synchronous.
+ * Errors: PR_EINVAL, PR_ENOMEM (scratch for one copy of the states),
+ * PR_ETIMEOUT, PR_ENONPHYS, PR_ECUDA. */
+int pr_force_autotune(pr_force* b, int nsteps);
+
 /* Average duration in ms of one step launch over the runs since the last
  * reset (CUDA events on the launching stream around each run, divided by its
  * steps); reset = 1 clears the accumulator. */

@@ -90,6 +90,7 @@ _SIGS = {
     "pr_iterations": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "pr_save": (C.c_int, [_VP, C.c_char_p]),
     "pr_batch_vpt": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+    "pr_force_autotune": (C.c_int, [_VP, C.c_int]),
     "pr_multi_create": (C.c_int, [C.POINTER(_VP), C.POINTER(_VP), C.c_int, C.POINTER(pr_instance), C.c_int]),
     "pr_multi_destroy": (C.c_int, [_VP]),
     "pr_multi_last_error": (C.c_char_p, [_VP]),
@@ -615,6 +616,13 @@ def pr_force_set_threads(b, threads):
 
 def pr_force_set_march(b, columns):
     _force_check(b, lib().pr_force_set_march(b.ptr, int(columns)))
+
+
+def pr_force_autotune(b, nsteps=4):
+    """Time the candidate step layouts on the current states and keep the
+    fastest (pr_force_autotune); the chosen (cluster, walk)."""
+    _force_check(b, lib().pr_force_autotune(b.ptr, int(nsteps)))
+    return pr_force_config(b)[0], pr_force_get_march(b)
 
 
 def pr_force_set_persistent(b, mode):

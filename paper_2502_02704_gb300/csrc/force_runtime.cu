@@ -976,4 +976,113 @@ int pr_force_dt_stab(const pr_force_instance* inst, double cfl, double* dt)
     return PR_OK;
 }
 
+// Time candidate step layouts on the current states and keep the fastest:
+// every CTA count per column for which the fused step applies, each with the
+// automatic walk and half and twice it, and the clustered step at its
+// default cluster size.  Each candidate runs nsteps steps twice from the
+// saved states (CUDA events on the stream, the second run counts); the
+// states and moments are restored afterwards.
+int pr_force_autotune(pr_force* b, int nsteps)
+{
+    if (!b) return PR_EINVAL;
+    if (nsteps < 1) return ffail(b, PR_EINVAL, "nsteps must be >= 1");
+    cudaStream_t s = b->stream;
+    FCUDA(b, cudaStreamSynchronize(s));
+    int rc = prf::take_status(b);
+    if (rc) return rc;
+    const size_t state = (size_t)b->nx * b->g.ncol * elem(b->precision);
+    std::vector<int> cur(b->n);
+    FCUDA(b, cudaMemcpy(cur.data(), b->d_cur, sizeof(int) * b->n, cudaMemcpyDeviceToHost));
+    void* save = nullptr;
+    double* saveU = nullptr;
+    if (cudaMalloc(&save, state * b->n) != cudaSuccess || cudaMalloc(&saveU, sizeof(double) * 5 * b->nx * b->n) != cudaSuccess) {
+        cudaFree(save);
+        cudaGetLastError();
+        return ffail(b, PR_ENOMEM, "autotune needs %zu bytes of scratch", state * b->n);
+    }
+    auto copy_states = [&](bool to_save) -> cudaError_t {
+        for (int i = 0; i < b->n; ++i) {
+            char* sv = static_cast<char*>(save) + state * i;
+            void* f = b->bufs[2 * i + cur[i]];
+            cudaError_t e = to_save ? cudaMemcpy(sv, f, state, cudaMemcpyDeviceToDevice)
+                                    : cudaMemcpy(f, sv, state, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) return e;
+        }
+        const size_t ub = sizeof(double) * 5 * b->nx * b->n;
+        cudaError_t e = to_save ? cudaMemcpy(saveU, b->d_U, ub, cudaMemcpyDeviceToDevice)
+                                : cudaMemcpy(b->d_U, saveU, ub, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_cur, cur.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice);
+        return e;
+    };
+    struct Cand {
+        prk::FGeom g;
+        size_t sm;
+    };
+    std::vector<Cand> cands;
+    auto add = [&](const prk::FGeom& g, size_t sm) {
+        for (const Cand& c : cands)
+            if (c.g.C == g.C && c.g.march == g.march) return;
+        cands.push_back({g, sm});
+    };
+    for (int C = 1; C <= prk::FORCE_MAX_CLUSTER; ++C) {
+        prk::FGeom g;
+        size_t sm;
+        if (!fused_geometry(b, C, b->max_threads, -1, &g, &sm) &&
+            !fused_geometry(b, C, b->max_threads, std::min(8, b->nx), &g, &sm))
+            continue;
+        add(g, sm);
+        const int S0 = g.march;
+        for (int S : {std::max(1, S0 / 2), std::min(b->nx, 2 * S0)}) {
+            prk::FGeom g2;
+            size_t sm2;
+            if (fused_geometry(b, C, b->max_threads, S, &g2, &sm2)) add(g2, sm2);
+        }
+    }
+    {
+        const int Cd = default_cluster(b->precision, b->scheme, b->nvx, b->nvp);
+        prk::FGeom g;
+        size_t sm;
+        if (Cd > 0 && pick_geometry(b, Cd, b->max_threads, 0, &g, &sm)) add(g, sm);
+    }
+    const prk::FGeom g_old = b->g;
+    const size_t sm_old = b->smem;
+    const int march_old = b->march_req;
+    double best_ms = 1e300;
+    int best = -1;
+    cudaError_t ce = copy_states(true);
+    for (size_t ci = 0; ci < cands.size() && ce == cudaSuccess && rc == PR_OK; ++ci) {
+        if (apply_geometry(b, cands[ci].g, cands[ci].sm) != PR_OK) continue;  // e.g. no room for its partials
+        double ms = 0.0;
+        for (int rep = 0; rep < 2 && rc == PR_OK; ++rep) {
+            if ((ce = copy_states(false)) != cudaSuccess) break;
+            std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);
+            fold_events(b);
+            b->step_ms_sum = 0.0;
+            b->steps_timed = 0;
+            rc = prf::enqueue_run(b, 0, b->n, nsteps, s, true);
+            if (rc == PR_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = ffail(b, PR_ECUDA, "autotune run");
+            if (rc == PR_OK) rc = prf::take_status(b);
+            fold_events(b);
+            ms = b->steps_timed ? b->step_ms_sum / b->steps_timed : 1e300;
+        }
+        if (rc == PR_OK && ms < best_ms) {
+            best_ms = ms;
+            best = (int)ci;
+        }
+    }
+    b->step_ms_sum = 0.0;
+    b->steps_timed = 0;
+    int rc2 = best >= 0 ? apply_geometry(b, cands[best].g, cands[best].sm) : apply_geometry(b, g_old, sm_old);
+    if (rc2 == PR_OK) b->march_req = best >= 0 ? cands[best].g.march : march_old;
+    if (ce == cudaSuccess) ce = copy_states(false);
+    std::fill(b->sums_ok.begin(), b->sums_ok.end(), 0);
+    cudaFree(save);
+    cudaFree(saveU);
+    if (ce != cudaSuccess) return ffail(b, PR_ECUDA, "autotune state copies: %s", cudaGetErrorString(ce));
+    if (rc) return rc;
+    if (rc2) return rc2;
+    FCUDA(b, cudaStreamSynchronize(s));
+    return PR_OK;
+}
+
 }  // extern "C"

@@ -511,3 +511,44 @@ def test_muscl_force_parareal_on_the_fused_step_matches_oracle(precision):
             assert moment_rel_err(pr.pr_moments(ctx, n), Uo[K][n]) < TOL[precision], n
     finally:
         pr.pr_destroy(ctx)
+
+
+@pytest.mark.parametrize("scheme", [pr.PR_UPWIND, pr.PR_MUSCL])
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_autotune_keeps_the_states_and_picks_a_valid_layout(scheme, precision):
+    nx, nvx, nvp, L = 40, 64, 16, 7.0
+    insts, kins, initial = _problem(nx, nvx, nvp, L, pr.PR_BC_PERIODIC, 1e-2, n_inst=4)
+    b = pr.pr_force_create(insts, scheme, precision)
+    try:
+        for i, U in enumerate(initial):
+            pr.pr_force_set_initial(b, i, U)
+        pr.pr_force_run(b, 2)
+        before = [(pr.pr_force_get_f(b, i), pr.pr_force_moments(b, i)) for i in range(4)]
+        cluster, walk = pr.pr_force_autotune(b, 3)
+        after = [(pr.pr_force_get_f(b, i), pr.pr_force_moments(b, i)) for i in range(4)]
+        for (f, V), (fa, Va) in zip(before, after):
+            assert np.array_equal(f, fa) and np.array_equal(V, Va)
+        assert pr.pr_force_config(b)[0] == cluster and pr.pr_force_get_march(b) == walk
+        pr.pr_force_run(b, 3)
+        tuned = [(pr.pr_force_get_f(b, i), pr.pr_force_moments(b, i)) for i in range(4)]
+    finally:
+        pr.pr_force_destroy(b)
+    # the same sequence with the layout set by hand (2 steps on the default
+    # layout, 3 on the chosen one) gives the same bits; the oracle agrees
+    b = pr.pr_force_create(insts, scheme, precision)
+    try:
+        for i, U in enumerate(initial):
+            pr.pr_force_set_initial(b, i, U)
+        pr.pr_force_run(b, 2)
+        pr.pr_force_set_cluster(b, cluster)
+        pr.pr_force_set_march(b, walk)
+        assert pr.pr_force_get_march(b) == walk
+        pr.pr_force_run(b, 3)
+        ref = [(pr.pr_force_get_f(b, i), pr.pr_force_moments(b, i)) for i in range(4)]
+    finally:
+        pr.pr_force_destroy(b)
+    for k, ((f, V), (fr, Vr)) in enumerate(zip(tuned, ref)):
+        assert np.array_equal(f, fr) and np.array_equal(V, Vr)
+        kins[k].scheme = O.MUSCL if scheme == pr.PR_MUSCL else O.UPWIND
+        fo = O.v_fine_run(kins[k], insts[k].c.dt, 5, O.v_lift(kins[k], initial[k]))
+        assert f_rel_err(f, fo) < FTOL[precision]
