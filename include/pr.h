@@ -322,8 +322,8 @@ int pr_batch_set_tile(pr_batch* b, int tx);
 
 /* Time candidate layouts on the current data with CUDA events and keep the
  * fastest: tile widths 8, 16, 32, 64 (capped at each nx) times velocities
- * per thread of the fine kernel, 8 and 4 in float32 when every nv is a
- * multiple of 8 (else 4).  The state is saved and restored.  Synchronous. */
+ * per thread of the fine kernel, 8 and 4 when every nv is a multiple of 8
+ * (else 4).  The state is saved and restored.  Synchronous. */
 int pr_batch_autotune(pr_batch* b);
 
 /* Velocities per thread of the fine kernel in use (4 or 8). */

@@ -664,7 +664,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
 
 // Resident CTAs per SM the register budget is sized for: float32 with 8
 // velocities per thread (128 threads): 4; float32 with 4 (256 threads): 3;
-// float64 (256 threads): 2.
+// float64 (256 or 128 threads): 2.
 template <typename T, int V>
 struct MinBlocks {
     static constexpr int value = sizeof(T) == 4 ? (V == 8 ? 4 : 3) : 2;
@@ -1074,6 +1074,7 @@ void* fine_kernel_ptr()
 
 void* fine_kernel(int precision, int scheme, int vpt)
 {
+    if (precision == 0 && vpt == 8) return scheme == 1 ? fine_kernel_ptr<double, 1, 8>() : fine_kernel_ptr<double, 0, 8>();
     if (precision == 0) return scheme == 1 ? fine_kernel_ptr<double, 1, 4>() : fine_kernel_ptr<double, 0, 4>();
     if (vpt == 8) return scheme == 1 ? fine_kernel_ptr<float, 1, 8>() : fine_kernel_ptr<float, 0, 8>();
     return scheme == 1 ? fine_kernel_ptr<float, 1, 4>() : fine_kernel_ptr<float, 0, 4>();
@@ -1108,7 +1109,7 @@ static void raise_smem(const void* fn, int max_smem)
 
 void prepare_fine_kernels(int max_smem)
 {
-    const int vp[3][2] = {{0, 4}, {1, 4}, {1, 8}};
+    const int vp[4][2] = {{0, 4}, {0, 8}, {1, 4}, {1, 8}};
     for (auto& c : vp)
         for (int sch = 0; sch < 2; ++sch) raise_smem(fine_kernel(c[0], sch, c[1]), max_smem);
     raise_smem(reinterpret_cast<const void*>(&k_lift<double>), max_smem);
@@ -1134,7 +1135,6 @@ cudaError_t launch_fine_run(int precision, int scheme, int vpt, const Inst* inst
                             unsigned long long* ticket, int* status, long long wait_ns, int grid, size_t smem,
                             cudaStream_t s, int poison)
 {
-    if (precision == 0) vpt = 4;
     void* args[] = {(void*)&insts, (void*)&st, (void*)&prefix, (void*)&active, (void*)&nsteps,
                     (void*)&ticket, (void*)&status, (void*)&wait_ns, (void*)&poison};
     return cudaLaunchKernel(fine_kernel(precision, scheme, vpt), dim3(grid), dim3(CHUNK / vpt), args, smem, s);
