@@ -1334,7 +1334,15 @@ __device__ __forceinline__ void fused_walk(const FInst* __restrict__ insts, cons
 // Branch-free minmod: the value of smaller magnitude when a and b have the
 // same sign, else 0 (equal to minmod() for every finite pair).
 __device__ __forceinline__ float mm2(float a, float b) { return fminf(fmaxf(b, fminf(a, 0.0f)), fmaxf(a, 0.0f)); }
-__device__ __forceinline__ double mm2(double a, double b) { return fmin(fmax(b, fmin(a, 0.0)), fmax(a, 0.0)); }
+// float64: the same selection on the IEEE bit patterns with integer
+// operations (equal sign bits: the smaller magnitude, else 0), off this
+// part's reduced-rate FP64 pipe
+__device__ __forceinline__ double mm2(double a, double b)
+{
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const long long ma = ia & 0x7fffffffffffffffLL, mb = ib & 0x7fffffffffffffffLL;
+    return (ia ^ ib) >= 0 ? __longlong_as_double(ma < mb ? ia : ib) : 0.0;
+}
 __device__ __forceinline__ float mmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ float mmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double mmin(double a, double b) { return fmin(a, b); }
@@ -1426,8 +1434,13 @@ __device__ __forceinline__ void fu_pass_m(const T* __restrict__ cen, const T* __
             for (int l = 0; l < VEC; ++l) {
                 const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
                 const T e = cc - a1.x[l], d1 = ad.x[l] - cc, d2 = a1.x[l] - af.x[l];
-                const T lo = mmin(e, T(0)), hi = mmax(e, T(0));  // minmod(e, x) = x clamped to [lo, hi]
-                const T D = tfma(T(0.5), mmin(mmax(d1, lo), hi) - mmin(mmax(d2, lo), hi), e);
+                T D;
+                if constexpr (sizeof(T) == sizeof(float)) {
+                    const T lo = mmin(e, T(0)), hi = mmax(e, T(0));  // minmod(e, x) = x clamped to [lo, hi]
+                    D = tfma(T(0.5), mmin(mmax(d1, lo), hi) - mmin(mmax(d2, lo), hi), e);
+                } else {
+                    D = tfma(T(0.5), mm2(e, d1) - mm2(e, d2), e);
+                }
                 T fs = tfma(-nvx_, D, cc);
                 if (!BND || (r > 0 && r < nvx - 1)) {
                     fs = tfma(-k.gE, u - d, fs);
