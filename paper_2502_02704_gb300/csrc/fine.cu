@@ -434,6 +434,11 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     const int nx = I.nx, nv = I.nv, ldv = I.ldv, bc = I.bc, tw = 3 * nv;
     const int c0 = xt * I.tx, c1 = min(nx, c0 + I.tx), ncols = c1 - c0;
     const int ne = ncols + 2 * H;
+    // odd tiles march right to left (the mirror image: v_x and the upwind side
+    // reversed, the same f* bit for bit), so two neighbouring tiles reach
+    // their shared halo columns together and the second read finds them in L2
+    const bool rev = (xt & 1) != 0;
+    const int cbase = rev ? c1 - 1 + H : c0 - H, cdir = rev ? -1 : 1;
     const int pin = (S.cur + s - 1) & 1, pout = (S.cur + s) & 1;
     const T* __restrict__ gin = reinterpret_cast<const T*>(I.g[pin]);
     T* __restrict__ gout = reinterpret_cast<T*>(I.g[pout]);
@@ -465,7 +470,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     auto issue = [&](int e) {
         if (load && e < ne) {
             bool fl;
-            int cc = map_col(c0 - H + e, nx, bc, fl);
+            int cc = map_col(cbase + cdir * e, nx, bc, fl);
             const T* src = gin + (size_t)cc * ldv + (fl ? v0f : v0);
             T* dst = myslot + (e % RING) * (NT * V);
 #pragma unroll
@@ -481,7 +486,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
         for (int idx = tid; idx < ne * rowv; idx += NT) {
             int e = idx / rowv, k = idx - e * rowv;
             bool fl;
-            int cc = map_col(c0 - H + e, nx, bc, fl);
+            int cc = map_col(cbase + cdir * e, nx, bc, fl);
             cp_async16(stab + e * tw + k * PER, tin + (size_t)cc * tw + k * PER);
         }
         cp_async_commit();
@@ -492,8 +497,8 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     __syncthreads();
 
     const double vxd = -I.L + (jx + 0.5) * I.dv;
-    const bool pos = vxd > 0.0;
-    const T cour = (T)(I.nu * vxd);
+    const bool pos = (vxd > 0.0) != rev;
+    const T cour = rev ? -(T)(I.nu * vxd) : (T)(I.nu * vxd);
     // moment weights in grid units, v = k dv with k = j + 1/2 - nv/2 (half
     // integers, exact in float32, so no weight carries a rounding error into
     // the sums): node q of this thread has k_z = kz0 + q, so sum k_z f =
@@ -506,7 +511,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
     // value of the current state at extended column e for this thread's V velocities
     auto recon = [&](int e, T (&o)[V]) {
         bool fl;
-        map_col(c0 - H + e, nx, bc, fl);
+        map_col(cbase + cdir * e, nx, bc, fl);
         int jxx = fl ? jxf : jx;
         const T* tb = stab + e * tw;
         T txy = tb[jxx] * tb[nv + jy];
@@ -554,12 +559,14 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
 
     const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
     const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
-    T* outp = gout + (size_t)c0 * ldv + v0;
+    T* outp = gout + (size_t)(rev ? c1 - 1 : c0) * ldv + v0;
+    const long long ostep = rev ? -(long long)ldv : (long long)ldv;
     // float64 steps two x cells per loop body (the window rotation becomes
     // register renaming: +2 % measured); float32 one (unrolling spills there)
     constexpr int XUNROLL = sizeof(T) == 8 ? 2 : 1;
 #pragma unroll XUNROLL
-    for (int i = 0; i < ncols; ++i, outp += ldv) {
+    for (int i = 0; i < ncols; ++i, outp += ostep) {
+        const int li = rev ? ncols - 1 - i : i;  // the column within the tile
         T fs[V];
         if (H == 2) {
             T fnn[V];
@@ -606,7 +613,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
             if constexpr (sizeof(T) == sizeof(double)) {
                 // the reverse sweep of the gradient records every step's f*
                 if (I.trace) {
-                    double* tp = I.trace + ((size_t)(s - 1) * nx + c0 + i) * ldv + v0;
+                    double* tp = I.trace + ((size_t)(s - 1) * nx + c0 + li) * ldv + v0;
 #pragma unroll
                     for (int k = 0; k < NV4; ++k) st4(tp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
                 }
@@ -630,7 +637,7 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
             for (int q = 0; q < 5; ++q) r[q] = T(0);
         }
         T tot = warp_sum5(r, lane);
-        if (writer) red[(i * NW + warp) * 5 + qsel] = tot;
+        if (writer) red[(li * NW + warp) * 5 + qsel] = tot;
     }
     cp_async_wait<0>();
     __syncthreads();
