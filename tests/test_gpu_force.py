@@ -139,6 +139,39 @@ def test_test3_full_size_beams_against_oracle(precision):
     assert f_rel_err(fg, f0) < 1e-14
 
 
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+def test_test3_full_size_muscl_batch_on_the_fused_step_against_oracle(precision):
+    # Test 3 at its full size with MUSCL-minmod x fluxes, four instances in
+    # one persistent fused launch (16 CTAs of 16 rows, walks of at least three
+    # columns), 5 steps from the beams: every instance's f and moments
+    # against the oracle's
+    nx, nvx, nvp, L = 100, 256, 16, 8.0
+    E = W.test3_force(nx)
+    k = _vkin(nx, nvx, nvp, L, pr.PR_BC_PERIODIC, 1e-5, pr.PR_MUSCL, E)
+    dt = O.v_fine_dt_stab(k, 0.5)
+    f0 = _beams_f_oracle(k)
+    inst = pr.ForceInstance(nx, nvx, nvp, dt, L=L, x0=0.0, x1=2.0, eps=1e-5, E=E)
+    b = pr.pr_force_create([inst] * 4, pr.PR_MUSCL, precision)
+    try:
+        assert pr.pr_force_config(b) == (16, 4096)
+        assert pr.pr_force_get_march(b) >= 3 and pr.pr_force_get_persistent(b, 5) == 1
+        for i in range(4):
+            pr.pr_force_set_f(b, i, f0)
+        pr.pr_force_run(b, 5)
+        got = [(pr.pr_force_get_f(b, i), pr.pr_force_moments(b, i)) for i in range(4)]
+    finally:
+        pr.pr_force_destroy(b)
+    O.set_threads(16)
+    try:
+        fo = O.v_fine_run(k, dt, 5, f0)
+    finally:
+        O.set_threads(1)
+    Vo = O.v_project(k, fo, conserved=True)
+    for f, V in got:
+        assert f_rel_err(f, fo) < (1e-12 if precision == pr.PR_FP64 else 2e-6)
+        assert moment_rel_err(V, Vo) < TOL[precision]
+
+
 def test_coarse_step_with_source_matches_oracle():
     nx, N, T = 24, 4, 0.08
     E = W.test3_force(nx)
