@@ -55,25 +55,55 @@ __global__ void k_adj_seed(Inst I, const double* lamV, double* lam)
 // coalesced.
 constexpr int ACT = 512;
 
+// One exchange of a transposed butterfly over lane bit w: lanes with the bit
+// clear keep values 0..n-1 and send n..2n-1 (the others the reverse).
+template <int n>
+__device__ __forceinline__ void adj_xchg(double (&y)[8], int lane, int w)
+{
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        const double send = up ? y[j] : y[j + n];
+        const double keep = up ? y[j + n] : y[j];
+        y[j] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+}
+
+// Warp sums of eight values: lanes 4q .. 4q+3 return the sum of value q.
+__device__ __forceinline__ double warp_sum8(double (&y)[8], int lane)
+{
+    adj_xchg<4>(y, lane, 16);
+    adj_xchg<2>(y, lane, 8);
+    adj_xchg<1>(y, lane, 4);
+    y[0] += __shfl_xor_sync(0xffffffffu, y[0], 2);
+    y[0] += __shfl_xor_sync(0xffffffffu, y[0], 1);
+    return y[0];
+}
+
+// Sum of NV (<= 8) per-thread values over the CTA, the totals in every
+// thread: a transposed butterfly in each warp, the warp sums through shared
+// memory (sh: ADJ_SH doubles), the same butterfly over them in warp 0.
+constexpr int ADJ_SH = 32 * 8 + 8;
 template <int NV>
 __device__ void block_sum_n(double (&x)[NV], double* sh)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    static_assert(NV <= 8, "at most eight sums");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    double y[8];
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-#pragma unroll
-        for (int o = 16; o; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+    for (int q = 0; q < 8; ++q) y[q] = q < NV ? x[q] : 0.0;
+    double r = warp_sum8(y, lane);
+    if ((lane & 3) == 0) sh[warp * 8 + (lane >> 2)] = r;
     __syncthreads();
-    if (lane == 0)
+    if (warp == 0) {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) sh[warp * NV + q] = x[q];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += sh[w * NV + q];
-        x[q] = t;
+        for (int q = 0; q < 8; ++q) y[q] = lane < nw ? sh[lane * 8 + q] : 0.0;
+        r = warp_sum8(y, lane);
+        if ((lane & 3) == 0) sh[32 * 8 + (lane >> 2)] = r;
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) x[q] = sh[32 * 8 + q];
     __syncthreads();
 }
 
@@ -230,7 +260,7 @@ __global__ void __launch_bounds__(APT) k_adj_apply(Inst I, const double* lam, co
         }
     }
     __syncthreads();
-    const int p = blockIdx.y * APT + threadIdx.x;
+    const int p = blockIdx.y * blockDim.x + threadIdx.x;
     if (p >= np) return;
     const int jy = p / nv, jz = p - jy * nv;
     const double vy = -I.L + (jy + 0.5) * I.dv, vz = -I.L + (jz + 0.5) * I.dv, vyz2 = vy * vy + vz * vz;
@@ -303,20 +333,31 @@ cudaError_t adj_seed(const Inst& I, const double* lamV, double* lam, cudaStream_
     return cudaGetLastError();
 }
 
-static size_t adj_smem(const Inst& I) { return (5 * (size_t)I.nv + (ACT / 32) * 6) * sizeof(double); }
+static size_t adj_smem(const Inst& I) { return (5 * (size_t)I.nv + ADJ_SH) * sizeof(double); }
+
+// Threads of the per-column kernels: two (v_y, v_z) planes each (nv^2 / 2,
+// rounded up to whole warps, at most ACT), so the planes split evenly and two
+// CTAs share an SM at the kernels' register counts.
+static int adj_threads(const Inst& I)
+{
+    const int t = ((I.nv * I.nv + 1) / 2 + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > ACT ? ACT : t);
+}
 
 cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const double* msum, double* coef,
                      double* eps_acc, double* lam_out, cudaStream_t s)
 {
-    k_adj_coef<<<I.nx, ACT, adj_smem(I), s>>>(I, lam_in, g, msum, coef, eps_acc);
-    k_adj_apply<<<dim3(I.nx, (I.nv * I.nv + APT - 1) / APT), APT, 4 * (size_t)I.nv * sizeof(double), s>>>(
-        I, lam_in, coef, lam_out);
+    k_adj_coef<<<I.nx, adj_threads(I), adj_smem(I), s>>>(I, lam_in, g, msum, coef, eps_acc);
+    // the planes of a column split evenly over as few CTAs of at most APT
+    // threads as hold them (24^2 planes: three CTAs of 192)
+    const int np = I.nv * I.nv, nb = (np + APT - 1) / APT, t = ((np + nb - 1) / nb + 31) / 32 * 32;
+    k_adj_apply<<<dim3(I.nx, (np + t - 1) / t), t, 4 * (size_t)I.nv * sizeof(double), s>>>(I, lam_in, coef, lam_out);
     return cudaGetLastError();
 }
 
 cudaError_t adj_lift(const Inst& I, const double* lam, const double* Uin, double* dU0, cudaStream_t s)
 {
-    k_adj_lift<<<I.nx, ACT, adj_smem(I), s>>>(I, lam, Uin, dU0);
+    k_adj_lift<<<I.nx, adj_threads(I), adj_smem(I), s>>>(I, lam, Uin, dU0);
     return cudaGetLastError();
 }
 
