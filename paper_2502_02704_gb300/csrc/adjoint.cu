@@ -348,10 +348,8 @@ cudaError_t adj_step(const Inst& I, const double* lam_in, const double* g, const
                      double* eps_acc, double* lam_out, cudaStream_t s)
 {
     k_adj_coef<<<I.nx, adj_threads(I), adj_smem(I), s>>>(I, lam_in, g, msum, coef, eps_acc);
-    // the planes of a column split evenly over as few CTAs of at most APT
-    // threads as hold them (24^2 planes: three CTAs of 192)
-    const int np = I.nv * I.nv, nb = (np + APT - 1) / APT, t = ((np + nb - 1) / nb + 31) / 32 * 32;
-    k_adj_apply<<<dim3(I.nx, (np + t - 1) / t), t, 4 * (size_t)I.nv * sizeof(double), s>>>(I, lam_in, coef, lam_out);
+    k_adj_apply<<<dim3(I.nx, (I.nv * I.nv + APT - 1) / APT), APT, 4 * (size_t)I.nv * sizeof(double), s>>>(
+        I, lam_in, coef, lam_out);
     return cudaGetLastError();
 }
 
