@@ -268,8 +268,10 @@ def _median_s(f, reps):
 
 def _serial_chain(pr, np, torch, inst, V0, N, nf, precision, reps):
     """The serial fine chain U^n = P F L(U^{n-1}), n = 1..N (what parareal
-    converges to at K = N), on one instance of the batch path in the given
-    precision.  Returns (seconds, median of reps; chain [N+1, 5, nx])."""
+    converges to at K = N), one pr_batch_propagate of one instance per slice
+    in the given precision (the cluster-resident run where the slice fits a
+    cluster, else the tiled one).  Returns (seconds, median of reps; chain
+    [N+1, 5, nx])."""
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
     one = pr.pr_batch_create([inst], precision)
@@ -278,8 +280,7 @@ def _serial_chain(pr, np, torch, inst, V0, N, nf, precision, reps):
     try:
         def run():
             for n in range(1, N + 1):
-                pr.pr_batch_set_initial_device(one, 0, chain[n - 1], pr.PR_CONSERVED, stream)
-                pr.pr_batch_run(one, nf, stream)
+                pr.pr_batch_propagate(one, nf, chain[n - 1], stream)
                 pr.pr_batch_moments_device(one, 0, chain[n], stream)
             torch.cuda.synchronize()
 

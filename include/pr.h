@@ -282,6 +282,20 @@ int pr_batch_run(pr_batch* b, int nsteps, void* stream);
  * outside the batch, nsteps < 0), PR_ECUDA. */
 int pr_batch_run_range(pr_batch* b, int first, int count, int nsteps, void* stream);
 
+/* The fine propagation P F L of Algorithm 2 for every instance (Eqs. 17,
+ * 11-13, 18): lift from a conserved state (U_dev: the instances' states one
+ * after another, [5][nx_i] each, device memory; NULL: the lift sources of the
+ * last pr_batch_set_initial calls), run nsteps >= 1 fine steps and project;
+ * read the moments with pr_batch_moments or pr_batch_moments_device.  When
+ * every instance has one shape whose slice fits a thread-block cluster's
+ * shared memory (mixed precision, the Maxwellian lifting, nv = 8 or 16) the
+ * run is cluster-resident (one cluster per instance, f never leaves shared
+ * memory), else the tiled persistent run.  The stored distributions are
+ * unspecified afterwards (set them again before pr_batch_run).  Enqueued on
+ * stream.  Errors: PR_EINVAL, PR_ECUDA (PR_ETIMEOUT, PR_ENONPHYS at the next
+ * synchronising call). */
+int pr_batch_propagate(pr_batch* b, const double* U_dev, int nsteps, void* stream);
+
 /* Moments (Eq. 18) of instance i into host out[5][nx_i]. Synchronous. */
 int pr_batch_moments(pr_batch* b, int i, int kind, double* out);
 

@@ -120,6 +120,7 @@ _SIGS = {
     "pr_fine_step_noalloc": (C.c_int, [C.POINTER(pr_instance), _VP, _VP, _VP]),
     "pr_fine_dt_stab": (C.c_int, [C.POINTER(pr_instance), C.c_double, _D]),
     "pr_batch_run_range": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int, _VP]),
+    "pr_batch_propagate": (C.c_int, [_VP, _VP, C.c_int, _VP]),
     "pr_probe_fp64_peak": (C.c_int, [_D]),
     "pr_force_create": (C.c_int, [C.POINTER(_VP), C.POINTER(pr_force_instance), C.c_int, C.c_int, C.c_int]),
     "pr_force_destroy": (C.c_int, [_VP]),
@@ -426,6 +427,14 @@ def pr_batch_run(b, nsteps, stream=None):
 
 def pr_batch_run_range(b, first, count, nsteps, stream=None):
     _batch_check(b, lib().pr_batch_run_range(b.ptr, int(first), int(count), int(nsteps), _stream(stream)))
+
+
+def pr_batch_propagate(b, nsteps, U_dev=None, stream=None):
+    """P F L of every instance (pr_batch_propagate): lift from U_dev (a device
+    tensor holding the instances' conserved states one after another) or from
+    the last set_initial sources, nsteps fine steps, projection."""
+    ptr = _dptr(U_dev) if U_dev is not None else None
+    _batch_check(b, lib().pr_batch_propagate(b.ptr, ptr, int(nsteps), _stream(stream)))
 
 
 def pr_batch_moments(b, i, kind=PR_CONSERVED):

@@ -646,6 +646,42 @@ int pr_batch_run(pr_batch* b, int nsteps, void* stream)
     return enqueue_run(b, nsteps, 0, pick(b, stream), true);
 }
 
+int pr_batch_propagate(pr_batch* b, const double* U_dev, int nsteps, void* stream)
+{
+    if (!b) return PR_EINVAL;
+    if (nsteps < 1) return bfail(b, PR_EINVAL, "nsteps must be >= 1");
+    cudaStream_t s = pick(b, stream);
+    if (U_dev) {  // the lift sources: the instances' conserved states one after another
+        size_t off = 0;
+        for (const Inst& I : b->h) {
+            BCUDA(b, cudaMemcpyAsync(const_cast<double*>(I.Uin), U_dev + off, sizeof(double) * 5 * I.nx,
+                                     cudaMemcpyDeviceToDevice, s));
+            off += 5 * (size_t)I.nx;
+        }
+    }
+    // cluster-resident when every instance has one shape that fits a
+    // cluster (the rule of the parareal fine phase)
+    const Inst& I0 = b->h[0];
+    bool same = true;
+    for (const Inst& I : b->h) same = same && I.nx == I0.nx && I.nv == I0.nv;
+    int C = 0, w = 0;
+    size_t sm = 0;
+    const bool fits = same && b->precision == PR_MIXED && b->lift_order == 0 &&
+                      prk::fine_cluster_plan(I0.nx, I0.nv, max_optin_smem(), &C, &w, &sm);
+    const int resident = fits ? prk::fine_cluster_resident(b->scheme, I0.nv, C, sm) : 0;
+    if (fits && resident > 0 && b->n <= 2 * resident) {
+        const prk::Active all{0, b->n};
+        BCUDA(b, cudaMemcpyAsync(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, s));
+        BCUDA(b, prk::launch_fine_cluster(b->scheme, I0.nv, b->d_inst, b->d_active, b->n, nsteps, C, w, sm,
+                                          b->d_status, s));
+        g_launches += 1;
+        return PR_OK;
+    }
+    const int rc = lift_instances(b, 0, b->n, s);
+    if (rc) return rc;
+    return enqueue_run(b, nsteps, 0, s, true);
+}
+
 int pr_batch_run_range(pr_batch* b, int first, int count, int nsteps, void* stream)
 {
     if (!b) return PR_EINVAL;

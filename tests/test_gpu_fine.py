@@ -264,3 +264,32 @@ def test_autotuned_layout_in_float32_keeps_results():
         assert pr.pr_batch_vpt(b) == 4
     finally:
         pr.pr_batch_destroy(b)
+
+
+@pytest.mark.parametrize("precision,nv", [(pr.PR_MIXED, 16), (pr.PR_MIXED, 24), (pr.PR_FP64, 16)])
+def test_propagate_is_the_fine_propagator(precision, nv):
+    # P F L of three instances of one shape: cluster-resident for mixed
+    # 64 x 16^3 slices, the tiled run otherwise; from device states, then
+    # again from the stored lift sources
+    import torch
+
+    nx, nf = 64, 12
+    dt = pr.fine_dt(nx, nv, 8.0)
+    epss = (1e-2, 1e-3, 1.0)
+    insts = [pr.instance(nx, nv, dt, bc=pr.PR_BC_OUTFLOW, eps=e) for e in epss]
+    Us = [W.sod(nx), W.sod(nx, split=0.3), W.smooth_periodic(nx)]
+    Vs = np.concatenate([O.prim_to_cons(U) for U in Us])
+    b = pr.pr_batch_create(insts, precision)
+    try:
+        pr.pr_batch_propagate(b, nf, torch.tensor(Vs, device="cuda"))
+        got = [pr.pr_batch_moments(b, i) for i in range(3)]
+        pr.pr_batch_propagate(b, nf)
+        again = [pr.pr_batch_moments(b, i) for i in range(3)]
+    finally:
+        pr.pr_batch_destroy(b)
+    for i, e in enumerate(epss):
+        k = _kin(nx, nv, 8.0, pr.PR_BC_OUTFLOW, e, pr.PR_UPWIND)
+        Vo = O.project(k, O.fine_run(k, dt, nf, O.lift(k, Us[i])), conserved=True)
+        tol = TOL_FP64 if precision == pr.PR_FP64 else TOL_MIXED
+        assert moment_rel_err(got[i], Vo) < tol, i
+        assert np.array_equal(got[i], again[i])
