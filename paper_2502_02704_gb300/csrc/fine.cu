@@ -129,6 +129,14 @@ __device__ __forceinline__ double minmod2(double a, double b)
     const long long r = ma < mb ? ia : ib;
     return (ia ^ ib) >= 0 ? __longlong_as_double(r) : 0.0;
 }
+// Packed float32 pairs: the limiter per lane, and a - b as one fused
+// multiply-add b (-1) + a (exact product, one rounding: the value of the
+// scalar subtraction).
+__device__ __forceinline__ float2 minmod2(float2 a, float2 b)
+{
+    return make_float2(minmod2(a.x, b.x), minmod2(a.y, b.y));
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 
 // Upwind interface value at the face between f0 and f1 (neighbours fm, f2):
 // from the left (f0 side) when v_x > 0, from the right otherwise (Eq. 13 with
@@ -533,111 +541,248 @@ __device__ void fine_item(const Inst& I, const InstState& S, int s, int nsteps, 
         issue(e + RING);
     };
 
-    // March along x.  State before output cell i: fc = f_i, fn = f_{i+1},
-    // dm = f_i - f_{i-1}, dp = f_{i+1} - f_i (MUSCL), sp = face value at i-1/2.
-    T fc[V], fn[V], dm[V], dp[V], sp[V];
-    if (H == 2) {
-        T f0[V], f1[V];
-        recon(0, f0);
-        recon(1, f1);
-        recon(2, fc);
-        recon(3, fn);
-#pragma unroll
-        for (int q = 0; q < V; ++q) {
-            T d0 = f1[q] - f0[q];
-            dm[q] = fc[q] - f1[q];
-            dp[q] = fn[q] - fc[q];
-            sp[q] = pos ? f1[q] + T(0.5) * minmod2(d0, dm[q]) : fc[q] - T(0.5) * minmod2(dm[q], dp[q]);
-        }
-    } else {
-        T f0[V];
-        recon(0, f0);
-        recon(1, fc);
-#pragma unroll
-        for (int q = 0; q < V; ++q) sp[q] = pos ? f0[q] : fc[q];
-    }
-
     const int qsel = lane < 4 ? 0 : lane < 8 ? 1 : lane < 16 ? 2 : lane < 24 ? 3 : 4;
     const bool writer = lane == 0 || lane == 4 || lane == 8 || lane == 16 || lane == 24;
     T* outp = gout + (size_t)(rev ? c1 - 1 : c0) * ldv + v0;
     const long long ostep = rev ? -(long long)ldv : (long long)ldv;
-    // float64 steps two x cells per loop body (the window rotation becomes
-    // register renaming: +2 % measured); float32 one (unrolling spills there)
-    constexpr int XUNROLL = sizeof(T) == 8 ? 2 : 1;
-#pragma unroll XUNROLL
-    for (int i = 0; i < ncols; ++i, outp += ostep) {
-        const int li = rev ? ncols - 1 - i : i;  // the column within the tile
-        T fs[V];
-        if (H == 2) {
-            T fnn[V];
-            recon(i + 4, fnn);
-            if (pos) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // float32: the arithmetic on pairs of v_z nodes with the packed
+        // two-lane instructions (add, multiply, fused multiply-add, IEEE
+        // round-to-nearest in each lane): half the issue slots of scalar code
+        constexpr int V2 = V / 2;
+        const float2 wg2 = make_float2(wg, wg), h2 = make_float2(0.5f, 0.5f), mh2 = make_float2(-0.5f, -0.5f);
+        const float2 mc2 = make_float2(-cour, -cour);
+        auto recon2 = [&](int e, float2 (&o)[V2]) {
+            bool fl;
+            map_col(cbase + cdir * e, nx, bc, fl);
+            const int jxx = fl ? jxf : jx;
+            const float* tb = stab + e * tw;
+            const float txy = tb[jxx] * tb[nv + jy];
+            const float2 t2 = make_float2(txy, txy);
+            float2 tz[V2];
 #pragma unroll
-                for (int q = 0; q < V; ++q) {
-                    T dpp = fnn[q] - fn[q];
-                    T face = fc[q] + T(0.5) * minmod2(dm[q], dp[q]);
-                    fs[q] = fc[q] - cour * (face - sp[q]);
-                    sp[q] = face;
-                    fc[q] = fn[q];
-                    fn[q] = fnn[q];
-                    dm[q] = dp[q];
-                    dp[q] = dpp;
+            for (int k = 0; k < NV4; ++k) {
+                const float4 z = *reinterpret_cast<const float4*>(tb + 2 * nv + jz + 4 * k);
+                tz[2 * k] = make_float2(z.x, z.y);
+                tz[2 * k + 1] = make_float2(z.z, z.w);
+            }
+            cp_async_wait<RING - 1>();
+            if (load) {
+                const float* sl = myslot + (e % RING) * (NT * V);
+#pragma unroll
+                for (int k = 0; k < NV4; ++k) {
+                    const float4 gv = *reinterpret_cast<const float4*>(sl + 4 * k);
+                    o[2 * k] = __ffma2_rn(wg2, make_float2(gv.x, gv.y), __fmul2_rn(t2, tz[2 * k]));
+                    o[2 * k + 1] = __ffma2_rn(wg2, make_float2(gv.z, gv.w), __fmul2_rn(t2, tz[2 * k + 1]));
                 }
             } else {
 #pragma unroll
+                for (int k = 0; k < V2; ++k) o[k] = __fmul2_rn(t2, tz[k]);
+            }
+            issue(e + RING);
+        };
+        // Output cell i: fs = f_i - cour (face_{i+1/2} - face_{i-1/2}), sp =
+        // face_{i-1/2}.  Upwind from the left (pos): face_{i+1/2} = f_i (+ half
+        // the minmod of f_i - f_{i-1} and f_{i+1} - f_i); from the right:
+        // f_{i+1} (- half the minmod of f_{i+1} - f_i and f_{i+2} - f_{i+1}).
+        // A thread's side is fixed, so each side carries only the state it
+        // needs: fc = f_i, sp, and fb = f_i - f_{i-1} (pos, MUSCL) or f_{i+1}.
+        float2 fc[V2], fb[V2], sp[V2];
+        if (H == 2) {
+            float2 f0[V2], f1[V2];
+            recon2(0, f0);
+            recon2(1, f1);
+            recon2(2, fc);
+            if (pos) {
+#pragma unroll
+                for (int k = 0; k < V2; ++k) {
+                    fb[k] = sub2(fc[k], f1[k]);
+                    sp[k] = __ffma2_rn(h2, minmod2(sub2(f1[k], f0[k]), fb[k]), f1[k]);
+                }
+            } else {
+                recon2(3, fb);
+#pragma unroll
+                for (int k = 0; k < V2; ++k)
+                    sp[k] = __ffma2_rn(mh2, minmod2(sub2(fc[k], f1[k]), sub2(fb[k], fc[k])), fc[k]);
+            }
+        } else {
+            float2 f0[V2];
+            recon2(0, f0);
+            recon2(1, fc);
+#pragma unroll
+            for (int k = 0; k < V2; ++k) sp[k] = pos ? f0[k] : fc[k];
+        }
+        // extended column read for output cell i: f_{i+1} (pos or upwind) or f_{i+2}
+        const int E0 = H == 2 ? (pos ? 3 : 4) : 2;
+        for (int i = 0; i < ncols; ++i, outp += ostep) {
+            const int li = rev ? ncols - 1 - i : i;  // the column within the tile
+            float2 fs[V2], fx[V2];
+            recon2(i + E0, fx);
+            if (H == 2) {
+                if (pos) {
+#pragma unroll
+                    for (int k = 0; k < V2; ++k) {
+                        const float2 dp = sub2(fx[k], fc[k]);
+                        const float2 face = __ffma2_rn(h2, minmod2(fb[k], dp), fc[k]);
+                        fs[k] = __ffma2_rn(mc2, sub2(face, sp[k]), fc[k]);
+                        sp[k] = face;
+                        fb[k] = dp;
+                        fc[k] = fx[k];
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < V2; ++k) {
+                        const float2 face = __ffma2_rn(mh2, minmod2(sub2(fb[k], fc[k]), sub2(fx[k], fb[k])), fb[k]);
+                        fs[k] = __ffma2_rn(mc2, sub2(face, sp[k]), fc[k]);
+                        sp[k] = face;
+                        fc[k] = fb[k];
+                        fb[k] = fx[k];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < V2; ++k) {
+                    const float2 face = pos ? fc[k] : fx[k];
+                    fs[k] = __ffma2_rn(mc2, sub2(face, sp[k]), fc[k]);
+                    sp[k] = face;
+                    fc[k] = fx[k];
+                }
+            }
+            T r[5];
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < NV4; ++k)
+                    __stcg(reinterpret_cast<float4*>(outp + 4 * k),
+                           make_float4(fs[2 * k].x, fs[2 * k].y, fs[2 * k + 1].x, fs[2 * k + 1].y));
+                // node q of pair k is 2k + lane: sum f, sum q f, sum q^2 f in
+                // pairs, the two lanes added last; explicit fused operations
+                // so that every build rounds the column sums alike
+                float2 a0 = fs[0];
+                float2 a1 = __fmul2_rn(make_float2(0.0f, 1.0f), fs[0]);
+                float2 a2 = a1;
+#pragma unroll
+                for (int k = 1; k < V2; ++k) {
+                    const float q0 = (float)(2 * k), q1 = (float)(2 * k + 1);
+                    a0 = __fadd2_rn(a0, fs[k]);
+                    a1 = __ffma2_rn(make_float2(q0, q1), fs[k], a1);
+                    a2 = __ffma2_rn(make_float2(q0 * q0, q1 * q1), fs[k], a2);
+                }
+                const float s0 = a0.x + a0.y, t1 = a1.x + a1.y, t2 = a2.x + a2.y;
+                r[0] = s0;
+                r[1] = kx * s0;
+                r[2] = ky * s0;
+                r[3] = fmaf(kz0, s0, t1);
+                r[4] = fmaf(kk0, s0, fmaf(kz1, t1, t2));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) r[q] = T(0);
+            }
+            T tot = warp_sum5(r, lane);
+            if (writer) red[(li * NW + warp) * 5 + qsel] = tot;
+        }
+    } else {
+        // March along x.  State before output cell i: fc = f_i, fn = f_{i+1},
+        // dm = f_i - f_{i-1}, dp = f_{i+1} - f_i (MUSCL), sp = face value at i-1/2.
+        T fc[V], fn[V], dm[V], dp[V], sp[V];
+        if (H == 2) {
+            T f0[V], f1[V];
+            recon(0, f0);
+            recon(1, f1);
+            recon(2, fc);
+            recon(3, fn);
+    #pragma unroll
+            for (int q = 0; q < V; ++q) {
+                T d0 = f1[q] - f0[q];
+                dm[q] = fc[q] - f1[q];
+                dp[q] = fn[q] - fc[q];
+                sp[q] = pos ? f1[q] + T(0.5) * minmod2(d0, dm[q]) : fc[q] - T(0.5) * minmod2(dm[q], dp[q]);
+            }
+        } else {
+            T f0[V];
+            recon(0, f0);
+            recon(1, fc);
+    #pragma unroll
+            for (int q = 0; q < V; ++q) sp[q] = pos ? f0[q] : fc[q];
+        }
+
+        // float64 steps two x cells per loop body (the window rotation becomes
+        // register renaming: +2 % measured); float32 one (unrolling spills there)
+        constexpr int XUNROLL = sizeof(T) == 8 ? 2 : 1;
+    #pragma unroll XUNROLL
+        for (int i = 0; i < ncols; ++i, outp += ostep) {
+            const int li = rev ? ncols - 1 - i : i;  // the column within the tile
+            T fs[V];
+            if (H == 2) {
+                T fnn[V];
+                recon(i + 4, fnn);
+                if (pos) {
+    #pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        T dpp = fnn[q] - fn[q];
+                        T face = fc[q] + T(0.5) * minmod2(dm[q], dp[q]);
+                        fs[q] = fc[q] - cour * (face - sp[q]);
+                        sp[q] = face;
+                        fc[q] = fn[q];
+                        fn[q] = fnn[q];
+                        dm[q] = dp[q];
+                        dp[q] = dpp;
+                    }
+                } else {
+    #pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        T dpp = fnn[q] - fn[q];
+                        T face = fn[q] - T(0.5) * minmod2(dp[q], dpp);
+                        fs[q] = fc[q] - cour * (face - sp[q]);
+                        sp[q] = face;
+                        fc[q] = fn[q];
+                        fn[q] = fnn[q];
+                        dm[q] = dp[q];
+                        dp[q] = dpp;
+                    }
+                }
+            } else {
+                recon(i + 2, fn);
+    #pragma unroll
                 for (int q = 0; q < V; ++q) {
-                    T dpp = fnn[q] - fn[q];
-                    T face = fn[q] - T(0.5) * minmod2(dp[q], dpp);
+                    T face = pos ? fc[q] : fn[q];
                     fs[q] = fc[q] - cour * (face - sp[q]);
                     sp[q] = face;
                     fc[q] = fn[q];
-                    fn[q] = fnn[q];
-                    dm[q] = dp[q];
-                    dp[q] = dpp;
                 }
             }
-        } else {
-            recon(i + 2, fn);
-#pragma unroll
-            for (int q = 0; q < V; ++q) {
-                T face = pos ? fc[q] : fn[q];
-                fs[q] = fc[q] - cour * (face - sp[q]);
-                sp[q] = face;
-                fc[q] = fn[q];
-            }
-        }
-        T r[5];
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < NV4; ++k) st4(outp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
-            if constexpr (sizeof(T) == sizeof(double)) {
-                // the reverse sweep of the gradient records every step's f*
-                if (I.trace) {
-                    double* tp = I.trace + ((size_t)(s - 1) * nx + c0 + li) * ldv + v0;
-#pragma unroll
-                    for (int k = 0; k < NV4; ++k) st4(tp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
+            T r[5];
+            if (act) {
+    #pragma unroll
+                for (int k = 0; k < NV4; ++k) st4(outp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
+                if constexpr (sizeof(T) == sizeof(double)) {
+                    // the reverse sweep of the gradient records every step's f*
+                    if (I.trace) {
+                        double* tp = I.trace + ((size_t)(s - 1) * nx + c0 + li) * ldv + v0;
+    #pragma unroll
+                        for (int k = 0; k < NV4; ++k) st4(tp + 4 * k, *reinterpret_cast<T(*)[4]>(fs + 4 * k));
+                    }
                 }
+                // the q = 0 terms of t1, t2 vanish (started at q = 1: the same
+                // bits for finite values, two operations fewer per column)
+                T s0 = fs[0], t1 = T(0), t2 = T(0);
+    #pragma unroll
+                for (int q = 1; q < V; ++q) {
+                    s0 += fs[q];
+                    t1 += T(q) * fs[q];
+                    t2 += T(q * q) * fs[q];
+                }
+                r[0] = s0;
+                r[1] = kx * s0;
+                r[2] = ky * s0;
+                r[3] = kz0 * s0 + t1;
+                r[4] = kk0 * s0 + kz1 * t1 + t2;
+            } else {
+    #pragma unroll
+                for (int q = 0; q < 5; ++q) r[q] = T(0);
             }
-            // the q = 0 terms of t1, t2 vanish (started at q = 1: the same
-            // bits for finite values, two operations fewer per column)
-            T s0 = fs[0], t1 = T(0), t2 = T(0);
-#pragma unroll
-            for (int q = 1; q < V; ++q) {
-                s0 += fs[q];
-                t1 += T(q) * fs[q];
-                t2 += T(q * q) * fs[q];
-            }
-            r[0] = s0;
-            r[1] = kx * s0;
-            r[2] = ky * s0;
-            r[3] = kz0 * s0 + t1;
-            r[4] = kk0 * s0 + kz1 * t1 + t2;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) r[q] = T(0);
+            T tot = warp_sum5(r, lane);
+            if (writer) red[(li * NW + warp) * 5 + qsel] = tot;
         }
-        T tot = warp_sum5(r, lane);
-        if (writer) red[(li * NW + warp) * 5 + qsel] = tot;
     }
     cp_async_wait<0>();
     __syncthreads();
