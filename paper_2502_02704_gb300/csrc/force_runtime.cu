@@ -232,7 +232,7 @@ bool ensure_partials(pr_force* b)
         }
         b->part_bytes = need;
     }
-    if (cudaMemset(b->d_part, 0, need) != cudaSuccess) return false;
+    if (prk::zero_now(b->d_part, need, b->stream) != cudaSuccess) return false;
     const int words = 1 + b->n * ((b->nx + b->g.march - 1) / b->g.march);
     if (words > b->fsync_words) {
         cudaFree(b->d_fsync);
@@ -666,7 +666,7 @@ int take_status(pr_force* b)
     int st = 0;
     FCUDA(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
-        cudaMemset(b->d_status, 0, sizeof(int));
+        prk::zero_now(b->d_status, sizeof(int), b->stream);
         return ffail(b, st,
                      st == PR_ENONPHYS   ? "a density or temperature became non-positive"
                      : st == PR_ETIMEOUT ? "a staging wait timed out"
@@ -725,7 +725,7 @@ int pr_force_set_initial(pr_force* b, int i, const double* U, int kind)
     cudaStream_t s = b->stream;
     FCUDA(b, cudaStreamSynchronize(s));
     double* dst = b->d_Ulift + (size_t)i * 5 * nx;
-    FCUDA(b, cudaMemcpy(dst, V.data(), sizeof(double) * 5 * nx, cudaMemcpyHostToDevice));
+    FCUDA(b, prk::copy_now(dst, V.data(), sizeof(double) * 5 * nx, cudaMemcpyHostToDevice, s));
     prf::bind(b, i, dst, nullptr);
     FCUDA(b, prf::upload(b, i, i + 1, s));
     int rc = prf::enqueue_lift_run(b, i, i + 1, 0, s, false);
@@ -745,7 +745,7 @@ int pr_force_set_f(pr_force* b, int i, const double* f)
         b->d_tmp = nullptr;
         return ffail(b, PR_ENOMEM, "staging buffer");
     }
-    FCUDA(b, cudaMemcpy(b->d_tmp, f, sizeof(double) * n, cudaMemcpyHostToDevice));
+    FCUDA(b, prk::copy_now(b->d_tmp, f, sizeof(double) * n, cudaMemcpyHostToDevice, s));
     const int p = b->precision == PR_FP64 ? 0 : 1;
     FCUDA(b, prk::launch_force_load(p, b->d_inst, i, b->d_cur, b->d_tmp, n, s));
     b->sums_ok[i] = 0;
@@ -1004,14 +1004,14 @@ int pr_force_autotune(pr_force* b, int nsteps)
         for (int i = 0; i < b->n; ++i) {
             char* sv = static_cast<char*>(save) + state * i;
             void* f = b->bufs[2 * i + cur[i]];
-            cudaError_t e = to_save ? cudaMemcpy(sv, f, state, cudaMemcpyDeviceToDevice)
-                                    : cudaMemcpy(f, sv, state, cudaMemcpyDeviceToDevice);
+            cudaError_t e = to_save ? prk::copy_now(sv, f, state, cudaMemcpyDeviceToDevice, s)
+                                    : prk::copy_now(f, sv, state, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
         }
         const size_t ub = sizeof(double) * 5 * b->nx * b->n;
-        cudaError_t e = to_save ? cudaMemcpy(saveU, b->d_U, ub, cudaMemcpyDeviceToDevice)
-                                : cudaMemcpy(b->d_U, saveU, ub, cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(b->d_cur, cur.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice);
+        cudaError_t e = to_save ? prk::copy_now(saveU, b->d_U, ub, cudaMemcpyDeviceToDevice, s)
+                                : prk::copy_now(b->d_U, saveU, ub, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = prk::copy_now(b->d_cur, cur.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, s);
         return e;
     };
     struct Cand {

@@ -235,4 +235,26 @@ cudaError_t launch_set_active(const int* dk, Active* active, int first_slice, in
 cudaError_t launch_set_active_multi(const int* dk, const int* nidx, int n_sl, int n_inst, Active* run, Active* lift,
                                     cudaStream_t s);
 
+// Host copy that is complete when it returns and ordered after the work
+// already queued on stream s.  A plain cudaMemcpy from pageable host memory,
+// or between device buffers, may return before its transfer lands, and the
+// transfer runs on the legacy default stream, which the runtime's
+// non-blocking streams neither wait for nor hold back: a kernel queued next on
+// s could read the buffer before the data arrives.
+inline cudaError_t copy_now(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
+// cudaMemset's counterpart: zeroes ordered after the work queued on s and
+// complete when it returns.
+inline cudaError_t zero_now(void* dst, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    const cudaError_t e = cudaMemsetAsync(dst, 0, bytes, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+}
+
 }  // namespace prk

@@ -208,10 +208,11 @@ static int upload_layout(pr_batch* b, const std::vector<int>& txs)
     std::vector<size_t> deps_off;
     int rc = layout_tiles(b, txs, prefix, deps_all, deps_off);
     if (rc) return rc;
-    BCUDA(b, cudaMemcpy(b->d_deps, deps_all.data(), deps_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    BCUDA(b, prk::copy_now(b->d_deps, deps_all.data(), deps_all.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     for (int i = 0; i < b->n; ++i) b->h[i].deps = b->d_deps + deps_off[i];
-    BCUDA(b, cudaMemcpy(b->d_prefix, prefix.data(), prefix.size() * sizeof(long long), cudaMemcpyHostToDevice));
-    BCUDA(b, cudaMemcpy(b->d_inst, b->h.data(), b->h.size() * sizeof(Inst), cudaMemcpyHostToDevice));
+    BCUDA(b, prk::copy_now(b->d_prefix, prefix.data(), prefix.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCUDA(b, prk::copy_now(b->d_inst, b->h.data(), b->h.size() * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
     // launch geometry
     int maxtx = 1, maxnv = 4;
     for (auto& I : b->h) {
@@ -399,8 +400,9 @@ static int create_batch(pr_batch** out, const pr_instance* inst, int n, int prec
     int rc = default_layout(b);
     if (rc) return fail(rc, b->err);
     prk::Active all{0, n};
-    if (cudaMemcpy(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->d_state, b->hstate.data(), sizeof(InstState) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (prk::copy_now(b->d_active, &all, sizeof all, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        prk::copy_now(b->d_state, b->hstate.data(), sizeof(InstState) * n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
         return fail(PR_ECUDA, "initial uploads");
     *out = b;
@@ -416,8 +418,8 @@ static int take_status(pr_batch* b, cudaStream_t s)
     int st = 0;
     BCUDA(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
-        cudaMemset(b->d_status, 0, sizeof(int));
-        cudaMemset(b->d_sync, 0, b->sync_bytes);
+        prk::zero_now(b->d_status, sizeof(int), s);
+        prk::zero_now(b->d_sync, b->sync_bytes, s);
         if (st == PR_ETIMEOUT) return bfail(b, PR_ETIMEOUT, "a device-side wait timed out; the launch was aborted");
         if (st == PR_ENONPHYS) return bfail(b, PR_ENONPHYS, "non-positive density or temperature (or NaN) encountered");
         return bfail(b, st, "device status %d", st);
@@ -948,8 +950,8 @@ extern "C" int pr_batch_autotune(pr_batch* b)
             size_t sz[4] = {gs, gs, ts, ts};
             for (int k = 0; k < 4; ++k) {
                 char* sv = static_cast<char*>(save) + off;
-                if (to_save) cudaMemcpy(sv, ptrs[k], sz[k], cudaMemcpyDeviceToDevice);
-                else cudaMemcpy(ptrs[k], sv, sz[k], cudaMemcpyDeviceToDevice);
+                if (to_save) prk::copy_now(sv, ptrs[k], sz[k], cudaMemcpyDeviceToDevice, b->stream);
+                else prk::copy_now(ptrs[k], sv, sz[k], cudaMemcpyDeviceToDevice, b->stream);
                 off += sz[k];
             }
         }
@@ -978,7 +980,7 @@ extern "C" int pr_batch_autotune(pr_batch* b)
         double ms_sum = 0;
         for (int rep = 0; rep < 2; ++rep) {
             copy_all(false);
-            cudaMemcpy(b->d_state, st.data(), sizeof(InstState) * b->n, cudaMemcpyHostToDevice);
+            prk::copy_now(b->d_state, st.data(), sizeof(InstState) * b->n, cudaMemcpyHostToDevice, b->stream);
             cudaEventRecord(e0, b->stream);
             rc = enqueue_run(b, steps, 0, b->stream, false);
             cudaEventRecord(e1, b->stream);
@@ -1006,7 +1008,7 @@ extern "C" int pr_batch_autotune(pr_batch* b)
         rc2 = default_layout(b);
     }
     copy_all(false);
-    cudaMemcpy(b->d_state, st.data(), sizeof(InstState) * b->n, cudaMemcpyHostToDevice);
+    prk::copy_now(b->d_state, st.data(), sizeof(InstState) * b->n, cudaMemcpyHostToDevice, b->stream);
     cudaFree(save);
     if (rc == PR_OK && rc2 == PR_OK && best_c >= 0)
         for (int i = 0; i < b->n; ++i) b->tuned[i] = 1;
@@ -1148,7 +1150,7 @@ static int take_ctx_status(pr_ctx* c)
     CCUDA(c, cudaMemcpy(&st, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost));
     int rc = c->ff ? prf::take_status(c->ff) : take_status(c->fine, c->fine->stream);
     if (st != 0) {
-        cudaMemset(c->dstatus, 0, sizeof(int));
+        prk::zero_now(c->dstatus, sizeof(int), ctx_stream(c));
         return cfail(c, st, st == PR_ENONPHYS ? "coarse propagator met a non-physical state" : "coarse status %d", st);
     }
     if (rc) return cfail(c, rc, "%s", c->ff ? c->ff->err.c_str() : c->fine->err.c_str());
@@ -1258,8 +1260,8 @@ static int ctx_create(pr_ctx** out, const pr_grid* g, const pr_velocity* v, doub
     c->live.assign(c->n_res, 0);
     for (int b = 0; b < c->n_res; ++b) bind_slice(c, b, b + 1);
     cudaError_t ue = force ? prf::upload(c->ff, 0, c->n_res, c->ff->stream)
-                           : cudaMemcpy(c->fine->d_inst, c->fine->h.data(), sizeof(Inst) * c->n_res,
-                                        cudaMemcpyHostToDevice);
+                           : prk::copy_now(c->fine->d_inst, c->fine->h.data(), sizeof(Inst) * c->n_res,
+                                           cudaMemcpyHostToDevice, c->fine->stream);
     if (ue != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
         free_ctx(c);
         return init_fail(PR_ECUDA, "descriptor upload");
@@ -1410,11 +1412,11 @@ int pr_load(pr_ctx* c, const char* path)
         if (!std::isfinite(e)) return cfail(c, PR_EINVAL, "%s holds a non-finite error", path);
     cudaStream_t s = ctx_stream(c);
     CCUDA(c, cudaStreamSynchronize(s));
-    CCUDA(c, cudaMemcpy(c->dU, U.data(), sizeof(double) * lvl, cudaMemcpyHostToDevice));
-    CCUDA(c, cudaMemcpy(c->dGs, G.data(), sizeof(double) * lvl, cudaMemcpyHostToDevice));
-    CCUDA(c, cudaMemcpy(c->derr, err.data(), sizeof(double) * err.size(), cudaMemcpyHostToDevice));
+    CCUDA(c, prk::copy_now(c->dU, U.data(), sizeof(double) * lvl, cudaMemcpyHostToDevice, s));
+    CCUDA(c, prk::copy_now(c->dGs, G.data(), sizeof(double) * lvl, cudaMemcpyHostToDevice, s));
+    CCUDA(c, prk::copy_now(c->derr, err.data(), sizeof(double) * err.size(), cudaMemcpyHostToDevice, s));
     const int next = k + 1;  // the device counter holds the iteration the next sweep runs
-    CCUDA(c, cudaMemcpy(c->dk, &next, sizeof(int), cudaMemcpyHostToDevice));
+    CCUDA(c, prk::copy_now(c->dk, &next, sizeof(int), cudaMemcpyHostToDevice, s));
     c->k = k;
     c->initialized = true;
     std::fill(c->live.begin(), c->live.end(), 0);
@@ -1625,7 +1627,7 @@ static int build_graph(pr_ctx* c)
     pr_batch* b = c->fine;
     cudaStream_t s = b->stream;
     for (int bi = 0; bi < c->n_res; ++bi) bind_slice(c, bi, bi + 1);
-    CCUDA(c, cudaMemcpy(b->d_inst, b->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice));
+    CCUDA(c, prk::copy_now(b->d_inst, b->h.data(), sizeof(Inst) * c->n_res, cudaMemcpyHostToDevice, s));
     CCUDA(c, cudaStreamSynchronize(s));
     c->descs_dirty = false;
     CCUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -2003,9 +2005,11 @@ int pr_multi_create(pr_multi** out, pr_ctx* const* ctxs, int n_ctx, const pr_ins
     const prk::Active act[2] = {{0, m->n_sl}, {m->n_sl, m->n_sl + n_extra}};
     bool ok = cudaMalloc(&m->d_n, sizeof(int) * std::max(1, m->n_sl)) == cudaSuccess &&
               cudaMalloc(&m->d_act, sizeof act) == cudaSuccess &&
-              cudaMemcpy(m->d_n, nidx.data(), sizeof(int) * m->n_sl, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(m->d_act, act, sizeof act, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(m->b->d_inst, m->b->h.data(), sizeof(Inst) * m->b->n, cudaMemcpyHostToDevice) == cudaSuccess;
+              prk::copy_now(m->d_n, nidx.data(), sizeof(int) * m->n_sl, cudaMemcpyHostToDevice, m->b->stream) ==
+                  cudaSuccess &&
+              prk::copy_now(m->d_act, act, sizeof act, cudaMemcpyHostToDevice, m->b->stream) == cudaSuccess &&
+              prk::copy_now(m->b->d_inst, m->b->h.data(), sizeof(Inst) * m->b->n, cudaMemcpyHostToDevice,
+                            m->b->stream) == cudaSuccess;
     m->side.assign(n_ctx, nullptr);
     m->ev.assign(n_ctx + 1, nullptr);
     for (int p = 0; p < n_ctx && ok; ++p) ok = cudaStreamCreateWithFlags(&m->side[p], cudaStreamNonBlocking) == cudaSuccess;
