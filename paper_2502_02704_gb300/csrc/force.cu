@@ -1348,6 +1348,20 @@ __device__ __forceinline__ float mmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double mmin(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double mmax(double a, double b) { return fmax(a, b); }
 
+// Packed float32 pairs (two (v_y, v_z) lanes per instruction; IEEE
+// round-to-nearest in each lane, so each lane's value is the scalar
+// operation's): lanes 2p, 2p+1 of a row, a - b as b (-1) + a (exact product,
+// one rounding), the limiters per lane.
+__device__ __forceinline__ float2 f2at(const float* x, int p) { return make_float2(x[2 * p], x[2 * p + 1]); }
+__device__ __forceinline__ void f2put(float* x, int p, float2 v)
+{
+    x[2 * p] = v.x;
+    x[2 * p + 1] = v.y;
+}
+__device__ __forceinline__ float2 splat(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 pmm2(float2 a, float2 b) { return make_float2(mm2(a.x, b.x), mm2(a.y, b.y)); }
+
 // Sums of one column of f^{n+1} (values h of its rows) with the limited
 // half-sum values g = h +- s/2 (sign + for rows with v_x > 0).
 template <typename T, int VEC>
@@ -1369,12 +1383,28 @@ __device__ __forceinline__ void fu_row_m(FuAccM<T, VEC>& s, const T (&h)[VEC], c
                                          int nvx)
 {
     T vs = T(0), gs = T(0);
+    if constexpr (sizeof(T) == sizeof(float)) {
+        // in lane pairs; the row sums add the pair's two lanes last
+        float2 vs2 = f2at(h, 0), gs2 = f2at(g, 0);
 #pragma unroll
-    for (int l = 0; l < VEC; ++l) {
-        s.S0[l] += h[l];
-        s.Tx[l] = tfma(vx, g[l], s.Tx[l]);
-        vs += h[l];
-        gs += g[l];
+        for (int p = 0; p < VEC / 2; ++p) {
+            f2put(s.S0, p, __fadd2_rn(f2at(s.S0, p), f2at(h, p)));
+            f2put(s.Tx, p, __ffma2_rn(splat(vx), f2at(g, p), f2at(s.Tx, p)));
+            if (p > 0) {
+                vs2 = __fadd2_rn(vs2, f2at(h, p));
+                gs2 = __fadd2_rn(gs2, f2at(g, p));
+            }
+        }
+        vs = vs2.x + vs2.y;
+        gs = gs2.x + gs2.y;
+    } else {
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+            s.S0[l] += h[l];
+            s.Tx[l] = tfma(vx, g[l], s.Tx[l]);
+            vs += h[l];
+            gs += g[l];
+        }
     }
     const T vx2 = vx * vx;
     s.R1 = tfma(vx, vs, s.R1);
@@ -1429,28 +1459,56 @@ __device__ __forceinline__ void fu_pass_m(const T* __restrict__ cen, const T* __
             const Pack<T, VEC> a1 = ldv<T, VEC>(x1s + o + (size_t)i * nvp2);
             const Pack<T, VEC> af = ldv<T, VEC>(xfs + o + (size_t)i * nvp2);
             const Pack<T, VEC> ad = ldv<T, VEC>(xds + o + (size_t)i * nvp2);
-            T v[VEC];
+            T v[VEC], dn[VEC];
+            if constexpr (sizeof(T) == sizeof(float)) {
+                // lane pairs: the same operations, two lanes per instruction
+                // (the limiters, scalar, as clamps: minmod(e, x) = x clamped
+                // to [min(e, 0), max(e, 0)])
+                const bool inner = !BND || (r > 0 && r < nvx - 1);
 #pragma unroll
-            for (int l = 0; l < VEC; ++l) {
-                const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
-                const T e = cc - a1.x[l], d1 = ad.x[l] - cc, d2 = a1.x[l] - af.x[l];
-                T D;
-                if constexpr (sizeof(T) == sizeof(float)) {
-                    const T lo = mmin(e, T(0)), hi = mmax(e, T(0));  // minmod(e, x) = x clamped to [lo, hi]
-                    D = tfma(T(0.5), mmin(mmax(d1, lo), hi) - mmin(mmax(d2, lo), hi), e);
-                } else {
-                    D = tfma(T(0.5), mm2(e, d1) - mm2(e, d2), e);
+                for (int p = 0; p < VEC / 2; ++p) {
+                    const float2 cc = f2at(cv.x, p), u = f2at(up.x, p), d = f2at(dnv.x, p), a1p = f2at(a1.x, p);
+                    const float2 e = psub(cc, a1p), d1 = psub(f2at(ad.x, p), cc), d2 = psub(a1p, f2at(af.x, p));
+                    const float lx = mmin(e.x, 0.0f), hx = mmax(e.x, 0.0f), ly = mmin(e.y, 0.0f), hy = mmax(e.y, 0.0f);
+                    const float2 c1 = make_float2(mmin(mmax(d1.x, lx), hx), mmin(mmax(d1.y, ly), hy));
+                    const float2 c2 = make_float2(mmin(mmax(d2.x, lx), hx), mmin(mmax(d2.y, ly), hy));
+                    float2 fs = __ffma2_rn(splat(-nvx_), __ffma2_rn(splat(0.5f), psub(c1, c2), e), cc);
+                    if (inner) {
+                        fs = __ffma2_rn(splat(-k.gE), psub(u, d), fs);
+                        fs = __ffma2_rn(splat(k.gM), __ffma2_rn(splat(-2.0f), cc, __fadd2_rn(u, d)), fs);
+                    } else {
+                        float fl[2] = {fs.x, fs.y};
+                        const float cl[2] = {cc.x, cc.y}, ul[2] = {u.x, u.y}, dl[2] = {d.x, d.y};
+#pragma unroll
+                        for (int l = 0; l < 2; ++l) {
+                            const float Gr = r < nvx - 1 ? k.hE * (cl[l] + ul[l]) - k.hEm * (ul[l] - cl[l]) : 0.0f;
+                            const float Gl = r > 0 ? k.hE * (dl[l] + cl[l]) - k.hEm * (cl[l] - dl[l]) : 0.0f;
+                            fl[l] = tfma(-k.nuv, Gr - Gl, fl[l]);
+                        }
+                        fs = make_float2(fl[0], fl[1]);
+                    }
+                    const float2 vp = __ffma2_rn(splat(k.a), fs, __fmul2_rn(splat(ve.y), f2at(myz, p)));
+                    f2put(v, p, vp);
+                    f2put(dn, p, psub(vp, f2at(h1[i], p)));
                 }
-                T fs = tfma(-nvx_, D, cc);
-                if (!BND || (r > 0 && r < nvx - 1)) {
-                    fs = tfma(-k.gE, u - d, fs);
-                    fs = tfma(k.gM, tfma(T(-2), cc, u + d), fs);
-                } else {
-                    const T Gr = r < nvx - 1 ? k.hE * (cc + u) - k.hEm * (u - cc) : T(0);
-                    const T Gl = r > 0 ? k.hE * (d + cc) - k.hEm * (cc - d) : T(0);
-                    fs = tfma(-k.nuv, Gr - Gl, fs);
+            } else {
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) {
+                    const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                    const T e = cc - a1.x[l], d1 = ad.x[l] - cc, d2 = a1.x[l] - af.x[l];
+                    const T D = tfma(T(0.5), mm2(e, d1) - mm2(e, d2), e);
+                    T fs = tfma(-nvx_, D, cc);
+                    if (!BND || (r > 0 && r < nvx - 1)) {
+                        fs = tfma(-k.gE, u - d, fs);
+                        fs = tfma(k.gM, tfma(T(-2), cc, u + d), fs);
+                    } else {
+                        const T Gr = r < nvx - 1 ? k.hE * (cc + u) - k.hEm * (u - cc) : T(0);
+                        const T Gl = r > 0 ? k.hE * (d + cc) - k.hEm * (cc - d) : T(0);
+                        fs = tfma(-k.nuv, Gr - Gl, fs);
+                    }
+                    v[l] = tfma(k.a, fs, ve.y * myz[l]);
+                    dn[l] = v[l] - h1[i][l];
                 }
-                v[l] = tfma(k.a, fs, ve.y * myz[l]);
             }
             if (out) {
                 Pack<T, VEC> pv;
@@ -1458,13 +1516,16 @@ __device__ __forceinline__ void fu_pass_m(const T* __restrict__ cen, const T* __
                 for (int l = 0; l < VEC; ++l) pv.x[l] = v[l];
                 stv<T, VEC>(out + (size_t)r * nvp2, pv);
             }
-            T dn[VEC];
-#pragma unroll
-            for (int l = 0; l < VEC; ++l) dn[l] = v[l] - h1[i][l];
             if (sums) {
                 T g[VEC];
+                if constexpr (sizeof(T) == sizeof(float)) {
 #pragma unroll
-                for (int l = 0; l < VEC; ++l) g[l] = tfma(hs, mm2(dd[i][l], dn[l]), h1[i][l]);
+                    for (int p = 0; p < VEC / 2; ++p)
+                        f2put(g, p, __ffma2_rn(splat(hs), pmm2(f2at(dd[i], p), f2at(dn, p)), f2at(h1[i], p)));
+                } else {
+#pragma unroll
+                    for (int l = 0; l < VEC; ++l) g[l] = tfma(hs, mm2(dd[i][l], dn[l]), h1[i][l]);
+                }
                 fu_row_m<BND>(acc, h1[i], g, vx, r, nvx);
             }
 #pragma unroll
