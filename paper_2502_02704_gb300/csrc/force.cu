@@ -865,6 +865,19 @@ __device__ __forceinline__ void fu_params(const double* tot, double* par, const 
     maxwell_params_d(t, par, report, status);
 }
 
+// Packed float32 pairs (two (v_y, v_z) lanes per instruction; IEEE
+// round-to-nearest in each lane, so each lane's value is the scalar
+// operation's): lanes 2p, 2p+1 of a row, and a - b as b (-1) + a (exact
+// product, one rounding).
+__device__ __forceinline__ float2 f2at(const float* x, int p) { return make_float2(x[2 * p], x[2 * p + 1]); }
+__device__ __forceinline__ void f2put(float* x, int p, float2 v)
+{
+    x[2 * p] = v.x;
+    x[2 * p + 1] = v.y;
+}
+__device__ __forceinline__ float2 splat(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
 // Per-thread sums of f^{n+1} over the thread's rows: per lane sum f and
 // sum v_x f; per row (vs = the row's lane sum) sum v_x vs, v_x^2 vs, v_x^3 vs
 // and the first / last row's vs.
@@ -1034,13 +1047,25 @@ __device__ __forceinline__ void fu_pass(const T* __restrict__ cen, const T* __re
         const Pack<T, VEC> x1 = ldv<T, VEC>(np);
         Pack<T, VEC> v;
         if (!BND || (r > 0 && r < nvx - 1)) {
+            if constexpr (sizeof(T) == sizeof(float)) {
+                // lane pairs: the same operations, two lanes per instruction
 #pragma unroll
-            for (int l = 0; l < VEC; ++l) {
-                const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
-                T fs = tfma(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
-                fs = tfma(-k.gE, u - d, fs);
-                fs = tfma(k.gM, tfma(T(-2), cc, u + d), fs);
-                v.x[l] = tfma(k.a, fs, ve.y * myz[l]);
+                for (int p = 0; p < VEC / 2; ++p) {
+                    const float2 cc = f2at(cv.x, p), u = f2at(up.x, p), d = f2at(dnv.x, p), xl = f2at(x1.x, p);
+                    float2 fs = __ffma2_rn(splat(-nvx_), POS ? psub(cc, xl) : psub(xl, cc), cc);
+                    fs = __ffma2_rn(splat(-k.gE), psub(u, d), fs);
+                    fs = __ffma2_rn(splat(k.gM), __ffma2_rn(splat(-2.0f), cc, __fadd2_rn(u, d)), fs);
+                    f2put(v.x, p, __ffma2_rn(splat(k.a), fs, __fmul2_rn(splat(ve.y), f2at(myz, p))));
+                }
+            } else {
+#pragma unroll
+                for (int l = 0; l < VEC; ++l) {
+                    const T cc = cv.x[l], u = up.x[l], d = dnv.x[l];
+                    T fs = tfma(-nvx_, POS ? cc - x1.x[l] : x1.x[l] - cc, cc);
+                    fs = tfma(-k.gE, u - d, fs);
+                    fs = tfma(k.gM, tfma(T(-2), cc, u + d), fs);
+                    v.x[l] = tfma(k.a, fs, ve.y * myz[l]);
+                }
             }
         } else {
 #pragma unroll
@@ -1348,18 +1373,7 @@ __device__ __forceinline__ float mmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double mmin(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ double mmax(double a, double b) { return fmax(a, b); }
 
-// Packed float32 pairs (two (v_y, v_z) lanes per instruction; IEEE
-// round-to-nearest in each lane, so each lane's value is the scalar
-// operation's): lanes 2p, 2p+1 of a row, a - b as b (-1) + a (exact product,
-// one rounding), the limiters per lane.
-__device__ __forceinline__ float2 f2at(const float* x, int p) { return make_float2(x[2 * p], x[2 * p + 1]); }
-__device__ __forceinline__ void f2put(float* x, int p, float2 v)
-{
-    x[2 * p] = v.x;
-    x[2 * p + 1] = v.y;
-}
-__device__ __forceinline__ float2 splat(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// The limiter per lane of a packed pair.
 __device__ __forceinline__ float2 pmm2(float2 a, float2 b) { return make_float2(mm2(a.x, b.x), mm2(a.y, b.y)); }
 
 // Sums of one column of f^{n+1} (values h of its rows) with the limited
