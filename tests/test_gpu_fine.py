@@ -233,6 +233,39 @@ def test_manual_tile_widths_keep_results(tx):
     assert moment_rel_err(V, Vo) < TOL_FP64
 
 
+@pytest.mark.parametrize("precision", [pr.PR_MIXED, pr.PR_FP64])
+@pytest.mark.parametrize("bc,scheme,nv", [
+    (pr.PR_BC_PERIODIC, pr.PR_MUSCL, 16),
+    (pr.PR_BC_OUTFLOW, pr.PR_MUSCL, 16),
+    (pr.PR_BC_REFLECT, pr.PR_MUSCL, 16),
+    (pr.PR_BC_OUTFLOW, pr.PR_MUSCL, 24),
+    (pr.PR_BC_PERIODIC, pr.PR_UPWIND, 16),
+    (pr.PR_BC_OUTFLOW, pr.PR_MUSCL, 12),   # four velocities per thread
+])
+def test_tile_width_and_march_direction_give_the_same_bits(precision, bc, scheme, nv):
+    # odd tiles march right to left, so a column changes direction with the
+    # tile width: each column's f* and moment sums must come out the same
+    # whatever the width (the upwind side's code paths round alike)
+    nx = 100
+    dt = pr.fine_dt(nx, nv, 8.0)
+    U = _profile(bc, nx)
+    ref = None
+    for tx in (32, 16, 8):
+        b = pr.pr_batch_create([pr.instance(nx, nv, dt, bc=bc, eps=1e-2, scheme=scheme)], precision)
+        try:
+            pr.pr_batch_set_tile(b, tx)
+            pr.pr_batch_set_initial(b, 0, U)
+            pr.pr_batch_run(b, 3)
+            got = (pr.pr_batch_get_f(b, 0), pr.pr_batch_moments(b, 0))
+        finally:
+            pr.pr_batch_destroy(b)
+        if ref is None:
+            ref = got
+        else:
+            assert np.array_equal(got[0], ref[0]), tx
+            assert np.array_equal(got[1], ref[1]), tx
+
+
 def test_autotuned_layout_in_float32_keeps_results():
     # nv = 16: the search covers 8 and 4 velocities per thread in float32
     nx, nv = 160, 16
