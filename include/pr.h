@@ -14,9 +14,9 @@
  * host data synchronise that stream.  Calls that only enqueue work report
  * device-side errors (time-outs, non-physical states) at the next synchronising
  * call on the same object.  Calls that upload host data into an object (initial
- * states, f, a resumed iterate, layouts) queue the copy on the object's stream
- * and finish it before they return, so work queued next on that stream sees
- * the data.
+ * states, f, a resumed iterate, layouts) queue the copy on the object's own
+ * stream ahead of the work they enqueue, so work queued next on that stream
+ * sees the data; the host array may be reused as soon as the call returns.
  *
  * Layouts (row-major, float64 unless stated):
  *   primitive state  U[5][nx] = (rho, u_x, u_y, u_z, theta)         (Def. 1)
