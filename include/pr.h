@@ -16,7 +16,10 @@
  * call on the same object.  Calls that upload host data into an object (initial
  * states, f, a resumed iterate, layouts) queue the copy on the object's own
  * stream ahead of the work they enqueue, so work queued next on that stream
- * sees the data; the host array may be reused as soon as the call returns.
+ * sees the data; the host array may be reused as soon as the call returns.  A
+ * caller that passes its own stream after calls that used the object's stream
+ * (set-up, uploads) orders the two itself, e.g. with an event or a
+ * synchronisation; the library does not join streams.
  *
  * Layouts (row-major, float64 unless stated):
  *   primitive state  U[5][nx] = (rho, u_x, u_y, u_z, theta)         (Def. 1)
